@@ -1,0 +1,853 @@
+/*
+ * dpcs_oracle.c -- FP64 CPU oracle for the DPCS projector-camera path tracer.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or call
+ * this file: only the tests, the smoke check and the benchmark's CPU-baseline
+ * leg use it.  It shares no code, header, table or constant generator with the
+ * CUDA library.
+ *
+ * What it computes (arxiv 2503.12174, "DPCS: Path Tracing-Based Differentiable
+ * Projector-Camera Systems", Sec. 3):
+ *   - Eq. 1   PRF:  Ep = Gp * Ip^gamma_p                      (prf_texel)
+ *   - Eq. 2   projector radiance Lp = Ep / phi, folded into k (nee)
+ *   - Eq. 3   rendering equation, estimated by Eq. 10          (trace_sample)
+ *   - Eq. 4   camera irradiance = mean over pixel samples      (or_render)
+ *   - Eq. 5   CRF + white balance: Ic = (Gc w Ec)^gamma_c      (crf)
+ *   - Eq. 6   projection xc = Kc xs, xp = Kp [Rp|tp] xs        (camera ray, nee)
+ *   - Eq. 12  radiance clipping (optional, off when clip == 0)
+ *   - the analytic adjoint of the same estimator with the sampled directions
+ *     held fixed (detached sampling), used by projector compensation (Eq. 13)
+ *     and scene-parameter fitting (Eq. 9).
+ *
+ * Readings where the paper is silent (each one is listed in the design notes):
+ *   - the projector is a pinhole point emitter at cp = -Rp^T tp with radiant
+ *     intensity k * Ep(xp) * cos(theta_p); irradiance at xs is that times
+ *     cos(theta_s) / r^2.  NEE is the only projector estimator.
+ *   - PRF is applied per projector texel, then Ep is bilinearly interpolated
+ *     with texel centres at (i + 1/2) and clamp-to-edge; outside [0,Wp)x[0,Hp)
+ *     or behind the projector there is no light.
+ *   - camera: pinhole at the world origin, OpenCV axes, pixel (i,j) spans
+ *     [i,i+1)x[j,j+1), box filter by uniform jitter (or pixel centre).
+ *   - BRDF: Lambert rho/pi + ks * D G F / (4 cos_i cos_o), GGX D with
+ *     alpha = r^2 (r clamped to [0.01, 1]), separable Smith G, Schlick F.
+ *     Sampling: probability 1/2 cosine lobe, 1/2 GGX visible normals (Heitz
+ *     2018); when ks == 0 only the cosine lobe is sampled.
+ *   - Russian roulette from vertex rr_start on with a fixed survival q.
+ *   - random numbers: Philox4x32-10 (Salmon et al., SC'11), key = seed,
+ *     counter = (pixel, sample, vertex, 0); u = (x >> 8) * 2^-24.
+ *   - Morton codes in FP32 without contraction (this file is compiled with
+ *     -ffp-contract=off), 10 bits per axis, x in the highest bit of each triple.
+ *
+ * Everything else is FP64.  Ray-triangle tests are brute force over all
+ * triangles in their original order (Moller-Trumbore 1997); ties in t go to the
+ * lowest triangle index.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_PI 3.14159265358979323846
+#define OR_MAX_VERTS 16
+#define OR_RAY_EPS 1e-4
+
+/* ------------------------------------------------------------------------- */
+/* Philox4x32-10, from its published definition (Salmon, Moraes, Dror, Shaw,  */
+/* "Parallel random numbers: as easy as 1, 2, 3", SC'11): each round takes    */
+/* the two 32x32->64 products M0*c0 and M1*c2 and permutes/xors the halves    */
+/* with the counter and the round key; the key is bumped by the Weyl          */
+/* constants between rounds.                                                  */
+/* ------------------------------------------------------------------------- */
+static void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1)
+{
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += W0; k1 += W1; }
+        uint64_t p0 = (uint64_t)M0 * (uint64_t)c[0];
+        uint64_t p1 = (uint64_t)M1 * (uint64_t)c[2];
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c[1] ^ k0;
+        uint32_t n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0; c[1] = lo1; c[2] = n2; c[3] = lo0;
+    }
+}
+
+void or_philox(const uint32_t *ctr, int64_t n, uint64_t seed, uint32_t *out)
+{
+    for (int64_t i = 0; i < n; ++i) {
+        uint32_t c[4] = {ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3]};
+        philox4x32_10(c, (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32));
+        memcpy(out + 4 * i, c, sizeof c);
+    }
+}
+
+/* the four uniforms of one (pixel, sample, vertex) counter, 24-bit exact */
+static void rand4(uint64_t seed, uint32_t pix, uint32_t s, uint32_t b, double u[4])
+{
+    uint32_t c[4] = {pix, s, b, 0u};
+    philox4x32_10(c, (uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32));
+    for (int i = 0; i < 4; ++i) u[i] = (double)(c[i] >> 8) * (1.0 / 16777216.0);
+}
+
+/* ------------------------------------------------------------------------- */
+/* small vector algebra                                                       */
+/* ------------------------------------------------------------------------- */
+typedef struct { double x, y, z; } d3;
+static d3 mk(double x, double y, double z) { d3 r = {x, y, z}; return r; }
+static d3 add(d3 a, d3 b) { return mk(a.x + b.x, a.y + b.y, a.z + b.z); }
+static d3 sub(d3 a, d3 b) { return mk(a.x - b.x, a.y - b.y, a.z - b.z); }
+static d3 scl(d3 a, double s) { return mk(a.x * s, a.y * s, a.z * s); }
+static double dot(d3 a, d3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+static d3 cross(d3 a, d3 b)
+{
+    return mk(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+static double len(d3 a) { return sqrt(dot(a, a)); }
+static d3 nrm(d3 a) { return scl(a, 1.0 / len(a)); }
+static d3 mat3v(const double *M, d3 v)
+{
+    return mk(M[0] * v.x + M[1] * v.y + M[2] * v.z, M[3] * v.x + M[4] * v.y + M[5] * v.z,
+              M[6] * v.x + M[7] * v.y + M[8] * v.z);
+}
+static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+static void inv3(const double *M, double *R)
+{
+    double a = M[0], b = M[1], c = M[2], d = M[3], e = M[4], f = M[5], g = M[6], h = M[7], i = M[8];
+    double A = e * i - f * h, B = -(d * i - f * g), C = d * h - e * g;
+    double det = a * A + b * B + c * C;
+    R[0] = A / det; R[1] = -(b * i - c * h) / det; R[2] = (b * f - c * e) / det;
+    R[3] = B / det; R[4] = (a * i - c * g) / det;  R[5] = -(a * f - c * d) / det;
+    R[6] = C / det; R[7] = -(a * h - b * g) / det; R[8] = (a * e - b * d) / det;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Parameters, view and scene as the callers hand them over                   */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    double gamma_p[3], gain_p;    /* Eq. 1 */
+    double gamma_c[3], gain_c;    /* Eq. 5 */
+    double wb[3];                 /* Eq. 5 white balance */
+    double k_proj;                /* Eq. 2 / Eq. 12 projector scale k (plays 1/phi) */
+    double ks, f0;                /* specular lobe weight and Schlick F0 */
+    int32_t rr_start;             /* first vertex subject to Russian roulette, 0 = off */
+    double rr_q;                  /* survival probability */
+    double clip;                  /* Eq. 12 clamp, 0 = off */
+    int32_t jitter;               /* 1 = box-filter jitter, 0 = pixel centre */
+} or_params;
+
+typedef struct {
+    double Kc[9]; int32_t Hc, Wc;                 /* camera at the origin (Eq. 6) */
+    double Kp[9], Rp[9], tp[3]; int32_t Hp, Wp;   /* projector (Eq. 6) */
+} or_view;
+
+typedef struct {
+    int T;
+    d3 *v0, *e1, *e2; /* FP64 copies of the FP32 input: differences are exact */
+    double *uv;       /* 6 per triangle */
+} dscene;
+
+static void scene_make(dscene *S, const float *verts, const int32_t *tris, int32_t T, const float *uv)
+{
+    S->T = T;
+    S->v0 = (d3 *)malloc(sizeof(d3) * (size_t)(T > 0 ? T : 1));
+    S->e1 = (d3 *)malloc(sizeof(d3) * (size_t)(T > 0 ? T : 1));
+    S->e2 = (d3 *)malloc(sizeof(d3) * (size_t)(T > 0 ? T : 1));
+    S->uv = (double *)malloc(sizeof(double) * 6 * (size_t)(T > 0 ? T : 1));
+    for (int i = 0; i < T; ++i) {
+        const float *a = verts + 3 * tris[3 * i], *b = verts + 3 * tris[3 * i + 1], *c = verts + 3 * tris[3 * i + 2];
+        d3 A = mk(a[0], a[1], a[2]), B = mk(b[0], b[1], b[2]), C = mk(c[0], c[1], c[2]);
+        S->v0[i] = A; S->e1[i] = sub(B, A); S->e2[i] = sub(C, A);
+        for (int k = 0; k < 3; ++k) {
+            S->uv[6 * i + 2 * k] = uv[2 * tris[3 * i + k]];
+            S->uv[6 * i + 2 * k + 1] = uv[2 * tris[3 * i + k] + 1];
+        }
+    }
+}
+static void scene_free(dscene *S) { free(S->v0); free(S->e1); free(S->e2); free(S->uv); }
+
+/* Moller-Trumbore (1997), two-sided, t in (tmin, tmax) */
+static int isect(const dscene *S, int i, d3 o, d3 d, double tmin, double tmax, double *t, double *bu, double *bv)
+{
+    d3 p = cross(d, S->e2[i]);
+    double det = dot(S->e1[i], p);
+    if (det == 0.0) return 0;
+    double inv = 1.0 / det;
+    d3 s = sub(o, S->v0[i]);
+    double u = dot(s, p) * inv;
+    if (u < 0.0 || u > 1.0) return 0;
+    d3 q = cross(s, S->e1[i]);
+    double v = dot(d, q) * inv;
+    if (v < 0.0 || u + v > 1.0) return 0;
+    double tt = dot(S->e2[i], q) * inv;
+    if (!(tt > tmin && tt < tmax)) return 0;
+    *t = tt; *bu = u; *bv = v;
+    return 1;
+}
+
+/* brute-force closest hit; strict '<' keeps the lowest index on ties */
+static int closest(const dscene *S, d3 o, d3 d, double tmax, double *t, double *bu, double *bv)
+{
+    int best = -1;
+    double bt = tmax, tu = 0, tv = 0;
+    for (int i = 0; i < S->T; ++i) {
+        double tt, uu, vv;
+        if (isect(S, i, o, d, 0.0, bt, &tt, &uu, &vv) && tt < bt) { bt = tt; best = i; tu = uu; tv = vv; }
+    }
+    if (best >= 0) { *t = bt; *bu = tu; *bv = tv; }
+    return best;
+}
+
+static int occluded(const dscene *S, d3 o, d3 d, double tmax)
+{
+    for (int i = 0; i < S->T; ++i) {
+        double tt, uu, vv;
+        if (isect(S, i, o, d, 0.0, tmax, &tt, &uu, &vv)) return 1;
+    }
+    return 0;
+}
+
+void or_closest(const float *verts, int32_t V, const int32_t *tris, int32_t T, const float *uv,
+                const double *o, const double *d, int64_t n, double *t_out, int32_t *tri_out)
+{
+    (void)V;
+    dscene S;
+    scene_make(&S, verts, tris, T, uv);
+    for (int64_t r = 0; r < n; ++r) {
+        double t = 0, bu, bv;
+        int h = closest(&S, mk(o[3 * r], o[3 * r + 1], o[3 * r + 2]), mk(d[3 * r], d[3 * r + 1], d[3 * r + 2]),
+                        INFINITY, &t, &bu, &bv);
+        tri_out[r] = h;
+        t_out[r] = h >= 0 ? t : INFINITY;
+    }
+    scene_free(&S);
+}
+
+/* ------------------------------------------------------------------------- */
+/* LBVH reference (integer work must match bit for bit):                       */
+/* Morton codes of FP32 centroids, sort of (code, index), binary radix tree   */
+/* over the sorted keys built top-down from its definition (each internal     */
+/* node splits its key range where the highest differing bit flips; keys are  */
+/* augmented by their sorted position), AABBs as FP32 unions.  Node numbering */
+/* follows Karras (HPG 2012): the root is 0, a left child that is internal is */
+/* numbered by its last key, a right child by its first key.                  */
+/* ------------------------------------------------------------------------- */
+static uint32_t expand10(uint32_t v)
+{
+    uint32_t r = 0;
+    for (int i = 0; i < 10; ++i) r |= ((v >> i) & 1u) << (3 * i);
+    return r;
+}
+
+void or_morton(const float *verts, const int32_t *tris, int32_t T, uint32_t *codes)
+{
+    if (T <= 0) return;
+    float *c = (float *)malloc(sizeof(float) * 3 * (size_t)T);
+    const float third = 1.0f / 3.0f;
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int i = 0; i < T; ++i)
+        for (int k = 0; k < 3; ++k) {
+            float a = verts[3 * tris[3 * i] + k], b = verts[3 * tris[3 * i + 1] + k], e = verts[3 * tris[3 * i + 2] + k];
+            float s = a + b;
+            s = s + e;
+            float m = s * third;
+            c[3 * i + k] = m;
+            if (m < lo[k]) lo[k] = m;
+            if (m > hi[k]) hi[k] = m;
+        }
+    float inv[3];
+    for (int k = 0; k < 3; ++k) {
+        float ext = hi[k] - lo[k];
+        inv[k] = ext > 0.0f ? 1.0f / ext : 0.0f;
+    }
+    for (int i = 0; i < T; ++i) {
+        uint32_t q[3];
+        for (int k = 0; k < 3; ++k) {
+            float nrmd = (c[3 * i + k] - lo[k]) * inv[k];
+            float sc = nrmd * 1024.0f;
+            float f = floorf(sc);
+            if (f < 0.0f) f = 0.0f;
+            if (f > 1023.0f) f = 1023.0f;
+            q[k] = (uint32_t)f;
+        }
+        codes[i] = (expand10(q[0]) << 2) | (expand10(q[1]) << 1) | expand10(q[2]);
+    }
+    free(c);
+}
+
+typedef struct { uint32_t code; int32_t idx; } kv;
+static int kv_cmp(const void *a, const void *b)
+{
+    const kv *x = (const kv *)a, *y = (const kv *)b;
+    if (x->code != y->code) return x->code < y->code ? -1 : 1;
+    return x->idx < y->idx ? -1 : (x->idx > y->idx);
+}
+
+static int clz64(uint64_t x)
+{
+    if (x == 0) return 64;
+    int n = 0;
+    while (!(x & 0x8000000000000000ull)) { x <<= 1; ++n; }
+    return n;
+}
+
+typedef struct {
+    const uint32_t *code;   /* sorted codes */
+    int32_t *child;         /* 2 per internal node; >= 0 internal, < 0 leaf ~pos */
+} radix_ctx;
+
+static uint64_t akey(const radix_ctx *R, int i) { return ((uint64_t)R->code[i] << 32) | (uint32_t)i; }
+
+static void radix_build(radix_ctx *R, int first, int last, int id)
+{
+    int common = clz64(akey(R, first) ^ akey(R, last));
+    int split = first;
+    for (int s = first; s < last; ++s)
+        if (clz64(akey(R, first) ^ akey(R, s)) > common) split = s;
+    int left = (split == first) ? ~split : split;
+    int right = (split + 1 == last) ? ~(split + 1) : split + 1;
+    R->child[2 * id] = left;
+    R->child[2 * id + 1] = right;
+    if (left >= 0) radix_build(R, first, split, left);
+    if (right >= 0) radix_build(R, split + 1, last, right);
+}
+
+/* box of child reference c: leaf -> triangle bounds, internal -> union */
+static void ref_box(const float *verts, const int32_t *tris, const int32_t *order, const int32_t *child, int c,
+                    float b[6])
+{
+    if (c < 0) {
+        int t = order[~c];
+        for (int k = 0; k < 3; ++k) {
+            float x0 = verts[3 * tris[3 * t] + k], x1 = verts[3 * tris[3 * t + 1] + k], x2 = verts[3 * tris[3 * t + 2] + k];
+            float lo = x0 < x1 ? x0 : x1, hi = x0 > x1 ? x0 : x1;
+            lo = lo < x2 ? lo : x2; hi = hi > x2 ? hi : x2;
+            b[k] = lo; b[3 + k] = hi;
+        }
+        return;
+    }
+    float l[6], r[6];
+    ref_box(verts, tris, order, child, child[2 * c], l);
+    ref_box(verts, tris, order, child, child[2 * c + 1], r);
+    for (int k = 0; k < 3; ++k) {
+        b[k] = l[k] < r[k] ? l[k] : r[k];
+        b[3 + k] = l[3 + k] > r[3 + k] ? l[3 + k] : r[3 + k];
+    }
+}
+
+/* outputs: sorted codes [T], triangle index per sorted position [T],
+ * child refs [(T-1)*2], child boxes [(T-1)*2*6] as (lo.xyz, hi.xyz) */
+void or_lbvh(const float *verts, const int32_t *tris, int32_t T, uint32_t *sorted_codes, int32_t *order,
+             int32_t *child, float *child_box)
+{
+    if (T <= 0) return;
+    uint32_t *codes = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)T);
+    or_morton(verts, tris, T, codes);
+    kv *a = (kv *)malloc(sizeof(kv) * (size_t)T);
+    for (int i = 0; i < T; ++i) { a[i].code = codes[i]; a[i].idx = i; }
+    qsort(a, (size_t)T, sizeof(kv), kv_cmp);
+    for (int i = 0; i < T; ++i) { sorted_codes[i] = a[i].code; order[i] = a[i].idx; }
+    if (T >= 2) {
+        radix_ctx R = {sorted_codes, child};
+        radix_build(&R, 0, T - 1, 0);
+        for (int n = 0; n < T - 1; ++n)
+            for (int s = 0; s < 2; ++s) ref_box(verts, tris, order, child, child[2 * n + s], child_box + 12 * n + 6 * s);
+    }
+    free(a);
+    free(codes);
+}
+
+/* ------------------------------------------------------------------------- */
+/* BRDF (Lambert + GGX), evaluation, derivative in roughness, sampling, pdf   */
+/* ------------------------------------------------------------------------- */
+static double alpha_of(double r, double *dadr)
+{
+    double rc = r;
+    double d = 2.0 * r;
+    if (rc < 0.01) { rc = 0.01; d = 0.0; }
+    if (rc > 1.0) { rc = 1.0; d = 0.0; }
+    *dadr = d;
+    return rc * rc;
+}
+
+/* GGX normal distribution D(h) for cos(theta_h) = ch */
+static double ggx_D(double ch, double a)
+{
+    double a2 = a * a;
+    double t = ch * ch * (a2 - 1.0) + 1.0;
+    return a2 / (OR_PI * t * t);
+}
+double or_ggx_D(double ch, double a) { return ggx_D(ch, a); }
+
+/* Smith masking for GGX, G1 = 2c / (c + sqrt(a^2 + (1 - a^2) c^2)) */
+static double ggx_G1(double c, double a)
+{
+    double a2 = a * a;
+    double s = sqrt(a2 + (1.0 - a2) * c * c);
+    return 2.0 * c / (c + s);
+}
+
+/* specular term D G F / (4 ci co) (without ks) and its derivative in alpha */
+static double spec_term(d3 n, d3 wo, d3 wi, double a, double f0, double *dspec_da)
+{
+    double co = dot(n, wo), ci = dot(n, wi);
+    *dspec_da = 0.0;
+    if (co <= 0.0 || ci <= 0.0) return 0.0;
+    d3 h = nrm(add(wo, wi));
+    double ch = dot(n, h);
+    double a2 = a * a;
+    double t = ch * ch * (a2 - 1.0) + 1.0;
+    double D = a2 / (OR_PI * t * t);
+    double si = sqrt(a2 + (1.0 - a2) * ci * ci), so = sqrt(a2 + (1.0 - a2) * co * co);
+    double G = (2.0 * ci / (ci + si)) * (2.0 * co / (co + so));
+    double m = 1.0 - dot(wo, h);
+    if (m < 0.0) m = 0.0;
+    double F = f0 + (1.0 - f0) * m * m * m * m * m;
+    double spec = D * G * F / (4.0 * ci * co);
+    /* d ln D / da = 2/a - 4 a ch^2 / t ; d ln G1 / da = -(a (1 - c^2) / s) / (c + s) */
+    double dlnD = 2.0 / a - 4.0 * a * ch * ch / t;
+    double dlnG = -(a * (1.0 - ci * ci) / si) / (ci + si) - (a * (1.0 - co * co) / so) / (co + so);
+    *dspec_da = spec * (dlnD + dlnG);
+    return spec;
+}
+
+/* f(wo, wi) per channel; *dfdr = d f / d r (same for all channels) */
+static void bsdf_eval(d3 n, d3 wo, d3 wi, const double rho[3], double r, double ks, double f0, double f[3],
+                      double *dfdr)
+{
+    double ci = dot(n, wi), co = dot(n, wo);
+    if (ci <= 0.0 || co <= 0.0) { f[0] = f[1] = f[2] = 0.0; *dfdr = 0.0; return; }
+    double dadr, a = alpha_of(r, &dadr), dsda = 0.0;
+    double sp = ks > 0.0 ? ks * spec_term(n, wo, wi, a, f0, &dsda) : 0.0;
+    for (int j = 0; j < 3; ++j) f[j] = rho[j] / OR_PI + sp;
+    *dfdr = ks > 0.0 ? ks * dsda * dadr : 0.0;
+}
+
+/* Orthonormal basis around n (Duff et al., JCGT 2017); sign taken as n.z >= 0 */
+static void onb(d3 n, d3 *t, d3 *b)
+{
+    double sg = n.z >= 0.0 ? 1.0 : -1.0;
+    double a = -1.0 / (sg + n.z);
+    double bb = n.x * n.y * a;
+    *t = mk(1.0 + sg * n.x * n.x * a, sg * bb, -sg * n.x);
+    *b = mk(bb, sg + n.y * n.y * a, -n.y);
+}
+
+static double spec_prob(double ks) { return ks > 0.0 ? 0.5 : 0.0; }
+
+/* mixture pdf (solid angle) of sampling wi given wo */
+static double bsdf_pdf(d3 n, d3 wo, d3 wi, double r, double ks)
+{
+    double ci = dot(n, wi), co = dot(n, wo);
+    if (ci <= 0.0 || co <= 0.0) return 0.0;
+    double ps = spec_prob(ks);
+    double p = (1.0 - ps) * ci / OR_PI;
+    if (ps > 0.0) {
+        double dadr, a = alpha_of(r, &dadr);
+        d3 h = nrm(add(wo, wi));
+        p += ps * ggx_G1(co, a) * ggx_D(dot(n, h), a) / (4.0 * co);
+    }
+    return p;
+}
+
+/* sample wi: u0 picks the lobe, (u1, u2) the direction; returns 0 on failure */
+static int bsdf_sample(d3 n, d3 wo, double r, double ks, double u0, double u1, double u2, d3 *wi)
+{
+    d3 T, B;
+    onb(n, &T, &B);
+    d3 l;
+    if (u0 >= spec_prob(ks)) {
+        /* cosine-weighted hemisphere */
+        double rr = sqrt(u1), ph = 2.0 * OR_PI * u2;
+        l = mk(rr * cos(ph), rr * sin(ph), sqrt(fmax(0.0, 1.0 - u1)));
+    } else {
+        /* GGX visible-normal sampling (Heitz, JCGT 2018) in the local frame */
+        double dadr, a = alpha_of(r, &dadr);
+        d3 wl = mk(dot(wo, T), dot(wo, B), dot(wo, n));
+        d3 Vh = nrm(mk(a * wl.x, a * wl.y, wl.z));
+        double lsq = Vh.x * Vh.x + Vh.y * Vh.y;
+        d3 T1 = lsq > 0.0 ? scl(mk(-Vh.y, Vh.x, 0.0), 1.0 / sqrt(lsq)) : mk(1.0, 0.0, 0.0);
+        d3 T2 = cross(Vh, T1);
+        double rr = sqrt(u1), ph = 2.0 * OR_PI * u2;
+        double t1 = rr * cos(ph), t2 = rr * sin(ph);
+        double s = 0.5 * (1.0 + Vh.z);
+        t2 = (1.0 - s) * sqrt(fmax(0.0, 1.0 - t1 * t1)) + s * t2;
+        d3 Nh = add(add(scl(T1, t1), scl(T2, t2)), scl(Vh, sqrt(fmax(0.0, 1.0 - t1 * t1 - t2 * t2))));
+        d3 Ne = nrm(mk(a * Nh.x, a * Nh.y, fmax(0.0, Nh.z)));
+        l = sub(scl(Ne, 2.0 * dot(wl, Ne)), wl);
+    }
+    *wi = add(add(scl(T, l.x), scl(B, l.y)), scl(n, l.z));
+    return dot(n, *wi) > 0.0;
+}
+
+/* exported for the BRDF pins */
+void or_bsdf_eval(const double *n, const double *wo, const double *wi, const double *rho, double r, double ks,
+                  double f0, double *f, double *dfdr)
+{
+    bsdf_eval(mk(n[0], n[1], n[2]), mk(wo[0], wo[1], wo[2]), mk(wi[0], wi[1], wi[2]), rho, r, ks, f0, f, dfdr);
+}
+double or_bsdf_pdf(const double *n, const double *wo, const double *wi, double r, double ks)
+{
+    return bsdf_pdf(mk(n[0], n[1], n[2]), mk(wo[0], wo[1], wo[2]), mk(wi[0], wi[1], wi[2]), r, ks);
+}
+int or_bsdf_sample(const double *n, const double *wo, double r, double ks, double u0, double u1, double u2,
+                   double *wi)
+{
+    d3 w;
+    int ok = bsdf_sample(mk(n[0], n[1], n[2]), mk(wo[0], wo[1], wo[2]), r, ks, u0, u1, u2, &w);
+    wi[0] = w.x; wi[1] = w.y; wi[2] = w.z;
+    return ok;
+}
+
+/* ------------------------------------------------------------------------- */
+/* bilinear lookup with texel centres at (i + 1/2), clamp to edge              */
+/* ------------------------------------------------------------------------- */
+static void bilin(double xp, double yp, int W, int H, int idx[4], double w[4])
+{
+    double x = xp - 0.5, y = yp - 0.5;
+    if (x < -1.0) x = -1.0;
+    if (x > (double)W) x = (double)W;
+    if (y < -1.0) y = -1.0;
+    if (y > (double)H) y = (double)H;
+    double fx0 = floor(x), fy0 = floor(y);
+    double fx = x - fx0, fy = y - fy0;
+    int x0 = (int)fx0, y0 = (int)fy0;
+    int xa = clampi(x0, 0, W - 1), xb = clampi(x0 + 1, 0, W - 1);
+    int ya = clampi(y0, 0, H - 1), yb = clampi(y0 + 1, 0, H - 1);
+    idx[0] = ya * W + xa; idx[1] = ya * W + xb; idx[2] = yb * W + xa; idx[3] = yb * W + xb;
+    w[0] = (1.0 - fx) * (1.0 - fy); w[1] = fx * (1.0 - fy); w[2] = (1.0 - fx) * fy; w[3] = fx * fy;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Eq. 1 (PRF) and Eq. 5 (CRF with white balance)                             */
+/* ------------------------------------------------------------------------- */
+static double prf_texel(double ip, double gamma, double gain)
+{
+    return ip > 0.0 ? gain * pow(ip, gamma) : 0.0;
+}
+void or_prf(const double *Ip, int64_t n_texels, const or_params *P, double *Ep)
+{
+    for (int64_t t = 0; t < n_texels; ++t)
+        for (int j = 0; j < 3; ++j) Ep[3 * t + j] = prf_texel(Ip[3 * t + j], P->gamma_p[j], P->gain_p);
+}
+static double crf(double ec, int j, const or_params *P)
+{
+    double a = P->gain_c * P->wb[j] * ec;
+    return a > 0.0 ? pow(a, P->gamma_c[j]) : 0.0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* One camera path (Eq. 10 with NEE to the projector), recording what the     */
+/* adjoint needs                                                              */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    int tex_idx[4]; double tex_w[4];
+    double rho[3];
+    double beta[3];
+    int nee;                      /* NEE light arrived (inside frustum, facing, unoccluded) */
+    int proj_idx[4]; double proj_w[4];
+    double Ep[3], G, fp[3], dfp_dr;
+    int unclipped[3];
+    int cont;                     /* a continuation ray was traced from here */
+    double cw, fi[3], dfi_dr;     /* cos_i / (pdf q), f(wo, wi), d f(wo,wi) / dr */
+} vrec;
+
+typedef struct {
+    const dscene *S;
+    const double *albedo, *rough; int Ht, Wt;
+    const double *Ep; int Hp, Wp;
+    double Kc_inv[9], Kp[9], Rp[9], tp[3], cp[3];
+    const or_params *P;
+    int spp, bounces;
+    uint64_t seed;
+    int Wc;
+} rctx;
+
+/* returns path radiance (RGB) and the vertex records */
+static int trace_sample(const rctx *C, uint32_t pix, uint32_t s, double L[3], vrec *rec)
+{
+    const or_params *P = C->P;
+    double u[4];
+    L[0] = L[1] = L[2] = 0.0;
+    rand4(C->seed, pix, s, 0u, u);
+    double fx = (double)(pix % (uint32_t)C->Wc) + (P->jitter ? u[0] : 0.5);
+    double fy = (double)(pix / (uint32_t)C->Wc) + (P->jitter ? u[1] : 0.5);
+    d3 o = mk(0.0, 0.0, 0.0);
+    d3 d = nrm(mat3v(C->Kc_inv, mk(fx, fy, 1.0)));
+    double beta[3] = {1.0, 1.0, 1.0};
+    d3 cp = mk(C->cp[0], C->cp[1], C->cp[2]);
+    int nv = 0;
+    for (int b = 1; b <= C->bounces; ++b) {
+        double t, bu, bv;
+        int tri = closest(C->S, o, d, INFINITY, &t, &bu, &bv);
+        if (tri < 0) break;
+        vrec *R = &rec[nv++];
+        memset(R, 0, sizeof *R);
+        const dscene *S = C->S;
+        d3 x = add(add(S->v0[tri], scl(S->e1[tri], bu)), scl(S->e2[tri], bv));
+        d3 n = nrm(cross(S->e1[tri], S->e2[tri]));
+        if (dot(n, d) > 0.0) n = scl(n, -1.0);
+        const double *tuv = S->uv + 6 * tri;
+        double w0 = 1.0 - bu - bv;
+        double su = w0 * tuv[0] + bu * tuv[2] + bv * tuv[4];
+        double sv = w0 * tuv[1] + bu * tuv[3] + bv * tuv[5];
+        bilin(su * C->Wt, sv * C->Ht, C->Wt, C->Ht, R->tex_idx, R->tex_w);
+        double r = 0.0;
+        for (int j = 0; j < 3; ++j) R->rho[j] = 0.0;
+        for (int k = 0; k < 4; ++k) {
+            for (int j = 0; j < 3; ++j) R->rho[j] += R->tex_w[k] * C->albedo[3 * R->tex_idx[k] + j];
+            r += R->tex_w[k] * C->rough[R->tex_idx[k]];
+        }
+        for (int j = 0; j < 3; ++j) R->beta[j] = beta[j];
+        d3 wo = scl(d, -1.0);
+
+        /* next-event estimation to the pinhole projector (Eqs. 1, 2, 3, 6) */
+        d3 X = add(mat3v(C->Rp, x), mk(C->tp[0], C->tp[1], C->tp[2]));
+        d3 q = mat3v(C->Kp, X);
+        if (q.z > 0.0 && X.z > 0.0) {
+            double up = q.x / q.z, vp = q.y / q.z;
+            if (up >= 0.0 && up < (double)C->Wp && vp >= 0.0 && vp < (double)C->Hp) {
+                d3 v = sub(cp, x);
+                double r2 = dot(v, v), dist = sqrt(r2);
+                d3 wp = scl(v, 1.0 / dist);
+                double cs = dot(n, wp);
+                if (cs > 0.0) {
+                    double cpz = X.z / len(X);
+                    d3 so = add(x, scl(n, OR_RAY_EPS));
+                    d3 sv = sub(cp, so);
+                    double sd = len(sv);
+                    if (!occluded(S, so, scl(sv, 1.0 / sd), sd - OR_RAY_EPS)) {
+                        R->nee = 1;
+                        bilin(up, vp, C->Wp, C->Hp, R->proj_idx, R->proj_w);
+                        for (int j = 0; j < 3; ++j) {
+                            R->Ep[j] = 0.0;
+                            for (int k = 0; k < 4; ++k) R->Ep[j] += R->proj_w[k] * C->Ep[3 * R->proj_idx[k] + j];
+                        }
+                        R->G = P->k_proj * cpz * cs / r2;
+                        bsdf_eval(n, wo, wp, R->rho, r, P->ks, P->f0, R->fp, &R->dfp_dr);
+                        for (int j = 0; j < 3; ++j) {
+                            double c = beta[j] * R->fp[j] * R->Ep[j] * R->G;
+                            R->unclipped[j] = 1;
+                            if (P->clip > 0.0 && c > P->clip) { c = P->clip; R->unclipped[j] = 0; }
+                            L[j] += c;
+                        }
+                    }
+                }
+            }
+        }
+        if (b == C->bounces) break;
+
+        /* continuation: BSDF sampling, throughput, Russian roulette */
+        rand4(C->seed, pix, s, (uint32_t)b, u);
+        d3 wi;
+        if (!bsdf_sample(n, wo, r, P->ks, u[0], u[1], u[2], &wi)) break;
+        double pdf = bsdf_pdf(n, wo, wi, r, P->ks);
+        if (!(pdf > 0.0)) break;
+        double qrr = 1.0;
+        if (P->rr_start > 0 && b >= P->rr_start) {
+            if (u[3] >= P->rr_q) break;
+            qrr = P->rr_q;
+        }
+        bsdf_eval(n, wo, wi, R->rho, r, P->ks, P->f0, R->fi, &R->dfi_dr);
+        R->cont = 1;
+        R->cw = dot(n, wi) / (pdf * qrr);
+        for (int j = 0; j < 3; ++j) beta[j] *= R->fi[j] * R->cw;
+        o = add(x, scl(n, OR_RAY_EPS));
+        d = wi;
+    }
+    return nv;
+}
+
+static void rctx_make(rctx *C, const dscene *S, const double *albedo, const double *rough, int Ht, int Wt,
+                      const double *Ep, const or_view *Vw, const or_params *P, int spp, int bounces, uint64_t seed)
+{
+    C->S = S; C->albedo = albedo; C->rough = rough; C->Ht = Ht; C->Wt = Wt;
+    C->Ep = Ep; C->Hp = Vw->Hp; C->Wp = Vw->Wp;
+    inv3(Vw->Kc, C->Kc_inv);
+    memcpy(C->Kp, Vw->Kp, sizeof C->Kp);
+    memcpy(C->Rp, Vw->Rp, sizeof C->Rp);
+    memcpy(C->tp, Vw->tp, sizeof C->tp);
+    /* projector centre cp = -Rp^T tp */
+    for (int i = 0; i < 3; ++i)
+        C->cp[i] = -(Vw->Rp[0 * 3 + i] * Vw->tp[0] + Vw->Rp[1 * 3 + i] * Vw->tp[1] + Vw->Rp[2 * 3 + i] * Vw->tp[2]);
+    C->P = P; C->spp = spp; C->bounces = bounces; C->seed = seed; C->Wc = Vw->Wc;
+}
+
+static int set_threads(int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+    return omp_get_max_threads();
+#else
+    (void)nthreads;
+    return 1;
+#endif
+}
+
+int or_num_threads(int nthreads) { return set_threads(nthreads); }
+
+/*
+ * Forward render of the listed pixels (pixel index = y * Wc + x); NULL list =
+ * every pixel.  Ec and Ic are npix x 3.  Returns 0, or -1 on bad arguments.
+ */
+int or_render(const float *verts, const int32_t *tris, int32_t T, const float *uv, const double *albedo,
+              const double *rough, int32_t Ht, int32_t Wt, const double *Ip, const or_view *Vw, const or_params *P,
+              int32_t spp, int32_t bounces, uint64_t seed, const int64_t *pixels, int64_t npix, double *Ec, double *Ic,
+              int32_t nthreads)
+{
+    if (spp <= 0 || bounces < 0 || bounces > OR_MAX_VERTS || Ht <= 0 || Wt <= 0 || Vw->Hp <= 0 || Vw->Wp <= 0)
+        return -1;
+    set_threads(nthreads);
+    dscene S;
+    scene_make(&S, verts, tris, T, uv);
+    int64_t ntex = (int64_t)Vw->Hp * Vw->Wp;
+    double *Ep = (double *)malloc(sizeof(double) * 3 * (size_t)ntex);
+    or_prf(Ip, ntex, P, Ep);
+    rctx C;
+    rctx_make(&C, &S, albedo, rough, Ht, Wt, Ep, Vw, P, spp, bounces, seed);
+    int64_t n = pixels ? npix : (int64_t)Vw->Hc * Vw->Wc;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t i = 0; i < n; ++i) {
+        uint32_t pix = (uint32_t)(pixels ? pixels[i] : i);
+        vrec rec[OR_MAX_VERTS];
+        double sum[3] = {0.0, 0.0, 0.0}, L[3];
+        for (int s = 0; s < spp; ++s) {
+            trace_sample(&C, pix, (uint32_t)s, L, rec);
+            for (int j = 0; j < 3; ++j) sum[j] += L[j];
+        }
+        for (int j = 0; j < 3; ++j) {
+            Ec[3 * i + j] = sum[j] / spp;
+            Ic[3 * i + j] = crf(Ec[3 * i + j], j, P);
+        }
+    }
+    free(Ep);
+    scene_free(&S);
+    return 0;
+}
+
+/*
+ * Adjoint of or_render for the listed pixels: given dLoss/dIc (npix x 3),
+ * accumulates (+=) dLoss/dIp [Hp*Wp*3], dLoss/dalbedo [Ht*Wt*3],
+ * dLoss/drough [Ht*Wt] and dParams [gamma_p(3), Gp, gamma_c(3), Gc, wb(3)].
+ * The forward is recomputed here; sampled directions are held fixed.
+ */
+int or_render_backward(const float *verts, const int32_t *tris, int32_t T, const float *uv, const double *albedo,
+                       const double *rough, int32_t Ht, int32_t Wt, const double *Ip, const or_view *Vw,
+                       const or_params *P, int32_t spp, int32_t bounces, uint64_t seed, const int64_t *pixels,
+                       int64_t npix, const double *dIc, double *dIp, double *dAlbedo, double *dRough, double *dParams,
+                       int32_t nthreads)
+{
+    if (spp <= 0 || bounces < 0 || bounces > OR_MAX_VERTS || Ht <= 0 || Wt <= 0 || Vw->Hp <= 0 || Vw->Wp <= 0)
+        return -1;
+    int nt = set_threads(nthreads);
+    dscene S;
+    scene_make(&S, verts, tris, T, uv);
+    int64_t ntex = (int64_t)Vw->Hp * Vw->Wp, nalb = (int64_t)Ht * Wt;
+    double *Ep = (double *)malloc(sizeof(double) * 3 * (size_t)ntex);
+    or_prf(Ip, ntex, P, Ep);
+    rctx C;
+    rctx_make(&C, &S, albedo, rough, Ht, Wt, Ep, Vw, P, spp, bounces, seed);
+    int64_t n = pixels ? npix : (int64_t)Vw->Hc * Vw->Wc;
+    /* per-thread gradient buffers, summed in thread order afterwards */
+    size_t per = (size_t)(3 * ntex + 3 * nalb + nalb + 3);
+    double *acc = (double *)calloc((size_t)nt * per, sizeof(double));
+    double crf_acc[8] = {0};
+#pragma omp parallel
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        double *gEp = acc + (size_t)tid * per, *gA = gEp + 3 * ntex, *gR = gA + 3 * nalb, *gC = gR + nalb;
+        (void)gC;
+#pragma omp for schedule(static)
+        for (int64_t i = 0; i < n; ++i) {
+            uint32_t pix = (uint32_t)(pixels ? pixels[i] : i);
+            vrec rec[OR_MAX_VERTS];
+            double sum[3] = {0.0, 0.0, 0.0}, L[3];
+            for (int s = 0; s < spp; ++s) {
+                trace_sample(&C, pix, (uint32_t)s, L, rec);
+                for (int j = 0; j < 3; ++j) sum[j] += L[j];
+            }
+            /* Eq. 5 adjoint: dL/dEc and the CRF / white-balance parameters */
+            double gE[3];
+            for (int j = 0; j < 3; ++j) {
+                double ec = sum[j] / spp;
+                double a = P->gain_c * P->wb[j] * ec;
+                gE[j] = 0.0;
+                if (a > 0.0) {
+                    double g = dIc[3 * i + j];
+                    double da = P->gamma_c[j] * pow(a, P->gamma_c[j] - 1.0); /* dIc/da */
+                    gE[j] = g * da * P->gain_c * P->wb[j];
+#pragma omp atomic
+                    crf_acc[j] += g * pow(a, P->gamma_c[j]) * log(a);            /* gamma_c */
+#pragma omp atomic
+                    crf_acc[3] += g * da * P->wb[j] * ec;                        /* Gc */
+#pragma omp atomic
+                    crf_acc[4 + j] += g * da * P->gain_c * ec;                   /* wb */
+                }
+            }
+            /* Eq. 4 adjoint (mean over samples), then the path adjoint */
+            double gbar[3] = {gE[0] / spp, gE[1] / spp, gE[2] / spp};
+            if (gbar[0] == 0.0 && gbar[1] == 0.0 && gbar[2] == 0.0) continue;
+            for (int s = 0; s < spp; ++s) {
+                int nv = trace_sample(&C, pix, (uint32_t)s, L, rec);
+                /* reverse sweep; A = dL/dbeta_{c+1} in units of beta_{c+1} */
+                double A[3] = {0.0, 0.0, 0.0};
+                for (int c = nv - 1; c >= 0; --c) {
+                    const vrec *R = &rec[c];
+                    double An[3] = {A[0], A[1], A[2]};
+                    double dr = 0.0;
+                    for (int j = 0; j < 3; ++j) {
+                        double gb = gbar[j] * R->beta[j];
+                        double ln_e = (R->nee && R->unclipped[j]) ? R->Ep[j] * R->G : 0.0; /* Ln / f */
+                        double cont = R->cont ? R->cw * An[j] : 0.0;                       /* w / f * A */
+                        if (R->nee && R->unclipped[j])
+                            for (int k = 0; k < 4; ++k)
+                                gEp[3 * R->proj_idx[k] + j] += gb * R->fp[j] * R->G * R->proj_w[k];
+                        for (int k = 0; k < 4; ++k) gA[3 * R->tex_idx[k] + j] += gb * R->tex_w[k] * (ln_e + cont) / OR_PI;
+                        dr += gb * (R->dfp_dr * ln_e + R->dfi_dr * cont);
+                        A[j] = R->fp[j] * ln_e + R->fi[j] * cont;
+                    }
+                    for (int k = 0; k < 4; ++k) gR[R->tex_idx[k]] += dr * R->tex_w[k];
+                }
+            }
+        }
+    }
+    /* Eq. 1 adjoint: dIp, gamma_p, Gp */
+    double prf_acc[4] = {0};
+    for (int64_t t = 0; t < ntex; ++t)
+        for (int j = 0; j < 3; ++j) {
+            double g = 0.0;
+            for (int th = 0; th < nt; ++th) g += acc[(size_t)th * per + 3 * t + j];
+            double ip = Ip[3 * t + j];
+            if (ip > 0.0 && g != 0.0) {
+                double gm = P->gamma_p[j];
+                dIp[3 * t + j] += g * P->gain_p * gm * pow(ip, gm - 1.0);
+                prf_acc[j] += g * P->gain_p * pow(ip, gm) * log(ip);
+                prf_acc[3] += g * pow(ip, gm);
+            }
+        }
+    for (int64_t t = 0; t < 3 * nalb; ++t) {
+        double g = 0.0;
+        for (int th = 0; th < nt; ++th) g += acc[(size_t)th * per + 3 * ntex + t];
+        dAlbedo[t] += g;
+    }
+    for (int64_t t = 0; t < nalb; ++t) {
+        double g = 0.0;
+        for (int th = 0; th < nt; ++th) g += acc[(size_t)th * per + 3 * ntex + 3 * nalb + t];
+        dRough[t] += g;
+    }
+    dParams[0] += prf_acc[0]; dParams[1] += prf_acc[1]; dParams[2] += prf_acc[2]; dParams[3] += prf_acc[3];
+    dParams[4] += crf_acc[0]; dParams[5] += crf_acc[1]; dParams[6] += crf_acc[2]; dParams[7] += crf_acc[3];
+    dParams[8] += crf_acc[4]; dParams[9] += crf_acc[5]; dParams[10] += crf_acc[6];
+    free(acc);
+    free(Ep);
+    scene_free(&S);
+    return 0;
+}

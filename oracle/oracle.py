@@ -1,0 +1,252 @@
+"""ctypes binding of the FP64 oracle (``dpcs_oracle.c``) -- test infrastructure.
+
+Inputs are the seeded arrays of ``paper_2503_12174_gb300.scenes``; every
+differentiable input (textures, projector image, parameters) is widened to
+float64 before it reaches the C code.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dpcs_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_OUT_DIR, "libdpcs_oracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (FP64, OpenMP, no FP contraction)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+               "-fno-fast-math", _SRC, "-o", tmp, "-lm"]
+        subprocess.check_call(cmd)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class OrParams(ctypes.Structure):
+    _fields_ = [("gamma_p", ctypes.c_double * 3), ("gain_p", ctypes.c_double),
+                ("gamma_c", ctypes.c_double * 3), ("gain_c", ctypes.c_double),
+                ("wb", ctypes.c_double * 3), ("k_proj", ctypes.c_double),
+                ("ks", ctypes.c_double), ("f0", ctypes.c_double),
+                ("rr_start", ctypes.c_int32), ("rr_q", ctypes.c_double),
+                ("clip", ctypes.c_double), ("jitter", ctypes.c_int32)]
+
+
+class OrView(ctypes.Structure):
+    _fields_ = [("Kc", ctypes.c_double * 9), ("Hc", ctypes.c_int32), ("Wc", ctypes.c_int32),
+                ("Kp", ctypes.c_double * 9), ("Rp", ctypes.c_double * 9), ("tp", ctypes.c_double * 3),
+                ("Hp", ctypes.c_int32), ("Wp", ctypes.c_int32)]
+
+
+def load():
+    global _lib
+    if _lib is None:
+        build()
+        _lib = ctypes.CDLL(_LIB)
+        P = ctypes.c_void_p
+        _lib.or_render.restype = ctypes.c_int
+        _lib.or_render_backward.restype = ctypes.c_int
+        _lib.or_ggx_D.restype = ctypes.c_double
+        _lib.or_ggx_D.argtypes = [ctypes.c_double, ctypes.c_double]
+        _lib.or_bsdf_pdf.restype = ctypes.c_double
+        _lib.or_bsdf_pdf.argtypes = [P, P, P, ctypes.c_double, ctypes.c_double]
+        _lib.or_bsdf_sample.restype = ctypes.c_int
+        _lib.or_bsdf_sample.argtypes = [P, P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_double, ctypes.c_double, P]
+        _lib.or_bsdf_eval.argtypes = [P, P, P, P, ctypes.c_double, ctypes.c_double, ctypes.c_double, P, P]
+        _lib.or_num_threads.restype = ctypes.c_int
+        _lib.or_num_threads.argtypes = [ctypes.c_int]
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def num_threads(n: int = 0) -> int:
+    return load().or_num_threads(int(n))
+
+
+def make_params(p) -> OrParams:
+    o = OrParams()
+    o.gamma_p[:] = [float(x) for x in p.gamma_p]
+    o.gain_p = float(p.gain_p)
+    o.gamma_c[:] = [float(x) for x in p.gamma_c]
+    o.gain_c = float(p.gain_c)
+    o.wb[:] = [float(x) for x in p.wb]
+    o.k_proj = float(p.k_proj)
+    o.ks = float(p.ks)
+    o.f0 = float(p.f0)
+    o.rr_start = int(p.rr_start)
+    o.rr_q = float(p.rr_q)
+    o.clip = float(p.clip)
+    o.jitter = int(p.jitter)
+    return o
+
+
+def make_view(sc) -> OrView:
+    v = OrView()
+    v.Kc[:] = [float(x) for x in np.asarray(sc.Kc, np.float64).ravel()]
+    v.Hc, v.Wc = int(sc.Hc), int(sc.Wc)
+    v.Kp[:] = [float(x) for x in np.asarray(sc.Kp, np.float64).ravel()]
+    v.Rp[:] = [float(x) for x in np.asarray(sc.Rp, np.float64).ravel()]
+    v.tp[:] = [float(x) for x in np.asarray(sc.tp, np.float64).ravel()]
+    v.Hp, v.Wp = int(sc.Ip.shape[0]), int(sc.Ip.shape[1])
+    return v
+
+
+# ---------------------------------------------------------------------------
+def philox(ctr: np.ndarray, seed: int) -> np.ndarray:
+    """Philox4x32-10 blocks for counters ``ctr`` (n, 4) uint32 under key ``seed``."""
+    ctr = _c(ctr, np.uint32).reshape(-1, 4)
+    out = np.empty_like(ctr)
+    load().or_philox(_p(ctr), ctypes.c_int64(len(ctr)), ctypes.c_uint64(seed), _p(out))
+    return out
+
+
+def morton(verts, tris) -> np.ndarray:
+    verts, tris = _c(verts, np.float32), _c(tris, np.int32)
+    out = np.empty(len(tris), np.uint32)
+    load().or_morton(_p(verts), _p(tris), ctypes.c_int32(len(tris)), _p(out))
+    return out
+
+
+def lbvh(verts, tris):
+    """(sorted codes, sorted triangle order, child refs (T-1, 2), child boxes (T-1, 2, 6))."""
+    verts, tris = _c(verts, np.float32), _c(tris, np.int32)
+    T = len(tris)
+    codes = np.empty(T, np.uint32)
+    order = np.empty(T, np.int32)
+    child = np.zeros((max(T - 1, 0), 2), np.int32)
+    box = np.zeros((max(T - 1, 0), 2, 6), np.float32)
+    load().or_lbvh(_p(verts), _p(tris), ctypes.c_int32(T), _p(codes), _p(order), _p(child), _p(box))
+    return codes, order, child, box
+
+
+def closest(verts, tris, o, d):
+    verts, tris = _c(verts, np.float32), _c(tris, np.int32)
+    o, d = _c(o, np.float64).reshape(-1, 3), _c(d, np.float64).reshape(-1, 3)
+    n = len(o)
+    t = np.empty(n, np.float64)
+    tri = np.empty(n, np.int32)
+    uv = np.zeros((max(len(verts), 1), 2), np.float32)
+    load().or_closest(_p(verts), ctypes.c_int32(len(verts)), _p(tris), ctypes.c_int32(len(tris)), _p(uv),
+                      _p(o), _p(d), ctypes.c_int64(n), _p(t), _p(tri))
+    return t, tri
+
+
+def ggx_D(cos_h: float, alpha: float) -> float:
+    return load().or_ggx_D(float(cos_h), float(alpha))
+
+
+def bsdf_eval(n, wo, wi, rho, r, ks, f0):
+    n, wo, wi, rho = (_c(x, np.float64) for x in (n, wo, wi, rho))
+    f = np.zeros(3)
+    dfdr = np.zeros(1)
+    load().or_bsdf_eval(_p(n), _p(wo), _p(wi), _p(rho), float(r), float(ks), float(f0), _p(f), _p(dfdr))
+    return f, float(dfdr[0])
+
+
+def bsdf_pdf(n, wo, wi, r, ks) -> float:
+    n, wo, wi = (_c(x, np.float64) for x in (n, wo, wi))
+    return load().or_bsdf_pdf(_p(n), _p(wo), _p(wi), float(r), float(ks))
+
+
+def bsdf_sample(n, wo, r, ks, u0, u1, u2):
+    n, wo = _c(n, np.float64), _c(wo, np.float64)
+    wi = np.zeros(3)
+    ok = load().or_bsdf_sample(_p(n), _p(wo), float(r), float(ks), float(u0), float(u1), float(u2), _p(wi))
+    return bool(ok), wi
+
+
+def prf(Ip, params) -> np.ndarray:
+    Ip = _c(Ip, np.float64)
+    out = np.empty_like(Ip)
+    P = make_params(params)
+    load().or_prf(_p(Ip), ctypes.c_int64(Ip.size // 3), ctypes.byref(P), _p(out))
+    return out
+
+
+def _scene_args(sc, albedo, rough, Ip):
+    verts, tris, uv = _c(sc.verts, np.float32), _c(sc.tris, np.int32), _c(sc.uv, np.float32)
+    albedo = _c(sc.albedo if albedo is None else albedo, np.float64)
+    rough = _c(sc.rough if rough is None else rough, np.float64)
+    Ip = _c(sc.Ip if Ip is None else Ip, np.float64)
+    return verts, tris, uv, albedo, rough, Ip
+
+
+def render(sc, pixels=None, *, albedo=None, rough=None, Ip=None, params=None, spp=None, bounces=None,
+           seed=None, nthreads: int = 0):
+    """FP64 forward render.  Returns (Ec, Ic), each (npix, 3) for a pixel list
+    or (Hc, Wc, 3) for the full image."""
+    verts, tris, uv, albedo, rough, Ip = _scene_args(sc, albedo, rough, Ip)
+    P = make_params(params or sc.params)
+    V = make_view(sc)
+    full = pixels is None
+    px = None if full else _c(pixels, np.int64)
+    n = sc.Hc * sc.Wc if full else len(px)
+    Ec = np.zeros((n, 3))
+    Ic = np.zeros((n, 3))
+    rc = load().or_render(_p(verts), _p(tris), ctypes.c_int32(len(tris)), _p(uv), _p(albedo), _p(rough),
+                          ctypes.c_int32(albedo.shape[0]), ctypes.c_int32(albedo.shape[1]), _p(Ip),
+                          ctypes.byref(V), ctypes.byref(P), ctypes.c_int32(spp or sc.spp),
+                          ctypes.c_int32(sc.bounces if bounces is None else bounces),
+                          ctypes.c_uint64(sc.seed if seed is None else seed),
+                          None if full else _p(px), ctypes.c_int64(n), _p(Ec), _p(Ic), ctypes.c_int32(nthreads))
+    if rc != 0:
+        raise ValueError("oracle render: invalid arguments")
+    if full:
+        return Ec.reshape(sc.Hc, sc.Wc, 3), Ic.reshape(sc.Hc, sc.Wc, 3)
+    return Ec, Ic
+
+
+def render_backward(sc, dIc, pixels=None, *, albedo=None, rough=None, Ip=None, params=None, spp=None,
+                    bounces=None, seed=None, nthreads: int = 0):
+    """FP64 adjoint.  ``dIc`` is (npix, 3) for a pixel list or (Hc, Wc, 3).
+    Returns dict(dIp, dalbedo, drough, dparams[11])."""
+    verts, tris, uv, albedo, rough, Ip = _scene_args(sc, albedo, rough, Ip)
+    P = make_params(params or sc.params)
+    V = make_view(sc)
+    full = pixels is None
+    px = None if full else _c(pixels, np.int64)
+    n = sc.Hc * sc.Wc if full else len(px)
+    dIc = _c(dIc, np.float64).reshape(n, 3)
+    dIp = np.zeros(Ip.shape)
+    dA = np.zeros(albedo.shape)
+    dR = np.zeros(rough.shape)
+    dP = np.zeros(11)
+    rc = load().or_render_backward(
+        _p(verts), _p(tris), ctypes.c_int32(len(tris)), _p(uv), _p(albedo), _p(rough),
+        ctypes.c_int32(albedo.shape[0]), ctypes.c_int32(albedo.shape[1]), _p(Ip), ctypes.byref(V),
+        ctypes.byref(P), ctypes.c_int32(spp or sc.spp), ctypes.c_int32(sc.bounces if bounces is None else bounces),
+        ctypes.c_uint64(sc.seed if seed is None else seed), None if full else _p(px), ctypes.c_int64(n), _p(dIc),
+        _p(dIp), _p(dA), _p(dR), _p(dP), ctypes.c_int32(nthreads))
+    if rc != 0:
+        raise ValueError("oracle render_backward: invalid arguments")
+    return {"dIp": dIp, "dalbedo": dA, "drough": dR, "dparams": dP}
+
+
+def adam_step(p, g, m, v, step, lr=1e-2, b1=0.9, b2=0.999, eps=1e-8, lo=0.0, hi=1.0):
+    """Adam (Kingma & Ba 2015) with bias correction, then clamp to [lo, hi];
+    in place on float64 arrays."""
+    m *= b1
+    m += (1.0 - b1) * g
+    v *= b2
+    v += (1.0 - b2) * g * g
+    mh = m / (1.0 - b1 ** step)
+    vh = v / (1.0 - b2 ** step)
+    p -= lr * mh / (np.sqrt(vh) + eps)
+    np.clip(p, lo, hi, out=p)
+    return p
