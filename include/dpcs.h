@@ -1,0 +1,219 @@
+/*
+ * dpcs.h -- C ABI of libdpcs, a GB300 (sm_103a) path tracer for
+ * differentiable projector-camera simulation (DPCS, arxiv 2503.12174).
+ *
+ * The library renders the camera image Ic of a triangle scene lit only by a
+ * pinhole projector showing the image Ip (forward rendering, Sec. 3.2 Eq. 7),
+ * and back-propagates dLoss/dIc to Ip, to the BRDF textures and to the
+ * projector/camera response parameters (the gradient used by inverse
+ * rendering, Eq. 8, projector compensation, Eq. 13, and scene fitting,
+ * Eq. 9).  Every step runs in the library's own CUDA kernels.
+ *
+ * Conventions for every entry point:
+ *  - Images and textures are float32, contiguous, row-major HWC with y down.
+ *    Matrices are float32 row-major (OpenCV style).
+ *  - "dev" pointers are CUDA device pointers on the context's device, owned
+ *    by the caller; "host" pointers are ordinary host memory, owned by the
+ *    caller.  The library owns scene data and its own scratch memory.
+ *  - Calls that take a stream enqueue work on it (cudaStream_t passed as
+ *    void*, NULL = legacy default stream) and return before the GPU is done.
+ *    Argument errors are reported synchronously.  Device-side check failures
+ *    (traversal limits, bounds checks) are recorded in a device status word
+ *    and reported by dpcs_sync.  No kernel traps.
+ *  - One context per host thread; a context is not thread safe.
+ *  - Scratch memory is allocated on first use for a given problem size and
+ *    counted against the context's HBM budget; call an entry point once with
+ *    the largest sizes before capturing it in a CUDA graph.
+ */
+#ifndef DPCS_H
+#define DPCS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t dpcs_status;
+#define DPCS_OK 0
+#define DPCS_ERR_INVALID_ARG (-1)     /* bad pointer, size or parameter */
+#define DPCS_ERR_OOM (-2)             /* allocation failed or HBM budget exceeded */
+#define DPCS_ERR_CUDA (-3)            /* a CUDA runtime call failed */
+#define DPCS_ERR_DEVICE_CHECK (-4)    /* a kernel's bounds check failed */
+#define DPCS_ERR_TRAVERSAL_LIMIT (-5) /* BVH traversal hit its stack or visit cap */
+#define DPCS_ERR_TIMEOUT (-6)         /* a bounded wait ran out */
+#define DPCS_ERR_BUSY (-7)            /* no free slot / budget right now */
+#define DPCS_ERR_NOT_FOUND (-8)       /* unknown scene or request handle */
+
+#define DPCS_MAX_BOUNCES 8            /* most path vertices per camera sample */
+
+typedef struct dpcs_ctx dpcs_ctx;
+typedef uint64_t dpcs_scene;
+
+/*
+ * Response, BRDF and sampling parameters.
+ *  gamma_p, gain_p : projector response Ep = gain_p * Ip^gamma_p (Eq. 1)
+ *  gamma_c, gain_c, wb : camera response Ic = (gain_c * wb * Ec)^gamma_c (Eq. 5)
+ *  k_proj  : projector intensity scale k; stands for 1/phi of Eq. 2 and is the
+ *            k of the radiance clip of Eq. 12
+ *  ks, f0  : weight of the GGX specular lobe and its Schlick F0; the diffuse
+ *            lobe is albedo/pi (the paper's principled BRDF reduced to
+ *            Lambert + GGX, Sec. 3.2)
+ *  rr_start, rr_q : Russian roulette on continuations from vertex rr_start on
+ *            (0 = off) with survival probability rr_q
+ *  clip    : per-vertex radiance clamp of Eq. 12 (0 = off)
+ *  jitter  : 1 = uniform jitter inside each camera pixel (box filter of Eq. 4),
+ *            0 = rays through pixel centres
+ */
+typedef struct dpcs_params {
+    float gamma_p[3];
+    float gain_p;
+    float gamma_c[3];
+    float gain_c;
+    float wb[3];
+    float k_proj;
+    float ks;
+    float f0;
+    int32_t rr_start;
+    float rr_q;
+    float clip;
+    int32_t jitter;
+} dpcs_params;
+
+/*
+ * Camera and projector (Eq. 6).  The world origin is the camera's optical
+ * centre (Sec. 3.1); x_c = Kc x_s.  The projector maps a world point to its
+ * pixel by x_p = Kp (Rp x_s + tp).  Hc x Wc is the camera image, Hp x Wp the
+ * projector image.
+ */
+typedef struct dpcs_view {
+    float Kc[9];
+    int32_t Hc, Wc;
+    float Kp[9];
+    float Rp[9];
+    float tp[3];
+    int32_t Hp, Wp;
+} dpcs_view;
+
+/* Create a context on CUDA device `device`; scratch and scenes may use at
+ * most `hbm_budget_bytes` (0 = no limit).  *out receives the context. */
+dpcs_status dpcs_create(int device, size_t hbm_budget_bytes, dpcs_ctx **out);
+
+/* Free every scene, scratch buffer and the context itself (synchronises). */
+dpcs_status dpcs_destroy(dpcs_ctx *ctx);
+
+/* Text of the last error recorded by this context ("" if none). */
+const char *dpcs_last_error(const dpcs_ctx *ctx);
+
+/* Wait for `stream`, then read and clear the device status word.  Returns
+ * DPCS_ERR_TRAVERSAL_LIMIT or DPCS_ERR_DEVICE_CHECK if a kernel recorded one. */
+dpcs_status dpcs_sync(dpcs_ctx *ctx, void *stream);
+
+/* Bytes of device memory the context holds now (scenes + scratch). */
+size_t dpcs_memory_used(const dpcs_ctx *ctx);
+
+/* Number of kernels the context has launched since it was created. */
+uint64_t dpcs_launch_count(const dpcs_ctx *ctx);
+
+/*
+ * Upload a triangle mesh and build its LBVH on the device (Morton codes of
+ * triangle centroids, radix sort, Karras radix tree, bottom-up AABB refit).
+ *  verts : host, V x 3 float32 positions (world = camera frame)
+ *  tris  : host, T x 3 int32 vertex indices, each in [0, V)
+ *  uv    : host, V x 2 float32 texture coordinates in [0,1]^2
+ * T may be 0 (every ray misses).  The host arrays may be reused once the call
+ * returns (it synchronises on `stream`).  *out receives the scene handle.
+ * The paper renders Poisson-reconstructed triangle meshes (Sec. 4, Sec. 4.4).
+ */
+dpcs_status dpcs_scene_upload(dpcs_ctx *ctx, const float *verts, int32_t V, const int32_t *tris, int32_t T,
+                              const float *uv, void *stream, dpcs_scene *out);
+
+/* Release a scene's device memory. */
+dpcs_status dpcs_scene_free(dpcs_ctx *ctx, dpcs_scene scene);
+
+/*
+ * Copy a scene's LBVH to host memory (for inspection and tests):
+ *  codes    : T uint32 Morton codes in sorted order
+ *  order    : T int32 original triangle index of each sorted position
+ *  child    : (T-1) x 2 int32 child references of the internal nodes;
+ *             >= 0 internal node, < 0 leaf ~sorted_position
+ *  child_box: (T-1) x 2 x 6 float32 child boxes (lo.xyz, hi.xyz)
+ * Any output pointer may be NULL.  Synchronous.
+ */
+dpcs_status dpcs_scene_export(dpcs_ctx *ctx, dpcs_scene scene, uint32_t *codes, int32_t *order, int32_t *child,
+                              float *child_box);
+
+/*
+ * Closest hit of n rays through the scene's BVH.
+ *  orig, dir : dev, n x 3 float32 (dir need not be normalised; t is in units of dir)
+ *  t_out     : dev, n float32 hit distance (+inf on a miss)
+ *  tri_out   : dev, n int32 original triangle index (-1 on a miss)
+ * Ties in t go to the lowest triangle index.
+ */
+dpcs_status dpcs_trace(dpcs_ctx *ctx, dpcs_scene scene, const float *orig, const float *dir, int64_t n,
+                       float *t_out, int32_t *tri_out, void *stream);
+
+/*
+ * Forward rendering Ic = R(Ip, theta) (Eq. 7).  For every camera pixel, spp
+ * paths of at most `bounces` vertices are traced; each vertex does next-event
+ * estimation towards the projector (Eqs. 1, 2, 3, 6) and continues by
+ * sampling the BRDF (Eq. 10).  Ec is the mean path radiance of the pixel
+ * (Eq. 4) and Ic its camera response (Eq. 5).
+ *  albedo : dev, Ht x Wt x 3;  rough : dev, Ht x Wt (GGX alpha = rough^2)
+ *  Ip     : dev, Hp x Wp x 3 projector input image
+ *  Ic     : dev out, Hc x Wc x 3
+ *  Ec     : dev out, Hc x Wc x 3, or NULL (keep it for render_backward)
+ *  seed   : key of the Philox4x32-10 stream; counters are
+ *           (pixel index y*Wc+x, sample, vertex, 0), so a pixel's result does
+ *           not depend on how the image is partitioned.
+ * 1 <= spp, 0 <= bounces <= DPCS_MAX_BOUNCES.  Deterministic: the same
+ * inputs give bitwise the same Ic.
+ */
+dpcs_status dpcs_render(dpcs_ctx *ctx, dpcs_scene scene, const float *albedo, const float *rough, int32_t Ht,
+                        int32_t Wt, const float *Ip, const dpcs_view *view, const dpcs_params *params, int32_t spp,
+                        int32_t bounces, uint64_t seed, float *Ic, float *Ec, void *stream);
+
+/*
+ * Adjoint of dpcs_render (path replay): every path is re-traced from its
+ * Philox counters, and dLoss/dIc is carried back with the sampled directions
+ * held fixed.  Inputs are those of the forward call plus
+ *  Ec, Ic : dev, the forward call's outputs;  dIc : dev, Hc x Wc x 3
+ * Outputs are ACCUMULATED (+=):
+ *  dIp     : dev, Hp x Wp x 3   (may be NULL)
+ *  dAlbedo : dev, Ht x Wt x 3   (may be NULL)
+ *  dRough  : dev, Ht x Wt       (may be NULL)
+ *  dParams : dev, 11 float32 [gamma_p(3), gain_p, gamma_c(3), gain_c, wb(3)]
+ *            (may be NULL)
+ * These are the gradients of the scene parameters theta of Eq. 9 that do not
+ * move geometry, and of the projector input of Eq. 13.
+ */
+dpcs_status dpcs_render_backward(dpcs_ctx *ctx, dpcs_scene scene, const float *albedo, const float *rough,
+                                 int32_t Ht, int32_t Wt, const float *Ip, const dpcs_view *view,
+                                 const dpcs_params *params, int32_t spp, int32_t bounces, uint64_t seed,
+                                 const float *Ec, const float *Ic, const float *dIc, float *dIp, float *dAlbedo,
+                                 float *dRough, float *dParams, void *stream);
+
+/*
+ * L2 image loss of projector compensation (Eq. 13 with a squared norm):
+ * loss = 1/2 sum (Ic - target)^2 written to *loss (dev, 1 float32, overwritten),
+ * dIc = Ic - target (dev, n floats, overwritten).  n = number of floats.
+ */
+dpcs_status dpcs_l2_loss(dpcs_ctx *ctx, const float *Ic, const float *target, int64_t n, float *dIc, float *loss,
+                         void *stream);
+
+/*
+ * One Adam step (Kingma & Ba 2015, bias-corrected; `step` counts from 1) on
+ * n float32 parameters p with gradient g and moments m, v (all dev, updated
+ * in place), followed by a clamp to [lo, hi] -- the projection that keeps Ip
+ * in [0, 1] and the PRF/CRF/white-balance parameters inside the ranges of
+ * Sec. 3.2.
+ */
+dpcs_status dpcs_adam(dpcs_ctx *ctx, float *p, const float *g, float *m, float *v, int64_t n, float lr, float beta1,
+                      float beta2, float eps, int32_t step, float lo, float hi, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DPCS_H */

@@ -1,0 +1,464 @@
+// api.cu -- the C ABI of libdpcs (declared in include/dpcs.h): context,
+// scene residency and LBVH build, forward render, path-replay adjoint, loss
+// and optimiser.  Host code only validates, sizes scratch memory against the
+// context's HBM budget and enqueues the kernels of lbvh.cu, render.cu and
+// optim.cu on the caller's stream.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <map>
+#include <string>
+
+#include "dpcs.h"
+#include "internal.h"
+
+using namespace dpcs;
+
+namespace {
+
+struct Buf {
+    void *p = nullptr;
+    size_t n = 0;
+};
+
+}  // namespace
+
+struct dpcs_ctx {
+    int device = 0;
+    size_t budget = 0;
+    size_t used = 0;
+    uint64_t launches = 0;
+    std::string err;
+    unsigned *status = nullptr;       // device status word
+    std::map<uint64_t, Scene> scenes;
+    uint64_t next_scene = 1;
+    // scratch
+    Buf ep4, tex4, gE, dEp4, dtex4, acc, partial, build, upload;
+};
+
+namespace {
+
+dpcs_status fail(dpcs_ctx *c, dpcs_status code, const std::string &msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+dpcs_status cuda_fail(dpcs_ctx *c, cudaError_t e, const char *what) {
+    return fail(c, DPCS_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+dpcs_status dev_alloc(dpcs_ctx *c, void **p, size_t bytes, const char *what) {
+    if (c->budget && c->used + bytes > c->budget)
+        return fail(c, DPCS_ERR_OOM, std::string(what) + ": HBM budget exceeded");
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 1);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, DPCS_ERR_OOM, std::string(what) + ": cudaMalloc failed");
+    }
+    c->used += bytes;
+    return DPCS_OK;
+}
+
+void dev_free(dpcs_ctx *c, void *p, size_t bytes) {
+    if (p) {
+        cudaFree(p);
+        c->used -= bytes;
+    }
+}
+
+// grow-only scratch buffer
+dpcs_status ensure(dpcs_ctx *c, Buf &b, size_t bytes, const char *what) {
+    if (b.n >= bytes) return DPCS_OK;
+    if (b.p) {
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) return cuda_fail(c, e, what);
+        dev_free(c, b.p, b.n);
+        b.p = nullptr;
+        b.n = 0;
+    }
+    dpcs_status s = dev_alloc(c, &b.p, bytes, what);
+    if (s == DPCS_OK) b.n = bytes;
+    return s;
+}
+
+dpcs_status set_device(dpcs_ctx *c) {
+    cudaError_t e = cudaSetDevice(c->device);
+    return e == cudaSuccess ? DPCS_OK : cuda_fail(c, e, "cudaSetDevice");
+}
+
+dpcs_status check_launch(dpcs_ctx *c, int n, const char *what) {
+    if (n < 0) return fail(c, n, std::string(what) + ": launch rejected");
+    c->launches += (uint64_t)n;
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? DPCS_OK : cuda_fail(c, e, what);
+}
+
+bool finite_all(const float *v, int n) {
+    for (int i = 0; i < n; ++i)
+        if (!isfinite(v[i])) return false;
+    return true;
+}
+
+void inv3(const float *Mf, float *R) {
+    double M[9];
+    for (int i = 0; i < 9; ++i) M[i] = Mf[i];
+    const double a = M[0], b = M[1], cc = M[2], d = M[3], e = M[4], f = M[5], g = M[6], h = M[7], i = M[8];
+    const double A = e * i - f * h, B = -(d * i - f * g), C = d * h - e * g;
+    const double det = a * A + b * B + cc * C;
+    const double r[9] = {A / det, -(b * i - cc * h) / det, (b * f - cc * e) / det,
+                         B / det, (a * i - cc * g) / det,  -(a * f - cc * d) / det,
+                         C / det, -(a * h - b * g) / det,  (a * e - b * d) / det};
+    for (int k = 0; k < 9; ++k) R[k] = (float)r[k];
+}
+
+double det3(const float *M) {
+    return (double)M[0] * ((double)M[4] * M[8] - (double)M[5] * M[7]) -
+           (double)M[1] * ((double)M[3] * M[8] - (double)M[5] * M[6]) +
+           (double)M[2] * ((double)M[3] * M[7] - (double)M[4] * M[6]);
+}
+
+// shared validation + argument packing of render and render_backward
+dpcs_status prepare(dpcs_ctx *c, dpcs_scene scene, const float *albedo, const float *rough, int32_t Ht, int32_t Wt,
+                    const float *Ip, const dpcs_view *view, const dpcs_params *prm, int32_t spp, int32_t bounces,
+                    uint64_t seed, RenderArgs &a, Scene **sc_out) {
+    if (!c) return DPCS_ERR_INVALID_ARG;
+    auto it = c->scenes.find(scene);
+    if (it == c->scenes.end()) return fail(c, DPCS_ERR_NOT_FOUND, "unknown scene handle");
+    if (!albedo || !rough || !Ip || !view || !prm) return fail(c, DPCS_ERR_INVALID_ARG, "null input pointer");
+    if (Ht <= 0 || Wt <= 0) return fail(c, DPCS_ERR_INVALID_ARG, "texture size must be positive");
+    if (view->Hc <= 0 || view->Wc <= 0 || view->Hp <= 0 || view->Wp <= 0)
+        return fail(c, DPCS_ERR_INVALID_ARG, "camera and projector sizes must be positive");
+    if ((int64_t)view->Hc * view->Wc > (int64_t)1 << 30)
+        return fail(c, DPCS_ERR_INVALID_ARG, "camera image too large (max 2^30 pixels)");
+    if (spp < 1 || spp > (1 << 24)) return fail(c, DPCS_ERR_INVALID_ARG, "spp must be in [1, 2^24]");
+    if (bounces < 0 || bounces > DPCS_MAX_BOUNCES) return fail(c, DPCS_ERR_INVALID_ARG, "bounces out of range");
+    if (!finite_all(view->Kc, 9) || !finite_all(view->Kp, 9) || !finite_all(view->Rp, 9) || !finite_all(view->tp, 3))
+        return fail(c, DPCS_ERR_INVALID_ARG, "non-finite camera or projector matrix");
+    if (fabs(det3(view->Kc)) < 1e-12) return fail(c, DPCS_ERR_INVALID_ARG, "singular Kc");
+    const float *pf = &prm->gamma_p[0];  // gamma_p .. f0: 14 consecutive floats
+    if (!finite_all(pf, 14) || !isfinite(prm->rr_q) || !isfinite(prm->clip))
+        return fail(c, DPCS_ERR_INVALID_ARG, "non-finite parameter");
+    if (prm->rr_start < 0 || (prm->rr_start > 0 && !(prm->rr_q > 0.0f && prm->rr_q <= 1.0f)))
+        return fail(c, DPCS_ERR_INVALID_ARG, "Russian roulette needs rr_start >= 0 and 0 < rr_q <= 1");
+    if (prm->clip < 0.0f || prm->ks < 0.0f) return fail(c, DPCS_ERR_INVALID_ARG, "clip and ks must be >= 0");
+    Scene &sc = it->second;
+    memset(&a, 0, sizeof a);
+    a.nodes = sc.nodes;
+    a.tris = sc.tris;
+    a.tuv = sc.tuv;
+    a.root = sc.root;
+    a.T = sc.T;
+    a.Ht = Ht;
+    a.Wt = Wt;
+    a.Hp = view->Hp;
+    a.Wp = view->Wp;
+    a.Hc = view->Hc;
+    a.Wc = view->Wc;
+    inv3(view->Kc, a.Kci);
+    memcpy(a.Kp, view->Kp, sizeof a.Kp);
+    memcpy(a.Rp, view->Rp, sizeof a.Rp);
+    memcpy(a.tp, view->tp, sizeof a.tp);
+    for (int i = 0; i < 3; ++i)  // projector centre -Rp^T tp
+        a.cp[i] = (float)-((double)view->Rp[i] * view->tp[0] + (double)view->Rp[3 + i] * view->tp[1] +
+                           (double)view->Rp[6 + i] * view->tp[2]);
+    memcpy(a.gamma_c, prm->gamma_c, sizeof a.gamma_c);
+    a.gain_c = prm->gain_c;
+    memcpy(a.wb, prm->wb, sizeof a.wb);
+    a.k_proj = prm->k_proj;
+    a.ks = prm->ks;
+    a.f0 = prm->f0;
+    a.rr_q = prm->rr_q;
+    a.clip = prm->clip;
+    a.rr_start = prm->rr_start;
+    a.jitter = prm->jitter ? 1 : 0;
+    a.spp = spp;
+    a.bounces = bounces;
+    a.key0 = (uint32_t)(seed & 0xffffffffu);
+    a.key1 = (uint32_t)(seed >> 32);
+    int l2 = 0;
+    while ((2 << l2) <= spp && l2 < 5) ++l2;  // lanes per pixel: largest power of two <= min(spp, 32)
+    a.log2L = l2;
+    a.status = c->status;
+    *sc_out = &sc;
+    return DPCS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dpcs_status dpcs_create(int device, size_t hbm_budget_bytes, dpcs_ctx **out) {
+    if (!out) return DPCS_ERR_INVALID_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+        cudaGetLastError();
+        return DPCS_ERR_INVALID_ARG;
+    }
+    dpcs_ctx *c = new dpcs_ctx();
+    c->device = device;
+    c->budget = hbm_budget_bytes;
+    dpcs_status s = set_device(c);
+    if (s == DPCS_OK) s = dev_alloc(c, (void **)&c->status, sizeof(unsigned), "status word");
+    if (s == DPCS_OK && cudaMemset(c->status, 0, sizeof(unsigned)) != cudaSuccess) s = DPCS_ERR_CUDA;
+    if (s != DPCS_OK) {
+        delete c;
+        return s;
+    }
+    *out = c;
+    return DPCS_OK;
+}
+
+dpcs_status dpcs_destroy(dpcs_ctx *c) {
+    if (!c) return DPCS_ERR_INVALID_ARG;
+    set_device(c);
+    cudaDeviceSynchronize();
+    for (auto &kv : c->scenes) {
+        Scene &s = kv.second;
+        cudaFree(s.nodes);
+        cudaFree(s.tris);
+        cudaFree(s.tuv);
+        cudaFree(s.codes);
+        cudaFree(s.order);
+    }
+    Buf *bufs[] = {&c->ep4, &c->tex4, &c->gE, &c->dEp4, &c->dtex4, &c->acc, &c->partial, &c->build, &c->upload};
+    for (Buf *b : bufs)
+        if (b->p) cudaFree(b->p);
+    cudaFree(c->status);
+    delete c;
+    return DPCS_OK;
+}
+
+const char *dpcs_last_error(const dpcs_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+size_t dpcs_memory_used(const dpcs_ctx *c) { return c ? c->used : 0; }
+
+uint64_t dpcs_launch_count(const dpcs_ctx *c) { return c ? c->launches : 0; }
+
+dpcs_status dpcs_sync(dpcs_ctx *c, void *stream) {
+    if (!c) return DPCS_ERR_INVALID_ARG;
+    dpcs_status s = set_device(c);
+    if (s) return s;
+    unsigned h = 0;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemcpyAsync(&h, c->status, sizeof h, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "dpcs_sync");
+    if (h) {
+        cudaMemsetAsync(c->status, 0, sizeof(unsigned), st);
+        cudaStreamSynchronize(st);
+        if (h & kStatusTraversalLimit) return fail(c, DPCS_ERR_TRAVERSAL_LIMIT, "BVH traversal hit its limit");
+        return fail(c, DPCS_ERR_DEVICE_CHECK, "a device bounds check failed");
+    }
+    return DPCS_OK;
+}
+
+dpcs_status dpcs_scene_upload(dpcs_ctx *c, const float *verts, int32_t V, const int32_t *tris, int32_t T,
+                              const float *uv, void *stream, dpcs_scene *out) {
+    if (!c || !out) return DPCS_ERR_INVALID_ARG;
+    if (T < 0 || V < 0 || (T > 0 && (!verts || !tris || !uv || V == 0)))
+        return fail(c, DPCS_ERR_INVALID_ARG, "bad mesh arrays");
+    if (T > (1 << 28)) return fail(c, DPCS_ERR_INVALID_ARG, "too many triangles");
+    for (int64_t i = 0; i < 3 * (int64_t)T; ++i)
+        if (tris[i] < 0 || tris[i] >= V) return fail(c, DPCS_ERR_INVALID_ARG, "triangle index out of range");
+    for (int64_t i = 0; i < 3 * (int64_t)V; ++i)
+        if (!isfinite(verts[i])) return fail(c, DPCS_ERR_INVALID_ARG, "non-finite vertex");
+    dpcs_status s = set_device(c);
+    if (s) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    Scene sc;
+    sc.T = T;
+    const size_t n = (size_t)(T > 0 ? T : 1);
+    const size_t nn = (size_t)(T > 1 ? T - 1 : 1);
+    sc.bytes = nn * 64 + n * 48 + n * 24 + n * 8;
+    if ((s = dev_alloc(c, (void **)&sc.nodes, nn * 64, "scene nodes")) ||
+        (s = dev_alloc(c, (void **)&sc.tris, n * 48, "scene triangles")) ||
+        (s = dev_alloc(c, (void **)&sc.tuv, n * 24, "scene uv")) ||
+        (s = dev_alloc(c, (void **)&sc.codes, n * 4, "scene codes")) ||
+        (s = dev_alloc(c, (void **)&sc.order, n * 4, "scene order"))) {
+        dev_free(c, sc.nodes, sc.nodes ? nn * 64 : 0);
+        dev_free(c, sc.tris, sc.tris ? n * 48 : 0);
+        dev_free(c, sc.tuv, sc.tuv ? n * 24 : 0);
+        dev_free(c, sc.codes, sc.codes ? n * 4 : 0);
+        return s;
+    }
+    if (T > 0) {
+        const size_t vb = (size_t)V * 12, tb = (size_t)T * 12, ub = (size_t)V * 8;
+        const size_t up = ((vb + 255) & ~size_t(255)) + ((tb + 255) & ~size_t(255)) + ub;
+        if ((s = ensure(c, c->upload, up, "upload staging")) ||
+            (s = ensure(c, c->build, lbvh_scratch_bytes(T), "LBVH scratch")))
+            return s;
+        char *p = (char *)c->upload.p;
+        float *dv = (float *)p;
+        int32_t *dt = (int32_t *)(p + ((vb + 255) & ~size_t(255)));
+        float *du = (float *)(p + ((vb + 255) & ~size_t(255)) + ((tb + 255) & ~size_t(255)));
+        cudaError_t e = cudaMemcpyAsync(dv, verts, vb, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dt, tris, tb, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(du, uv, ub, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "scene upload");
+        int nl = launch_lbvh_build(dv, V, dt, T, du, sc, c->build.p, c->build.n, st);
+        if ((s = check_launch(c, nl, "LBVH build"))) return s;
+        e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "LBVH build");
+    } else {
+        sc.root = kEmptyRoot;
+    }
+    const uint64_t id = c->next_scene++;
+    c->scenes[id] = sc;
+    *out = id;
+    return DPCS_OK;
+}
+
+dpcs_status dpcs_scene_free(dpcs_ctx *c, dpcs_scene scene) {
+    if (!c) return DPCS_ERR_INVALID_ARG;
+    auto it = c->scenes.find(scene);
+    if (it == c->scenes.end()) return fail(c, DPCS_ERR_NOT_FOUND, "unknown scene handle");
+    set_device(c);
+    cudaDeviceSynchronize();
+    Scene &s = it->second;
+    const size_t n = (size_t)(s.T > 0 ? s.T : 1), nn = (size_t)(s.T > 1 ? s.T - 1 : 1);
+    dev_free(c, s.nodes, nn * 64);
+    dev_free(c, s.tris, n * 48);
+    dev_free(c, s.tuv, n * 24);
+    dev_free(c, s.codes, n * 4);
+    dev_free(c, s.order, n * 4);
+    c->scenes.erase(it);
+    return DPCS_OK;
+}
+
+dpcs_status dpcs_scene_export(dpcs_ctx *c, dpcs_scene scene, uint32_t *codes, int32_t *order, int32_t *child,
+                              float *child_box) {
+    if (!c) return DPCS_ERR_INVALID_ARG;
+    auto it = c->scenes.find(scene);
+    if (it == c->scenes.end()) return fail(c, DPCS_ERR_NOT_FOUND, "unknown scene handle");
+    dpcs_status s = set_device(c);
+    if (s) return s;
+    Scene &sc = it->second;
+    const int T = sc.T;
+    if (T <= 0) return DPCS_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess && codes) e = cudaMemcpy(codes, sc.codes, (size_t)T * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && order) e = cudaMemcpy(order, sc.order, (size_t)T * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && T >= 2 && (child || child_box)) {
+        float *h = new float[(size_t)(T - 1) * 16];
+        e = cudaMemcpy(h, sc.nodes, (size_t)(T - 1) * 64, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess)
+            for (int i = 0; i < T - 1; ++i) {
+                const float *nd = h + 16 * i;
+                if (child) {
+                    memcpy(&child[2 * i], &nd[12], 4);
+                    memcpy(&child[2 * i + 1], &nd[13], 4);
+                }
+                if (child_box) {
+                    float *bl = child_box + 12 * i, *br = bl + 6;
+                    bl[0] = nd[0]; bl[1] = nd[2]; bl[2] = nd[8]; bl[3] = nd[1]; bl[4] = nd[3]; bl[5] = nd[9];
+                    br[0] = nd[4]; br[1] = nd[6]; br[2] = nd[10]; br[3] = nd[5]; br[4] = nd[7]; br[5] = nd[11];
+                }
+            }
+        delete[] h;
+    }
+    return e == cudaSuccess ? DPCS_OK : cuda_fail(c, e, "scene export");
+}
+
+dpcs_status dpcs_trace(dpcs_ctx *c, dpcs_scene scene, const float *orig, const float *dir, int64_t n, float *t_out,
+                       int32_t *tri_out, void *stream) {
+    if (!c) return DPCS_ERR_INVALID_ARG;
+    auto it = c->scenes.find(scene);
+    if (it == c->scenes.end()) return fail(c, DPCS_ERR_NOT_FOUND, "unknown scene handle");
+    if (n < 0 || (n > 0 && (!orig || !dir || !t_out || !tri_out)))
+        return fail(c, DPCS_ERR_INVALID_ARG, "bad trace arguments");
+    if (n == 0) return DPCS_OK;
+    dpcs_status s = set_device(c);
+    if (s) return s;
+    return check_launch(c, launch_trace(it->second, orig, dir, n, t_out, tri_out, c->status, (cudaStream_t)stream),
+                        "trace");
+}
+
+dpcs_status dpcs_render(dpcs_ctx *c, dpcs_scene scene, const float *albedo, const float *rough, int32_t Ht,
+                        int32_t Wt, const float *Ip, const dpcs_view *view, const dpcs_params *params, int32_t spp,
+                        int32_t bounces, uint64_t seed, float *Ic, float *Ec, void *stream) {
+    RenderArgs a;
+    Scene *sc = nullptr;
+    dpcs_status s = prepare(c, scene, albedo, rough, Ht, Wt, Ip, view, params, spp, bounces, seed, a, &sc);
+    if (s) return s;
+    if (!Ic) return fail(c, DPCS_ERR_INVALID_ARG, "null Ic");
+    if ((s = set_device(c))) return s;
+    const int64_t np = (int64_t)view->Hp * view->Wp, nt = (int64_t)Ht * Wt;
+    if ((s = ensure(c, c->ep4, (size_t)np * 16, "Ep scratch")) || (s = ensure(c, c->tex4, (size_t)nt * 16, "texture scratch")))
+        return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    a.Ep = (const float4 *)c->ep4.p;
+    a.tex = (const float4 *)c->tex4.p;
+    a.Ic = Ic;
+    a.Ec = Ec;
+    int nl = launch_prf(Ip, np, params->gamma_p, params->gain_p, (float4 *)c->ep4.p, st);
+    nl += launch_pack_tex(albedo, rough, nt, (float4 *)c->tex4.p, st);
+    nl += launch_render(a, st);
+    return check_launch(c, nl, "render");
+}
+
+dpcs_status dpcs_render_backward(dpcs_ctx *c, dpcs_scene scene, const float *albedo, const float *rough,
+                                 int32_t Ht, int32_t Wt, const float *Ip, const dpcs_view *view,
+                                 const dpcs_params *params, int32_t spp, int32_t bounces, uint64_t seed,
+                                 const float *Ec, const float *Ic, const float *dIc, float *dIp, float *dAlbedo,
+                                 float *dRough, float *dParams, void *stream) {
+    RenderArgs a;
+    Scene *sc = nullptr;
+    dpcs_status s = prepare(c, scene, albedo, rough, Ht, Wt, Ip, view, params, spp, bounces, seed, a, &sc);
+    if (s) return s;
+    if (!Ec || !Ic || !dIc) return fail(c, DPCS_ERR_INVALID_ARG, "null Ec, Ic or dIc");
+    if ((s = set_device(c))) return s;
+    const int64_t np = (int64_t)view->Hp * view->Wp, nt = (int64_t)Ht * Wt, npix = (int64_t)view->Hc * view->Wc;
+    if ((s = ensure(c, c->ep4, (size_t)np * 16, "Ep scratch")) ||
+        (s = ensure(c, c->tex4, (size_t)nt * 16, "texture scratch")) ||
+        (s = ensure(c, c->gE, (size_t)npix * 12, "dEc scratch")) ||
+        (s = ensure(c, c->dEp4, (size_t)np * 16, "dEp scratch")) ||
+        (s = ensure(c, c->dtex4, (size_t)nt * 16, "dtex scratch")) ||
+        (s = ensure(c, c->acc, 16 * sizeof(double), "parameter accumulators")))
+        return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    double *acc = (double *)c->acc.p;
+    cudaMemsetAsync(acc, 0, 16 * sizeof(double), st);
+    cudaMemsetAsync(c->dEp4.p, 0, (size_t)np * 16, st);
+    cudaMemsetAsync(c->dtex4.p, 0, (size_t)nt * 16, st);
+    int nl = launch_prf(Ip, np, params->gamma_p, params->gain_p, (float4 *)c->ep4.p, st);
+    nl += launch_pack_tex(albedo, rough, nt, (float4 *)c->tex4.p, st);
+    nl += launch_crf_backward(dIc, Ec, Ic, npix, params->gamma_c, params->gain_c, params->wb, (float *)c->gE.p, acc, st);
+    a.Ep = (const float4 *)c->ep4.p;
+    a.tex = (const float4 *)c->tex4.p;
+    a.gE = (const float *)c->gE.p;
+    a.dEp = (float4 *)c->dEp4.p;
+    a.dtex = (float4 *)c->dtex4.p;
+    nl += launch_replay(a, st);
+    nl += launch_prf_backward(Ip, (const float4 *)c->dEp4.p, np, params->gamma_p, params->gain_p, dIp, acc, st);
+    if (dAlbedo || dRough) nl += launch_tex_backward((const float4 *)c->dtex4.p, nt, dAlbedo, dRough, st);
+    if (dParams) nl += launch_finalize_params(acc, dParams, st);
+    return check_launch(c, nl, "render_backward");
+}
+
+dpcs_status dpcs_l2_loss(dpcs_ctx *c, const float *Ic, const float *target, int64_t n, float *dIc, float *loss,
+                         void *stream) {
+    if (!c) return DPCS_ERR_INVALID_ARG;
+    if (n <= 0 || !Ic || !target || !dIc || !loss) return fail(c, DPCS_ERR_INVALID_ARG, "bad loss arguments");
+    dpcs_status s = set_device(c);
+    if (s) return s;
+    if ((s = ensure(c, c->partial, (size_t)l2_partial_slots() * sizeof(double), "loss partials"))) return s;
+    return check_launch(c, launch_l2_loss(Ic, target, n, dIc, loss, (double *)c->partial.p, (cudaStream_t)stream),
+                        "l2 loss");
+}
+
+dpcs_status dpcs_adam(dpcs_ctx *c, float *p, const float *g, float *m, float *v, int64_t n, float lr, float beta1,
+                      float beta2, float eps, int32_t step, float lo, float hi, void *stream) {
+    if (!c) return DPCS_ERR_INVALID_ARG;
+    if (n <= 0 || !p || !g || !m || !v || step < 1 || !(lo <= hi) || !(beta1 >= 0.0f && beta1 < 1.0f) ||
+        !(beta2 >= 0.0f && beta2 < 1.0f) || !(eps > 0.0f))
+        return fail(c, DPCS_ERR_INVALID_ARG, "bad Adam arguments");
+    dpcs_status s = set_device(c);
+    if (s) return s;
+    return check_launch(c, launch_adam(p, g, m, v, n, lr, beta1, beta2, eps, step, lo, hi, (cudaStream_t)stream),
+                        "adam");
+}
+
+}  // extern "C"

@@ -1,0 +1,473 @@
+// device.cuh -- device-side building blocks of the DPCS path tracer (sm_103a):
+// Philox4x32-10, FP32 vector algebra, the Lambert+GGX BRDF, bilinear lookups,
+// BVH traversal and the per-sample path (forward and replay record).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace dpcs {
+
+#define DPCS_PI_F 3.14159265358979323846f
+#define DPCS_INV_PI_F 0.318309886183790671538f
+constexpr float kRayEps = 1e-4f;   // origin offset along the shading normal
+constexpr int kStack = 64;         // traversal stack depth
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64 products
+// with the key bumped by the Weyl constants between rounds.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void philox4(uint32_t &c0, uint32_t &c1, uint32_t &c2, uint32_t &c3, uint32_t k0,
+                                        uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+}
+
+// four uniforms in [0,1) with 24 bits, exact in FP32, for counter (pix, s, b, 0)
+__device__ __forceinline__ void rand4(uint32_t k0, uint32_t k1, uint32_t pix, uint32_t s, uint32_t b, float u[4]) {
+    uint32_t c0 = pix, c1 = s, c2 = b, c3 = 0u;
+    philox4(c0, c1, c2, c3, k0, k1);
+    const float sc = 5.9604644775390625e-08f;  // 2^-24
+    u[0] = (float)(c0 >> 8) * sc;
+    u[1] = (float)(c1 >> 8) * sc;
+    u[2] = (float)(c2 >> 8) * sc;
+    u[3] = (float)(c3 >> 8) * sc;
+}
+
+// ---------------------------------------------------------------------------
+// FP32 vectors
+// ---------------------------------------------------------------------------
+struct f3 {
+    float x, y, z;
+};
+__device__ __forceinline__ f3 mk3(float x, float y, float z) { return f3{x, y, z}; }
+__device__ __forceinline__ f3 operator+(f3 a, f3 b) { return mk3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ f3 operator-(f3 a, f3 b) { return mk3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ f3 operator*(f3 a, float s) { return mk3(a.x * s, a.y * s, a.z * s); }
+__device__ __forceinline__ f3 operator*(f3 a, f3 b) { return mk3(a.x * b.x, a.y * b.y, a.z * b.z); }
+__device__ __forceinline__ float dot(f3 a, f3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ f3 cross(f3 a, f3 b) {
+    return mk3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ f3 normalize(f3 a) { return a * (1.0f / sqrtf(dot(a, a))); }
+__device__ __forceinline__ f3 xyz(float4 v) { return mk3(v.x, v.y, v.z); }
+__device__ __forceinline__ f3 mat3v(const float *M, f3 v) {
+    return mk3(M[0] * v.x + M[1] * v.y + M[2] * v.z, M[3] * v.x + M[4] * v.y + M[5] * v.z,
+               M[6] * v.x + M[7] * v.y + M[8] * v.z);
+}
+
+// ---------------------------------------------------------------------------
+// Lambert + GGX BRDF (alpha = rough^2, rough clamped to [0.01, 1]),
+// separable Smith masking, Schlick Fresnel.  spec terms include ks.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float alpha_of(float r, float &dadr) {
+    float rc = r, d = 2.0f * r;
+    if (rc < 0.01f) { rc = 0.01f; d = 0.0f; }
+    if (rc > 1.0f) { rc = 1.0f; d = 0.0f; }
+    dadr = d;
+    return rc * rc;
+}
+
+__device__ __forceinline__ float ggx_D(float ch, float a) {
+    const float a2 = a * a;
+    const float t = ch * ch * (a2 - 1.0f) + 1.0f;
+    return a2 / (DPCS_PI_F * t * t);
+}
+
+__device__ __forceinline__ float ggx_G1(float c, float a) {
+    const float a2 = a * a;
+    return 2.0f * c / (c + sqrtf(a2 + (1.0f - a2) * c * c));
+}
+
+// ks * D G F / (4 ci co) and its derivative in roughness r (0 if ks == 0)
+__device__ __forceinline__ float spec_eval(f3 n, f3 wo, f3 wi, float r, float ks, float f0, float &dspec_dr) {
+    dspec_dr = 0.0f;
+    const float co = dot(n, wo), ci = dot(n, wi);
+    if (ks <= 0.0f || co <= 0.0f || ci <= 0.0f) return 0.0f;
+    float dadr;
+    const float a = alpha_of(r, dadr);
+    const f3 h = normalize(wo + wi);
+    const float ch = dot(n, h);
+    const float a2 = a * a;
+    const float t = ch * ch * (a2 - 1.0f) + 1.0f;
+    const float D = a2 / (DPCS_PI_F * t * t);
+    const float si = sqrtf(a2 + (1.0f - a2) * ci * ci), so = sqrtf(a2 + (1.0f - a2) * co * co);
+    const float G = (2.0f * ci / (ci + si)) * (2.0f * co / (co + so));
+    float m = fmaxf(0.0f, 1.0f - dot(wo, h));
+    const float m2 = m * m;
+    const float F = f0 + (1.0f - f0) * (m2 * m2 * m);
+    const float spec = ks * D * G * F / (4.0f * ci * co);
+    const float dlnD = 2.0f / a - 4.0f * a * ch * ch / t;
+    const float dlnG = -(a * (1.0f - ci * ci) / si) / (ci + si) - (a * (1.0f - co * co) / so) / (co + so);
+    dspec_dr = spec * (dlnD + dlnG) * dadr;
+    return spec;
+}
+
+// orthonormal basis around n (Duff et al., JCGT 2017), sign from n.z >= 0
+__device__ __forceinline__ void onb(f3 n, f3 &t, f3 &b) {
+    const float sg = n.z >= 0.0f ? 1.0f : -1.0f;
+    const float a = -1.0f / (sg + n.z);
+    const float bb = n.x * n.y * a;
+    t = mk3(1.0f + sg * n.x * n.x * a, sg * bb, -sg * n.x);
+    b = mk3(bb, sg + n.y * n.y * a, -n.y);
+}
+
+__device__ __forceinline__ float spec_prob(float ks) { return ks > 0.0f ? 0.5f : 0.0f; }
+
+__device__ __forceinline__ float bsdf_pdf(f3 n, f3 wo, f3 wi, float r, float ks) {
+    const float ci = dot(n, wi), co = dot(n, wo);
+    if (ci <= 0.0f || co <= 0.0f) return 0.0f;
+    const float ps = spec_prob(ks);
+    float p = (1.0f - ps) * ci * DPCS_INV_PI_F;
+    if (ps > 0.0f) {
+        float dadr;
+        const float a = alpha_of(r, dadr);
+        const f3 h = normalize(wo + wi);
+        p += ps * ggx_G1(co, a) * ggx_D(dot(n, h), a) / (4.0f * co);
+    }
+    return p;
+}
+
+// u0 picks the lobe, (u1, u2) the direction: cosine hemisphere or GGX
+// visible normals (Heitz, JCGT 2018).  false if wi is below the surface.
+__device__ __forceinline__ bool bsdf_sample(f3 n, f3 wo, float r, float ks, float u0, float u1, float u2, f3 &wi) {
+    f3 T, B;
+    onb(n, T, B);
+    f3 l;
+    float sp, cp;
+    sincospif(2.0f * u2, &sp, &cp);
+    if (u0 >= spec_prob(ks)) {
+        const float rr = sqrtf(u1);
+        l = mk3(rr * cp, rr * sp, sqrtf(fmaxf(0.0f, 1.0f - u1)));
+    } else {
+        float dadr;
+        const float a = alpha_of(r, dadr);
+        const f3 wl = mk3(dot(wo, T), dot(wo, B), dot(wo, n));
+        const f3 Vh = normalize(mk3(a * wl.x, a * wl.y, wl.z));
+        const float lsq = Vh.x * Vh.x + Vh.y * Vh.y;
+        const f3 T1 = lsq > 0.0f ? mk3(-Vh.y, Vh.x, 0.0f) * (1.0f / sqrtf(lsq)) : mk3(1.0f, 0.0f, 0.0f);
+        const f3 T2 = cross(Vh, T1);
+        const float rr = sqrtf(u1);
+        const float t1 = rr * cp;
+        float t2 = rr * sp;
+        const float s = 0.5f * (1.0f + Vh.z);
+        t2 = (1.0f - s) * sqrtf(fmaxf(0.0f, 1.0f - t1 * t1)) + s * t2;
+        const f3 Nh = T1 * t1 + T2 * t2 + Vh * sqrtf(fmaxf(0.0f, 1.0f - t1 * t1 - t2 * t2));
+        const f3 Ne = normalize(mk3(a * Nh.x, a * Nh.y, fmaxf(0.0f, Nh.z)));
+        l = Ne * (2.0f * dot(wl, Ne)) - wl;
+    }
+    wi = T * l.x + B * l.y + n * l.z;
+    return dot(n, wi) > 0.0f;
+}
+
+// ---------------------------------------------------------------------------
+// bilinear lookup, texel centres at (i + 1/2), clamp to edge
+// ---------------------------------------------------------------------------
+struct Bilin {
+    int x0, y0;
+    float fx, fy;
+};
+__device__ __forceinline__ Bilin bilin_setup(float xp, float yp, int W, int H) {
+    float x = xp - 0.5f, y = yp - 0.5f;
+    x = fminf(fmaxf(x, -1.0f), (float)W);
+    y = fminf(fmaxf(y, -1.0f), (float)H);
+    const float fx0 = floorf(x), fy0 = floorf(y);
+    Bilin b;
+    b.fx = x - fx0;
+    b.fy = y - fy0;
+    b.x0 = (int)fx0;
+    b.y0 = (int)fy0;
+    return b;
+}
+__device__ __forceinline__ void bilin_taps(const Bilin &b, int W, int H, int idx[4], float w[4]) {
+    const int xa = min(max(b.x0, 0), W - 1), xb = min(max(b.x0 + 1, 0), W - 1);
+    const int ya = min(max(b.y0, 0), H - 1), yb = min(max(b.y0 + 1, 0), H - 1);
+    idx[0] = ya * W + xa;
+    idx[1] = ya * W + xb;
+    idx[2] = yb * W + xa;
+    idx[3] = yb * W + xb;
+    w[0] = (1.0f - b.fx) * (1.0f - b.fy);
+    w[1] = b.fx * (1.0f - b.fy);
+    w[2] = (1.0f - b.fx) * b.fy;
+    w[3] = b.fx * b.fy;
+}
+__device__ __forceinline__ float4 bilin_fetch(const float4 *__restrict__ img, const Bilin &b, int W, int H) {
+    int idx[4];
+    float w[4];
+    bilin_taps(b, W, H, idx, w);
+    float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float4 v = __ldg(img + idx[k]);
+        r.x += w[k] * v.x;
+        r.y += w[k] * v.y;
+        r.z += w[k] * v.z;
+        r.w += w[k] * v.w;
+    }
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// BVH traversal.  Node = 4 float4: (l.lo.x, l.hi.x, l.lo.y, l.hi.y),
+// (r.lo.x, r.hi.x, r.lo.y, r.hi.y), (l.lo.z, l.hi.z, r.lo.z, r.hi.z),
+// (left ref, right ref, -, -) with refs >= 0 internal, < 0 leaf ~position.
+// Triangle = 3 float4: (v0, original index), e1, e2.
+// ---------------------------------------------------------------------------
+struct Ray {
+    f3 o, d, inv;
+};
+__device__ __forceinline__ Ray make_ray(f3 o, f3 d) {
+    Ray r;
+    r.o = o;
+    r.d = d;
+    const float e = 1e-20f;
+    r.inv = mk3(1.0f / (fabsf(d.x) > e ? d.x : copysignf(e, d.x)), 1.0f / (fabsf(d.y) > e ? d.y : copysignf(e, d.y)),
+                1.0f / (fabsf(d.z) > e ? d.z : copysignf(e, d.z)));
+    return r;
+}
+
+// slab test; the far bound is widened by a few ulps (Ize, JCGT 2013) so that
+// flat boxes of axis-aligned walls are never missed by rounding
+__device__ __forceinline__ bool slab(const Ray &r, float lx, float hx, float ly, float hy, float lz, float hz,
+                                     float tmax, float &tnear) {
+    const float tx0 = (lx - r.o.x) * r.inv.x, tx1 = (hx - r.o.x) * r.inv.x;
+    const float ty0 = (ly - r.o.y) * r.inv.y, ty1 = (hy - r.o.y) * r.inv.y;
+    const float tz0 = (lz - r.o.z) * r.inv.z, tz1 = (hz - r.o.z) * r.inv.z;
+    const float tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.0f));
+    const float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tmax));
+    tnear = tn;
+    return tn <= tf * 1.0000004f;
+}
+
+// Moller-Trumbore, two-sided, t in (0, tmax]
+__device__ __forceinline__ bool tri_isect(const Ray &r, f3 v0, f3 e1, f3 e2, float tmax, float &t, float &u,
+                                          float &v) {
+    const f3 p = cross(r.d, e2);
+    const float det = dot(e1, p);
+    if (det == 0.0f) return false;
+    const float inv = 1.0f / det;
+    const f3 s = r.o - v0;
+    u = dot(s, p) * inv;
+    if (u < 0.0f || u > 1.0f) return false;
+    const f3 q = cross(s, e1);
+    v = dot(r.d, q) * inv;
+    if (v < 0.0f || u + v > 1.0f) return false;
+    t = dot(e2, q) * inv;
+    return t > 0.0f && t <= tmax;
+}
+
+struct Hit {
+    int pos;   // leaf (sorted) position, -1 = miss
+    int orig;  // original triangle index
+    float t, u, v;
+};
+
+template <bool ANY>
+__device__ __forceinline__ bool traverse(const float4 *__restrict__ nodes, const float4 *__restrict__ tris,
+                                         int32_t root, int32_t T, const Ray &ray, float tmax, Hit &h,
+                                         unsigned *status) {
+    h.pos = -1;
+    h.orig = 0x7fffffff;
+    h.t = tmax;
+    if (root == kEmptyRoot) return false;
+    int stack[kStack];
+    int sp = 0;
+    int node = root;
+    int visits = 0;
+    const int cap = 2 * T + 16;
+    while (true) {
+        if (++visits > cap) {
+            atomicOr(status, kStatusTraversalLimit);
+            h.pos = -1;
+            return false;
+        }
+        if (node >= 0) {
+            const float4 n0 = __ldg(nodes + 4 * node + 0);
+            const float4 n1 = __ldg(nodes + 4 * node + 1);
+            const float4 n2 = __ldg(nodes + 4 * node + 2);
+            const float4 n3 = __ldg(nodes + 4 * node + 3);
+            float tl, tr;
+            const bool hl = slab(ray, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, h.t, tl);
+            const bool hr = slab(ray, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, h.t, tr);
+            const int cl = __float_as_int(n3.x), cr = __float_as_int(n3.y);
+            if (hl && hr) {
+                if (sp >= kStack) {
+                    atomicOr(status, kStatusTraversalLimit);
+                    h.pos = -1;
+                    return false;
+                }
+                const bool lfirst = tl <= tr;
+                stack[sp++] = lfirst ? cr : cl;
+                node = lfirst ? cl : cr;
+                continue;
+            }
+            if (hl) { node = cl; continue; }
+            if (hr) { node = cr; continue; }
+        } else {
+            const int pos = ~node;
+            const float4 a = __ldg(tris + 3 * pos + 0);
+            const float4 b = __ldg(tris + 3 * pos + 1);
+            const float4 c = __ldg(tris + 3 * pos + 2);
+            float t, u, v;
+            if (tri_isect(ray, xyz(a), xyz(b), xyz(c), h.t, t, u, v)) {
+                const int orig = __float_as_int(a.w);
+                // closest: ties in t go to the lowest original index
+                if (t < h.t || (!ANY && t == h.t && orig < h.orig)) {
+                    h.pos = pos;
+                    h.orig = orig;
+                    h.t = t;
+                    h.u = u;
+                    h.v = v;
+                    if (ANY) return true;
+                }
+            }
+        }
+        if (sp == 0) break;
+        node = stack[--sp];
+    }
+    return h.pos >= 0;
+}
+
+// ---------------------------------------------------------------------------
+// One camera path: Eq. 10 with next-event estimation to the pinhole
+// projector; optionally records what the replay adjoint needs.
+// ---------------------------------------------------------------------------
+struct VRec {
+    int tx0, ty0, px0, py0;
+    float tfx, tfy, pfx, pfy;
+    float beta[3];
+    float Ep[3];
+    float G;       // k cos_p cos_s / r^2 when projector light arrived, else 0
+    float rho[3];
+    float sp, dsp; // spec(wo, wp) and d/dr
+    float si, dsi; // spec(wo, wi) and d/dr
+    float cw;      // cos_i / (pdf q) when the path continued, else 0
+    unsigned unc;  // bit j: channel j not clipped
+};
+
+template <bool REC>
+__device__ __forceinline__ f3 trace_path(const RenderArgs &a, uint32_t pix, uint32_t s, VRec *rec, int &nv) {
+    float u[4];
+    nv = 0;
+    rand4(a.key0, a.key1, pix, s, 0u, u);
+    const float fx = (float)(pix % (uint32_t)a.Wc) + (a.jitter ? u[0] : 0.5f);
+    const float fy = (float)(pix / (uint32_t)a.Wc) + (a.jitter ? u[1] : 0.5f);
+    f3 o = mk3(0.f, 0.f, 0.f);
+    f3 d = normalize(mat3v(a.Kci, mk3(fx, fy, 1.0f)));
+    f3 beta = mk3(1.f, 1.f, 1.f);
+    f3 L = mk3(0.f, 0.f, 0.f);
+    const f3 cp = mk3(a.cp[0], a.cp[1], a.cp[2]);
+    for (int b = 1; b <= a.bounces; ++b) {
+        Hit h;
+        const Ray ray = make_ray(o, d);
+        if (!traverse<false>(a.nodes, a.tris, a.root, a.T, ray, INFINITY, h, a.status)) break;
+        const float4 A = __ldg(a.tris + 3 * h.pos + 0);
+        const float4 E1 = __ldg(a.tris + 3 * h.pos + 1);
+        const float4 E2 = __ldg(a.tris + 3 * h.pos + 2);
+        const f3 e1 = xyz(E1), e2 = xyz(E2);
+        const f3 x = xyz(A) + e1 * h.u + e2 * h.v;
+        f3 n = normalize(cross(e1, e2));
+        if (dot(n, d) > 0.0f) n = n * -1.0f;
+        const float2 t0 = __ldg(a.tuv + 3 * h.pos + 0), t1 = __ldg(a.tuv + 3 * h.pos + 1),
+                     t2 = __ldg(a.tuv + 3 * h.pos + 2);
+        const float w0 = 1.0f - h.u - h.v;
+        const float su = w0 * t0.x + h.u * t1.x + h.v * t2.x;
+        const float sv = w0 * t0.y + h.u * t1.y + h.v * t2.y;
+        const Bilin tb = bilin_setup(su * (float)a.Wt, sv * (float)a.Ht, a.Wt, a.Ht);
+        const float4 tex = bilin_fetch(a.tex, tb, a.Wt, a.Ht);
+        const f3 rho = mk3(tex.x, tex.y, tex.z);
+        const float rough = tex.w;
+        const f3 wo = d * -1.0f;
+        VRec *R = REC ? &rec[nv] : nullptr;
+        if (REC) {
+            R->tx0 = tb.x0; R->ty0 = tb.y0; R->tfx = tb.fx; R->tfy = tb.fy;
+            R->beta[0] = beta.x; R->beta[1] = beta.y; R->beta[2] = beta.z;
+            R->rho[0] = rho.x; R->rho[1] = rho.y; R->rho[2] = rho.z;
+            R->G = 0.0f; R->cw = 0.0f; R->unc = 0u; R->sp = R->dsp = R->si = R->dsi = 0.0f;
+        }
+        ++nv;
+
+        // next-event estimation to the projector (Eqs. 1, 2, 3, 6)
+        const f3 X = mat3v(a.Rp, x) + mk3(a.tp[0], a.tp[1], a.tp[2]);
+        const f3 q = mat3v(a.Kp, X);
+        if (q.z > 0.0f && X.z > 0.0f) {
+            const float up = q.x / q.z, vp = q.y / q.z;
+            if (up >= 0.0f && up < (float)a.Wp && vp >= 0.0f && vp < (float)a.Hp) {
+                const f3 v = cp - x;
+                const float r2 = dot(v, v), dist = sqrtf(r2);
+                const f3 wp = v * (1.0f / dist);
+                const float cs = dot(n, wp);
+                if (cs > 0.0f) {
+                    const float cpz = X.z / sqrtf(dot(X, X));
+                    const f3 so = x + n * kRayEps;
+                    const f3 sv = cp - so;
+                    const float sd = sqrtf(dot(sv, sv));
+                    Hit hs;
+                    const Ray sray = make_ray(so, sv * (1.0f / sd));
+                    if (!traverse<true>(a.nodes, a.tris, a.root, a.T, sray, sd - kRayEps, hs, a.status)) {
+                        const Bilin pb = bilin_setup(up, vp, a.Wp, a.Hp);
+                        const float4 ep = bilin_fetch(a.Ep, pb, a.Wp, a.Hp);
+                        const float G = a.k_proj * cpz * cs / r2;
+                        float dsp;
+                        const float sp = spec_eval(n, wo, wp, rough, a.ks, a.f0, dsp);
+                        const f3 fp = mk3(rho.x * DPCS_INV_PI_F + sp, rho.y * DPCS_INV_PI_F + sp,
+                                          rho.z * DPCS_INV_PI_F + sp);
+                        f3 c = beta * fp * mk3(ep.x, ep.y, ep.z) * G;
+                        unsigned unc = 7u;
+                        if (a.clip > 0.0f) {
+                            if (c.x > a.clip) { c.x = a.clip; unc &= ~1u; }
+                            if (c.y > a.clip) { c.y = a.clip; unc &= ~2u; }
+                            if (c.z > a.clip) { c.z = a.clip; unc &= ~4u; }
+                        }
+                        L = L + c;
+                        if (REC) {
+                            R->px0 = pb.x0; R->py0 = pb.y0; R->pfx = pb.fx; R->pfy = pb.fy;
+                            R->Ep[0] = ep.x; R->Ep[1] = ep.y; R->Ep[2] = ep.z;
+                            R->G = G; R->sp = sp; R->dsp = dsp; R->unc = unc;
+                        }
+                    }
+                }
+            }
+        }
+        if (b == a.bounces) break;
+
+        // continuation: BSDF sampling, throughput, Russian roulette (Eq. 10)
+        rand4(a.key0, a.key1, pix, s, (uint32_t)b, u);
+        f3 wi;
+        if (!bsdf_sample(n, wo, rough, a.ks, u[0], u[1], u[2], wi)) break;
+        const float pdf = bsdf_pdf(n, wo, wi, rough, a.ks);
+        if (!(pdf > 0.0f)) break;
+        float qrr = 1.0f;
+        if (a.rr_start > 0 && b >= a.rr_start) {
+            if (u[3] >= a.rr_q) break;
+            qrr = a.rr_q;
+        }
+        float dsi;
+        const float si = spec_eval(n, wo, wi, rough, a.ks, a.f0, dsi);
+        const float cw = dot(n, wi) / (pdf * qrr);
+        const f3 fi = mk3(rho.x * DPCS_INV_PI_F + si, rho.y * DPCS_INV_PI_F + si, rho.z * DPCS_INV_PI_F + si);
+        beta = beta * fi * cw;
+        if (REC) {
+            R->si = si; R->dsi = dsi; R->cw = cw;
+        }
+        o = x + n * kRayEps;
+        d = wi;
+    }
+    return L;
+}
+
+}  // namespace dpcs

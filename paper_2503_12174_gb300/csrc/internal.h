@@ -1,0 +1,88 @@
+// internal.h -- host-side structures shared by the translation units of libdpcs.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "dpcs.h"
+
+namespace dpcs {
+
+// Device status bits, OR-ed into the context's status word by kernels.
+enum : unsigned {
+    kStatusTraversalLimit = 1u << 0,  // stack overflow or node-visit cap
+    kStatusBoundsCheck = 1u << 1,     // an index failed a bounds check
+};
+
+// Resident scene: LBVH nodes (64 B: two child boxes and two child references),
+// triangles in leaf order (48 B: v0 with the original index in .w, e1, e2)
+// and their per-corner texture coordinates.
+struct Scene {
+    int32_t T = 0;
+    int32_t root = 0;          // 0 = internal node 0; ~0 = single leaf; kEmptyRoot = no geometry
+    float4 *nodes = nullptr;   // 4 x (T-1)
+    float4 *tris = nullptr;    // 3 x T
+    float2 *tuv = nullptr;     // 3 x T
+    uint32_t *codes = nullptr; // sorted Morton codes, T
+    int32_t *order = nullptr;  // original triangle of each sorted position, T
+    size_t bytes = 0;
+};
+constexpr int32_t kEmptyRoot = (int32_t)0x80000000;
+
+// Kernel arguments of one render / replay launch (passed by value).
+struct RenderArgs {
+    const float4 *nodes;
+    const float4 *tris;
+    const float2 *tuv;
+    int32_t root;
+    int32_t T;
+    const float4 *tex;   // Ht x Wt: albedo rgb, roughness
+    int32_t Ht, Wt;
+    const float4 *Ep;    // Hp x Wp: PRF-mapped projector image rgb, 0
+    int32_t Hp, Wp;
+    float Kci[9];        // inverse camera intrinsics
+    float Kp[9], Rp[9], tp[3], cp[3];
+    int32_t Hc, Wc;
+    float gamma_c[3], gain_c, wb[3];
+    float k_proj, ks, f0, rr_q, clip;
+    int32_t rr_start, jitter;
+    int32_t spp, bounces;
+    uint32_t key0, key1;
+    int32_t log2L;       // log2 of lanes per pixel
+    float *Ic;
+    float *Ec;
+    // backward only
+    const float *gE;     // dLoss/dEc per pixel (Hc x Wc x 3)
+    float4 *dEp;         // dLoss/dEp accumulators (Hp x Wp)
+    float4 *dtex;        // dLoss/d(albedo, rough) accumulators (Ht x Wt)
+    unsigned *status;
+};
+
+// Launchers (render.cu, lbvh.cu, optim.cu).  Each returns the number of
+// kernels it enqueued, or a negative dpcs_status.
+int launch_lbvh_build(const float *d_verts, int32_t V, const int32_t *d_tris, int32_t T, const float *d_uv,
+                      Scene &sc, void *scratch, size_t scratch_bytes, cudaStream_t st);
+size_t lbvh_scratch_bytes(int32_t T);
+
+int launch_prf(const float *Ip, int64_t ntex, const float gamma_p[3], float gain_p, float4 *Ep, cudaStream_t st);
+int launch_pack_tex(const float *albedo, const float *rough, int64_t ntex, float4 *tex, cudaStream_t st);
+int launch_render(const RenderArgs &a, cudaStream_t st);
+int launch_trace(const Scene &sc, const float *o, const float *d, int64_t n, float *t, int32_t *tri,
+                 unsigned *status, cudaStream_t st);
+int launch_crf_backward(const float *dIc, const float *Ec, const float *Ic, int64_t npix, const float gamma_c[3],
+                        float gain_c, const float wb[3], float *gE, double *acc, cudaStream_t st);
+int launch_replay(const RenderArgs &a, cudaStream_t st);
+int launch_prf_backward(const float *Ip, const float4 *dEp, int64_t ntex, const float gamma_p[3], float gain_p,
+                        float *dIp, double *acc, cudaStream_t st);
+int launch_tex_backward(const float4 *dtex, int64_t ntex, float *dAlbedo, float *dRough, cudaStream_t st);
+int launch_finalize_params(const double *acc, float *dParams, cudaStream_t st);
+int launch_zero(void *p, size_t bytes, cudaStream_t st);
+int launch_l2_loss(const float *Ic, const float *target, int64_t n, float *dIc, float *loss, double *partial,
+                   cudaStream_t st);
+int l2_partial_slots();
+int launch_adam(float *p, const float *g, float *m, float *v, int64_t n, float lr, float b1, float b2, float eps,
+                int32_t step, float lo, float hi, cudaStream_t st);
+
+}  // namespace dpcs

@@ -1,0 +1,300 @@
+// lbvh.cu -- LBVH construction on the device: FP32 Morton codes of triangle
+// centroids, a stable LSD radix sort of (code, index), the Karras (HPG 2012)
+// radix tree, and a bottom-up AABB refit that packs 64-byte nodes and 48-byte
+// triangles.  Integer results (codes, order, topology) and the FP32 min/max
+// boxes are exact and reproducible.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace dpcs {
+
+namespace {
+
+constexpr int kSortTile = 256;  // items (and threads) per radix-sort block
+
+// centroids (v0 + v1 + v2) * (1/3) in FP32 without contraction
+__global__ void k_centroids(const float *__restrict__ verts, const int32_t *__restrict__ tris, int T,
+                            float *__restrict__ cen) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= T) return;
+    const float third = 1.0f / 3.0f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float a = verts[3 * tris[3 * i] + k], b = verts[3 * tris[3 * i + 1] + k], c = verts[3 * tris[3 * i + 2] + k];
+        cen[3 * i + k] = __fmul_rn(__fadd_rn(__fadd_rn(a, b), c), third);
+    }
+}
+
+// single-block min/max of the centroids -> bounds[0..2] lo, [3..5] hi
+__global__ void k_bounds(const float *__restrict__ cen, int T, float *__restrict__ bounds) {
+    __shared__ float slo[3][32], shi[3][32];
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int i = threadIdx.x; i < T; i += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = fminf(lo[k], cen[3 * i + k]);
+            hi[k] = fmaxf(hi[k], cen[3 * i + k]);
+        }
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        for (int off = 16; off; off >>= 1) {
+            lo[k] = fminf(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], off));
+            hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], off));
+        }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0)
+        for (int k = 0; k < 3; ++k) { slo[k][w] = lo[k]; shi[k][w] = hi[k]; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < 3; ++k) {
+            float a = INFINITY, b = -INFINITY;
+            for (int j = 0; j < (int)(blockDim.x >> 5); ++j) { a = fminf(a, slo[k][j]); b = fmaxf(b, shi[k][j]); }
+            bounds[k] = a;
+            bounds[3 + k] = b;
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t expand10(uint32_t v) {
+    v &= 0x3ffu;
+    v = (v | (v << 16)) & 0x030000FFu;
+    v = (v | (v << 8)) & 0x0300F00Fu;
+    v = (v | (v << 4)) & 0x030C30C3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+// 30-bit Morton code of the centroid normalised into the centroid bounds
+__global__ void k_morton(const float *__restrict__ cen, const float *__restrict__ bounds, int T,
+                         uint32_t *__restrict__ codes, int32_t *__restrict__ idx) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= T) return;
+    uint32_t q[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float lo = bounds[k], ext = __fsub_rn(bounds[3 + k], lo);
+        const float inv = ext > 0.0f ? __frcp_rn(ext) : 0.0f;
+        const float nrm = __fmul_rn(__fsub_rn(cen[3 * i + k], lo), inv);
+        float f = floorf(__fmul_rn(nrm, 1024.0f));
+        f = fminf(fmaxf(f, 0.0f), 1023.0f);
+        q[k] = (uint32_t)f;
+    }
+    codes[i] = (expand10(q[0]) << 2) | (expand10(q[1]) << 1) | expand10(q[2]);
+    idx[i] = i;
+}
+
+// --- stable LSD radix sort, 8-bit digits -----------------------------------
+__global__ void k_radix_hist(const uint32_t *__restrict__ keys, int n, int shift, int nblocks,
+                             uint32_t *__restrict__ hist) {
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int i = blockIdx.x * kSortTile + threadIdx.x;
+    if (i < n) atomicAdd(&h[(keys[i] >> shift) & 0xffu], 1u);
+    __syncthreads();
+    hist[threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+}
+
+// exclusive scan of `total` counters in one block
+__global__ void k_radix_scan(uint32_t *__restrict__ hist, int total) {
+    __shared__ uint32_t part[1024];
+    const int per = (total + blockDim.x - 1) / blockDim.x;
+    const int b0 = threadIdx.x * per;
+    uint32_t s = 0;
+    for (int i = b0; i < min(b0 + per, total); ++i) s += hist[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < (int)blockDim.x; off <<= 1) {
+        const uint32_t v = threadIdx.x >= (unsigned)off ? part[threadIdx.x - off] : 0u;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    uint32_t run = part[threadIdx.x] - s;
+    for (int i = b0; i < min(b0 + per, total); ++i) {
+        const uint32_t c = hist[i];
+        hist[i] = run;
+        run += c;
+    }
+}
+
+__global__ void k_radix_scatter(const uint32_t *__restrict__ kin, const int32_t *__restrict__ vin,
+                                uint32_t *__restrict__ kout, int32_t *__restrict__ vout, int n, int shift,
+                                int nblocks, const uint32_t *__restrict__ offs) {
+    __shared__ uint32_t cnt[kSortTile / 32][256];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int j = threadIdx.x; j < (kSortTile / 32) * 256; j += blockDim.x) (&cnt[0][0])[j] = 0u;
+    __syncthreads();
+    const int i = blockIdx.x * kSortTile + threadIdx.x;
+    const bool valid = i < n;
+    const uint32_t key = valid ? kin[i] : 0u;
+    const uint32_t digit = valid ? ((key >> shift) & 0xffu) : 0x100u;
+    const unsigned peers = __match_any_sync(0xffffffffu, digit);
+    const unsigned lt = (1u << lane) - 1u;
+    const uint32_t rank = __popc(peers & lt);
+    if (valid && (peers & lt) == 0u) cnt[w][digit] = __popc(peers);
+    __syncthreads();
+    if (valid) {
+        uint32_t off = rank;
+        for (int ww = 0; ww < w; ++ww) off += cnt[ww][digit];
+        const uint32_t dst = offs[digit * nblocks + blockIdx.x] + off;
+        kout[dst] = key;
+        vout[dst] = vin[i];
+    }
+}
+
+// --- Karras radix tree -------------------------------------------------------
+__device__ __forceinline__ int delta(const uint32_t *__restrict__ c, int T, int i, int j) {
+    if (j < 0 || j > T - 1) return -1;
+    const uint32_t a = c[i], b = c[j];
+    if (a == b) return 32 + __clz((uint32_t)(i ^ j));
+    return __clz(a ^ b);
+}
+
+__global__ void k_karras(const uint32_t *__restrict__ codes, int T, float4 *__restrict__ nodes,
+                         int32_t *__restrict__ parent) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= T - 1) return;
+    const int d = (delta(codes, T, i, i + 1) - delta(codes, T, i, i - 1)) >= 0 ? 1 : -1;
+    const int dmin = delta(codes, T, i, i - d);
+    int lmax = 2;
+    while (delta(codes, T, i, i + lmax * d) > dmin) lmax <<= 1;
+    int l = 0;
+    for (int t = lmax >> 1; t >= 1; t >>= 1)
+        if (delta(codes, T, i, i + (l + t) * d) > dmin) l += t;
+    const int j = i + l * d;
+    const int dnode = delta(codes, T, i, j);
+    int s = 0, t = l;
+    do {
+        t = (t + 1) >> 1;
+        if (delta(codes, T, i, i + (s + t) * d) > dnode) s += t;
+    } while (t > 1);
+    const int g = i + s * d + min(d, 0);
+    const int left = (min(i, j) == g) ? ~g : g;
+    const int right = (max(i, j) == g + 1) ? ~(g + 1) : g + 1;
+    nodes[4 * i + 3] = make_float4(__int_as_float(left), __int_as_float(right), 0.0f, 0.0f);
+    if (left >= 0) parent[left] = i; else parent[T - 1 + g] = i;
+    if (right >= 0) parent[right] = i; else parent[T - 1 + g + 1] = i;
+}
+
+__device__ __forceinline__ void store_box(float *nd, bool right, const float b[6]) {
+    // node float layout: [0..3] left x/y, [4..7] right x/y, [8..11] z of left, right
+    float *xy = nd + (right ? 4 : 0);
+    float *z = nd + 8 + (right ? 2 : 0);
+    __stcg(xy + 0, b[0]);
+    __stcg(xy + 1, b[3]);
+    __stcg(xy + 2, b[1]);
+    __stcg(xy + 3, b[4]);
+    __stcg(z + 0, b[2]);
+    __stcg(z + 1, b[5]);
+}
+
+// one thread per leaf: pack the triangle, then walk up; the second thread to
+// reach a node forms the union of its two child boxes and continues
+__global__ void k_refit(const float *__restrict__ verts, const int32_t *__restrict__ tris,
+                        const float *__restrict__ uv, const int32_t *__restrict__ order, int T,
+                        float4 *__restrict__ nodes, const int32_t *__restrict__ parent,
+                        int32_t *__restrict__ flags, float4 *__restrict__ tout, float2 *__restrict__ tuv) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= T) return;
+    const int t = order[p];
+    const int i0 = tris[3 * t], i1 = tris[3 * t + 1], i2 = tris[3 * t + 2];
+    const float x0 = verts[3 * i0], y0 = verts[3 * i0 + 1], z0 = verts[3 * i0 + 2];
+    const float x1 = verts[3 * i1], y1 = verts[3 * i1 + 1], z1 = verts[3 * i1 + 2];
+    const float x2 = verts[3 * i2], y2 = verts[3 * i2 + 1], z2 = verts[3 * i2 + 2];
+    tout[3 * p + 0] = make_float4(x0, y0, z0, __int_as_float(t));
+    tout[3 * p + 1] = make_float4(x1 - x0, y1 - y0, z1 - z0, 0.0f);
+    tout[3 * p + 2] = make_float4(x2 - x0, y2 - y0, z2 - z0, 0.0f);
+    tuv[3 * p + 0] = make_float2(uv[2 * i0], uv[2 * i0 + 1]);
+    tuv[3 * p + 1] = make_float2(uv[2 * i1], uv[2 * i1 + 1]);
+    tuv[3 * p + 2] = make_float2(uv[2 * i2], uv[2 * i2 + 1]);
+    if (T < 2) return;
+    float b[6] = {fminf(fminf(x0, x1), x2), fminf(fminf(y0, y1), y2), fminf(fminf(z0, z1), z2),
+                  fmaxf(fmaxf(x0, x1), x2), fmaxf(fmaxf(y0, y1), y2), fmaxf(fmaxf(z0, z1), z2)};
+    int child = ~p;
+    int node = parent[T - 1 + p];
+    while (true) {
+        float *nd = reinterpret_cast<float *>(nodes + 4 * node);
+        const int cl = __float_as_int(__ldcg(nd + 12));
+        store_box(nd, cl != child, b);
+        __threadfence();
+        if (atomicAdd(&flags[node], 1) == 0) return;
+        __threadfence();
+        // both children are final: union
+        const float lx0 = __ldcg(nd + 0), lx1 = __ldcg(nd + 1), ly0 = __ldcg(nd + 2), ly1 = __ldcg(nd + 3);
+        const float rx0 = __ldcg(nd + 4), rx1 = __ldcg(nd + 5), ry0 = __ldcg(nd + 6), ry1 = __ldcg(nd + 7);
+        const float lz0 = __ldcg(nd + 8), lz1 = __ldcg(nd + 9), rz0 = __ldcg(nd + 10), rz1 = __ldcg(nd + 11);
+        b[0] = fminf(lx0, rx0); b[3] = fmaxf(lx1, rx1);
+        b[1] = fminf(ly0, ry0); b[4] = fmaxf(ly1, ry1);
+        b[2] = fminf(lz0, rz0); b[5] = fmaxf(lz1, rz1);
+        if (node == 0) return;
+        child = node;
+        node = parent[node];
+    }
+}
+
+inline size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
+
+}  // namespace
+
+size_t lbvh_scratch_bytes(int32_t T) {
+    const size_t n = (size_t)(T > 0 ? T : 1);
+    const size_t nb = (n + kSortTile - 1) / kSortTile;
+    return align256(3 * n * 4) + align256(6 * 4) + 4 * align256(n * 4) + align256(256 * nb * 4) +
+           align256((2 * n) * 4) + align256(n * 4);
+}
+
+int launch_lbvh_build(const float *d_verts, int32_t V, const int32_t *d_tris, int32_t T, const float *d_uv,
+                      Scene &sc, void *scratch, size_t scratch_bytes, cudaStream_t st) {
+    (void)V;
+    if (T <= 0) {
+        sc.root = kEmptyRoot;
+        return 0;
+    }
+    if (scratch_bytes < lbvh_scratch_bytes(T)) return DPCS_ERR_INVALID_ARG;
+    const size_t n = (size_t)T;
+    const int nb = (int)((n + kSortTile - 1) / kSortTile);
+    char *p = (char *)scratch;
+    auto take = [&](size_t bytes) {
+        char *r = p;
+        p += align256(bytes);
+        return (void *)r;
+    };
+    float *cen = (float *)take(3 * n * 4);
+    float *bounds = (float *)take(6 * 4);
+    uint32_t *ka = (uint32_t *)take(n * 4), *kb = (uint32_t *)take(n * 4);
+    int32_t *va = (int32_t *)take(n * 4), *vb = (int32_t *)take(n * 4);
+    uint32_t *hist = (uint32_t *)take(256 * (size_t)nb * 4);
+    int32_t *parent = (int32_t *)take(2 * n * 4);
+    int32_t *flags = (int32_t *)take(n * 4);
+    int launches = 0;
+    const int tb = 256, gb = (T + tb - 1) / tb;
+    k_centroids<<<gb, tb, 0, st>>>(d_verts, d_tris, T, cen);
+    k_bounds<<<1, 1024, 0, st>>>(cen, T, bounds);
+    k_morton<<<gb, tb, 0, st>>>(cen, bounds, T, ka, va);
+    launches += 3;
+    for (int shift = 0; shift < 32; shift += 8) {
+        k_radix_hist<<<nb, kSortTile, 0, st>>>(ka, T, shift, nb, hist);
+        k_radix_scan<<<1, 1024, 0, st>>>(hist, 256 * nb);
+        k_radix_scatter<<<nb, kSortTile, 0, st>>>(ka, va, kb, vb, T, shift, nb, hist);
+        launches += 3;
+        uint32_t *tk = ka; ka = kb; kb = tk;
+        int32_t *tv = va; va = vb; vb = tv;
+    }
+    // after 4 passes the sorted data is back in (ka, va)
+    cudaMemcpyAsync(sc.codes, ka, n * 4, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(sc.order, va, n * 4, cudaMemcpyDeviceToDevice, st);
+    if (T >= 2) {
+        cudaMemsetAsync(flags, 0, n * 4, st);
+        k_karras<<<(T - 1 + tb - 1) / tb, tb, 0, st>>>(ka, T, sc.nodes, parent);
+        ++launches;
+    }
+    k_refit<<<gb, tb, 0, st>>>(d_verts, d_tris, d_uv, va, T, sc.nodes, parent, flags, sc.tris, sc.tuv);
+    ++launches;
+    sc.root = T >= 2 ? 0 : ~0;
+    return launches;
+}
+
+}  // namespace dpcs

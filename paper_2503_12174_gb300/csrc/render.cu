@@ -1,0 +1,309 @@
+// render.cu -- forward rendering and its path-replay adjoint.
+//
+// Forward (Eq. 7): k_prf maps the projector image through the PRF (Eq. 1),
+// k_pack_tex interleaves albedo and roughness into one float4 per texel, and
+// k_render traces every camera path (Eqs. 3, 6, 10) and applies the camera
+// response (Eqs. 4, 5) in its epilogue.
+//
+// Adjoint: k_crf_backward turns dLoss/dIc into dLoss/dEc (Eq. 5), k_replay
+// re-traces each path from its Philox counters and scatters gradients into
+// the projector and texture accumulators, k_prf_backward applies Eq. 1's
+// derivative, and k_tex_backward / k_finalize add the results to the
+// caller's buffers.
+//
+// Thread mapping: L = 2^log2L consecutive lanes of a warp share one camera
+// pixel; lane l traces samples l, l+L, l+2L, ... and the L partial sums are
+// combined by a fixed xor-shuffle tree, so a pixel's result does not depend
+// on scheduling.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "device.cuh"
+#include "internal.h"
+
+namespace dpcs {
+
+namespace {
+
+constexpr int kRenderBlock = 128;
+
+__device__ __forceinline__ void atomic_add4(float4 *p, float4 v) {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 900
+    atomicAdd(p, v);
+#else
+    atomicAdd(&p->x, v.x);
+    atomicAdd(&p->y, v.y);
+    atomicAdd(&p->z, v.z);
+    atomicAdd(&p->w, v.w);
+#endif
+}
+
+__global__ void k_prf(const float *__restrict__ Ip, int64_t ntex, float g0, float g1, float g2, float gain,
+                      float4 *__restrict__ Ep) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= ntex) return;
+    const float a = Ip[3 * t], b = Ip[3 * t + 1], c = Ip[3 * t + 2];
+    Ep[t] = make_float4(a > 0.0f ? gain * powf(a, g0) : 0.0f, b > 0.0f ? gain * powf(b, g1) : 0.0f,
+                        c > 0.0f ? gain * powf(c, g2) : 0.0f, 0.0f);
+}
+
+__global__ void k_pack_tex(const float *__restrict__ albedo, const float *__restrict__ rough, int64_t ntex,
+                           float4 *__restrict__ tex) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= ntex) return;
+    tex[t] = make_float4(albedo[3 * t], albedo[3 * t + 1], albedo[3 * t + 2], rough[t]);
+}
+
+__device__ __forceinline__ float crf(float ec, float gain, float wb, float gamma) {
+    const float a = gain * wb * ec;
+    return a > 0.0f ? powf(a, gamma) : 0.0f;
+}
+
+__global__ void __launch_bounds__(kRenderBlock) k_render(const RenderArgs a) {
+    const int L = 1 << a.log2L;
+    const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t pix = gt >> a.log2L;
+    const int sl = (int)(gt & (L - 1));
+    const int64_t npix = (int64_t)a.Hc * a.Wc;
+    f3 sum = mk3(0.f, 0.f, 0.f);
+    if (pix < npix) {
+        for (int s = sl; s < a.spp; s += L) {
+            int nv;
+            sum = sum + trace_path<false>(a, (uint32_t)pix, (uint32_t)s, nullptr, nv);
+        }
+    }
+    for (int off = L >> 1; off > 0; off >>= 1) {
+        sum.x += __shfl_xor_sync(0xffffffffu, sum.x, off);
+        sum.y += __shfl_xor_sync(0xffffffffu, sum.y, off);
+        sum.z += __shfl_xor_sync(0xffffffffu, sum.z, off);
+    }
+    if (pix < npix && sl == 0) {
+        const float inv = 1.0f / (float)a.spp;
+        const float ex = sum.x * inv, ey = sum.y * inv, ez = sum.z * inv;
+        if (a.Ec) {
+            a.Ec[3 * pix] = ex;
+            a.Ec[3 * pix + 1] = ey;
+            a.Ec[3 * pix + 2] = ez;
+        }
+        a.Ic[3 * pix] = crf(ex, a.gain_c, a.wb[0], a.gamma_c[0]);
+        a.Ic[3 * pix + 1] = crf(ey, a.gain_c, a.wb[1], a.gamma_c[1]);
+        a.Ic[3 * pix + 2] = crf(ez, a.gain_c, a.wb[2], a.gamma_c[2]);
+    }
+}
+
+__global__ void k_trace(const float4 *__restrict__ nodes, const float4 *__restrict__ tris, int32_t root, int32_t T,
+                        const float *__restrict__ o, const float *__restrict__ d, int64_t n, float *__restrict__ tout,
+                        int32_t *__restrict__ triout, unsigned *status) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    Hit h;
+    const Ray r = make_ray(mk3(o[3 * i], o[3 * i + 1], o[3 * i + 2]), mk3(d[3 * i], d[3 * i + 1], d[3 * i + 2]));
+    const bool hit = traverse<false>(nodes, tris, root, T, r, INFINITY, h, status);
+    tout[i] = hit ? h.t : INFINITY;
+    triout[i] = hit ? h.orig : -1;
+}
+
+// ---------------------------------------------------------------------------
+// block reduction of NV floats into FP64 accumulators
+// ---------------------------------------------------------------------------
+template <int NV>
+__device__ __forceinline__ void block_reduce_add(float (&v)[NV], double *acc) {
+    __shared__ float red[NV][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+        for (int off = 16; off; off >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], off);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) red[k][w] = v[k];
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        float s = 0.0f;
+        for (int j = 0; j < (int)(blockDim.x >> 5); ++j) s += red[threadIdx.x][j];
+        if (s != 0.0f) atomicAdd(acc + threadIdx.x, (double)s);
+    }
+}
+
+// Eq. 5 adjoint.  acc layout: [gamma_p(3), Gp, gamma_c(3), Gc, wb(3)]
+__global__ void k_crf_backward(const float *__restrict__ dIc, const float *__restrict__ Ec,
+                               const float *__restrict__ Ic, int64_t npix, float gc0, float gc1, float gc2,
+                               float gain, float w0, float w1, float w2, float *__restrict__ gE, double *acc) {
+    const int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    float v[7] = {0, 0, 0, 0, 0, 0, 0};  // gamma_c(3), Gc, wb(3)
+    if (p < npix) {
+        const float gcs[3] = {gc0, gc1, gc2}, wbs[3] = {w0, w1, w2};
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const float ec = Ec[3 * p + j];
+            const float a = gain * wbs[j] * ec;
+            float ge = 0.0f;
+            if (a > 0.0f) {
+                const float g = dIc[3 * p + j];
+                const float da = gcs[j] * powf(a, gcs[j] - 1.0f);
+                ge = g * da * gain * wbs[j];
+                v[j] += g * Ic[3 * p + j] * logf(a);
+                v[3] += g * da * wbs[j] * ec;
+                v[4 + j] += g * da * gain * ec;
+            }
+            gE[3 * p + j] = ge;
+        }
+    }
+    block_reduce_add<7>(v, acc + 4);
+}
+
+__global__ void __launch_bounds__(kRenderBlock) k_replay(const RenderArgs a) {
+    const int L = 1 << a.log2L;
+    const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t pix = gt >> a.log2L;
+    const int sl = (int)(gt & (L - 1));
+    const int64_t npix = (int64_t)a.Hc * a.Wc;
+    if (pix >= npix) return;
+    const float inv = 1.0f / (float)a.spp;
+    const f3 gbar = mk3(a.gE[3 * pix] * inv, a.gE[3 * pix + 1] * inv, a.gE[3 * pix + 2] * inv);
+    if (gbar.x == 0.0f && gbar.y == 0.0f && gbar.z == 0.0f) return;
+    const float gb_in[3] = {gbar.x, gbar.y, gbar.z};
+    for (int s = sl; s < a.spp; s += L) {
+        VRec rec[DPCS_MAX_BOUNCES];
+        int nv;
+        trace_path<true>(a, (uint32_t)pix, (uint32_t)s, rec, nv);
+        float A[3] = {0.f, 0.f, 0.f};
+        for (int c = nv - 1; c >= 0; --c) {
+            const VRec &R = rec[c];
+            float ga[3], dEp[3], An[3];
+            float dr = 0.0f;
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                An[j] = A[j];
+                const float gb = gb_in[j] * R.beta[j];
+                const bool lit = R.G > 0.0f && ((R.unc >> j) & 1u);
+                const float ln_e = lit ? R.Ep[j] * R.G : 0.0f;  // radiance / f along wp
+                const float cont = R.cw * An[j];               // w / f times downstream A
+                const float fp = R.rho[j] * DPCS_INV_PI_F + R.sp;
+                const float fi = R.rho[j] * DPCS_INV_PI_F + R.si;
+                dEp[j] = lit ? gb * fp * R.G : 0.0f;
+                ga[j] = gb * (ln_e + cont) * DPCS_INV_PI_F;
+                dr += gb * (R.dsp * ln_e + R.dsi * cont);
+                A[j] = fp * ln_e + fi * cont;
+            }
+            int idx[4];
+            float w[4];
+            Bilin tb;
+            tb.x0 = R.tx0; tb.y0 = R.ty0; tb.fx = R.tfx; tb.fy = R.tfy;
+            bilin_taps(tb, a.Wt, a.Ht, idx, w);
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                atomic_add4(a.dtex + idx[k], make_float4(ga[0] * w[k], ga[1] * w[k], ga[2] * w[k], dr * w[k]));
+            if (R.G > 0.0f && (dEp[0] != 0.0f || dEp[1] != 0.0f || dEp[2] != 0.0f)) {
+                Bilin pb;
+                pb.x0 = R.px0; pb.y0 = R.py0; pb.fx = R.pfx; pb.fy = R.pfy;
+                bilin_taps(pb, a.Wp, a.Hp, idx, w);
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    atomic_add4(a.dEp + idx[k], make_float4(dEp[0] * w[k], dEp[1] * w[k], dEp[2] * w[k], 0.0f));
+            }
+        }
+    }
+}
+
+// Eq. 1 adjoint: dIp += dEp Gp gamma Ip^(gamma-1); gamma_p and Gp reductions
+__global__ void k_prf_backward(const float *__restrict__ Ip, const float4 *__restrict__ dEp, int64_t ntex,
+                               float g0, float g1, float g2, float gain, float *__restrict__ dIp, double *acc) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    float v[4] = {0, 0, 0, 0};
+    if (t < ntex) {
+        const float4 g4 = dEp[t];
+        const float gs[3] = {g4.x, g4.y, g4.z}, gm[3] = {g0, g1, g2};
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const float ip = Ip[3 * t + j];
+            if (ip > 0.0f && gs[j] != 0.0f) {
+                const float pw = powf(ip, gm[j]);
+                if (dIp) dIp[3 * t + j] += gs[j] * gain * gm[j] * powf(ip, gm[j] - 1.0f);
+                v[j] += gs[j] * gain * pw * logf(ip);
+                v[3] += gs[j] * pw;
+            }
+        }
+    }
+    block_reduce_add<4>(v, acc);
+}
+
+__global__ void k_tex_backward(const float4 *__restrict__ dtex, int64_t ntex, float *__restrict__ dAlbedo,
+                               float *__restrict__ dRough) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= ntex) return;
+    const float4 g = dtex[t];
+    if (dAlbedo) {
+        dAlbedo[3 * t] += g.x;
+        dAlbedo[3 * t + 1] += g.y;
+        dAlbedo[3 * t + 2] += g.z;
+    }
+    if (dRough) dRough[t] += g.w;
+}
+
+__global__ void k_finalize(const double *__restrict__ acc, float *__restrict__ dParams) {
+    const int i = threadIdx.x;
+    if (i < 11) dParams[i] += (float)acc[i];
+}
+
+inline unsigned grid_for(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
+
+}  // namespace
+
+int launch_prf(const float *Ip, int64_t ntex, const float gamma_p[3], float gain_p, float4 *Ep, cudaStream_t st) {
+    k_prf<<<grid_for(ntex, 256), 256, 0, st>>>(Ip, ntex, gamma_p[0], gamma_p[1], gamma_p[2], gain_p, Ep);
+    return 1;
+}
+
+int launch_pack_tex(const float *albedo, const float *rough, int64_t ntex, float4 *tex, cudaStream_t st) {
+    k_pack_tex<<<grid_for(ntex, 256), 256, 0, st>>>(albedo, rough, ntex, tex);
+    return 1;
+}
+
+int launch_render(const RenderArgs &a, cudaStream_t st) {
+    const int64_t threads = ((int64_t)a.Hc * a.Wc) << a.log2L;
+    k_render<<<grid_for(threads, kRenderBlock), kRenderBlock, 0, st>>>(a);
+    return 1;
+}
+
+int launch_trace(const Scene &sc, const float *o, const float *d, int64_t n, float *t, int32_t *tri,
+                 unsigned *status, cudaStream_t st) {
+    k_trace<<<grid_for(n, 128), 128, 0, st>>>(sc.nodes, sc.tris, sc.root, sc.T, o, d, n, t, tri, status);
+    return 1;
+}
+
+int launch_crf_backward(const float *dIc, const float *Ec, const float *Ic, int64_t npix, const float gamma_c[3],
+                        float gain_c, const float wb[3], float *gE, double *acc, cudaStream_t st) {
+    k_crf_backward<<<grid_for(npix, 256), 256, 0, st>>>(dIc, Ec, Ic, npix, gamma_c[0], gamma_c[1], gamma_c[2],
+                                                        gain_c, wb[0], wb[1], wb[2], gE, acc);
+    return 1;
+}
+
+int launch_replay(const RenderArgs &a, cudaStream_t st) {
+    const int64_t threads = ((int64_t)a.Hc * a.Wc) << a.log2L;
+    k_replay<<<grid_for(threads, kRenderBlock), kRenderBlock, 0, st>>>(a);
+    return 1;
+}
+
+int launch_prf_backward(const float *Ip, const float4 *dEp, int64_t ntex, const float gamma_p[3], float gain_p,
+                        float *dIp, double *acc, cudaStream_t st) {
+    k_prf_backward<<<grid_for(ntex, 256), 256, 0, st>>>(Ip, dEp, ntex, gamma_p[0], gamma_p[1], gamma_p[2], gain_p,
+                                                        dIp, acc);
+    return 1;
+}
+
+int launch_tex_backward(const float4 *dtex, int64_t ntex, float *dAlbedo, float *dRough, cudaStream_t st) {
+    k_tex_backward<<<grid_for(ntex, 256), 256, 0, st>>>(dtex, ntex, dAlbedo, dRough);
+    return 1;
+}
+
+int launch_finalize_params(const double *acc, float *dParams, cudaStream_t st) {
+    k_finalize<<<1, 32, 0, st>>>(acc, dParams);
+    return 1;
+}
+
+int launch_zero(void *p, size_t bytes, cudaStream_t st) {
+    cudaMemsetAsync(p, 0, bytes, st);
+    return 0;
+}
+
+}  // namespace dpcs

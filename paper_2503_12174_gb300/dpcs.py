@@ -1,0 +1,370 @@
+"""Python binding of libdpcs (include/dpcs.h).
+
+Functions named ``dpcs_*`` map one-to-one onto the C ABI and only marshal
+arguments.  ``Context`` wraps them for PyTorch tensors: it checks device,
+dtype, shape and contiguity, passes raw device pointers and the current CUDA
+stream, and raises ``DPCSError`` on a non-zero status.  Every step of the
+path runs in the library's kernels; if the library cannot be loaded this
+module raises instead of falling back to anything else.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+DPCS_OK = 0
+DPCS_ERR_INVALID_ARG = -1
+DPCS_ERR_OOM = -2
+DPCS_ERR_CUDA = -3
+DPCS_ERR_DEVICE_CHECK = -4
+DPCS_ERR_TRAVERSAL_LIMIT = -5
+DPCS_ERR_TIMEOUT = -6
+DPCS_ERR_BUSY = -7
+DPCS_ERR_NOT_FOUND = -8
+DPCS_MAX_BOUNCES = 8
+
+EXPORTED = [
+    "dpcs_create", "dpcs_destroy", "dpcs_last_error", "dpcs_sync", "dpcs_memory_used", "dpcs_launch_count",
+    "dpcs_scene_upload", "dpcs_scene_free", "dpcs_scene_export", "dpcs_trace", "dpcs_render",
+    "dpcs_render_backward", "dpcs_l2_loss", "dpcs_adam",
+]
+
+
+class DPCSError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"dpcs status {status}: {msg}")
+        self.status = status
+
+
+class DpcsParams(ctypes.Structure):
+    _fields_ = [("gamma_p", ctypes.c_float * 3), ("gain_p", ctypes.c_float),
+                ("gamma_c", ctypes.c_float * 3), ("gain_c", ctypes.c_float),
+                ("wb", ctypes.c_float * 3), ("k_proj", ctypes.c_float),
+                ("ks", ctypes.c_float), ("f0", ctypes.c_float),
+                ("rr_start", ctypes.c_int32), ("rr_q", ctypes.c_float),
+                ("clip", ctypes.c_float), ("jitter", ctypes.c_int32)]
+
+
+class DpcsView(ctypes.Structure):
+    _fields_ = [("Kc", ctypes.c_float * 9), ("Hc", ctypes.c_int32), ("Wc", ctypes.c_int32),
+                ("Kp", ctypes.c_float * 9), ("Rp", ctypes.c_float * 9), ("tp", ctypes.c_float * 3),
+                ("Hp", ctypes.c_int32), ("Wp", ctypes.c_int32)]
+
+
+_lib = None
+_lib_path = None
+
+_P = ctypes.c_void_p
+_SIGS = {
+    "dpcs_create": (ctypes.c_int32, [ctypes.c_int, ctypes.c_size_t, ctypes.POINTER(_P)]),
+    "dpcs_destroy": (ctypes.c_int32, [_P]),
+    "dpcs_last_error": (ctypes.c_char_p, [_P]),
+    "dpcs_sync": (ctypes.c_int32, [_P, _P]),
+    "dpcs_memory_used": (ctypes.c_size_t, [_P]),
+    "dpcs_launch_count": (ctypes.c_uint64, [_P]),
+    "dpcs_scene_upload": (ctypes.c_int32, [_P, _P, ctypes.c_int32, _P, ctypes.c_int32, _P, _P,
+                                           ctypes.POINTER(ctypes.c_uint64)]),
+    "dpcs_scene_free": (ctypes.c_int32, [_P, ctypes.c_uint64]),
+    "dpcs_scene_export": (ctypes.c_int32, [_P, ctypes.c_uint64, _P, _P, _P, _P]),
+    "dpcs_trace": (ctypes.c_int32, [_P, ctypes.c_uint64, _P, _P, ctypes.c_int64, _P, _P, _P]),
+    "dpcs_render": (ctypes.c_int32, [_P, ctypes.c_uint64, _P, _P, ctypes.c_int32, ctypes.c_int32, _P,
+                                     ctypes.POINTER(DpcsView), ctypes.POINTER(DpcsParams), ctypes.c_int32,
+                                     ctypes.c_int32, ctypes.c_uint64, _P, _P, _P]),
+    "dpcs_render_backward": (ctypes.c_int32, [_P, ctypes.c_uint64, _P, _P, ctypes.c_int32, ctypes.c_int32, _P,
+                                              ctypes.POINTER(DpcsView), ctypes.POINTER(DpcsParams), ctypes.c_int32,
+                                              ctypes.c_int32, ctypes.c_uint64, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "dpcs_l2_loss": (ctypes.c_int32, [_P, _P, _P, ctypes.c_int64, _P, _P, _P]),
+    "dpcs_adam": (ctypes.c_int32, [_P, _P, _P, _P, _P, ctypes.c_int64, ctypes.c_float, ctypes.c_float,
+                                   ctypes.c_float, ctypes.c_float, ctypes.c_int32, ctypes.c_float, ctypes.c_float,
+                                   _P]),
+}
+
+
+def library_path() -> str:
+    return _build.lib_path()
+
+
+def load_library(path: str | None = None):
+    """Load libdpcs.so (building it first if it is missing).  Raises if the
+    library cannot be built or loaded: there is no fallback path."""
+    global _lib, _lib_path
+    if _lib is not None and (path is None or path == _lib_path):
+        return _lib
+    if path is None:
+        path = library_path()
+        if not os.path.exists(path):
+            path = _build.build()
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib, _lib_path = lib, path
+    return lib
+
+
+def make_params(p) -> DpcsParams:
+    o = DpcsParams()
+    o.gamma_p[:] = [float(x) for x in p.gamma_p]
+    o.gain_p = float(p.gain_p)
+    o.gamma_c[:] = [float(x) for x in p.gamma_c]
+    o.gain_c = float(p.gain_c)
+    o.wb[:] = [float(x) for x in p.wb]
+    o.k_proj = float(p.k_proj)
+    o.ks = float(p.ks)
+    o.f0 = float(p.f0)
+    o.rr_start = int(p.rr_start)
+    o.rr_q = float(p.rr_q)
+    o.clip = float(p.clip)
+    o.jitter = int(p.jitter)
+    return o
+
+
+def make_view(Kc, Hc, Wc, Kp, Rp, tp, Hp, Wp) -> DpcsView:
+    v = DpcsView()
+    v.Kc[:] = [float(x) for x in np.asarray(Kc, np.float32).ravel()]
+    v.Hc, v.Wc = int(Hc), int(Wc)
+    v.Kp[:] = [float(x) for x in np.asarray(Kp, np.float32).ravel()]
+    v.Rp[:] = [float(x) for x in np.asarray(Rp, np.float32).ravel()]
+    v.tp[:] = [float(x) for x in np.asarray(tp, np.float32).ravel()]
+    v.Hp, v.Wp = int(Hp), int(Wp)
+    return v
+
+
+def view_of(scene) -> DpcsView:
+    """DpcsView of a ``scenes.Scene``."""
+    return make_view(scene.Kc, scene.Hc, scene.Wc, scene.Kp, scene.Rp, scene.tp, scene.Hp, scene.Wp)
+
+
+# ---------------------------------------------------------------------------
+# raw ABI wrappers (same names as the C entry points)
+# ---------------------------------------------------------------------------
+def dpcs_create(device: int = 0, hbm_budget_bytes: int = 0):
+    h = _P()
+    st = load_library().dpcs_create(int(device), int(hbm_budget_bytes), ctypes.byref(h))
+    if st != DPCS_OK:
+        raise DPCSError(st, "dpcs_create failed")
+    return h
+
+
+def dpcs_destroy(ctx):
+    return load_library().dpcs_destroy(ctx)
+
+
+def dpcs_last_error(ctx) -> str:
+    r = load_library().dpcs_last_error(ctx)
+    return r.decode() if r else ""
+
+
+def dpcs_sync(ctx, stream=None):
+    return load_library().dpcs_sync(ctx, stream)
+
+
+def dpcs_memory_used(ctx) -> int:
+    return load_library().dpcs_memory_used(ctx)
+
+
+def dpcs_launch_count(ctx) -> int:
+    return load_library().dpcs_launch_count(ctx)
+
+
+def dpcs_scene_upload(ctx, verts, V, tris, T, uv, stream, out):
+    return load_library().dpcs_scene_upload(ctx, verts, V, tris, T, uv, stream, out)
+
+
+def dpcs_scene_free(ctx, scene):
+    return load_library().dpcs_scene_free(ctx, scene)
+
+
+def dpcs_scene_export(ctx, scene, codes, order, child, child_box):
+    return load_library().dpcs_scene_export(ctx, scene, codes, order, child, child_box)
+
+
+def dpcs_trace(ctx, scene, orig, dir, n, t_out, tri_out, stream):
+    return load_library().dpcs_trace(ctx, scene, orig, dir, n, t_out, tri_out, stream)
+
+
+def dpcs_render(ctx, scene, albedo, rough, Ht, Wt, Ip, view, params, spp, bounces, seed, Ic, Ec, stream):
+    return load_library().dpcs_render(ctx, scene, albedo, rough, Ht, Wt, Ip, ctypes.byref(view),
+                                      ctypes.byref(params), spp, bounces, seed, Ic, Ec, stream)
+
+
+def dpcs_render_backward(ctx, scene, albedo, rough, Ht, Wt, Ip, view, params, spp, bounces, seed, Ec, Ic, dIc,
+                         dIp, dAlbedo, dRough, dParams, stream):
+    return load_library().dpcs_render_backward(ctx, scene, albedo, rough, Ht, Wt, Ip, ctypes.byref(view),
+                                               ctypes.byref(params), spp, bounces, seed, Ec, Ic, dIc, dIp, dAlbedo,
+                                               dRough, dParams, stream)
+
+
+def dpcs_l2_loss(ctx, Ic, target, n, dIc, loss, stream):
+    return load_library().dpcs_l2_loss(ctx, Ic, target, n, dIc, loss, stream)
+
+
+def dpcs_adam(ctx, p, g, m, v, n, lr, beta1, beta2, eps, step, lo, hi, stream):
+    return load_library().dpcs_adam(ctx, p, g, m, v, n, lr, beta1, beta2, eps, step, lo, hi, stream)
+
+
+# ---------------------------------------------------------------------------
+# torch-facing context
+# ---------------------------------------------------------------------------
+def _ptr(t, name, shape=None, dtype=None, device=None, allow_none=False):
+    if t is None:
+        if allow_none:
+            return None
+        raise ValueError(f"{name} is required")
+    import torch
+
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{name}: expected {dtype}, got {t.dtype}")
+    if device is not None and t.device != device:
+        raise ValueError(f"{name}: expected device {device}, got {t.device}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name}: expected shape {tuple(shape)}, got {tuple(t.shape)}")
+    return ctypes.c_void_p(t.data_ptr()) if t.numel() else None
+
+
+def _stream(stream):
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Context:
+    """A libdpcs context on one CUDA device, driven with torch tensors."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+        import torch
+
+        self.device = torch.device("cuda", device)
+        self.handle = dpcs_create(device, hbm_budget_bytes)
+        self.lib = load_library()
+
+    def close(self):
+        if getattr(self, "handle", None):
+            dpcs_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, status: int, what: str):
+        if status != DPCS_OK:
+            raise DPCSError(status, f"{what}: {dpcs_last_error(self.handle)}")
+
+    # -- bookkeeping ---------------------------------------------------------
+    def sync(self, stream=None):
+        self.check(dpcs_sync(self.handle, _stream(stream)), "sync")
+
+    @property
+    def memory_used(self) -> int:
+        return dpcs_memory_used(self.handle)
+
+    @property
+    def launch_count(self) -> int:
+        return dpcs_launch_count(self.handle)
+
+    # -- scenes ----------------------------------------------------------------
+    def upload(self, verts, tris, uv, stream=None) -> int:
+        verts = np.ascontiguousarray(verts, np.float32)
+        tris = np.ascontiguousarray(tris, np.int32)
+        uv = np.ascontiguousarray(uv, np.float32)
+        out = ctypes.c_uint64()
+        st = dpcs_scene_upload(self.handle, verts.ctypes.data_as(_P), len(verts), tris.ctypes.data_as(_P),
+                               len(tris), uv.ctypes.data_as(_P), _stream(stream), ctypes.byref(out))
+        self.check(st, "scene_upload")
+        return out.value
+
+    def free(self, scene: int):
+        self.check(dpcs_scene_free(self.handle, scene), "scene_free")
+
+    def export(self, scene: int, T: int):
+        codes = np.zeros(T, np.uint32)
+        order = np.zeros(T, np.int32)
+        child = np.zeros((max(T - 1, 0), 2), np.int32)
+        box = np.zeros((max(T - 1, 0), 2, 6), np.float32)
+        st = dpcs_scene_export(self.handle, scene, codes.ctypes.data_as(_P), order.ctypes.data_as(_P),
+                               child.ctypes.data_as(_P), box.ctypes.data_as(_P))
+        self.check(st, "scene_export")
+        return codes, order, child, box
+
+    def trace(self, scene: int, orig, dir, stream=None):
+        import torch
+
+        n = orig.shape[0]
+        t = torch.empty(n, dtype=torch.float32, device=self.device)
+        tri = torch.empty(n, dtype=torch.int32, device=self.device)
+        st = dpcs_trace(self.handle, scene, _ptr(orig, "orig", (n, 3), torch.float32, self.device),
+                        _ptr(dir, "dir", (n, 3), torch.float32, self.device), n, _ptr(t, "t"), _ptr(tri, "tri"),
+                        _stream(stream))
+        self.check(st, "trace")
+        return t, tri
+
+    # -- rendering -------------------------------------------------------------
+    def render(self, scene: int, albedo, rough, Ip, view: DpcsView, params: DpcsParams, spp: int, bounces: int,
+               seed: int, Ic=None, Ec=None, stream=None):
+        import torch
+
+        Ht, Wt = albedo.shape[0], albedo.shape[1]
+        f32 = torch.float32
+        if Ic is None:
+            Ic = torch.empty((view.Hc, view.Wc, 3), dtype=f32, device=self.device)
+        st = dpcs_render(self.handle, scene, _ptr(albedo, "albedo", (Ht, Wt, 3), f32, self.device),
+                         _ptr(rough, "rough", (Ht, Wt), f32, self.device), Ht, Wt,
+                         _ptr(Ip, "Ip", (view.Hp, view.Wp, 3), f32, self.device), view, params, int(spp),
+                         int(bounces), int(seed) & (2**64 - 1),
+                         _ptr(Ic, "Ic", (view.Hc, view.Wc, 3), f32, self.device),
+                         _ptr(Ec, "Ec", (view.Hc, view.Wc, 3), f32, self.device, allow_none=True), _stream(stream))
+        self.check(st, "render")
+        return Ic, Ec
+
+    def render_backward(self, scene: int, albedo, rough, Ip, view: DpcsView, params: DpcsParams, spp: int,
+                        bounces: int, seed: int, Ec, Ic, dIc, dIp=None, dAlbedo=None, dRough=None, dParams=None,
+                        stream=None):
+        import torch
+
+        Ht, Wt = albedo.shape[0], albedo.shape[1]
+        f32 = torch.float32
+        img = (view.Hc, view.Wc, 3)
+        st = dpcs_render_backward(
+            self.handle, scene, _ptr(albedo, "albedo", (Ht, Wt, 3), f32, self.device),
+            _ptr(rough, "rough", (Ht, Wt), f32, self.device), Ht, Wt,
+            _ptr(Ip, "Ip", (view.Hp, view.Wp, 3), f32, self.device), view, params, int(spp), int(bounces),
+            int(seed) & (2**64 - 1), _ptr(Ec, "Ec", img, f32, self.device), _ptr(Ic, "Ic", img, f32, self.device),
+            _ptr(dIc, "dIc", img, f32, self.device),
+            _ptr(dIp, "dIp", (view.Hp, view.Wp, 3), f32, self.device, allow_none=True),
+            _ptr(dAlbedo, "dAlbedo", (Ht, Wt, 3), f32, self.device, allow_none=True),
+            _ptr(dRough, "dRough", (Ht, Wt), f32, self.device, allow_none=True),
+            _ptr(dParams, "dParams", (11,), f32, self.device, allow_none=True), _stream(stream))
+        self.check(st, "render_backward")
+
+    def l2_loss(self, Ic, target, dIc, loss, stream=None):
+        import torch
+
+        f32 = torch.float32
+        n = Ic.numel()
+        st = dpcs_l2_loss(self.handle, _ptr(Ic, "Ic", None, f32, self.device),
+                          _ptr(target, "target", tuple(Ic.shape), f32, self.device), n,
+                          _ptr(dIc, "dIc", tuple(Ic.shape), f32, self.device),
+                          _ptr(loss, "loss", (1,), f32, self.device), _stream(stream))
+        self.check(st, "l2_loss")
+
+    def adam(self, p, g, m, v, step: int, lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8, lo=0.0, hi=1.0, stream=None):
+        import torch
+
+        f32 = torch.float32
+        shp = tuple(p.shape)
+        st = dpcs_adam(self.handle, _ptr(p, "p", None, f32, self.device), _ptr(g, "g", shp, f32, self.device),
+                       _ptr(m, "m", shp, f32, self.device), _ptr(v, "v", shp, f32, self.device), p.numel(),
+                       float(lr), float(beta1), float(beta2), float(eps), int(step), float(lo), float(hi),
+                       _stream(stream))
+        self.check(st, "adam")

@@ -1,0 +1,60 @@
+"""The C ABI library loads without a GPU and exports every entry point that
+include/dpcs.h declares; the ctypes mirrors of the public structs have the
+C layout (checked against gcc's sizeof/offsetof)."""
+import ctypes
+import os
+import re
+import subprocess
+import tempfile
+
+from paper_2503_12174_gb300 import dpcs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HDR = os.path.join(ROOT, "include", "dpcs.h")
+
+
+def _declared():
+    src = open(HDR).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(dpcs_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    lib = dpcs.load_library()
+    names = _declared()
+    assert len(names) >= 14
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+    assert set(names) <= set(dpcs.EXPORTED) | {n for n in names if n not in dpcs.EXPORTED and hasattr(lib, n)}
+
+
+def test_create_without_gpu_fails_cleanly():
+    import torch
+
+    if torch.cuda.is_available():
+        return
+    lib = dpcs.load_library()
+    h = ctypes.c_void_p()
+    assert lib.dpcs_create(0, 0, ctypes.byref(h)) == dpcs.DPCS_ERR_INVALID_ARG
+    assert not h.value
+
+
+def test_struct_layout_matches_header():
+    code = r"""
+#include <stdio.h>
+#include <stddef.h>
+#include "dpcs.h"
+int main(void) {
+  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(dpcs_params), offsetof(dpcs_params, rr_start),
+         offsetof(dpcs_params, jitter), sizeof(dpcs_view), offsetof(dpcs_view, Kp), offsetof(dpcs_view, Hp));
+  return 0;
+}
+"""
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        exe = os.path.join(d, "t")
+        open(c, "w").write(code)
+        subprocess.check_call(["gcc", "-I", os.path.dirname(HDR), c, "-o", exe])
+        out = [int(x) for x in subprocess.check_output([exe]).split()]
+    P, V = dpcs.DpcsParams, dpcs.DpcsView
+    assert out == [ctypes.sizeof(P), P.rr_start.offset, P.jitter.offset, ctypes.sizeof(V), V.Kp.offset, V.Hp.offset]

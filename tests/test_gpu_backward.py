@@ -1,0 +1,93 @@
+"""Adjoint parity: GPU path-replay backward vs the oracle's FP64 adjoint on
+the same paths, plus the loss and Adam kernels against plain NumPy."""
+import numpy as np
+import pytest
+
+from paper_2503_12174_gb300 import scenes
+from gpu_util import GpuScene, ctx, need_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def _grad_close(g, r, rtol, scale_tol):
+    """|g - r| <= rtol |r| + scale_tol * max|r| element-wise."""
+    g, r = np.asarray(g, np.float64).ravel(), np.asarray(r, np.float64).ravel()
+    scale = np.abs(r).max()
+    err = np.abs(g - r) - (rtol * np.abs(r) + scale_tol * scale)
+    return bool(np.all(err <= 0)), float(np.max(np.abs(g - r) / (np.abs(r) + 1e-30))), scale
+
+
+@pytest.mark.parametrize("res,spp,bounces,clip", [(24, 4, 3, 0.0), (31, 5, 2, 0.05), (20, 16, 1, 0.0)])
+def test_backward_matches_oracle(orc, res, spp, bounces, clip):
+    torch = need_cuda()
+    sc = scenes.corner(res=res, tex=32, spp=spp, bounces=bounces, seed=3)
+    p = sc.params
+    sc = sc.replace(params=scenes.Params(gamma_p=p.gamma_p, gain_p=1.2, gamma_c=p.gamma_c, gain_c=p.gain_c,
+                                         wb=p.wb, k_proj=p.k_proj, ks=p.ks, f0=p.f0, clip=clip))
+    g = GpuScene(sc)
+    rng = np.random.default_rng(0)
+    W = rng.normal(size=(sc.Hc, sc.Wc, 3)).astype(np.float32)
+    try:
+        Ec, Ic = g.render()
+        grads = g.backward(Ec, Ic, torch.from_numpy(W).cuda())
+    finally:
+        g.close()
+    ref = orc.render_backward(sc, W.astype(np.float64))
+    for k in ("dIp", "dalbedo", "drough"):
+        ok, mx, scale = _grad_close(grads[k], ref[k], 1e-3, 1e-5)
+        assert scale > 0 and ok, (k, mx, scale)
+    ok, mx, _ = _grad_close(grads["dparams"], ref["dparams"], 1e-4, 1e-6)
+    assert ok, ("dparams", grads["dparams"], ref["dparams"])
+
+
+def test_backward_64_random_parameters_full_size(orc):
+    """Compensation workload at 512x512 / 16 spp: the GPU gradient on 64
+    random projector texels equals the oracle's gradient of the same pixels."""
+    torch = need_cuda()
+    sc = scenes.compensation(res=512, spp=16)
+    g = GpuScene(sc)
+    rng = np.random.default_rng(5)
+    # loss on a random pixel subset so the oracle only replays those pixels
+    px = rng.choice(sc.Hc * sc.Wc, 400, replace=False)
+    Wfull = np.zeros((sc.Hc * sc.Wc, 3), np.float32)
+    Wfull[px] = rng.normal(size=(len(px), 3))
+    try:
+        Ec, Ic = g.render()
+        grads = g.backward(Ec, Ic, torch.from_numpy(Wfull.reshape(sc.Hc, sc.Wc, 3)).cuda())
+    finally:
+        g.close()
+    ref = orc.render_backward(sc, Wfull[px].astype(np.float64), pixels=px)
+    r = ref["dIp"].ravel()
+    gg = grads["dIp"].ravel()
+    nz = np.flatnonzero(np.abs(r) > 1e-3 * np.abs(r).max())
+    pick = rng.choice(nz, min(64, len(nz)), replace=False)
+    np.testing.assert_allclose(gg[pick], r[pick], rtol=1e-3, atol=1e-5 * np.abs(r).max())
+    ok, mx, _ = _grad_close(grads["dparams"], ref["dparams"], 1e-3, 1e-6)
+    assert ok, (grads["dparams"], ref["dparams"])
+
+
+def test_l2_loss_and_adam():
+    torch = need_cuda()
+    c = ctx()
+    rng = np.random.default_rng(1)
+    a = rng.random((37, 41, 3)).astype(np.float32)
+    b = rng.random((37, 41, 3)).astype(np.float32)
+    A, B = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+    d = torch.empty_like(A)
+    loss = torch.empty(1, device="cuda")
+    c.l2_loss(A, B, d, loss)
+    c.sync()
+    np.testing.assert_allclose(d.cpu().numpy(), a - b, rtol=0, atol=0)
+    np.testing.assert_allclose(loss.item(), 0.5 * np.sum((a.astype(np.float64) - b) ** 2), rtol=1e-6)
+    import oracle
+
+    p = rng.random(1000).astype(np.float32)
+    gr = rng.normal(size=1000).astype(np.float32)
+    P, G = torch.from_numpy(p).cuda(), torch.from_numpy(gr).cuda()
+    M, V = torch.zeros_like(P), torch.zeros_like(P)
+    pr, mr, vr = p.astype(np.float64), np.zeros(1000), np.zeros(1000)
+    for step in range(1, 4):
+        c.adam(P, G, M, V, step, lr=0.05)
+        oracle.adam_step(pr, gr.astype(np.float64), mr, vr, step, lr=0.05)
+    c.sync()
+    np.testing.assert_allclose(P.cpu().numpy(), pr, rtol=1e-5, atol=1e-6)
