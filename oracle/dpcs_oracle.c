@@ -35,6 +35,7 @@
  *   - Russian roulette from vertex rr_start on with a fixed survival q.
  *   - random numbers: Philox4x32-10 (Salmon et al., SC'11), key = seed,
  *     counter = (pixel, sample, vertex, 0); u = (x >> 8) * 2^-24.
+ *   - local shading frame: Duff et al. (JCGT 2017) with its seam at n.z = -1/pi.
  *   - Morton codes in FP32 without contraction (this file is compiled with
  *     -ffp-contract=off), 10 bits per axis, x in the highest bit of each triple.
  *
@@ -428,10 +429,14 @@ static void bsdf_eval(d3 n, d3 wo, d3 wi, const double rho[3], double r, double 
     *dfdr = ks > 0.0 ? ks * dsda * dadr : 0.0;
 }
 
-/* Orthonormal basis around n (Duff et al., JCGT 2017); sign taken as n.z >= 0 */
+/* Orthonormal basis around n (Duff et al., JCGT 2017).  Every frame field on
+ * the sphere has a seam; it is put at n.z = -1/pi instead of n.z = 0 so that
+ * the axis-aligned and mirror-symmetric facets common in meshes (n.z exactly
+ * 0, or 0 up to rounding) never sit on it.  Both branches stay well
+ * conditioned (|sg + n.z| >= 1 - 1/pi). */
 static void onb(d3 n, d3 *t, d3 *b)
 {
-    double sg = n.z >= 0.0 ? 1.0 : -1.0;
+    double sg = n.z >= -0.318309886183790671538 ? 1.0 : -1.0;
     double a = -1.0 / (sg + n.z);
     double bb = n.x * n.y * a;
     *t = mk(1.0 + sg * n.x * n.x * a, sg * bb, -sg * n.x);

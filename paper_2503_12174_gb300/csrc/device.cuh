@@ -82,10 +82,17 @@ __device__ __forceinline__ float alpha_of(float r, float &dadr) {
     return rc * rc;
 }
 
-__device__ __forceinline__ float ggx_D(float ch, float a) {
+// GGX D for cos(theta_h) = ch and sin^2(theta_h) = s2.  The denominator
+// cos^2 (a^2 - 1) + 1 is formed as s2 + a^2 cos^2 with s2 = |n x h|^2: the
+// textbook form cancels catastrophically in FP32 near the peak of sharp lobes.
+__device__ __forceinline__ float ggx_D(float ch, float s2, float a) {
     const float a2 = a * a;
-    const float t = ch * ch * (a2 - 1.0f) + 1.0f;
+    const float t = s2 + a2 * ch * ch;
     return a2 / (DPCS_PI_F * t * t);
+}
+__device__ __forceinline__ float sin2(f3 n, f3 h) {
+    const f3 c = cross(n, h);
+    return dot(c, c);
 }
 
 __device__ __forceinline__ float ggx_G1(float c, float a) {
@@ -103,7 +110,7 @@ __device__ __forceinline__ float spec_eval(f3 n, f3 wo, f3 wi, float r, float ks
     const f3 h = normalize(wo + wi);
     const float ch = dot(n, h);
     const float a2 = a * a;
-    const float t = ch * ch * (a2 - 1.0f) + 1.0f;
+    const float t = sin2(n, h) + a2 * ch * ch;
     const float D = a2 / (DPCS_PI_F * t * t);
     const float si = sqrtf(a2 + (1.0f - a2) * ci * ci), so = sqrtf(a2 + (1.0f - a2) * co * co);
     const float G = (2.0f * ci / (ci + si)) * (2.0f * co / (co + so));
@@ -117,9 +124,11 @@ __device__ __forceinline__ float spec_eval(f3 n, f3 wo, f3 wi, float r, float ks
     return spec;
 }
 
-// orthonormal basis around n (Duff et al., JCGT 2017), sign from n.z >= 0
+// orthonormal basis around n (Duff et al., JCGT 2017) with its seam at
+// n.z = -1/pi, away from the n.z = 0 of axis-aligned and symmetric facets
+// whose sign FP32 rounding could otherwise flip
 __device__ __forceinline__ void onb(f3 n, f3 &t, f3 &b) {
-    const float sg = n.z >= 0.0f ? 1.0f : -1.0f;
+    const float sg = n.z >= -DPCS_INV_PI_F ? 1.0f : -1.0f;
     const float a = -1.0f / (sg + n.z);
     const float bb = n.x * n.y * a;
     t = mk3(1.0f + sg * n.x * n.x * a, sg * bb, -sg * n.x);
@@ -137,7 +146,7 @@ __device__ __forceinline__ float bsdf_pdf(f3 n, f3 wo, f3 wi, float r, float ks)
         float dadr;
         const float a = alpha_of(r, dadr);
         const f3 h = normalize(wo + wi);
-        p += ps * ggx_G1(co, a) * ggx_D(dot(n, h), a) / (4.0f * co);
+        p += ps * ggx_G1(co, a) * ggx_D(dot(n, h), sin2(n, h), a) / (4.0f * co);
     }
     return p;
 }

@@ -68,12 +68,26 @@ class GpuScene:
         self.ctx.free(self.handle)
 
 
+def crf_atol(sc, Ec_ref, atol_E=1e-7):
+    """Absolute tolerance of Ic implied by an absolute tolerance atol_E on Ec:
+    |dIc/dEc| * atol_E with Ic = (Gc w Ec)^gamma_c (Eq. 5)."""
+    p = sc.params
+    E = np.asarray(Ec_ref, np.float64).reshape(-1, 3)
+    g = np.asarray(p.gamma_c, np.float64)[None, :]
+    a = p.gain_c * np.asarray(p.wb, np.float64)[None, :] * E
+    with np.errstate(divide="ignore", invalid="ignore"):
+        d = np.where(a > 0, g * np.power(np.maximum(a, 1e-300), g - 1) * p.gain_c * np.asarray(p.wb)[None, :], 0.0)
+    return d * atol_E + 1e-12
+
+
 def pixel_parity(gpu, ref, rtol=1e-4, atol=1e-7, frac=0.999, mean_rtol=1e-5):
     """North-star image gate: |g - r| <= rtol |r| + atol per channel on at
     least `frac` of the pixels (edge flips between FP32 and FP64 paths take
-    the rest), and the image mean within mean_rtol."""
+    the rest), and the image mean within mean_rtol.  ``atol`` may be an array
+    of per-element tolerances."""
     gpu = np.asarray(gpu, np.float64).reshape(-1, 3)
     ref = np.asarray(ref, np.float64).reshape(-1, 3)
+    atol = np.broadcast_to(np.asarray(atol, np.float64).reshape(-1, 3) if np.ndim(atol) else atol, ref.shape)
     ok = np.all(np.abs(gpu - ref) <= rtol * np.abs(ref) + atol, axis=1)
     n_bad = int((~ok).sum())
     allowed = int(np.floor((1.0 - frac) * len(ok)))
@@ -81,4 +95,7 @@ def pixel_parity(gpu, ref, rtol=1e-4, atol=1e-7, frac=0.999, mean_rtol=1e-5):
     mean_ok = abs(m_g - m_r) <= mean_rtol * abs(m_r) + 1e-12
     return n_bad <= allowed and mean_ok, {"bad_pixels": n_bad, "allowed": allowed, "n": len(ok),
                                           "mean_gpu": m_g, "mean_ref": m_r,
-                                          "max_rel": float(np.max(np.abs(gpu - ref) / (np.abs(ref) + 1e-7)))}
+                                          "max_rel": float(np.max(np.abs(gpu - ref) / (np.abs(ref) + 1e-7))),
+                                          "worst": [(int(i), gpu[i].tolist(), ref[i].tolist())
+                                                    for i in np.argsort(-np.max(np.abs(gpu - ref) / (
+                                                        np.abs(ref) + atol + 1e-30), axis=1))[:3]]}

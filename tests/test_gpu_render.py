@@ -5,7 +5,7 @@ import numpy as np
 import pytest
 
 from paper_2503_12174_gb300 import scenes
-from gpu_util import GpuScene, need_cuda, pixel_parity
+from gpu_util import GpuScene, crf_atol, need_cuda, pixel_parity
 
 pytestmark = pytest.mark.gpu
 
@@ -28,7 +28,7 @@ def _check(orc, sc, pixels=None, spp=None):
         Ec, Ic = Ec.reshape(-1, 3)[pixels], Ic.reshape(-1, 3)[pixels]
     ok, info = pixel_parity(Ec, rE)
     assert ok, ("Ec", info)
-    ok, info = pixel_parity(Ic, rI)
+    ok, info = pixel_parity(Ic, rI, atol=crf_atol(sc, rE))
     assert ok, ("Ic", info)
     assert np.abs(rE).max() > 0
     return info
