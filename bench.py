@@ -1,0 +1,422 @@
+"""Throughput of the DPCS path tracer on one or more GPUs.
+
+Default workload (one step = one forward render, Eq. 7): the interreflection
+corner scene -- three orthogonal planes and an occluding box, T = 1026,
+Lambert+GGX textures 256x256, projector 256x256, camera 256x256, 64 samples
+per pixel, 3 bounces.  Metric: camera samples per second (Msamples/s).
+
+The same JSON line also carries
+  fwd_bwd   : one projector-compensation step (render, L2 loss, path-replay
+              adjoint, Adam on Ip; Eq. 13) on the corner scene at 512x512,
+              16 spp -- the forward+backward throughput;
+  e2e       : the forward metric through the public API with the projector
+              image uploaded from pinned host memory and Ic read back every step;
+  roofline  : the render kernel's FP32 arithmetic rate against the GPU's FP32
+              peak (algorithmic FLOPs counted by the DPCS_COUNTERS build);
+  cpu_baseline : the FP64 oracle on the host cores over a bounded pixel sample.
+
+``--impl reference`` times the oracle alone (the reference arm).  Under
+torchrun every rank renders its own independent image (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Msamples/s fwd and fwd+bwd; relight p50/p99 ms under load vs per-call render"
+UNIT = "Msamples/s"
+WORKLOAD = "corner scene T=1026, camera/projector/textures 256x256, 64 spp, 3 bounces, forward render"
+FWD_BWD_WORKLOAD = "corner scene T=1026 at 512x512 (camera, projector, textures), 16 spp, 3 bounces: " \
+                   "render + L2 loss + path-replay adjoint + Adam on Ip"
+L2_FLUSH_BYTES = 256 << 20
+
+# FP32 arithmetic operations (add, sub, mul, div, sqrt; an FMA counts 2) per
+# unit of work, counted from the formulas the kernels evaluate:
+FLOP = {
+    "node_visits": 26,     # two slab tests: 6 sub + 6 mul each, plus the far-bound widening
+    "tri_tests": 46,       # Moller-Trumbore: 2 cross, 4 dot, reciprocal, 3 scalings, origin shift, u+v
+    "paths": 27,           # film point, Kc^-1 product, normalisation
+    "vertices": 140,       # hit point, normal, UVs, bilinear albedo/roughness, projector projection, shadow setup
+    "lit": 160,            # bilinear Ep, geometry term, GGX evaluation with roughness derivative, contribution
+    "continuations": 230,  # frame, lobe sample (cosine or visible-normal GGX), pdf, BRDF, throughput
+}
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="dpcs", choices=["dpcs", "reference"])
+    ap.add_argument("--fwd-bwd-steps", type=int, default=10)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target oracle time for cpu_baseline")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        cmd = ["nvidia-smi", "--query-gpu=" + ",".join(self.FIELDS), "--format=csv,noheader,nounits", "-lms", "100"]
+        if self.gpu_id:
+            cmd += ["-i", self.gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.15)
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.15)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _cpu_baseline(sc, seconds: float, steps: int | None = None):
+    """The FP64 oracle on a bounded random pixel sample of ``sc`` (all host
+    cores).  Returns (Msamples/s, cores, sample description, per-step values)."""
+    import oracle
+
+    oracle.build()
+    cores = oracle.num_threads(os.cpu_count() or 1)
+    rng = np.random.default_rng(123)
+    npix = sc.Hc * sc.Wc
+    probe = rng.choice(npix, min(64, npix), replace=False)
+    t0 = time.perf_counter()
+    oracle.render(sc, pixels=probe)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    per_pixel = dt / len(probe)
+    if steps is None:
+        n = int(min(npix, max(64, seconds / per_pixel)))
+        px = rng.choice(npix, n, replace=False)
+        t0 = time.perf_counter()
+        oracle.render(sc, pixels=px)
+        dt = time.perf_counter() - t0
+        val = n * sc.spp / dt / 1e6
+        return val, cores, f"{n} random pixels x {sc.spp} spp of the workload ({dt:.1f} s, brute-force FP64)", [val]
+    n = int(min(npix, max(32, seconds / per_pixel)))
+    vals = []
+    for k in range(steps):
+        px = rng.choice(npix, n, replace=False)
+        t0 = time.perf_counter()
+        oracle.render(sc, pixels=px)
+        vals.append(n * sc.spp / (time.perf_counter() - t0) / 1e6)
+    return statistics.mean(vals), cores, f"{n} random pixels x {sc.spp} spp per step (brute-force FP64)", vals
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    from paper_2503_12174_gb300 import scenes
+
+    sc = scenes.corner(res=256, spp=64, bounces=3)
+    _, cores, sample, vals = _cpu_baseline(sc, seconds=4.0, steps=args.warmup + args.steps)
+    timed = vals[args.warmup:]
+    v = statistics.mean(timed)
+    ms = sc.n_samples / (v * 1e6) * 1e3
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "reference": "FP64 CPU oracle (brute-force ray-triangle)",
+                       "ms_per_step_note": "extrapolated from the per-step pixel sample to the full image"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+def main():
+    args = _args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2503_12174_gb300 import build as _build
+
+    if rank == 0:
+        _build.build()
+    if dist:
+        dist.barrier()
+    from paper_2503_12174_gb300 import dpcs, scenes
+
+    dev = torch.device("cuda", local)
+    ctx = dpcs.Context(local)
+    flush_buf = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def flush(k):
+        flush_buf.fill_(float(k))
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x: float) -> float:
+        if not dist:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    # ------------------------------------------------------------ forward
+    sc = scenes.corner(res=256, spp=64, bounces=3, seed=1000 + rank)
+    h = ctx.upload(sc.verts, sc.tris, sc.uv)
+    alb = torch.from_numpy(sc.albedo).to(dev)
+    rough = torch.from_numpy(sc.rough).to(dev)
+    Ip = torch.from_numpy(sc.Ip).to(dev)
+    view, prm = dpcs.view_of(sc), dpcs.make_params(sc.params)
+    Ic = torch.empty((sc.Hc, sc.Wc, 3), device=dev)
+    Ec = torch.empty_like(Ic)
+    stream = torch.cuda.current_stream()
+
+    def fwd():
+        ctx.render(h, alb, rough, Ip, view, prm, sc.spp, sc.bounces, sc.seed, Ic=Ic, Ec=Ec)
+
+    for k in range(args.warmup):
+        flush(k)
+        fwd()
+    ctx.sync()
+    gpu_uuid = None
+    try:
+        gpu_uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    launches0 = ctx.launch_count
+    barrier()
+    ctx.timing(True)
+    with ClockSampler(gpu_uuid) as clocks:
+        for k in range(args.steps):
+            flush(k)
+            starts[k].record(stream)
+            fwd()
+            ends[k].record(stream)
+        barrier()
+    ctx.sync()
+    launches = ctx.launch_count - launches0
+    render_ms, render_n = ctx.kernel_time(0)
+    ctx.timing(False)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = max_over_ranks(sum(step_ms))
+    ms_per_step = total_ms / args.steps
+    value = sc.n_samples * ws * args.steps / (total_ms / 1e3) / 1e6
+    kernel_ms = render_ms / max(render_n, 1)
+
+    # ------------------------------------------------------------ e2e (host buffers)
+    Ip_host = torch.from_numpy(sc.Ip.copy()).pin_memory()
+    Ic_host = torch.empty((sc.Hc, sc.Wc, 3), dtype=torch.float32).pin_memory()
+    Ip_dev = torch.empty_like(Ip)
+
+    def e2e_step():
+        Ip_dev.copy_(Ip_host, non_blocking=True)
+        ctx.render(h, alb, rough, Ip_dev, view, prm, sc.spp, sc.bounces, sc.seed, Ic=Ic)
+        Ic_host.copy_(Ic, non_blocking=True)
+
+    for k in range(args.warmup):
+        e2e_step()
+    torch.cuda.synchronize()
+    e_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    e_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier()
+    for k in range(args.steps):
+        flush(k)
+        e_s[k].record(stream)
+        e2e_step()
+        e_e[k].record(stream)
+    barrier()
+    e2e_ms = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(e_s, e_e)))
+    e2e_val = sc.n_samples * ws * args.steps / (e2e_ms / 1e3) / 1e6
+    np.testing.assert_array_equal(Ic_host.numpy(), Ic.cpu().numpy())
+
+    # ------------------------------------------------------------ fwd + bwd (compensation step)
+    cs = scenes.compensation(res=512, spp=16, seed=2000 + rank)
+    hc = ctx.upload(cs.verts, cs.tris, cs.uv)
+    calb = torch.from_numpy(cs.albedo).to(dev)
+    crough = torch.from_numpy(cs.rough).to(dev)
+    cview, cprm = dpcs.view_of(cs), dpcs.make_params(cs.params)
+    target = torch.empty((cs.Hc, cs.Wc, 3), device=dev)
+    ctx.render(hc, calb, crough, torch.from_numpy(cs.Ip).to(dev), cview, cprm, cs.spp, cs.bounces, cs.seed + 7,
+               Ic=target)
+    P = torch.full((cs.Hp, cs.Wp, 3), 0.5, device=dev)
+    M, V, G = torch.zeros_like(P), torch.zeros_like(P), torch.zeros_like(P)
+    cIc = torch.empty((cs.Hc, cs.Wc, 3), device=dev)
+    cEc = torch.empty_like(cIc)
+    dIc = torch.empty_like(cIc)
+    loss = torch.empty(1, device=dev)
+    step_no = [0]
+
+    def comp_step():
+        step_no[0] += 1
+        ctx.render(hc, calb, crough, P, cview, cprm, cs.spp, cs.bounces, cs.seed + step_no[0], Ic=cIc, Ec=cEc)
+        ctx.l2_loss(cIc, target, dIc, loss)
+        G.zero_()
+        ctx.render_backward(hc, calb, crough, P, cview, cprm, cs.spp, cs.bounces, cs.seed + step_no[0], cEc, cIc,
+                            dIc, dIp=G)
+        ctx.adam(P, G, M, V, step_no[0], lr=1e-2)
+
+    for k in range(args.warmup):
+        flush(k)
+        comp_step()
+    ctx.sync()
+    fb_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.fwd_bwd_steps)]
+    fb_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.fwd_bwd_steps)]
+    barrier()
+    ctx.timing(True)
+    for k in range(args.fwd_bwd_steps):
+        flush(k)
+        fb_s[k].record(stream)
+        comp_step()
+        fb_e[k].record(stream)
+    barrier()
+    ctx.sync()
+    replay_ms, replay_n = ctx.kernel_time(1)
+    crender_ms, crender_n = ctx.kernel_time(0)
+    ctx.timing(False)
+    fb_ms = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(fb_s, fb_e)))
+    fb_val = cs.n_samples * ws * args.fwd_bwd_steps / (fb_ms / 1e3) / 1e6
+
+    # ------------------------------------------------------------ roofline (counters build, untimed)
+    counts = None
+    flops = None
+    try:
+        cctx = dpcs.Context(local, lib=dpcs.counters_library())
+        ch = cctx.upload(sc.verts, sc.tris, sc.uv)
+        cctx.counters(reset=True)
+        cctx.render(ch, alb, rough, Ip, view, prm, sc.spp, sc.bounces, sc.seed, Ic=torch.empty_like(Ic))
+        counts = cctx.counters(reset=True)
+        cctx.close()
+        flops = sum(FLOP[k] * counts[k] for k in FLOP)
+    except Exception as e:  # the roofline stays unreported rather than guessed
+        counts = {"error": str(e)[:200]}
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tflops = sms * 128 * 2 * sm_max_mhz * 1e6 / 1e12
+    roof = None
+    if flops:
+        achieved = flops / (kernel_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "kernel": "k_render", "achieved": achieved, "peak": peak_tflops,
+                "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": None,
+                "flops_per_launch": flops, "kernel_ms": kernel_ms,
+                "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 FLOP/FMA x {sm_max_mhz:.0f} MHz (max SM clock)",
+                "counts_per_launch": counts}
+
+    # ------------------------------------------------------------ CPU baseline
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        v, cores, sample, _ = _cpu_baseline(sc, seconds=args.cpu_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+
+    clk = clocks.summary()
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "samples_per_step_per_gpu": sc.n_samples, "spp": sc.spp,
+                       "bounces": sc.bounces, "triangles": sc.T, "resolution": [sc.Hc, sc.Wc],
+                       "l2": f"flushed: {L2_FLUSH_BYTES >> 20} MiB write between timed steps (inputs < L2)",
+                       "parallelism": f"replicas x{ws} (independent images, no collective)"},
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(Ip_host.numel() * 4),
+                    "d2h_bytes_per_step": int(Ic_host.numel() * 4)},
+            "fwd_bwd": {"value": fb_val, "unit": UNIT, "workload": FWD_BWD_WORKLOAD,
+                        "ms_per_step": fb_ms / args.fwd_bwd_steps, "steps": args.fwd_bwd_steps,
+                        "samples_per_step_per_gpu": cs.n_samples,
+                        "replay_kernel_ms": replay_ms / max(replay_n, 1),
+                        "render_kernel_ms": crender_ms / max(crender_n, 1)},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "gpu_launches": int(launches),
+            "kernel_ms_per_step": kernel_ms,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.free(h)
+    ctx.free(hc)
+    ctx.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -117,6 +117,27 @@ size_t dpcs_memory_used(const dpcs_ctx *ctx);
 uint64_t dpcs_launch_count(const dpcs_ctx *ctx);
 
 /*
+ * Kernel timing with CUDA events recorded on the launching stream around the
+ * path-tracing kernels: kernel 0 = forward render (k_render), 1 = path replay
+ * (k_replay).  dpcs_timing_enable(ctx, 1) clears and starts recording,
+ * (ctx, 0) stops it.  dpcs_timing_read waits for the recorded events and
+ * returns the summed duration in milliseconds and the number of launches.
+ * Measurement support, not part of the paper's method.
+ */
+dpcs_status dpcs_timing_enable(dpcs_ctx *ctx, int32_t on);
+dpcs_status dpcs_timing_read(dpcs_ctx *ctx, int32_t kernel, double *total_ms, int64_t *launches);
+
+/*
+ * Work counters of a library built with DPCS_COUNTERS: out[0..7] = BVH node
+ * visits, triangle tests, closest-hit rays, shadow rays, path vertices,
+ * vertices lit by the projector, BRDF continuations, camera paths, summed
+ * over every render / replay launch since the last reset (reset != 0 clears
+ * them after reading).  Synchronous.  Returns DPCS_ERR_INVALID_ARG in a
+ * library built without counters.  Measurement support for the roofline.
+ */
+dpcs_status dpcs_counters_read(dpcs_ctx *ctx, uint64_t *out, int32_t reset);
+
+/*
  * Upload a triangle mesh and build its LBVH on the device (Morton codes of
  * triangle centroids, radix sort, Karras radix tree, bottom-up AABB refit).
  *  verts : host, V x 3 float32 positions (world = camera frame)

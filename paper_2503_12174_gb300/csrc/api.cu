@@ -10,6 +10,7 @@
 
 #include <map>
 #include <string>
+#include <vector>
 
 #include "dpcs.h"
 #include "internal.h"
@@ -21,6 +22,11 @@ namespace {
 struct Buf {
     void *p = nullptr;
     size_t n = 0;
+};
+
+struct TimedLaunch {
+    cudaEvent_t a = nullptr, b = nullptr;
+    int kernel = 0;
 };
 
 }  // namespace
@@ -36,6 +42,11 @@ struct dpcs_ctx {
     uint64_t next_scene = 1;
     // scratch
     Buf ep4, tex4, gE, dEp4, dtex4, acc, partial, build, upload;
+    // measurement support
+    unsigned long long *counters = nullptr;  // 8 totals (DPCS_COUNTERS build)
+    bool timing = false;
+    std::vector<TimedLaunch> timed;
+    size_t n_timed = 0;
 };
 
 namespace {
@@ -93,6 +104,27 @@ dpcs_status check_launch(dpcs_ctx *c, int n, const char *what) {
     c->launches += (uint64_t)n;
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? DPCS_OK : cuda_fail(c, e, what);
+}
+
+// events around a path-tracing kernel when timing is on
+TimedLaunch *timing_begin(dpcs_ctx *c, int kernel, cudaStream_t st) {
+    if (!c->timing) return nullptr;
+    if (c->n_timed == c->timed.size()) {
+        TimedLaunch t;
+        if (cudaEventCreate(&t.a) != cudaSuccess || cudaEventCreate(&t.b) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        c->timed.push_back(t);
+    }
+    TimedLaunch *t = &c->timed[c->n_timed++];
+    t->kernel = kernel;
+    cudaEventRecord(t->a, st);
+    return t;
+}
+
+void timing_end(TimedLaunch *t, cudaStream_t st) {
+    if (t) cudaEventRecord(t->b, st);
 }
 
 bool finite_all(const float *v, int n) {
@@ -181,6 +213,11 @@ dpcs_status prepare(dpcs_ctx *c, dpcs_scene scene, const float *albedo, const fl
     while ((2 << l2) <= spp && l2 < 5) ++l2;  // lanes per pixel: largest power of two <= min(spp, 32)
     a.log2L = l2;
     a.status = c->status;
+#ifdef DPCS_COUNTERS
+    a.counters = c->counters;
+#else
+    a.counters = nullptr;
+#endif
     *sc_out = &sc;
     return DPCS_OK;
 }
@@ -203,6 +240,8 @@ dpcs_status dpcs_create(int device, size_t hbm_budget_bytes, dpcs_ctx **out) {
     dpcs_status s = set_device(c);
     if (s == DPCS_OK) s = dev_alloc(c, (void **)&c->status, sizeof(unsigned), "status word");
     if (s == DPCS_OK && cudaMemset(c->status, 0, sizeof(unsigned)) != cudaSuccess) s = DPCS_ERR_CUDA;
+    if (s == DPCS_OK) s = dev_alloc(c, (void **)&c->counters, 8 * sizeof(unsigned long long), "counters");
+    if (s == DPCS_OK && cudaMemset(c->counters, 0, 8 * sizeof(unsigned long long)) != cudaSuccess) s = DPCS_ERR_CUDA;
     if (s != DPCS_OK) {
         delete c;
         return s;
@@ -227,8 +266,60 @@ dpcs_status dpcs_destroy(dpcs_ctx *c) {
     for (Buf *b : bufs)
         if (b->p) cudaFree(b->p);
     cudaFree(c->status);
+    cudaFree(c->counters);
+    for (TimedLaunch &t : c->timed) {
+        cudaEventDestroy(t.a);
+        cudaEventDestroy(t.b);
+    }
     delete c;
     return DPCS_OK;
+}
+
+dpcs_status dpcs_timing_enable(dpcs_ctx *c, int32_t on) {
+    if (!c) return DPCS_ERR_INVALID_ARG;
+    dpcs_status s = set_device(c);
+    if (s) return s;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(c, e, "timing_enable");
+    c->timing = on != 0;
+    if (on) c->n_timed = 0;
+    return DPCS_OK;
+}
+
+dpcs_status dpcs_timing_read(dpcs_ctx *c, int32_t kernel, double *total_ms, int64_t *launches) {
+    if (!c || !total_ms || !launches) return DPCS_ERR_INVALID_ARG;
+    dpcs_status s = set_device(c);
+    if (s) return s;
+    double tot = 0.0;
+    int64_t n = 0;
+    for (size_t i = 0; i < c->n_timed; ++i) {
+        TimedLaunch &t = c->timed[i];
+        if (t.kernel != kernel) continue;
+        cudaError_t e = cudaEventSynchronize(t.b);
+        float ms = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, t.a, t.b);
+        if (e != cudaSuccess) return cuda_fail(c, e, "timing_read");
+        tot += ms;
+        ++n;
+    }
+    *total_ms = tot;
+    *launches = n;
+    return DPCS_OK;
+}
+
+dpcs_status dpcs_counters_read(dpcs_ctx *c, uint64_t *out, int32_t reset) {
+    if (!c || !out) return DPCS_ERR_INVALID_ARG;
+#ifndef DPCS_COUNTERS
+    (void)reset;
+    return fail(c, DPCS_ERR_INVALID_ARG, "library built without DPCS_COUNTERS");
+#else
+    dpcs_status s = set_device(c);
+    if (s) return s;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(out, c->counters, 8 * sizeof(uint64_t), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && reset) e = cudaMemset(c->counters, 0, 8 * sizeof(unsigned long long));
+    return e == cudaSuccess ? DPCS_OK : cuda_fail(c, e, "counters_read");
+#endif
 }
 
 const char *dpcs_last_error(const dpcs_ctx *c) { return c ? c->err.c_str() : "null context"; }
@@ -395,7 +486,9 @@ dpcs_status dpcs_render(dpcs_ctx *c, dpcs_scene scene, const float *albedo, cons
     a.Ec = Ec;
     int nl = launch_prf(Ip, np, params->gamma_p, params->gain_p, (float4 *)c->ep4.p, st);
     nl += launch_pack_tex(albedo, rough, nt, (float4 *)c->tex4.p, st);
+    TimedLaunch *tl = timing_begin(c, 0, st);
     nl += launch_render(a, st);
+    timing_end(tl, st);
     return check_launch(c, nl, "render");
 }
 
@@ -431,7 +524,9 @@ dpcs_status dpcs_render_backward(dpcs_ctx *c, dpcs_scene scene, const float *alb
     a.gE = (const float *)c->gE.p;
     a.dEp = (float4 *)c->dEp4.p;
     a.dtex = (float4 *)c->dtex4.p;
+    TimedLaunch *tl = timing_begin(c, 1, st);
     nl += launch_replay(a, st);
+    timing_end(tl, st);
     nl += launch_prf_backward(Ip, (const float4 *)c->dEp4.p, np, params->gamma_p, params->gain_p, dIp, acc, st);
     if (dAlbedo || dRough) nl += launch_tex_backward((const float4 *)c->dtex4.p, nt, dAlbedo, dRough, st);
     if (dParams) nl += launch_finalize_params(acc, dParams, st);

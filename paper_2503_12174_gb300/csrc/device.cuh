@@ -15,6 +15,31 @@ namespace dpcs {
 constexpr float kRayEps = 1e-4f;   // origin offset along the shading normal
 constexpr int kStack = 64;         // traversal stack depth
 
+// Work counters of the DPCS_COUNTERS build (node visits, triangle tests,
+// closest rays, shadow rays, vertices, lit NEE, continuations, paths); in
+// the normal build every increment compiles away.
+enum { kCntNode = 0, kCntTri, kCntRay, kCntShadow, kCntVert, kCntLit, kCntCont, kCntPath, kCntN };
+struct Cnt {
+#ifdef DPCS_COUNTERS
+    uint32_t v[kCntN];
+    __device__ Cnt() {
+        for (int i = 0; i < kCntN; ++i) v[i] = 0u;
+    }
+    __device__ __forceinline__ void add(int i, uint32_t k = 1u) { v[i] += k; }
+    __device__ __forceinline__ void flush(unsigned long long *out) {
+        if (!out) return;
+        for (int i = 0; i < kCntN; ++i) {
+            unsigned long long x = v[i];
+            for (int off = 16; off; off >>= 1) x += __shfl_xor_sync(0xffffffffu, x, off);
+            if ((threadIdx.x & 31) == 0 && x) atomicAdd(out + i, x);
+        }
+    }
+#else
+    __device__ __forceinline__ void add(int, uint32_t = 1u) {}
+    __device__ __forceinline__ void flush(unsigned long long *) {}
+#endif
+};
+
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon et al., SC'11): ten rounds of two 32x32->64 products
 // with the key bumped by the Weyl constants between rounds.
@@ -288,7 +313,7 @@ struct Hit {
 template <bool ANY>
 __device__ __forceinline__ bool traverse(const float4 *__restrict__ nodes, const float4 *__restrict__ tris,
                                          int32_t root, int32_t T, const Ray &ray, float tmax, Hit &h,
-                                         unsigned *status) {
+                                         unsigned *status, Cnt &cnt) {
     h.pos = -1;
     h.orig = 0x7fffffff;
     h.t = tmax;
@@ -305,6 +330,7 @@ __device__ __forceinline__ bool traverse(const float4 *__restrict__ nodes, const
             return false;
         }
         if (node >= 0) {
+            cnt.add(kCntNode);
             const float4 n0 = __ldg(nodes + 4 * node + 0);
             const float4 n1 = __ldg(nodes + 4 * node + 1);
             const float4 n2 = __ldg(nodes + 4 * node + 2);
@@ -328,6 +354,7 @@ __device__ __forceinline__ bool traverse(const float4 *__restrict__ nodes, const
             if (hr) { node = cr; continue; }
         } else {
             const int pos = ~node;
+            cnt.add(kCntTri);
             const float4 a = __ldg(tris + 3 * pos + 0);
             const float4 b = __ldg(tris + 3 * pos + 1);
             const float4 c = __ldg(tris + 3 * pos + 2);
@@ -369,9 +396,11 @@ struct VRec {
 };
 
 template <bool REC>
-__device__ __forceinline__ f3 trace_path(const RenderArgs &a, uint32_t pix, uint32_t s, VRec *rec, int &nv) {
+__device__ __forceinline__ f3 trace_path(const RenderArgs &a, uint32_t pix, uint32_t s, VRec *rec, int &nv,
+                                         Cnt &cnt) {
     float u[4];
     nv = 0;
+    cnt.add(kCntPath);
     rand4(a.key0, a.key1, pix, s, 0u, u);
     const float fx = (float)(pix % (uint32_t)a.Wc) + (a.jitter ? u[0] : 0.5f);
     const float fy = (float)(pix / (uint32_t)a.Wc) + (a.jitter ? u[1] : 0.5f);
@@ -383,7 +412,9 @@ __device__ __forceinline__ f3 trace_path(const RenderArgs &a, uint32_t pix, uint
     for (int b = 1; b <= a.bounces; ++b) {
         Hit h;
         const Ray ray = make_ray(o, d);
-        if (!traverse<false>(a.nodes, a.tris, a.root, a.T, ray, INFINITY, h, a.status)) break;
+        cnt.add(kCntRay);
+        if (!traverse<false>(a.nodes, a.tris, a.root, a.T, ray, INFINITY, h, a.status, cnt)) break;
+        cnt.add(kCntVert);
         const float4 A = __ldg(a.tris + 3 * h.pos + 0);
         const float4 E1 = __ldg(a.tris + 3 * h.pos + 1);
         const float4 E2 = __ldg(a.tris + 3 * h.pos + 2);
@@ -427,7 +458,9 @@ __device__ __forceinline__ f3 trace_path(const RenderArgs &a, uint32_t pix, uint
                     const float sd = sqrtf(dot(sv, sv));
                     Hit hs;
                     const Ray sray = make_ray(so, sv * (1.0f / sd));
-                    if (!traverse<true>(a.nodes, a.tris, a.root, a.T, sray, sd - kRayEps, hs, a.status)) {
+                    cnt.add(kCntShadow);
+                    if (!traverse<true>(a.nodes, a.tris, a.root, a.T, sray, sd - kRayEps, hs, a.status, cnt)) {
+                        cnt.add(kCntLit);
                         const Bilin pb = bilin_setup(up, vp, a.Wp, a.Hp);
                         const float4 ep = bilin_fetch(a.Ep, pb, a.Wp, a.Hp);
                         const float G = a.k_proj * cpz * cs / r2;
@@ -470,6 +503,7 @@ __device__ __forceinline__ f3 trace_path(const RenderArgs &a, uint32_t pix, uint
         const float cw = dot(n, wi) / (pdf * qrr);
         const f3 fi = mk3(rho.x * DPCS_INV_PI_F + si, rho.y * DPCS_INV_PI_F + si, rho.z * DPCS_INV_PI_F + si);
         beta = beta * fi * cw;
+        cnt.add(kCntCont);
         if (REC) {
             R->si = si; R->dsi = dsi; R->cw = cw;
         }

@@ -58,6 +58,7 @@ struct RenderArgs {
     float4 *dEp;         // dLoss/dEp accumulators (Hp x Wp)
     float4 *dtex;        // dLoss/d(albedo, rough) accumulators (Ht x Wt)
     unsigned *status;
+    unsigned long long *counters;  // DPCS_COUNTERS build only (8 totals)
 };
 
 // Launchers (render.cu, lbvh.cu, optim.cu).  Each returns the number of

@@ -66,12 +66,14 @@ __global__ void __launch_bounds__(kRenderBlock) k_render(const RenderArgs a) {
     const int sl = (int)(gt & (L - 1));
     const int64_t npix = (int64_t)a.Hc * a.Wc;
     f3 sum = mk3(0.f, 0.f, 0.f);
+    Cnt cnt;
     if (pix < npix) {
         for (int s = sl; s < a.spp; s += L) {
             int nv;
-            sum = sum + trace_path<false>(a, (uint32_t)pix, (uint32_t)s, nullptr, nv);
+            sum = sum + trace_path<false>(a, (uint32_t)pix, (uint32_t)s, nullptr, nv, cnt);
         }
     }
+    cnt.flush(a.counters);
     for (int off = L >> 1; off > 0; off >>= 1) {
         sum.x += __shfl_xor_sync(0xffffffffu, sum.x, off);
         sum.y += __shfl_xor_sync(0xffffffffu, sum.y, off);
@@ -97,8 +99,9 @@ __global__ void k_trace(const float4 *__restrict__ nodes, const float4 *__restri
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     Hit h;
+    Cnt cnt;
     const Ray r = make_ray(mk3(o[3 * i], o[3 * i + 1], o[3 * i + 2]), mk3(d[3 * i], d[3 * i + 1], d[3 * i + 2]));
-    const bool hit = traverse<false>(nodes, tris, root, T, r, INFINITY, h, status);
+    const bool hit = traverse<false>(nodes, tris, root, T, r, INFINITY, h, status, cnt);
     tout[i] = hit ? h.t : INFINITY;
     triout[i] = hit ? h.orig : -1;
 }
@@ -157,15 +160,17 @@ __global__ void __launch_bounds__(kRenderBlock) k_replay(const RenderArgs a) {
     const int64_t pix = gt >> a.log2L;
     const int sl = (int)(gt & (L - 1));
     const int64_t npix = (int64_t)a.Hc * a.Wc;
-    if (pix >= npix) return;
+    Cnt cnt;
     const float inv = 1.0f / (float)a.spp;
-    const f3 gbar = mk3(a.gE[3 * pix] * inv, a.gE[3 * pix + 1] * inv, a.gE[3 * pix + 2] * inv);
-    if (gbar.x == 0.0f && gbar.y == 0.0f && gbar.z == 0.0f) return;
+    const bool live = pix < npix;
+    const f3 gbar = live ? mk3(a.gE[3 * pix] * inv, a.gE[3 * pix + 1] * inv, a.gE[3 * pix + 2] * inv)
+                         : mk3(0.f, 0.f, 0.f);
     const float gb_in[3] = {gbar.x, gbar.y, gbar.z};
-    for (int s = sl; s < a.spp; s += L) {
+    const bool any = gbar.x != 0.0f || gbar.y != 0.0f || gbar.z != 0.0f;
+    for (int s = sl; any && s < a.spp; s += L) {
         VRec rec[DPCS_MAX_BOUNCES];
         int nv;
-        trace_path<true>(a, (uint32_t)pix, (uint32_t)s, rec, nv);
+        trace_path<true>(a, (uint32_t)pix, (uint32_t)s, rec, nv, cnt);
         float A[3] = {0.f, 0.f, 0.f};
         for (int c = nv - 1; c >= 0; --c) {
             const VRec &R = rec[c];
@@ -203,6 +208,7 @@ __global__ void __launch_bounds__(kRenderBlock) k_replay(const RenderArgs a) {
             }
         }
     }
+    cnt.flush(a.counters);
 }
 
 // Eq. 1 adjoint: dIp += dEp Gp gamma Ip^(gamma-1); gamma_p and Gp reductions

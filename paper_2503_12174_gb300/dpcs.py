@@ -30,7 +30,8 @@ DPCS_MAX_BOUNCES = 8
 EXPORTED = [
     "dpcs_create", "dpcs_destroy", "dpcs_last_error", "dpcs_sync", "dpcs_memory_used", "dpcs_launch_count",
     "dpcs_scene_upload", "dpcs_scene_free", "dpcs_scene_export", "dpcs_trace", "dpcs_render",
-    "dpcs_render_backward", "dpcs_l2_loss", "dpcs_adam",
+    "dpcs_render_backward", "dpcs_l2_loss", "dpcs_adam", "dpcs_timing_enable", "dpcs_timing_read",
+    "dpcs_counters_read",
 ]
 
 
@@ -77,6 +78,10 @@ _SIGS = {
     "dpcs_render_backward": (ctypes.c_int32, [_P, ctypes.c_uint64, _P, _P, ctypes.c_int32, ctypes.c_int32, _P,
                                               ctypes.POINTER(DpcsView), ctypes.POINTER(DpcsParams), ctypes.c_int32,
                                               ctypes.c_int32, ctypes.c_uint64, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "dpcs_timing_enable": (ctypes.c_int32, [_P, ctypes.c_int32]),
+    "dpcs_timing_read": (ctypes.c_int32, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_int64)]),
+    "dpcs_counters_read": (ctypes.c_int32, [_P, _P, ctypes.c_int32]),
     "dpcs_l2_loss": (ctypes.c_int32, [_P, _P, _P, ctypes.c_int64, _P, _P, _P]),
     "dpcs_adam": (ctypes.c_int32, [_P, _P, _P, _P, _P, ctypes.c_int64, ctypes.c_float, ctypes.c_float,
                                    ctypes.c_float, ctypes.c_float, ctypes.c_int32, ctypes.c_float, ctypes.c_float,
@@ -86,6 +91,16 @@ _SIGS = {
 
 def library_path() -> str:
     return _build.lib_path()
+
+
+def open_library(path: str):
+    """ctypes handle of a libdpcs build at ``path`` with every signature set."""
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
 
 
 def load_library(path: str | None = None):
@@ -98,13 +113,13 @@ def load_library(path: str | None = None):
         path = library_path()
         if not os.path.exists(path):
             path = _build.build()
-    lib = ctypes.CDLL(path)
-    for name, (res, args) in _SIGS.items():
-        fn = getattr(lib, name)
-        fn.restype = res
-        fn.argtypes = args
-    _lib, _lib_path = lib, path
-    return lib
+    _lib, _lib_path = open_library(path), path
+    return _lib
+
+
+def counters_library():
+    """The DPCS_COUNTERS build (counts node visits, triangle tests, ...)."""
+    return open_library(_build.build(variant="_counters", defines=("DPCS_COUNTERS",)))
 
 
 def make_params(p) -> DpcsParams:
@@ -200,6 +215,18 @@ def dpcs_render_backward(ctx, scene, albedo, rough, Ht, Wt, Ip, view, params, sp
                                                dRough, dParams, stream)
 
 
+def dpcs_timing_enable(ctx, on):
+    return load_library().dpcs_timing_enable(ctx, int(on))
+
+
+def dpcs_timing_read(ctx, kernel, total_ms, launches):
+    return load_library().dpcs_timing_read(ctx, int(kernel), total_ms, launches)
+
+
+def dpcs_counters_read(ctx, out, reset):
+    return load_library().dpcs_counters_read(ctx, out, int(reset))
+
+
 def dpcs_l2_loss(ctx, Ic, target, n, dIc, loss, stream):
     return load_library().dpcs_l2_loss(ctx, Ic, target, n, dIc, loss, stream)
 
@@ -239,16 +266,37 @@ def _stream(stream):
 class Context:
     """A libdpcs context on one CUDA device, driven with torch tensors."""
 
-    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, lib=None):
         import torch
 
+        self.lib = lib if lib is not None else load_library()
         self.device = torch.device("cuda", device)
-        self.handle = dpcs_create(device, hbm_budget_bytes)
-        self.lib = load_library()
+        h = _P()
+        st = self.lib.dpcs_create(int(device), int(hbm_budget_bytes), ctypes.byref(h))
+        if st != DPCS_OK:
+            raise DPCSError(st, "dpcs_create failed")
+        self.handle = h
+
+    # -- measurement -------------------------------------------------------------
+    def timing(self, on: bool):
+        self.check(self.lib.dpcs_timing_enable(self.handle, 1 if on else 0), "timing_enable")
+
+    def counters(self, reset: bool = True):
+        """Work counters (counters build only): dict of totals."""
+        out = (ctypes.c_uint64 * 8)()
+        self.check(self.lib.dpcs_counters_read(self.handle, out, 1 if reset else 0), "counters_read")
+        keys = ("node_visits", "tri_tests", "rays", "shadow_rays", "vertices", "lit", "continuations", "paths")
+        return dict(zip(keys, [int(x) for x in out]))
+
+    def kernel_time(self, kernel: int):
+        """(total ms, launches) of kernel 0 = render, 1 = replay since timing(True)."""
+        ms, n = ctypes.c_double(), ctypes.c_int64()
+        self.check(self.lib.dpcs_timing_read(self.handle, kernel, ctypes.byref(ms), ctypes.byref(n)), "timing_read")
+        return ms.value, n.value
 
     def close(self):
         if getattr(self, "handle", None):
-            dpcs_destroy(self.handle)
+            self.lib.dpcs_destroy(self.handle)
             self.handle = None
 
     def __del__(self):
@@ -259,19 +307,20 @@ class Context:
 
     def check(self, status: int, what: str):
         if status != DPCS_OK:
-            raise DPCSError(status, f"{what}: {dpcs_last_error(self.handle)}")
+            msg = self.lib.dpcs_last_error(self.handle)
+            raise DPCSError(status, f"{what}: {msg.decode() if msg else ''}")
 
     # -- bookkeeping ---------------------------------------------------------
     def sync(self, stream=None):
-        self.check(dpcs_sync(self.handle, _stream(stream)), "sync")
+        self.check(self.lib.dpcs_sync(self.handle, _stream(stream)), "sync")
 
     @property
     def memory_used(self) -> int:
-        return dpcs_memory_used(self.handle)
+        return int(self.lib.dpcs_memory_used(self.handle))
 
     @property
     def launch_count(self) -> int:
-        return dpcs_launch_count(self.handle)
+        return self.lib.dpcs_launch_count(self.handle)
 
     # -- scenes ----------------------------------------------------------------
     def upload(self, verts, tris, uv, stream=None) -> int:
@@ -279,20 +328,20 @@ class Context:
         tris = np.ascontiguousarray(tris, np.int32)
         uv = np.ascontiguousarray(uv, np.float32)
         out = ctypes.c_uint64()
-        st = dpcs_scene_upload(self.handle, verts.ctypes.data_as(_P), len(verts), tris.ctypes.data_as(_P),
+        st = self.lib.dpcs_scene_upload(self.handle, verts.ctypes.data_as(_P), len(verts), tris.ctypes.data_as(_P),
                                len(tris), uv.ctypes.data_as(_P), _stream(stream), ctypes.byref(out))
         self.check(st, "scene_upload")
         return out.value
 
     def free(self, scene: int):
-        self.check(dpcs_scene_free(self.handle, scene), "scene_free")
+        self.check(self.lib.dpcs_scene_free(self.handle, scene), "scene_free")
 
     def export(self, scene: int, T: int):
         codes = np.zeros(T, np.uint32)
         order = np.zeros(T, np.int32)
         child = np.zeros((max(T - 1, 0), 2), np.int32)
         box = np.zeros((max(T - 1, 0), 2, 6), np.float32)
-        st = dpcs_scene_export(self.handle, scene, codes.ctypes.data_as(_P), order.ctypes.data_as(_P),
+        st = self.lib.dpcs_scene_export(self.handle, scene, codes.ctypes.data_as(_P), order.ctypes.data_as(_P),
                                child.ctypes.data_as(_P), box.ctypes.data_as(_P))
         self.check(st, "scene_export")
         return codes, order, child, box
@@ -303,7 +352,7 @@ class Context:
         n = orig.shape[0]
         t = torch.empty(n, dtype=torch.float32, device=self.device)
         tri = torch.empty(n, dtype=torch.int32, device=self.device)
-        st = dpcs_trace(self.handle, scene, _ptr(orig, "orig", (n, 3), torch.float32, self.device),
+        st = self.lib.dpcs_trace(self.handle, scene, _ptr(orig, "orig", (n, 3), torch.float32, self.device),
                         _ptr(dir, "dir", (n, 3), torch.float32, self.device), n, _ptr(t, "t"), _ptr(tri, "tri"),
                         _stream(stream))
         self.check(st, "trace")
@@ -318,9 +367,10 @@ class Context:
         f32 = torch.float32
         if Ic is None:
             Ic = torch.empty((view.Hc, view.Wc, 3), dtype=f32, device=self.device)
-        st = dpcs_render(self.handle, scene, _ptr(albedo, "albedo", (Ht, Wt, 3), f32, self.device),
+        st = self.lib.dpcs_render(self.handle, scene, _ptr(albedo, "albedo", (Ht, Wt, 3), f32, self.device),
                          _ptr(rough, "rough", (Ht, Wt), f32, self.device), Ht, Wt,
-                         _ptr(Ip, "Ip", (view.Hp, view.Wp, 3), f32, self.device), view, params, int(spp),
+                         _ptr(Ip, "Ip", (view.Hp, view.Wp, 3), f32, self.device), ctypes.byref(view),
+                         ctypes.byref(params), int(spp),
                          int(bounces), int(seed) & (2**64 - 1),
                          _ptr(Ic, "Ic", (view.Hc, view.Wc, 3), f32, self.device),
                          _ptr(Ec, "Ec", (view.Hc, view.Wc, 3), f32, self.device, allow_none=True), _stream(stream))
@@ -335,10 +385,11 @@ class Context:
         Ht, Wt = albedo.shape[0], albedo.shape[1]
         f32 = torch.float32
         img = (view.Hc, view.Wc, 3)
-        st = dpcs_render_backward(
+        st = self.lib.dpcs_render_backward(
             self.handle, scene, _ptr(albedo, "albedo", (Ht, Wt, 3), f32, self.device),
             _ptr(rough, "rough", (Ht, Wt), f32, self.device), Ht, Wt,
-            _ptr(Ip, "Ip", (view.Hp, view.Wp, 3), f32, self.device), view, params, int(spp), int(bounces),
+            _ptr(Ip, "Ip", (view.Hp, view.Wp, 3), f32, self.device), ctypes.byref(view),
+                         ctypes.byref(params), int(spp), int(bounces),
             int(seed) & (2**64 - 1), _ptr(Ec, "Ec", img, f32, self.device), _ptr(Ic, "Ic", img, f32, self.device),
             _ptr(dIc, "dIc", img, f32, self.device),
             _ptr(dIp, "dIp", (view.Hp, view.Wp, 3), f32, self.device, allow_none=True),
@@ -352,7 +403,7 @@ class Context:
 
         f32 = torch.float32
         n = Ic.numel()
-        st = dpcs_l2_loss(self.handle, _ptr(Ic, "Ic", None, f32, self.device),
+        st = self.lib.dpcs_l2_loss(self.handle, _ptr(Ic, "Ic", None, f32, self.device),
                           _ptr(target, "target", tuple(Ic.shape), f32, self.device), n,
                           _ptr(dIc, "dIc", tuple(Ic.shape), f32, self.device),
                           _ptr(loss, "loss", (1,), f32, self.device), _stream(stream))
@@ -363,7 +414,7 @@ class Context:
 
         f32 = torch.float32
         shp = tuple(p.shape)
-        st = dpcs_adam(self.handle, _ptr(p, "p", None, f32, self.device), _ptr(g, "g", shp, f32, self.device),
+        st = self.lib.dpcs_adam(self.handle, _ptr(p, "p", None, f32, self.device), _ptr(g, "g", shp, f32, self.device),
                        _ptr(m, "m", shp, f32, self.device), _ptr(v, "v", shp, f32, self.device), p.numel(),
                        float(lr), float(beta1), float(beta2), float(eps), int(step), float(lo), float(hi),
                        _stream(stream))
