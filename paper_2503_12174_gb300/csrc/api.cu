@@ -17,7 +17,13 @@
 
 using namespace dpcs;
 
+#ifndef DPCS_MIN_SAMPLES_PER_LANE
+#define DPCS_MIN_SAMPLES_PER_LANE 1
+#endif
+
 namespace {
+
+constexpr int kMinSamplesPerLane = DPCS_MIN_SAMPLES_PER_LANE;
 
 struct Buf {
     void *p = nullptr;
@@ -209,8 +215,10 @@ dpcs_status prepare(dpcs_ctx *c, dpcs_scene scene, const float *albedo, const fl
     a.bounces = bounces;
     a.key0 = (uint32_t)(seed & 0xffffffffu);
     a.key1 = (uint32_t)(seed >> 32);
+    // lanes per pixel: the largest power of two L <= 32 with spp / L >= kMinSamplesPerLane
+    // (at least 1), so that each lane has several paths to regenerate into
     int l2 = 0;
-    while ((2 << l2) <= spp && l2 < 5) ++l2;  // lanes per pixel: largest power of two <= min(spp, 32)
+    while (l2 < 5 && (2 << l2) * kMinSamplesPerLane <= spp) ++l2;
     a.log2L = l2;
     a.status = c->status;
 #ifdef DPCS_COUNTERS

@@ -310,9 +310,11 @@ struct Hit {
     float t, u, v;
 };
 
-template <bool ANY>
+// any = true: stop at the first hit with t < tmax (shadow rays); false: closest
+// hit, ties in t to the lowest original index.  One loop serves both kinds so
+// that lanes tracing shadow and extension rays stay converged.
 __device__ __forceinline__ bool traverse(const float4 *__restrict__ nodes, const float4 *__restrict__ tris,
-                                         int32_t root, int32_t T, const Ray &ray, float tmax, Hit &h,
+                                         int32_t root, int32_t T, const Ray &ray, float tmax, bool any, Hit &h,
                                          unsigned *status, Cnt &cnt) {
     h.pos = -1;
     h.orig = 0x7fffffff;
@@ -361,14 +363,13 @@ __device__ __forceinline__ bool traverse(const float4 *__restrict__ nodes, const
             float t, u, v;
             if (tri_isect(ray, xyz(a), xyz(b), xyz(c), h.t, t, u, v)) {
                 const int orig = __float_as_int(a.w);
-                // closest: ties in t go to the lowest original index
-                if (t < h.t || (!ANY && t == h.t && orig < h.orig)) {
+                if (t < h.t || (!any && t == h.t && orig < h.orig)) {
                     h.pos = pos;
                     h.orig = orig;
                     h.t = t;
                     h.u = u;
                     h.v = v;
-                    if (ANY) return true;
+                    if (any) return true;
                 }
             }
         }
@@ -376,6 +377,92 @@ __device__ __forceinline__ bool traverse(const float4 *__restrict__ nodes, const
         node = stack[--sp];
     }
     return h.pos >= 0;
+}
+
+// Resumable traversal: the same node/leaf steps as traverse(), with its state
+// (current node, stack depth, visit count, best hit) kept by the caller so
+// that a lane can leave the loop and come back.  After at least one step the
+// loop yields (returns false) when fewer than `min_active` lanes of the warp
+// are still traversing, which lets the finished lanes shade and start new
+// rays instead of idling; it returns true once the ray is resolved.  Every
+// call advances the traversal by one or more steps, so a lane that keeps
+// calling it finishes its ray within the visit cap.
+struct Trav {
+    int node, sp, visits;
+    bool any;
+    Hit h;
+};
+
+__device__ __forceinline__ void trav_begin(Trav &st, int32_t root, float tmax, bool any) {
+    st.node = root;
+    st.sp = 0;
+    st.visits = 0;
+    st.any = any;
+    st.h.pos = -1;
+    st.h.orig = 0x7fffffff;
+    st.h.t = tmax;
+}
+
+__device__ __forceinline__ bool trav_resume(const float4 *__restrict__ nodes, const float4 *__restrict__ tris,
+                                            int32_t root, int32_t T, const Ray &ray, Trav &st, int *stack,
+                                            unsigned *status, Cnt &cnt, int min_active) {
+    if (root == kEmptyRoot) return true;
+    const int cap = 2 * T + 16;
+    bool first = true;
+    while (true) {
+        if (!first && __popc(__activemask()) < min_active) return false;
+        first = false;
+        if (++st.visits > cap) {
+            atomicOr(status, kStatusTraversalLimit);
+            st.h.pos = -1;
+            return true;
+        }
+        const int node = st.node;
+        if (node >= 0) {
+            cnt.add(kCntNode);
+            const float4 n0 = __ldg(nodes + 4 * node + 0);
+            const float4 n1 = __ldg(nodes + 4 * node + 1);
+            const float4 n2 = __ldg(nodes + 4 * node + 2);
+            const float4 n3 = __ldg(nodes + 4 * node + 3);
+            float tl, tr;
+            const bool hl = slab(ray, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, st.h.t, tl);
+            const bool hr = slab(ray, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, st.h.t, tr);
+            const int cl = __float_as_int(n3.x), cr = __float_as_int(n3.y);
+            if (hl && hr) {
+                if (st.sp >= kStack) {
+                    atomicOr(status, kStatusTraversalLimit);
+                    st.h.pos = -1;
+                    return true;
+                }
+                const bool lfirst = tl <= tr;
+                stack[st.sp++] = lfirst ? cr : cl;
+                st.node = lfirst ? cl : cr;
+                continue;
+            }
+            if (hl) { st.node = cl; continue; }
+            if (hr) { st.node = cr; continue; }
+        } else {
+            const int pos = ~node;
+            cnt.add(kCntTri);
+            const float4 a = __ldg(tris + 3 * pos + 0);
+            const float4 b = __ldg(tris + 3 * pos + 1);
+            const float4 c = __ldg(tris + 3 * pos + 2);
+            float t, u, v;
+            if (tri_isect(ray, xyz(a), xyz(b), xyz(c), st.h.t, t, u, v)) {
+                const int orig = __float_as_int(a.w);
+                if (t < st.h.t || (!st.any && t == st.h.t && orig < st.h.orig)) {
+                    st.h.pos = pos;
+                    st.h.orig = orig;
+                    st.h.t = t;
+                    st.h.u = u;
+                    st.h.v = v;
+                    if (st.any) return true;
+                }
+            }
+        }
+        if (st.sp == 0) return true;
+        st.node = stack[--st.sp];
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -395,122 +482,117 @@ struct VRec {
     unsigned unc;  // bit j: channel j not clipped
 };
 
-template <bool REC>
-__device__ __forceinline__ f3 trace_path(const RenderArgs &a, uint32_t pix, uint32_t s, VRec *rec, int &nv,
-                                         Cnt &cnt) {
+// first camera ray of sample s of pixel pix (Eq. 6 with the Eq. 4 box filter)
+__device__ __forceinline__ void camera_ray(const RenderArgs &a, uint32_t pix, uint32_t s, f3 &o, f3 &d) {
     float u[4];
-    nv = 0;
-    cnt.add(kCntPath);
     rand4(a.key0, a.key1, pix, s, 0u, u);
     const float fx = (float)(pix % (uint32_t)a.Wc) + (a.jitter ? u[0] : 0.5f);
     const float fy = (float)(pix / (uint32_t)a.Wc) + (a.jitter ? u[1] : 0.5f);
-    f3 o = mk3(0.f, 0.f, 0.f);
-    f3 d = normalize(mat3v(a.Kci, mk3(fx, fy, 1.0f)));
-    f3 beta = mk3(1.f, 1.f, 1.f);
-    f3 L = mk3(0.f, 0.f, 0.f);
+    o = mk3(0.f, 0.f, 0.f);
+    d = normalize(mat3v(a.Kci, mk3(fx, fy, 1.0f)));
+}
+
+// surface interaction at a hit: position, two-sided normal, textures
+struct Surf {
+    f3 x, n, wo, rho;
+    float rough;
+    Bilin tb;
+};
+__device__ __forceinline__ Surf surface_at(const RenderArgs &a, const Hit &h, f3 d) {
+    Surf S;
+    const float4 A = __ldg(a.tris + 3 * h.pos + 0);
+    const float4 E1 = __ldg(a.tris + 3 * h.pos + 1);
+    const float4 E2 = __ldg(a.tris + 3 * h.pos + 2);
+    const f3 e1 = xyz(E1), e2 = xyz(E2);
+    S.x = xyz(A) + e1 * h.u + e2 * h.v;
+    S.n = normalize(cross(e1, e2));
+    if (dot(S.n, d) > 0.0f) S.n = S.n * -1.0f;
+    const float2 t0 = __ldg(a.tuv + 3 * h.pos + 0), t1 = __ldg(a.tuv + 3 * h.pos + 1),
+                 t2 = __ldg(a.tuv + 3 * h.pos + 2);
+    const float w0 = 1.0f - h.u - h.v;
+    const float su = w0 * t0.x + h.u * t1.x + h.v * t2.x;
+    const float sv = w0 * t0.y + h.u * t1.y + h.v * t2.y;
+    S.tb = bilin_setup(su * (float)a.Wt, sv * (float)a.Ht, a.Wt, a.Ht);
+    const float4 tex = bilin_fetch(a.tex, S.tb, a.Wt, a.Ht);
+    S.rho = mk3(tex.x, tex.y, tex.z);
+    S.rough = tex.w;
+    S.wo = d * -1.0f;
+    return S;
+}
+
+// next-event estimation towards the pinhole projector (Eqs. 1, 2, 3, 6)
+// without the visibility test: the shadow ray and everything the
+// contribution needs.  false if the projector cannot light the point.
+struct Nee {
+    f3 so, sdir;
+    float smax;
+    Bilin pb;
+    float4 ep;
+    float G, sp, dsp;
+    f3 fp;
+};
+__device__ __forceinline__ bool nee_prepare(const RenderArgs &a, const Surf &S, Nee &N) {
     const f3 cp = mk3(a.cp[0], a.cp[1], a.cp[2]);
-    for (int b = 1; b <= a.bounces; ++b) {
-        Hit h;
-        const Ray ray = make_ray(o, d);
-        cnt.add(kCntRay);
-        if (!traverse<false>(a.nodes, a.tris, a.root, a.T, ray, INFINITY, h, a.status, cnt)) break;
-        cnt.add(kCntVert);
-        const float4 A = __ldg(a.tris + 3 * h.pos + 0);
-        const float4 E1 = __ldg(a.tris + 3 * h.pos + 1);
-        const float4 E2 = __ldg(a.tris + 3 * h.pos + 2);
-        const f3 e1 = xyz(E1), e2 = xyz(E2);
-        const f3 x = xyz(A) + e1 * h.u + e2 * h.v;
-        f3 n = normalize(cross(e1, e2));
-        if (dot(n, d) > 0.0f) n = n * -1.0f;
-        const float2 t0 = __ldg(a.tuv + 3 * h.pos + 0), t1 = __ldg(a.tuv + 3 * h.pos + 1),
-                     t2 = __ldg(a.tuv + 3 * h.pos + 2);
-        const float w0 = 1.0f - h.u - h.v;
-        const float su = w0 * t0.x + h.u * t1.x + h.v * t2.x;
-        const float sv = w0 * t0.y + h.u * t1.y + h.v * t2.y;
-        const Bilin tb = bilin_setup(su * (float)a.Wt, sv * (float)a.Ht, a.Wt, a.Ht);
-        const float4 tex = bilin_fetch(a.tex, tb, a.Wt, a.Ht);
-        const f3 rho = mk3(tex.x, tex.y, tex.z);
-        const float rough = tex.w;
-        const f3 wo = d * -1.0f;
-        VRec *R = REC ? &rec[nv] : nullptr;
-        if (REC) {
-            R->tx0 = tb.x0; R->ty0 = tb.y0; R->tfx = tb.fx; R->tfy = tb.fy;
-            R->beta[0] = beta.x; R->beta[1] = beta.y; R->beta[2] = beta.z;
-            R->rho[0] = rho.x; R->rho[1] = rho.y; R->rho[2] = rho.z;
-            R->G = 0.0f; R->cw = 0.0f; R->unc = 0u; R->sp = R->dsp = R->si = R->dsi = 0.0f;
-        }
-        ++nv;
+    const f3 X = mat3v(a.Rp, S.x) + mk3(a.tp[0], a.tp[1], a.tp[2]);
+    const f3 q = mat3v(a.Kp, X);
+    if (!(q.z > 0.0f && X.z > 0.0f)) return false;
+    const float up = q.x / q.z, vp = q.y / q.z;
+    if (!(up >= 0.0f && up < (float)a.Wp && vp >= 0.0f && vp < (float)a.Hp)) return false;
+    const f3 v = cp - S.x;
+    const float r2 = dot(v, v), dist = sqrtf(r2);
+    const f3 wp = v * (1.0f / dist);
+    const float cs = dot(S.n, wp);
+    if (!(cs > 0.0f)) return false;
+    const float cpz = X.z / sqrtf(dot(X, X));
+    N.so = S.x + S.n * kRayEps;
+    const f3 sv = cp - N.so;
+    const float sd = sqrtf(dot(sv, sv));
+    N.sdir = sv * (1.0f / sd);
+    N.smax = sd - kRayEps;
+    N.pb = bilin_setup(up, vp, a.Wp, a.Hp);
+    N.ep = bilin_fetch(a.Ep, N.pb, a.Wp, a.Hp);
+    N.G = a.k_proj * cpz * cs / r2;
+    N.sp = spec_eval(S.n, S.wo, wp, S.rough, a.ks, a.f0, N.dsp);
+    N.fp = mk3(S.rho.x * DPCS_INV_PI_F + N.sp, S.rho.y * DPCS_INV_PI_F + N.sp, S.rho.z * DPCS_INV_PI_F + N.sp);
+    return true;
+}
 
-        // next-event estimation to the projector (Eqs. 1, 2, 3, 6)
-        const f3 X = mat3v(a.Rp, x) + mk3(a.tp[0], a.tp[1], a.tp[2]);
-        const f3 q = mat3v(a.Kp, X);
-        if (q.z > 0.0f && X.z > 0.0f) {
-            const float up = q.x / q.z, vp = q.y / q.z;
-            if (up >= 0.0f && up < (float)a.Wp && vp >= 0.0f && vp < (float)a.Hp) {
-                const f3 v = cp - x;
-                const float r2 = dot(v, v), dist = sqrtf(r2);
-                const f3 wp = v * (1.0f / dist);
-                const float cs = dot(n, wp);
-                if (cs > 0.0f) {
-                    const float cpz = X.z / sqrtf(dot(X, X));
-                    const f3 so = x + n * kRayEps;
-                    const f3 sv = cp - so;
-                    const float sd = sqrtf(dot(sv, sv));
-                    Hit hs;
-                    const Ray sray = make_ray(so, sv * (1.0f / sd));
-                    cnt.add(kCntShadow);
-                    if (!traverse<true>(a.nodes, a.tris, a.root, a.T, sray, sd - kRayEps, hs, a.status, cnt)) {
-                        cnt.add(kCntLit);
-                        const Bilin pb = bilin_setup(up, vp, a.Wp, a.Hp);
-                        const float4 ep = bilin_fetch(a.Ep, pb, a.Wp, a.Hp);
-                        const float G = a.k_proj * cpz * cs / r2;
-                        float dsp;
-                        const float sp = spec_eval(n, wo, wp, rough, a.ks, a.f0, dsp);
-                        const f3 fp = mk3(rho.x * DPCS_INV_PI_F + sp, rho.y * DPCS_INV_PI_F + sp,
-                                          rho.z * DPCS_INV_PI_F + sp);
-                        f3 c = beta * fp * mk3(ep.x, ep.y, ep.z) * G;
-                        unsigned unc = 7u;
-                        if (a.clip > 0.0f) {
-                            if (c.x > a.clip) { c.x = a.clip; unc &= ~1u; }
-                            if (c.y > a.clip) { c.y = a.clip; unc &= ~2u; }
-                            if (c.z > a.clip) { c.z = a.clip; unc &= ~4u; }
-                        }
-                        L = L + c;
-                        if (REC) {
-                            R->px0 = pb.x0; R->py0 = pb.y0; R->pfx = pb.fx; R->pfy = pb.fy;
-                            R->Ep[0] = ep.x; R->Ep[1] = ep.y; R->Ep[2] = ep.z;
-                            R->G = G; R->sp = sp; R->dsp = dsp; R->unc = unc;
-                        }
-                    }
-                }
-            }
-        }
-        if (b == a.bounces) break;
-
-        // continuation: BSDF sampling, throughput, Russian roulette (Eq. 10)
-        rand4(a.key0, a.key1, pix, s, (uint32_t)b, u);
-        f3 wi;
-        if (!bsdf_sample(n, wo, rough, a.ks, u[0], u[1], u[2], wi)) break;
-        const float pdf = bsdf_pdf(n, wo, wi, rough, a.ks);
-        if (!(pdf > 0.0f)) break;
-        float qrr = 1.0f;
-        if (a.rr_start > 0 && b >= a.rr_start) {
-            if (u[3] >= a.rr_q) break;
-            qrr = a.rr_q;
-        }
-        float dsi;
-        const float si = spec_eval(n, wo, wi, rough, a.ks, a.f0, dsi);
-        const float cw = dot(n, wi) / (pdf * qrr);
-        const f3 fi = mk3(rho.x * DPCS_INV_PI_F + si, rho.y * DPCS_INV_PI_F + si, rho.z * DPCS_INV_PI_F + si);
-        beta = beta * fi * cw;
-        cnt.add(kCntCont);
-        if (REC) {
-            R->si = si; R->dsi = dsi; R->cw = cw;
-        }
-        o = x + n * kRayEps;
-        d = wi;
+// contribution beta f Ep G of a visible projector, clipped per channel (Eq. 12)
+__device__ __forceinline__ f3 nee_contrib(const RenderArgs &a, f3 beta, const Nee &N, unsigned &unc) {
+    f3 c = beta * N.fp * mk3(N.ep.x, N.ep.y, N.ep.z) * N.G;
+    unc = 7u;
+    if (a.clip > 0.0f) {
+        if (c.x > a.clip) { c.x = a.clip; unc &= ~1u; }
+        if (c.y > a.clip) { c.y = a.clip; unc &= ~2u; }
+        if (c.z > a.clip) { c.z = a.clip; unc &= ~4u; }
     }
-    return L;
+    return c;
+}
+
+// continuation from vertex b: BRDF sampling, throughput weight, Russian
+// roulette (Eq. 10).  false ends the path.
+struct Cont {
+    f3 wi, w;       // direction and throughput factor f cos / (pdf q)
+    float cw, si, dsi;
+};
+__device__ __forceinline__ bool continue_prepare(const RenderArgs &a, uint32_t pix, uint32_t s, int b,
+                                                 const Surf &S, Cont &C) {
+    float u[4];
+    rand4(a.key0, a.key1, pix, s, (uint32_t)b, u);
+    if (!bsdf_sample(S.n, S.wo, S.rough, a.ks, u[0], u[1], u[2], C.wi)) return false;
+    const float pdf = bsdf_pdf(S.n, S.wo, C.wi, S.rough, a.ks);
+    if (!(pdf > 0.0f)) return false;
+    float qrr = 1.0f;
+    if (a.rr_start > 0 && b >= a.rr_start) {
+        if (u[3] >= a.rr_q) return false;
+        qrr = a.rr_q;
+    }
+    C.si = spec_eval(S.n, S.wo, C.wi, S.rough, a.ks, a.f0, C.dsi);
+    C.cw = dot(S.n, C.wi) / (pdf * qrr);
+    const f3 fi = mk3(S.rho.x * DPCS_INV_PI_F + C.si, S.rho.y * DPCS_INV_PI_F + C.si,
+                      S.rho.z * DPCS_INV_PI_F + C.si);
+    C.w = fi * C.cw;
+    return true;
 }
 
 }  // namespace dpcs

@@ -26,6 +26,14 @@ namespace dpcs {
 namespace {
 
 constexpr int kRenderBlock = 128;
+#ifndef DPCS_YIELD_MIN
+// Traversal yields when fewer lanes of the warp are still traversing.  Off
+// (0): on GB300 yielding at 8..24 lanes cost 1.6-2x more than it recovered.
+#define DPCS_YIELD_MIN 0
+#endif
+#ifndef DPCS_RENDER_MINB
+#define DPCS_RENDER_MINB 8  // minimum resident blocks per SM requested from ptxas (64 registers)
+#endif
 
 __device__ __forceinline__ void atomic_add4(float4 *p, float4 v) {
 #if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 900
@@ -59,7 +67,14 @@ __device__ __forceinline__ float crf(float ec, float gain, float wb, float gamma
     return a > 0.0f ? powf(a, gamma) : 0.0f;
 }
 
-__global__ void __launch_bounds__(kRenderBlock) k_render(const RenderArgs a) {
+// Forward megakernel.  Every loop iteration traces exactly one ray per lane --
+// the extension ray of the current vertex or its shadow ray towards the
+// projector -- through the same traversal loop, then advances that lane's
+// path.  A lane whose path ends starts its next sample at once, so lanes of a
+// warp stay busy while their paths have different lengths (warp-level path
+// regeneration).  Each lane adds its paths in sample order; the per-vertex
+// arithmetic is the one of trace_path_rec.
+__global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB) k_render(const RenderArgs a) {
     const int L = 1 << a.log2L;
     const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t pix = gt >> a.log2L;
@@ -67,10 +82,103 @@ __global__ void __launch_bounds__(kRenderBlock) k_render(const RenderArgs a) {
     const int64_t npix = (int64_t)a.Hc * a.Wc;
     f3 sum = mk3(0.f, 0.f, 0.f);
     Cnt cnt;
-    if (pix < npix) {
-        for (int s = sl; s < a.spp; s += L) {
-            int nv;
-            sum = sum + trace_path<false>(a, (uint32_t)pix, (uint32_t)s, nullptr, nv, cnt);
+    int s = pix < npix ? sl : a.spp;
+    int b = 1;
+    bool shadow = false, has_ext = false, pending = false;
+    f3 beta = mk3(0.f, 0.f, 0.f), Lp = beta, c = beta, ed = beta;  // throughput, path sum, pending NEE, extension dir
+    Ray ray;
+    ray.o = ray.d = ray.inv = beta;
+    float tmax = INFINITY;
+    Trav st;
+    int stack[kStack];
+    if (s < a.spp && a.bounces > 0) {
+        f3 o, d;
+        camera_ray(a, (uint32_t)pix, (uint32_t)s, o, d);
+        ray = make_ray(o, d);
+        beta = mk3(1.f, 1.f, 1.f);
+        cnt.add(kCntPath);
+    } else {
+        s = a.spp;
+    }
+    // defensive bound on loop iterations: every iteration either advances a
+    // traversal by at least one node or consumes a finished ray
+    const int64_t max_iter = ((int64_t)(a.spp / L + 1) * (2 * a.bounces + 1)) * (2 * (int64_t)a.T + 18);
+    int64_t iter = 0;
+    while (s < a.spp) {
+        if (++iter > max_iter) {
+            atomicOr(a.status, kStatusTraversalLimit);
+            break;
+        }
+        // yield only while some live lane of the warp could take a new ray
+        const int alive = __popc(__activemask());
+        if (!pending) {
+            cnt.add(shadow ? kCntShadow : kCntRay);
+            trav_begin(st, a.root, shadow ? tmax : INFINITY, shadow);
+            pending = true;
+        }
+        if (!trav_resume(a.nodes, a.tris, a.root, a.T, ray, st, stack, a.status, cnt, min(DPCS_YIELD_MIN, alive)))
+            continue;
+        pending = false;
+        const bool hit = st.h.pos >= 0;
+        bool end = false;
+        if (shadow) {
+            if (!hit) {
+                Lp = Lp + c;
+                cnt.add(kCntLit);
+            }
+            shadow = false;
+            if (has_ext) {  // the extension ray starts where the shadow ray did (x + n eps)
+                ray = make_ray(ray.o, ed);
+                ++b;
+            } else {
+                end = true;
+            }
+        } else if (!hit) {
+            end = true;
+        } else {
+            cnt.add(kCntVert);
+            const Surf S = surface_at(a, st.h, ray.d);
+            Nee N;
+            const bool cand = nee_prepare(a, S, N);
+            if (cand) {
+                unsigned unc;
+                c = nee_contrib(a, beta, N, unc);
+            }
+            has_ext = false;
+            if (b < a.bounces) {
+                Cont C;
+                if (continue_prepare(a, (uint32_t)pix, (uint32_t)s, b, S, C)) {
+                    cnt.add(kCntCont);
+                    beta = beta * C.w;
+                    ed = C.wi;
+                    has_ext = true;
+                }
+            }
+            if (cand) {
+                shadow = true;
+                ray = make_ray(N.so, N.sdir);
+                tmax = N.smax;
+            } else if (has_ext) {
+                ray = make_ray(S.x + S.n * kRayEps, ed);
+                ++b;
+            } else {
+                end = true;
+            }
+        }
+        if (end) {
+            sum = sum + Lp;
+            s += L;
+            if (s < a.spp) {
+                f3 o, d;
+                camera_ray(a, (uint32_t)pix, (uint32_t)s, o, d);
+                ray = make_ray(o, d);
+                beta = mk3(1.f, 1.f, 1.f);
+                Lp = mk3(0.f, 0.f, 0.f);
+                b = 1;
+                shadow = false;
+                has_ext = false;
+                cnt.add(kCntPath);
+            }
         }
     }
     cnt.flush(a.counters);
@@ -101,7 +209,7 @@ __global__ void k_trace(const float4 *__restrict__ nodes, const float4 *__restri
     Hit h;
     Cnt cnt;
     const Ray r = make_ray(mk3(o[3 * i], o[3 * i + 1], o[3 * i + 2]), mk3(d[3 * i], d[3 * i + 1], d[3 * i + 2]));
-    const bool hit = traverse<false>(nodes, tris, root, T, r, INFINITY, h, status, cnt);
+    const bool hit = traverse(nodes, tris, root, T, r, INFINITY, false, h, status, cnt);
     tout[i] = hit ? h.t : INFINITY;
     triout[i] = hit ? h.orig : -1;
 }
@@ -154,7 +262,53 @@ __global__ void k_crf_backward(const float *__restrict__ dIc, const float *__res
     block_reduce_add<7>(v, acc + 4);
 }
 
-__global__ void __launch_bounds__(kRenderBlock) k_replay(const RenderArgs a) {
+// reverse sweep over the recorded vertices of one path: with A the
+// derivative of the path radiance with respect to the throughput entering
+// the next vertex (A_c = [lit] f(wp) Ep G + f(wi) cw A_{c+1}), scatter
+// dLoss/dEp, dLoss/dalbedo and dLoss/droughness into the accumulators.
+__device__ __forceinline__ void replay_sweep(const RenderArgs &a, const VRec *rec, int nv, const float gb_in[3]) {
+    float A[3] = {0.f, 0.f, 0.f};
+    for (int c = nv - 1; c >= 0; --c) {
+        const VRec &R = rec[c];
+        float ga[3], dEp[3];
+        float dr = 0.0f;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const float An = A[j];
+            const float gb = gb_in[j] * R.beta[j];
+            const bool lit = R.G > 0.0f && ((R.unc >> j) & 1u);
+            const float ln_e = lit ? R.Ep[j] * R.G : 0.0f;  // radiance / f along wp
+            const float cont = R.cw * An;                  // w / f times downstream A
+            const float fp = R.rho[j] * DPCS_INV_PI_F + R.sp;
+            const float fi = R.rho[j] * DPCS_INV_PI_F + R.si;
+            dEp[j] = lit ? gb * fp * R.G : 0.0f;
+            ga[j] = gb * (ln_e + cont) * DPCS_INV_PI_F;
+            dr += gb * (R.dsp * ln_e + R.dsi * cont);
+            A[j] = fp * ln_e + fi * cont;
+        }
+        int idx[4];
+        float w[4];
+        Bilin tb;
+        tb.x0 = R.tx0; tb.y0 = R.ty0; tb.fx = R.tfx; tb.fy = R.tfy;
+        bilin_taps(tb, a.Wt, a.Ht, idx, w);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            atomic_add4(a.dtex + idx[k], make_float4(ga[0] * w[k], ga[1] * w[k], ga[2] * w[k], dr * w[k]));
+        if (R.G > 0.0f && (dEp[0] != 0.0f || dEp[1] != 0.0f || dEp[2] != 0.0f)) {
+            Bilin pb;
+            pb.x0 = R.px0; pb.y0 = R.py0; pb.fx = R.pfx; pb.fy = R.pfy;
+            bilin_taps(pb, a.Wp, a.Hp, idx, w);
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                atomic_add4(a.dEp + idx[k], make_float4(dEp[0] * w[k], dEp[1] * w[k], dEp[2] * w[k], 0.0f));
+        }
+    }
+}
+
+// Path-replay adjoint.  Same thread mapping and flat loop as k_render: each
+// lane re-traces its paths from their Philox counters one ray per iteration,
+// records every vertex, and at the end of a path runs the reverse sweep.
+__global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB) k_replay(const RenderArgs a) {
     const int L = 1 << a.log2L;
     const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t pix = gt >> a.log2L;
@@ -162,49 +316,114 @@ __global__ void __launch_bounds__(kRenderBlock) k_replay(const RenderArgs a) {
     const int64_t npix = (int64_t)a.Hc * a.Wc;
     Cnt cnt;
     const float inv = 1.0f / (float)a.spp;
-    const bool live = pix < npix;
-    const f3 gbar = live ? mk3(a.gE[3 * pix] * inv, a.gE[3 * pix + 1] * inv, a.gE[3 * pix + 2] * inv)
-                         : mk3(0.f, 0.f, 0.f);
-    const float gb_in[3] = {gbar.x, gbar.y, gbar.z};
-    const bool any = gbar.x != 0.0f || gbar.y != 0.0f || gbar.z != 0.0f;
-    for (int s = sl; any && s < a.spp; s += L) {
-        VRec rec[DPCS_MAX_BOUNCES];
-        int nv;
-        trace_path<true>(a, (uint32_t)pix, (uint32_t)s, rec, nv, cnt);
-        float A[3] = {0.f, 0.f, 0.f};
-        for (int c = nv - 1; c >= 0; --c) {
-            const VRec &R = rec[c];
-            float ga[3], dEp[3], An[3];
-            float dr = 0.0f;
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                An[j] = A[j];
-                const float gb = gb_in[j] * R.beta[j];
-                const bool lit = R.G > 0.0f && ((R.unc >> j) & 1u);
-                const float ln_e = lit ? R.Ep[j] * R.G : 0.0f;  // radiance / f along wp
-                const float cont = R.cw * An[j];               // w / f times downstream A
-                const float fp = R.rho[j] * DPCS_INV_PI_F + R.sp;
-                const float fi = R.rho[j] * DPCS_INV_PI_F + R.si;
-                dEp[j] = lit ? gb * fp * R.G : 0.0f;
-                ga[j] = gb * (ln_e + cont) * DPCS_INV_PI_F;
-                dr += gb * (R.dsp * ln_e + R.dsi * cont);
-                A[j] = fp * ln_e + fi * cont;
+    float gb_in[3] = {0.f, 0.f, 0.f};
+    if (pix < npix) {
+        gb_in[0] = a.gE[3 * pix] * inv;
+        gb_in[1] = a.gE[3 * pix + 1] * inv;
+        gb_in[2] = a.gE[3 * pix + 2] * inv;
+    }
+    const bool any = gb_in[0] != 0.0f || gb_in[1] != 0.0f || gb_in[2] != 0.0f;
+    int s = (pix < npix && any) ? sl : a.spp;
+    int b = 1, nv = 0;
+    bool shadow = false, has_ext = false, pending = false;
+    f3 beta = mk3(0.f, 0.f, 0.f), ed = beta;
+    Ray ray;
+    ray.o = ray.d = ray.inv = beta;
+    float tmax = INFINITY;
+    Trav st;
+    int stack[kStack];
+    VRec rec[DPCS_MAX_BOUNCES];
+    if (s < a.spp && a.bounces > 0) {
+        f3 o, d;
+        camera_ray(a, (uint32_t)pix, (uint32_t)s, o, d);
+        ray = make_ray(o, d);
+        beta = mk3(1.f, 1.f, 1.f);
+        cnt.add(kCntPath);
+    } else {
+        s = a.spp;
+    }
+    const int64_t max_iter = ((int64_t)(a.spp / L + 1) * (2 * a.bounces + 1)) * (2 * (int64_t)a.T + 18);
+    int64_t iter = 0;
+    while (s < a.spp) {
+        if (++iter > max_iter) {
+            atomicOr(a.status, kStatusTraversalLimit);
+            break;
+        }
+        const int alive = __popc(__activemask());
+        if (!pending) {
+            cnt.add(shadow ? kCntShadow : kCntRay);
+            trav_begin(st, a.root, shadow ? tmax : INFINITY, shadow);
+            pending = true;
+        }
+        if (!trav_resume(a.nodes, a.tris, a.root, a.T, ray, st, stack, a.status, cnt, min(DPCS_YIELD_MIN, alive)))
+            continue;
+        pending = false;
+        const bool hit = st.h.pos >= 0;
+        bool end = false;
+        if (shadow) {
+            if (hit) rec[nv - 1].G = 0.0f;  // occluded: no projector light at this vertex
+            else cnt.add(kCntLit);
+            shadow = false;
+            if (has_ext) {
+                ray = make_ray(ray.o, ed);
+                ++b;
+            } else {
+                end = true;
             }
-            int idx[4];
-            float w[4];
-            Bilin tb;
-            tb.x0 = R.tx0; tb.y0 = R.ty0; tb.fx = R.tfx; tb.fy = R.tfy;
-            bilin_taps(tb, a.Wt, a.Ht, idx, w);
-#pragma unroll
-            for (int k = 0; k < 4; ++k)
-                atomic_add4(a.dtex + idx[k], make_float4(ga[0] * w[k], ga[1] * w[k], ga[2] * w[k], dr * w[k]));
-            if (R.G > 0.0f && (dEp[0] != 0.0f || dEp[1] != 0.0f || dEp[2] != 0.0f)) {
-                Bilin pb;
-                pb.x0 = R.px0; pb.y0 = R.py0; pb.fx = R.pfx; pb.fy = R.pfy;
-                bilin_taps(pb, a.Wp, a.Hp, idx, w);
-#pragma unroll
-                for (int k = 0; k < 4; ++k)
-                    atomic_add4(a.dEp + idx[k], make_float4(dEp[0] * w[k], dEp[1] * w[k], dEp[2] * w[k], 0.0f));
+        } else if (!hit) {
+            end = true;
+        } else {
+            cnt.add(kCntVert);
+            const Surf S = surface_at(a, st.h, ray.d);
+            VRec *R = &rec[nv++];
+            R->tx0 = S.tb.x0; R->ty0 = S.tb.y0; R->tfx = S.tb.fx; R->tfy = S.tb.fy;
+            R->beta[0] = beta.x; R->beta[1] = beta.y; R->beta[2] = beta.z;
+            R->rho[0] = S.rho.x; R->rho[1] = S.rho.y; R->rho[2] = S.rho.z;
+            R->G = 0.0f; R->cw = 0.0f; R->unc = 0u; R->sp = R->dsp = R->si = R->dsi = 0.0f;
+            Nee N;
+            const bool cand = nee_prepare(a, S, N);
+            if (cand) {
+                unsigned unc;
+                nee_contrib(a, beta, N, unc);
+                R->px0 = N.pb.x0; R->py0 = N.pb.y0; R->pfx = N.pb.fx; R->pfy = N.pb.fy;
+                R->Ep[0] = N.ep.x; R->Ep[1] = N.ep.y; R->Ep[2] = N.ep.z;
+                R->G = N.G; R->sp = N.sp; R->dsp = N.dsp; R->unc = unc;
+            }
+            has_ext = false;
+            if (b < a.bounces) {
+                Cont C;
+                if (continue_prepare(a, (uint32_t)pix, (uint32_t)s, b, S, C)) {
+                    cnt.add(kCntCont);
+                    beta = beta * C.w;
+                    ed = C.wi;
+                    has_ext = true;
+                    R->si = C.si; R->dsi = C.dsi; R->cw = C.cw;
+                }
+            }
+            if (cand) {
+                shadow = true;
+                ray = make_ray(N.so, N.sdir);
+                tmax = N.smax;
+            } else if (has_ext) {
+                ray = make_ray(S.x + S.n * kRayEps, ed);
+                ++b;
+            } else {
+                end = true;
+            }
+        }
+        if (end) {
+            replay_sweep(a, rec, nv, gb_in);
+            nv = 0;
+            s += L;
+            if (s < a.spp) {
+                f3 o, d;
+                camera_ray(a, (uint32_t)pix, (uint32_t)s, o, d);
+                ray = make_ray(o, d);
+                beta = mk3(1.f, 1.f, 1.f);
+                b = 1;
+                shadow = false;
+                has_ext = false;
+                cnt.add(kCntPath);
             }
         }
     }
