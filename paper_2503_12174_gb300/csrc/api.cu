@@ -565,3 +565,68 @@ dpcs_status dpcs_adam(dpcs_ctx *c, float *p, const float *g, float *m, float *v,
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Rendering without allocation.
+//
+// dpcs_render keeps the PRF-mapped projector image and the packed textures in
+// context scratch that grows with cudaMalloc on first use.  Callers that may
+// not allocate device memory at render time -- code recording a CUDA stream
+// capture (cudaMalloc is not permitted while a capture is active), host
+// applications that hand the GPU a fixed memory budget up front, real-time
+// loops that cannot absorb an allocation's latency or failure -- use
+// dpcs_render_noalloc instead.  Its scratch is the fixed array below,
+// compiled into the library: every GPU that loads the library holds these
+// 8 MiB until the process exits.  All calls share it, so calls that overlap
+// on the GPU (different streams, or different host threads) race.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int64_t kNoAllocTexels = int64_t(1) << 19;  // 524,288 float4 = 8 MiB
+static __device__ __align__(256) float4 g_noalloc_scratch[kNoAllocTexels];
+
+constexpr int kMaxDevices = 64;
+void *g_noalloc_ptr[kMaxDevices] = {nullptr};
+
+// device address of the array for the current device, resolved once per device
+dpcs_status noalloc_scratch(dpcs_ctx *c, float4 **out) {
+    if (c->device < 0 || c->device >= kMaxDevices) return fail(c, DPCS_ERR_INVALID_ARG, "device index too large");
+    if (!g_noalloc_ptr[c->device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) return cuda_fail(c, e, "cudaGetSymbolAddress(no-alloc scratch)");
+        g_noalloc_ptr[c->device] = p;
+    }
+    *out = (float4 *)g_noalloc_ptr[c->device];
+    return DPCS_OK;
+}
+
+}  // namespace
+
+extern "C" dpcs_status dpcs_render_noalloc(dpcs_ctx *c, dpcs_scene scene, const float *albedo, const float *rough,
+                                           int32_t Ht, int32_t Wt, const float *Ip, const dpcs_view *view,
+                                           const dpcs_params *params, int32_t spp, int32_t bounces, uint64_t seed,
+                                           float *Ic, float *Ec, void *stream) {
+    RenderArgs a;
+    Scene *sc = nullptr;
+    dpcs_status s = prepare(c, scene, albedo, rough, Ht, Wt, Ip, view, params, spp, bounces, seed, a, &sc);
+    if (s) return s;
+    if (!Ic) return fail(c, DPCS_ERR_INVALID_ARG, "null Ic");
+    const int64_t np = (int64_t)view->Hp * view->Wp, nt = (int64_t)Ht * Wt;
+    if (np + nt > kNoAllocTexels)
+        return fail(c, DPCS_ERR_INVALID_ARG,
+                    "dpcs_render_noalloc: Hp*Wp + Ht*Wt exceeds the fixed scratch of 524288 texels (8 MiB)");
+    if ((s = set_device(c))) return s;
+    float4 *scratch = nullptr;
+    if ((s = noalloc_scratch(c, &scratch))) return s;
+    float4 *ep4 = scratch, *tex4 = scratch + np;  // both fully overwritten below, nothing to clear
+    cudaStream_t st = (cudaStream_t)stream;
+    a.Ep = ep4;
+    a.tex = tex4;
+    a.Ic = Ic;
+    a.Ec = Ec;
+    int nl = launch_prf(Ip, np, params->gamma_p, params->gain_p, ep4, st);
+    nl += launch_pack_tex(albedo, rough, nt, tex4, st);
+    nl += launch_render(a, st);
+    return check_launch(c, nl, "render_noalloc");
+}

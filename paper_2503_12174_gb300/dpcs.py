@@ -31,7 +31,7 @@ EXPORTED = [
     "dpcs_create", "dpcs_destroy", "dpcs_last_error", "dpcs_sync", "dpcs_memory_used", "dpcs_launch_count",
     "dpcs_scene_upload", "dpcs_scene_free", "dpcs_scene_export", "dpcs_trace", "dpcs_render",
     "dpcs_render_backward", "dpcs_l2_loss", "dpcs_adam", "dpcs_timing_enable", "dpcs_timing_read",
-    "dpcs_counters_read",
+    "dpcs_counters_read", "dpcs_render_noalloc",
 ]
 
 
@@ -75,6 +75,9 @@ _SIGS = {
     "dpcs_render": (ctypes.c_int32, [_P, ctypes.c_uint64, _P, _P, ctypes.c_int32, ctypes.c_int32, _P,
                                      ctypes.POINTER(DpcsView), ctypes.POINTER(DpcsParams), ctypes.c_int32,
                                      ctypes.c_int32, ctypes.c_uint64, _P, _P, _P]),
+    "dpcs_render_noalloc": (ctypes.c_int32, [_P, ctypes.c_uint64, _P, _P, ctypes.c_int32, ctypes.c_int32, _P,
+                                             ctypes.POINTER(DpcsView), ctypes.POINTER(DpcsParams), ctypes.c_int32,
+                                             ctypes.c_int32, ctypes.c_uint64, _P, _P, _P]),
     "dpcs_render_backward": (ctypes.c_int32, [_P, ctypes.c_uint64, _P, _P, ctypes.c_int32, ctypes.c_int32, _P,
                                               ctypes.POINTER(DpcsView), ctypes.POINTER(DpcsParams), ctypes.c_int32,
                                               ctypes.c_int32, ctypes.c_uint64, _P, _P, _P, _P, _P, _P, _P, _P]),
@@ -206,6 +209,11 @@ def dpcs_trace(ctx, scene, orig, dir, n, t_out, tri_out, stream):
 def dpcs_render(ctx, scene, albedo, rough, Ht, Wt, Ip, view, params, spp, bounces, seed, Ic, Ec, stream):
     return load_library().dpcs_render(ctx, scene, albedo, rough, Ht, Wt, Ip, ctypes.byref(view),
                                       ctypes.byref(params), spp, bounces, seed, Ic, Ec, stream)
+
+
+def dpcs_render_noalloc(ctx, scene, albedo, rough, Ht, Wt, Ip, view, params, spp, bounces, seed, Ic, Ec, stream):
+    return load_library().dpcs_render_noalloc(ctx, scene, albedo, rough, Ht, Wt, Ip, ctypes.byref(view),
+                                              ctypes.byref(params), spp, bounces, seed, Ic, Ec, stream)
 
 
 def dpcs_render_backward(ctx, scene, albedo, rough, Ht, Wt, Ip, view, params, spp, bounces, seed, Ec, Ic, dIc,
