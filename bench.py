@@ -64,6 +64,9 @@ def _args():
     ap.add_argument("--fwd-bwd-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target oracle time for cpu_baseline")
+    ap.add_argument("--serve-requests", type=int, default=120, help="requests per serving run (0 = skip)")
+    ap.add_argument("--serve-rates", default="5,8,11", help="Poisson arrival rates (requests/s) of the load sweep")
+    ap.add_argument("--heightfield-steps", type=int, default=2, help="timed steps of the 200k-triangle workload (0 = skip)")
     return ap.parse_args()
 
 
@@ -380,6 +383,86 @@ def main():
                 "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 FLOP/FMA x {sm_max_mhz:.0f} MHz (max SM clock)",
                 "counts_per_launch": counts}
 
+    # ------------------------------------------------------------ large displaced surface (T = 199,712)
+    hf_out = None
+    if args.heightfield_steps > 0:
+        hs = scenes.heightfield(spp=256, seed=3000 + rank)
+        hh = ctx.upload(hs.verts, hs.tris, hs.uv)
+        halb = torch.from_numpy(hs.albedo).to(dev)
+        hrough = torch.from_numpy(hs.rough).to(dev)
+        hIp = torch.from_numpy(hs.Ip).to(dev)
+        hview, hprm = dpcs.view_of(hs), dpcs.make_params(hs.params)
+        hIc = torch.empty((hs.Hc, hs.Wc, 3), device=dev)
+        hEc = torch.empty_like(hIc)
+        hdIc = torch.randn_like(hIc)
+        hG = torch.zeros_like(hIp)
+
+        def hf_fwd(spp):
+            ctx.render(hh, halb, hrough, hIp, hview, hprm, spp, hs.bounces, hs.seed, Ic=hIc, Ec=hEc)
+
+        def hf_fb(spp):
+            hf_fwd(spp)
+            ctx.render_backward(hh, halb, hrough, hIp, hview, hprm, spp, hs.bounces, hs.seed, hEc, hIc, hdIc, dIp=hG)
+
+        res = {}
+        for name, fn, spp in (("fwd", hf_fwd, 256), ("fwd_bwd", hf_fb, 32)):
+            fn(spp)
+            torch.cuda.synchronize()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.heightfield_steps)]
+            barrier()
+            for k in range(args.heightfield_steps):
+                flush(k)
+                ev[k][0].record(stream)
+                fn(spp)
+                ev[k][1].record(stream)
+            barrier()
+            ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev)) / args.heightfield_steps
+            res[name] = {"value": hs.Hc * hs.Wc * spp * ws / (ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": ms,
+                         "spp": spp}
+        ctx.sync()
+        ctx.free(hh)
+        hf_out = {"workload": f"heightfield T={hs.T}, camera {hs.Hc}x{hs.Wc}, projector {hs.Wp}x{hs.Hp}, "
+                              f"textures 512x512, {hs.bounces} bounces, Russian roulette from vertex 2 (q=0.75)",
+                  **res}
+
+    # ------------------------------------------------------------ serving vs one call per request
+    serving_out = None
+    if args.serve_requests > 0:
+        from paper_2503_12174_gb300 import serving
+
+        scs = serving.resident_scenes()
+        gs = serving.GpuScenes(ctx, scs)
+        host = serving.HostData(scs)
+        warm = serving.make_workload(6, rate=0.0, seed=99, sides=(128, 256), spp_range=(16, 32), comp_steps=2)
+        serving.run_server(ctx, gs, host, warm)
+        serving.run_per_call(ctx, gs, host, warm)
+        keep = ("requests_per_s", "relight_p50_ms", "relight_p99_ms", "compensation_p50_ms", "compensation_p99_ms",
+                "samples_per_s_M", "wall_s")
+        sweep = []
+        for rate in [float(x) for x in args.serve_rates.split(",") if x]:
+            wl = serving.make_workload(args.serve_requests, rate=rate, seed=100 + rank)
+            srv = serving.run_server(ctx, gs, host, wl)
+            per = serving.run_per_call(ctx, gs, host, wl)
+            sweep.append({"offered_rate_per_s": rate, "server": {k: srv[k] for k in keep},
+                          "per_call": {k: per[k] for k in keep}, "server_iterations": srv["server"]["iterations"],
+                          "server_memory_high_water_bytes": srv["server"]["memory_high_water"]})
+        sat = serving.make_workload(args.serve_requests, rate=0.0, seed=200 + rank)
+        srv_sat = serving.run_server(ctx, gs, host, sat)
+        per_sat = serving.run_per_call(ctx, gs, host, sat)
+        for hh in gs.handles:
+            ctx.free(hh)
+        serving_out = {
+            "workload": f"{args.serve_requests} requests per run over 3 resident scenes (plane, corner256, corner512); "
+                        "camera side in {128..1024 step 64}, spp log-uniform 16-256; 90% relight, "
+                        "10% compensation (50 Adam steps, 16 spp); Poisson arrivals",
+            "load_sweep": sweep,
+            "saturated": {"server_requests_per_s": srv_sat["requests_per_s"],
+                          "per_call_requests_per_s": per_sat["requests_per_s"],
+                          "server_relight_p99_ms": srv_sat["relight_p99_ms"],
+                          "per_call_relight_p99_ms": per_sat["relight_p99_ms"]},
+        }
+
     # ------------------------------------------------------------ CPU baseline
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -404,6 +487,8 @@ def main():
                         "replay_kernel_ms": replay_ms / max(replay_n, 1),
                         "render_kernel_ms": crender_ms / max(crender_n, 1)},
             "roofline": roof,
+            "heightfield": hf_out,
+            "serving": serving_out,
             "cpu_baseline": cpu,
             "clocks": clk,
             "gpu_launches": int(launches),

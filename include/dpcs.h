@@ -256,6 +256,91 @@ dpcs_status dpcs_l2_loss(dpcs_ctx *ctx, const float *Ic, const float *target, in
 dpcs_status dpcs_adam(dpcs_ctx *ctx, float *p, const float *g, float *m, float *v, int64_t n, float lr, float beta1,
                       float beta2, float eps, int32_t step, float lo, float hi, void *stream);
 
+/* ------------------------------------------------------------------------ */
+/* Serving: continuous batching of relighting and compensation requests      */
+/* ------------------------------------------------------------------------ */
+/*
+ * The paper's two downstream tasks -- ProCams relighting, Ic' = R(Ip', theta)
+ * (Sec. 3.2, Eq. 7) and projector compensation, Ip* = argmin |R(Ip) - Ic|
+ * (Eq. 13) -- served as requests on resident scenes.  The paper runs them
+ * one at a time; batching them is this library's addition.
+ *
+ * A server owns a CUDA stream and device memory for admitted requests.  Each
+ * dpcs_serve_step is one scheduler iteration: it retires finished work,
+ * admits waiting requests (FIFO) while their device memory fits the HBM
+ * budget and fewer than max_active are admitted, and launches one batched
+ * render in which every active relighting request gets up to
+ * quantum_samples of camera samples (fewest remaining first) and every
+ * active compensation request renders its full image; the compensation
+ * requests' loss, path-replay adjoint and Adam step follow on the same
+ * stream.  Requests that arrive while others run join at the next
+ * iteration.  A pixel's result is computed exactly as dpcs_render computes
+ * it, whatever else is in the batch.  Waits are bounded; nothing spins on
+ * the GPU.  A server is not thread safe; use it from one host thread.
+ */
+typedef struct dpcs_server dpcs_server;
+
+typedef struct dpcs_serve_config {
+    size_t hbm_budget_bytes;        /* device memory for admitted requests (0 = no limit) */
+    int32_t max_active;             /* most requests admitted at once (1..1024) */
+    int32_t max_inflight;           /* batched iterations queued on the GPU at once (1..4) */
+    int64_t samples_per_iteration;  /* camera samples one batched launch may take */
+    int64_t quantum_samples;        /* samples a relighting request gets per iteration */
+} dpcs_serve_config;
+
+#define DPCS_REQ_RELIGHT 0
+#define DPCS_REQ_COMPENSATE 1
+
+#define DPCS_REQ_WAITING 0
+#define DPCS_REQ_ACTIVE 1
+#define DPCS_REQ_DONE 2
+#define DPCS_REQ_FAILED (-1)
+
+typedef struct dpcs_request {
+    int32_t kind;          /* DPCS_REQ_RELIGHT or DPCS_REQ_COMPENSATE */
+    int32_t scene;         /* slot returned by dpcs_serve_add_scene */
+    int32_t Hc, Wc;        /* camera image; the scene camera's field of view is kept */
+    int32_t spp;           /* samples per pixel */
+    uint64_t seed;         /* Philox key; compensation step k uses seed + k */
+    int32_t steps;         /* compensation: Adam steps (Eq. 13) */
+    float lr;              /* compensation: Adam learning rate */
+    const float *Ip;       /* host, Hp x Wp x 3: the image to relight / the compensation start */
+    const float *target;   /* host, Hc x Wc x 3: compensation target Ic (NULL for relighting) */
+    float *Ic_out;         /* host, Hc x Wc x 3: rendered image (compensation: of the last step) */
+    float *Ip_out;         /* host, Hp x Wp x 3: compensated projector image, or NULL */
+} dpcs_request;
+
+typedef struct dpcs_serve_stats {
+    int64_t submitted, completed, failed, waiting, active;
+    int64_t iterations, launches;
+    size_t memory_used, memory_high_water;
+} dpcs_serve_stats;
+
+/* Create a server on ctx's device.  The host buffers of a request must stay
+ * valid until it is done. */
+dpcs_status dpcs_serve_create(dpcs_ctx *ctx, const dpcs_serve_config *cfg, dpcs_server **out);
+/* Wait (bounded by the GPU work queued) and free everything. */
+dpcs_status dpcs_serve_destroy(dpcs_server *srv);
+/* Register a resident scene with its textures (dev, caller-owned, kept
+ * unchanged while the server lives), the scene's camera/projector and
+ * parameters; *slot receives its index. */
+dpcs_status dpcs_serve_add_scene(dpcs_server *srv, dpcs_scene scene, const float *albedo, const float *rough,
+                                 int32_t Ht, int32_t Wt, const dpcs_view *view, const dpcs_params *params,
+                                 int32_t bounces, int32_t *slot);
+/* Queue a request; *id receives its handle.  Sizes are validated here. */
+dpcs_status dpcs_serve_submit(dpcs_server *srv, const dpcs_request *req, uint64_t *id);
+/* One scheduler iteration (see above); *completed (may be NULL) receives the
+ * number of requests that finished during it.  Returns without waiting
+ * unless max_inflight iterations are already queued on the GPU. */
+dpcs_status dpcs_serve_step(dpcs_server *srv, int32_t *completed);
+/* State of request id (DPCS_REQ_*) and, once done, its latency in ms from
+ * submission to the moment the server saw its result in host memory. */
+dpcs_status dpcs_serve_query(dpcs_server *srv, uint64_t id, int32_t *state, double *latency_ms);
+/* Step until no request is waiting or active, for at most timeout_s seconds
+ * (DPCS_ERR_TIMEOUT after that). */
+dpcs_status dpcs_serve_drain(dpcs_server *srv, double timeout_s);
+dpcs_status dpcs_serve_stats_get(dpcs_server *srv, dpcs_serve_stats *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -274,6 +274,30 @@ __device__ __forceinline__ Ray make_ray(f3 o, f3 d) {
     return r;
 }
 
+#ifndef DPCS_SLAB_MINMAX3
+#define DPCS_SLAB_MINMAX3 1  // three-input min/max (PTX ISA 8.8, sm_100+)
+#endif
+
+__device__ __forceinline__ float fmax3f(float a, float b, float c) {
+#if DPCS_SLAB_MINMAX3
+    float d;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+#else
+    return fmaxf(fmaxf(a, b), c);
+#endif
+}
+
+__device__ __forceinline__ float fmin3f(float a, float b, float c) {
+#if DPCS_SLAB_MINMAX3
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+#else
+    return fminf(fminf(a, b), c);
+#endif
+}
+
 // slab test; the far bound is widened by a few ulps (Ize, JCGT 2013) so that
 // flat boxes of axis-aligned walls are never missed by rounding
 __device__ __forceinline__ bool slab(const Ray &r, float lx, float hx, float ly, float hy, float lz, float hz,
@@ -281,8 +305,8 @@ __device__ __forceinline__ bool slab(const Ray &r, float lx, float hx, float ly,
     const float tx0 = (lx - r.o.x) * r.inv.x, tx1 = (hx - r.o.x) * r.inv.x;
     const float ty0 = (ly - r.o.y) * r.inv.y, ty1 = (hy - r.o.y) * r.inv.y;
     const float tz0 = (lz - r.o.z) * r.inv.z, tz1 = (hz - r.o.z) * r.inv.z;
-    const float tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.0f));
-    const float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fminf(fmaxf(tz0, tz1), tmax));
+    const float tn = fmax3f(fminf(tx0, tx1), fminf(ty0, ty1), fmaxf(fminf(tz0, tz1), 0.0f));
+    const float tf = fmin3f(fmaxf(tx0, tx1), fmaxf(ty0, ty1), fminf(fmaxf(tz0, tz1), tmax));
     tnear = tn;
     return tn <= tf * 1.0000004f;
 }
@@ -310,83 +334,20 @@ struct Hit {
     float t, u, v;
 };
 
-// any = true: stop at the first hit with t < tmax (shadow rays); false: closest
-// hit, ties in t to the lowest original index.  One loop serves both kinds so
-// that lanes tracing shadow and extension rays stay converged.
-__device__ __forceinline__ bool traverse(const float4 *__restrict__ nodes, const float4 *__restrict__ tris,
-                                         int32_t root, int32_t T, const Ray &ray, float tmax, bool any, Hit &h,
-                                         unsigned *status, Cnt &cnt) {
-    h.pos = -1;
-    h.orig = 0x7fffffff;
-    h.t = tmax;
-    if (root == kEmptyRoot) return false;
-    int stack[kStack];
-    int sp = 0;
-    int node = root;
-    int visits = 0;
-    const int cap = 2 * T + 16;
-    while (true) {
-        if (++visits > cap) {
-            atomicOr(status, kStatusTraversalLimit);
-            h.pos = -1;
-            return false;
-        }
-        if (node >= 0) {
-            cnt.add(kCntNode);
-            const float4 n0 = __ldg(nodes + 4 * node + 0);
-            const float4 n1 = __ldg(nodes + 4 * node + 1);
-            const float4 n2 = __ldg(nodes + 4 * node + 2);
-            const float4 n3 = __ldg(nodes + 4 * node + 3);
-            float tl, tr;
-            const bool hl = slab(ray, n0.x, n0.y, n0.z, n0.w, n2.x, n2.y, h.t, tl);
-            const bool hr = slab(ray, n1.x, n1.y, n1.z, n1.w, n2.z, n2.w, h.t, tr);
-            const int cl = __float_as_int(n3.x), cr = __float_as_int(n3.y);
-            if (hl && hr) {
-                if (sp >= kStack) {
-                    atomicOr(status, kStatusTraversalLimit);
-                    h.pos = -1;
-                    return false;
-                }
-                const bool lfirst = tl <= tr;
-                stack[sp++] = lfirst ? cr : cl;
-                node = lfirst ? cl : cr;
-                continue;
-            }
-            if (hl) { node = cl; continue; }
-            if (hr) { node = cr; continue; }
-        } else {
-            const int pos = ~node;
-            cnt.add(kCntTri);
-            const float4 a = __ldg(tris + 3 * pos + 0);
-            const float4 b = __ldg(tris + 3 * pos + 1);
-            const float4 c = __ldg(tris + 3 * pos + 2);
-            float t, u, v;
-            if (tri_isect(ray, xyz(a), xyz(b), xyz(c), h.t, t, u, v)) {
-                const int orig = __float_as_int(a.w);
-                if (t < h.t || (!any && t == h.t && orig < h.orig)) {
-                    h.pos = pos;
-                    h.orig = orig;
-                    h.t = t;
-                    h.u = u;
-                    h.v = v;
-                    if (any) return true;
-                }
-            }
-        }
-        if (sp == 0) break;
-        node = stack[--sp];
-    }
-    return h.pos >= 0;
-}
-
-// Resumable traversal: the same node/leaf steps as traverse(), with its state
-// (current node, stack depth, visit count, best hit) kept by the caller so
-// that a lane can leave the loop and come back.  After at least one step the
-// loop yields (returns false) when fewer than `min_active` lanes of the warp
-// are still traversing, which lets the finished lanes shade and start new
-// rays instead of idling; it returns true once the ray is resolved.  Every
-// call advances the traversal by one or more steps, so a lane that keeps
-// calling it finishes its ray within the visit cap.
+// Traversal of the 4-wide BVH.  A node holds the boxes of up to four
+// children (SoA, one 128-byte line) and their references (>= 0 node, < 0
+// leaf ~position, kEmptyChild).  The hit children are ordered near to far by
+// a 5-comparator sorting network; the nearest is visited next and the others
+// are pushed farthest first.  any = true stops at the first hit with
+// t < tmax (shadow rays); otherwise the closest hit is kept, ties in t to the
+// lowest original triangle index.
+//
+// The traversal is resumable: its state (node, stack depth, visit count, best
+// hit) lives in Trav, kept by the caller.  After at least one step the loop
+// yields (returns false) when fewer than `min_active` lanes of the warp are
+// still traversing; it returns true once the ray is resolved.  Every call
+// advances by one or more steps, so a lane that keeps calling it finishes its
+// ray within the visit cap.
 struct Trav {
     int node, sp, visits;
     bool any;
@@ -403,14 +364,95 @@ __device__ __forceinline__ void trav_begin(Trav &st, int32_t root, float tmax, b
     st.h.t = tmax;
 }
 
-__device__ __forceinline__ bool trav_resume(const float4 *__restrict__ nodes, const float4 *__restrict__ tris,
+__device__ __forceinline__ void cswap(float &ta, int &ra, float &tb, int &rb) {
+    const bool sw = tb < ta;
+    const float t = sw ? tb : ta;
+    const int r = sw ? rb : ra;
+    tb = sw ? ta : tb;
+    rb = sw ? ra : rb;
+    ta = t;
+    ra = r;
+}
+
+__device__ __forceinline__ bool trav_resume4(const float4 *__restrict__ nodes, const float4 *__restrict__ tris,
                                             int32_t root, int32_t T, const Ray &ray, Trav &st, int *stack,
                                             unsigned *status, Cnt &cnt, int min_active) {
     if (root == kEmptyRoot) return true;
     const int cap = 2 * T + 16;
     bool first = true;
     while (true) {
-        if (!first && __popc(__activemask()) < min_active) return false;
+        if (min_active > 0 && !first && __popc(__activemask()) < min_active) return false;
+        first = false;
+        if (++st.visits > cap) {
+            atomicOr(status, kStatusTraversalLimit);
+            st.h.pos = -1;
+            return true;
+        }
+        const int node = st.node;
+        if (node >= 0) {
+            cnt.add(kCntNode);
+            const float4 *nd = nodes + 8 * (size_t)node;
+            const float4 lx = __ldg(nd + 0), hx = __ldg(nd + 1), ly = __ldg(nd + 2), hy = __ldg(nd + 3);
+            const float4 lz = __ldg(nd + 4), hz = __ldg(nd + 5), rf = __ldg(nd + 6);
+            float t0, t1, t2, t3;
+            int r0 = __float_as_int(rf.x), r1 = __float_as_int(rf.y), r2 = __float_as_int(rf.z),
+                r3 = __float_as_int(rf.w);
+            const float tcut = st.h.t;
+            if (!(slab(ray, lx.x, hx.x, ly.x, hy.x, lz.x, hz.x, tcut, t0) && r0 != kEmptyChild)) t0 = INFINITY;
+            if (!(slab(ray, lx.y, hx.y, ly.y, hy.y, lz.y, hz.y, tcut, t1) && r1 != kEmptyChild)) t1 = INFINITY;
+            if (!(slab(ray, lx.z, hx.z, ly.z, hy.z, lz.z, hz.z, tcut, t2) && r2 != kEmptyChild)) t2 = INFINITY;
+            if (!(slab(ray, lx.w, hx.w, ly.w, hy.w, lz.w, hz.w, tcut, t3) && r3 != kEmptyChild)) t3 = INFINITY;
+            cswap(t0, r0, t1, r1);
+            cswap(t2, r2, t3, r3);
+            cswap(t0, r0, t2, r2);
+            cswap(t1, r1, t3, r3);
+            cswap(t1, r1, t2, r2);
+            const int nh = (t0 < INFINITY) + (t1 < INFINITY) + (t2 < INFINITY) + (t3 < INFINITY);
+            if (nh > 0) {
+                if (st.sp + nh - 1 > kStack) {
+                    atomicOr(status, kStatusTraversalLimit);
+                    st.h.pos = -1;
+                    return true;
+                }
+                if (nh == 4) stack[st.sp++] = r3;
+                if (nh >= 3) stack[st.sp++] = r2;
+                if (nh >= 2) stack[st.sp++] = r1;
+                st.node = r0;
+                continue;
+            }
+        } else {
+            const int pos = ~node;
+            cnt.add(kCntTri);
+            const float4 a = __ldg(tris + 3 * pos + 0);
+            const float4 b = __ldg(tris + 3 * pos + 1);
+            const float4 c = __ldg(tris + 3 * pos + 2);
+            float t, u, v;
+            if (tri_isect(ray, xyz(a), xyz(b), xyz(c), st.h.t, t, u, v)) {
+                const int orig = __float_as_int(a.w);
+                if (t < st.h.t || (!st.any && t == st.h.t && orig < st.h.orig)) {
+                    st.h.pos = pos;
+                    st.h.orig = orig;
+                    st.h.t = t;
+                    st.h.u = u;
+                    st.h.v = v;
+                    if (st.any) return true;
+                }
+            }
+        }
+        if (st.sp == 0) return true;
+        st.node = stack[--st.sp];
+    }
+}
+
+// binary-node steps: 64-byte nodes with two child boxes
+__device__ __forceinline__ bool trav_resume2(const float4 *__restrict__ nodes, const float4 *__restrict__ tris,
+                                            int32_t root, int32_t T, const Ray &ray, Trav &st, int *stack,
+                                            unsigned *status, Cnt &cnt, int min_active) {
+    if (root == kEmptyRoot) return true;
+    const int cap = 2 * T + 16;
+    bool first = true;
+    while (true) {
+        if (min_active > 0 && !first && __popc(__activemask()) < min_active) return false;
         first = false;
         if (++st.visits > cap) {
             atomicOr(status, kStatusTraversalLimit);
@@ -463,6 +505,36 @@ __device__ __forceinline__ bool trav_resume(const float4 *__restrict__ nodes, co
         if (st.sp == 0) return true;
         st.node = stack[--st.sp];
     }
+}
+
+
+#ifndef DPCS_BVH_WIDTH
+#define DPCS_BVH_WIDTH 2  // traversal of the binary LBVH (2) or of its 4-wide collapse (4)
+#endif
+
+__device__ __forceinline__ bool trav_resume(const float4 *__restrict__ nodes2, const float4 *__restrict__ nodes4,
+                                            const float4 *__restrict__ tris, int32_t root2, int32_t root4, int32_t T,
+                                            const Ray &ray, Trav &st, int *stack, unsigned *status, Cnt &cnt,
+                                            int min_active) {
+#if DPCS_BVH_WIDTH == 4
+    (void)nodes2; (void)root2;
+    return trav_resume4(nodes4, tris, root4, T, ray, st, stack, status, cnt, min_active);
+#else
+    (void)nodes4; (void)root4;
+    return trav_resume2(nodes2, tris, root2, T, ray, st, stack, status, cnt, min_active);
+#endif
+}
+
+// traversal to completion (no yielding)
+__device__ __forceinline__ bool traverse(const float4 *__restrict__ nodes2, const float4 *__restrict__ nodes4,
+                                         const float4 *__restrict__ tris, int32_t root2, int32_t root4, int32_t T,
+                                         const Ray &ray, float tmax, bool any, Hit &h, unsigned *status, Cnt &cnt) {
+    Trav st;
+    int stack[kStack];
+    trav_begin(st, DPCS_BVH_WIDTH == 4 ? root4 : root2, tmax, any);
+    trav_resume(nodes2, nodes4, tris, root2, root4, T, ray, st, stack, status, cnt, 0);
+    h = st.h;
+    return h.pos >= 0;
 }
 
 // ---------------------------------------------------------------------------

@@ -27,16 +27,23 @@ struct Scene {
     float2 *tuv = nullptr;     // 3 x T
     uint32_t *codes = nullptr; // sorted Morton codes, T
     int32_t *order = nullptr;  // original triangle of each sorted position, T
+    // 4-wide BVH collapsed from the binary tree (the one traversal uses):
+    // 8 float4 per node = lo.x[4], hi.x[4], lo.y[4], hi.y[4], lo.z[4],
+    // hi.z[4], child refs[4] (>= 0 node, < 0 leaf ~pos, kEmptyChild), pad
+    float4 *nodes4 = nullptr;  // 8 x (T-1) at most
+    int32_t root4 = 0;
     size_t bytes = 0;
 };
 constexpr int32_t kEmptyRoot = (int32_t)0x80000000;
+constexpr int32_t kEmptyChild = 0x7fffffff;
 
 // Kernel arguments of one render / replay launch (passed by value).
 struct RenderArgs {
-    const float4 *nodes;
+    const float4 *nodes;   // binary LBVH nodes
+    const float4 *nodes4;  // its 4-wide collapse
     const float4 *tris;
     const float2 *tuv;
-    int32_t root;
+    int32_t root, root4;   // root references of the two trees
     int32_t T;
     const float4 *tex;   // Ht x Wt: albedo rgb, roughness
     int32_t Ht, Wt;
@@ -61,6 +68,15 @@ struct RenderArgs {
     unsigned long long *counters;  // DPCS_COUNTERS build only (8 totals)
 };
 
+// One pixel range of one request in a batched render launch.
+struct BatchSeg {
+    int64_t vb_begin;   // first virtual block of the segment
+    int64_t pix_begin;  // first pixel (y * Wc + x) of the range
+    int64_t npix;       // pixels in the range
+    int32_t slot;       // index of the request's RenderArgs
+    int32_t pad;
+};
+
 // Launchers (render.cu, lbvh.cu, optim.cu).  Each returns the number of
 // kernels it enqueued, or a negative dpcs_status.
 int launch_lbvh_build(const float *d_verts, int32_t V, const int32_t *d_tris, int32_t T, const float *d_uv,
@@ -70,6 +86,10 @@ size_t lbvh_scratch_bytes(int32_t T);
 int launch_prf(const float *Ip, int64_t ntex, const float gamma_p[3], float gain_p, float4 *Ep, cudaStream_t st);
 int launch_pack_tex(const float *albedo, const float *rough, int64_t ntex, float4 *tex, cudaStream_t st);
 int launch_render(const RenderArgs &a, cudaStream_t st);
+int launch_render_batch(const RenderArgs *descs, const BatchSeg *segs, int nseg, int64_t total_vb,
+                        unsigned long long *counter, int grid, cudaStream_t st);
+int render_batch_grid(int device);
+int64_t render_batch_vblocks(int64_t npix, int log2L);
 int launch_trace(const Scene &sc, const float *o, const float *d, int64_t n, float *t, int32_t *tri,
                  unsigned *status, cudaStream_t st);
 int launch_crf_backward(const float *dIc, const float *Ec, const float *Ic, int64_t npix, const float gamma_c[3],
@@ -85,5 +105,13 @@ int launch_l2_loss(const float *Ic, const float *target, int64_t n, float *dIc, 
 int l2_partial_slots();
 int launch_adam(float *p, const float *g, float *m, float *v, int64_t n, float lr, float b1, float b2, float eps,
                 int32_t step, float lo, float hi, cudaStream_t st);
+
+// context accessors (api.cu) for the serving loop
+dpcs_status ctx_render_args(dpcs_ctx *c, dpcs_scene scene, const float *albedo, const float *rough, int32_t Ht,
+                            int32_t Wt, const float *Ip, const dpcs_view *view, const dpcs_params *params,
+                            int32_t spp, int32_t bounces, uint64_t seed, RenderArgs &a);
+int ctx_device(const dpcs_ctx *c);
+void ctx_add_launches(dpcs_ctx *c, int n);
+dpcs_status ctx_fail(dpcs_ctx *c, dpcs_status code, const char *msg);
 
 }  // namespace dpcs

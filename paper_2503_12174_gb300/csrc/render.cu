@@ -74,15 +74,16 @@ __device__ __forceinline__ float crf(float ec, float gain, float wb, float gamma
 // warp stay busy while their paths have different lengths (warp-level path
 // regeneration).  Each lane adds its paths in sample order; the per-vertex
 // arithmetic is the one of trace_path_rec.
-__global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB) k_render(const RenderArgs a) {
+// The L lanes (L = 2^log2L, a divisor of 32) that share camera pixel `pix`:
+// lane `sl` traces samples sl, sl+L, ...; the lanes then combine their sums
+// and lane 0 writes Ec and Ic.  Every lane of the warp must call this (the
+// reduction shuffles over the full warp); lanes with valid == false only
+// take part in the shuffles.
+__device__ __forceinline__ void render_lanes(const RenderArgs &a, int64_t pix, int sl, bool valid) {
     const int L = 1 << a.log2L;
-    const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int64_t pix = gt >> a.log2L;
-    const int sl = (int)(gt & (L - 1));
-    const int64_t npix = (int64_t)a.Hc * a.Wc;
     f3 sum = mk3(0.f, 0.f, 0.f);
     Cnt cnt;
-    int s = pix < npix ? sl : a.spp;
+    int s = valid ? sl : a.spp;
     int b = 1;
     bool shadow = false, has_ext = false, pending = false;
     f3 beta = mk3(0.f, 0.f, 0.f), Lp = beta, c = beta, ed = beta;  // throughput, path sum, pending NEE, extension dir
@@ -110,13 +111,14 @@ __global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB) k_render(const
             break;
         }
         // yield only while some live lane of the warp could take a new ray
-        const int alive = __popc(__activemask());
+        const int alive = DPCS_YIELD_MIN > 0 ? __popc(__activemask()) : 0;
         if (!pending) {
             cnt.add(shadow ? kCntShadow : kCntRay);
-            trav_begin(st, a.root, shadow ? tmax : INFINITY, shadow);
+            trav_begin(st, DPCS_BVH_WIDTH == 4 ? a.root4 : a.root, shadow ? tmax : INFINITY, shadow);
             pending = true;
         }
-        if (!trav_resume(a.nodes, a.tris, a.root, a.T, ray, st, stack, a.status, cnt, min(DPCS_YIELD_MIN, alive)))
+        if (!trav_resume(a.nodes, a.nodes4, a.tris, a.root, a.root4, a.T, ray, st, stack, a.status, cnt,
+                         min(DPCS_YIELD_MIN, alive)))
             continue;
         pending = false;
         const bool hit = st.h.pos >= 0;
@@ -187,7 +189,7 @@ __global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB) k_render(const
         sum.y += __shfl_xor_sync(0xffffffffu, sum.y, off);
         sum.z += __shfl_xor_sync(0xffffffffu, sum.z, off);
     }
-    if (pix < npix && sl == 0) {
+    if (valid && sl == 0) {
         const float inv = 1.0f / (float)a.spp;
         const float ex = sum.x * inv, ey = sum.y * inv, ez = sum.z * inv;
         if (a.Ec) {
@@ -201,7 +203,55 @@ __global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB) k_render(const
     }
 }
 
-__global__ void k_trace(const float4 *__restrict__ nodes, const float4 *__restrict__ tris, int32_t root, int32_t T,
+__global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB) k_render(const RenderArgs a) {
+    const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t pix = gt >> a.log2L;
+    render_lanes(a, pix, (int)(gt & ((1 << a.log2L) - 1)), pix < (int64_t)a.Hc * a.Wc);
+}
+
+// Batched persistent render: CTAs pull virtual blocks from a device counter;
+// virtual block vb belongs to the segment whose range [vb_begin, vb_begin +
+// ceil(npix L / 128)) holds it, and covers that segment's pixels from
+// pix_begin on.  A segment is a pixel range of one request whose arguments
+// are descs[slot].  Per pixel the computation is render_lanes, exactly as in
+// k_render.  The loop ends when the counter passes the last virtual block:
+// there is no waiting on other CTAs.
+__global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB)
+    k_render_batch(const RenderArgs *__restrict__ descs, const BatchSeg *__restrict__ segs, int nseg,
+                   int64_t total_vb, unsigned long long *counter) {
+    __shared__ RenderArgs sa;
+    __shared__ int64_t s_vb;
+    __shared__ int s_seg;
+    while (true) {
+        if (threadIdx.x == 0) {
+            const int64_t vb = (int64_t)atomicAdd(counter, 1ull);
+            int lo = 0, hi = nseg - 1;  // last segment with vb_begin <= vb
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (segs[mid].vb_begin <= vb) lo = mid; else hi = mid - 1;
+            }
+            s_vb = vb;
+            s_seg = lo;
+        }
+        __syncthreads();
+        const int64_t vb = s_vb;
+        if (vb >= total_vb) break;
+        const BatchSeg sg = segs[s_seg];
+        {
+            const int *src = reinterpret_cast<const int *>(descs + sg.slot);
+            int *dst = reinterpret_cast<int *>(&sa);
+            for (int i = threadIdx.x; i < (int)(sizeof(RenderArgs) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+        }
+        __syncthreads();
+        const int64_t lt = (vb - sg.vb_begin) * kRenderBlock + threadIdx.x;  // thread index within the segment
+        const int64_t lp = lt >> sa.log2L;
+        render_lanes(sa, sg.pix_begin + lp, (int)(lt & ((1 << sa.log2L) - 1)), lp < sg.npix);
+        __syncthreads();
+    }
+}
+
+__global__ void k_trace(const float4 *__restrict__ nodes, const float4 *__restrict__ nodes4,
+                        const float4 *__restrict__ tris, int32_t root, int32_t root4, int32_t T,
                         const float *__restrict__ o, const float *__restrict__ d, int64_t n, float *__restrict__ tout,
                         int32_t *__restrict__ triout, unsigned *status) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -209,7 +259,7 @@ __global__ void k_trace(const float4 *__restrict__ nodes, const float4 *__restri
     Hit h;
     Cnt cnt;
     const Ray r = make_ray(mk3(o[3 * i], o[3 * i + 1], o[3 * i + 2]), mk3(d[3 * i], d[3 * i + 1], d[3 * i + 2]));
-    const bool hit = traverse(nodes, tris, root, T, r, INFINITY, false, h, status, cnt);
+    const bool hit = traverse(nodes, nodes4, tris, root, root4, T, r, INFINITY, false, h, status, cnt);
     tout[i] = hit ? h.t : INFINITY;
     triout[i] = hit ? h.orig : -1;
 }
@@ -349,13 +399,14 @@ __global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB) k_replay(const
             atomicOr(a.status, kStatusTraversalLimit);
             break;
         }
-        const int alive = __popc(__activemask());
+        const int alive = DPCS_YIELD_MIN > 0 ? __popc(__activemask()) : 0;
         if (!pending) {
             cnt.add(shadow ? kCntShadow : kCntRay);
-            trav_begin(st, a.root, shadow ? tmax : INFINITY, shadow);
+            trav_begin(st, DPCS_BVH_WIDTH == 4 ? a.root4 : a.root, shadow ? tmax : INFINITY, shadow);
             pending = true;
         }
-        if (!trav_resume(a.nodes, a.tris, a.root, a.T, ray, st, stack, a.status, cnt, min(DPCS_YIELD_MIN, alive)))
+        if (!trav_resume(a.nodes, a.nodes4, a.tris, a.root, a.root4, a.T, ray, st, stack, a.status, cnt,
+                         min(DPCS_YIELD_MIN, alive)))
             continue;
         pending = false;
         const bool hit = st.h.pos >= 0;
@@ -490,9 +541,27 @@ int launch_render(const RenderArgs &a, cudaStream_t st) {
     return 1;
 }
 
+int launch_render_batch(const RenderArgs *descs, const BatchSeg *segs, int nseg, int64_t total_vb,
+                        unsigned long long *counter, int grid, cudaStream_t st) {
+    k_render_batch<<<grid, kRenderBlock, 0, st>>>(descs, segs, nseg, total_vb, counter);
+    return 1;
+}
+
+int render_batch_grid(int device) {
+    int per_sm = 0, sms = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render_batch, kRenderBlock, 0);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    return per_sm > 0 && sms > 0 ? per_sm * sms : 1;
+}
+
+int64_t render_batch_vblocks(int64_t npix, int log2L) {
+    return ((npix << log2L) + kRenderBlock - 1) / kRenderBlock;
+}
+
 int launch_trace(const Scene &sc, const float *o, const float *d, int64_t n, float *t, int32_t *tri,
                  unsigned *status, cudaStream_t st) {
-    k_trace<<<grid_for(n, 128), 128, 0, st>>>(sc.nodes, sc.tris, sc.root, sc.T, o, d, n, t, tri, status);
+    k_trace<<<grid_for(n, 128), 128, 0, st>>>(sc.nodes, sc.nodes4, sc.tris, sc.root, sc.root4, sc.T, o, d, n, t, tri,
+                                              status);
     return 1;
 }
 

@@ -31,8 +31,16 @@ EXPORTED = [
     "dpcs_create", "dpcs_destroy", "dpcs_last_error", "dpcs_sync", "dpcs_memory_used", "dpcs_launch_count",
     "dpcs_scene_upload", "dpcs_scene_free", "dpcs_scene_export", "dpcs_trace", "dpcs_render",
     "dpcs_render_backward", "dpcs_l2_loss", "dpcs_adam", "dpcs_timing_enable", "dpcs_timing_read",
-    "dpcs_counters_read", "dpcs_render_noalloc",
+    "dpcs_counters_read", "dpcs_render_noalloc", "dpcs_serve_create", "dpcs_serve_destroy", "dpcs_serve_add_scene",
+    "dpcs_serve_submit", "dpcs_serve_step", "dpcs_serve_query", "dpcs_serve_drain", "dpcs_serve_stats_get",
 ]
+
+DPCS_REQ_RELIGHT = 0
+DPCS_REQ_COMPENSATE = 1
+DPCS_REQ_WAITING = 0
+DPCS_REQ_ACTIVE = 1
+DPCS_REQ_DONE = 2
+DPCS_REQ_FAILED = -1
 
 
 class DPCSError(RuntimeError):
@@ -54,6 +62,25 @@ class DpcsView(ctypes.Structure):
     _fields_ = [("Kc", ctypes.c_float * 9), ("Hc", ctypes.c_int32), ("Wc", ctypes.c_int32),
                 ("Kp", ctypes.c_float * 9), ("Rp", ctypes.c_float * 9), ("tp", ctypes.c_float * 3),
                 ("Hp", ctypes.c_int32), ("Wp", ctypes.c_int32)]
+
+
+class DpcsServeConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_active", ctypes.c_int32), ("max_inflight", ctypes.c_int32),
+                ("samples_per_iteration", ctypes.c_int64), ("quantum_samples", ctypes.c_int64)]
+
+
+class DpcsRequest(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("scene", ctypes.c_int32), ("Hc", ctypes.c_int32), ("Wc", ctypes.c_int32),
+                ("spp", ctypes.c_int32), ("seed", ctypes.c_uint64), ("steps", ctypes.c_int32), ("lr", ctypes.c_float),
+                ("Ip", ctypes.c_void_p), ("target", ctypes.c_void_p), ("Ic_out", ctypes.c_void_p),
+                ("Ip_out", ctypes.c_void_p)]
+
+
+class DpcsServeStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("waiting", ctypes.c_int64), ("active", ctypes.c_int64), ("iterations", ctypes.c_int64),
+                ("launches", ctypes.c_int64), ("memory_used", ctypes.c_size_t),
+                ("memory_high_water", ctypes.c_size_t)]
 
 
 _lib = None
@@ -85,6 +112,17 @@ _SIGS = {
     "dpcs_timing_read": (ctypes.c_int32, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_int64)]),
     "dpcs_counters_read": (ctypes.c_int32, [_P, _P, ctypes.c_int32]),
+    "dpcs_serve_create": (ctypes.c_int32, [_P, ctypes.POINTER(DpcsServeConfig), ctypes.POINTER(_P)]),
+    "dpcs_serve_destroy": (ctypes.c_int32, [_P]),
+    "dpcs_serve_add_scene": (ctypes.c_int32, [_P, ctypes.c_uint64, _P, _P, ctypes.c_int32, ctypes.c_int32,
+                                              ctypes.POINTER(DpcsView), ctypes.POINTER(DpcsParams), ctypes.c_int32,
+                                              ctypes.POINTER(ctypes.c_int32)]),
+    "dpcs_serve_submit": (ctypes.c_int32, [_P, ctypes.POINTER(DpcsRequest), ctypes.POINTER(ctypes.c_uint64)]),
+    "dpcs_serve_step": (ctypes.c_int32, [_P, ctypes.POINTER(ctypes.c_int32)]),
+    "dpcs_serve_query": (ctypes.c_int32, [_P, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int32),
+                                          ctypes.POINTER(ctypes.c_double)]),
+    "dpcs_serve_drain": (ctypes.c_int32, [_P, ctypes.c_double]),
+    "dpcs_serve_stats_get": (ctypes.c_int32, [_P, ctypes.POINTER(DpcsServeStats)]),
     "dpcs_l2_loss": (ctypes.c_int32, [_P, _P, _P, ctypes.c_int64, _P, _P, _P]),
     "dpcs_adam": (ctypes.c_int32, [_P, _P, _P, _P, _P, ctypes.c_int64, ctypes.c_float, ctypes.c_float,
                                    ctypes.c_float, ctypes.c_float, ctypes.c_int32, ctypes.c_float, ctypes.c_float,
@@ -427,3 +465,80 @@ class Context:
                        float(lr), float(beta1), float(beta2), float(eps), int(step), float(lo), float(hi),
                        _stream(stream))
         self.check(st, "adam")
+
+
+class Server:
+    """Continuous-batching server (dpcs_serve_*) on a Context.  Host buffers
+    handed to submit() are kept alive here until the request is done."""
+
+    def __init__(self, ctx: Context, hbm_budget_bytes: int = 0, max_active: int = 64, max_inflight: int = 2,
+                 samples_per_iteration: int = 48 << 20, quantum_samples: int = 8 << 20):
+        self.ctx = ctx
+        self.lib = ctx.lib
+        cfg = DpcsServeConfig(int(hbm_budget_bytes), int(max_active), int(max_inflight), int(samples_per_iteration),
+                              int(quantum_samples))
+        h = _P()
+        ctx.check(self.lib.dpcs_serve_create(ctx.handle, ctypes.byref(cfg), ctypes.byref(h)), "serve_create")
+        self.handle = h
+        self._keep = {}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            self.lib.dpcs_serve_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def add_scene(self, scene: int, albedo, rough, view: DpcsView, params: DpcsParams, bounces: int) -> int:
+        import torch
+
+        Ht, Wt = albedo.shape[0], albedo.shape[1]
+        slot = ctypes.c_int32()
+        st = self.lib.dpcs_serve_add_scene(self.handle, scene,
+                                           _ptr(albedo, "albedo", (Ht, Wt, 3), torch.float32, self.ctx.device),
+                                           _ptr(rough, "rough", (Ht, Wt), torch.float32, self.ctx.device), Ht, Wt,
+                                           ctypes.byref(view), ctypes.byref(params), int(bounces), ctypes.byref(slot))
+        self.ctx.check(st, "serve_add_scene")
+        self._keep[("scene", slot.value)] = (albedo, rough)
+        return slot.value
+
+    def submit(self, kind: int, scene: int, Hc: int, Wc: int, spp: int, seed: int, Ip, Ic_out, target=None,
+               Ip_out=None, steps: int = 0, lr: float = 1e-2) -> int:
+        """Ip, target, Ic_out, Ip_out: contiguous float32 host arrays (pinned
+        memory keeps the server's copies asynchronous)."""
+        def hp(a):
+            if a is None:
+                return None
+            return ctypes.c_void_p(a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data)
+
+        req = DpcsRequest(int(kind), int(scene), int(Hc), int(Wc), int(spp), int(seed) & (2**64 - 1), int(steps),
+                          float(lr), hp(Ip), hp(target), hp(Ic_out), hp(Ip_out))
+        rid = ctypes.c_uint64()
+        self.ctx.check(self.lib.dpcs_serve_submit(self.handle, ctypes.byref(req), ctypes.byref(rid)), "serve_submit")
+        self._keep[rid.value] = (Ip, target, Ic_out, Ip_out)
+        return rid.value
+
+    def step(self) -> int:
+        n = ctypes.c_int32()
+        self.ctx.check(self.lib.dpcs_serve_step(self.handle, ctypes.byref(n)), "serve_step")
+        return n.value
+
+    def query(self, rid: int):
+        st, lat = ctypes.c_int32(), ctypes.c_double()
+        self.ctx.check(self.lib.dpcs_serve_query(self.handle, rid, ctypes.byref(st), ctypes.byref(lat)), "serve_query")
+        if st.value in (DPCS_REQ_DONE, DPCS_REQ_FAILED):
+            self._keep.pop(rid, None)
+        return st.value, lat.value
+
+    def drain(self, timeout_s: float = 600.0):
+        self.ctx.check(self.lib.dpcs_serve_drain(self.handle, float(timeout_s)), "serve_drain")
+
+    def stats(self) -> dict:
+        o = DpcsServeStats()
+        self.ctx.check(self.lib.dpcs_serve_stats_get(self.handle, ctypes.byref(o)), "serve_stats")
+        return {k: getattr(o, k) for k, _ in DpcsServeStats._fields_}

@@ -45,8 +45,10 @@ def test_struct_layout_matches_header():
 #include <stddef.h>
 #include "dpcs.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu\n", sizeof(dpcs_params), offsetof(dpcs_params, rr_start),
-         offsetof(dpcs_params, jitter), sizeof(dpcs_view), offsetof(dpcs_view, Kp), offsetof(dpcs_view, Hp));
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(dpcs_params), offsetof(dpcs_params, rr_start),
+         offsetof(dpcs_params, jitter), sizeof(dpcs_view), offsetof(dpcs_view, Kp), offsetof(dpcs_view, Hp),
+         sizeof(dpcs_request), offsetof(dpcs_request, seed), offsetof(dpcs_request, Ip_out),
+         sizeof(dpcs_serve_config), offsetof(dpcs_serve_config, quantum_samples), sizeof(dpcs_serve_stats));
   return 0;
 }
 """
@@ -56,5 +58,7 @@ int main(void) {
         open(c, "w").write(code)
         subprocess.check_call(["gcc", "-I", os.path.dirname(HDR), c, "-o", exe])
         out = [int(x) for x in subprocess.check_output([exe]).split()]
-    P, V = dpcs.DpcsParams, dpcs.DpcsView
-    assert out == [ctypes.sizeof(P), P.rr_start.offset, P.jitter.offset, ctypes.sizeof(V), V.Kp.offset, V.Hp.offset]
+    P, V, R, C = dpcs.DpcsParams, dpcs.DpcsView, dpcs.DpcsRequest, dpcs.DpcsServeConfig
+    assert out == [ctypes.sizeof(P), P.rr_start.offset, P.jitter.offset, ctypes.sizeof(V), V.Kp.offset, V.Hp.offset,
+                   ctypes.sizeof(R), R.seed.offset, R.Ip_out.offset, ctypes.sizeof(C), C.quantum_samples.offset,
+                   ctypes.sizeof(dpcs.DpcsServeStats)]
