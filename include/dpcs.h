@@ -269,11 +269,12 @@ dpcs_status dpcs_adam(dpcs_ctx *ctx, float *p, const float *g, float *m, float *
  * dpcs_serve_step is one scheduler iteration: it retires finished work,
  * admits waiting requests (FIFO) while their device memory fits the HBM
  * budget and fewer than max_active are admitted, and launches one batched
- * render in which every active relighting request gets up to
- * quantum_samples of camera samples (fewest remaining first) and every
- * active compensation request renders its full image; the compensation
- * requests' loss, path-replay adjoint and Adam step follow on the same
- * stream.  Requests that arrive while others run join at the next
+ * render of about samples_per_iteration camera samples: every active
+ * relighting request first gets quantum_samples (so short requests finish
+ * within an iteration or two), compensation requests render their full
+ * images within half of the iteration, and the rest goes to relighting
+ * requests in arrival order; the compensation requests' loss, path-replay
+ * adjoint and Adam step follow on the same stream.  Requests that arrive while others run join at the next
  * iteration.  A pixel's result is computed exactly as dpcs_render computes
  * it, whatever else is in the batch.  Waits are bounded; nothing spins on
  * the GPU.  A server is not thread safe; use it from one host thread.
@@ -284,8 +285,8 @@ typedef struct dpcs_serve_config {
     size_t hbm_budget_bytes;        /* device memory for admitted requests (0 = no limit) */
     int32_t max_active;             /* most requests admitted at once (1..1024) */
     int32_t max_inflight;           /* batched iterations queued on the GPU at once (1..4) */
-    int64_t samples_per_iteration;  /* camera samples one batched launch may take */
-    int64_t quantum_samples;        /* samples a relighting request gets per iteration */
+    int64_t samples_per_iteration;  /* camera samples one batched iteration aims at */
+    int64_t quantum_samples;        /* samples every active relighting request gets first */
 } dpcs_serve_config;
 
 #define DPCS_REQ_RELIGHT 0

@@ -1,0 +1,76 @@
+"""Projector compensation (Eq. 13): Ip* = argmin_Ip |R(Ip, theta) - Ic|.
+
+The loop runs entirely on the device through the C ABI.  Each step renders
+Ic = R(Ip) with a fresh Philox key (seed + k), takes the L2 loss against the
+target, carries dL/dIc back to Ip with the path-replay adjoint, and applies
+an Adam step followed by the clamp of Ip to [0, 1].
+
+With ``graph=True`` the whole loop is captured once as a CUDA graph and then
+replayed.  The steps are unrolled in the graph, so every step keeps its own
+seed and Adam step number, and one replay runs the full compensation.  The
+library's scratch memory is sized by one eager step before the capture.
+"""
+from __future__ import annotations
+
+from . import dpcs
+
+
+class Compensation:
+    """Device state and (optionally) a captured CUDA graph for one scene,
+    view and target size."""
+
+    def __init__(self, ctx: dpcs.Context, scene: int, albedo, rough, view: dpcs.DpcsView, params: dpcs.DpcsParams,
+                 spp: int, bounces: int, steps: int, lr: float = 1e-2, seed: int = 0, graph: bool = True):
+        import torch
+
+        self.ctx, self.scene, self.albedo, self.rough = ctx, scene, albedo, rough
+        self.view, self.params, self.spp, self.bounces = view, params, int(spp), int(bounces)
+        self.steps, self.lr, self.seed = int(steps), float(lr), int(seed)
+        dev = ctx.device
+        f32 = torch.float32
+        self.P = torch.zeros((view.Hp, view.Wp, 3), dtype=f32, device=dev)
+        self.P0 = torch.zeros_like(self.P)
+        self.M, self.V, self.G = torch.zeros_like(self.P), torch.zeros_like(self.P), torch.zeros_like(self.P)
+        self.target = torch.zeros((view.Hc, view.Wc, 3), dtype=f32, device=dev)
+        self.Ic = torch.empty_like(self.target)
+        self.Ec = torch.empty_like(self.target)
+        self.dIc = torch.empty_like(self.target)
+        self.loss = torch.zeros(1, dtype=f32, device=dev)
+        self.history = torch.zeros(self.steps, dtype=f32, device=dev)
+        self.graph = None
+        if graph:
+            self._step(0)  # sizes the library's scratch outside the capture
+            torch.cuda.synchronize()
+            self.graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(self.graph):
+                self._loop()
+
+    def _step(self, k: int):
+        c = self.ctx
+        s = self.seed + k
+        c.render(self.scene, self.albedo, self.rough, self.P, self.view, self.params, self.spp, self.bounces, s,
+                 Ic=self.Ic, Ec=self.Ec)
+        c.l2_loss(self.Ic, self.target, self.dIc, self.loss)
+        self.history[k].copy_(self.loss[0])
+        self.G.zero_()
+        c.render_backward(self.scene, self.albedo, self.rough, self.P, self.view, self.params, self.spp, self.bounces, s,
+                          self.Ec, self.Ic, self.dIc, dIp=self.G)
+        c.adam(self.P, self.G, self.M, self.V, k + 1, lr=self.lr, lo=0.0, hi=1.0)
+
+    def _loop(self):
+        self.P.copy_(self.P0)
+        self.M.zero_()
+        self.V.zero_()
+        for k in range(self.steps):
+            self._step(k)
+
+    def run(self, Ip_init, target):
+        """Compensate towards `target` (Hc x Wc x 3) from `Ip_init` (Hp x Wp x
+        3); returns (Ip*, per-step losses) as device tensors."""
+        self.P0.copy_(Ip_init)
+        self.target.copy_(target)
+        if self.graph is not None:
+            self.graph.replay()
+        else:
+            self._loop()
+        return self.P, self.history

@@ -184,11 +184,9 @@ dpcs_status prepare(dpcs_ctx *c, dpcs_scene scene, const float *albedo, const fl
     Scene &sc = it->second;
     memset(&a, 0, sizeof a);
     a.nodes = sc.nodes;
-    a.nodes4 = sc.nodes4;
     a.tris = sc.tris;
     a.tuv = sc.tuv;
     a.root = sc.root;
-    a.root4 = sc.root4;
     a.T = sc.T;
     a.Ht = Ht;
     a.Wt = Wt;
@@ -267,7 +265,6 @@ dpcs_status dpcs_destroy(dpcs_ctx *c) {
     for (auto &kv : c->scenes) {
         Scene &s = kv.second;
         cudaFree(s.nodes);
-        cudaFree(s.nodes4);
         cudaFree(s.tris);
         cudaFree(s.tuv);
         cudaFree(s.codes);
@@ -374,15 +371,13 @@ dpcs_status dpcs_scene_upload(dpcs_ctx *c, const float *verts, int32_t V, const 
     sc.T = T;
     const size_t n = (size_t)(T > 0 ? T : 1);
     const size_t nn = (size_t)(T > 1 ? T - 1 : 1);
-    sc.bytes = nn * 64 + nn * 128 + n * 48 + n * 24 + n * 8;
+    sc.bytes = nn * 64 + n * 48 + n * 24 + n * 8;
     if ((s = dev_alloc(c, (void **)&sc.nodes, nn * 64, "scene nodes")) ||
-        (s = dev_alloc(c, (void **)&sc.nodes4, nn * 128, "scene 4-wide nodes")) ||
         (s = dev_alloc(c, (void **)&sc.tris, n * 48, "scene triangles")) ||
         (s = dev_alloc(c, (void **)&sc.tuv, n * 24, "scene uv")) ||
         (s = dev_alloc(c, (void **)&sc.codes, n * 4, "scene codes")) ||
         (s = dev_alloc(c, (void **)&sc.order, n * 4, "scene order"))) {
         dev_free(c, sc.nodes, sc.nodes ? nn * 64 : 0);
-        dev_free(c, sc.nodes4, sc.nodes4 ? nn * 128 : 0);
         dev_free(c, sc.tris, sc.tris ? n * 48 : 0);
         dev_free(c, sc.tuv, sc.tuv ? n * 24 : 0);
         dev_free(c, sc.codes, sc.codes ? n * 4 : 0);
@@ -408,7 +403,6 @@ dpcs_status dpcs_scene_upload(dpcs_ctx *c, const float *verts, int32_t V, const 
         if (e != cudaSuccess) return cuda_fail(c, e, "LBVH build");
     } else {
         sc.root = kEmptyRoot;
-        sc.root4 = kEmptyRoot;
     }
     const uint64_t id = c->next_scene++;
     c->scenes[id] = sc;
@@ -425,7 +419,6 @@ dpcs_status dpcs_scene_free(dpcs_ctx *c, dpcs_scene scene) {
     Scene &s = it->second;
     const size_t n = (size_t)(s.T > 0 ? s.T : 1), nn = (size_t)(s.T > 1 ? s.T - 1 : 1);
     dev_free(c, s.nodes, nn * 64);
-    dev_free(c, s.nodes4, nn * 128);
     dev_free(c, s.tris, n * 48);
     dev_free(c, s.tuv, n * 24);
     dev_free(c, s.codes, n * 4);

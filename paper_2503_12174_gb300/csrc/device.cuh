@@ -261,8 +261,16 @@ __device__ __forceinline__ float4 bilin_fetch(const float4 *__restrict__ img, co
 // (left ref, right ref, -, -) with refs >= 0 internal, < 0 leaf ~position.
 // Triangle = 3 float4: (v0, original index), e1, e2.
 // ---------------------------------------------------------------------------
+#ifndef DPCS_SLAB_FMA
+#define DPCS_SLAB_FMA 1  // slab distances as fma(lo, 1/d, -o/d) with a per-ray absolute error margin
+#endif
+
 struct Ray {
     f3 o, d, inv;
+#if DPCS_SLAB_FMA
+    f3 oinv;    // o / d per axis
+    float err;  // bound on the extra rounding of the fused form
+#endif
 };
 __device__ __forceinline__ Ray make_ray(f3 o, f3 d) {
     Ray r;
@@ -271,6 +279,10 @@ __device__ __forceinline__ Ray make_ray(f3 o, f3 d) {
     const float e = 1e-20f;
     r.inv = mk3(1.0f / (fabsf(d.x) > e ? d.x : copysignf(e, d.x)), 1.0f / (fabsf(d.y) > e ? d.y : copysignf(e, d.y)),
                 1.0f / (fabsf(d.z) > e ? d.z : copysignf(e, d.z)));
+#if DPCS_SLAB_FMA
+    r.oinv = mk3(o.x * r.inv.x, o.y * r.inv.y, o.z * r.inv.z);
+    r.err = 4.8e-7f * fmaxf(fmaxf(fabsf(r.oinv.x), fabsf(r.oinv.y)), fabsf(r.oinv.z));
+#endif
     return r;
 }
 
@@ -302,6 +314,17 @@ __device__ __forceinline__ float fmin3f(float a, float b, float c) {
 // flat boxes of axis-aligned walls are never missed by rounding
 __device__ __forceinline__ bool slab(const Ray &r, float lx, float hx, float ly, float hy, float lz, float hz,
                                      float tmax, float &tnear) {
+#if DPCS_SLAB_FMA
+    // fused form: its rounding error is bounded by a few ulps of |t| plus a
+    // few ulps of |o / d|, which r.err covers
+    const float tx0 = fmaf(lx, r.inv.x, -r.oinv.x), tx1 = fmaf(hx, r.inv.x, -r.oinv.x);
+    const float ty0 = fmaf(ly, r.inv.y, -r.oinv.y), ty1 = fmaf(hy, r.inv.y, -r.oinv.y);
+    const float tz0 = fmaf(lz, r.inv.z, -r.oinv.z), tz1 = fmaf(hz, r.inv.z, -r.oinv.z);
+    const float tn = fmax3f(fminf(tx0, tx1), fminf(ty0, ty1), fmaxf(fminf(tz0, tz1), 0.0f));
+    const float tf = fmin3f(fmaxf(tx0, tx1), fmaxf(ty0, ty1), fminf(fmaxf(tz0, tz1), tmax));
+    tnear = tn;
+    return tn <= fmaf(tf, 1.0000004f, r.err);
+#else
     const float tx0 = (lx - r.o.x) * r.inv.x, tx1 = (hx - r.o.x) * r.inv.x;
     const float ty0 = (ly - r.o.y) * r.inv.y, ty1 = (hy - r.o.y) * r.inv.y;
     const float tz0 = (lz - r.o.z) * r.inv.z, tz1 = (hz - r.o.z) * r.inv.z;
@@ -309,6 +332,7 @@ __device__ __forceinline__ bool slab(const Ray &r, float lx, float hx, float ly,
     const float tf = fmin3f(fmaxf(tx0, tx1), fmaxf(ty0, ty1), fminf(fmaxf(tz0, tz1), tmax));
     tnear = tn;
     return tn <= tf * 1.0000004f;
+#endif
 }
 
 // Moller-Trumbore, two-sided, t in (0, tmax]
@@ -334,13 +358,15 @@ struct Hit {
     float t, u, v;
 };
 
-// Traversal of the 4-wide BVH.  A node holds the boxes of up to four
-// children (SoA, one 128-byte line) and their references (>= 0 node, < 0
-// leaf ~position, kEmptyChild).  The hit children are ordered near to far by
-// a 5-comparator sorting network; the nearest is visited next and the others
-// are pushed farthest first.  any = true stops at the first hit with
-// t < tmax (shadow rays); otherwise the closest hit is kept, ties in t to the
-// lowest original triangle index.
+// BVH traversal.  Node = 4 float4: (l.lo.x, l.hi.x, l.lo.y, l.hi.y),
+// (r.lo.x, r.hi.x, r.lo.y, r.hi.y), (l.lo.z, l.hi.z, r.lo.z, r.hi.z),
+// (left ref, right ref, -, -) with refs >= 0 internal, < 0 leaf ~position.
+// Triangle = 3 float4: (v0, original index), e1, e2.  Both children's boxes
+// are tested; the nearer hit child is visited next and the other pushed.
+// any = true stops at the first hit with t < tmax (shadow rays); otherwise
+// the closest hit is kept, ties in t to the lowest original triangle index.
+// (A 4-wide collapse of this tree was measured slower on GB300: its child
+// sorting and masking cost more ALU issue than the halved node visits save.)
 //
 // The traversal is resumable: its state (node, stack depth, visit count, best
 // hit) lives in Trav, kept by the caller.  After at least one step the loop
@@ -364,88 +390,7 @@ __device__ __forceinline__ void trav_begin(Trav &st, int32_t root, float tmax, b
     st.h.t = tmax;
 }
 
-__device__ __forceinline__ void cswap(float &ta, int &ra, float &tb, int &rb) {
-    const bool sw = tb < ta;
-    const float t = sw ? tb : ta;
-    const int r = sw ? rb : ra;
-    tb = sw ? ta : tb;
-    rb = sw ? ra : rb;
-    ta = t;
-    ra = r;
-}
-
-__device__ __forceinline__ bool trav_resume4(const float4 *__restrict__ nodes, const float4 *__restrict__ tris,
-                                            int32_t root, int32_t T, const Ray &ray, Trav &st, int *stack,
-                                            unsigned *status, Cnt &cnt, int min_active) {
-    if (root == kEmptyRoot) return true;
-    const int cap = 2 * T + 16;
-    bool first = true;
-    while (true) {
-        if (min_active > 0 && !first && __popc(__activemask()) < min_active) return false;
-        first = false;
-        if (++st.visits > cap) {
-            atomicOr(status, kStatusTraversalLimit);
-            st.h.pos = -1;
-            return true;
-        }
-        const int node = st.node;
-        if (node >= 0) {
-            cnt.add(kCntNode);
-            const float4 *nd = nodes + 8 * (size_t)node;
-            const float4 lx = __ldg(nd + 0), hx = __ldg(nd + 1), ly = __ldg(nd + 2), hy = __ldg(nd + 3);
-            const float4 lz = __ldg(nd + 4), hz = __ldg(nd + 5), rf = __ldg(nd + 6);
-            float t0, t1, t2, t3;
-            int r0 = __float_as_int(rf.x), r1 = __float_as_int(rf.y), r2 = __float_as_int(rf.z),
-                r3 = __float_as_int(rf.w);
-            const float tcut = st.h.t;
-            if (!(slab(ray, lx.x, hx.x, ly.x, hy.x, lz.x, hz.x, tcut, t0) && r0 != kEmptyChild)) t0 = INFINITY;
-            if (!(slab(ray, lx.y, hx.y, ly.y, hy.y, lz.y, hz.y, tcut, t1) && r1 != kEmptyChild)) t1 = INFINITY;
-            if (!(slab(ray, lx.z, hx.z, ly.z, hy.z, lz.z, hz.z, tcut, t2) && r2 != kEmptyChild)) t2 = INFINITY;
-            if (!(slab(ray, lx.w, hx.w, ly.w, hy.w, lz.w, hz.w, tcut, t3) && r3 != kEmptyChild)) t3 = INFINITY;
-            cswap(t0, r0, t1, r1);
-            cswap(t2, r2, t3, r3);
-            cswap(t0, r0, t2, r2);
-            cswap(t1, r1, t3, r3);
-            cswap(t1, r1, t2, r2);
-            const int nh = (t0 < INFINITY) + (t1 < INFINITY) + (t2 < INFINITY) + (t3 < INFINITY);
-            if (nh > 0) {
-                if (st.sp + nh - 1 > kStack) {
-                    atomicOr(status, kStatusTraversalLimit);
-                    st.h.pos = -1;
-                    return true;
-                }
-                if (nh == 4) stack[st.sp++] = r3;
-                if (nh >= 3) stack[st.sp++] = r2;
-                if (nh >= 2) stack[st.sp++] = r1;
-                st.node = r0;
-                continue;
-            }
-        } else {
-            const int pos = ~node;
-            cnt.add(kCntTri);
-            const float4 a = __ldg(tris + 3 * pos + 0);
-            const float4 b = __ldg(tris + 3 * pos + 1);
-            const float4 c = __ldg(tris + 3 * pos + 2);
-            float t, u, v;
-            if (tri_isect(ray, xyz(a), xyz(b), xyz(c), st.h.t, t, u, v)) {
-                const int orig = __float_as_int(a.w);
-                if (t < st.h.t || (!st.any && t == st.h.t && orig < st.h.orig)) {
-                    st.h.pos = pos;
-                    st.h.orig = orig;
-                    st.h.t = t;
-                    st.h.u = u;
-                    st.h.v = v;
-                    if (st.any) return true;
-                }
-            }
-        }
-        if (st.sp == 0) return true;
-        st.node = stack[--st.sp];
-    }
-}
-
-// binary-node steps: 64-byte nodes with two child boxes
-__device__ __forceinline__ bool trav_resume2(const float4 *__restrict__ nodes, const float4 *__restrict__ tris,
+__device__ __forceinline__ bool trav_resume(const float4 *__restrict__ nodes, const float4 *__restrict__ tris,
                                             int32_t root, int32_t T, const Ray &ray, Trav &st, int *stack,
                                             unsigned *status, Cnt &cnt, int min_active) {
     if (root == kEmptyRoot) return true;
@@ -507,32 +452,14 @@ __device__ __forceinline__ bool trav_resume2(const float4 *__restrict__ nodes, c
     }
 }
 
-
-#ifndef DPCS_BVH_WIDTH
-#define DPCS_BVH_WIDTH 2  // traversal of the binary LBVH (2) or of its 4-wide collapse (4)
-#endif
-
-__device__ __forceinline__ bool trav_resume(const float4 *__restrict__ nodes2, const float4 *__restrict__ nodes4,
-                                            const float4 *__restrict__ tris, int32_t root2, int32_t root4, int32_t T,
-                                            const Ray &ray, Trav &st, int *stack, unsigned *status, Cnt &cnt,
-                                            int min_active) {
-#if DPCS_BVH_WIDTH == 4
-    (void)nodes2; (void)root2;
-    return trav_resume4(nodes4, tris, root4, T, ray, st, stack, status, cnt, min_active);
-#else
-    (void)nodes4; (void)root4;
-    return trav_resume2(nodes2, tris, root2, T, ray, st, stack, status, cnt, min_active);
-#endif
-}
-
 // traversal to completion (no yielding)
-__device__ __forceinline__ bool traverse(const float4 *__restrict__ nodes2, const float4 *__restrict__ nodes4,
-                                         const float4 *__restrict__ tris, int32_t root2, int32_t root4, int32_t T,
-                                         const Ray &ray, float tmax, bool any, Hit &h, unsigned *status, Cnt &cnt) {
+__device__ __forceinline__ bool traverse(const float4 *__restrict__ nodes, const float4 *__restrict__ tris,
+                                         int32_t root, int32_t T, const Ray &ray, float tmax, bool any, Hit &h,
+                                         unsigned *status, Cnt &cnt) {
     Trav st;
     int stack[kStack];
-    trav_begin(st, DPCS_BVH_WIDTH == 4 ? root4 : root2, tmax, any);
-    trav_resume(nodes2, nodes4, tris, root2, root4, T, ray, st, stack, status, cnt, 0);
+    trav_begin(st, root, tmax, any);
+    trav_resume(nodes, tris, root, T, ray, st, stack, status, cnt, 0);
     h = st.h;
     return h.pos >= 0;
 }

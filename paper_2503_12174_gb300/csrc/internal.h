@@ -27,23 +27,16 @@ struct Scene {
     float2 *tuv = nullptr;     // 3 x T
     uint32_t *codes = nullptr; // sorted Morton codes, T
     int32_t *order = nullptr;  // original triangle of each sorted position, T
-    // 4-wide BVH collapsed from the binary tree (the one traversal uses):
-    // 8 float4 per node = lo.x[4], hi.x[4], lo.y[4], hi.y[4], lo.z[4],
-    // hi.z[4], child refs[4] (>= 0 node, < 0 leaf ~pos, kEmptyChild), pad
-    float4 *nodes4 = nullptr;  // 8 x (T-1) at most
-    int32_t root4 = 0;
     size_t bytes = 0;
 };
 constexpr int32_t kEmptyRoot = (int32_t)0x80000000;
-constexpr int32_t kEmptyChild = 0x7fffffff;
 
 // Kernel arguments of one render / replay launch (passed by value).
 struct RenderArgs {
-    const float4 *nodes;   // binary LBVH nodes
-    const float4 *nodes4;  // its 4-wide collapse
+    const float4 *nodes;   // LBVH nodes
     const float4 *tris;
     const float2 *tuv;
-    int32_t root, root4;   // root references of the two trees
+    int32_t root;          // root reference
     int32_t T;
     const float4 *tex;   // Ht x Wt: albedo rgb, roughness
     int32_t Ht, Wt;

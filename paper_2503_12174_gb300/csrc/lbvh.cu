@@ -235,62 +235,6 @@ __global__ void k_refit(const float *__restrict__ verts, const int32_t *__restri
     }
 }
 
-// --- collapse to a 4-wide BVH --------------------------------------------------
-// Binary internal nodes at even depth become 4-wide nodes; their children
-// are their grandchildren (or their children where those are leaves).
-__global__ void k_depth_parity(const int32_t *__restrict__ parent, int T, uint32_t *__restrict__ even) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= T - 1) return;
-    int d = 0;
-    for (int j = i; j != 0 && d < 4 * 64; j = parent[j]) ++d;  // depth is bounded by the tree height
-    even[i] = (d & 1) == 0 ? 1u : 0u;
-}
-
-__global__ void k_collapse4(const float4 *__restrict__ nodes, const uint32_t *__restrict__ idx4,
-                            const uint32_t *__restrict__ even_flag, int T, float4 *__restrict__ nodes4) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= T - 1) return;
-    // idx4 is the exclusive scan of the even-depth flags; even_flag[i] tells if i is one
-    if (!even_flag[i]) return;
-    const float *nd = reinterpret_cast<const float *>(nodes + 4 * i);
-    float lo[3][4], hi[3][4];
-    int ref[4];
-    int cnt = 0;
-    for (int side = 0; side < 2; ++side) {
-        const int c = __float_as_int(nd[12 + side]);
-        // child box of i on this side: x at [0..3] or [4..7], z at [8..11]
-        const float *xy = nd + (side ? 4 : 0);
-        const float *zz = nd + 8 + (side ? 2 : 0);
-        if (c < 0) {
-            lo[0][cnt] = xy[0]; hi[0][cnt] = xy[1]; lo[1][cnt] = xy[2]; hi[1][cnt] = xy[3];
-            lo[2][cnt] = zz[0]; hi[2][cnt] = zz[1];
-            ref[cnt++] = c;
-            continue;
-        }
-        const float *cd = reinterpret_cast<const float *>(nodes + 4 * c);
-        for (int s2 = 0; s2 < 2; ++s2) {
-            const int g = __float_as_int(cd[12 + s2]);
-            const float *gxy = cd + (s2 ? 4 : 0);
-            const float *gz = cd + 8 + (s2 ? 2 : 0);
-            lo[0][cnt] = gxy[0]; hi[0][cnt] = gxy[1]; lo[1][cnt] = gxy[2]; hi[1][cnt] = gxy[3];
-            lo[2][cnt] = gz[0]; hi[2][cnt] = gz[1];
-            ref[cnt++] = g < 0 ? g : (int)idx4[g];
-        }
-    }
-    for (; cnt < 4; ++cnt) {
-        lo[0][cnt] = lo[1][cnt] = lo[2][cnt] = 0.0f;
-        hi[0][cnt] = hi[1][cnt] = hi[2][cnt] = 0.0f;
-        ref[cnt] = kEmptyChild;
-    }
-    float4 *o = nodes4 + 8 * (size_t)idx4[i];
-    for (int a = 0; a < 3; ++a) {
-        o[2 * a] = make_float4(lo[a][0], lo[a][1], lo[a][2], lo[a][3]);
-        o[2 * a + 1] = make_float4(hi[a][0], hi[a][1], hi[a][2], hi[a][3]);
-    }
-    o[6] = make_float4(__int_as_float(ref[0]), __int_as_float(ref[1]), __int_as_float(ref[2]), __int_as_float(ref[3]));
-    o[7] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-}
-
 inline size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
 
 }  // namespace
@@ -299,7 +243,7 @@ size_t lbvh_scratch_bytes(int32_t T) {
     const size_t n = (size_t)(T > 0 ? T : 1);
     const size_t nb = (n + kSortTile - 1) / kSortTile;
     return align256(3 * n * 4) + align256(6 * 4) + 4 * align256(n * 4) + align256(256 * nb * 4) +
-           align256((2 * n) * 4) + align256(n * 4) + 2 * align256(n * 4);
+           align256((2 * n) * 4) + align256(n * 4);
 }
 
 int launch_lbvh_build(const float *d_verts, int32_t V, const int32_t *d_tris, int32_t T, const float *d_uv,
@@ -325,7 +269,6 @@ int launch_lbvh_build(const float *d_verts, int32_t V, const int32_t *d_tris, in
     uint32_t *hist = (uint32_t *)take(256 * (size_t)nb * 4);
     int32_t *parent = (int32_t *)take(2 * n * 4);
     int32_t *flags = (int32_t *)take(n * 4);
-    uint32_t *even = (uint32_t *)take(n * 4), *idx4 = (uint32_t *)take(n * 4);
     int launches = 0;
     const int tb = 256, gb = (T + tb - 1) / tb;
     k_centroids<<<gb, tb, 0, st>>>(d_verts, d_tris, T, cen);
@@ -351,15 +294,6 @@ int launch_lbvh_build(const float *d_verts, int32_t V, const int32_t *d_tris, in
     k_refit<<<gb, tb, 0, st>>>(d_verts, d_tris, d_uv, va, T, sc.nodes, parent, flags, sc.tris, sc.tuv);
     ++launches;
     sc.root = T >= 2 ? 0 : ~0;
-    sc.root4 = T >= 2 ? 0 : ~0;  // binary root 0 has depth 0 and scan index 0
-    if (T >= 2) {
-        const int gi = (T - 1 + tb - 1) / tb;
-        k_depth_parity<<<gi, tb, 0, st>>>(parent, T, even);
-        cudaMemcpyAsync(idx4, even, (size_t)(T - 1) * 4, cudaMemcpyDeviceToDevice, st);
-        k_radix_scan<<<1, 1024, 0, st>>>(idx4, T - 1);
-        k_collapse4<<<gi, tb, 0, st>>>(sc.nodes, idx4, even, T, sc.nodes4);
-        launches += 3;
-    }
     return launches;
 }
 

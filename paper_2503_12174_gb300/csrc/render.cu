@@ -32,7 +32,7 @@ constexpr int kRenderBlock = 128;
 #define DPCS_YIELD_MIN 0
 #endif
 #ifndef DPCS_RENDER_MINB
-#define DPCS_RENDER_MINB 8  // minimum resident blocks per SM requested from ptxas (64 registers)
+#define DPCS_RENDER_MINB 10  // minimum resident blocks per SM requested from ptxas (48 registers; sweep: 9-12 within 3 %)
 #endif
 
 __device__ __forceinline__ void atomic_add4(float4 *p, float4 v) {
@@ -114,11 +114,10 @@ __device__ __forceinline__ void render_lanes(const RenderArgs &a, int64_t pix, i
         const int alive = DPCS_YIELD_MIN > 0 ? __popc(__activemask()) : 0;
         if (!pending) {
             cnt.add(shadow ? kCntShadow : kCntRay);
-            trav_begin(st, DPCS_BVH_WIDTH == 4 ? a.root4 : a.root, shadow ? tmax : INFINITY, shadow);
+            trav_begin(st, a.root, shadow ? tmax : INFINITY, shadow);
             pending = true;
         }
-        if (!trav_resume(a.nodes, a.nodes4, a.tris, a.root, a.root4, a.T, ray, st, stack, a.status, cnt,
-                         min(DPCS_YIELD_MIN, alive)))
+        if (!trav_resume(a.nodes, a.tris, a.root, a.T, ray, st, stack, a.status, cnt, min(DPCS_YIELD_MIN, alive)))
             continue;
         pending = false;
         const bool hit = st.h.pos >= 0;
@@ -250,8 +249,7 @@ __global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB)
     }
 }
 
-__global__ void k_trace(const float4 *__restrict__ nodes, const float4 *__restrict__ nodes4,
-                        const float4 *__restrict__ tris, int32_t root, int32_t root4, int32_t T,
+__global__ void k_trace(const float4 *__restrict__ nodes, const float4 *__restrict__ tris, int32_t root, int32_t T,
                         const float *__restrict__ o, const float *__restrict__ d, int64_t n, float *__restrict__ tout,
                         int32_t *__restrict__ triout, unsigned *status) {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -259,7 +257,7 @@ __global__ void k_trace(const float4 *__restrict__ nodes, const float4 *__restri
     Hit h;
     Cnt cnt;
     const Ray r = make_ray(mk3(o[3 * i], o[3 * i + 1], o[3 * i + 2]), mk3(d[3 * i], d[3 * i + 1], d[3 * i + 2]));
-    const bool hit = traverse(nodes, nodes4, tris, root, root4, T, r, INFINITY, false, h, status, cnt);
+    const bool hit = traverse(nodes, tris, root, T, r, INFINITY, false, h, status, cnt);
     tout[i] = hit ? h.t : INFINITY;
     triout[i] = hit ? h.orig : -1;
 }
@@ -402,11 +400,10 @@ __global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB) k_replay(const
         const int alive = DPCS_YIELD_MIN > 0 ? __popc(__activemask()) : 0;
         if (!pending) {
             cnt.add(shadow ? kCntShadow : kCntRay);
-            trav_begin(st, DPCS_BVH_WIDTH == 4 ? a.root4 : a.root, shadow ? tmax : INFINITY, shadow);
+            trav_begin(st, a.root, shadow ? tmax : INFINITY, shadow);
             pending = true;
         }
-        if (!trav_resume(a.nodes, a.nodes4, a.tris, a.root, a.root4, a.T, ray, st, stack, a.status, cnt,
-                         min(DPCS_YIELD_MIN, alive)))
+        if (!trav_resume(a.nodes, a.tris, a.root, a.T, ray, st, stack, a.status, cnt, min(DPCS_YIELD_MIN, alive)))
             continue;
         pending = false;
         const bool hit = st.h.pos >= 0;
@@ -560,8 +557,7 @@ int64_t render_batch_vblocks(int64_t npix, int log2L) {
 
 int launch_trace(const Scene &sc, const float *o, const float *d, int64_t n, float *t, int32_t *tri,
                  unsigned *status, cudaStream_t st) {
-    k_trace<<<grid_for(n, 128), 128, 0, st>>>(sc.nodes, sc.nodes4, sc.tris, sc.root, sc.root4, sc.T, o, d, n, t, tri,
-                                              status);
+    k_trace<<<grid_for(n, 128), 128, 0, st>>>(sc.nodes, sc.tris, sc.root, sc.T, o, d, n, t, tri, status);
     return 1;
 }
 

@@ -7,10 +7,10 @@
 //      reached host memory and release their device memory;
 //   2. admit waiting requests in arrival order while their device memory
 //      fits the HBM budget and fewer than max_active are admitted;
-//   3. build one batch: every compensation request that still has steps
-//      renders its full image; relighting requests get up to
-//      quantum_samples each, fewest remaining samples first, until the
-//      iteration holds samples_per_iteration;
+//   3. build one batch of about samples_per_iteration samples: every
+//      relighting request first gets quantum_samples; compensation
+//      requests render their full images within half of the iteration;
+//      the rest goes to relighting requests in arrival order;
 //   4. enqueue on the server stream: the batch descriptors, one persistent
 //      k_render_batch launch, each compensation request's loss + path
 //      replay + Adam + PRF, the host copies of requests that finish in this
@@ -286,11 +286,10 @@ dpcs_status launch_iteration(dpcs_server *s, Batch &b) {
         }
     }
     if (comp.empty() && relight.empty()) return DPCS_OK;
-    std::stable_sort(relight.begin(), relight.end(),
-                     [](const Req *x, const Req *y) { return x->remaining_samples() < y->remaining_samples(); });
     int nseg = 0;
-    int64_t vb = 0, budget = s->cfg.samples_per_iteration;
-    const int cap = s->cfg.max_active;
+    int64_t vb = 0;
+    const int64_t total_budget = s->cfg.samples_per_iteration;
+    int64_t budget = total_budget;
     auto add_seg = [&](Req *q, int64_t pix0, int64_t npx) {
         b.descs_host[nseg] = q->args;
         BatchSeg &g = b.segs_host[nseg];
@@ -302,24 +301,43 @@ dpcs_status launch_iteration(dpcs_server *s, Batch &b) {
         vb += render_batch_vblocks(npx, q->args.log2L);
         ++nseg;
     };
+    // `active` is in arrival order.  1) every relighting request gets a small
+    // quantum, so short requests finish within an iteration or two;
+    std::vector<int64_t> give(relight.size(), 0);
+    for (size_t i = 0; i < relight.size() && budget > 0; ++i) {
+        Req *q = relight[i];
+        give[i] = std::min(q->npix - q->next_pix, std::max<int64_t>(1, s->cfg.quantum_samples / q->r.spp));
+        budget -= give[i] * q->r.spp;
+    }
+    // 2) compensation steps (full images) take at most half of the iteration;
+    int64_t comp_used = 0;
     for (Req *q : comp) {
-        if (nseg >= cap) break;
+        const int64_t need = q->npix * q->r.spp;
+        if (!b.steps.empty() && comp_used + need > total_budget / 2) break;
         // a fresh Philox key per step: step k uses seed + k
         q->args.key0 = (uint32_t)((q->r.seed + (uint64_t)q->steps_issued) & 0xffffffffu);
         q->args.key1 = (uint32_t)((q->r.seed + (uint64_t)q->steps_issued) >> 32);
         add_seg(q, 0, q->npix);
-        budget -= q->npix * q->r.spp;
+        comp_used += need;
         b.steps.push_back(q);
     }
-    for (Req *q : relight) {
-        if (nseg >= cap || (budget <= 0 && nseg > 0)) break;
-        const int64_t want = std::max<int64_t>(1, std::min(s->cfg.quantum_samples, std::max<int64_t>(budget, 1)) /
-                                                      q->r.spp);
-        const int64_t npx = std::min(q->npix - q->next_pix, want);
-        add_seg(q, q->next_pix, npx);
-        b.pixels.push_back({q, npx});
-        q->next_pix += npx;
-        budget -= npx * q->r.spp;
+    budget -= comp_used;
+    // 3) the rest goes to relighting requests in arrival order, so long
+    //    requests advance first-come first-served and none is starved.
+    for (size_t i = 0; i < relight.size() && budget > 0; ++i) {
+        Req *q = relight[i];
+        const int64_t extra = std::min(q->npix - q->next_pix - give[i], budget / q->r.spp);
+        if (extra > 0) {
+            give[i] += extra;
+            budget -= extra * q->r.spp;
+        }
+    }
+    for (size_t i = 0; i < relight.size(); ++i) {
+        if (give[i] <= 0) continue;
+        Req *q = relight[i];
+        add_seg(q, q->next_pix, give[i]);
+        b.pixels.push_back({q, give[i]});
+        q->next_pix += give[i];
     }
     cudaStream_t st = s->stream;
     cudaError_t e = cudaMemcpyAsync(b.descs_dev, b.descs_host, sizeof(RenderArgs) * nseg, cudaMemcpyHostToDevice, st);

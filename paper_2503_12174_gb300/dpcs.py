@@ -472,7 +472,7 @@ class Server:
     handed to submit() are kept alive here until the request is done."""
 
     def __init__(self, ctx: Context, hbm_budget_bytes: int = 0, max_active: int = 64, max_inflight: int = 2,
-                 samples_per_iteration: int = 48 << 20, quantum_samples: int = 8 << 20):
+                 samples_per_iteration: int = 48 << 20, quantum_samples: int = 2 << 20):
         self.ctx = ctx
         self.lib = ctx.lib
         cfg = DpcsServeConfig(int(hbm_budget_bytes), int(max_active), int(max_inflight), int(samples_per_iteration),
