@@ -47,7 +47,7 @@ L2_FLUSH_BYTES = 256 << 20
 # ncu capture summarised in profiles/k_render_corner256.md.  It holds only for
 # the kernel sources it was measured on; once they change, the roofline's
 # traffic is reported as null until a new capture is taken.
-RENDER_TRAFFIC = {"bytes": 62593792, "sources_sha256": "9ab0b53deeaa19fc01b03d31825a75efc71e0b7f3b4995fdc1a0128ff936b2e9"}
+RENDER_TRAFFIC = {"bytes": 63269888, "sources_sha256": "0b05ee9bd04406a44715b082a1193e1fa7a195ddc33d0eee40d8f7b95ecef225"}
 KERNEL_SOURCES = ("paper_2503_12174_gb300/csrc/render.cu", "paper_2503_12174_gb300/csrc/device.cuh",
                   "paper_2503_12174_gb300/csrc/internal.h")
 
@@ -85,6 +85,7 @@ def _args():
     ap.add_argument("--serve-requests", type=int, default=120, help="requests per serving run (0 = skip)")
     ap.add_argument("--serve-rates", default="5,8,11", help="Poisson arrival rates (requests/s) of the load sweep")
     ap.add_argument("--heightfield-steps", type=int, default=2, help="timed steps of the 200k-triangle workload (0 = skip)")
+    ap.add_argument("--comp-steps", type=int, default=100, help="Adam steps of the full compensation run (0 = skip)")
     return ap.parse_args()
 
 
@@ -241,8 +242,9 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_2503_12174_gb300 import build as _build
 
-    if rank == 0:
+    if rank == 0:  # one rank compiles; the others load what it built
         _build.build()
+        _build.build(variant="_counters", defines=("DPCS_COUNTERS",))
     if dist:
         dist.barrier()
     from paper_2503_12174_gb300 import dpcs, scenes
@@ -416,6 +418,32 @@ def main():
                 "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 FLOP/FMA x {sm_max_mhz:.0f} MHz (max SM clock)",
                 "counts_per_launch": counts}
 
+    # ------------------------------------------------------------ full compensation (Eq. 13): eager vs CUDA graph
+    comp_out = None
+    if args.comp_steps > 0:
+        from paper_2503_12174_gb300 import compensate
+
+        cmp_res = {}
+        for mode in ("eager", "graph"):
+            cm = compensate.Compensation(ctx, hc, calb, crough, cview, cprm, cs.spp, cs.bounces, args.comp_steps,
+                                         lr=1e-2, seed=4000 + rank, graph=(mode == "graph"))
+            init = torch.full((cs.Hp, cs.Wp, 3), 0.5, device=dev)
+            cm.run(init, target)
+            torch.cuda.synchronize()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(2)]
+            barrier()
+            for k in range(2):
+                ev[k][0].record(stream)
+                _, hist = cm.run(init, target)
+                ev[k][1].record(stream)
+            barrier()
+            ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev)) / 2
+            losses = hist.cpu().numpy()
+            cmp_res[mode] = {"ms": ms, "Msamples_per_s": cs.n_samples * args.comp_steps * ws / (ms / 1e3) / 1e6,
+                             "loss_first": float(losses[0]), "loss_last": float(losses[-1])}
+            del cm
+        comp_out = {"workload": f"{FWD_BWD_WORKLOAD}; {args.comp_steps} steps from Ip = 0.5", **cmp_res}
+
     # ------------------------------------------------------------ large displaced surface (T = 199,712)
     hf_out = None
     if args.heightfield_steps > 0:
@@ -520,6 +548,7 @@ def main():
                         "replay_kernel_ms": replay_ms / max(replay_n, 1),
                         "render_kernel_ms": crender_ms / max(crender_n, 1)},
             "roofline": roof,
+            "compensation": comp_out,
             "heightfield": hf_out,
             "serving": serving_out,
             "cpu_baseline": cpu,

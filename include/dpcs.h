@@ -138,6 +138,16 @@ dpcs_status dpcs_timing_read(dpcs_ctx *ctx, int32_t kernel, double *total_ms, in
 dpcs_status dpcs_counters_read(dpcs_ctx *ctx, uint64_t *out, int32_t reset);
 
 /*
+ * Failure-path testing: cap every ray's BVH traversal at `cap` steps in the
+ * render and replay calls that follow (0 restores the default, 2T + 16, which
+ * a correct tree never reaches).  A ray that reaches the cap ends as a miss
+ * and sets the status bit that dpcs_sync reports as
+ * DPCS_ERR_TRAVERSAL_LIMIT; nothing traps and the context stays usable.
+ * Not part of the paper's method.
+ */
+dpcs_status dpcs_debug_set_visit_cap(dpcs_ctx *ctx, int32_t cap);
+
+/*
  * Upload a triangle mesh and build its LBVH on the device (Morton codes of
  * triangle centroids, radix sort, Karras radix tree, bottom-up AABB refit).
  *  verts : host, V x 3 float32 positions (world = camera frame)

@@ -51,6 +51,7 @@ struct dpcs_ctx {
     // measurement support
     unsigned long long *counters = nullptr;  // 8 totals (DPCS_COUNTERS build)
     bool timing = false;
+    int32_t visit_cap = 0;  // debug override of the traversal visit cap
     std::vector<TimedLaunch> timed;
     size_t n_timed = 0;
 };
@@ -221,6 +222,7 @@ dpcs_status prepare(dpcs_ctx *c, dpcs_scene scene, const float *albedo, const fl
     while (l2 < 5 && (2 << l2) * kMinSamplesPerLane <= spp) ++l2;
     a.log2L = l2;
     a.status = c->status;
+    a.visit_cap = c->visit_cap;
 #ifdef DPCS_COUNTERS
     a.counters = c->counters;
 #else
@@ -312,6 +314,12 @@ dpcs_status dpcs_timing_read(dpcs_ctx *c, int32_t kernel, double *total_ms, int6
     }
     *total_ms = tot;
     *launches = n;
+    return DPCS_OK;
+}
+
+dpcs_status dpcs_debug_set_visit_cap(dpcs_ctx *c, int32_t cap) {
+    if (!c || cap < 0) return DPCS_ERR_INVALID_ARG;
+    c->visit_cap = cap;
     return DPCS_OK;
 }
 

@@ -392,9 +392,10 @@ __device__ __forceinline__ void trav_begin(Trav &st, int32_t root, float tmax, b
 
 __device__ __forceinline__ bool trav_resume(const float4 *__restrict__ nodes, const float4 *__restrict__ tris,
                                             int32_t root, int32_t T, const Ray &ray, Trav &st, int *stack,
-                                            unsigned *status, Cnt &cnt, int min_active) {
+                                            unsigned *status, Cnt &cnt, int min_active, int cap_override = 0) {
     if (root == kEmptyRoot) return true;
-    const int cap = 2 * T + 16;
+    // a correct tree needs at most T - 1 node and T leaf visits per ray
+    const int cap = cap_override > 0 ? cap_override : 2 * T + 16;
     bool first = true;
     while (true) {
         if (min_active > 0 && !first && __popc(__activemask()) < min_active) return false;

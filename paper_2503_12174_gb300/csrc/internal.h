@@ -59,6 +59,7 @@ struct RenderArgs {
     float4 *dtex;        // dLoss/d(albedo, rough) accumulators (Ht x Wt)
     unsigned *status;
     unsigned long long *counters;  // DPCS_COUNTERS build only (8 totals)
+    int32_t visit_cap;             // traversal steps per ray before giving up (0 = 2T + 16)
 };
 
 // One pixel range of one request in a batched render launch.

@@ -117,7 +117,7 @@ __device__ __forceinline__ void render_lanes(const RenderArgs &a, int64_t pix, i
             trav_begin(st, a.root, shadow ? tmax : INFINITY, shadow);
             pending = true;
         }
-        if (!trav_resume(a.nodes, a.tris, a.root, a.T, ray, st, stack, a.status, cnt, min(DPCS_YIELD_MIN, alive)))
+        if (!trav_resume(a.nodes, a.tris, a.root, a.T, ray, st, stack, a.status, cnt, min(DPCS_YIELD_MIN, alive), a.visit_cap))
             continue;
         pending = false;
         const bool hit = st.h.pos >= 0;
@@ -403,7 +403,7 @@ __global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB) k_replay(const
             trav_begin(st, a.root, shadow ? tmax : INFINITY, shadow);
             pending = true;
         }
-        if (!trav_resume(a.nodes, a.tris, a.root, a.T, ray, st, stack, a.status, cnt, min(DPCS_YIELD_MIN, alive)))
+        if (!trav_resume(a.nodes, a.tris, a.root, a.T, ray, st, stack, a.status, cnt, min(DPCS_YIELD_MIN, alive), a.visit_cap))
             continue;
         pending = false;
         const bool hit = st.h.pos >= 0;

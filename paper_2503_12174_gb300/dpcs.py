@@ -31,7 +31,7 @@ EXPORTED = [
     "dpcs_create", "dpcs_destroy", "dpcs_last_error", "dpcs_sync", "dpcs_memory_used", "dpcs_launch_count",
     "dpcs_scene_upload", "dpcs_scene_free", "dpcs_scene_export", "dpcs_trace", "dpcs_render",
     "dpcs_render_backward", "dpcs_l2_loss", "dpcs_adam", "dpcs_timing_enable", "dpcs_timing_read",
-    "dpcs_counters_read", "dpcs_render_noalloc", "dpcs_serve_create", "dpcs_serve_destroy", "dpcs_serve_add_scene",
+    "dpcs_counters_read", "dpcs_debug_set_visit_cap", "dpcs_render_noalloc", "dpcs_serve_create", "dpcs_serve_destroy", "dpcs_serve_add_scene",
     "dpcs_serve_submit", "dpcs_serve_step", "dpcs_serve_query", "dpcs_serve_drain", "dpcs_serve_stats_get",
 ]
 
@@ -112,6 +112,7 @@ _SIGS = {
     "dpcs_timing_read": (ctypes.c_int32, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_int64)]),
     "dpcs_counters_read": (ctypes.c_int32, [_P, _P, ctypes.c_int32]),
+    "dpcs_debug_set_visit_cap": (ctypes.c_int32, [_P, ctypes.c_int32]),
     "dpcs_serve_create": (ctypes.c_int32, [_P, ctypes.POINTER(DpcsServeConfig), ctypes.POINTER(_P)]),
     "dpcs_serve_destroy": (ctypes.c_int32, [_P]),
     "dpcs_serve_add_scene": (ctypes.c_int32, [_P, ctypes.c_uint64, _P, _P, ctypes.c_int32, ctypes.c_int32,
@@ -326,6 +327,10 @@ class Context:
     # -- measurement -------------------------------------------------------------
     def timing(self, on: bool):
         self.check(self.lib.dpcs_timing_enable(self.handle, 1 if on else 0), "timing_enable")
+
+    def set_visit_cap(self, cap: int):
+        """Failure-path testing: cap BVH traversal steps per ray (0 = default)."""
+        self.check(self.lib.dpcs_debug_set_visit_cap(self.handle, int(cap)), "debug_set_visit_cap")
 
     def counters(self, reset: bool = True):
         """Work counters (counters build only): dict of totals."""
