@@ -72,8 +72,10 @@ __device__ __forceinline__ float crf(float ec, float gain, float wb, float gamma
 // projector -- through the same traversal loop, then advances that lane's
 // path.  A lane whose path ends starts its next sample at once, so lanes of a
 // warp stay busy while their paths have different lengths (warp-level path
-// regeneration).  Each lane adds its paths in sample order; the per-vertex
-// arithmetic is the one of trace_path_rec.
+// regeneration).  Each lane adds its lit vertices' contributions to its
+// pixel sum in sample-then-vertex order; the per-vertex arithmetic
+// (surface_at, nee_prepare, continue_prepare) is shared with k_replay.
+//
 // The L lanes (L = 2^log2L, a divisor of 32) that share camera pixel `pix`:
 // lane `sl` traces samples sl, sl+L, ...; the lanes then combine their sums
 // and lane 0 writes Ec and Ic.  Every lane of the warp must call this (the
@@ -86,7 +88,9 @@ __device__ __forceinline__ void render_lanes(const RenderArgs &a, int64_t pix, i
     int s = valid ? sl : a.spp;
     int b = 1;
     bool shadow = false, has_ext = false, pending = false;
-    f3 beta = mk3(0.f, 0.f, 0.f), Lp = beta, c = beta, ed = beta;  // throughput, path sum, pending NEE, extension dir
+    // throughput, pending NEE contribution, extension direction; each lit
+    // vertex's contribution goes straight into the lane's pixel sum
+    f3 beta = mk3(0.f, 0.f, 0.f), c = beta, ed = beta;
     Ray ray;
     ray.o = ray.d = ray.inv = beta;
     float tmax = INFINITY;
@@ -124,7 +128,7 @@ __device__ __forceinline__ void render_lanes(const RenderArgs &a, int64_t pix, i
         bool end = false;
         if (shadow) {
             if (!hit) {
-                Lp = Lp + c;
+                sum = sum + c;
                 cnt.add(kCntLit);
             }
             shadow = false;
@@ -167,14 +171,12 @@ __device__ __forceinline__ void render_lanes(const RenderArgs &a, int64_t pix, i
             }
         }
         if (end) {
-            sum = sum + Lp;
             s += L;
             if (s < a.spp) {
                 f3 o, d;
                 camera_ray(a, (uint32_t)pix, (uint32_t)s, o, d);
                 ray = make_ray(o, d);
                 beta = mk3(1.f, 1.f, 1.f);
-                Lp = mk3(0.f, 0.f, 0.f);
                 b = 1;
                 shadow = false;
                 has_ext = false;
