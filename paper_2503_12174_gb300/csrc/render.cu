@@ -46,6 +46,48 @@ __device__ __forceinline__ void atomic_add4(float4 *p, float4 v) {
 #endif
 }
 
+#ifndef DPCS_WARP_PREREDUCE
+// Combine same-texel gradient scatters of a warp before the atomic.  Off: on
+// GB300 the vote and warp syncs inside the divergent sweep cost more (replay
+// +14 % at 16 spp, +23 % at 64 spp) than the float4 atomics they save (the
+// atomics take 5-7 % of the replay).
+#define DPCS_WARP_PREREDUCE 0
+#endif
+
+// Gradient scatter with warp pre-reduction: when every lane taking part adds
+// to the same texel (typical at a pixel's first vertex, where the L lanes of
+// the pixel hit nearly the same point), the lanes sum their values through a
+// per-warp shared-memory row and one lane issues the float4 atomic;
+// otherwise each lane adds its own value.  `row` is this warp's 32 float4.
+__device__ __forceinline__ void scatter_add4(float4 *base, int key, float4 v, float4 *row) {
+#if DPCS_WARP_PREREDUCE
+    const unsigned active = __activemask();
+    int same = 0;
+    __match_all_sync(active, key, &same);
+    if (same && (active & (active - 1u)) != 0u) {
+        const int lane = threadIdx.x & 31;
+        row[lane] = v;
+        __syncwarp(active);
+        if (lane == __ffs(active) - 1) {
+            float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (unsigned m = active; m; m &= m - 1u) {
+                const float4 o = row[__ffs(m) - 1];
+                t.x += o.x;
+                t.y += o.y;
+                t.z += o.z;
+                t.w += o.w;
+            }
+            atomic_add4(base + key, t);
+        }
+        __syncwarp(active);  // the row is reused by the next scatter
+        return;
+    }
+#else
+    (void)row;
+#endif
+    atomic_add4(base + key, v);
+}
+
 __global__ void k_prf(const float *__restrict__ Ip, int64_t ntex, float g0, float g1, float g2, float gain,
                       float4 *__restrict__ Ep) {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -316,7 +358,8 @@ __global__ void k_crf_backward(const float *__restrict__ dIc, const float *__res
 // derivative of the path radiance with respect to the throughput entering
 // the next vertex (A_c = [lit] f(wp) Ep G + f(wi) cw A_{c+1}), scatter
 // dLoss/dEp, dLoss/dalbedo and dLoss/droughness into the accumulators.
-__device__ __forceinline__ void replay_sweep(const RenderArgs &a, const VRec *rec, int nv, const float gb_in[3]) {
+__device__ __forceinline__ void replay_sweep(const RenderArgs &a, const VRec *rec, int nv, const float gb_in[3],
+                                             float4 *row) {
     float A[3] = {0.f, 0.f, 0.f};
     for (int c = nv - 1; c >= 0; --c) {
         const VRec &R = rec[c];
@@ -343,14 +386,14 @@ __device__ __forceinline__ void replay_sweep(const RenderArgs &a, const VRec *re
         bilin_taps(tb, a.Wt, a.Ht, idx, w);
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-            atomic_add4(a.dtex + idx[k], make_float4(ga[0] * w[k], ga[1] * w[k], ga[2] * w[k], dr * w[k]));
+            scatter_add4(a.dtex, idx[k], make_float4(ga[0] * w[k], ga[1] * w[k], ga[2] * w[k], dr * w[k]), row);
         if (R.G > 0.0f && (dEp[0] != 0.0f || dEp[1] != 0.0f || dEp[2] != 0.0f)) {
             Bilin pb;
             pb.x0 = R.px0; pb.y0 = R.py0; pb.fx = R.pfx; pb.fy = R.pfy;
             bilin_taps(pb, a.Wp, a.Hp, idx, w);
 #pragma unroll
             for (int k = 0; k < 4; ++k)
-                atomic_add4(a.dEp + idx[k], make_float4(dEp[0] * w[k], dEp[1] * w[k], dEp[2] * w[k], 0.0f));
+                scatter_add4(a.dEp, idx[k], make_float4(dEp[0] * w[k], dEp[1] * w[k], dEp[2] * w[k], 0.0f), row);
         }
     }
 }
@@ -373,6 +416,7 @@ __global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB) k_replay(const
         gb_in[2] = a.gE[3 * pix + 2] * inv;
     }
     const bool any = gb_in[0] != 0.0f || gb_in[1] != 0.0f || gb_in[2] != 0.0f;
+    __shared__ float4 s_row[kRenderBlock];  // per-warp rows for scatter_add4
     int s = (pix < npix && any) ? sl : a.spp;
     int b = 1, nv = 0;
     bool shadow = false, has_ext = false, pending = false;
@@ -462,7 +506,7 @@ __global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB) k_replay(const
             }
         }
         if (end) {
-            replay_sweep(a, rec, nv, gb_in);
+            replay_sweep(a, rec, nv, gb_in, &s_row[threadIdx.x & ~31]);
             nv = 0;
             s += L;
             if (s < a.spp) {
