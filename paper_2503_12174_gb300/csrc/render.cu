@@ -31,6 +31,9 @@ constexpr int kRenderBlock = 128;
 // (0): on GB300 yielding at 8..24 lanes cost 1.6-2x more than it recovered.
 #define DPCS_YIELD_MIN 0
 #endif
+#ifndef DPCS_BATCH_MINB
+#define DPCS_BATCH_MINB 8  // resident blocks per SM for the batched render: it reads its arguments from shared memory and needs the registers
+#endif
 #ifndef DPCS_RENDER_MINB
 #define DPCS_RENDER_MINB 10  // minimum resident blocks per SM requested from ptxas (48 registers; sweep: 9-12 within 3 %)
 #endif
@@ -259,7 +262,7 @@ __global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB) k_render(const
 // are descs[slot].  Per pixel the computation is render_lanes, exactly as in
 // k_render.  The loop ends when the counter passes the last virtual block:
 // there is no waiting on other CTAs.
-__global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB)
+__global__ void __launch_bounds__(kRenderBlock, DPCS_BATCH_MINB)
     k_render_batch(const RenderArgs *__restrict__ descs, const BatchSeg *__restrict__ segs, int nseg,
                    int64_t total_vb, unsigned long long *counter) {
     __shared__ RenderArgs sa;
