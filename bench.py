@@ -47,7 +47,7 @@ L2_FLUSH_BYTES = 256 << 20
 # ncu capture summarised in profiles/k_render_corner256.md.  It holds only for
 # the kernel sources it was measured on; once they change, the roofline's
 # traffic is reported as null until a new capture is taken.
-RENDER_TRAFFIC = {"bytes": 63269888, "sources_sha256": "0b05ee9bd04406a44715b082a1193e1fa7a195ddc33d0eee40d8f7b95ecef225"}
+RENDER_TRAFFIC = {"bytes": 41101312, "sources_sha256": "9e1ee8808e6ad4d373d6eb14a54b4e3ac2308b054eae4e055114bac0499a859f"}
 KERNEL_SOURCES = ("paper_2503_12174_gb300/csrc/render.cu", "paper_2503_12174_gb300/csrc/device.cuh",
                   "paper_2503_12174_gb300/csrc/internal.h")
 
