@@ -47,7 +47,7 @@ L2_FLUSH_BYTES = 256 << 20
 # ncu capture summarised in profiles/k_render_corner256.md.  It holds only for
 # the kernel sources it was measured on; once they change, the roofline's
 # traffic is reported as null until a new capture is taken.
-RENDER_TRAFFIC = {"bytes": 41101312, "sources_sha256": "9e1ee8808e6ad4d373d6eb14a54b4e3ac2308b054eae4e055114bac0499a859f"}
+RENDER_TRAFFIC = {"bytes": 41291776, "sources_sha256": "ee105f7f1d2e448d3dc51c6115df4375f7e4c2577a3ef4c581d28d1d14668b70"}
 KERNEL_SOURCES = ("paper_2503_12174_gb300/csrc/render.cu", "paper_2503_12174_gb300/csrc/device.cuh",
                   "paper_2503_12174_gb300/csrc/internal.h")
 
@@ -71,6 +71,14 @@ FLOP = {
     "lit": 160,            # bilinear Ep, geometry term, GGX evaluation with roughness derivative, contribution
     "continuations": 230,  # frame, lobe sample (cosine or visible-normal GGX), pdf, BRDF, throughput
 }
+# bytes each unit of work loads through L1 (128-bit loads of the layouts in
+# csrc/internal.h): a 64-byte node, a 48-byte triangle, three 8-byte UVs,
+# four 16-byte texels for albedo+roughness and four for Ep
+LOAD_BYTES = {"node_visits": 64, "tri_tests": 48, "vertices": 24 + 4 * 16, "lit": 4 * 16}
+# the probes' sizes: a buffer that stays in L2 like the scene and textures, and
+# the 512 x 512 gradient texture the compensation replay scatters into
+PROBE_L2_BYTES = 32 << 20
+PROBE_ATOMIC_TEXELS = 512 * 512
 
 
 def _args():
@@ -395,10 +403,21 @@ def main():
         cctx.counters(reset=True)
         cctx.render(ch, alb, rough, Ip, view, prm, sc.spp, sc.bounces, sc.seed, Ic=torch.empty_like(Ic))
         counts = cctx.counters(reset=True)
+        # the replay of one compensation step: its float4 atomic scatters
+        cch = cctx.upload(cs.verts, cs.tris, cs.uv)
+        cctx.render(cch, calb, crough, P, cview, cprm, cs.spp, cs.bounces, cs.seed + 1, Ic=cIc, Ec=cEc)
+        cctx.counters(reset=True)
+        cctx.render_backward(cch, calb, crough, P, cview, cprm, cs.spp, cs.bounces, cs.seed + 1, cEc, cIc, dIc,
+                             dIp=torch.zeros_like(P))
+        replay_counts = cctx.counters(reset=True)
         cctx.close()
         flops = sum(FLOP[k] * counts[k] for k in FLOP)
     except Exception as e:  # the roofline stays unreported rather than guessed
         counts = {"error": str(e)[:200]}
+        replay_counts = None
+    # measured roofs the driver's peaks file lacks: L2 load bandwidth and scattered float4 atomics
+    l2_gbs = ctx.probe_l2_load(PROBE_L2_BYTES, 256)
+    atomic_g = ctx.probe_atomic4(PROBE_ATOMIC_TEXELS, 1 << 28)
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
     peaks = {}
@@ -409,7 +428,25 @@ def main():
     sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     peak_tflops = sms * 128 * 2 * sm_max_mhz * 1e6 / 1e12
     roof = None
+    roof_load = None
+    roof_atomic = None
     if flops:
+        lbytes = sum(LOAD_BYTES[k] * counts[k] for k in LOAD_BYTES)
+        l_tbs = lbytes / (kernel_ms / 1e3) / 1e12
+        roof_load = {"bound": "l2", "kernel": "k_render", "achieved": l_tbs, "peak": l2_gbs / 1e3, "unit": "TB/s",
+                     "frac": l_tbs / (l2_gbs / 1e3), "bytes_per_launch": lbytes,
+                     "peak_basis": f"measured: dpcs_probe_l2_load, {PROBE_L2_BYTES >> 20} MiB read with 16 B "
+                                   "L2-only loads, best of 3",
+                     "l1_nominal_peak": sms * 128 * sm_max_mhz * 1e6 / 1e12}
+    if replay_counts and replay_n:
+        n_atom = 4 * (replay_counts["vertices"] + replay_counts["lit"])
+        r_ms = replay_ms / replay_n
+        roof_atomic = {"bound": "atomic", "kernel": "k_replay", "achieved": n_atom / (r_ms / 1e3) / 1e9,
+                       "peak": atomic_g, "unit": "Gatomics/s", "frac": n_atom / (r_ms / 1e3) / 1e9 / atomic_g,
+                       "atomics_per_launch": n_atom, "kernel_ms": r_ms,
+                       "peak_basis": f"measured: dpcs_probe_atomic4, float4 adds at random texels of a "
+                                     f"{PROBE_ATOMIC_TEXELS}-texel buffer, best of 3",
+                       "counts_per_launch": replay_counts}
         achieved = flops / (kernel_ms / 1e3) / 1e12
         traffic = RENDER_TRAFFIC["bytes"] if RENDER_TRAFFIC["sources_sha256"] == kernel_sources_sha256() else None
         roof = {"bound": "alu", "kernel": "k_render", "achieved": achieved, "peak": peak_tflops,
@@ -548,6 +585,8 @@ def main():
                         "replay_kernel_ms": replay_ms / max(replay_n, 1),
                         "render_kernel_ms": crender_ms / max(crender_n, 1)},
             "roofline": roof,
+            "roofline_load": roof_load,
+            "roofline_atomic": roof_atomic,
             "compensation": comp_out,
             "heightfield": hf_out,
             "serving": serving_out,

@@ -138,6 +138,29 @@ dpcs_status dpcs_timing_read(dpcs_ctx *ctx, int32_t kernel, double *total_ms, in
 dpcs_status dpcs_counters_read(dpcs_ctx *ctx, uint64_t *out, int32_t reset);
 
 /*
+ * Roof probes: measurement helpers with no counterpart in the paper.  The
+ * render and replay kernels load a scene and textures that stay resident in
+ * L2, and the replay scatters gradients with float4 atomics; these calls
+ * measure both rates on ctx's device so the kernels' rooflines can be stated
+ * against them.  Each call allocates its own device buffer (outside the HBM
+ * budget) for the call's duration, runs on the legacy default stream, times
+ * the best of three launches after one warm-up with CUDA events, and
+ * returns after synchronising.
+ *
+ * dpcs_probe_l2_load: reads a zeroed `bytes` buffer `passes` times with
+ * 16-byte loads that cache in L2 only; *gbs = bytes * passes / time in GB/s.
+ * bytes must be a positive multiple of 16 up to 64 MiB (so it stays in L2)
+ * and passes in [1, 4096], else DPCS_ERR_INVALID_ARG.
+ *
+ * dpcs_probe_atomic4: about n_atomics float4 atomic adds (rounded up to a
+ * whole number per thread) at pseudo-random texels of a `texels`-entry float4
+ * buffer, so the lanes of a warp hit unrelated addresses; *gatomics = adds
+ * per second / 1e9.  texels in [1, 2^24], n_atomics in [1, 2^34].
+ */
+dpcs_status dpcs_probe_l2_load(dpcs_ctx *ctx, size_t bytes, int32_t passes, double *gbs);
+dpcs_status dpcs_probe_atomic4(dpcs_ctx *ctx, int32_t texels, int64_t n_atomics, double *gatomics);
+
+/*
  * Failure-path testing: cap every ray's BVH traversal at `cap` steps in the
  * render and replay calls that follow (0 restores the default, 2T + 16, which
  * a correct tree never reaches).  A ray that reaches the cap ends as a miss
@@ -240,7 +263,9 @@ dpcs_status dpcs_render_noalloc(dpcs_ctx *ctx, dpcs_scene scene, const float *al
  *  dParams : dev, 11 float32 [gamma_p(3), gain_p, gamma_c(3), gain_c, wb(3)]
  *            (may be NULL)
  * These are the gradients of the scene parameters theta of Eq. 9 that do not
- * move geometry, and of the projector input of Eq. 13.
+ * move geometry, and of the projector input of Eq. 13.  With dAlbedo and
+ * dRough both NULL the replay skips the texture scatters (compensation
+ * needs only dIp); the other outputs are unchanged.
  */
 dpcs_status dpcs_render_backward(dpcs_ctx *ctx, dpcs_scene scene, const float *albedo, const float *rough,
                                  int32_t Ht, int32_t Wt, const float *Ip, const dpcs_view *view,
@@ -278,14 +303,16 @@ dpcs_status dpcs_adam(dpcs_ctx *ctx, float *p, const float *g, float *m, float *
  * A server owns a CUDA stream and device memory for admitted requests.  Each
  * dpcs_serve_step is one scheduler iteration: it retires finished work,
  * admits waiting requests (FIFO) while their device memory fits the HBM
- * budget and fewer than max_active are admitted, and launches one batched
- * render of about samples_per_iteration camera samples: every active
- * relighting request first gets quantum_samples (so short requests finish
- * within an iteration or two), compensation requests render their full
- * images within half of the iteration, and the rest goes to relighting
- * requests in arrival order; the compensation requests' loss, path-replay
- * adjoint and Adam step follow on the same stream.  Requests that arrive while others run join at the next
- * iteration.  A pixel's result is computed exactly as dpcs_render computes
+ * budget and fewer than max_active are admitted, and plans about
+ * samples_per_iteration camera samples of work: every active relighting
+ * request first gets quantum_samples (so short requests finish within an
+ * iteration or two); then one compensation step per request (a full-image
+ * render, loss, path-replay adjoint and Adam step) within half of the
+ * iteration's samples; the rest goes to relighting
+ * requests in arrival order, and budget that relighting leaves unused runs
+ * further consecutive compensation steps, still within that half.  The relighting pixels run as one batched
+ * render; the compensation steps follow on the same stream.  Requests that
+ * arrive while others run join at the next iteration.  A pixel's result is computed exactly as dpcs_render computes
  * it, whatever else is in the batch.  Waits are bounded; nothing spins on
  * the GPU.  A server is not thread safe; use it from one host thread.
  */

@@ -524,14 +524,15 @@ dpcs_status dpcs_render_backward(dpcs_ctx *c, dpcs_scene scene, const float *alb
         (s = ensure(c, c->tex4, (size_t)nt * 16, "texture scratch")) ||
         (s = ensure(c, c->gE, (size_t)npix * 12, "dEc scratch")) ||
         (s = ensure(c, c->dEp4, (size_t)np * 16, "dEp scratch")) ||
-        (s = ensure(c, c->dtex4, (size_t)nt * 16, "dtex scratch")) ||
         (s = ensure(c, c->acc, 16 * sizeof(double), "parameter accumulators")))
         return s;
+    const bool want_tex = dAlbedo || dRough;  // otherwise the replay skips the texture scatters
+    if (want_tex && (s = ensure(c, c->dtex4, (size_t)nt * 16, "dtex scratch"))) return s;
     cudaStream_t st = (cudaStream_t)stream;
     double *acc = (double *)c->acc.p;
     cudaMemsetAsync(acc, 0, 16 * sizeof(double), st);
     cudaMemsetAsync(c->dEp4.p, 0, (size_t)np * 16, st);
-    cudaMemsetAsync(c->dtex4.p, 0, (size_t)nt * 16, st);
+    if (want_tex) cudaMemsetAsync(c->dtex4.p, 0, (size_t)nt * 16, st);
     int nl = launch_prf(Ip, np, params->gamma_p, params->gain_p, (float4 *)c->ep4.p, st);
     nl += launch_pack_tex(albedo, rough, nt, (float4 *)c->tex4.p, st);
     nl += launch_crf_backward(dIc, Ec, Ic, npix, params->gamma_c, params->gain_c, params->wb, (float *)c->gE.p, acc, st);
@@ -539,12 +540,12 @@ dpcs_status dpcs_render_backward(dpcs_ctx *c, dpcs_scene scene, const float *alb
     a.tex = (const float4 *)c->tex4.p;
     a.gE = (const float *)c->gE.p;
     a.dEp = (float4 *)c->dEp4.p;
-    a.dtex = (float4 *)c->dtex4.p;
+    a.dtex = want_tex ? (float4 *)c->dtex4.p : nullptr;
     TimedLaunch *tl = timing_begin(c, 1, st);
     nl += launch_replay(a, st);
     timing_end(tl, st);
     nl += launch_prf_backward(Ip, (const float4 *)c->dEp4.p, np, params->gamma_p, params->gain_p, dIp, acc, st);
-    if (dAlbedo || dRough) nl += launch_tex_backward((const float4 *)c->dtex4.p, nt, dAlbedo, dRough, st);
+    if (want_tex) nl += launch_tex_backward((const float4 *)c->dtex4.p, nt, dAlbedo, dRough, st);
     if (dParams) nl += launch_finalize_params(acc, dParams, st);
     return check_launch(c, nl, "render_backward");
 }

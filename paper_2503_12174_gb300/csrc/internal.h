@@ -56,7 +56,7 @@ struct RenderArgs {
     // backward only
     const float *gE;     // dLoss/dEc per pixel (Hc x Wc x 3)
     float4 *dEp;         // dLoss/dEp accumulators (Hp x Wp)
-    float4 *dtex;        // dLoss/d(albedo, rough) accumulators (Ht x Wt)
+    float4 *dtex;        // dLoss/d(albedo, rough) accumulators (Ht x Wt); null = not wanted
     unsigned *status;
     unsigned long long *counters;  // DPCS_COUNTERS build only (8 totals)
     int32_t visit_cap;             // traversal steps per ray before giving up (0 = 2T + 16)

@@ -384,12 +384,14 @@ __device__ __forceinline__ void replay_sweep(const RenderArgs &a, const VRec *re
         }
         int idx[4];
         float w[4];
-        Bilin tb;
-        tb.x0 = R.tx0; tb.y0 = R.ty0; tb.fx = R.tfx; tb.fy = R.tfy;
-        bilin_taps(tb, a.Wt, a.Ht, idx, w);
+        if (a.dtex) {  // null when the caller wants no texture gradient
+            Bilin tb;
+            tb.x0 = R.tx0; tb.y0 = R.ty0; tb.fx = R.tfx; tb.fy = R.tfy;
+            bilin_taps(tb, a.Wt, a.Ht, idx, w);
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-            scatter_add4(a.dtex, idx[k], make_float4(ga[0] * w[k], ga[1] * w[k], ga[2] * w[k], dr * w[k]), row);
+            for (int k = 0; k < 4; ++k)
+                scatter_add4(a.dtex, idx[k], make_float4(ga[0] * w[k], ga[1] * w[k], ga[2] * w[k], dr * w[k]), row);
+        }
         if (R.G > 0.0f && (dEp[0] != 0.0f || dEp[1] != 0.0f || dEp[2] != 0.0f)) {
             Bilin pb;
             pb.x0 = R.px0; pb.y0 = R.py0; pb.fx = R.pfx; pb.fy = R.pfy;

@@ -7,12 +7,15 @@
 //      reached host memory and release their device memory;
 //   2. admit waiting requests in arrival order while their device memory
 //      fits the HBM budget and fewer than max_active are admitted;
-//   3. build one batch of about samples_per_iteration samples: every
-//      relighting request first gets quantum_samples; compensation
-//      requests render their full images within half of the iteration;
-//      the rest goes to relighting requests in arrival order;
+//   3. plan about samples_per_iteration samples of work: every relighting
+//      request first gets quantum_samples; then one compensation step per
+//      request (a full image) within half of the iteration's samples; the
+//      rest goes to relighting requests in arrival order, and what
+//      relighting leaves unused runs further consecutive compensation
+//      steps, still within that half;
 //   4. enqueue on the server stream: the batch descriptors, one persistent
-//      k_render_batch launch, each compensation request's loss + path
+//      k_render_batch launch over the relighting pixels, each compensation
+//      request's render (a whole image, one k_render launch) + loss + path
 //      replay + Adam + PRF, the host copies of requests that finish in this
 //      batch, and the iteration's completion event.
 // Everything runs on one stream, so a compensation step always sees the
@@ -63,7 +66,7 @@ struct Req {
     // device buffers (sub-allocations of mem)
     float *Ip = nullptr, *Ic = nullptr, *Ec = nullptr, *target = nullptr, *dIc = nullptr, *gE = nullptr;
     float *M = nullptr, *V = nullptr, *G = nullptr, *loss = nullptr;
-    float4 *Ep4 = nullptr, *dEp4 = nullptr, *dtex4 = nullptr;
+    float4 *Ep4 = nullptr, *dEp4 = nullptr;
     double *acc = nullptr, *partial = nullptr;
     RenderArgs args{};
     int64_t npix = 0, next_pix = 0, pix_done = 0;
@@ -94,6 +97,7 @@ struct dpcs_server {
     int device = 0;
     dpcs_serve_config cfg{};
     cudaStream_t stream = nullptr;
+    cudaMemPool_t pool = nullptr;  // request memory; keeps what requests free for the next admissions
     std::vector<ServeScene> scenes;
     std::deque<Req *> waiting;
     std::vector<Req *> active;
@@ -118,11 +122,11 @@ dpcs_status scuda(dpcs_server *s, cudaError_t e, const char *what) {
 // device bytes a request holds while admitted
 size_t request_bytes(const dpcs_server *s, const dpcs_request &r) {
     const ServeScene &sc = s->scenes[r.scene];
-    const size_t np = (size_t)sc.view.Hp * sc.view.Wp, npix = (size_t)r.Hc * r.Wc, nt = (size_t)sc.Ht * sc.Wt;
+    const size_t np = (size_t)sc.view.Hp * sc.view.Wp, npix = (size_t)r.Hc * r.Wc;
     size_t b = al256(np * 12) + al256(np * 16) + al256(npix * 12);  // Ip, Ep4, Ic
-    if (r.kind == DPCS_REQ_COMPENSATE)
-        b += 4 * al256(npix * 12) + 3 * al256(np * 12) + al256(np * 16) + al256(nt * 16) + al256(16 * 8) +
-             al256(4) + al256((size_t)l2_partial_slots() * 8);  // Ec target dIc gE; M V G; dEp4; dtex4; acc; loss
+    if (r.kind == DPCS_REQ_COMPENSATE)  // compensation moves Ip only: no texture gradient is kept
+        b += 4 * al256(npix * 12) + 3 * al256(np * 12) + al256(np * 16) + al256(16 * 8) + al256(4) +
+             al256((size_t)l2_partial_slots() * 8);  // Ec target dIc gE; M V G; dEp4; acc; loss
     return b;
 }
 
@@ -139,11 +143,11 @@ dpcs_view request_view(const ServeScene &sc, const dpcs_request &r) {
 dpcs_status admit(dpcs_server *s, Req *q) {
     const ServeScene &sc = s->scenes[q->r.scene];
     const dpcs_request &r = q->r;
-    const size_t np = (size_t)sc.view.Hp * sc.view.Wp, npix = (size_t)r.Hc * r.Wc, nt = (size_t)sc.Ht * sc.Wt;
-    cudaError_t e = cudaMallocAsync((void **)&q->mem, q->bytes, s->stream);
+    const size_t np = (size_t)sc.view.Hp * sc.view.Wp, npix = (size_t)r.Hc * r.Wc;
+    cudaError_t e = cudaMallocFromPoolAsync((void **)&q->mem, q->bytes, s->pool, s->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        return sfail(s, DPCS_ERR_OOM, "serve: cudaMallocAsync failed");
+        return sfail(s, DPCS_ERR_OOM, "serve: stream-ordered allocation failed");
     }
     s->used += q->bytes;  // released with the memory in release()
     s->high_water = std::max(s->high_water, s->used);
@@ -165,7 +169,6 @@ dpcs_status admit(dpcs_server *s, Req *q) {
         q->V = (float *)take(np * 12);
         q->G = (float *)take(np * 12);
         q->dEp4 = (float4 *)take(np * 16);
-        q->dtex4 = (float4 *)take(nt * 16);
         q->acc = (double *)take(16 * 8);
         q->loss = (float *)take(4);
         q->partial = (double *)take((size_t)l2_partial_slots() * 8);
@@ -194,19 +197,18 @@ dpcs_status admit(dpcs_server *s, Req *q) {
 // adjoint, Adam on Ip with the clamp to [0, 1], then Ep for the next render
 int enqueue_comp_backward(dpcs_server *s, Req *q) {
     const ServeScene &sc = s->scenes[q->r.scene];
-    const int64_t np = (int64_t)sc.view.Hp * sc.view.Wp, nt = (int64_t)sc.Ht * sc.Wt;
+    const int64_t np = (int64_t)sc.view.Hp * sc.view.Wp;
     cudaStream_t st = s->stream;
     int n = launch_l2_loss(q->Ic, q->target, q->npix * 3, q->dIc, q->loss, q->partial, st);
     cudaMemsetAsync(q->acc, 0, 16 * 8, st);
     cudaMemsetAsync(q->dEp4, 0, (size_t)np * 16, st);
-    cudaMemsetAsync(q->dtex4, 0, (size_t)nt * 16, st);
     cudaMemsetAsync(q->G, 0, (size_t)np * 12, st);
     n += launch_crf_backward(q->dIc, q->Ec, q->Ic, q->npix, sc.params.gamma_c, sc.params.gain_c, sc.params.wb, q->gE,
                              q->acc, st);
     RenderArgs a = q->args;
     a.gE = q->gE;
     a.dEp = q->dEp4;
-    a.dtex = q->dtex4;
+    a.dtex = nullptr;  // only Ip is optimised
     n += launch_replay(a, st);
     n += launch_prf_backward(q->Ip, q->dEp4, np, sc.params.gamma_p, sc.params.gain_p, q->G, q->acc, st);
     n += launch_adam(q->Ip, q->G, q->M, q->V, np * 3, q->r.lr, 0.9f, 0.999f, 1e-8f, q->steps_issued, 0.0f, 1.0f, st);
@@ -309,27 +311,43 @@ dpcs_status launch_iteration(dpcs_server *s, Batch &b) {
         give[i] = std::min(q->npix - q->next_pix, std::max<int64_t>(1, s->cfg.quantum_samples / q->r.spp));
         budget -= give[i] * q->r.spp;
     }
-    // 2) compensation steps (full images) take at most half of the iteration;
+    // 2) one compensation step per request in arrival order (a full image)
+    //    within half of the iteration's samples;
+    const int64_t comp_cap = total_budget / 2;
     int64_t comp_used = 0;
     for (Req *q : comp) {
         const int64_t need = q->npix * q->r.spp;
-        if (!b.steps.empty() && comp_used + need > total_budget / 2) break;
-        // a fresh Philox key per step: step k uses seed + k
-        q->args.key0 = (uint32_t)((q->r.seed + (uint64_t)q->steps_issued) & 0xffffffffu);
-        q->args.key1 = (uint32_t)((q->r.seed + (uint64_t)q->steps_issued) >> 32);
-        add_seg(q, 0, q->npix);
+        if (!b.steps.empty() && comp_used + need > comp_cap) break;
         comp_used += need;
         b.steps.push_back(q);
     }
     budget -= comp_used;
     // 3) the rest goes to relighting requests in arrival order, so long
-    //    requests advance first-come first-served and none is starved.
+    //    requests advance first-come first-served and none is starved;
     for (size_t i = 0; i < relight.size() && budget > 0; ++i) {
         Req *q = relight[i];
         const int64_t extra = std::min(q->npix - q->next_pix - give[i], budget / q->r.spp);
         if (extra > 0) {
             give[i] += extra;
             budget -= extra * q->r.spp;
+        }
+    }
+    // 4) budget that relighting left unused runs further consecutive steps of
+    //    the same compensation requests, in rounds, still within half of the
+    //    iteration (rounds keep each request's steps in order on the stream).
+    const size_t n_first = b.steps.size();
+    std::vector<int> planned(n_first, 1);
+    for (bool more = true; more;) {
+        more = false;
+        for (size_t i = 0; i < n_first; ++i) {
+            Req *q = b.steps[i];
+            const int64_t need = q->npix * q->r.spp;
+            if (q->steps_issued + planned[i] >= q->r.steps || comp_used + need > comp_cap || need > budget) continue;
+            comp_used += need;
+            budget -= need;
+            b.steps.push_back(q);
+            ++planned[i];
+            more = true;
         }
     }
     for (size_t i = 0; i < relight.size(); ++i) {
@@ -340,12 +358,22 @@ dpcs_status launch_iteration(dpcs_server *s, Batch &b) {
         q->next_pix += give[i];
     }
     cudaStream_t st = s->stream;
-    cudaError_t e = cudaMemcpyAsync(b.descs_dev, b.descs_host, sizeof(RenderArgs) * nseg, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(b.segs_dev, b.segs_host, sizeof(BatchSeg) * nseg, cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(b.counter, 0, sizeof(unsigned long long), st);
-    if (e != cudaSuccess) return scuda(s, e, "serve: batch upload");
-    int n = launch_render_batch(b.descs_dev, b.segs_dev, nseg, vb, b.counter, s->grid, st);
+    cudaError_t e = cudaSuccess;
+    int n = 0;
+    if (nseg > 0) {
+        e = cudaMemcpyAsync(b.descs_dev, b.descs_host, sizeof(RenderArgs) * nseg, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(b.segs_dev, b.segs_host, sizeof(BatchSeg) * nseg, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(b.counter, 0, sizeof(unsigned long long), st);
+        if (e != cudaSuccess) return scuda(s, e, "serve: batch upload");
+        n += launch_render_batch(b.descs_dev, b.segs_dev, nseg, vb, b.counter, s->grid, st);
+    }
     for (Req *q : b.steps) {
+        // a fresh Philox key per step (step k uses seed + k); a whole image is
+        // one k_render launch, whose arguments sit in constant space
+        q->args.key0 = (uint32_t)((q->r.seed + (uint64_t)q->steps_issued) & 0xffffffffu);
+        q->args.key1 = (uint32_t)((q->r.seed + (uint64_t)q->steps_issued) >> 32);
+        n += launch_render(q->args, st);
         q->steps_issued++;
         n += enqueue_comp_backward(s, q);
         if (q->steps_issued == q->r.steps) {
@@ -395,6 +423,17 @@ dpcs_status dpcs_serve_create(dpcs_ctx *ctx, const dpcs_serve_config *cfg, dpcs_
     s->device = ctx_device(ctx);
     cudaError_t e = cudaSetDevice(s->device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) {
+        // a pool of its own whose freed memory is never trimmed back to the
+        // driver, so admissions after the first reuse mapped memory
+        cudaMemPoolProps pp{};
+        pp.allocType = cudaMemAllocationTypePinned;
+        pp.location.type = cudaMemLocationTypeDevice;
+        pp.location.id = s->device;
+        e = cudaMemPoolCreate(&s->pool, &pp);
+        uint64_t keep = ~0ull;
+        if (e == cudaSuccess) e = cudaMemPoolSetAttribute(s->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
     s->batches.resize(cfg->max_inflight);
     for (Batch &b : s->batches) {
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.ev, cudaEventDisableTiming);
@@ -408,6 +447,7 @@ dpcs_status dpcs_serve_create(dpcs_ctx *ctx, const dpcs_serve_config *cfg, dpcs_
         dpcs_status st = ctx_fail(ctx, DPCS_ERR_CUDA, "serve: create failed");
         for (Batch &b : s->batches) free_batch_bufs(b);
         if (s->stream) cudaStreamDestroy(s->stream);
+        if (s->pool) cudaMemPoolDestroy(s->pool);
         delete s;
         return st;
     }
@@ -429,6 +469,7 @@ dpcs_status dpcs_serve_destroy(dpcs_server *s) {
     for (Batch &b : s->batches) free_batch_bufs(b);
     cudaStreamSynchronize(s->stream);
     cudaStreamDestroy(s->stream);
+    cudaMemPoolDestroy(s->pool);
     delete s;
     return DPCS_OK;
 }

@@ -33,6 +33,7 @@ EXPORTED = [
     "dpcs_render_backward", "dpcs_l2_loss", "dpcs_adam", "dpcs_timing_enable", "dpcs_timing_read",
     "dpcs_counters_read", "dpcs_debug_set_visit_cap", "dpcs_render_noalloc", "dpcs_serve_create", "dpcs_serve_destroy", "dpcs_serve_add_scene",
     "dpcs_serve_submit", "dpcs_serve_step", "dpcs_serve_query", "dpcs_serve_drain", "dpcs_serve_stats_get",
+    "dpcs_probe_l2_load", "dpcs_probe_atomic4",
 ]
 
 DPCS_REQ_RELIGHT = 0
@@ -113,6 +114,8 @@ _SIGS = {
                                           ctypes.POINTER(ctypes.c_int64)]),
     "dpcs_counters_read": (ctypes.c_int32, [_P, _P, ctypes.c_int32]),
     "dpcs_debug_set_visit_cap": (ctypes.c_int32, [_P, ctypes.c_int32]),
+    "dpcs_probe_l2_load": (ctypes.c_int32, [_P, ctypes.c_size_t, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
+    "dpcs_probe_atomic4": (ctypes.c_int32, [_P, ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)]),
     "dpcs_serve_create": (ctypes.c_int32, [_P, ctypes.POINTER(DpcsServeConfig), ctypes.POINTER(_P)]),
     "dpcs_serve_destroy": (ctypes.c_int32, [_P]),
     "dpcs_serve_add_scene": (ctypes.c_int32, [_P, ctypes.c_uint64, _P, _P, ctypes.c_int32, ctypes.c_int32,
@@ -274,6 +277,14 @@ def dpcs_counters_read(ctx, out, reset):
     return load_library().dpcs_counters_read(ctx, out, int(reset))
 
 
+def dpcs_probe_l2_load(ctx, nbytes, passes, gbs):
+    return load_library().dpcs_probe_l2_load(ctx, nbytes, int(passes), gbs)
+
+
+def dpcs_probe_atomic4(ctx, texels, n_atomics, gatomics):
+    return load_library().dpcs_probe_atomic4(ctx, int(texels), int(n_atomics), gatomics)
+
+
 def dpcs_l2_loss(ctx, Ic, target, n, dIc, loss, stream):
     return load_library().dpcs_l2_loss(ctx, Ic, target, n, dIc, loss, stream)
 
@@ -338,6 +349,20 @@ class Context:
         self.check(self.lib.dpcs_counters_read(self.handle, out, 1 if reset else 0), "counters_read")
         keys = ("node_visits", "tri_tests", "rays", "shadow_rays", "vertices", "lit", "continuations", "paths")
         return dict(zip(keys, [int(x) for x in out]))
+
+    def probe_l2_load(self, nbytes: int = 32 << 20, passes: int = 64) -> float:
+        """Measured L2 load bandwidth in GB/s (16-byte loads that bypass L1)."""
+        out = ctypes.c_double()
+        self.check(self.lib.dpcs_probe_l2_load(self.handle, int(nbytes), int(passes), ctypes.byref(out)),
+                   "probe_l2_load")
+        return out.value
+
+    def probe_atomic4(self, texels: int = 512 * 512, n_atomics: int = 1 << 28) -> float:
+        """Measured scattered float4 atomic-add throughput in 1e9 adds per second."""
+        out = ctypes.c_double()
+        self.check(self.lib.dpcs_probe_atomic4(self.handle, int(texels), int(n_atomics), ctypes.byref(out)),
+                   "probe_atomic4")
+        return out.value
 
     def kernel_time(self, kernel: int):
         """(total ms, launches) of kernel 0 = render, 1 = replay since timing(True)."""

@@ -66,6 +66,35 @@ def test_backward_64_random_parameters_full_size(orc):
     assert ok, (grads["dparams"], ref["dparams"])
 
 
+def test_backward_without_texture_outputs(orc):
+    """dAlbedo = dRough = NULL (compensation's call) skips the texture
+    scatters; dIp and dParams still equal the oracle's, and a later call that
+    asks for the textures gets them."""
+    torch = need_cuda()
+    sc = scenes.corner(res=28, tex=32, spp=4, bounces=3, seed=9)
+    g = GpuScene(sc)
+    rng = np.random.default_rng(2)
+    W = rng.normal(size=(sc.Hc, sc.Wc, 3)).astype(np.float32)
+    try:
+        Ec, Ic = g.render()
+        dIp = torch.zeros_like(g.Ip)
+        dP = torch.zeros(11, dtype=torch.float32, device=g.ctx.device)
+        g.ctx.render_backward(g.handle, g.albedo, g.rough, g.Ip, g.view, g.params, sc.spp, sc.bounces, sc.seed, Ec,
+                              Ic, torch.from_numpy(W).cuda(), dIp=dIp, dParams=dP)
+        g.ctx.sync()
+        full = g.backward(Ec, Ic, torch.from_numpy(W).cuda())
+    finally:
+        g.close()
+    ref = orc.render_backward(sc, W.astype(np.float64))
+    ok, mx, scale = _grad_close(dIp.cpu().numpy(), ref["dIp"], 1e-3, 1e-5)
+    assert scale > 0 and ok, ("dIp", mx, scale)
+    ok, mx, _ = _grad_close(dP.cpu().numpy(), ref["dparams"], 1e-4, 1e-6)
+    assert ok, ("dparams", dP.cpu().numpy(), ref["dparams"])
+    for k in ("dalbedo", "drough"):
+        ok, mx, scale = _grad_close(full[k], ref[k], 1e-3, 1e-5)
+        assert scale > 0 and ok, (k, mx, scale)
+
+
 def test_l2_loss_and_adam():
     torch = need_cuda()
     c = ctx()
