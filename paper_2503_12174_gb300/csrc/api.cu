@@ -217,7 +217,7 @@ dpcs_status prepare(dpcs_ctx *c, dpcs_scene scene, const float *albedo, const fl
     a.key0 = (uint32_t)(seed & 0xffffffffu);
     a.key1 = (uint32_t)(seed >> 32);
     // lanes per pixel: the largest power of two L <= 32 with spp / L >= kMinSamplesPerLane
-    // (at least 1), so that each lane has several paths to regenerate into
+    // (at least 1)
     int l2 = 0;
     while (l2 < 5 && (2 << l2) * kMinSamplesPerLane <= spp) ++l2;
     a.log2L = l2;
