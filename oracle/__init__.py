@@ -23,4 +23,7 @@ from .oracle import (  # noqa: F401
     bsdf_sample,
     ggx_D,
     adam_step,
+    gbuffer,
+    denoise,
+    denoise_backward,
 )

@@ -15,6 +15,8 @@
  *   - Eq. 5   CRF + white balance: Ic = (Gc w Ec)^gamma_c      (crf)
  *   - Eq. 6   projection xc = Kc xs, xp = Kp [Rp|tp] xs        (camera ray, nee)
  *   - Eq. 12  radiance clipping (optional, off when clip == 0)
+ *   - Eq. 11  the guide features of the cross-bilateral denoiser (or_gbuffer;
+ *             the filter itself is in oracle.py)
  *   - the analytic adjoint of the same estimator with the sampled directions
  *     held fixed (detached sampling), used by projector compensation (Eq. 13)
  *     and scene-parameter fitting (Eq. 9).
@@ -853,6 +855,52 @@ int or_render_backward(const float *verts, const int32_t *tris, int32_t T, const
     dParams[8] += crf_acc[4]; dParams[9] += crf_acc[5]; dParams[10] += crf_acc[6];
     free(acc);
     free(Ep);
+    scene_free(&S);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Guide features of the cross-bilateral denoiser of Eq. 11: what the camera */
+/* ray through each pixel centre sees first.  Per pixel 8 values: bilinear   */
+/* albedo (3), geometric normal turned towards the camera (3), hit distance  */
+/* along the unit ray, and 1 for a hit; all 8 are 0 where the ray misses.    */
+/* The paper names the filter but not its guide; these are the noise-free    */
+/* first-hit quantities of the renderer itself.                              */
+/* ------------------------------------------------------------------------- */
+int or_gbuffer(const float *verts, const int32_t *tris, int32_t T, const float *uv, const double *albedo,
+               int32_t Ht, int32_t Wt, const or_view *Vw, double *guide, int32_t nthreads)
+{
+    if (Ht <= 0 || Wt <= 0 || Vw->Hc <= 0 || Vw->Wc <= 0) return -1;
+    set_threads(nthreads);
+    dscene S;
+    scene_make(&S, verts, tris, T, uv);
+    double Kc_inv[9];
+    inv3(Vw->Kc, Kc_inv);
+    const int64_t n = (int64_t)Vw->Hc * Vw->Wc;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t p = 0; p < n; ++p) {
+        double *g = guide + 8 * p;
+        for (int k = 0; k < 8; ++k) g[k] = 0.0;
+        double fx = (double)(p % Vw->Wc) + 0.5, fy = (double)(p / Vw->Wc) + 0.5;
+        d3 d = nrm(mat3v(Kc_inv, mk(fx, fy, 1.0)));
+        double t, bu, bv;
+        int tri = closest(&S, mk(0.0, 0.0, 0.0), d, INFINITY, &t, &bu, &bv);
+        if (tri < 0) continue;
+        d3 nn = nrm(cross(S.e1[tri], S.e2[tri]));
+        if (dot(nn, d) > 0.0) nn = scl(nn, -1.0);
+        const double *tuv = S.uv + 6 * tri;
+        double w0 = 1.0 - bu - bv;
+        double su = w0 * tuv[0] + bu * tuv[2] + bv * tuv[4];
+        double sv = w0 * tuv[1] + bu * tuv[3] + bv * tuv[5];
+        int idx[4];
+        double w[4];
+        bilin(su * Wt, sv * Ht, Wt, Ht, idx, w);
+        for (int k = 0; k < 4; ++k)
+            for (int j = 0; j < 3; ++j) g[j] += w[k] * albedo[3 * idx[k] + j];
+        g[3] = nn.x; g[4] = nn.y; g[5] = nn.z;
+        g[6] = t;
+        g[7] = 1.0;
+    }
     scene_free(&S);
     return 0;
 }

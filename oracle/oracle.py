@@ -62,6 +62,7 @@ def load():
         _lib.or_bsdf_sample.argtypes = [P, P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                         ctypes.c_double, ctypes.c_double, P]
         _lib.or_bsdf_eval.argtypes = [P, P, P, P, ctypes.c_double, ctypes.c_double, ctypes.c_double, P, P]
+        _lib.or_gbuffer.restype = ctypes.c_int
         _lib.or_num_threads.restype = ctypes.c_int
         _lib.or_num_threads.argtypes = [ctypes.c_int]
     return _lib
@@ -250,3 +251,87 @@ def adam_step(p, g, m, v, step, lr=1e-2, b1=0.9, b2=0.999, eps=1e-8, lo=0.0, hi=
     p -= lr * mh / (np.sqrt(vh) + eps)
     np.clip(p, lo, hi, out=p)
     return p
+
+
+# ---------------------------------------------------------------------------
+# Eq. 11: Ic' = D(Ic), a cross-bilateral filter.  The paper names the filter
+# (a differentiable cross-bilateral filter) but not its guide, window or
+# widths; the reading taken here:
+#   D(I)(p) = sum_q w(p,q) I(q) / W(p),  W(p) = sum_q w(p,q),
+#   w(p,q)  = exp(-|p-q|^2 / (2 s_s^2) - sum_f |g_f(p) - g_f(q)|^2 / (2 s_f^2)),
+# q over the (2r+1)^2 window around p that lies inside the image, g_f the
+# guide features of gbuffer() (albedo, normal, depth); a width <= 0 drops
+# its feature.  The weights depend on the guide only, so D is linear in I and
+# its adjoint is dI(q) = sum_p w(p,q) dD(p) / W(p).
+# ---------------------------------------------------------------------------
+def gbuffer(sc, albedo=None, nthreads: int = 0):
+    """First-hit guide through each camera pixel centre: (Hc, Wc, 8) =
+    albedo rgb, normal xyz (towards the camera), hit distance, hit flag."""
+    verts, tris, uv = _c(sc.verts, np.float32), _c(sc.tris, np.int32), _c(sc.uv, np.float32)
+    albedo = _c(sc.albedo if albedo is None else albedo, np.float64)
+    V = make_view(sc)
+    g = np.zeros((sc.Hc, sc.Wc, 8))
+    rc = load().or_gbuffer(_p(verts), _p(tris), ctypes.c_int32(len(tris)), _p(uv), _p(albedo),
+                           ctypes.c_int32(albedo.shape[0]), ctypes.c_int32(albedo.shape[1]), ctypes.byref(V), _p(g),
+                           ctypes.c_int32(nthreads))
+    if rc != 0:
+        raise ValueError("oracle gbuffer: invalid arguments")
+    return g
+
+
+_FEATURES = (("sigma_albedo", slice(0, 3)), ("sigma_normal", slice(3, 6)), ("sigma_depth", slice(6, 7)))
+
+
+def _bilateral_weight(guide, p_sl, q_sl, dy, dx, prm):
+    """w(p, q) for every p in the window slice p_sl with q = p + (dy, dx)."""
+    e = (dx * dx + dy * dy) / (2.0 * prm["sigma_s"] ** 2)
+    for name, fs in _FEATURES:
+        s = prm[name]
+        if s > 0.0:
+            diff = guide[p_sl][..., fs] - guide[q_sl][..., fs]
+            e = e + np.sum(diff * diff, axis=-1) / (2.0 * s * s)
+    return np.exp(-e)
+
+
+def _offsets(H, W, r):
+    """(dy, dx, p-slices, q-slices) of every window offset, q = p + (dy, dx)."""
+    for dy in range(-r, r + 1):
+        for dx in range(-r, r + 1):
+            py = slice(max(0, -dy), min(H, H - dy))
+            px = slice(max(0, -dx), min(W, W - dx))
+            qy = slice(py.start + dy, py.stop + dy)
+            qx = slice(px.start + dx, px.stop + dx)
+            yield dy, dx, (py, px), (qy, qx)
+
+
+def denoise(I, guide, prm):
+    """FP64 cross-bilateral filter of Eq. 11.  I (H, W, 3), guide (H, W, 8),
+    prm dict(radius, sigma_s, sigma_albedo, sigma_normal, sigma_depth).
+    Returns (D(I), W) with W the per-pixel weight sum."""
+    I = np.asarray(I, np.float64)
+    guide = np.asarray(guide, np.float64)
+    H, W = I.shape[:2]
+    num = np.zeros((H, W, 3))
+    den = np.zeros((H, W))
+    for dy, dx, ps, qs in _offsets(H, W, int(prm["radius"])):
+        w = _bilateral_weight(guide, ps, qs, dy, dx, prm)
+        num[ps] += w[..., None] * I[qs]
+        den[ps] += w
+    return num / den[..., None], den
+
+
+def denoise_backward(dout, guide, prm):
+    """Adjoint of denoise(): dI(q) = sum_p w(p,q) dout(p) / W(p), scattered
+    from every output pixel p to the inputs q it read."""
+    dout = np.asarray(dout, np.float64)
+    guide = np.asarray(guide, np.float64)
+    H, W = dout.shape[:2]
+    den = np.zeros((H, W))
+    for dy, dx, ps, qs in _offsets(H, W, int(prm["radius"])):
+        den[ps] += _bilateral_weight(guide, ps, qs, dy, dx, prm)
+    g = dout / den[..., None]
+    dI = np.zeros((H, W, 3))
+    for dy, dx, ps, qs in _offsets(H, W, int(prm["radius"])):
+        w = _bilateral_weight(guide, ps, qs, dy, dx, prm)
+        dI[qs] += w[..., None] * g[ps]
+    return dI
