@@ -297,6 +297,8 @@ def _offsets(H, W, r):
     """(dy, dx, p-slices, q-slices) of every window offset, q = p + (dy, dx)."""
     for dy in range(-r, r + 1):
         for dx in range(-r, r + 1):
+            if abs(dy) >= H or abs(dx) >= W:
+                continue  # no pixel pair this far apart inside the image
             py = slice(max(0, -dy), min(H, H - dy))
             px = slice(max(0, -dx), min(W, W - dx))
             qy = slice(py.start + dy, py.stop + dy)

@@ -71,12 +71,13 @@ def test_denoise_keeps_a_constant_image(orc):
     np.testing.assert_allclose(out, I, rtol=1e-14)
 
 
-def test_denoise_without_guide_terms_is_a_normalised_gaussian(orc):
+@pytest.mark.parametrize("H,W,r,s", [(17, 23, 4, 1.7), (3, 5, 6, 2.5)])
+def test_denoise_without_guide_terms_is_a_normalised_gaussian(orc, H, W, r, s):
     """All feature widths off: the filter is a Gaussian blur renormalised by
     the part of the window inside the image -- scipy's correlate of the image
-    and of ones with zero padding, divided."""
+    and of ones with zero padding, divided.  The second case has a window
+    wider than the image."""
     rng = np.random.default_rng(2)
-    H, W, r, s = 17, 23, 4, 1.7
     I = rng.uniform(size=(H, W, 3))
     out, den = orc.denoise(I, _random_guide(rng, H, W), _prm(radius=r, sigma_s=s))
     yy, xx = np.mgrid[-r:r + 1, -r:r + 1]
