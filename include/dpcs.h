@@ -273,6 +273,54 @@ dpcs_status dpcs_render_backward(dpcs_ctx *ctx, dpcs_scene scene, const float *a
                                  const float *Ec, const float *Ic, const float *dIc, float *dIp, float *dAlbedo,
                                  float *dRough, float *dParams, void *stream);
 
+/* ------------------------------------------------------------------------ */
+/* Denoiser of Eq. 11: Ic' = D(Ic), a differentiable cross-bilateral filter  */
+/* ------------------------------------------------------------------------ */
+/*
+ * The paper applies a differentiable cross-bilateral filter D to the
+ * rendered camera image before the loss (Sec. 3.3, Eq. 11), without naming
+ * its guide or widths.  Here the guide is the renderer's own noise-free
+ * first hit through each pixel centre, and
+ *   D(I)(p) = sum_q w(p,q) I(q) / W(p),   W(p) = sum_q w(p,q),
+ *   w(p,q)  = exp(-|p-q|^2/(2 s^2) - |a_p-a_q|^2/(2 sa^2) - |n_p-n_q|^2/(2 sn^2)
+ *                 - (t_p-t_q)^2/(2 sd^2))
+ * over the (2r+1)^2 window around p that lies inside the image (a albedo,
+ * n normal, t hit distance; a width <= 0 drops its term).  The weights depend
+ * on the guide only: D is linear in I and the gradient does not flow into
+ * the guide.
+ */
+typedef struct dpcs_denoise_params {
+    int32_t radius;      /* window half-width r, 0..8 (0 = identity) */
+    float sigma_s;       /* spatial width in pixels, > 0 */
+    float sigma_albedo;  /* albedo width (<= 0: term off) */
+    float sigma_normal;  /* normal width (<= 0: term off) */
+    float sigma_depth;   /* hit-distance width, scene units (<= 0: term off) */
+} dpcs_denoise_params;
+
+/* Guide features of scene `scene` seen through each camera pixel centre of
+ * `view` (jitter and the projector fields of the view are not used):
+ * guide (dev, 16-byte aligned, Hc x Wc x 8 float32) = albedo rgb (bilinear,
+ * as the renderer samples it), geometric normal turned towards the camera,
+ * hit distance along the unit ray, 1; all 8 are 0 where the ray misses.
+ * albedo/rough: dev textures as in dpcs_render.  Allocates a temporary
+ * 16 * Ht * Wt byte texture, stream-ordered, for the call. */
+dpcs_status dpcs_gbuffer(dpcs_ctx *ctx, dpcs_scene scene, const float *albedo, const float *rough, int32_t Ht,
+                         int32_t Wt, const dpcs_view *view, float *guide, void *stream);
+
+/* out = D(Ic) (dev, Hc x Wc x 3, must not alias Ic); wsum (dev, Hc x Wc, may
+ * be NULL) receives W, which dpcs_denoise_backward needs.  guide from
+ * dpcs_gbuffer.  DPCS_ERR_INVALID_ARG for radius outside 0..8, sigma_s <= 0,
+ * a misaligned guide or null pointers. */
+dpcs_status dpcs_denoise(dpcs_ctx *ctx, const float *Ic, const float *guide, int32_t Hc, int32_t Wc,
+                         const dpcs_denoise_params *params, float *out, float *wsum, void *stream);
+
+/* Adjoint of dpcs_denoise: dIc (dev, Hc x Wc x 3) += D^T(dOut), i.e.
+ * dIc(q) += sum_p w(p,q) dOut(p) / W(p), with wsum = W from the forward call
+ * (same guide and params).  dIc must not alias dOut. */
+dpcs_status dpcs_denoise_backward(dpcs_ctx *ctx, const float *dOut, const float *guide, const float *wsum,
+                                  int32_t Hc, int32_t Wc, const dpcs_denoise_params *params, float *dIc,
+                                  void *stream);
+
 /*
  * L2 image loss of projector compensation (Eq. 13 with a squared norm):
  * loss = 1/2 sum (Ic - target)^2 written to *loss (dev, 1 float32, overwritten),

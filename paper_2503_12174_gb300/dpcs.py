@@ -33,7 +33,7 @@ EXPORTED = [
     "dpcs_render_backward", "dpcs_l2_loss", "dpcs_adam", "dpcs_timing_enable", "dpcs_timing_read",
     "dpcs_counters_read", "dpcs_debug_set_visit_cap", "dpcs_render_noalloc", "dpcs_serve_create", "dpcs_serve_destroy", "dpcs_serve_add_scene",
     "dpcs_serve_submit", "dpcs_serve_step", "dpcs_serve_query", "dpcs_serve_drain", "dpcs_serve_stats_get",
-    "dpcs_probe_l2_load", "dpcs_probe_atomic4",
+    "dpcs_probe_l2_load", "dpcs_probe_atomic4", "dpcs_gbuffer", "dpcs_denoise", "dpcs_denoise_backward",
 ]
 
 DPCS_REQ_RELIGHT = 0
@@ -84,6 +84,16 @@ class DpcsServeStats(ctypes.Structure):
                 ("memory_high_water", ctypes.c_size_t)]
 
 
+class DpcsDenoiseParams(ctypes.Structure):
+    _fields_ = [("radius", ctypes.c_int32), ("sigma_s", ctypes.c_float), ("sigma_albedo", ctypes.c_float),
+                ("sigma_normal", ctypes.c_float), ("sigma_depth", ctypes.c_float)]
+
+
+def make_denoise_params(radius: int = 5, sigma_s: float = 2.0, sigma_albedo: float = 0.1, sigma_normal: float = 0.3,
+                        sigma_depth: float = 0.1) -> DpcsDenoiseParams:
+    return DpcsDenoiseParams(int(radius), float(sigma_s), float(sigma_albedo), float(sigma_normal), float(sigma_depth))
+
+
 _lib = None
 _lib_path = None
 
@@ -114,6 +124,12 @@ _SIGS = {
                                           ctypes.POINTER(ctypes.c_int64)]),
     "dpcs_counters_read": (ctypes.c_int32, [_P, _P, ctypes.c_int32]),
     "dpcs_debug_set_visit_cap": (ctypes.c_int32, [_P, ctypes.c_int32]),
+    "dpcs_gbuffer": (ctypes.c_int32, [_P, ctypes.c_uint64, _P, _P, ctypes.c_int32, ctypes.c_int32,
+                                      ctypes.POINTER(DpcsView), _P, _P]),
+    "dpcs_denoise": (ctypes.c_int32, [_P, _P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(DpcsDenoiseParams),
+                                      _P, _P, _P]),
+    "dpcs_denoise_backward": (ctypes.c_int32, [_P, _P, _P, _P, ctypes.c_int32, ctypes.c_int32,
+                                               ctypes.POINTER(DpcsDenoiseParams), _P, _P]),
     "dpcs_probe_l2_load": (ctypes.c_int32, [_P, ctypes.c_size_t, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
     "dpcs_probe_atomic4": (ctypes.c_int32, [_P, ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)]),
     "dpcs_serve_create": (ctypes.c_int32, [_P, ctypes.POINTER(DpcsServeConfig), ctypes.POINTER(_P)]),
@@ -283,6 +299,18 @@ def dpcs_probe_l2_load(ctx, nbytes, passes, gbs):
 
 def dpcs_probe_atomic4(ctx, texels, n_atomics, gatomics):
     return load_library().dpcs_probe_atomic4(ctx, int(texels), int(n_atomics), gatomics)
+
+
+def dpcs_gbuffer(ctx, scene, albedo, rough, Ht, Wt, view, guide, stream):
+    return load_library().dpcs_gbuffer(ctx, scene, albedo, rough, Ht, Wt, ctypes.byref(view), guide, stream)
+
+
+def dpcs_denoise(ctx, Ic, guide, Hc, Wc, params, out, wsum, stream):
+    return load_library().dpcs_denoise(ctx, Ic, guide, Hc, Wc, ctypes.byref(params), out, wsum, stream)
+
+
+def dpcs_denoise_backward(ctx, dOut, guide, wsum, Hc, Wc, params, dIc, stream):
+    return load_library().dpcs_denoise_backward(ctx, dOut, guide, wsum, Hc, Wc, ctypes.byref(params), dIc, stream)
 
 
 def dpcs_l2_loss(ctx, Ic, target, n, dIc, loss, stream):
@@ -473,6 +501,53 @@ class Context:
             _ptr(dRough, "dRough", (Ht, Wt), f32, self.device, allow_none=True),
             _ptr(dParams, "dParams", (11,), f32, self.device, allow_none=True), _stream(stream))
         self.check(st, "render_backward")
+
+    def gbuffer(self, scene: int, albedo, rough, view: DpcsView, guide=None, stream=None):
+        """Guide features (Hc, Wc, 8) of the first hit through each pixel centre."""
+        import torch
+
+        Ht, Wt = albedo.shape[0], albedo.shape[1]
+        f32 = torch.float32
+        if guide is None:
+            guide = torch.empty((view.Hc, view.Wc, 8), dtype=f32, device=self.device)
+        st = self.lib.dpcs_gbuffer(self.handle, scene, _ptr(albedo, "albedo", (Ht, Wt, 3), f32, self.device),
+                                   _ptr(rough, "rough", (Ht, Wt), f32, self.device), Ht, Wt, ctypes.byref(view),
+                                   _ptr(guide, "guide", (view.Hc, view.Wc, 8), f32, self.device), _stream(stream))
+        self.check(st, "gbuffer")
+        return guide
+
+    def denoise(self, Ic, guide, params: DpcsDenoiseParams, out=None, wsum=None, stream=None):
+        """Eq. 11: out = D(Ic); also returns the weight sums the adjoint needs."""
+        import torch
+
+        Hc, Wc = Ic.shape[0], Ic.shape[1]
+        f32 = torch.float32
+        if out is None:
+            out = torch.empty_like(Ic)
+        if wsum is None:
+            wsum = torch.empty((Hc, Wc), dtype=f32, device=self.device)
+        st = self.lib.dpcs_denoise(self.handle, _ptr(Ic, "Ic", (Hc, Wc, 3), f32, self.device),
+                                   _ptr(guide, "guide", (Hc, Wc, 8), f32, self.device), Hc, Wc, ctypes.byref(params),
+                                   _ptr(out, "out", (Hc, Wc, 3), f32, self.device),
+                                   _ptr(wsum, "wsum", (Hc, Wc), f32, self.device), _stream(stream))
+        self.check(st, "denoise")
+        return out, wsum
+
+    def denoise_backward(self, dOut, guide, wsum, params: DpcsDenoiseParams, dIc=None, stream=None):
+        """dIc += D^T(dOut) (dIc is zero-initialised when not given)."""
+        import torch
+
+        Hc, Wc = dOut.shape[0], dOut.shape[1]
+        f32 = torch.float32
+        if dIc is None:
+            dIc = torch.zeros_like(dOut)
+        st = self.lib.dpcs_denoise_backward(self.handle, _ptr(dOut, "dOut", (Hc, Wc, 3), f32, self.device),
+                                            _ptr(guide, "guide", (Hc, Wc, 8), f32, self.device),
+                                            _ptr(wsum, "wsum", (Hc, Wc), f32, self.device), Hc, Wc,
+                                            ctypes.byref(params), _ptr(dIc, "dIc", (Hc, Wc, 3), f32, self.device),
+                                            _stream(stream))
+        self.check(st, "denoise_backward")
+        return dIc
 
     def l2_loss(self, Ic, target, dIc, loss, stream=None):
         import torch
