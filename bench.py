@@ -75,6 +75,21 @@ FLOP = {
 # csrc/internal.h): a 64-byte node, a 48-byte triangle, three 8-byte UVs,
 # four 16-byte texels for albedo+roughness and four for Ep
 LOAD_BYTES = {"node_visits": 64, "tri_tests": 48, "vertices": 24 + 4 * 16, "lit": 4 * 16}
+# the Eq. 11 filter's settings in the benchmark, and its FP32 operations per
+# window tap: albedo, normal and depth distances (8 + 8 + 2), the exponent
+# (7), the exponential (2) and the weighted sums (7)
+DENOISE_PARAMS = {"radius": 5, "sigma_s": 2.0, "sigma_albedo": 0.1, "sigma_normal": 0.3, "sigma_depth": 0.1}
+DENOISE_FLOP_PER_TAP = 34
+
+
+def denoise_taps(H: int, W: int, r: int) -> int:
+    """Window taps inside an H x W image over all pixels (the window is
+    separable in its clipping: taps = sum_y n_y * sum_x n_x)."""
+    def n(L):
+        return sum(min(L - 1, i + r) - max(0, i - r) + 1 for i in range(L))
+    return n(H) * n(W)
+
+
 # the probes' sizes: a buffer that stays in L2 like the scene and textures, and
 # the 512 x 512 gradient texture the compensation replay scatters into
 PROBE_L2_BYTES = 32 << 20
@@ -94,6 +109,8 @@ def _args():
     ap.add_argument("--serve-rates", default="5,8,11", help="Poisson arrival rates (requests/s) of the load sweep")
     ap.add_argument("--heightfield-steps", type=int, default=2, help="timed steps of the 200k-triangle workload (0 = skip)")
     ap.add_argument("--comp-steps", type=int, default=100, help="Adam steps of the full compensation run (0 = skip)")
+    ap.add_argument("--denoise-steps", type=int, default=20,
+                    help="timed calls of the Eq. 11 filter and denoised compensation steps (0 = skip)")
     return ap.parse_args()
 
 
@@ -481,6 +498,61 @@ def main():
             del cm
         comp_out = {"workload": f"{FWD_BWD_WORKLOAD}; {args.comp_steps} steps from Ip = 0.5", **cmp_res}
 
+    # ------------------------------------------------------------ Eq. 11 denoiser (cross-bilateral filter)
+    den_out = None
+    if args.denoise_steps > 0:
+        from paper_2503_12174_gb300 import compensate
+
+        dprm = dpcs.make_denoise_params(**DENOISE_PARAMS)
+        guide = ctx.gbuffer(hc, calb, crough, cview)
+        X = torch.rand((cs.Hc, cs.Wc, 3), device=dev)
+        Dout, Wsum, dX = torch.empty_like(X), torch.empty((cs.Hc, cs.Wc), device=dev), torch.zeros_like(X)
+
+        def timed(fn, n):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(n):
+                fn()
+            e1.record(stream)
+            e1.synchronize()
+            return e0.elapsed_time(e1) / n
+
+        n = args.denoise_steps
+        f_ms = timed(lambda: ctx.denoise(X, guide, dprm, out=Dout, wsum=Wsum), n)
+        b_ms = timed(lambda: ctx.denoise_backward(X, guide, Wsum, dprm, dIc=dX), n)
+        g_ms = timed(lambda: ctx.gbuffer(hc, calb, crough, cview, guide=guide), n)
+        flops = denoise_taps(cs.Hc, cs.Wc, DENOISE_PARAMS["radius"]) * DENOISE_FLOP_PER_TAP
+        d_tflops = flops / (f_ms / 1e3) / 1e12
+        cm = compensate.Compensation(ctx, hc, calb, crough, cview, cprm, cs.spp, cs.bounces, n, lr=1e-2,
+                                     seed=5000 + rank, graph=True, denoise=dprm)
+        init = torch.full((cs.Hp, cs.Wp, 3), 0.5, device=dev)
+        cm.run(init, target)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record(stream)
+        _, dhist = cm.run(init, target)
+        e1.record(stream)
+        barrier()
+        dc_ms = max_over_ranks(e0.elapsed_time(e1))
+        dl = dhist.cpu().numpy()
+        del cm
+        den_out = {
+            "workload": f"cross-bilateral filter of Eq. 11 on the {cs.Hc}x{cs.Wc} compensation image, "
+                        f"radius {DENOISE_PARAMS['radius']}, guide = first hit through each pixel centre",
+            "params": DENOISE_PARAMS, "filter_ms": f_ms, "adjoint_ms": b_ms, "gbuffer_ms": g_ms,
+            "roofline": {"bound": "alu", "kernel": "k_bilateral", "achieved": d_tflops, "peak": peak_tflops,
+                         "unit": "TFLOP/s", "frac": d_tflops / peak_tflops, "flops_per_launch": flops,
+                         "flop_per_tap": DENOISE_FLOP_PER_TAP},
+            "denoised_compensation": {"steps": n, "ms": dc_ms,
+                                      "Msamples_per_s": cs.n_samples * n * ws / (dc_ms / 1e3) / 1e6,
+                                      "loss_first": float(dl[0]), "loss_last": float(dl[-1]),
+                                      "workload": f"{FWD_BWD_WORKLOAD} with the loss on D(Ic), one CUDA graph"},
+        }
+
     # ------------------------------------------------------------ large displaced surface (T = 199,712)
     hf_out = None
     if args.heightfield_steps > 0:
@@ -588,6 +660,7 @@ def main():
             "roofline_load": roof_load,
             "roofline_atomic": roof_atomic,
             "compensation": comp_out,
+            "denoise": den_out,
             "heightfield": hf_out,
             "serving": serving_out,
             "cpu_baseline": cpu,

@@ -5,6 +5,11 @@ Ic = R(Ip) with a fresh Philox key (seed + k), takes the L2 loss against the
 target, carries dL/dIc back to Ip with the path-replay adjoint, and applies
 an Adam step followed by the clamp of Ip to [0, 1].
 
+With ``denoise`` set (a ``dpcs.DpcsDenoiseParams``), the loss is taken on
+the denoised image D(Ic) of Eq. 11 instead, and dL/dD is carried back to
+dL/dIc by the filter's adjoint before the replay.  The filter's guide is the
+scene's first hit through each pixel centre, computed once.
+
 With ``graph=True`` the whole loop is captured once as a CUDA graph and then
 replayed.  The steps are unrolled in the graph, so every step keeps its own
 seed and Adam step number, and one replay runs the full compensation.  The
@@ -20,7 +25,8 @@ class Compensation:
     view and target size."""
 
     def __init__(self, ctx: dpcs.Context, scene: int, albedo, rough, view: dpcs.DpcsView, params: dpcs.DpcsParams,
-                 spp: int, bounces: int, steps: int, lr: float = 1e-2, seed: int = 0, graph: bool = True):
+                 spp: int, bounces: int, steps: int, lr: float = 1e-2, seed: int = 0, graph: bool = True,
+                 denoise: dpcs.DpcsDenoiseParams | None = None, guide=None):
         import torch
 
         self.ctx, self.scene, self.albedo, self.rough = ctx, scene, albedo, rough
@@ -37,6 +43,12 @@ class Compensation:
         self.dIc = torch.empty_like(self.target)
         self.loss = torch.zeros(1, dtype=f32, device=dev)
         self.history = torch.zeros(self.steps, dtype=f32, device=dev)
+        self.denoise = denoise
+        if denoise is not None:
+            self.guide = guide if guide is not None else ctx.gbuffer(scene, albedo, rough, view)
+            self.D = torch.empty_like(self.target)
+            self.wsum = torch.empty((view.Hc, view.Wc), dtype=f32, device=dev)
+            self.dD = torch.empty_like(self.target)
         self.graph = None
         if graph:
             self._step(0)  # sizes the library's scratch outside the capture
@@ -50,7 +62,13 @@ class Compensation:
         s = self.seed + k
         c.render(self.scene, self.albedo, self.rough, self.P, self.view, self.params, self.spp, self.bounces, s,
                  Ic=self.Ic, Ec=self.Ec)
-        c.l2_loss(self.Ic, self.target, self.dIc, self.loss)
+        if self.denoise is None:
+            c.l2_loss(self.Ic, self.target, self.dIc, self.loss)
+        else:
+            c.denoise(self.Ic, self.guide, self.denoise, out=self.D, wsum=self.wsum)
+            c.l2_loss(self.D, self.target, self.dD, self.loss)
+            self.dIc.zero_()
+            c.denoise_backward(self.dD, self.guide, self.wsum, self.denoise, dIc=self.dIc)
         self.history[k].copy_(self.loss[0])
         self.G.zero_()
         c.render_backward(self.scene, self.albedo, self.rough, self.P, self.view, self.params, self.spp, self.bounces, s,

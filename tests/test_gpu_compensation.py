@@ -65,3 +65,41 @@ def test_graph_replay_matches_eager(orc):
         assert hg[-1].item() < hg[0].item()
     finally:
         g.close()
+
+
+def test_denoised_compensation_follows_oracle(orc):
+    """The loss on D(Ic) (Eq. 11 before the Eq. 13 loss), step by step against
+    the oracle's loop with its own filter and adjoint; then the same loop as a
+    CUDA-graph replay."""
+    torch, sc, target = _setup(orc)
+    steps, lr = 3, 0.05
+    prm = dict(radius=3, sigma_s=1.5, sigma_albedo=0.1, sigma_normal=0.3, sigma_depth=0.1)
+    guide = orc.gbuffer(sc).astype(np.float32)  # one guide for both sides
+    g = GpuScene(sc)
+    try:
+        kw = dict(lr=lr, seed=sc.seed, denoise=dpcs.make_denoise_params(**prm), guide=torch.from_numpy(guide).cuda())
+        args = (g.ctx, g.handle, g.albedo, g.rough, g.view, g.params, sc.spp, sc.bounces, steps)
+        init, tgt = torch.full_like(g.Ip, 0.5), torch.from_numpy(target).cuda()
+        P, hist = compensate.Compensation(*args, graph=False, **kw).run(init, tgt)
+        P, hist = P.clone().cpu().numpy().astype(np.float64), hist.clone().cpu().numpy().astype(np.float64)
+        Pg, hg = compensate.Compensation(*args, graph=True, **kw).run(init, tgt)
+        g.ctx.sync()
+        Pg, hg = Pg.cpu().numpy(), hg.cpu().numpy()
+    finally:
+        g.close()
+    gd = guide.astype(np.float64)
+    Pr = np.full(sc.Ip.shape, 0.5)
+    m, v = np.zeros_like(Pr), np.zeros_like(Pr)
+    losses = []
+    for k in range(steps):
+        _, Ic = orc.render(sc, Ip=Pr, seed=sc.seed + k)
+        D, _ = orc.denoise(Ic, gd, prm)
+        dD = D - target
+        losses.append(0.5 * np.sum(dD * dD))
+        grad = orc.render_backward(sc, orc.denoise_backward(dD, gd, prm), Ip=Pr, seed=sc.seed + k)["dIp"]
+        orc.adam_step(Pr, grad, m, v, k + 1, lr=lr)
+    np.testing.assert_allclose(hist, losses, rtol=1e-3)
+    assert losses[-1] < losses[0]
+    np.testing.assert_allclose(P, Pr, rtol=0, atol=2e-3)
+    np.testing.assert_allclose(hg, hist, rtol=1e-4)
+    np.testing.assert_allclose(Pg, P, rtol=0, atol=1e-4)
