@@ -26,4 +26,6 @@ from .oracle import (  # noqa: F401
     gbuffer,
     denoise,
     denoise_backward,
+    l1_loss,
+    tv_loss,
 )

@@ -337,3 +337,32 @@ def denoise_backward(dout, guide, prm):
         w = _bilateral_weight(guide, ps, qs, dy, dx, prm)
         dI[qs] += w[..., None] * g[ps]
     return dI
+
+
+# ---------------------------------------------------------------------------
+# Eq. 9: theta* = argmin (1/K) sum_i |R(Ip_i, theta) - Ic_i| + lambda L(m).
+# Readings: |.| is the L1 norm (scaled by the caller, e.g. 1/(K n) for a
+# mean), L(m) the anisotropic total variation of a BRDF map over right and
+# down neighbours.  sign(0) = 0 in both subgradients.
+# ---------------------------------------------------------------------------
+def l1_loss(I, target, scale=1.0):
+    """(scale * sum |I - target|, scale * sign(I - target))."""
+    d = np.asarray(I, np.float64) - np.asarray(target, np.float64)
+    return scale * float(np.sum(np.abs(d))), scale * np.sign(d)
+
+
+def tv_loss(m, weight=1.0):
+    """(weight * sum |m(x+1,y) - m(x,y)| + |m(x,y+1) - m(x,y)|, its
+    subgradient) for m of shape (H, W) or (H, W, C).  The subgradient is
+    scattered difference by difference: each difference d = m(q) - m(p) adds
+    sign(d) to q and subtracts it from p."""
+    m = np.asarray(m, np.float64)
+    dx = m[:, 1:] - m[:, :-1]
+    dy = m[1:, :] - m[:-1, :]
+    loss = weight * (float(np.sum(np.abs(dx))) + float(np.sum(np.abs(dy))))
+    g = np.zeros_like(m)
+    g[:, 1:] += np.sign(dx)
+    g[:, :-1] -= np.sign(dx)
+    g[1:, :] += np.sign(dy)
+    g[:-1, :] -= np.sign(dy)
+    return loss, weight * g
