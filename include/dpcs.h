@@ -339,6 +339,27 @@ dpcs_status dpcs_l2_loss(dpcs_ctx *ctx, const float *Ic, const float *target, in
 dpcs_status dpcs_adam(dpcs_ctx *ctx, float *p, const float *g, float *m, float *v, int64_t n, float lr, float beta1,
                       float beta2, float eps, int32_t step, float lo, float hi, void *stream);
 
+/*
+ * Scene-parameter fitting (Eq. 9):
+ *   theta* = argmin (1/K) sum_i |R(Ip_i, theta) - Ic_i| + lambda L(m),
+ * with |.| read as an L1 norm and L(m) as the total variation of the BRDF
+ * maps m (albedo, roughness).  The render_backward outputs of the K pairs
+ * accumulate; dpcs_adam with the ranges of Sec. 3.2 as bounds updates the
+ * textures and the response parameters.
+ *
+ * dpcs_l1_loss: dIc (dev, n floats) = scale * sign(Ic - target) (sign(0) =
+ * 0), *loss (dev float) = scale * sum |Ic - target| (reduced in FP64).
+ * scale > 0 (e.g. 1 / (K n) for the mean over K pairs).
+ *
+ * dpcs_tv_loss: tex (dev, H x W x C, C <= 4): *loss (dev float) = weight *
+ * sum over texels and channels of |m(x+1,y) - m(x,y)| + |m(x,y+1) - m(x,y)|,
+ * and grad (dev, same shape) += its derivative (sign terms; 0 at ties).
+ */
+dpcs_status dpcs_l1_loss(dpcs_ctx *ctx, const float *Ic, const float *target, int64_t n, float scale, float *dIc,
+                         float *loss, void *stream);
+dpcs_status dpcs_tv_loss(dpcs_ctx *ctx, const float *tex, int32_t H, int32_t W, int32_t C, float weight, float *grad,
+                         float *loss, void *stream);
+
 /* ------------------------------------------------------------------------ */
 /* Serving: continuous batching of relighting and compensation requests      */
 /* ------------------------------------------------------------------------ */

@@ -561,6 +561,31 @@ dpcs_status dpcs_l2_loss(dpcs_ctx *c, const float *Ic, const float *target, int6
                         "l2 loss");
 }
 
+dpcs_status dpcs_l1_loss(dpcs_ctx *c, const float *Ic, const float *target, int64_t n, float scale, float *dIc,
+                         float *loss, void *stream) {
+    if (!c) return DPCS_ERR_INVALID_ARG;
+    if (n <= 0 || !Ic || !target || !dIc || !loss || !(scale > 0.0f))
+        return fail(c, DPCS_ERR_INVALID_ARG, "bad L1 loss arguments");
+    dpcs_status s = set_device(c);
+    if (s) return s;
+    if ((s = ensure(c, c->partial, (size_t)l2_partial_slots() * sizeof(double), "loss partials"))) return s;
+    return check_launch(c,
+                        launch_l1_loss(Ic, target, n, scale, dIc, loss, (double *)c->partial.p, (cudaStream_t)stream),
+                        "l1 loss");
+}
+
+dpcs_status dpcs_tv_loss(dpcs_ctx *c, const float *tex, int32_t H, int32_t W, int32_t C, float weight, float *grad,
+                         float *loss, void *stream) {
+    if (!c) return DPCS_ERR_INVALID_ARG;
+    if (H <= 0 || W <= 0 || C <= 0 || C > 4 || !tex || !grad || !loss || !(weight >= 0.0f))
+        return fail(c, DPCS_ERR_INVALID_ARG, "bad total-variation arguments");
+    dpcs_status s = set_device(c);
+    if (s) return s;
+    if ((s = ensure(c, c->partial, (size_t)l2_partial_slots() * sizeof(double), "loss partials"))) return s;
+    return check_launch(c, launch_tv_loss(tex, H, W, C, weight, grad, loss, (double *)c->partial.p,
+                                          (cudaStream_t)stream), "total variation");
+}
+
 dpcs_status dpcs_adam(dpcs_ctx *c, float *p, const float *g, float *m, float *v, int64_t n, float lr, float beta1,
                       float beta2, float eps, int32_t step, float lo, float hi, void *stream) {
     if (!c) return DPCS_ERR_INVALID_ARG;

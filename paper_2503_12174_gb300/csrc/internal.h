@@ -96,6 +96,10 @@ int launch_finalize_params(const double *acc, float *dParams, cudaStream_t st);
 int launch_zero(void *p, size_t bytes, cudaStream_t st);
 int launch_l2_loss(const float *Ic, const float *target, int64_t n, float *dIc, float *loss, double *partial,
                    cudaStream_t st);
+int launch_l1_loss(const float *Ic, const float *target, int64_t n, float scale, float *dIc, float *loss,
+                   double *partial, cudaStream_t st);
+int launch_tv_loss(const float *m, int H, int W, int C, float weight, float *grad, float *loss, double *partial,
+                   cudaStream_t st);
 int l2_partial_slots();
 int launch_adam(float *p, const float *g, float *m, float *v, int64_t n, float lr, float b1, float b2, float eps,
                 int32_t step, float lo, float hi, cudaStream_t st);

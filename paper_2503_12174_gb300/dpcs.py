@@ -34,6 +34,7 @@ EXPORTED = [
     "dpcs_counters_read", "dpcs_debug_set_visit_cap", "dpcs_render_noalloc", "dpcs_serve_create", "dpcs_serve_destroy", "dpcs_serve_add_scene",
     "dpcs_serve_submit", "dpcs_serve_step", "dpcs_serve_query", "dpcs_serve_drain", "dpcs_serve_stats_get",
     "dpcs_probe_l2_load", "dpcs_probe_atomic4", "dpcs_gbuffer", "dpcs_denoise", "dpcs_denoise_backward",
+    "dpcs_l1_loss", "dpcs_tv_loss",
 ]
 
 DPCS_REQ_RELIGHT = 0
@@ -144,6 +145,9 @@ _SIGS = {
     "dpcs_serve_drain": (ctypes.c_int32, [_P, ctypes.c_double]),
     "dpcs_serve_stats_get": (ctypes.c_int32, [_P, ctypes.POINTER(DpcsServeStats)]),
     "dpcs_l2_loss": (ctypes.c_int32, [_P, _P, _P, ctypes.c_int64, _P, _P, _P]),
+    "dpcs_l1_loss": (ctypes.c_int32, [_P, _P, _P, ctypes.c_int64, ctypes.c_float, _P, _P, _P]),
+    "dpcs_tv_loss": (ctypes.c_int32, [_P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_float, _P, _P,
+                                      _P]),
     "dpcs_adam": (ctypes.c_int32, [_P, _P, _P, _P, _P, ctypes.c_int64, ctypes.c_float, ctypes.c_float,
                                    ctypes.c_float, ctypes.c_float, ctypes.c_int32, ctypes.c_float, ctypes.c_float,
                                    _P]),
@@ -315,6 +319,14 @@ def dpcs_denoise_backward(ctx, dOut, guide, wsum, Hc, Wc, params, dIc, stream):
 
 def dpcs_l2_loss(ctx, Ic, target, n, dIc, loss, stream):
     return load_library().dpcs_l2_loss(ctx, Ic, target, n, dIc, loss, stream)
+
+
+def dpcs_l1_loss(ctx, Ic, target, n, scale, dIc, loss, stream):
+    return load_library().dpcs_l1_loss(ctx, Ic, target, n, scale, dIc, loss, stream)
+
+
+def dpcs_tv_loss(ctx, tex, H, W, C, weight, grad, loss, stream):
+    return load_library().dpcs_tv_loss(ctx, tex, H, W, C, weight, grad, loss, stream)
 
 
 def dpcs_adam(ctx, p, g, m, v, n, lr, beta1, beta2, eps, step, lo, hi, stream):
@@ -548,6 +560,30 @@ class Context:
                                             _stream(stream))
         self.check(st, "denoise_backward")
         return dIc
+
+    def l1_loss(self, Ic, target, dIc, loss, scale: float = 1.0, stream=None):
+        """Eq. 9 data term: dIc = scale sign(Ic - target), loss = scale sum |Ic - target|."""
+        import torch
+
+        f32 = torch.float32
+        st = self.lib.dpcs_l1_loss(self.handle, _ptr(Ic, "Ic", None, f32, self.device),
+                                   _ptr(target, "target", tuple(Ic.shape), f32, self.device), Ic.numel(),
+                                   float(scale), _ptr(dIc, "dIc", tuple(Ic.shape), f32, self.device),
+                                   _ptr(loss, "loss", (1,), f32, self.device), _stream(stream))
+        self.check(st, "l1_loss")
+
+    def tv_loss(self, tex, grad, loss, weight: float, stream=None):
+        """Eq. 9 regulariser: loss = weight TV(tex); grad += its derivative.
+        tex is (H, W) or (H, W, C)."""
+        import torch
+
+        f32 = torch.float32
+        H, W = tex.shape[0], tex.shape[1]
+        C = 1 if tex.dim() == 2 else tex.shape[2]
+        st = self.lib.dpcs_tv_loss(self.handle, _ptr(tex, "tex", None, f32, self.device), H, W, C, float(weight),
+                                   _ptr(grad, "grad", tuple(tex.shape), f32, self.device),
+                                   _ptr(loss, "loss", (1,), f32, self.device), _stream(stream))
+        self.check(st, "tv_loss")
 
     def l2_loss(self, Ic, target, dIc, loss, stream=None):
         import torch

@@ -1,0 +1,121 @@
+"""Scene-parameter fitting (Eq. 9): estimate the BRDF maps and the projector
+/ camera responses from K projected images and their captures,
+
+    theta* = argmin (1/K) sum_i |D(R(Ip_i, theta)) - Ic_i| + lambda L(m),
+
+with |.| the L1 norm (a mean over the pixels and channels of the K pairs),
+L(m) the total variation of the albedo and roughness maps, and D the
+optional cross-bilateral denoiser of Eq. 11.  theta = albedo, roughness,
+gamma_p, gamma_c and the white balance w; the gains Gp and Gc stay at their
+given constants (Sec. 3.2).  Each step renders every pair with a fresh
+Philox key, accumulates the path-replay gradients of all pairs, adds the
+total-variation gradient and takes one Adam step per parameter group, each
+followed by the clamp to the group's range: albedo [0, 1], roughness
+[0.01, 1], gamma_p [2, 3], gamma_c [1/3, 1], w [0.2, 2.5] (Sec. 3.2).
+
+Every step runs in the library's kernels; the only host traffic per step is
+reading back the 11 response parameters the next renders take by value.
+"""
+from __future__ import annotations
+
+from . import dpcs
+
+PARAM_RANGES = {"gamma_p": (slice(0, 3), 2.0, 3.0), "gamma_c": (slice(4, 7), 1.0 / 3.0, 1.0),
+                "wb": (slice(8, 11), 0.2, 2.5)}
+ROUGH_MIN = 0.01
+
+
+def params_vector(p: dpcs.DpcsParams):
+    """[gamma_p(3), Gp, gamma_c(3), Gc, wb(3)] -- the layout of dParams."""
+    return list(p.gamma_p) + [p.gain_p] + list(p.gamma_c) + [p.gain_c] + list(p.wb)
+
+
+def with_vector(p: dpcs.DpcsParams, v) -> dpcs.DpcsParams:
+    q = dpcs.DpcsParams.from_buffer_copy(bytes(p))
+    q.gamma_p[:] = [float(x) for x in v[0:3]]
+    q.gain_p = float(v[3])
+    q.gamma_c[:] = [float(x) for x in v[4:7]]
+    q.gain_c = float(v[7])
+    q.wb[:] = [float(x) for x in v[8:11]]
+    return q
+
+
+class SceneFit:
+    """Device state of one fit: the parameters, their Adam moments and the
+    per-pair buffers.  ``pairs`` is a list of (Ip, Ic) device tensors."""
+
+    def __init__(self, ctx: dpcs.Context, scene: int, view: dpcs.DpcsView, params0: dpcs.DpcsParams, albedo0, rough0,
+                 pairs, spp: int, bounces: int, lr_tex: float = 2e-2, lr_params: float = 1e-2, tv_weight: float = 0.0,
+                 denoise: dpcs.DpcsDenoiseParams | None = None, fit_params: bool = True, seed: int = 0):
+        import torch
+
+        self.ctx, self.scene, self.view = ctx, scene, view
+        self.pairs = list(pairs)
+        self.K = len(self.pairs)
+        self.spp, self.bounces, self.seed = int(spp), int(bounces), int(seed)
+        self.lr_tex, self.lr_params, self.tv_weight = float(lr_tex), float(lr_params), float(tv_weight)
+        self.denoise, self.fit_params = denoise, bool(fit_params)
+        dev = ctx.device
+        f32 = torch.float32
+        self.albedo = albedo0.clone().contiguous()
+        self.rough = rough0.clone().contiguous()
+        self.params = params0
+        self.pvec = torch.tensor(params_vector(params0), dtype=f32, device=dev)
+        self.gA, self.gR = torch.zeros_like(self.albedo), torch.zeros_like(self.rough)
+        self.gP = torch.zeros(11, dtype=f32, device=dev)
+        self.mA, self.vA = torch.zeros_like(self.albedo), torch.zeros_like(self.albedo)
+        self.mR, self.vR = torch.zeros_like(self.rough), torch.zeros_like(self.rough)
+        self.mP, self.vP = torch.zeros(11, dtype=f32, device=dev), torch.zeros(11, dtype=f32, device=dev)
+        img = (view.Hc, view.Wc, 3)
+        self.Ic, self.Ec = torch.empty(img, dtype=f32, device=dev), torch.empty(img, dtype=f32, device=dev)
+        self.dIc = torch.empty(img, dtype=f32, device=dev)
+        if denoise is not None:
+            self.guide = torch.empty((view.Hc, view.Wc, 8), dtype=f32, device=dev)
+            self.D, self.dD = torch.empty(img, dtype=f32, device=dev), torch.empty(img, dtype=f32, device=dev)
+            self.wsum = torch.empty((view.Hc, view.Wc), dtype=f32, device=dev)
+        self.losses = torch.zeros(self.K + 2, dtype=f32, device=dev)  # K data terms, TV(albedo), TV(rough)
+        self.scale = 1.0 / (self.K * view.Hc * view.Wc * 3)
+        self.k = 0
+
+    def step(self):
+        """One Adam step over all K pairs; returns the device loss terms."""
+        c = self.ctx
+        self.k += 1
+        self.gA.zero_()
+        self.gR.zero_()
+        self.gP.zero_()
+        if self.denoise is not None:  # the guide follows the current albedo; its weights are not differentiated
+            c.gbuffer(self.scene, self.albedo, self.rough, self.view, guide=self.guide)
+        for i, (Ip, target) in enumerate(self.pairs):
+            s = self.seed + (self.k - 1) * self.K + i
+            c.render(self.scene, self.albedo, self.rough, Ip, self.view, self.params, self.spp, self.bounces, s,
+                     Ic=self.Ic, Ec=self.Ec)
+            if self.denoise is None:
+                c.l1_loss(self.Ic, target, self.dIc, self.losses[i:i + 1], scale=self.scale)
+            else:
+                c.denoise(self.Ic, self.guide, self.denoise, out=self.D, wsum=self.wsum)
+                c.l1_loss(self.D, target, self.dD, self.losses[i:i + 1], scale=self.scale)
+                self.dIc.zero_()
+                c.denoise_backward(self.dD, self.guide, self.wsum, self.denoise, dIc=self.dIc)
+            c.render_backward(self.scene, self.albedo, self.rough, Ip, self.view, self.params, self.spp, self.bounces,
+                              s, self.Ec, self.Ic, self.dIc, dAlbedo=self.gA, dRough=self.gR,
+                              dParams=self.gP if self.fit_params else None)
+        K = self.K
+        c.tv_loss(self.albedo, self.gA, self.losses[K:K + 1], self.tv_weight)
+        c.tv_loss(self.rough, self.gR, self.losses[K + 1:K + 2], self.tv_weight)
+        c.adam(self.albedo, self.gA, self.mA, self.vA, self.k, lr=self.lr_tex, lo=0.0, hi=1.0)
+        c.adam(self.rough, self.gR, self.mR, self.vR, self.k, lr=self.lr_tex, lo=ROUGH_MIN, hi=1.0)
+        if self.fit_params:
+            for sl, lo, hi in PARAM_RANGES.values():
+                c.adam(self.pvec[sl], self.gP[sl], self.mP[sl], self.vP[sl], self.k, lr=self.lr_params, lo=lo, hi=hi)
+            self.params = with_vector(self.params, self.pvec.cpu().tolist())
+        return self.losses
+
+    def run(self, steps: int):
+        """`steps` Adam steps; returns the per-step total loss (host list)."""
+        import torch
+
+        hist = torch.zeros(steps, dtype=torch.float32, device=self.ctx.device)
+        for k in range(steps):
+            hist[k] = self.step().sum()
+        return hist.cpu().tolist()
