@@ -80,6 +80,7 @@ LOAD_BYTES = {"node_visits": 64, "tri_tests": 48, "vertices": 24 + 4 * 16, "lit"
 # (7), the exponential (2) and the weighted sums (7)
 DENOISE_PARAMS = {"radius": 5, "sigma_s": 2.0, "sigma_albedo": 0.1, "sigma_normal": 0.3, "sigma_depth": 0.1}
 DENOISE_FLOP_PER_TAP = 34
+FIT_PAIRS = 15  # the paper's training set size K
 
 
 def denoise_taps(H: int, W: int, r: int) -> int:
@@ -109,6 +110,7 @@ def _args():
     ap.add_argument("--serve-rates", default="5,8,11", help="Poisson arrival rates (requests/s) of the load sweep")
     ap.add_argument("--heightfield-steps", type=int, default=2, help="timed steps of the 200k-triangle workload (0 = skip)")
     ap.add_argument("--comp-steps", type=int, default=100, help="Adam steps of the full compensation run (0 = skip)")
+    ap.add_argument("--fit-steps", type=int, default=10, help="timed steps of the Eq. 9 scene fit (0 = skip)")
     ap.add_argument("--denoise-steps", type=int, default=20,
                     help="timed calls of the Eq. 11 filter and denoised compensation steps (0 = skip)")
     return ap.parse_args()
@@ -553,6 +555,51 @@ def main():
                                       "workload": f"{FWD_BWD_WORKLOAD} with the loss on D(Ic), one CUDA graph"},
         }
 
+    # ------------------------------------------------------------ scene-parameter fitting (Eq. 9)
+    fit_out = None
+    if args.fit_steps > 0:
+        from paper_2503_12174_gb300 import fit
+
+        fs = scenes.corner(res=256, tex=256, spp=16, bounces=3, seed=6000 + rank)
+        fh = ctx.upload(fs.verts, fs.tris, fs.uv)
+        f_alb, f_rough = torch.from_numpy(fs.albedo).to(dev), torch.from_numpy(fs.rough).to(dev)
+        fview, fprm = dpcs.view_of(fs), dpcs.make_params(fs.params)
+        frng = np.random.default_rng(6100 + rank)
+        pairs = []
+        for i in range(FIT_PAIRS):  # captures: the true scene at 64 spp
+            Ip_i = torch.from_numpy(scenes.blob_image(frng, fs.Hp, fs.Wp).astype(np.float32)).to(dev)
+            cap, _ = ctx.render(fh, f_alb, f_rough, Ip_i, fview, fprm, 64, fs.bounces, 6200 + i)
+            pairs.append((Ip_i, cap))
+        p0 = scenes.Params(gamma_p=(2.5, 2.5, 2.5), gain_p=fs.params.gain_p, gamma_c=(0.7, 0.7, 0.7),
+                           gain_c=fs.params.gain_c, wb=(1.0, 1.0, 1.0), k_proj=fs.params.k_proj, ks=fs.params.ks,
+                           f0=fs.params.f0)
+        half = torch.full_like(f_alb, 0.5)
+        fobj = fit.SceneFit(ctx, fh, fview, dpcs.make_params(p0), half, torch.full_like(f_rough, 0.5), pairs, fs.spp,
+                            fs.bounces, tv_weight=1e-5, denoise=dpcs.make_denoise_params(**DENOISE_PARAMS),
+                            seed=6300 + rank)
+        fobj.step()  # warm-up
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        e0.record(stream)
+        fhist = fobj.run(args.fit_steps)
+        e1.record(stream)
+        barrier()
+        fit_ms = max_over_ranks(e0.elapsed_time(e1))
+        true_alb = f_alb.double()
+        fit_out = {
+            "workload": f"Eq. 9 fit on the corner scene at {fs.Hc}x{fs.Wc} (camera, projector, textures): "
+                        f"{FIT_PAIRS} projector/capture pairs per step at {fs.spp} spp, {fs.bounces} bounces, "
+                        "Eq. 11 denoiser before the L1 loss, TV 1e-5, Adam on albedo, roughness, gamma_p, gamma_c, w",
+            "steps": args.fit_steps, "ms_per_step": fit_ms / args.fit_steps,
+            "Msamples_per_s": FIT_PAIRS * fs.n_samples * args.fit_steps * ws / (fit_ms / 1e3) / 1e6,
+            "loss_first": float(fhist[0]), "loss_last": float(fhist[-1]),
+            "albedo_mae_start": float((half.double() - true_alb).abs().mean()),
+            "albedo_mae_end": float((fobj.albedo.double() - true_alb).abs().mean()),
+        }
+        del fobj, pairs
+        ctx.free(fh)
+
     # ------------------------------------------------------------ large displaced surface (T = 199,712)
     hf_out = None
     if args.heightfield_steps > 0:
@@ -661,6 +708,7 @@ def main():
             "roofline_atomic": roof_atomic,
             "compensation": comp_out,
             "denoise": den_out,
+            "fit": fit_out,
             "heightfield": hf_out,
             "serving": serving_out,
             "cpu_baseline": cpu,
