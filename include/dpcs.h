@@ -183,6 +183,20 @@ dpcs_status dpcs_debug_set_visit_cap(dpcs_ctx *ctx, int32_t cap);
 dpcs_status dpcs_scene_upload(dpcs_ctx *ctx, const float *verts, int32_t V, const int32_t *tris, int32_t T,
                               const float *uv, void *stream, dpcs_scene *out);
 
+/*
+ * Move the vertices of an uploaded scene (novel scene simulation and
+ * deforming surfaces, Sec. 4.4: a morphing mesh re-lit frame by frame).
+ * verts (host, V x 3) are the new positions of the same V vertices; the
+ * triangles and texture coordinates stay as uploaded.  The library rewrites
+ * its triangle records and refits every box of the existing tree bottom-up
+ * (topology and leaf order kept, so the tree stays valid; it loses quality
+ * as the motion grows, and a re-upload rebuilds it).  Enqueued on `stream`
+ * after the host copy; renders that use the scene must be ordered after it
+ * on the same stream.  DPCS_ERR_INVALID_ARG if V differs from the upload or
+ * a coordinate is not finite; DPCS_ERR_NOT_FOUND for an unknown scene.
+ */
+dpcs_status dpcs_scene_update(dpcs_ctx *ctx, dpcs_scene scene, const float *verts, int32_t V, void *stream);
+
 /* Release a scene's device memory. */
 dpcs_status dpcs_scene_free(dpcs_ctx *ctx, dpcs_scene scene);
 

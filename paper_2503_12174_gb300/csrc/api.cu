@@ -379,16 +379,22 @@ dpcs_status dpcs_scene_upload(dpcs_ctx *c, const float *verts, int32_t V, const 
     sc.T = T;
     const size_t n = (size_t)(T > 0 ? T : 1);
     const size_t nn = (size_t)(T > 1 ? T - 1 : 1);
-    sc.bytes = nn * 64 + n * 48 + n * 24 + n * 8;
+    const size_t nv = (size_t)(V > 0 ? V : 1);
+    sc.V = V;
+    sc.bytes = nn * 64 + n * 48 + n * 24 + n * 8 + n * 12 + nv * 8;
     if ((s = dev_alloc(c, (void **)&sc.nodes, nn * 64, "scene nodes")) ||
         (s = dev_alloc(c, (void **)&sc.tris, n * 48, "scene triangles")) ||
         (s = dev_alloc(c, (void **)&sc.tuv, n * 24, "scene uv")) ||
         (s = dev_alloc(c, (void **)&sc.codes, n * 4, "scene codes")) ||
-        (s = dev_alloc(c, (void **)&sc.order, n * 4, "scene order"))) {
+        (s = dev_alloc(c, (void **)&sc.order, n * 4, "scene order")) ||
+        (s = dev_alloc(c, (void **)&sc.vidx, n * 12, "scene vertex indices")) ||
+        (s = dev_alloc(c, (void **)&sc.uv, nv * 8, "scene vertex uv"))) {
         dev_free(c, sc.nodes, sc.nodes ? nn * 64 : 0);
         dev_free(c, sc.tris, sc.tris ? n * 48 : 0);
         dev_free(c, sc.tuv, sc.tuv ? n * 24 : 0);
         dev_free(c, sc.codes, sc.codes ? n * 4 : 0);
+        dev_free(c, sc.order, sc.order ? n * 4 : 0);
+        dev_free(c, sc.vidx, sc.vidx ? n * 12 : 0);
         return s;
     }
     if (T > 0) {
@@ -407,6 +413,9 @@ dpcs_status dpcs_scene_upload(dpcs_ctx *c, const float *verts, int32_t V, const 
         if (e != cudaSuccess) return cuda_fail(c, e, "scene upload");
         int nl = launch_lbvh_build(dv, V, dt, T, du, sc, c->build.p, c->build.n, st);
         if ((s = check_launch(c, nl, "LBVH build"))) return s;
+        e = cudaMemcpyAsync(sc.vidx, dt, tb, cudaMemcpyDeviceToDevice, st);  // kept for dpcs_scene_update
+        if (e == cudaSuccess) e = cudaMemcpyAsync(sc.uv, du, ub, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(c, e, "scene upload");
         e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return cuda_fail(c, e, "LBVH build");
     } else {
@@ -431,8 +440,33 @@ dpcs_status dpcs_scene_free(dpcs_ctx *c, dpcs_scene scene) {
     dev_free(c, s.tuv, n * 24);
     dev_free(c, s.codes, n * 4);
     dev_free(c, s.order, n * 4);
+    dev_free(c, s.vidx, n * 12);
+    dev_free(c, s.uv, (size_t)(s.V > 0 ? s.V : 1) * 8);
     c->scenes.erase(it);
     return DPCS_OK;
+}
+
+dpcs_status dpcs_scene_update(dpcs_ctx *c, dpcs_scene scene, const float *verts, int32_t V, void *stream) {
+    if (!c) return DPCS_ERR_INVALID_ARG;
+    auto it = c->scenes.find(scene);
+    if (it == c->scenes.end()) return fail(c, DPCS_ERR_NOT_FOUND, "unknown scene handle");
+    Scene &sc = it->second;
+    if (V != sc.V) return fail(c, DPCS_ERR_INVALID_ARG, "scene_update: vertex count differs from the upload");
+    if (sc.T <= 0) return DPCS_OK;
+    if (!verts) return fail(c, DPCS_ERR_INVALID_ARG, "scene_update: null vertices");
+    for (int64_t i = 0; i < 3 * (int64_t)V; ++i)
+        if (!isfinite(verts[i])) return fail(c, DPCS_ERR_INVALID_ARG, "scene_update: non-finite vertex");
+    dpcs_status s = set_device(c);
+    if (s) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t vb = (size_t)V * 12;
+    if ((s = ensure(c, c->upload, vb, "upload staging")) ||
+        (s = ensure(c, c->build, lbvh_refit_scratch_bytes(sc.T), "refit scratch")))
+        return s;
+    cudaError_t e = cudaMemcpyAsync(c->upload.p, verts, vb, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "scene_update upload");
+    return check_launch(c, launch_lbvh_refit((const float *)c->upload.p, sc, c->build.p, c->build.n, st),
+                        "LBVH refit");
 }
 
 dpcs_status dpcs_scene_export(dpcs_ctx *c, dpcs_scene scene, uint32_t *codes, int32_t *order, int32_t *child,

@@ -27,6 +27,9 @@ struct Scene {
     float2 *tuv = nullptr;     // 3 x T
     uint32_t *codes = nullptr; // sorted Morton codes, T
     int32_t *order = nullptr;  // original triangle of each sorted position, T
+    int32_t V = 0;             // vertex count the mesh was uploaded with
+    int32_t *vidx = nullptr;   // triangle vertex indices, 3 x T (kept for refits)
+    float *uv = nullptr;       // per-vertex texture coordinates, 2 x V (kept for refits)
     size_t bytes = 0;
 };
 constexpr int32_t kEmptyRoot = (int32_t)0x80000000;
@@ -76,6 +79,11 @@ struct BatchSeg {
 int launch_lbvh_build(const float *d_verts, int32_t V, const int32_t *d_tris, int32_t T, const float *d_uv,
                       Scene &sc, void *scratch, size_t scratch_bytes, cudaStream_t st);
 size_t lbvh_scratch_bytes(int32_t T);
+// Refit after the vertices moved: new triangle records and node boxes over
+// the existing tree (topology and leaf order kept).  d_verts holds sc.V
+// vertices.  Returns the kernels enqueued or a negative dpcs_status.
+int launch_lbvh_refit(const float *d_verts, Scene &sc, void *scratch, size_t scratch_bytes, cudaStream_t st);
+size_t lbvh_refit_scratch_bytes(int32_t T);
 
 int launch_prf(const float *Ip, int64_t ntex, const float gamma_p[3], float gain_p, float4 *Ep, cudaStream_t st);
 int launch_pack_tex(const float *albedo, const float *rough, int64_t ntex, float4 *tex, cudaStream_t st);

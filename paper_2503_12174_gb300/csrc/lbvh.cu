@@ -235,6 +235,17 @@ __global__ void k_refit(const float *__restrict__ verts, const int32_t *__restri
     }
 }
 
+// parent of every internal node and leaf, read back from the child
+// references the Karras pass stored in the nodes
+__global__ void k_parents(const float4 *__restrict__ nodes, int T, int32_t *__restrict__ parent) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= T - 1) return;
+    const float4 r = nodes[4 * i + 3];
+    const int left = __float_as_int(r.x), right = __float_as_int(r.y);
+    parent[left >= 0 ? left : T - 1 + ~left] = i;
+    parent[right >= 0 ? right : T - 1 + ~right] = i;
+}
+
 inline size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
 
 }  // namespace
@@ -244,6 +255,29 @@ size_t lbvh_scratch_bytes(int32_t T) {
     const size_t nb = (n + kSortTile - 1) / kSortTile;
     return align256(3 * n * 4) + align256(6 * 4) + 4 * align256(n * 4) + align256(256 * nb * 4) +
            align256((2 * n) * 4) + align256(n * 4);
+}
+
+size_t lbvh_refit_scratch_bytes(int32_t T) {
+    const size_t n = (size_t)(T > 0 ? T : 1);
+    return align256((2 * n) * 4) + align256(n * 4);
+}
+
+int launch_lbvh_refit(const float *d_verts, Scene &sc, void *scratch, size_t scratch_bytes, cudaStream_t st) {
+    const int T = sc.T;
+    if (T <= 0) return 0;
+    if (scratch_bytes < lbvh_refit_scratch_bytes(T)) return DPCS_ERR_INVALID_ARG;
+    const size_t n = (size_t)T;
+    int32_t *parent = (int32_t *)scratch;
+    int32_t *flags = (int32_t *)((char *)scratch + align256(2 * n * 4));
+    const int tb = 256, gb = (T + tb - 1) / tb;
+    int launches = 0;
+    if (T >= 2) {
+        cudaMemsetAsync(flags, 0, n * 4, st);
+        k_parents<<<(T - 1 + tb - 1) / tb, tb, 0, st>>>(sc.nodes, T, parent);
+        ++launches;
+    }
+    k_refit<<<gb, tb, 0, st>>>(d_verts, sc.vidx, sc.uv, sc.order, T, sc.nodes, parent, flags, sc.tris, sc.tuv);
+    return launches + 1;
 }
 
 int launch_lbvh_build(const float *d_verts, int32_t V, const int32_t *d_tris, int32_t T, const float *d_uv,

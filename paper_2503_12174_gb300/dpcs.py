@@ -34,7 +34,7 @@ EXPORTED = [
     "dpcs_counters_read", "dpcs_debug_set_visit_cap", "dpcs_render_noalloc", "dpcs_serve_create", "dpcs_serve_destroy", "dpcs_serve_add_scene",
     "dpcs_serve_submit", "dpcs_serve_step", "dpcs_serve_query", "dpcs_serve_drain", "dpcs_serve_stats_get",
     "dpcs_probe_l2_load", "dpcs_probe_atomic4", "dpcs_gbuffer", "dpcs_denoise", "dpcs_denoise_backward",
-    "dpcs_l1_loss", "dpcs_tv_loss",
+    "dpcs_l1_loss", "dpcs_tv_loss", "dpcs_scene_update",
 ]
 
 DPCS_REQ_RELIGHT = 0
@@ -109,6 +109,7 @@ _SIGS = {
     "dpcs_scene_upload": (ctypes.c_int32, [_P, _P, ctypes.c_int32, _P, ctypes.c_int32, _P, _P,
                                            ctypes.POINTER(ctypes.c_uint64)]),
     "dpcs_scene_free": (ctypes.c_int32, [_P, ctypes.c_uint64]),
+    "dpcs_scene_update": (ctypes.c_int32, [_P, ctypes.c_uint64, _P, ctypes.c_int32, _P]),
     "dpcs_scene_export": (ctypes.c_int32, [_P, ctypes.c_uint64, _P, _P, _P, _P]),
     "dpcs_trace": (ctypes.c_int32, [_P, ctypes.c_uint64, _P, _P, ctypes.c_int64, _P, _P, _P]),
     "dpcs_render": (ctypes.c_int32, [_P, ctypes.c_uint64, _P, _P, ctypes.c_int32, ctypes.c_int32, _P,
@@ -321,6 +322,10 @@ def dpcs_l2_loss(ctx, Ic, target, n, dIc, loss, stream):
     return load_library().dpcs_l2_loss(ctx, Ic, target, n, dIc, loss, stream)
 
 
+def dpcs_scene_update(ctx, scene, verts, V, stream):
+    return load_library().dpcs_scene_update(ctx, scene, verts, V, stream)
+
+
 def dpcs_l1_loss(ctx, Ic, target, n, scale, dIc, loss, stream):
     return load_library().dpcs_l1_loss(ctx, Ic, target, n, scale, dIc, loss, stream)
 
@@ -448,6 +453,12 @@ class Context:
                                len(tris), uv.ctypes.data_as(_P), _stream(stream), ctypes.byref(out))
         self.check(st, "scene_upload")
         return out.value
+
+    def update(self, scene: int, verts, stream=None):
+        """New positions for the scene's vertices (same count); refits the tree."""
+        verts = np.ascontiguousarray(verts, np.float32)
+        st = self.lib.dpcs_scene_update(self.handle, scene, verts.ctypes.data_as(_P), len(verts), _stream(stream))
+        self.check(st, "scene_update")
 
     def free(self, scene: int):
         self.check(self.lib.dpcs_scene_free(self.handle, scene), "scene_free")
