@@ -47,7 +47,7 @@ L2_FLUSH_BYTES = 256 << 20
 # ncu capture summarised in profiles/k_render_corner256.md.  It holds only for
 # the kernel sources it was measured on; once they change, the roofline's
 # traffic is reported as null until a new capture is taken.
-RENDER_TRAFFIC = {"bytes": 36694784, "sources_sha256": "5064f5ad0b0e0d0b41a81199600e82b50e1128582e67ffcee487e1b637f464d8"}
+RENDER_TRAFFIC = {"bytes": 36866816, "sources_sha256": "26cc7bc1037f74f5cfdc4abcde9d0afcd5ff898be6a81d2eab5dc18d54d09a89"}
 KERNEL_SOURCES = ("paper_2503_12174_gb300/csrc/render.cu", "paper_2503_12174_gb300/csrc/device.cuh",
                   "paper_2503_12174_gb300/csrc/internal.h")
 
@@ -637,6 +637,34 @@ def main():
             ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev)) / args.heightfield_steps
             res[name] = {"value": hs.Hc * hs.Wc * spp * ws / (ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": ms,
                          "spp": spp}
+        # a morphing surface re-lit frame by frame (Sec. 4.4): per frame the
+        # new vertex positions go up from host memory, the tree is refitted
+        # and the frame is rendered at 16 spp; against a full re-upload
+        nfr = args.heightfield_steps + 2
+        frames = [(hs.verts + np.float32(0.01 * np.sin(0.7 * f + 3.0 * hs.verts[:, :1]))
+                   * np.asarray([0.0, 0.0, 1.0], np.float32)).astype(np.float32) for f in range(nfr)]
+        ctx.update(hh, frames[0])
+        hf_fwd(16)
+        torch.cuda.synchronize()
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(nfr - 1)]
+        barrier()
+        for f in range(1, nfr):
+            ev[f - 1][0].record(stream)
+            ctx.update(hh, frames[f])
+            ev[f - 1][1].record(stream)
+            hf_fwd(16)
+            ev[f - 1][2].record(stream)
+        barrier()
+        torch.cuda.synchronize()
+        upd_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b, _ in ev)) / (nfr - 1)
+        frame_ms = max_over_ranks(sum(a.elapsed_time(c) for a, _, c in ev)) / (nfr - 1)
+        t0 = time.perf_counter()
+        hh2 = ctx.upload(frames[-1], hs.tris, hs.uv)
+        rebuild_ms = (time.perf_counter() - t0) * 1e3
+        ctx.free(hh2)
+        res["morph"] = {"workload": "heightfield vertices moved every frame, then rendered at 16 spp",
+                        "update_ms": upd_ms, "frame_ms": frame_ms, "full_upload_ms": rebuild_ms,
+                        "frames": nfr - 1}
         ctx.sync()
         ctx.free(hh)
         hf_out = {"workload": f"heightfield T={hs.T}, camera {hs.Hc}x{hs.Wc}, projector {hs.Wp}x{hs.Hp}, "
