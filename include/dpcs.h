@@ -336,6 +336,29 @@ dpcs_status dpcs_denoise_backward(dpcs_ctx *ctx, const float *dOut, const float 
                                   void *stream);
 
 /*
+ * Forward render, per-pixel loss and adjoint in one call, for the losses of
+ * Eqs. 13 and 9 that compare each pixel with a target on its own:
+ *   loss_kind 0 (L2): *loss = 1/2 scale sum |Ic - target|^2, dLoss/dIc = scale (Ic - target)
+ *   loss_kind 1 (L1): *loss = scale sum |Ic - target|,       dLoss/dIc = scale sign(Ic - target)
+ * Inputs are those of dpcs_render plus target (dev, Hc x Wc x 3); Ic (dev,
+ * required) and Ec (dev, may be NULL) receive the forward results, equal bit
+ * for bit to dpcs_render's; *loss (dev float) the loss; dIp, dAlbedo,
+ * dRough, dParams are ACCUMULATED as in dpcs_render_backward.
+ * When every lane's paths fit its vertex records (ceil(spp / L) samples of
+ * `bounces` vertices, at most 4 samples and 12 vertices; L is the lanes per
+ * pixel, min(32, the largest power of two <= spp)), each path is traced
+ * once: the warp renders its pixels, derives dLoss/dEc from them and sweeps
+ * the recorded vertices backwards.  Otherwise the call renders, takes the
+ * loss and replays the paths, as the separate calls would.
+ */
+dpcs_status dpcs_render_loss_backward(dpcs_ctx *ctx, dpcs_scene scene, const float *albedo, const float *rough,
+                                      int32_t Ht, int32_t Wt, const float *Ip, const dpcs_view *view,
+                                      const dpcs_params *params, int32_t spp, int32_t bounces, uint64_t seed,
+                                      const float *target, int32_t loss_kind, float scale, float *Ic, float *Ec,
+                                      float *loss, float *dIp, float *dAlbedo, float *dRough, float *dParams,
+                                      void *stream);
+
+/*
  * L2 image loss of projector compensation (Eq. 13 with a squared norm):
  * loss = 1/2 sum (Ic - target)^2 written to *loss (dev, 1 float32, overwritten),
  * dIc = Ic - target (dev, n floats, overwritten).  n = number of floats.

@@ -47,7 +47,7 @@ struct dpcs_ctx {
     std::map<uint64_t, Scene> scenes;
     uint64_t next_scene = 1;
     // scratch
-    Buf ep4, tex4, gE, dEp4, dtex4, acc, partial, build, upload;
+    Buf ep4, tex4, gE, dEp4, dtex4, acc, partial, build, upload, pix;  // pix: per-pixel dIc and Ec of the unfused loss path
     // measurement support
     unsigned long long *counters = nullptr;  // 8 totals (DPCS_COUNTERS build)
     bool timing = false;
@@ -272,7 +272,7 @@ dpcs_status dpcs_destroy(dpcs_ctx *c) {
         cudaFree(s.codes);
         cudaFree(s.order);
     }
-    Buf *bufs[] = {&c->ep4, &c->tex4, &c->gE, &c->dEp4, &c->dtex4, &c->acc, &c->partial, &c->build, &c->upload};
+    Buf *bufs[] = {&c->ep4, &c->tex4, &c->gE, &c->dEp4, &c->dtex4, &c->acc, &c->partial, &c->build, &c->upload, &c->pix};
     for (Buf *b : bufs)
         if (b->p) cudaFree(b->p);
     cudaFree(c->status);
@@ -582,6 +582,72 @@ dpcs_status dpcs_render_backward(dpcs_ctx *c, dpcs_scene scene, const float *alb
     if (want_tex) nl += launch_tex_backward((const float4 *)c->dtex4.p, nt, dAlbedo, dRough, st);
     if (dParams) nl += launch_finalize_params(acc, dParams, st);
     return check_launch(c, nl, "render_backward");
+}
+
+dpcs_status dpcs_render_loss_backward(dpcs_ctx *c, dpcs_scene scene, const float *albedo, const float *rough,
+                                      int32_t Ht, int32_t Wt, const float *Ip, const dpcs_view *view,
+                                      const dpcs_params *params, int32_t spp, int32_t bounces, uint64_t seed,
+                                      const float *target, int32_t loss_kind, float scale, float *Ic, float *Ec,
+                                      float *loss, float *dIp, float *dAlbedo, float *dRough, float *dParams,
+                                      void *stream) {
+    RenderArgs a;
+    Scene *sc = nullptr;
+    dpcs_status s = prepare(c, scene, albedo, rough, Ht, Wt, Ip, view, params, spp, bounces, seed, a, &sc);
+    if (s) return s;
+    if (!target || !Ic || !loss) return fail(c, DPCS_ERR_INVALID_ARG, "null target, Ic or loss");
+    if ((loss_kind != 0 && loss_kind != 1) || !(scale > 0.0f))
+        return fail(c, DPCS_ERR_INVALID_ARG, "loss_kind must be 0 (L2) or 1 (L1) and scale > 0");
+    if ((s = set_device(c))) return s;
+    const int64_t np = (int64_t)view->Hp * view->Wp, nt = (int64_t)Ht * Wt, npix = (int64_t)view->Hc * view->Wc;
+    const int L = 1 << a.log2L;
+    const int spl = (spp + L - 1) / L;  // samples per lane
+    const bool fused = spl <= kFusedSamples && spl * bounces <= kFusedRecs;
+    const bool want_tex = dAlbedo || dRough;
+    if ((s = ensure(c, c->ep4, (size_t)np * 16, "Ep scratch")) ||
+        (s = ensure(c, c->tex4, (size_t)nt * 16, "texture scratch")) ||
+        (s = ensure(c, c->dEp4, (size_t)np * 16, "dEp scratch")) ||
+        (s = ensure(c, c->acc, 16 * sizeof(double), "parameter accumulators")) ||
+        (want_tex && (s = ensure(c, c->dtex4, (size_t)nt * 16, "dtex scratch"))) ||
+        (!fused && ((s = ensure(c, c->gE, (size_t)npix * 12, "dEc scratch")) ||
+                    (s = ensure(c, c->pix, (size_t)npix * 24, "per-pixel loss scratch")))))
+        return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    double *acc = (double *)c->acc.p;
+    cudaMemsetAsync(acc, 0, 16 * sizeof(double), st);
+    cudaMemsetAsync(c->dEp4.p, 0, (size_t)np * 16, st);
+    if (want_tex) cudaMemsetAsync(c->dtex4.p, 0, (size_t)nt * 16, st);
+    int nl = launch_prf(Ip, np, params->gamma_p, params->gain_p, (float4 *)c->ep4.p, st);
+    nl += launch_pack_tex(albedo, rough, nt, (float4 *)c->tex4.p, st);
+    a.Ep = (const float4 *)c->ep4.p;
+    a.tex = (const float4 *)c->tex4.p;
+    a.Ic = Ic;
+    a.dEp = (float4 *)c->dEp4.p;
+    a.dtex = want_tex ? (float4 *)c->dtex4.p : nullptr;
+    const LossArgs l{target, scale, loss_kind, acc};
+    if (fused) {
+        a.Ec = Ec;
+        TimedLaunch *tl = timing_begin(c, 0, st);
+        nl += launch_render_grad(a, l, st);
+        timing_end(tl, st);
+    } else {  // render, per-pixel loss, Eq. 5 adjoint, replay
+        float *dIc = (float *)c->pix.p, *ec = Ec ? Ec : (float *)c->pix.p + 3 * npix;
+        a.Ec = ec;
+        TimedLaunch *tl = timing_begin(c, 0, st);
+        nl += launch_render(a, st);
+        timing_end(tl, st);
+        nl += launch_pixel_loss(Ic, npix * 3, l, dIc, st);
+        nl += launch_crf_backward(dIc, ec, Ic, npix, params->gamma_c, params->gain_c, params->wb, (float *)c->gE.p,
+                                  acc, st);
+        a.gE = (const float *)c->gE.p;
+        TimedLaunch *tr = timing_begin(c, 1, st);
+        nl += launch_replay(a, st);
+        timing_end(tr, st);
+    }
+    nl += launch_loss_out(acc, loss, st);
+    nl += launch_prf_backward(Ip, (const float4 *)c->dEp4.p, np, params->gamma_p, params->gain_p, dIp, acc, st);
+    if (want_tex) nl += launch_tex_backward((const float4 *)c->dtex4.p, nt, dAlbedo, dRough, st);
+    if (dParams) nl += launch_finalize_params(acc, dParams, st);
+    return check_launch(c, nl, "render_loss_backward");
 }
 
 dpcs_status dpcs_l2_loss(dpcs_ctx *c, const float *Ic, const float *target, int64_t n, float *dIc, float *loss,

@@ -65,6 +65,18 @@ struct RenderArgs {
     int32_t visit_cap;             // traversal steps per ray before giving up (0 = 2T + 16)
 };
 
+// Per-pixel loss of the fused forward + adjoint kernel (k_render_grad).
+struct LossArgs {
+    const float *target;  // Hc x Wc x 3
+    float scale;          // kind 0: loss 1/2 scale |Ic - t|^2, gradient scale (Ic - t); kind 1: scale |Ic - t|, scale sign
+    int32_t kind;
+    double *acc;          // parameter accumulators; acc[11] receives the loss
+};
+// Vertex records the fused kernel keeps per lane: up to kFusedSamples
+// samples (ceil(spp / L)) and kFusedRecs vertices in all.
+constexpr int kFusedSamples = 4;
+constexpr int kFusedRecs = 12;
+
 // One pixel range of one request in a batched render launch.
 struct BatchSeg {
     int64_t vb_begin;   // first virtual block of the segment
@@ -97,6 +109,9 @@ int launch_trace(const Scene &sc, const float *o, const float *d, int64_t n, flo
 int launch_crf_backward(const float *dIc, const float *Ec, const float *Ic, int64_t npix, const float gamma_c[3],
                         float gain_c, const float wb[3], float *gE, double *acc, cudaStream_t st);
 int launch_replay(const RenderArgs &a, cudaStream_t st);
+int launch_render_grad(const RenderArgs &a, const LossArgs &l, cudaStream_t st);
+int launch_pixel_loss(const float *Ic, int64_t n, const LossArgs &l, float *dIc, cudaStream_t st);
+int launch_loss_out(const double *acc, float *loss, cudaStream_t st);
 int launch_prf_backward(const float *Ip, const float4 *dEp, int64_t ntex, const float gamma_p[3], float gain_p,
                         float *dIp, double *acc, cudaStream_t st);
 int launch_tex_backward(const float4 *dtex, int64_t ntex, float *dAlbedo, float *dRough, cudaStream_t st);

@@ -538,6 +538,179 @@ __global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB) k_replay(const
     cnt.flush(a.counters);
 }
 
+// Forward render, per-pixel loss and path-replay adjoint in one pass, for
+// losses that act on each pixel alone (the L2 loss of Eq. 13, the L1 term of
+// Eq. 9).  Each lane traces its samples as k_render does -- the same rounds,
+// the same per-lane sum, the same xor-shuffle tree, so Ec and Ic are those of
+// k_render bit for bit -- and records every vertex as k_replay does.  Once
+// the warp holds its pixels' Ec, every lane knows its pixel's dLoss/dEc
+// (the loss's gradient through Eq. 5), and runs the reverse sweeps over the
+// vertices it recorded: the paths are traced once, not twice.  The host
+// calls it only when ceil(spp / L) <= kFusedSamples and ceil(spp / L) *
+// bounces <= kFusedRecs.
+__global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB) k_render_grad(const RenderArgs a, const LossArgs l) {
+    const int L = 1 << a.log2L;
+    const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t pix = gt >> a.log2L;
+    const int sl = (int)(gt & (L - 1));
+    const bool valid = pix < (int64_t)a.Hc * a.Wc;
+    Cnt cnt;
+    __shared__ float4 s_row[kRenderBlock];  // per-warp rows for scatter_add4
+    int s = valid ? sl : a.spp;
+    int b = 1, nv = 0, k = 0;
+    bool shadow = false, has_ext = false, pending = false;
+    f3 sum = mk3(0.f, 0.f, 0.f);
+    f3 beta = sum, c = sum, ed = sum;
+    Ray ray;
+    ray.o = ray.d = ray.inv = beta;
+    float tmax = INFINITY;
+    Trav st;
+    int stack[kStack];
+    VRec rec[kFusedRecs];
+    int nvs[kFusedSamples];
+#pragma unroll
+    for (int i = 0; i < kFusedSamples; ++i) nvs[i] = 0;
+    if (s < a.spp && a.bounces > 0) {
+        f3 o, d;
+        camera_ray(a, (uint32_t)pix, (uint32_t)s, o, d);
+        ray = make_ray(o, d);
+        beta = mk3(1.f, 1.f, 1.f);
+        cnt.add(kCntPath);
+    } else {
+        s = a.spp;
+    }
+    const int64_t max_iter = ((int64_t)(a.spp / L + 1) * (2 * a.bounces + 1)) * (2 * (int64_t)a.T + 18);
+    int64_t iter = 0;
+    while (s < a.spp) {
+        VRec *rs = rec + k * a.bounces;  // this sample's records
+        while (true) {  // the lane's current path; the warp starts its next samples together
+            if (++iter > max_iter) {
+                atomicOr(a.status, kStatusTraversalLimit);
+                s = a.spp;
+                nv = 0;
+                break;
+            }
+            if (!pending) {
+                cnt.add(shadow ? kCntShadow : kCntRay);
+                trav_begin(st, a.root, shadow ? tmax : INFINITY, shadow);
+                pending = true;
+            }
+            if (!trav_resume(a.nodes, a.tris, a.root, a.T, ray, st, stack, a.status, cnt, 0, a.visit_cap)) continue;
+            pending = false;
+            const bool hit = st.h.pos >= 0;
+            bool end = false;
+            if (shadow) {
+                if (hit) {
+                    rs[nv - 1].G = 0.0f;  // occluded: no projector light at this vertex
+                } else {
+                    sum = sum + c;
+                    cnt.add(kCntLit);
+                }
+                shadow = false;
+                if (has_ext) {
+                    ray = make_ray(ray.o, ed);
+                    ++b;
+                } else {
+                    end = true;
+                }
+            } else if (!hit) {
+                end = true;
+            } else {
+                cnt.add(kCntVert);
+                const Surf S = surface_at(a, st.h, ray.d);
+                VRec *R = &rs[nv++];
+                R->tx0 = S.tb.x0; R->ty0 = S.tb.y0; R->tfx = S.tb.fx; R->tfy = S.tb.fy;
+                R->beta[0] = beta.x; R->beta[1] = beta.y; R->beta[2] = beta.z;
+                R->rho[0] = S.rho.x; R->rho[1] = S.rho.y; R->rho[2] = S.rho.z;
+                R->G = 0.0f; R->cw = 0.0f; R->unc = 0u; R->sp = R->dsp = R->si = R->dsi = 0.0f;
+                Nee N;
+                const bool cand = nee_prepare(a, S, N);
+                if (cand) {
+                    unsigned unc;
+                    c = nee_contrib(a, beta, N, unc);
+                    R->px0 = N.pb.x0; R->py0 = N.pb.y0; R->pfx = N.pb.fx; R->pfy = N.pb.fy;
+                    R->Ep[0] = N.ep.x; R->Ep[1] = N.ep.y; R->Ep[2] = N.ep.z;
+                    R->G = N.G; R->sp = N.sp; R->dsp = N.dsp; R->unc = unc;
+                }
+                has_ext = false;
+                if (b < a.bounces) {
+                    Cont C;
+                    if (continue_prepare(a, (uint32_t)pix, (uint32_t)s, b, S, C)) {
+                        cnt.add(kCntCont);
+                        beta = beta * C.w;
+                        ed = C.wi;
+                        has_ext = true;
+                        R->si = C.si; R->dsi = C.dsi; R->cw = C.cw;
+                    }
+                }
+                if (cand) {
+                    shadow = true;
+                    ray = make_ray(N.so, N.sdir);
+                    tmax = N.smax;
+                } else if (has_ext) {
+                    ray = make_ray(S.x + S.n * kRayEps, ed);
+                    ++b;
+                } else {
+                    end = true;
+                }
+            }
+            if (end) break;
+        }
+        nvs[k < kFusedSamples ? k : kFusedSamples - 1] = nv;
+        ++k;
+        nv = 0;
+        s += L;
+        if (s < a.spp) {
+            f3 o, d;
+            camera_ray(a, (uint32_t)pix, (uint32_t)s, o, d);
+            ray = make_ray(o, d);
+            beta = mk3(1.f, 1.f, 1.f);
+            b = 1;
+            shadow = false;
+            has_ext = false;
+            cnt.add(kCntPath);
+        }
+    }
+    cnt.flush(a.counters);
+    // every lane of a pixel ends with the pixel's sum (the tree of render_lanes)
+    for (int off = L >> 1; off > 0; off >>= 1) {
+        sum.x += __shfl_xor_sync(0xffffffffu, sum.x, off);
+        sum.y += __shfl_xor_sync(0xffffffffu, sum.y, off);
+        sum.z += __shfl_xor_sync(0xffffffffu, sum.z, off);
+    }
+    const float inv = 1.0f / (float)a.spp;
+    const float ec[3] = {sum.x * inv, sum.y * inv, sum.z * inv};
+    float gb_in[3] = {0.f, 0.f, 0.f};
+    float v[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // gamma_c(3), Gc, wb(3), loss
+    if (valid) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const float ic = crf(ec[j], a.gain_c, a.wb[j], a.gamma_c[j]);
+            if (sl == 0) {
+                if (a.Ec) a.Ec[3 * pix + j] = ec[j];
+                a.Ic[3 * pix + j] = ic;
+            }
+            const float d = ic - l.target[3 * pix + j];
+            const float g = l.kind == 0 ? l.scale * d : (d > 0.0f ? l.scale : (d < 0.0f ? -l.scale : 0.0f));
+            const float w = a.gain_c * a.wb[j] * ec[j];
+            if (w > 0.0f) {
+                const float da = a.gamma_c[j] * powf(w, a.gamma_c[j] - 1.0f);
+                gb_in[j] = g * da * a.gain_c * a.wb[j] * inv;
+                if (sl == 0) {
+                    v[j] += g * ic * logf(w);
+                    v[3] += g * da * a.wb[j] * ec[j];
+                    v[4 + j] += g * da * a.gain_c * ec[j];
+                }
+            }
+            if (sl == 0) v[7] += l.kind == 0 ? 0.5f * l.scale * d * d : l.scale * fabsf(d);
+        }
+    }
+    block_reduce_add<8>(v, l.acc + 4);  // acc[4..10]: gamma_c, Gc, wb; acc[11]: the loss
+    const bool any = gb_in[0] != 0.0f || gb_in[1] != 0.0f || gb_in[2] != 0.0f;
+    for (int i = 0; any && i < k && i < kFusedSamples; ++i)
+        replay_sweep(a, rec + i * a.bounces, nvs[i], gb_in, &s_row[threadIdx.x & ~31]);
+}
+
 // Eq. 1 adjoint: dIp += dEp Gp gamma Ip^(gamma-1); gamma_p and Gp reductions
 __global__ void k_prf_backward(const float *__restrict__ Ip, const float4 *__restrict__ dEp, int64_t ntex,
                                float g0, float g1, float g2, float gain, float *__restrict__ dIp, double *acc) {
@@ -572,6 +745,21 @@ __global__ void k_tex_backward(const float4 *__restrict__ dtex, int64_t ntex, fl
     }
     if (dRough) dRough[t] += g.w;
 }
+
+// the per-pixel loss of LossArgs as its own pass (when k_render_grad would
+// need more records than it keeps): dIc, and the loss into acc[11]
+__global__ void k_pixel_loss(const float *__restrict__ Ic, int64_t n, const LossArgs l, float *__restrict__ dIc) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    float v[1] = {0.0f};
+    if (i < n) {
+        const float d = Ic[i] - l.target[i];
+        dIc[i] = l.kind == 0 ? l.scale * d : (d > 0.0f ? l.scale : (d < 0.0f ? -l.scale : 0.0f));
+        v[0] = l.kind == 0 ? 0.5f * l.scale * d * d : l.scale * fabsf(d);
+    }
+    block_reduce_add<1>(v, l.acc + 11);
+}
+
+__global__ void k_loss_out(const double *__restrict__ acc, float *__restrict__ loss) { *loss = (float)acc[11]; }
 
 __global__ void k_finalize(const double *__restrict__ acc, float *__restrict__ dParams) {
     const int i = threadIdx.x;
@@ -631,6 +819,22 @@ int launch_crf_backward(const float *dIc, const float *Ec, const float *Ic, int6
 int launch_replay(const RenderArgs &a, cudaStream_t st) {
     const int64_t threads = ((int64_t)a.Hc * a.Wc) << a.log2L;
     k_replay<<<grid_for(threads, kRenderBlock), kRenderBlock, 0, st>>>(a);
+    return 1;
+}
+
+int launch_render_grad(const RenderArgs &a, const LossArgs &l, cudaStream_t st) {
+    const int64_t threads = ((int64_t)a.Hc * a.Wc) << a.log2L;
+    k_render_grad<<<grid_for(threads, kRenderBlock), kRenderBlock, 0, st>>>(a, l);
+    return 1;
+}
+
+int launch_pixel_loss(const float *Ic, int64_t n, const LossArgs &l, float *dIc, cudaStream_t st) {
+    k_pixel_loss<<<grid_for(n, 256), 256, 0, st>>>(Ic, n, l, dIc);
+    return 1;
+}
+
+int launch_loss_out(const double *acc, float *loss, cudaStream_t st) {
+    k_loss_out<<<1, 1, 0, st>>>(acc, loss);
     return 1;
 }
 

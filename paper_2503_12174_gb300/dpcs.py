@@ -34,7 +34,7 @@ EXPORTED = [
     "dpcs_counters_read", "dpcs_debug_set_visit_cap", "dpcs_render_noalloc", "dpcs_serve_create", "dpcs_serve_destroy", "dpcs_serve_add_scene",
     "dpcs_serve_submit", "dpcs_serve_step", "dpcs_serve_query", "dpcs_serve_drain", "dpcs_serve_stats_get",
     "dpcs_probe_l2_load", "dpcs_probe_atomic4", "dpcs_gbuffer", "dpcs_denoise", "dpcs_denoise_backward",
-    "dpcs_l1_loss", "dpcs_tv_loss", "dpcs_scene_update",
+    "dpcs_l1_loss", "dpcs_tv_loss", "dpcs_scene_update", "dpcs_render_loss_backward",
 ]
 
 DPCS_REQ_RELIGHT = 0
@@ -121,6 +121,10 @@ _SIGS = {
     "dpcs_render_backward": (ctypes.c_int32, [_P, ctypes.c_uint64, _P, _P, ctypes.c_int32, ctypes.c_int32, _P,
                                               ctypes.POINTER(DpcsView), ctypes.POINTER(DpcsParams), ctypes.c_int32,
                                               ctypes.c_int32, ctypes.c_uint64, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "dpcs_render_loss_backward": (ctypes.c_int32, [_P, ctypes.c_uint64, _P, _P, ctypes.c_int32, ctypes.c_int32, _P,
+                                                   ctypes.POINTER(DpcsView), ctypes.POINTER(DpcsParams),
+                                                   ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, _P, ctypes.c_int32,
+                                                   ctypes.c_float, _P, _P, _P, _P, _P, _P, _P, _P]),
     "dpcs_timing_enable": (ctypes.c_int32, [_P, ctypes.c_int32]),
     "dpcs_timing_read": (ctypes.c_int32, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_int64)]),
@@ -284,6 +288,13 @@ def dpcs_render_backward(ctx, scene, albedo, rough, Ht, Wt, Ip, view, params, sp
     return load_library().dpcs_render_backward(ctx, scene, albedo, rough, Ht, Wt, Ip, ctypes.byref(view),
                                                ctypes.byref(params), spp, bounces, seed, Ec, Ic, dIc, dIp, dAlbedo,
                                                dRough, dParams, stream)
+
+
+def dpcs_render_loss_backward(ctx, scene, albedo, rough, Ht, Wt, Ip, view, params, spp, bounces, seed, target,
+                              loss_kind, scale, Ic, Ec, loss, dIp, dAlbedo, dRough, dParams, stream):
+    return load_library().dpcs_render_loss_backward(ctx, scene, albedo, rough, Ht, Wt, Ip, ctypes.byref(view),
+                                                    ctypes.byref(params), spp, bounces, seed, target, loss_kind, scale,
+                                                    Ic, Ec, loss, dIp, dAlbedo, dRough, dParams, stream)
 
 
 def dpcs_timing_enable(ctx, on):
@@ -571,6 +582,32 @@ class Context:
                                             _stream(stream))
         self.check(st, "denoise_backward")
         return dIc
+
+    def render_loss_backward(self, scene: int, albedo, rough, Ip, view: DpcsView, params: DpcsParams, spp: int,
+                             bounces: int, seed: int, target, loss, loss_kind: int = 0, scale: float = 1.0, Ic=None,
+                             Ec=None, dIp=None, dAlbedo=None, dRough=None, dParams=None, stream=None):
+        """Render, per-pixel loss (0 = L2, 1 = L1) and adjoint in one call;
+        returns Ic.  Gradient outputs accumulate."""
+        import torch
+
+        Ht, Wt = albedo.shape[0], albedo.shape[1]
+        f32 = torch.float32
+        img = (view.Hc, view.Wc, 3)
+        if Ic is None:
+            Ic = torch.empty(img, dtype=f32, device=self.device)
+        st = self.lib.dpcs_render_loss_backward(
+            self.handle, scene, _ptr(albedo, "albedo", (Ht, Wt, 3), f32, self.device),
+            _ptr(rough, "rough", (Ht, Wt), f32, self.device), Ht, Wt,
+            _ptr(Ip, "Ip", (view.Hp, view.Wp, 3), f32, self.device), ctypes.byref(view), ctypes.byref(params),
+            int(spp), int(bounces), int(seed) & (2**64 - 1), _ptr(target, "target", img, f32, self.device),
+            int(loss_kind), float(scale), _ptr(Ic, "Ic", img, f32, self.device),
+            _ptr(Ec, "Ec", img, f32, self.device, allow_none=True), _ptr(loss, "loss", (1,), f32, self.device),
+            _ptr(dIp, "dIp", (view.Hp, view.Wp, 3), f32, self.device, allow_none=True),
+            _ptr(dAlbedo, "dAlbedo", (Ht, Wt, 3), f32, self.device, allow_none=True),
+            _ptr(dRough, "dRough", (Ht, Wt), f32, self.device, allow_none=True),
+            _ptr(dParams, "dParams", (11,), f32, self.device, allow_none=True), _stream(stream))
+        self.check(st, "render_loss_backward")
+        return Ic
 
     def l1_loss(self, Ic, target, dIc, loss, scale: float = 1.0, stream=None):
         """Eq. 9 data term: dIc = scale sign(Ic - target), loss = scale sum |Ic - target|."""
