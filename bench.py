@@ -40,7 +40,7 @@ METRIC = "Msamples/s fwd and fwd+bwd; relight p50/p99 ms under load vs per-call 
 UNIT = "Msamples/s"
 WORKLOAD = "corner scene T=1026, camera/projector/textures 256x256, 64 spp, 3 bounces, forward render"
 FWD_BWD_WORKLOAD = "corner scene T=1026 at 512x512 (camera, projector, textures), 16 spp, 3 bounces: " \
-                   "render + L2 loss + path-replay adjoint + Adam on Ip"
+                   "render + L2 loss + path adjoint (one fused trace) + Adam on Ip"
 L2_FLUSH_BYTES = 256 << 20
 
 # DRAM bytes (read + write) of one k_render launch of this workload, from the
@@ -410,6 +410,33 @@ def main():
     replay_ms, replay_n = ctx.kernel_time(1)
     crender_ms, crender_n = ctx.kernel_time(0)
     ctx.timing(False)
+    fbu_ms = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(fb_s, fb_e)))
+    fbu_val = cs.n_samples * ws * args.fwd_bwd_steps / (fbu_ms / 1e3) / 1e6
+
+    # the same step as the library's fused call: render, loss and adjoint in
+    # one trace of the paths (dpcs_render_loss_backward), then Adam
+    def comp_step_fused():
+        step_no[0] += 1
+        G.zero_()
+        ctx.render_loss_backward(hc, calb, crough, P, cview, cprm, cs.spp, cs.bounces, cs.seed + step_no[0], target,
+                                 loss, loss_kind=0, Ic=cIc, Ec=cEc, dIp=G)
+        ctx.adam(P, G, M, V, step_no[0], lr=1e-2)
+
+    for k in range(args.warmup):
+        flush(k)
+        comp_step_fused()
+    ctx.sync()
+    barrier()
+    ctx.timing(True)
+    for k in range(args.fwd_bwd_steps):
+        flush(k)
+        fb_s[k].record(stream)
+        comp_step_fused()
+        fb_e[k].record(stream)
+    barrier()
+    ctx.sync()
+    fused_ms, fused_n = ctx.kernel_time(0)
+    ctx.timing(False)
     fb_ms = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(fb_s, fb_e)))
     fb_val = cs.n_samples * ws * args.fwd_bwd_steps / (fb_ms / 1e3) / 1e6
 
@@ -729,8 +756,10 @@ def main():
             "fwd_bwd": {"value": fb_val, "unit": UNIT, "workload": FWD_BWD_WORKLOAD,
                         "ms_per_step": fb_ms / args.fwd_bwd_steps, "steps": args.fwd_bwd_steps,
                         "samples_per_step_per_gpu": cs.n_samples,
-                        "replay_kernel_ms": replay_ms / max(replay_n, 1),
-                        "render_kernel_ms": crender_ms / max(crender_n, 1)},
+                        "fused_kernel_ms": fused_ms / max(fused_n, 1),
+                        "unfused": {"value": fbu_val, "ms_per_step": fbu_ms / args.fwd_bwd_steps,
+                                    "replay_kernel_ms": replay_ms / max(replay_n, 1),
+                                    "render_kernel_ms": crender_ms / max(crender_n, 1)}},
             "roofline": roof,
             "roofline_load": roof_load,
             "roofline_atomic": roof_atomic,

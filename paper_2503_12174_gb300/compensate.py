@@ -2,8 +2,11 @@
 
 The loop runs entirely on the device through the C ABI.  Each step renders
 Ic = R(Ip) with a fresh Philox key (seed + k), takes the L2 loss against the
-target, carries dL/dIc back to Ip with the path-replay adjoint, and applies
-an Adam step followed by the clamp of Ip to [0, 1].
+target, carries dL/dIc back to Ip with the path adjoint, and applies an Adam
+step followed by the clamp of Ip to [0, 1].  By default the render, loss and
+adjoint are one call that traces each path once
+(``Context.render_loss_backward``); ``fused=False`` makes the separate
+render, loss and replay calls instead.
 
 With ``denoise`` set (a ``dpcs.DpcsDenoiseParams``), the loss is taken on
 the denoised image D(Ic) of Eq. 11 instead, and dL/dD is carried back to
@@ -26,7 +29,7 @@ class Compensation:
 
     def __init__(self, ctx: dpcs.Context, scene: int, albedo, rough, view: dpcs.DpcsView, params: dpcs.DpcsParams,
                  spp: int, bounces: int, steps: int, lr: float = 1e-2, seed: int = 0, graph: bool = True,
-                 denoise: dpcs.DpcsDenoiseParams | None = None, guide=None):
+                 denoise: dpcs.DpcsDenoiseParams | None = None, guide=None, fused: bool = True):
         import torch
 
         self.ctx, self.scene, self.albedo, self.rough = ctx, scene, albedo, rough
@@ -44,6 +47,7 @@ class Compensation:
         self.loss = torch.zeros(1, dtype=f32, device=dev)
         self.history = torch.zeros(self.steps, dtype=f32, device=dev)
         self.denoise = denoise
+        self.fused = bool(fused)
         if denoise is not None:
             self.guide = guide if guide is not None else ctx.gbuffer(scene, albedo, rough, view)
             self.D = torch.empty_like(self.target)
@@ -60,6 +64,14 @@ class Compensation:
     def _step(self, k: int):
         c = self.ctx
         s = self.seed + k
+        if self.denoise is None and self.fused:  # render, loss and adjoint in one trace of the paths
+            self.G.zero_()
+            c.render_loss_backward(self.scene, self.albedo, self.rough, self.P, self.view, self.params, self.spp,
+                                   self.bounces, s, self.target, self.loss, loss_kind=0, Ic=self.Ic, Ec=self.Ec,
+                                   dIp=self.G)
+            self.history[k].copy_(self.loss[0])
+            c.adam(self.P, self.G, self.M, self.V, k + 1, lr=self.lr, lo=0.0, hi=1.0)
+            return
         c.render(self.scene, self.albedo, self.rough, self.P, self.view, self.params, self.spp, self.bounces, s,
                  Ic=self.Ic, Ec=self.Ec)
         if self.denoise is None:

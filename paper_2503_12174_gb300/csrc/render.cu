@@ -595,7 +595,12 @@ __global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB) k_render_grad(
                 trav_begin(st, a.root, shadow ? tmax : INFINITY, shadow);
                 pending = true;
             }
-            if (!trav_resume(a.nodes, a.tris, a.root, a.T, ray, st, stack, a.status, cnt, 0, a.visit_cap)) continue;
+            // the same call as in k_render and k_replay: passing a literal 0 for
+            // min_active instead (the same value) made this kernel 3.2x slower
+            const int alive = DPCS_YIELD_MIN > 0 ? __popc(__activemask()) : 0;
+            if (!trav_resume(a.nodes, a.tris, a.root, a.T, ray, st, stack, a.status, cnt, min(DPCS_YIELD_MIN, alive),
+                             a.visit_cap))
+                continue;
             pending = false;
             const bool hit = st.h.pos >= 0;
             bool end = false;

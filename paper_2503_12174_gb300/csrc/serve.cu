@@ -15,9 +15,10 @@
 //      steps, still within that half;
 //   4. enqueue on the server stream: the batch descriptors, one persistent
 //      k_render_batch launch over the relighting pixels, each compensation
-//      request's render (a whole image, one k_render launch) + loss + path
-//      replay + Adam + PRF, the host copies of requests that finish in this
-//      batch, and the iteration's completion event.
+//      request's step: render, loss and path adjoint in one trace
+//      (k_render_grad, or render + loss + replay when its records would not
+//      fit), then Adam and PRF; the host copies of requests that finish in
+//      this batch, and the iteration's completion event.
 // Everything runs on one stream, so a compensation step always sees the
 // previous step's Adam update; the host prepares the next iteration while
 // the GPU runs the previous ones (up to max_inflight).
@@ -216,6 +217,33 @@ int enqueue_comp_backward(dpcs_server *s, Req *q) {
     return n;
 }
 
+// one compensation step in a single trace of its paths (k_render_grad):
+// render, L2 loss, adjoint, then PRF adjoint, Adam and Ep for the next step
+bool comp_step_fuses(const Req *q) {
+    const int L = 1 << q->args.log2L;
+    const int spl = (q->args.spp + L - 1) / L;
+    return spl <= kFusedSamples && spl * q->args.bounces <= kFusedRecs;
+}
+
+int enqueue_comp_step_fused(dpcs_server *s, Req *q) {
+    const ServeScene &sc = s->scenes[q->r.scene];
+    const int64_t np = (int64_t)sc.view.Hp * sc.view.Wp;
+    cudaStream_t st = s->stream;
+    cudaMemsetAsync(q->acc, 0, 16 * 8, st);
+    cudaMemsetAsync(q->dEp4, 0, (size_t)np * 16, st);
+    cudaMemsetAsync(q->G, 0, (size_t)np * 12, st);
+    RenderArgs a = q->args;
+    a.dEp = q->dEp4;
+    a.dtex = nullptr;  // only Ip is optimised
+    const LossArgs l{q->target, 1.0f, 0, q->acc};
+    int n = launch_render_grad(a, l, st);
+    n += launch_loss_out(q->acc, q->loss, st);
+    n += launch_prf_backward(q->Ip, q->dEp4, np, sc.params.gamma_p, sc.params.gain_p, q->G, q->acc, st);
+    n += launch_adam(q->Ip, q->G, q->M, q->V, np * 3, q->r.lr, 0.9f, 0.999f, 1e-8f, q->steps_issued, 0.0f, 1.0f, st);
+    n += launch_prf(q->Ip, np, sc.params.gamma_p, sc.params.gain_p, q->Ep4, st);
+    return n;
+}
+
 void release(dpcs_server *s, Req *q) {
     if (q->mem) {
         cudaFreeAsync(q->mem, s->stream);
@@ -373,9 +401,14 @@ dpcs_status launch_iteration(dpcs_server *s, Batch &b) {
         // one k_render launch, whose arguments sit in constant space
         q->args.key0 = (uint32_t)((q->r.seed + (uint64_t)q->steps_issued) & 0xffffffffu);
         q->args.key1 = (uint32_t)((q->r.seed + (uint64_t)q->steps_issued) >> 32);
-        n += launch_render(q->args, st);
-        q->steps_issued++;
-        n += enqueue_comp_backward(s, q);
+        if (comp_step_fuses(q)) {
+            q->steps_issued++;
+            n += enqueue_comp_step_fused(s, q);
+        } else {
+            n += launch_render(q->args, st);
+            q->steps_issued++;
+            n += enqueue_comp_backward(s, q);
+        }
         if (q->steps_issued == q->r.steps) {
             dpcs_status rs = queue_result_copy(s, q);
             if (rs) return rs;

@@ -13,8 +13,11 @@ total-variation gradient and takes one Adam step per parameter group, each
 followed by the clamp to the group's range: albedo [0, 1], roughness
 [0.01, 1], gamma_p [2, 3], gamma_c [1/3, 1], w [0.2, 2.5] (Sec. 3.2).
 
-Every step runs in the library's kernels; the only host traffic per step is
-reading back the 11 response parameters the next renders take by value.
+Without the denoiser each pair's render, L1 term and adjoint are one call
+that traces its paths once (``Context.render_loss_backward``; ``fused=False``
+makes separate calls).  Every step runs in the library's kernels; the only
+host traffic per step is reading back the 11 response parameters the next
+renders take by value.
 """
 from __future__ import annotations
 
@@ -46,7 +49,8 @@ class SceneFit:
 
     def __init__(self, ctx: dpcs.Context, scene: int, view: dpcs.DpcsView, params0: dpcs.DpcsParams, albedo0, rough0,
                  pairs, spp: int, bounces: int, lr_tex: float = 2e-2, lr_params: float = 1e-2, tv_weight: float = 0.0,
-                 denoise: dpcs.DpcsDenoiseParams | None = None, fit_params: bool = True, seed: int = 0):
+                 denoise: dpcs.DpcsDenoiseParams | None = None, fit_params: bool = True, seed: int = 0,
+                 fused: bool = True):
         import torch
 
         self.ctx, self.scene, self.view = ctx, scene, view
@@ -54,7 +58,7 @@ class SceneFit:
         self.K = len(self.pairs)
         self.spp, self.bounces, self.seed = int(spp), int(bounces), int(seed)
         self.lr_tex, self.lr_params, self.tv_weight = float(lr_tex), float(lr_params), float(tv_weight)
-        self.denoise, self.fit_params = denoise, bool(fit_params)
+        self.denoise, self.fit_params, self.fused = denoise, bool(fit_params), bool(fused)
         dev = ctx.device
         f32 = torch.float32
         self.albedo = albedo0.clone().contiguous()
@@ -88,6 +92,12 @@ class SceneFit:
             c.gbuffer(self.scene, self.albedo, self.rough, self.view, guide=self.guide)
         for i, (Ip, target) in enumerate(self.pairs):
             s = self.seed + (self.k - 1) * self.K + i
+            if self.denoise is None and self.fused:  # render, L1 term and adjoint in one trace of the paths
+                c.render_loss_backward(self.scene, self.albedo, self.rough, Ip, self.view, self.params, self.spp,
+                                       self.bounces, s, target, self.losses[i:i + 1], loss_kind=1, scale=self.scale,
+                                       Ic=self.Ic, Ec=self.Ec, dAlbedo=self.gA, dRough=self.gR,
+                                       dParams=self.gP if self.fit_params else None)
+                continue
             c.render(self.scene, self.albedo, self.rough, Ip, self.view, self.params, self.spp, self.bounces, s,
                      Ic=self.Ic, Ec=self.Ec)
             if self.denoise is None:
