@@ -210,8 +210,9 @@ def run_server(ctx, gs: GpuScenes, host: HostData, workload, keep_outputs=False,
 def compensate_alone(ctx, gs: GpuScenes, scene: int, side: int, spp: int, seed: int, Ip_host, target_host, steps: int,
                      lr: float = 1e-2):
     """The compensation loop of one request through the plain per-call API:
-    step k renders with seed + k, takes the L2 loss, runs the path-replay
-    adjoint and an Adam step on Ip clamped to [0, 1]."""
+    step k renders with seed + k, takes the L2 loss and the path adjoint in
+    one call (render_loss_backward), then an Adam step on Ip clamped to
+    [0, 1]."""
     import torch
 
     sc = gs.scs[scene]
@@ -222,16 +223,12 @@ def compensate_alone(ctx, gs: GpuScenes, scene: int, side: int, spp: int, seed: 
     M, V, G = torch.zeros_like(P), torch.zeros_like(P), torch.zeros_like(P)
     Ic = torch.empty((side, side, 3), device=dev)
     Ec = torch.empty_like(Ic)
-    dIc = torch.empty_like(Ic)
     loss = torch.empty(1, device=dev)
     for k in range(steps):
         s = seed + k
-        ctx.render(gs.handles[scene], gs.alb[scene], gs.rough[scene], P, view, gs.params[scene], spp, sc.bounces, s,
-                   Ic=Ic, Ec=Ec)
-        ctx.l2_loss(Ic, tgt, dIc, loss)
         G.zero_()
-        ctx.render_backward(gs.handles[scene], gs.alb[scene], gs.rough[scene], P, view, gs.params[scene], spp,
-                            sc.bounces, s, Ec, Ic, dIc, dIp=G)
+        ctx.render_loss_backward(gs.handles[scene], gs.alb[scene], gs.rough[scene], P, view, gs.params[scene], spp,
+                                 sc.bounces, s, tgt, loss, loss_kind=0, Ic=Ic, Ec=Ec, dIp=G)
         ctx.adam(P, G, M, V, k + 1, lr=lr)
     return Ic, P
 
