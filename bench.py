@@ -638,15 +638,20 @@ def main():
         hview, hprm = dpcs.view_of(hs), dpcs.make_params(hs.params)
         hIc = torch.empty((hs.Hc, hs.Wc, 3), device=dev)
         hEc = torch.empty_like(hIc)
-        hdIc = torch.randn_like(hIc)
         hG = torch.zeros_like(hIp)
 
         def hf_fwd(spp):
             ctx.render(hh, halb, hrough, hIp, hview, hprm, spp, hs.bounces, hs.seed, Ic=hIc, Ec=hEc)
 
+        # a compensation step against a target image: render, L2 loss and the
+        # adjoint to Ip in one trace of the paths (4 bounces, 1 sample per lane)
+        htarget = (torch.rand_like(hIc) * 0.5).contiguous()
+        hloss = torch.zeros(1, device=dev)
+
         def hf_fb(spp):
-            hf_fwd(spp)
-            ctx.render_backward(hh, halb, hrough, hIp, hview, hprm, spp, hs.bounces, hs.seed, hEc, hIc, hdIc, dIp=hG)
+            hG.zero_()
+            ctx.render_loss_backward(hh, halb, hrough, hIp, hview, hprm, spp, hs.bounces, hs.seed, htarget, hloss,
+                                     loss_kind=0, Ic=hIc, Ec=hEc, dIp=hG)
 
         res = {}
         for name, fn, spp in (("fwd", hf_fwd, 256), ("fwd_bwd", hf_fb, 32)):
@@ -695,7 +700,8 @@ def main():
         ctx.sync()
         ctx.free(hh)
         hf_out = {"workload": f"heightfield T={hs.T}, camera {hs.Hc}x{hs.Wc}, projector {hs.Wp}x{hs.Hp}, "
-                              f"textures 512x512, {hs.bounces} bounces, Russian roulette from vertex 2 (q=0.75)",
+                              f"textures 512x512, {hs.bounces} bounces, Russian roulette from vertex 2 (q=0.75); "
+                              "fwd_bwd = render + L2 loss + adjoint to Ip in one fused call",
                   **res}
 
     # ------------------------------------------------------------ serving vs one call per request
