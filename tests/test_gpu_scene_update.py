@@ -133,3 +133,45 @@ def test_update_refuses_bad_input():
         c.sync()
     finally:
         c.free(h)
+
+
+def test_compensation_on_a_deforming_surface(orc):
+    """Compensation while the surface moves (Sec. 4.4 with Eq. 13): before
+    each step the vertices take the frame's positions; each step's loss and
+    Adam update follow the oracle run on that frame's mesh."""
+    torch = need_cuda()
+    sc = scenes.corner(res=20, tex=16, spp=4, bounces=2, seed=11)
+    rng = np.random.default_rng(0)
+    _, target = orc.render(sc, Ip=rng.random(sc.Ip.shape), seed=777)
+    frames = [_deform(sc.verts, amp=0.01 * f) for f in range(3)]
+    lr = 0.05
+    g = GpuScene(sc)
+    try:
+        P = torch.full_like(g.Ip, 0.5)
+        M, V, G = torch.zeros_like(P), torch.zeros_like(P), torch.zeros_like(P)
+        tgt = torch.from_numpy(target.astype(np.float32)).cuda()
+        loss = torch.zeros(1, device="cuda")
+        losses = []
+        for k, fv in enumerate(frames):
+            g.ctx.update(g.handle, fv)
+            G.zero_()
+            g.ctx.render_loss_backward(g.handle, g.albedo, g.rough, P, g.view, g.params, sc.spp, sc.bounces,
+                                       sc.seed + k, tgt, loss, loss_kind=0, dIp=G)
+            losses.append(loss.item())
+            g.ctx.adam(P, G, M, V, k + 1, lr=lr)
+        g.ctx.sync()
+        P = P.cpu().numpy().astype(np.float64)
+    finally:
+        g.close()
+    Pr = np.full(sc.Ip.shape, 0.5)
+    m, v = np.zeros_like(Pr), np.zeros_like(Pr)
+    ref = []
+    for k, fv in enumerate(frames):
+        fsc = sc.replace(verts=fv)
+        _, Ic = orc.render(fsc, Ip=Pr, seed=sc.seed + k)
+        d = Ic - target
+        ref.append(0.5 * np.sum(d * d))
+        grad = orc.render_backward(fsc, d, Ip=Pr, seed=sc.seed + k)["dIp"]
+        orc.adam_step(Pr, grad, m, v, k + 1, lr=lr)
+    np.testing.assert_allclose(losses, ref, rtol=1e-3)
+    np.testing.assert_allclose(P, Pr, rtol=0, atol=2e-3)
