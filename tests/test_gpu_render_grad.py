@@ -68,6 +68,27 @@ def test_fused_equals_separate_calls(spp, bounces, kind, scale):
         g.close()
 
 
+def test_fused_full_size_equals_separate_calls():
+    """The benchmark's launch configuration (512 x 512, 16 spp, 3 bounces,
+    the compensation step): the fused call against the separate calls."""
+    torch = need_cuda()
+    sc = scenes.compensation(512, 16)
+    g = GpuScene(sc)
+    rng = np.random.default_rng(3)
+    try:
+        target = torch.from_numpy(rng.uniform(0.0, 1.0, (sc.Hc, sc.Wc, 3)).astype(np.float32)).cuda()
+        Ia, Ea, la, ga = _separate(g, sc, target, 0, 1.0, sc.spp, sc.bounces)
+        Ib, Eb, lb, gb = _fused(g, sc, target, 0, 1.0, sc.spp, sc.bounces)
+        g.ctx.sync()
+        assert torch.equal(Ia, Ib) and torch.equal(Ea, Eb)
+        np.testing.assert_allclose(lb.item(), la.item(), rtol=1e-5)
+        for k in ("dIp", "dparams"):
+            a, b = ga[k].cpu().numpy(), gb[k].cpu().numpy()
+            np.testing.assert_allclose(b, a, rtol=1e-4, atol=1e-6 * np.abs(a).max(), err_msg=k)
+    finally:
+        g.close()
+
+
 def test_fused_gradient_matches_oracle(orc):
     torch = need_cuda()
     sc = scenes.corner(res=24, tex=16, spp=8, bounces=2, seed=7)
