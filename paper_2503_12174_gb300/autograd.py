@@ -1,0 +1,75 @@
+"""The renderer as a torch.autograd.Function: Ic = R(Ip, theta) (Eq. 7) with
+its path-replay adjoint as the backward, so that projector compensation
+(Eq. 13) and scene fitting (Eq. 9) can be written with torch optimisers.
+
+    Ic = render(ctx, scene, albedo, rough, Ip, view, params, spp, bounces, seed, pvec=None)
+
+``albedo`` (Ht x Wt x 3), ``rough`` (Ht x Wt) and ``Ip`` (Hp x Wp x 3) are
+device tensors; ``pvec`` (11 floats: gamma_p(3), Gp, gamma_c(3), Gc, w(3)),
+when given, replaces the response parameters of ``params`` and receives their
+gradient.  The backward asks the library only for the gradients autograd
+needs: without albedo or roughness gradients the replay skips the texture
+scatters.  Both passes run in the library's kernels; each call renders with
+Philox key ``seed``, and the backward re-traces the same paths.
+"""
+from __future__ import annotations
+
+from . import dpcs
+
+
+def params_vector(p: dpcs.DpcsParams):
+    """[gamma_p(3), Gp, gamma_c(3), Gc, wb(3)] -- the layout of dParams."""
+    return list(p.gamma_p) + [p.gain_p] + list(p.gamma_c) + [p.gain_c] + list(p.wb)
+
+
+def with_vector(p: dpcs.DpcsParams, v) -> dpcs.DpcsParams:
+    """A copy of p with its response parameters taken from v (params_vector layout)."""
+    q = dpcs.DpcsParams.from_buffer_copy(bytes(p))
+    q.gamma_p[:] = [float(x) for x in v[0:3]]
+    q.gain_p = float(v[3])
+    q.gamma_c[:] = [float(x) for x in v[4:7]]
+    q.gain_c = float(v[7])
+    q.wb[:] = [float(x) for x in v[8:11]]
+    return q
+
+
+def _function():
+    import torch
+
+    class DPCSRender(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, albedo, rough, Ip, pvec, ctx, scene, view, params, spp, bounces, seed):
+            p = params if pvec is None else with_vector(params, pvec.detach().cpu().tolist())
+            Ec = torch.empty((view.Hc, view.Wc, 3), dtype=torch.float32, device=ctx.device)
+            Ic, _ = ctx.render(scene, albedo, rough, Ip, view, p, spp, bounces, seed, Ec=Ec)
+            fctx.save_for_backward(albedo, rough, Ip, Ec, Ic)
+            fctx.meta = (ctx, scene, view, p, spp, bounces, seed, pvec is not None)
+            return Ic
+
+        @staticmethod
+        def backward(fctx, dIc):
+            albedo, rough, Ip, Ec, Ic = fctx.saved_tensors
+            ctx, scene, view, p, spp, bounces, seed, has_pvec = fctx.meta
+            need = fctx.needs_input_grad
+            dA = torch.zeros_like(albedo) if need[0] else None
+            dR = torch.zeros_like(rough) if need[1] else None
+            dIp = torch.zeros_like(Ip) if need[2] else None
+            dP = torch.zeros(11, dtype=torch.float32, device=ctx.device) if has_pvec and need[3] else None
+            if any(x is not None for x in (dA, dR, dIp, dP)):
+                ctx.render_backward(scene, albedo, rough, Ip, view, p, spp, bounces, seed, Ec, Ic,
+                                    dIc.to(torch.float32).contiguous(), dIp=dIp, dAlbedo=dA, dRough=dR, dParams=dP)
+            return dA, dR, dIp, dP, None, None, None, None, None, None, None
+
+    return DPCSRender
+
+
+_DPCSRender = None
+
+
+def render(ctx: dpcs.Context, scene: int, albedo, rough, Ip, view: dpcs.DpcsView, params: dpcs.DpcsParams,
+           spp: int, bounces: int, seed: int, pvec=None):
+    """Differentiable Ic = R(Ip, theta); see the module docstring."""
+    global _DPCSRender
+    if _DPCSRender is None:
+        _DPCSRender = _function()
+    return _DPCSRender.apply(albedo, rough, Ip, pvec, ctx, scene, view, params, int(spp), int(bounces), int(seed))

@@ -22,25 +22,11 @@ renders take by value.
 from __future__ import annotations
 
 from . import dpcs
+from .autograd import params_vector, with_vector  # noqa: F401  (re-exported for callers of the fit)
 
 PARAM_RANGES = {"gamma_p": (slice(0, 3), 2.0, 3.0), "gamma_c": (slice(4, 7), 1.0 / 3.0, 1.0),
                 "wb": (slice(8, 11), 0.2, 2.5)}
 ROUGH_MIN = 0.01
-
-
-def params_vector(p: dpcs.DpcsParams):
-    """[gamma_p(3), Gp, gamma_c(3), Gc, wb(3)] -- the layout of dParams."""
-    return list(p.gamma_p) + [p.gain_p] + list(p.gamma_c) + [p.gain_c] + list(p.wb)
-
-
-def with_vector(p: dpcs.DpcsParams, v) -> dpcs.DpcsParams:
-    q = dpcs.DpcsParams.from_buffer_copy(bytes(p))
-    q.gamma_p[:] = [float(x) for x in v[0:3]]
-    q.gain_p = float(v[3])
-    q.gamma_c[:] = [float(x) for x in v[4:7]]
-    q.gain_c = float(v[7])
-    q.wb[:] = [float(x) for x in v[8:11]]
-    return q
 
 
 class SceneFit:
