@@ -94,6 +94,48 @@ class Compensation:
         for k in range(self.steps):
             self._step(k)
 
+    # -- step by step, with checkpoints -----------------------------------------
+    def start(self, Ip_init, target):
+        """Eager use: set the start image and target, clear the Adam state."""
+        self.P0.copy_(Ip_init)
+        self.target.copy_(target)
+        self.P.copy_(self.P0)
+        self.M.zero_()
+        self.V.zero_()
+        self.done = 0
+
+    def advance(self, n: int):
+        """Run the next n steps eagerly (steps done + 1 .. done + n)."""
+        first = getattr(self, "done", 0)
+        if first + n > self.steps:
+            raise ValueError(f"{first} + {n} steps exceed the {self.steps} this object was built for")
+        for k in range(first, first + n):
+            self._step(k)
+        self.done = first + n
+        return self.P, self.history[:self.done]
+
+    def save(self, path: str):
+        """Checkpoint: Ip, the Adam moments, the target, the steps done, the seed and lr (.npz)."""
+        import numpy as np
+
+        np.savez(path, P=self.P.cpu().numpy(), M=self.M.cpu().numpy(), V=self.V.cpu().numpy(),
+                 target=self.target.cpu().numpy(), history=self.history.cpu().numpy(),
+                 done=getattr(self, "done", 0), seed=self.seed, lr=self.lr)
+
+    def resume(self, path: str):
+        """Restore a checkpoint written by save(); advance() then continues
+        with the next step's Philox key and Adam step number."""
+        import numpy as np
+        import torch
+
+        z = np.load(path)
+        if int(z["seed"]) != self.seed or float(z["lr"]) != self.lr:
+            raise ValueError("checkpoint seed or learning rate differs from this compensation")
+        for name in ("P", "M", "V", "target"):
+            getattr(self, name).copy_(torch.from_numpy(z[name]))
+        self.history.copy_(torch.from_numpy(z["history"]))
+        self.done = int(z["done"])
+
     def run(self, Ip_init, target):
         """Compensate towards `target` (Hc x Wc x 3) from `Ip_init` (Hp x Wp x
         3); returns (Ip*, per-step losses) as device tensors."""

@@ -13,6 +13,8 @@
 #include <vector>
 
 #include "dpcs.h"
+#include <nvtx3/nvToolsExt.h>
+
 #include "internal.h"
 
 using namespace dpcs;
@@ -57,6 +59,13 @@ struct dpcs_ctx {
 };
 
 namespace {
+
+// NVTX range around an entry point: visible in Nsight tools, free when no
+// tool is attached
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
 
 dpcs_status fail(dpcs_ctx *c, dpcs_status code, const std::string &msg) {
     if (c) c->err = msg;
@@ -364,6 +373,7 @@ dpcs_status dpcs_sync(dpcs_ctx *c, void *stream) {
 
 dpcs_status dpcs_scene_upload(dpcs_ctx *c, const float *verts, int32_t V, const int32_t *tris, int32_t T,
                               const float *uv, void *stream, dpcs_scene *out) {
+    Range range("dpcs_scene_upload");
     if (!c || !out) return DPCS_ERR_INVALID_ARG;
     if (T < 0 || V < 0 || (T > 0 && (!verts || !tris || !uv || V == 0)))
         return fail(c, DPCS_ERR_INVALID_ARG, "bad mesh arrays");
@@ -447,6 +457,7 @@ dpcs_status dpcs_scene_free(dpcs_ctx *c, dpcs_scene scene) {
 }
 
 dpcs_status dpcs_scene_update(dpcs_ctx *c, dpcs_scene scene, const float *verts, int32_t V, void *stream) {
+    Range range("dpcs_scene_update");
     if (!c) return DPCS_ERR_INVALID_ARG;
     auto it = c->scenes.find(scene);
     if (it == c->scenes.end()) return fail(c, DPCS_ERR_NOT_FOUND, "unknown scene handle");
@@ -505,6 +516,7 @@ dpcs_status dpcs_scene_export(dpcs_ctx *c, dpcs_scene scene, uint32_t *codes, in
 
 dpcs_status dpcs_trace(dpcs_ctx *c, dpcs_scene scene, const float *orig, const float *dir, int64_t n, float *t_out,
                        int32_t *tri_out, void *stream) {
+    Range range("dpcs_trace");
     if (!c) return DPCS_ERR_INVALID_ARG;
     auto it = c->scenes.find(scene);
     if (it == c->scenes.end()) return fail(c, DPCS_ERR_NOT_FOUND, "unknown scene handle");
@@ -520,6 +532,7 @@ dpcs_status dpcs_trace(dpcs_ctx *c, dpcs_scene scene, const float *orig, const f
 dpcs_status dpcs_render(dpcs_ctx *c, dpcs_scene scene, const float *albedo, const float *rough, int32_t Ht,
                         int32_t Wt, const float *Ip, const dpcs_view *view, const dpcs_params *params, int32_t spp,
                         int32_t bounces, uint64_t seed, float *Ic, float *Ec, void *stream) {
+    Range range("dpcs_render");
     RenderArgs a;
     Scene *sc = nullptr;
     dpcs_status s = prepare(c, scene, albedo, rough, Ht, Wt, Ip, view, params, spp, bounces, seed, a, &sc);
@@ -547,6 +560,7 @@ dpcs_status dpcs_render_backward(dpcs_ctx *c, dpcs_scene scene, const float *alb
                                  const dpcs_params *params, int32_t spp, int32_t bounces, uint64_t seed,
                                  const float *Ec, const float *Ic, const float *dIc, float *dIp, float *dAlbedo,
                                  float *dRough, float *dParams, void *stream) {
+    Range range("dpcs_render_backward");
     RenderArgs a;
     Scene *sc = nullptr;
     dpcs_status s = prepare(c, scene, albedo, rough, Ht, Wt, Ip, view, params, spp, bounces, seed, a, &sc);
@@ -590,6 +604,7 @@ dpcs_status dpcs_render_loss_backward(dpcs_ctx *c, dpcs_scene scene, const float
                                       const float *target, int32_t loss_kind, float scale, float *Ic, float *Ec,
                                       float *loss, float *dIp, float *dAlbedo, float *dRough, float *dParams,
                                       void *stream) {
+    Range range("dpcs_render_loss_backward");
     RenderArgs a;
     Scene *sc = nullptr;
     dpcs_status s = prepare(c, scene, albedo, rough, Ht, Wt, Ip, view, params, spp, bounces, seed, a, &sc);

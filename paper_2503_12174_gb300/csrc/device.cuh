@@ -406,6 +406,15 @@ __device__ __forceinline__ bool trav_resume(const float4 *__restrict__ nodes, co
             return true;
         }
         const int node = st.node;
+#ifdef DPCS_CHECK
+        // debug build: every node and leaf reference is checked against the
+        // tree before it is read; a bad one ends the ray and is reported
+        if (node >= T - 1 || (node < 0 && ~node >= T)) {
+            atomicOr(status, kStatusBoundsCheck);
+            st.h.pos = -1;
+            return true;
+        }
+#endif
         if (node >= 0) {
             cnt.add(kCntNode);
             const float4 n0 = __ldg(nodes + 4 * node + 0);

@@ -187,6 +187,13 @@ def load_library(path: str | None = None):
     return _lib
 
 
+def check_library():
+    """The DPCS_CHECK debug build: every node and leaf reference is checked
+    before it is read; a bad one ends the ray and dpcs_sync reports
+    DPCS_ERR_DEVICE_CHECK."""
+    return open_library(_build.build(variant="_check", defines=("DPCS_CHECK",)))
+
+
 def counters_library():
     """The DPCS_COUNTERS build (counts node visits, triangle tests, ...)."""
     return open_library(_build.build(variant="_counters", defines=("DPCS_COUNTERS",)))

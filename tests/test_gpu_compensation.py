@@ -103,3 +103,33 @@ def test_denoised_compensation_follows_oracle(orc):
     np.testing.assert_allclose(P, Pr, rtol=0, atol=2e-3)
     np.testing.assert_allclose(hg, hist, rtol=1e-4)
     np.testing.assert_allclose(Pg, P, rtol=0, atol=1e-4)
+
+
+def test_checkpoint_and_resume(orc, tmp_path):
+    """Three steps, a checkpoint, a fresh object that resumes and runs three
+    more: the same trajectory as six steps in one go (up to the rounding of
+    the adjoint's float atomics)."""
+    torch, sc, target = _setup(orc, res=20, steps=6)
+    g = GpuScene(sc)
+    try:
+        args = (g.ctx, g.handle, g.albedo, g.rough, g.view, g.params, sc.spp, sc.bounces, 6)
+        init, tgt = torch.full_like(g.Ip, 0.5), torch.from_numpy(target).cuda()
+        whole = compensate.Compensation(*args, lr=0.05, seed=7, graph=False)
+        whole.start(init, tgt)
+        Pw, hw = whole.advance(6)
+        Pw, hw = Pw.clone(), hw.clone()
+        first = compensate.Compensation(*args, lr=0.05, seed=7, graph=False)
+        first.start(init, tgt)
+        first.advance(3)
+        path = str(tmp_path / "comp.npz")
+        first.save(path)
+        second = compensate.Compensation(*args, lr=0.05, seed=7, graph=False)
+        second.resume(path)
+        Pr, hr = second.advance(3)
+        g.ctx.sync()
+        np.testing.assert_allclose(hr.cpu().numpy(), hw.cpu().numpy(), rtol=1e-4)
+        np.testing.assert_allclose(Pr.cpu().numpy(), Pw.cpu().numpy(), rtol=0, atol=1e-4)
+        with pytest.raises(ValueError):
+            compensate.Compensation(*args, lr=0.05, seed=8, graph=False).resume(path)
+    finally:
+        g.close()

@@ -71,3 +71,30 @@ def test_hbm_budget_refuses_scratch():
         small.upload(sc.verts, sc.tris, sc.uv)
     assert e.value.status == dpcs.DPCS_ERR_OOM
     small.close()
+
+
+def test_bounds_checked_build_renders_the_same_image():
+    """The DPCS_CHECK debug build checks every tree reference before reading
+    it; on a correct tree it reports nothing and renders the image of the
+    normal build bit for bit."""
+    torch = need_cuda()
+    from gpu_util import GpuScene
+
+    sc = scenes.corner(res=32, tex=16, spp=8, bounces=3)
+    g = GpuScene(sc)
+    try:
+        _, Ic = g.render()
+        ref = Ic.cpu().numpy()
+    finally:
+        g.close()
+    c = dpcs.Context(0, lib=dpcs.check_library())
+    try:
+        h = c.upload(sc.verts, sc.tris, sc.uv)
+        dev = c.device
+        alb, rough, Ip = (torch.from_numpy(np.ascontiguousarray(x)).to(dev) for x in (sc.albedo, sc.rough, sc.Ip))
+        Ic2, _ = c.render(h, alb, rough, Ip, dpcs.view_of(sc), dpcs.make_params(sc.params), sc.spp, sc.bounces, sc.seed)
+        c.sync()  # raises if a check fired
+        np.testing.assert_array_equal(Ic2.cpu().numpy(), ref)
+        c.free(h)
+    finally:
+        c.close()
