@@ -336,6 +336,32 @@ dpcs_status dpcs_denoise_backward(dpcs_ctx *ctx, const float *dOut, const float 
                                   void *stream);
 
 /*
+ * dpcs_render that also keeps every path's vertex records on the device, so
+ * that the adjoint of a loss that is not per-pixel (e.g. after the Eq. 11
+ * filter) can run without tracing the paths again.  Arguments and results
+ * are those of dpcs_render (Ic and Ec equal bit for bit).  The records
+ * (96 B per recorded vertex: ceil(spp / L) samples x `bounces` vertices per
+ * lane, L lanes per pixel, L = min(32, the largest power of two <= spp))
+ * live in context scratch, counted against the HBM budget, until the next
+ * dpcs_render_keep; DPCS_ERR_OOM if they do not fit.
+ *
+ * dpcs_render_backward_kept: the adjoint of the last dpcs_render_keep call,
+ * with the arguments and outputs of dpcs_render_backward.  The call must
+ * repeat that render's arguments (scene, textures, Ip, view, params, spp,
+ * bounces, seed); the scene, image size, spp, bounces and seed are checked
+ * (DPCS_ERR_INVALID_ARG when they differ).  It runs the reverse sweeps over
+ * the kept records instead of re-tracing.
+ */
+dpcs_status dpcs_render_keep(dpcs_ctx *ctx, dpcs_scene scene, const float *albedo, const float *rough, int32_t Ht,
+                             int32_t Wt, const float *Ip, const dpcs_view *view, const dpcs_params *params,
+                             int32_t spp, int32_t bounces, uint64_t seed, float *Ic, float *Ec, void *stream);
+dpcs_status dpcs_render_backward_kept(dpcs_ctx *ctx, dpcs_scene scene, const float *albedo, const float *rough,
+                                      int32_t Ht, int32_t Wt, const float *Ip, const dpcs_view *view,
+                                      const dpcs_params *params, int32_t spp, int32_t bounces, uint64_t seed,
+                                      const float *Ec, const float *Ic, const float *dIc, float *dIp, float *dAlbedo,
+                                      float *dRough, float *dParams, void *stream);
+
+/*
  * Forward render, per-pixel loss and adjoint in one call, for the losses of
  * Eqs. 13 and 9 that compare each pixel with a target on its own:
  *   loss_kind 0 (L2): *loss = 1/2 scale sum |Ic - target|^2, dLoss/dIc = scale (Ic - target)

@@ -491,6 +491,9 @@ struct VRec {
     unsigned unc;  // bit j: channel j not clipped
 };
 
+constexpr int kRecWords = (int)(sizeof(VRec) / 4);  // VRec as 32-bit words (records kept in device memory)
+static_assert(kRecWords == kRecWordsHost, "the host sizes kept records with kRecWordsHost");
+
 // first camera ray of sample s of pixel pix (Eq. 6 with the Eq. 4 box filter)
 __device__ __forceinline__ void camera_ray(const RenderArgs &a, uint32_t pix, uint32_t s, f3 &o, f3 &d) {
     float u[4];

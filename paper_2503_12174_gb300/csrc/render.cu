@@ -716,6 +716,197 @@ __global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB) k_render_grad(
         replay_sweep(a, rec + i * a.bounces, nvs[i], gb_in, &s_row[threadIdx.x & ~31]);
 }
 
+// Forward render that keeps every path's vertex records in device memory
+// (dpcs_render_keep): the loop is k_render_grad's, with the records of each
+// sample copied out when its path ends and Ec / Ic written as k_render
+// writes them, so a later k_sweep_kept can run the adjoint of any loss,
+// including one that couples pixels (the Eq. 11 filter), without tracing
+// the paths again.
+__global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB)
+    k_render_keep(const RenderArgs a, uint32_t *__restrict__ words, uint8_t *__restrict__ nvs) {
+    const int L = 1 << a.log2L;
+    const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t pix = gt >> a.log2L;
+    const int sl = (int)(gt & (L - 1));
+    const bool valid = pix < (int64_t)a.Hc * a.Wc;
+    Cnt cnt;
+    const int64_t nthr = ((int64_t)a.Hc * a.Wc) << a.log2L;
+    int s = valid ? sl : a.spp;
+    int b = 1, nv = 0, k = 0;
+    bool shadow = false, has_ext = false, pending = false;
+    f3 sum = mk3(0.f, 0.f, 0.f);
+    f3 beta = sum, c = sum, ed = sum;
+    Ray ray;
+    ray.o = ray.d = ray.inv = beta;
+    float tmax = INFINITY;
+    Trav st;
+    int stack[kStack];
+    VRec rec[DPCS_MAX_BOUNCES];
+    if (s < a.spp && a.bounces > 0) {
+        f3 o, d;
+        camera_ray(a, (uint32_t)pix, (uint32_t)s, o, d);
+        ray = make_ray(o, d);
+        beta = mk3(1.f, 1.f, 1.f);
+        cnt.add(kCntPath);
+    } else {
+        s = a.spp;
+    }
+    const int64_t max_iter = ((int64_t)(a.spp / L + 1) * (2 * a.bounces + 1)) * (2 * (int64_t)a.T + 18);
+    int64_t iter = 0;
+    while (s < a.spp) {
+        VRec *rs = rec;  // this sample's records, copied out when its path ends
+        while (true) {  // the lane's current path; the warp starts its next samples together
+            if (++iter > max_iter) {
+                atomicOr(a.status, kStatusTraversalLimit);
+                s = a.spp;
+                nv = 0;
+                break;
+            }
+            if (!pending) {
+                cnt.add(shadow ? kCntShadow : kCntRay);
+                trav_begin(st, a.root, shadow ? tmax : INFINITY, shadow);
+                pending = true;
+            }
+            // the same call as in k_render and k_replay: passing a literal 0 for
+            // min_active instead (the same value) made this kernel 3.2x slower
+            const int alive = DPCS_YIELD_MIN > 0 ? __popc(__activemask()) : 0;
+            if (!trav_resume(a.nodes, a.tris, a.root, a.T, ray, st, stack, a.status, cnt, min(DPCS_YIELD_MIN, alive),
+                             a.visit_cap))
+                continue;
+            pending = false;
+            const bool hit = st.h.pos >= 0;
+            bool end = false;
+            if (shadow) {
+                if (hit) {
+                    rs[nv - 1].G = 0.0f;  // occluded: no projector light at this vertex
+                } else {
+                    sum = sum + c;
+                    cnt.add(kCntLit);
+                }
+                shadow = false;
+                if (has_ext) {
+                    ray = make_ray(ray.o, ed);
+                    ++b;
+                } else {
+                    end = true;
+                }
+            } else if (!hit) {
+                end = true;
+            } else {
+                cnt.add(kCntVert);
+                const Surf S = surface_at(a, st.h, ray.d);
+                VRec *R = &rs[nv++];
+                R->tx0 = S.tb.x0; R->ty0 = S.tb.y0; R->tfx = S.tb.fx; R->tfy = S.tb.fy;
+                R->beta[0] = beta.x; R->beta[1] = beta.y; R->beta[2] = beta.z;
+                R->rho[0] = S.rho.x; R->rho[1] = S.rho.y; R->rho[2] = S.rho.z;
+                R->G = 0.0f; R->cw = 0.0f; R->unc = 0u; R->sp = R->dsp = R->si = R->dsi = 0.0f;
+                Nee N;
+                const bool cand = nee_prepare(a, S, N);
+                if (cand) {
+                    unsigned unc;
+                    c = nee_contrib(a, beta, N, unc);
+                    R->px0 = N.pb.x0; R->py0 = N.pb.y0; R->pfx = N.pb.fx; R->pfy = N.pb.fy;
+                    R->Ep[0] = N.ep.x; R->Ep[1] = N.ep.y; R->Ep[2] = N.ep.z;
+                    R->G = N.G; R->sp = N.sp; R->dsp = N.dsp; R->unc = unc;
+                }
+                has_ext = false;
+                if (b < a.bounces) {
+                    Cont C;
+                    if (continue_prepare(a, (uint32_t)pix, (uint32_t)s, b, S, C)) {
+                        cnt.add(kCntCont);
+                        beta = beta * C.w;
+                        ed = C.wi;
+                        has_ext = true;
+                        R->si = C.si; R->dsi = C.dsi; R->cw = C.cw;
+                    }
+                }
+                if (cand) {
+                    shadow = true;
+                    ray = make_ray(N.so, N.sdir);
+                    tmax = N.smax;
+                } else if (has_ext) {
+                    ray = make_ray(S.x + S.n * kRayEps, ed);
+                    ++b;
+                } else {
+                    end = true;
+                }
+            }
+            if (end) break;
+        }
+        // sample k's records to the structure-of-arrays buffer: word w of
+        // record v at words[((w * spl + k) * bounces + v) * nthr + gt]
+        if (valid) {
+            const int spl = (a.spp + L - 1) / L;
+            nvs[(int64_t)k * nthr + gt] = (uint8_t)nv;
+            for (int v = 0; v < nv; ++v) {
+                const uint32_t *src = reinterpret_cast<const uint32_t *>(&rec[v]);
+#pragma unroll
+                for (int w = 0; w < kRecWords; ++w)
+                    __stcs(words + (((int64_t)w * spl + k) * a.bounces + v) * nthr + gt, src[w]);
+            }
+        }
+        ++k;
+        nv = 0;
+        s += L;
+        if (s < a.spp) {
+            f3 o, d;
+            camera_ray(a, (uint32_t)pix, (uint32_t)s, o, d);
+            ray = make_ray(o, d);
+            beta = mk3(1.f, 1.f, 1.f);
+            b = 1;
+            shadow = false;
+            has_ext = false;
+            cnt.add(kCntPath);
+        }
+    }
+    cnt.flush(a.counters);
+    for (int off = L >> 1; off > 0; off >>= 1) {
+        sum.x += __shfl_xor_sync(0xffffffffu, sum.x, off);
+        sum.y += __shfl_xor_sync(0xffffffffu, sum.y, off);
+        sum.z += __shfl_xor_sync(0xffffffffu, sum.z, off);
+    }
+    if (valid && sl == 0) {
+        const float inv = 1.0f / (float)a.spp;
+        const float ex = sum.x * inv, ey = sum.y * inv, ez = sum.z * inv;
+        if (a.Ec) {
+            a.Ec[3 * pix] = ex;
+            a.Ec[3 * pix + 1] = ey;
+            a.Ec[3 * pix + 2] = ez;
+        }
+        a.Ic[3 * pix] = crf(ex, a.gain_c, a.wb[0], a.gamma_c[0]);
+        a.Ic[3 * pix + 1] = crf(ey, a.gain_c, a.wb[1], a.gamma_c[1]);
+        a.Ic[3 * pix + 2] = crf(ez, a.gain_c, a.wb[2], a.gamma_c[2]);
+    }
+}
+
+// The adjoint from the records k_render_keep wrote: the reverse sweep of
+// every recorded path with its pixel's dLoss/dEc, without tracing again.
+__global__ void __launch_bounds__(kRenderBlock) k_sweep_kept(const RenderArgs a, const uint32_t *__restrict__ words,
+                                                             const uint8_t *__restrict__ nvs) {
+    const int L = 1 << a.log2L;
+    const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t pix = gt >> a.log2L;
+    const int64_t nthr = ((int64_t)a.Hc * a.Wc) << a.log2L;
+    __shared__ float4 s_row[kRenderBlock];  // per-warp rows for scatter_add4
+    if (pix >= (int64_t)a.Hc * a.Wc) return;
+    const float inv = 1.0f / (float)a.spp;
+    const float gb_in[3] = {a.gE[3 * pix] * inv, a.gE[3 * pix + 1] * inv, a.gE[3 * pix + 2] * inv};
+    if (gb_in[0] == 0.0f && gb_in[1] == 0.0f && gb_in[2] == 0.0f) return;
+    const int sl = (int)(gt & (L - 1));
+    const int spl = (a.spp + L - 1) / L;
+    VRec rec[DPCS_MAX_BOUNCES];
+    for (int k = 0; k < spl && sl + k * L < a.spp; ++k) {
+        const int nv = nvs[(int64_t)k * nthr + gt];
+        for (int v = 0; v < nv; ++v) {
+            uint32_t *dst = reinterpret_cast<uint32_t *>(&rec[v]);
+#pragma unroll
+            for (int w = 0; w < kRecWords; ++w)
+                dst[w] = __ldcs(words + (((int64_t)w * spl + k) * a.bounces + v) * nthr + gt);
+        }
+        replay_sweep(a, rec, nv, gb_in, &s_row[threadIdx.x & ~31]);
+    }
+}
+
 // Eq. 1 adjoint: dIp += dEp Gp gamma Ip^(gamma-1); gamma_p and Gp reductions
 __global__ void k_prf_backward(const float *__restrict__ Ip, const float4 *__restrict__ dEp, int64_t ntex,
                                float g0, float g1, float g2, float gain, float *__restrict__ dIp, double *acc) {
@@ -830,6 +1021,18 @@ int launch_replay(const RenderArgs &a, cudaStream_t st) {
 int launch_render_grad(const RenderArgs &a, const LossArgs &l, cudaStream_t st) {
     const int64_t threads = ((int64_t)a.Hc * a.Wc) << a.log2L;
     k_render_grad<<<grid_for(threads, kRenderBlock), kRenderBlock, 0, st>>>(a, l);
+    return 1;
+}
+
+int launch_render_keep(const RenderArgs &a, uint32_t *words, uint8_t *nvs, cudaStream_t st) {
+    const int64_t threads = ((int64_t)a.Hc * a.Wc) << a.log2L;
+    k_render_keep<<<grid_for(threads, kRenderBlock), kRenderBlock, 0, st>>>(a, words, nvs);
+    return 1;
+}
+
+int launch_sweep_kept(const RenderArgs &a, const uint32_t *words, const uint8_t *nvs, cudaStream_t st) {
+    const int64_t threads = ((int64_t)a.Hc * a.Wc) << a.log2L;
+    k_sweep_kept<<<grid_for(threads, kRenderBlock), kRenderBlock, 0, st>>>(a, words, nvs);
     return 1;
 }
 

@@ -34,7 +34,8 @@ EXPORTED = [
     "dpcs_counters_read", "dpcs_debug_set_visit_cap", "dpcs_render_noalloc", "dpcs_serve_create", "dpcs_serve_destroy", "dpcs_serve_add_scene",
     "dpcs_serve_submit", "dpcs_serve_step", "dpcs_serve_query", "dpcs_serve_drain", "dpcs_serve_stats_get",
     "dpcs_probe_l2_load", "dpcs_probe_atomic4", "dpcs_gbuffer", "dpcs_denoise", "dpcs_denoise_backward",
-    "dpcs_l1_loss", "dpcs_tv_loss", "dpcs_scene_update", "dpcs_render_loss_backward",
+    "dpcs_l1_loss", "dpcs_tv_loss", "dpcs_scene_update", "dpcs_render_loss_backward", "dpcs_render_keep",
+    "dpcs_render_backward_kept",
 ]
 
 DPCS_REQ_RELIGHT = 0
@@ -118,6 +119,13 @@ _SIGS = {
     "dpcs_render_noalloc": (ctypes.c_int32, [_P, ctypes.c_uint64, _P, _P, ctypes.c_int32, ctypes.c_int32, _P,
                                              ctypes.POINTER(DpcsView), ctypes.POINTER(DpcsParams), ctypes.c_int32,
                                              ctypes.c_int32, ctypes.c_uint64, _P, _P, _P]),
+    "dpcs_render_keep": (ctypes.c_int32, [_P, ctypes.c_uint64, _P, _P, ctypes.c_int32, ctypes.c_int32, _P,
+                                          ctypes.POINTER(DpcsView), ctypes.POINTER(DpcsParams), ctypes.c_int32,
+                                          ctypes.c_int32, ctypes.c_uint64, _P, _P, _P]),
+    "dpcs_render_backward_kept": (ctypes.c_int32, [_P, ctypes.c_uint64, _P, _P, ctypes.c_int32, ctypes.c_int32, _P,
+                                                   ctypes.POINTER(DpcsView), ctypes.POINTER(DpcsParams),
+                                                   ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, _P, _P, _P, _P, _P,
+                                                   _P, _P, _P]),
     "dpcs_render_backward": (ctypes.c_int32, [_P, ctypes.c_uint64, _P, _P, ctypes.c_int32, ctypes.c_int32, _P,
                                               ctypes.POINTER(DpcsView), ctypes.POINTER(DpcsParams), ctypes.c_int32,
                                               ctypes.c_int32, ctypes.c_uint64, _P, _P, _P, _P, _P, _P, _P, _P]),
@@ -302,6 +310,18 @@ def dpcs_render_loss_backward(ctx, scene, albedo, rough, Ht, Wt, Ip, view, param
     return load_library().dpcs_render_loss_backward(ctx, scene, albedo, rough, Ht, Wt, Ip, ctypes.byref(view),
                                                     ctypes.byref(params), spp, bounces, seed, target, loss_kind, scale,
                                                     Ic, Ec, loss, dIp, dAlbedo, dRough, dParams, stream)
+
+
+def dpcs_render_keep(ctx, scene, albedo, rough, Ht, Wt, Ip, view, params, spp, bounces, seed, Ic, Ec, stream):
+    return load_library().dpcs_render_keep(ctx, scene, albedo, rough, Ht, Wt, Ip, ctypes.byref(view),
+                                           ctypes.byref(params), spp, bounces, seed, Ic, Ec, stream)
+
+
+def dpcs_render_backward_kept(ctx, scene, albedo, rough, Ht, Wt, Ip, view, params, spp, bounces, seed, Ec, Ic, dIc,
+                              dIp, dAlbedo, dRough, dParams, stream):
+    return load_library().dpcs_render_backward_kept(ctx, scene, albedo, rough, Ht, Wt, Ip, ctypes.byref(view),
+                                                    ctypes.byref(params), spp, bounces, seed, Ec, Ic, dIc, dIp,
+                                                    dAlbedo, dRough, dParams, stream)
 
 
 def dpcs_timing_enable(ctx, on):
@@ -505,14 +525,15 @@ class Context:
 
     # -- rendering -------------------------------------------------------------
     def render(self, scene: int, albedo, rough, Ip, view: DpcsView, params: DpcsParams, spp: int, bounces: int,
-               seed: int, Ic=None, Ec=None, stream=None):
+               seed: int, Ic=None, Ec=None, stream=None, keep: bool = False):
         import torch
 
         Ht, Wt = albedo.shape[0], albedo.shape[1]
         f32 = torch.float32
         if Ic is None:
             Ic = torch.empty((view.Hc, view.Wc, 3), dtype=f32, device=self.device)
-        st = self.lib.dpcs_render(self.handle, scene, _ptr(albedo, "albedo", (Ht, Wt, 3), f32, self.device),
+        fn = self.lib.dpcs_render_keep if keep else self.lib.dpcs_render  # keep: path records for render_backward(kept=True)
+        st = fn(self.handle, scene, _ptr(albedo, "albedo", (Ht, Wt, 3), f32, self.device),
                          _ptr(rough, "rough", (Ht, Wt), f32, self.device), Ht, Wt,
                          _ptr(Ip, "Ip", (view.Hp, view.Wp, 3), f32, self.device), ctypes.byref(view),
                          ctypes.byref(params), int(spp),
@@ -524,13 +545,14 @@ class Context:
 
     def render_backward(self, scene: int, albedo, rough, Ip, view: DpcsView, params: DpcsParams, spp: int,
                         bounces: int, seed: int, Ec, Ic, dIc, dIp=None, dAlbedo=None, dRough=None, dParams=None,
-                        stream=None):
+                        stream=None, kept: bool = False):
         import torch
 
         Ht, Wt = albedo.shape[0], albedo.shape[1]
         f32 = torch.float32
         img = (view.Hc, view.Wc, 3)
-        st = self.lib.dpcs_render_backward(
+        fn = self.lib.dpcs_render_backward_kept if kept else self.lib.dpcs_render_backward  # kept: no re-trace
+        st = fn(
             self.handle, scene, _ptr(albedo, "albedo", (Ht, Wt, 3), f32, self.device),
             _ptr(rough, "rough", (Ht, Wt), f32, self.device), Ht, Wt,
             _ptr(Ip, "Ip", (view.Hp, view.Wp, 3), f32, self.device), ctypes.byref(view),
