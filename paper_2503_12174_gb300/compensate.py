@@ -5,8 +5,10 @@ Ic = R(Ip) with a fresh Philox key (seed + k), takes the L2 loss against the
 target, carries dL/dIc back to Ip with the path adjoint, and applies an Adam
 step followed by the clamp of Ip to [0, 1].  By default the render, loss and
 adjoint are one call that traces each path once
-(``Context.render_loss_backward``); ``fused=False`` makes the separate
-render, loss and replay calls instead.
+(``Context.render_loss_backward``); with the denoiser the render keeps its
+path records and the adjoint sweeps them (``keep`` / ``kept``) instead of
+tracing again.  ``fused=False`` makes the separate render, loss and replay
+calls instead.
 
 With ``denoise`` set (a ``dpcs.DpcsDenoiseParams``), the loss is taken on
 the denoised image D(Ic) of Eq. 11 instead, and dL/dD is carried back to
@@ -72,8 +74,9 @@ class Compensation:
             self.history[k].copy_(self.loss[0])
             c.adam(self.P, self.G, self.M, self.V, k + 1, lr=self.lr, lo=0.0, hi=1.0)
             return
+        keep = self.denoise is not None and self.fused  # the filter couples pixels: keep the paths for the adjoint
         c.render(self.scene, self.albedo, self.rough, self.P, self.view, self.params, self.spp, self.bounces, s,
-                 Ic=self.Ic, Ec=self.Ec)
+                 Ic=self.Ic, Ec=self.Ec, keep=keep)
         if self.denoise is None:
             c.l2_loss(self.Ic, self.target, self.dIc, self.loss)
         else:
@@ -84,7 +87,7 @@ class Compensation:
         self.history[k].copy_(self.loss[0])
         self.G.zero_()
         c.render_backward(self.scene, self.albedo, self.rough, self.P, self.view, self.params, self.spp, self.bounces, s,
-                          self.Ec, self.Ic, self.dIc, dIp=self.G)
+                          self.Ec, self.Ic, self.dIc, dIp=self.G, kept=keep)
         c.adam(self.P, self.G, self.M, self.V, k + 1, lr=self.lr, lo=0.0, hi=1.0)
 
     def _loop(self):

@@ -14,8 +14,9 @@ followed by the clamp to the group's range: albedo [0, 1], roughness
 [0.01, 1], gamma_p [2, 3], gamma_c [1/3, 1], w [0.2, 2.5] (Sec. 3.2).
 
 Without the denoiser each pair's render, L1 term and adjoint are one call
-that traces its paths once (``Context.render_loss_backward``; ``fused=False``
-makes separate calls).  Every step runs in the library's kernels; the only
+that traces its paths once (``Context.render_loss_backward``); with it, the
+render keeps its path records and the adjoint sweeps them.  ``fused=False``
+makes separate calls that trace twice.  Every step runs in the library's kernels; the only
 host traffic per step is reading back the 11 response parameters the next
 renders take by value.
 """
@@ -84,8 +85,9 @@ class SceneFit:
                                        Ic=self.Ic, Ec=self.Ec, dAlbedo=self.gA, dRough=self.gR,
                                        dParams=self.gP if self.fit_params else None)
                 continue
+            keep = self.fused  # the denoiser couples pixels: keep the paths for the adjoint
             c.render(self.scene, self.albedo, self.rough, Ip, self.view, self.params, self.spp, self.bounces, s,
-                     Ic=self.Ic, Ec=self.Ec)
+                     Ic=self.Ic, Ec=self.Ec, keep=keep)
             if self.denoise is None:
                 c.l1_loss(self.Ic, target, self.dIc, self.losses[i:i + 1], scale=self.scale)
             else:
@@ -95,7 +97,7 @@ class SceneFit:
                 c.denoise_backward(self.dD, self.guide, self.wsum, self.denoise, dIc=self.dIc)
             c.render_backward(self.scene, self.albedo, self.rough, Ip, self.view, self.params, self.spp, self.bounces,
                               s, self.Ec, self.Ic, self.dIc, dAlbedo=self.gA, dRough=self.gR,
-                              dParams=self.gP if self.fit_params else None)
+                              dParams=self.gP if self.fit_params else None, kept=keep)
         K = self.K
         c.tv_loss(self.albedo, self.gA, self.losses[K:K + 1], self.tv_weight)
         c.tv_loss(self.rough, self.gR, self.losses[K + 1:K + 2], self.tv_weight)
