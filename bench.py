@@ -47,7 +47,7 @@ L2_FLUSH_BYTES = 256 << 20
 # ncu capture summarised in profiles/k_render_corner256.md.  It holds only for
 # the kernel sources it was measured on; once they change, the roofline's
 # traffic is reported as null until a new capture is taken.
-RENDER_TRAFFIC = {"bytes": 36726016, "sources_sha256": "ebcf179047fb9e9679f88b3714327d5e8bd925e3ea0724bf8c3cab03b4b83077"}
+RENDER_TRAFFIC = {"bytes": 36696832, "sources_sha256": "49c5bc28f35748f9f7edd4f4a8eaf5b316ec42460c62a3c12a4948a554e1ed11"}
 KERNEL_SOURCES = ("paper_2503_12174_gb300/csrc/render.cu", "paper_2503_12174_gb300/csrc/device.cuh",
                   "paper_2503_12174_gb300/csrc/internal.h")
 
@@ -579,7 +579,10 @@ def main():
             "denoised_compensation": {"steps": n, "ms": dc_ms,
                                       "Msamples_per_s": cs.n_samples * n * ws / (dc_ms / 1e3) / 1e6,
                                       "loss_first": float(dl[0]), "loss_last": float(dl[-1]),
-                                      "workload": f"{FWD_BWD_WORKLOAD} with the loss on D(Ic), one CUDA graph"},
+                                      "workload": f"corner scene T=1026 at {cs.Hc}x{cs.Wc} (camera, projector, textures), "
+                                                  f"{cs.spp} spp, {cs.bounces} bounces: render keeping the path records + "
+                                                  "Eq. 11 filter + L2 loss on D(Ic) + filter adjoint + sweep over the "
+                                                  "kept records + Adam on Ip, one CUDA graph"},
         }
 
     # ------------------------------------------------------------ scene-parameter fitting (Eq. 9)
