@@ -19,6 +19,7 @@ from .oracle import (  # noqa: F401
     render,
     render_backward,
     bsdf_eval,
+    pbr_eval,
     bsdf_pdf,
     bsdf_sample,
     ggx_D,

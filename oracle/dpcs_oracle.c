@@ -17,6 +17,9 @@
  *   - Eq. 12  radiance clipping (optional, off when clip == 0)
  *   - Eq. 11  the guide features of the cross-bilateral denoiser (or_gbuffer;
  *             the filter itself is in oracle.py)
+ *   - Sec. 3.2's scene parameters m and Vn: the principled BRDF's metallic
+ *     map and the normal map (or_render_m / or_render_backward_m; NULL maps
+ *     give metallic 0 and the unperturbed normal, i.e. or_render)
  *   - the analytic adjoint of the same estimator with the sampled directions
  *     held fixed (detached sampling), used by projector compensation (Eq. 13)
  *     and scene-parameter fitting (Eq. 9).
@@ -38,6 +41,14 @@
  *   - random numbers: Philox4x32-10 (Salmon et al., SC'11), key = seed,
  *     counter = (pixel, sample, vertex, 0); u = (x >> 8) * 2^-24.
  *   - local shading frame: Duff et al. (JCGT 2017) with its seam at n.z = -1/pi.
+ *   - metallic m (Burley 2012's metallic workflow): diffuse weight (1 - m),
+ *     Schlick F0 per channel (1 - m) f0 + m rho.
+ *   - normal map: Vn in [0,1]^3 decodes to v = 2 Vn - 1 in the tangent frame
+ *     (T = dp/du made orthogonal to the geometric normal N turned towards
+ *     the incoming ray, B = N x T); the shading normal is v / |v| in that
+ *     frame and replaces N in the BRDF, its sampling and both cosines.  N
+ *     stays the ray-offset direction, and light or continuations below the
+ *     geometric surface are dropped.
  *   - Morton codes in FP32 without contraction (this file is compiled with
  *     -ffp-contract=off), 10 bits per axis, x in the highest bit of each triple.
  *
@@ -512,6 +523,92 @@ int or_bsdf_sample(const double *n, const double *wo, double r, double ks, doubl
 }
 
 /* ------------------------------------------------------------------------- */
+/* Principled BRDF with a metallic parameter m (Burley 2012):                 */
+/*   f_j = (1 - m) rho_j / pi + ks S F_j,   S = D G / (4 ci co),              */
+/*   F_j = F0_j + (1 - F0_j) (1 - wo.h)^5,  F0_j = (1 - m) f0 + m rho_j.      */
+/* m = 0 is bsdf_eval.  With it come its partial derivatives in r (through   */
+/* alpha), rho_j, m and the shading normal n (wo, wi and h held fixed):      */
+/*   d ln S / dn = (d ln D / d ch) h + (d ln G1(co)/d co - 1/co) wo          */
+/*               + (d ln G1(ci)/d ci - 1/ci) wi,                             */
+/*   d ln D / d ch = -4 ch (a^2 - 1) / t,                                    */
+/*   d ln G1(c) / dc - 1/c = -(1 + (1 - a^2) c / s) / (c + s).               */
+/* ------------------------------------------------------------------------- */
+typedef struct {
+    double f[3], dr[3], drho[3], dm[3];
+    d3 dn[3];
+} pbr_f;
+
+static void pbr_eval(d3 n, d3 wo, d3 wi, const double rho[3], double r, double m, double ks, double f0, pbr_f *o)
+{
+    memset(o, 0, sizeof *o);
+    double ci = dot(n, wi), co = dot(n, wo);
+    if (ci <= 0.0 || co <= 0.0) return;
+    double S = 0.0, dSda = 0.0, s5 = 0.0, dadr = 0.0;
+    d3 dSdn = mk(0.0, 0.0, 0.0);
+    if (ks > 0.0) {
+        double a = alpha_of(r, &dadr);
+        d3 h = nrm(add(wo, wi));
+        double ch = dot(n, h);
+        double a2 = a * a;
+        double t = ch * ch * (a2 - 1.0) + 1.0;
+        double D = a2 / (OR_PI * t * t);
+        double si = sqrt(a2 + (1.0 - a2) * ci * ci), so = sqrt(a2 + (1.0 - a2) * co * co);
+        double G = (2.0 * ci / (ci + si)) * (2.0 * co / (co + so));
+        S = D * G / (4.0 * ci * co);
+        double dlnD = 2.0 / a - 4.0 * a * ch * ch / t;
+        double dlnG = -(a * (1.0 - ci * ci) / si) / (ci + si) - (a * (1.0 - co * co) / so) / (co + so);
+        dSda = S * (dlnD + dlnG);
+        double kh = -4.0 * ch * (a2 - 1.0) / t;
+        double ko = -(1.0 + (1.0 - a2) * co / so) / (co + so);
+        double ki = -(1.0 + (1.0 - a2) * ci / si) / (ci + si);
+        dSdn = scl(add(add(scl(h, kh), scl(wo, ko)), scl(wi, ki)), S);
+        double mm = 1.0 - dot(wo, h);
+        if (mm < 0.0) mm = 0.0;
+        s5 = mm * mm * mm * mm * mm;
+    }
+    for (int j = 0; j < 3; ++j) {
+        double F0 = (1.0 - m) * f0 + m * rho[j];
+        double F = F0 + (1.0 - F0) * s5;
+        o->f[j] = (1.0 - m) * rho[j] / OR_PI + ks * S * F;
+        o->dr[j] = ks * dSda * dadr * F;
+        o->drho[j] = (1.0 - m) / OR_PI + ks * S * (1.0 - s5) * m;
+        o->dm[j] = -rho[j] / OR_PI + ks * S * (1.0 - s5) * (rho[j] - f0);
+        o->dn[j] = scl(dSdn, ks * F);
+    }
+}
+
+/* exported for the pins: f[3], dr[3], drho[3], dm[3], dn[3][3] (row j = channel) */
+void or_pbr_eval(const double *n, const double *wo, const double *wi, const double *rho, double r, double m,
+                 double ks, double f0, double *f, double *dr, double *drho, double *dm, double *dn)
+{
+    pbr_f o;
+    pbr_eval(mk(n[0], n[1], n[2]), mk(wo[0], wo[1], wo[2]), mk(wi[0], wi[1], wi[2]), rho, r, m, ks, f0, &o);
+    for (int j = 0; j < 3; ++j) {
+        f[j] = o.f[j]; dr[j] = o.dr[j]; drho[j] = o.drho[j]; dm[j] = o.dm[j];
+        dn[3 * j] = o.dn[j].x; dn[3 * j + 1] = o.dn[j].y; dn[3 * j + 2] = o.dn[j].z;
+    }
+}
+
+/* Tangent of triangle (e1, e2) with corner texture coordinates tuv (u0 v0 u1
+ * v1 u2 v2): dp/du from e1 = dp/du du1 + dp/dv dv1, e2 = dp/du du2 + dp/dv
+ * dv2, made orthogonal to the unit normal N.  A degenerate parameterisation
+ * falls back to the shading-frame tangent of onb(). */
+static d3 tangent_of(d3 e1, d3 e2, const double *tuv, d3 N)
+{
+    double du1 = tuv[2] - tuv[0], dv1 = tuv[3] - tuv[1], du2 = tuv[4] - tuv[0], dv2 = tuv[5] - tuv[1];
+    double det = du1 * dv2 - du2 * dv1;
+    if (det != 0.0) {
+        d3 dpdu = scl(sub(scl(e1, dv2), scl(e2, dv1)), 1.0 / det);
+        d3 t = sub(dpdu, scl(N, dot(N, dpdu)));
+        double l = len(t);
+        if (l > 1e-12 * len(dpdu)) return scl(t, 1.0 / l);
+    }
+    d3 t, b;
+    onb(N, &t, &b);
+    return t;
+}
+
+/* ------------------------------------------------------------------------- */
 /* bilinear lookup with texel centres at (i + 1/2), clamp to edge              */
 /* ------------------------------------------------------------------------- */
 static void bilin(double xp, double yp, int W, int H, int idx[4], double w[4])
@@ -554,19 +651,25 @@ static double crf(double ec, int j, const or_params *P)
 /* ------------------------------------------------------------------------- */
 typedef struct {
     int tex_idx[4]; double tex_w[4];
-    double rho[3];
+    double rho[3], m;             /* albedo and metallic at the hit */
     double beta[3];
+    d3 T, B, N, ns; double ulen;  /* tangent frame, shading normal ns = u / |u| (normal map) */
     int nee;                      /* NEE light arrived (inside frustum, facing, unoccluded) */
     int proj_idx[4]; double proj_w[4];
-    double Ep[3], G, fp[3], dfp_dr;
+    double Ep[3], G;
+    pbr_f fp;                     /* f(wo, wp) and its partial derivatives */
+    d3 wp_cs;                     /* wp / cos_s */
     int unclipped[3];
     int cont;                     /* a continuation ray was traced from here */
-    double cw, fi[3], dfi_dr;     /* cos_i / (pdf q), f(wo, wi), d f(wo,wi) / dr */
+    double cw;                    /* cos_i / (pdf q) */
+    pbr_f fi;                     /* f(wo, wi) and its partial derivatives */
+    d3 wi_ci;                     /* wi / cos_i */
 } vrec;
 
 typedef struct {
     const dscene *S;
     const double *albedo, *rough; int Ht, Wt;
+    const double *metal, *nmap;   /* Ht x Wt and Ht x Wt x 3, or NULL */
     const double *Ep; int Hp, Wp;
     double Kc_inv[9], Kp[9], Rp[9], tp[3], cp[3];
     const or_params *P;
@@ -610,6 +713,24 @@ static int trace_sample(const rctx *C, uint32_t pix, uint32_t s, double L[3], vr
             for (int j = 0; j < 3; ++j) R->rho[j] += R->tex_w[k] * C->albedo[3 * R->tex_idx[k] + j];
             r += R->tex_w[k] * C->rough[R->tex_idx[k]];
         }
+        R->m = 0.0;
+        if (C->metal)
+            for (int k = 0; k < 4; ++k) R->m += R->tex_w[k] * C->metal[R->tex_idx[k]];
+        /* shading normal: the normal map in the triangle's tangent frame */
+        d3 ns = n;
+        R->N = n;
+        R->ulen = 0.0;
+        if (C->nmap) {
+            double vn[3] = {0.0, 0.0, 0.0};
+            for (int k = 0; k < 4; ++k)
+                for (int j = 0; j < 3; ++j) vn[j] += R->tex_w[k] * C->nmap[3 * R->tex_idx[k] + j];
+            R->T = tangent_of(S->e1[tri], S->e2[tri], tuv, n);
+            R->B = cross(n, R->T);
+            d3 u = add(add(scl(R->T, 2.0 * vn[0] - 1.0), scl(R->B, 2.0 * vn[1] - 1.0)), scl(n, 2.0 * vn[2] - 1.0));
+            R->ulen = len(u);
+            if (R->ulen > 1e-12) ns = scl(u, 1.0 / R->ulen);
+        }
+        R->ns = ns;
         for (int j = 0; j < 3; ++j) R->beta[j] = beta[j];
         d3 wo = scl(d, -1.0);
 
@@ -622,8 +743,8 @@ static int trace_sample(const rctx *C, uint32_t pix, uint32_t s, double L[3], vr
                 d3 v = sub(cp, x);
                 double r2 = dot(v, v), dist = sqrt(r2);
                 d3 wp = scl(v, 1.0 / dist);
-                double cs = dot(n, wp);
-                if (cs > 0.0) {
+                double cs = dot(ns, wp);
+                if (cs > 0.0 && dot(n, wp) > 0.0) {
                     double cpz = X.z / len(X);
                     d3 so = add(x, scl(n, OR_RAY_EPS));
                     d3 sv = sub(cp, so);
@@ -636,9 +757,10 @@ static int trace_sample(const rctx *C, uint32_t pix, uint32_t s, double L[3], vr
                             for (int k = 0; k < 4; ++k) R->Ep[j] += R->proj_w[k] * C->Ep[3 * R->proj_idx[k] + j];
                         }
                         R->G = P->k_proj * cpz * cs / r2;
-                        bsdf_eval(n, wo, wp, R->rho, r, P->ks, P->f0, R->fp, &R->dfp_dr);
+                        pbr_eval(ns, wo, wp, R->rho, r, R->m, P->ks, P->f0, &R->fp);
+                        R->wp_cs = scl(wp, 1.0 / cs);
                         for (int j = 0; j < 3; ++j) {
-                            double c = beta[j] * R->fp[j] * R->Ep[j] * R->G;
+                            double c = beta[j] * R->fp.f[j] * R->Ep[j] * R->G;
                             R->unclipped[j] = 1;
                             if (P->clip > 0.0 && c > P->clip) { c = P->clip; R->unclipped[j] = 0; }
                             L[j] += c;
@@ -652,18 +774,21 @@ static int trace_sample(const rctx *C, uint32_t pix, uint32_t s, double L[3], vr
         /* continuation: BSDF sampling, throughput, Russian roulette */
         rand4(C->seed, pix, s, (uint32_t)b, u);
         d3 wi;
-        if (!bsdf_sample(n, wo, r, P->ks, u[0], u[1], u[2], &wi)) break;
-        double pdf = bsdf_pdf(n, wo, wi, r, P->ks);
+        if (!bsdf_sample(ns, wo, r, P->ks, u[0], u[1], u[2], &wi)) break;
+        if (!(dot(n, wi) > 0.0)) break; /* below the geometric surface */
+        double pdf = bsdf_pdf(ns, wo, wi, r, P->ks);
         if (!(pdf > 0.0)) break;
         double qrr = 1.0;
         if (P->rr_start > 0 && b >= P->rr_start) {
             if (u[3] >= P->rr_q) break;
             qrr = P->rr_q;
         }
-        bsdf_eval(n, wo, wi, R->rho, r, P->ks, P->f0, R->fi, &R->dfi_dr);
+        pbr_eval(ns, wo, wi, R->rho, r, R->m, P->ks, P->f0, &R->fi);
         R->cont = 1;
-        R->cw = dot(n, wi) / (pdf * qrr);
-        for (int j = 0; j < 3; ++j) beta[j] *= R->fi[j] * R->cw;
+        double ci = dot(ns, wi);
+        R->cw = ci / (pdf * qrr);
+        R->wi_ci = scl(wi, 1.0 / ci);
+        for (int j = 0; j < 3; ++j) beta[j] *= R->fi.f[j] * R->cw;
         o = add(x, scl(n, OR_RAY_EPS));
         d = wi;
     }
@@ -674,6 +799,7 @@ static void rctx_make(rctx *C, const dscene *S, const double *albedo, const doub
                       const double *Ep, const or_view *Vw, const or_params *P, int spp, int bounces, uint64_t seed)
 {
     C->S = S; C->albedo = albedo; C->rough = rough; C->Ht = Ht; C->Wt = Wt;
+    C->metal = NULL; C->nmap = NULL;
     C->Ep = Ep; C->Hp = Vw->Hp; C->Wp = Vw->Wp;
     inv3(Vw->Kc, C->Kc_inv);
     memcpy(C->Kp, Vw->Kp, sizeof C->Kp);
@@ -700,12 +826,14 @@ int or_num_threads(int nthreads) { return set_threads(nthreads); }
 
 /*
  * Forward render of the listed pixels (pixel index = y * Wc + x); NULL list =
- * every pixel.  Ec and Ic are npix x 3.  Returns 0, or -1 on bad arguments.
+ * every pixel.  Ec and Ic are npix x 3.  metal (Ht x Wt) and nmap (Ht x Wt x
+ * 3) are the principled material's metallic and normal maps; NULL = metallic
+ * 0 and no normal map.  Returns 0, or -1 on bad arguments.
  */
-int or_render(const float *verts, const int32_t *tris, int32_t T, const float *uv, const double *albedo,
-              const double *rough, int32_t Ht, int32_t Wt, const double *Ip, const or_view *Vw, const or_params *P,
-              int32_t spp, int32_t bounces, uint64_t seed, const int64_t *pixels, int64_t npix, double *Ec, double *Ic,
-              int32_t nthreads)
+int or_render_m(const float *verts, const int32_t *tris, int32_t T, const float *uv, const double *albedo,
+                const double *rough, const double *metal, const double *nmap, int32_t Ht, int32_t Wt,
+                const double *Ip, const or_view *Vw, const or_params *P, int32_t spp, int32_t bounces, uint64_t seed,
+                const int64_t *pixels, int64_t npix, double *Ec, double *Ic, int32_t nthreads)
 {
     if (spp <= 0 || bounces < 0 || bounces > OR_MAX_VERTS || Ht <= 0 || Wt <= 0 || Vw->Hp <= 0 || Vw->Wp <= 0)
         return -1;
@@ -717,6 +845,8 @@ int or_render(const float *verts, const int32_t *tris, int32_t T, const float *u
     or_prf(Ip, ntex, P, Ep);
     rctx C;
     rctx_make(&C, &S, albedo, rough, Ht, Wt, Ep, Vw, P, spp, bounces, seed);
+    C.metal = metal;
+    C.nmap = nmap;
     int64_t n = pixels ? npix : (int64_t)Vw->Hc * Vw->Wc;
 #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t i = 0; i < n; ++i) {
@@ -737,17 +867,29 @@ int or_render(const float *verts, const int32_t *tris, int32_t T, const float *u
     return 0;
 }
 
+int or_render(const float *verts, const int32_t *tris, int32_t T, const float *uv, const double *albedo,
+              const double *rough, int32_t Ht, int32_t Wt, const double *Ip, const or_view *Vw, const or_params *P,
+              int32_t spp, int32_t bounces, uint64_t seed, const int64_t *pixels, int64_t npix, double *Ec, double *Ic,
+              int32_t nthreads)
+{
+    return or_render_m(verts, tris, T, uv, albedo, rough, NULL, NULL, Ht, Wt, Ip, Vw, P, spp, bounces, seed, pixels,
+                       npix, Ec, Ic, nthreads);
+}
+
 /*
- * Adjoint of or_render for the listed pixels: given dLoss/dIc (npix x 3),
+ * Adjoint of or_render_m for the listed pixels: given dLoss/dIc (npix x 3),
  * accumulates (+=) dLoss/dIp [Hp*Wp*3], dLoss/dalbedo [Ht*Wt*3],
- * dLoss/drough [Ht*Wt] and dParams [gamma_p(3), Gp, gamma_c(3), Gc, wb(3)].
- * The forward is recomputed here; sampled directions are held fixed.
+ * dLoss/drough [Ht*Wt], dLoss/dmetal [Ht*Wt] and dLoss/dnmap [Ht*Wt*3]
+ * (each only where its map was given) and dParams [gamma_p(3), Gp,
+ * gamma_c(3), Gc, wb(3)].  The forward is recomputed here; sampled
+ * directions are held fixed.
  */
-int or_render_backward(const float *verts, const int32_t *tris, int32_t T, const float *uv, const double *albedo,
-                       const double *rough, int32_t Ht, int32_t Wt, const double *Ip, const or_view *Vw,
-                       const or_params *P, int32_t spp, int32_t bounces, uint64_t seed, const int64_t *pixels,
-                       int64_t npix, const double *dIc, double *dIp, double *dAlbedo, double *dRough, double *dParams,
-                       int32_t nthreads)
+int or_render_backward_m(const float *verts, const int32_t *tris, int32_t T, const float *uv, const double *albedo,
+                         const double *rough, const double *metal, const double *nmap, int32_t Ht, int32_t Wt,
+                         const double *Ip, const or_view *Vw, const or_params *P, int32_t spp, int32_t bounces,
+                         uint64_t seed, const int64_t *pixels, int64_t npix, const double *dIc, double *dIp,
+                         double *dAlbedo, double *dRough, double *dMetal, double *dNmap, double *dParams,
+                         int32_t nthreads)
 {
     if (spp <= 0 || bounces < 0 || bounces > OR_MAX_VERTS || Ht <= 0 || Wt <= 0 || Vw->Hp <= 0 || Vw->Wp <= 0)
         return -1;
@@ -759,9 +901,12 @@ int or_render_backward(const float *verts, const int32_t *tris, int32_t T, const
     or_prf(Ip, ntex, P, Ep);
     rctx C;
     rctx_make(&C, &S, albedo, rough, Ht, Wt, Ep, Vw, P, spp, bounces, seed);
+    C.metal = metal;
+    C.nmap = nmap;
     int64_t n = pixels ? npix : (int64_t)Vw->Hc * Vw->Wc;
-    /* per-thread gradient buffers, summed in thread order afterwards */
-    size_t per = (size_t)(3 * ntex + 3 * nalb + nalb + 3);
+    /* per-thread gradient buffers (Ep, albedo, roughness, metallic, normal
+     * map), summed in thread order afterwards */
+    size_t per = (size_t)(3 * ntex + 3 * nalb + nalb + nalb + 3 * nalb);
     double *acc = (double *)calloc((size_t)nt * per, sizeof(double));
     double crf_acc[8] = {0};
 #pragma omp parallel
@@ -770,8 +915,8 @@ int or_render_backward(const float *verts, const int32_t *tris, int32_t T, const
 #ifdef _OPENMP
         tid = omp_get_thread_num();
 #endif
-        double *gEp = acc + (size_t)tid * per, *gA = gEp + 3 * ntex, *gR = gA + 3 * nalb, *gC = gR + nalb;
-        (void)gC;
+        double *gEp = acc + (size_t)tid * per, *gA = gEp + 3 * ntex, *gR = gA + 3 * nalb, *gM = gR + nalb,
+               *gN = gM + nalb;
 #pragma omp for schedule(static)
         for (int64_t i = 0; i < n; ++i) {
             uint32_t pix = (uint32_t)(pixels ? pixels[i] : i);
@@ -809,19 +954,36 @@ int or_render_backward(const float *verts, const int32_t *tris, int32_t T, const
                 for (int c = nv - 1; c >= 0; --c) {
                     const vrec *R = &rec[c];
                     double An[3] = {A[0], A[1], A[2]};
-                    double dr = 0.0;
+                    double dr = 0.0, dm = 0.0;
+                    d3 gn = mk(0.0, 0.0, 0.0); /* dL / d(shading normal) */
                     for (int j = 0; j < 3; ++j) {
                         double gb = gbar[j] * R->beta[j];
                         double ln_e = (R->nee && R->unclipped[j]) ? R->Ep[j] * R->G : 0.0; /* Ln / f */
                         double cont = R->cont ? R->cw * An[j] : 0.0;                       /* w / f * A */
                         if (R->nee && R->unclipped[j])
                             for (int k = 0; k < 4; ++k)
-                                gEp[3 * R->proj_idx[k] + j] += gb * R->fp[j] * R->G * R->proj_w[k];
-                        for (int k = 0; k < 4; ++k) gA[3 * R->tex_idx[k] + j] += gb * R->tex_w[k] * (ln_e + cont) / OR_PI;
-                        dr += gb * (R->dfp_dr * ln_e + R->dfi_dr * cont);
-                        A[j] = R->fp[j] * ln_e + R->fi[j] * cont;
+                                gEp[3 * R->proj_idx[k] + j] += gb * R->fp.f[j] * R->G * R->proj_w[k];
+                        double ga = gb * (R->fp.drho[j] * ln_e + R->fi.drho[j] * cont);
+                        for (int k = 0; k < 4; ++k) gA[3 * R->tex_idx[k] + j] += ga * R->tex_w[k];
+                        dr += gb * (R->fp.dr[j] * ln_e + R->fi.dr[j] * cont);
+                        dm += gb * (R->fp.dm[j] * ln_e + R->fi.dm[j] * cont);
+                        /* the normal enters f and cos_s (NEE), f and cos_i (continuation) */
+                        if (ln_e != 0.0)
+                            gn = add(gn, scl(add(R->fp.dn[j], scl(R->wp_cs, R->fp.f[j])), gb * ln_e));
+                        if (cont != 0.0)
+                            gn = add(gn, scl(add(R->fi.dn[j], scl(R->wi_ci, R->fi.f[j])), gb * cont));
+                        A[j] = R->fp.f[j] * ln_e + R->fi.f[j] * cont;
                     }
                     for (int k = 0; k < 4; ++k) gR[R->tex_idx[k]] += dr * R->tex_w[k];
+                    if (metal)
+                        for (int k = 0; k < 4; ++k) gM[R->tex_idx[k]] += dm * R->tex_w[k];
+                    if (nmap && R->ulen > 1e-12) {
+                        /* ns = u / |u|, u = T v0 + B v1 + N v2, v = 2 Vn - 1 */
+                        d3 gu = scl(sub(gn, scl(R->ns, dot(R->ns, gn))), 1.0 / R->ulen);
+                        double gv[3] = {2.0 * dot(R->T, gu), 2.0 * dot(R->B, gu), 2.0 * dot(R->N, gu)};
+                        for (int k = 0; k < 4; ++k)
+                            for (int j = 0; j < 3; ++j) gN[3 * R->tex_idx[k] + j] += gv[j] * R->tex_w[k];
+                    }
                 }
             }
         }
@@ -850,6 +1012,18 @@ int or_render_backward(const float *verts, const int32_t *tris, int32_t T, const
         for (int th = 0; th < nt; ++th) g += acc[(size_t)th * per + 3 * ntex + 3 * nalb + t];
         dRough[t] += g;
     }
+    if (metal && dMetal)
+        for (int64_t t = 0; t < nalb; ++t) {
+            double g = 0.0;
+            for (int th = 0; th < nt; ++th) g += acc[(size_t)th * per + 3 * ntex + 4 * nalb + t];
+            dMetal[t] += g;
+        }
+    if (nmap && dNmap)
+        for (int64_t t = 0; t < 3 * nalb; ++t) {
+            double g = 0.0;
+            for (int th = 0; th < nt; ++th) g += acc[(size_t)th * per + 3 * ntex + 5 * nalb + t];
+            dNmap[t] += g;
+        }
     dParams[0] += prf_acc[0]; dParams[1] += prf_acc[1]; dParams[2] += prf_acc[2]; dParams[3] += prf_acc[3];
     dParams[4] += crf_acc[0]; dParams[5] += crf_acc[1]; dParams[6] += crf_acc[2]; dParams[7] += crf_acc[3];
     dParams[8] += crf_acc[4]; dParams[9] += crf_acc[5]; dParams[10] += crf_acc[6];
@@ -857,6 +1031,16 @@ int or_render_backward(const float *verts, const int32_t *tris, int32_t T, const
     free(Ep);
     scene_free(&S);
     return 0;
+}
+
+int or_render_backward(const float *verts, const int32_t *tris, int32_t T, const float *uv, const double *albedo,
+                       const double *rough, int32_t Ht, int32_t Wt, const double *Ip, const or_view *Vw,
+                       const or_params *P, int32_t spp, int32_t bounces, uint64_t seed, const int64_t *pixels,
+                       int64_t npix, const double *dIc, double *dIp, double *dAlbedo, double *dRough, double *dParams,
+                       int32_t nthreads)
+{
+    return or_render_backward_m(verts, tris, T, uv, albedo, rough, NULL, NULL, Ht, Wt, Ip, Vw, P, spp, bounces, seed,
+                                pixels, npix, dIc, dIp, dAlbedo, dRough, NULL, NULL, dParams, nthreads);
 }
 
 /* ------------------------------------------------------------------------- */

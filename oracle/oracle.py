@@ -62,6 +62,10 @@ def load():
         _lib.or_bsdf_sample.argtypes = [P, P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                         ctypes.c_double, ctypes.c_double, P]
         _lib.or_bsdf_eval.argtypes = [P, P, P, P, ctypes.c_double, ctypes.c_double, ctypes.c_double, P, P]
+        _lib.or_pbr_eval.argtypes = [P, P, P, P, ctypes.c_double, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                     P, P, P, P, P]
+        _lib.or_render_m.restype = ctypes.c_int
+        _lib.or_render_backward_m.restype = ctypes.c_int
         _lib.or_gbuffer.restype = ctypes.c_int
         _lib.or_num_threads.restype = ctypes.c_int
         _lib.or_num_threads.argtypes = [ctypes.c_int]
@@ -160,6 +164,16 @@ def bsdf_eval(n, wo, wi, rho, r, ks, f0):
     return f, float(dfdr[0])
 
 
+def pbr_eval(n, wo, wi, rho, r, m, ks, f0):
+    """Principled BRDF with metallic ``m``: dict(f, dr, drho, dm (3,) and dn (3, 3), row = channel)."""
+    n, wo, wi, rho = (_c(x, np.float64) for x in (n, wo, wi, rho))
+    out = {k: np.zeros(3) for k in ("f", "dr", "drho", "dm")}
+    out["dn"] = np.zeros((3, 3))
+    load().or_pbr_eval(_p(n), _p(wo), _p(wi), _p(rho), float(r), float(m), float(ks), float(f0), _p(out["f"]),
+                       _p(out["dr"]), _p(out["drho"]), _p(out["dm"]), _p(out["dn"]))
+    return out
+
+
 def bsdf_pdf(n, wo, wi, r, ks) -> float:
     n, wo, wi = (_c(x, np.float64) for x in (n, wo, wi))
     return load().or_bsdf_pdf(_p(n), _p(wo), _p(wi), float(r), float(ks))
@@ -188,11 +202,29 @@ def _scene_args(sc, albedo, rough, Ip):
     return verts, tris, uv, albedo, rough, Ip
 
 
+_SCENE = object()  # default: take the map from the scene (None there = not used)
+
+
+def _maps(sc, metallic, normal, Ht, Wt):
+    """The principled maps as float64 arrays (or None); checked against the albedo's size."""
+    m = getattr(sc, "metallic", None) if metallic is _SCENE else metallic
+    nm = getattr(sc, "normal", None) if normal is _SCENE else normal
+    m = None if m is None else _c(m, np.float64)
+    nm = None if nm is None else _c(nm, np.float64)
+    if m is not None and m.shape != (Ht, Wt):
+        raise ValueError(f"metallic map {m.shape} != {(Ht, Wt)}")
+    if nm is not None and nm.shape != (Ht, Wt, 3):
+        raise ValueError(f"normal map {nm.shape} != {(Ht, Wt, 3)}")
+    return m, nm
+
+
 def render(sc, pixels=None, *, albedo=None, rough=None, Ip=None, params=None, spp=None, bounces=None,
-           seed=None, nthreads: int = 0):
+           seed=None, nthreads: int = 0, metallic=_SCENE, normal=_SCENE):
     """FP64 forward render.  Returns (Ec, Ic), each (npix, 3) for a pixel list
-    or (Hc, Wc, 3) for the full image."""
+    or (Hc, Wc, 3) for the full image.  ``metallic`` (Ht, Wt) and ``normal``
+    (Ht, Wt, 3) default to the scene's maps; None = metallic 0 / no normal map."""
     verts, tris, uv, albedo, rough, Ip = _scene_args(sc, albedo, rough, Ip)
+    m, nm = _maps(sc, metallic, normal, albedo.shape[0], albedo.shape[1])
     P = make_params(params or sc.params)
     V = make_view(sc)
     full = pixels is None
@@ -200,12 +232,13 @@ def render(sc, pixels=None, *, albedo=None, rough=None, Ip=None, params=None, sp
     n = sc.Hc * sc.Wc if full else len(px)
     Ec = np.zeros((n, 3))
     Ic = np.zeros((n, 3))
-    rc = load().or_render(_p(verts), _p(tris), ctypes.c_int32(len(tris)), _p(uv), _p(albedo), _p(rough),
-                          ctypes.c_int32(albedo.shape[0]), ctypes.c_int32(albedo.shape[1]), _p(Ip),
-                          ctypes.byref(V), ctypes.byref(P), ctypes.c_int32(spp or sc.spp),
-                          ctypes.c_int32(sc.bounces if bounces is None else bounces),
-                          ctypes.c_uint64(sc.seed if seed is None else seed),
-                          None if full else _p(px), ctypes.c_int64(n), _p(Ec), _p(Ic), ctypes.c_int32(nthreads))
+    rc = load().or_render_m(_p(verts), _p(tris), ctypes.c_int32(len(tris)), _p(uv), _p(albedo), _p(rough),
+                            None if m is None else _p(m), None if nm is None else _p(nm),
+                            ctypes.c_int32(albedo.shape[0]), ctypes.c_int32(albedo.shape[1]), _p(Ip),
+                            ctypes.byref(V), ctypes.byref(P), ctypes.c_int32(spp or sc.spp),
+                            ctypes.c_int32(sc.bounces if bounces is None else bounces),
+                            ctypes.c_uint64(sc.seed if seed is None else seed),
+                            None if full else _p(px), ctypes.c_int64(n), _p(Ec), _p(Ic), ctypes.c_int32(nthreads))
     if rc != 0:
         raise ValueError("oracle render: invalid arguments")
     if full:
@@ -214,10 +247,12 @@ def render(sc, pixels=None, *, albedo=None, rough=None, Ip=None, params=None, sp
 
 
 def render_backward(sc, dIc, pixels=None, *, albedo=None, rough=None, Ip=None, params=None, spp=None,
-                    bounces=None, seed=None, nthreads: int = 0):
+                    bounces=None, seed=None, nthreads: int = 0, metallic=_SCENE, normal=_SCENE):
     """FP64 adjoint.  ``dIc`` is (npix, 3) for a pixel list or (Hc, Wc, 3).
-    Returns dict(dIp, dalbedo, drough, dparams[11])."""
+    Returns dict(dIp, dalbedo, drough, dparams[11]) plus dmetallic / dnormal
+    where those maps are used (see ``render``)."""
     verts, tris, uv, albedo, rough, Ip = _scene_args(sc, albedo, rough, Ip)
+    m, nm = _maps(sc, metallic, normal, albedo.shape[0], albedo.shape[1])
     P = make_params(params or sc.params)
     V = make_view(sc)
     full = pixels is None
@@ -227,16 +262,25 @@ def render_backward(sc, dIc, pixels=None, *, albedo=None, rough=None, Ip=None, p
     dIp = np.zeros(Ip.shape)
     dA = np.zeros(albedo.shape)
     dR = np.zeros(rough.shape)
+    dM = None if m is None else np.zeros(m.shape)
+    dN = None if nm is None else np.zeros(nm.shape)
     dP = np.zeros(11)
-    rc = load().or_render_backward(
+    rc = load().or_render_backward_m(
         _p(verts), _p(tris), ctypes.c_int32(len(tris)), _p(uv), _p(albedo), _p(rough),
+        None if m is None else _p(m), None if nm is None else _p(nm),
         ctypes.c_int32(albedo.shape[0]), ctypes.c_int32(albedo.shape[1]), _p(Ip), ctypes.byref(V),
         ctypes.byref(P), ctypes.c_int32(spp or sc.spp), ctypes.c_int32(sc.bounces if bounces is None else bounces),
         ctypes.c_uint64(sc.seed if seed is None else seed), None if full else _p(px), ctypes.c_int64(n), _p(dIc),
-        _p(dIp), _p(dA), _p(dR), _p(dP), ctypes.c_int32(nthreads))
+        _p(dIp), _p(dA), _p(dR), None if dM is None else _p(dM), None if dN is None else _p(dN), _p(dP),
+        ctypes.c_int32(nthreads))
     if rc != 0:
         raise ValueError("oracle render_backward: invalid arguments")
-    return {"dIp": dIp, "dalbedo": dA, "drough": dR, "dparams": dP}
+    out = {"dIp": dIp, "dalbedo": dA, "drough": dR, "dparams": dP}
+    if dM is not None:
+        out["dmetallic"] = dM
+    if dN is not None:
+        out["dnormal"] = dN
+    return out
 
 
 def adam_step(p, g, m, v, step, lr=1e-2, b1=0.9, b2=0.999, eps=1e-8, lo=0.0, hi=1.0):

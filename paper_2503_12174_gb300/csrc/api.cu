@@ -50,7 +50,7 @@ struct dpcs_ctx {
     uint64_t next_scene = 1;
     // scratch
     Buf ep4, tex4, gE, dEp4, dtex4, acc, partial, build, upload, pix;  // pix: per-pixel dIc and Ec of the unfused loss path
-    Buf kept;  // path records of the last dpcs_render_keep: 32-bit words (structure of arrays), then per-sample vertex counts
+    Buf kept;  // path records of the last dpcs_render_keep: 16-byte chunks (structure of arrays), then per-sample vertex counts
     struct {
         bool valid = false;
         uint64_t scene = 0, seed = 0;
@@ -633,7 +633,7 @@ dpcs_status dpcs_render_keep(dpcs_ctx *c, dpcs_scene scene, const float *albedo,
     a.Ec = Ec;
     char *kp = (char *)c->kept.p;
     TimedLaunch *tl = timing_begin(c, 0, st);
-    nl += launch_render_keep(a, (uint32_t *)kp, (uint8_t *)(kp + ((words + 255) & ~size_t(255))), st);
+    nl += launch_render_keep(a, kp, (uint8_t *)(kp + ((words + 255) & ~size_t(255))), st);
     timing_end(tl, st);
     if ((s = check_launch(c, nl, "render_keep"))) return s;
     c->kept_key.valid = true;
@@ -685,7 +685,7 @@ dpcs_status dpcs_render_backward_kept(dpcs_ctx *c, dpcs_scene scene, const float
     a.dtex = want_tex ? (float4 *)c->dtex4.p : nullptr;
     const char *kp = (const char *)c->kept.p;
     TimedLaunch *tl = timing_begin(c, 1, st);
-    nl += launch_sweep_kept(a, (const uint32_t *)kp, (const uint8_t *)(kp + ((words + 255) & ~size_t(255))), st);
+    nl += launch_sweep_kept(a, kp, (const uint8_t *)(kp + ((words + 255) & ~size_t(255))), st);
     timing_end(tl, st);
     nl += launch_prf_backward(Ip, (const float4 *)c->dEp4.p, np, params->gamma_p, params->gain_p, dIp, acc, st);
     if (want_tex) nl += launch_tex_backward((const float4 *)c->dtex4.p, nt, dAlbedo, dRough, st);

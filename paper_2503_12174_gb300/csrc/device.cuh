@@ -4,6 +4,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include "internal.h"
@@ -493,6 +494,18 @@ struct VRec {
 
 constexpr int kRecWords = (int)(sizeof(VRec) / 4);  // VRec as 32-bit words (records kept in device memory)
 static_assert(kRecWords == kRecWordsHost, "the host sizes kept records with kRecWordsHost");
+
+// Kept records in device memory: each VRec as six 16-byte chunks (words
+// 4c..4c+3 of the struct); chunk c of record v of sample k of thread t sits
+// at chunk index ((c * spl + k) * bounces + v) * nthreads + t, so a warp's
+// accesses to one chunk are contiguous.
+constexpr int kKeptChunks = kRecWords / 4;
+static_assert(kRecWords % 4 == 0, "VRec must be whole 16-byte chunks");
+constexpr int kKeptGChunk = (int)(offsetof(VRec, G) / 16), kKeptGWord = (int)(offsetof(VRec, G) % 16) / 4;
+static_assert(offsetof(VRec, G) == 14 * 4, "k_render_keep writes G as word 2 of chunk 3");
+__device__ __forceinline__ int64_t kept_chunk(int c, int k, int v, int spl, int bounces, int64_t nthr, int64_t t) {
+    return (((int64_t)c * spl + k) * bounces + v) * nthr + t;
+}
 
 // first camera ray of sample s of pixel pix (Eq. 6 with the Eq. 4 box filter)
 __device__ __forceinline__ void camera_ray(const RenderArgs &a, uint32_t pix, uint32_t s, f3 &o, f3 &d) {

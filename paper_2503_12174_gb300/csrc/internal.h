@@ -111,8 +111,8 @@ int launch_crf_backward(const float *dIc, const float *Ec, const float *Ic, int6
 int launch_replay(const RenderArgs &a, cudaStream_t st);
 int launch_render_grad(const RenderArgs &a, const LossArgs &l, cudaStream_t st);
 int launch_pixel_loss(const float *Ic, int64_t n, const LossArgs &l, float *dIc, cudaStream_t st);
-int launch_render_keep(const RenderArgs &a, uint32_t *words, uint8_t *nvs, cudaStream_t st);
-int launch_sweep_kept(const RenderArgs &a, const uint32_t *words, const uint8_t *nvs, cudaStream_t st);
+int launch_render_keep(const RenderArgs &a, void *chunks, uint8_t *nvs, cudaStream_t st);
+int launch_sweep_kept(const RenderArgs &a, const void *chunks, const uint8_t *nvs, cudaStream_t st);
 constexpr int kRecWordsHost = 24;  // 32-bit words of one kept vertex record (VRec)
 int launch_loss_out(const double *acc, float *loss, cudaStream_t st);
 int launch_prf_backward(const float *Ip, const float4 *dEp, int64_t ntex, const float gamma_p[3], float gain_p,

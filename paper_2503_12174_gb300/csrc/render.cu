@@ -723,7 +723,7 @@ __global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB) k_render_grad(
 // including one that couples pixels (the Eq. 11 filter), without tracing
 // the paths again.
 __global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB)
-    k_render_keep(const RenderArgs a, uint32_t *__restrict__ words, uint8_t *__restrict__ nvs) {
+    k_render_keep(const RenderArgs a, uint4 *__restrict__ chunks, uint8_t *__restrict__ nvs) {
     const int L = 1 << a.log2L;
     const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t pix = gt >> a.log2L;
@@ -741,7 +741,7 @@ __global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB)
     float tmax = INFINITY;
     Trav st;
     int stack[kStack];
-    VRec rec[DPCS_MAX_BOUNCES];
+    const int spl = (a.spp + L - 1) / L;
     if (s < a.spp && a.bounces > 0) {
         f3 o, d;
         camera_ray(a, (uint32_t)pix, (uint32_t)s, o, d);
@@ -754,7 +754,6 @@ __global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB)
     const int64_t max_iter = ((int64_t)(a.spp / L + 1) * (2 * a.bounces + 1)) * (2 * (int64_t)a.T + 18);
     int64_t iter = 0;
     while (s < a.spp) {
-        VRec *rs = rec;  // this sample's records, copied out when its path ends
         while (true) {  // the lane's current path; the warp starts its next samples together
             if (++iter > max_iter) {
                 atomicOr(a.status, kStatusTraversalLimit);
@@ -778,7 +777,12 @@ __global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB)
             bool end = false;
             if (shadow) {
                 if (hit) {
-                    rs[nv - 1].G = 0.0f;  // occluded: no projector light at this vertex
+                    // occluded: no projector light at the last recorded vertex
+                    if (valid) {
+                        uint32_t *w = reinterpret_cast<uint32_t *>(chunks + kept_chunk(kKeptGChunk, k, nv - 1, spl,
+                                                                                       a.bounces, nthr, gt));
+                        __stcs(w + kKeptGWord, 0u);
+                    }
                 } else {
                     sum = sum + c;
                     cnt.add(kCntLit);
@@ -795,31 +799,47 @@ __global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB)
             } else {
                 cnt.add(kCntVert);
                 const Surf S = surface_at(a, st.h, ray.d);
-                VRec *R = &rs[nv++];
-                R->tx0 = S.tb.x0; R->ty0 = S.tb.y0; R->tfx = S.tb.fx; R->tfy = S.tb.fy;
-                R->beta[0] = beta.x; R->beta[1] = beta.y; R->beta[2] = beta.z;
-                R->rho[0] = S.rho.x; R->rho[1] = S.rho.y; R->rho[2] = S.rho.z;
-                R->G = 0.0f; R->cw = 0.0f; R->unc = 0u; R->sp = R->dsp = R->si = R->dsi = 0.0f;
+                const f3 beta_v = beta;
                 Nee N;
                 const bool cand = nee_prepare(a, S, N);
-                if (cand) {
-                    unsigned unc;
-                    c = nee_contrib(a, beta, N, unc);
-                    R->px0 = N.pb.x0; R->py0 = N.pb.y0; R->pfx = N.pb.fx; R->pfy = N.pb.fy;
-                    R->Ep[0] = N.ep.x; R->Ep[1] = N.ep.y; R->Ep[2] = N.ep.z;
-                    R->G = N.G; R->sp = N.sp; R->dsp = N.dsp; R->unc = unc;
-                }
+                unsigned unc = 0u;
+                if (cand) c = nee_contrib(a, beta, N, unc);
                 has_ext = false;
+                Cont C;
+                C.si = C.dsi = C.cw = 0.0f;
                 if (b < a.bounces) {
-                    Cont C;
                     if (continue_prepare(a, (uint32_t)pix, (uint32_t)s, b, S, C)) {
                         cnt.add(kCntCont);
                         beta = beta * C.w;
                         ed = C.wi;
                         has_ext = true;
-                        R->si = C.si; R->dsi = C.dsi; R->cw = C.cw;
+                    } else {
+                        C.si = C.dsi = C.cw = 0.0f;
                     }
                 }
+                // the vertex record (the fields of VRec, in order) straight to
+                // the kept buffer: six 16-byte chunks, streaming stores
+                if (valid) {
+                    const uint32_t px0 = cand ? (uint32_t)N.pb.x0 : 0u, py0 = cand ? (uint32_t)N.pb.y0 : 0u;
+                    const float pfx = cand ? N.pb.fx : 0.0f, pfy = cand ? N.pb.fy : 0.0f;
+                    const float e0 = cand ? N.ep.x : 0.0f, e1 = cand ? N.ep.y : 0.0f, e2 = cand ? N.ep.z : 0.0f;
+                    const float G = cand ? N.G : 0.0f, sp = cand ? N.sp : 0.0f, dsp = cand ? N.dsp : 0.0f;
+                    const uint4 q[kKeptChunks] = {
+                        make_uint4((uint32_t)S.tb.x0, (uint32_t)S.tb.y0, px0, py0),
+                        make_uint4(__float_as_uint(S.tb.fx), __float_as_uint(S.tb.fy), __float_as_uint(pfx),
+                                   __float_as_uint(pfy)),
+                        make_uint4(__float_as_uint(beta_v.x), __float_as_uint(beta_v.y), __float_as_uint(beta_v.z),
+                                   __float_as_uint(e0)),
+                        make_uint4(__float_as_uint(e1), __float_as_uint(e2), __float_as_uint(G),
+                                   __float_as_uint(S.rho.x)),
+                        make_uint4(__float_as_uint(S.rho.y), __float_as_uint(S.rho.z), __float_as_uint(sp),
+                                   __float_as_uint(dsp)),
+                        make_uint4(__float_as_uint(C.si), __float_as_uint(C.dsi), __float_as_uint(C.cw), unc)};
+#pragma unroll
+                    for (int q4 = 0; q4 < kKeptChunks; ++q4)
+                        __stcs(chunks + kept_chunk(q4, k, nv, spl, a.bounces, nthr, gt), q[q4]);
+                }
+                ++nv;
                 if (cand) {
                     shadow = true;
                     ray = make_ray(N.so, N.sdir);
@@ -833,18 +853,7 @@ __global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB)
             }
             if (end) break;
         }
-        // sample k's records to the structure-of-arrays buffer: word w of
-        // record v at words[((w * spl + k) * bounces + v) * nthr + gt]
-        if (valid) {
-            const int spl = (a.spp + L - 1) / L;
-            nvs[(int64_t)k * nthr + gt] = (uint8_t)nv;
-            for (int v = 0; v < nv; ++v) {
-                const uint32_t *src = reinterpret_cast<const uint32_t *>(&rec[v]);
-#pragma unroll
-                for (int w = 0; w < kRecWords; ++w)
-                    __stcs(words + (((int64_t)w * spl + k) * a.bounces + v) * nthr + gt, src[w]);
-            }
-        }
+        if (valid) nvs[(int64_t)k * nthr + gt] = (uint8_t)nv;  // sample k's vertex count
         ++k;
         nv = 0;
         s += L;
@@ -881,7 +890,7 @@ __global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB)
 
 // The adjoint from the records k_render_keep wrote: the reverse sweep of
 // every recorded path with its pixel's dLoss/dEc, without tracing again.
-__global__ void __launch_bounds__(kRenderBlock) k_sweep_kept(const RenderArgs a, const uint32_t *__restrict__ words,
+__global__ void __launch_bounds__(kRenderBlock) k_sweep_kept(const RenderArgs a, const uint4 *__restrict__ chunks,
                                                              const uint8_t *__restrict__ nvs) {
     const int L = 1 << a.log2L;
     const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -898,10 +907,9 @@ __global__ void __launch_bounds__(kRenderBlock) k_sweep_kept(const RenderArgs a,
     for (int k = 0; k < spl && sl + k * L < a.spp; ++k) {
         const int nv = nvs[(int64_t)k * nthr + gt];
         for (int v = 0; v < nv; ++v) {
-            uint32_t *dst = reinterpret_cast<uint32_t *>(&rec[v]);
+            uint4 *dst = reinterpret_cast<uint4 *>(&rec[v]);
 #pragma unroll
-            for (int w = 0; w < kRecWords; ++w)
-                dst[w] = __ldcs(words + (((int64_t)w * spl + k) * a.bounces + v) * nthr + gt);
+            for (int q4 = 0; q4 < kKeptChunks; ++q4) dst[q4] = __ldcs(chunks + kept_chunk(q4, k, v, spl, a.bounces, nthr, gt));
         }
         replay_sweep(a, rec, nv, gb_in, &s_row[threadIdx.x & ~31]);
     }
@@ -1024,15 +1032,15 @@ int launch_render_grad(const RenderArgs &a, const LossArgs &l, cudaStream_t st) 
     return 1;
 }
 
-int launch_render_keep(const RenderArgs &a, uint32_t *words, uint8_t *nvs, cudaStream_t st) {
+int launch_render_keep(const RenderArgs &a, void *chunks, uint8_t *nvs, cudaStream_t st) {
     const int64_t threads = ((int64_t)a.Hc * a.Wc) << a.log2L;
-    k_render_keep<<<grid_for(threads, kRenderBlock), kRenderBlock, 0, st>>>(a, words, nvs);
+    k_render_keep<<<grid_for(threads, kRenderBlock), kRenderBlock, 0, st>>>(a, (uint4 *)chunks, nvs);
     return 1;
 }
 
-int launch_sweep_kept(const RenderArgs &a, const uint32_t *words, const uint8_t *nvs, cudaStream_t st) {
+int launch_sweep_kept(const RenderArgs &a, const void *chunks, const uint8_t *nvs, cudaStream_t st) {
     const int64_t threads = ((int64_t)a.Hc * a.Wc) << a.log2L;
-    k_sweep_kept<<<grid_for(threads, kRenderBlock), kRenderBlock, 0, st>>>(a, words, nvs);
+    k_sweep_kept<<<grid_for(threads, kRenderBlock), kRenderBlock, 0, st>>>(a, (const uint4 *)chunks, nvs);
     return 1;
 }
 

@@ -69,6 +69,8 @@ class Scene:
     bounces: int
     seed: int
     name: str = ""
+    metallic: np.ndarray | None = None  # (Ht, Wt) float32 in [0, 1]; None = 0 everywhere
+    normal: np.ndarray | None = None    # (Ht, Wt, 3) float32 normal map in [0, 1]^3; None = unperturbed
 
     @property
     def Hp(self) -> int:
@@ -378,3 +380,22 @@ CONFIGS = {
     "compensation": compensation,
     "heightfield": heightfield,
 }
+
+
+def principled_maps(rng, Ht: int, Wt: int, metal_max: float = 0.8, bump: float = 0.35):
+    """Seeded maps of the principled material (Sec. 3.2, Sec. 4.3): metallic
+    in [0, metal_max] from smooth noise, and a normal map from the slopes of
+    a smooth bump field h (tangent-space normal (-bump dh/du, -bump dh/dv, 1)
+    normalised, stored as (n + 1) / 2 in [0, 1]^3)."""
+    metallic = (metal_max * smooth_noise(rng, Ht, Wt)).astype(np.float32)
+    h = smooth_noise(rng, Ht, Wt)
+    dhdv, dhdu = np.gradient(h)
+    n = np.stack([-bump * dhdu * Wt / 8.0, -bump * dhdv * Ht / 8.0, np.ones_like(h)], -1)
+    n /= np.linalg.norm(n, axis=-1, keepdims=True)
+    return metallic, ((n + 1.0) * 0.5).astype(np.float32)
+
+
+def with_principled(sc: Scene, seed: int = 21, **kw) -> Scene:
+    """``sc`` with seeded metallic and normal maps of its texture size."""
+    metallic, normal = principled_maps(np.random.default_rng(seed), sc.Ht, sc.Wt, **kw)
+    return sc.replace(metallic=metallic, normal=normal)
