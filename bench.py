@@ -111,6 +111,8 @@ def _args():
     ap.add_argument("--heightfield-steps", type=int, default=2, help="timed steps of the 200k-triangle workload (0 = skip)")
     ap.add_argument("--comp-steps", type=int, default=100, help="Adam steps of the full compensation run (0 = skip)")
     ap.add_argument("--fit-steps", type=int, default=10, help="timed steps of the Eq. 9 scene fit (0 = skip)")
+    ap.add_argument("--principled-steps", type=int, default=5,
+                    help="timed steps of the principled-material renders (0 = skip)")
     ap.add_argument("--denoise-steps", type=int, default=20,
                     help="timed calls of the Eq. 11 filter and denoised compensation steps (0 = skip)")
     return ap.parse_args()
@@ -707,6 +709,63 @@ def main():
                               "fwd_bwd = render + L2 loss + adjoint to Ip in one fused call",
                   **res}
 
+    # ------------------------------------------------------------ principled material (metallic + normal maps)
+    pbr_out = None
+    if args.principled_steps > 0:
+        # the forward workload and the compensation workload with seeded
+        # metallic and normal maps of their texture sizes
+        ps = scenes.with_principled(sc, seed=4000 + rank)
+        pm = torch.from_numpy(ps.metallic).to(dev)
+        pn = torch.from_numpy(ps.normal).to(dev)
+        pcs = scenes.with_principled(cs, seed=4100 + rank)
+        cpm = torch.from_numpy(pcs.metallic).to(dev)
+        cpn = torch.from_numpy(pcs.normal).to(dev)
+        gA, gR = torch.zeros_like(calb), torch.zeros_like(crough)
+        gM, gN = torch.zeros_like(cpm), torch.zeros_like(cpn)
+
+        def pbr_fwd():
+            ctx.render_principled(h, alb, rough, pm, pn, Ip, view, prm, sc.spp, sc.bounces, sc.seed, Ic=Ic, Ec=Ec)
+
+        def pbr_step():  # compensation step: render, L2 loss, adjoint to Ip, Adam
+            step_no[0] += 1
+            ctx.render_principled(hc, calb, crough, cpm, cpn, P, cview, cprm, cs.spp, cs.bounces,
+                                  cs.seed + step_no[0], Ic=cIc, Ec=cEc)
+            ctx.l2_loss(cIc, target, dIc, loss)
+            G.zero_()
+            ctx.render_backward_principled(hc, calb, crough, cpm, cpn, P, cview, cprm, cs.spp, cs.bounces,
+                                           cs.seed + step_no[0], cEc, cIc, dIc, dIp=G)
+            ctx.adam(P, G, M, V, step_no[0], lr=1e-2)
+
+        def pbr_all():  # one fitting pass: every material gradient (albedo, roughness, metallic, normal map)
+            ctx.render_principled(hc, calb, crough, cpm, cpn, P, cview, cprm, cs.spp, cs.bounces, cs.seed,
+                                  Ic=cIc, Ec=cEc)
+            ctx.render_backward_principled(hc, calb, crough, cpm, cpn, P, cview, cprm, cs.spp, cs.bounces, cs.seed,
+                                           cEc, cIc, dIc, dAlbedo=gA, dRough=gR, dMetallic=gM, dNormal=gN)
+
+        res = {}
+        for name, fn, n_samp in (("fwd", pbr_fwd, sc.n_samples), ("fwd_bwd", pbr_step, cs.n_samples),
+                                 ("fwd_bwd_material", pbr_all, cs.n_samples)):
+            for k in range(args.warmup):
+                flush(k)
+                fn()
+            torch.cuda.synchronize()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(args.principled_steps)]
+            barrier()
+            for k in range(args.principled_steps):
+                flush(k)
+                ev[k][0].record(stream)
+                fn()
+                ev[k][1].record(stream)
+            barrier()
+            ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev)) / args.principled_steps
+            res[name] = {"value": n_samp * ws / (ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": ms}
+        pbr_out = {"workload": f"principled material (metallic map + normal map): fwd = corner {sc.Hc}x{sc.Wc}, "
+                               f"{sc.spp} spp, {sc.bounces} bounces; fwd_bwd = compensation step at {cs.Hc}x{cs.Wc}, "
+                               f"{cs.spp} spp (render, L2 loss, replay adjoint to Ip, Adam); fwd_bwd_material = "
+                               "render + replay with albedo, roughness, metallic and normal-map gradients",
+                   **res}
+
     # ------------------------------------------------------------ serving vs one call per request
     serving_out = None
     if args.serve_requests > 0:
@@ -776,6 +835,7 @@ def main():
             "denoise": den_out,
             "fit": fit_out,
             "heightfield": hf_out,
+            "principled": pbr_out,
             "serving": serving_out,
             "cpu_baseline": cpu,
             "clocks": clk,

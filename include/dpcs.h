@@ -303,6 +303,55 @@ dpcs_status dpcs_render_backward(dpcs_ctx *ctx, dpcs_scene scene, const float *a
  * on the guide only: D is linear in I and the gradient does not flow into
  * the guide.
  */
+/*
+ * Principled material (Sec. 3.2: the BRDF maps m -- here base colour,
+ * roughness and metallic -- and the normal map Vn; Sec. 4.3 gives metallic
+ * in [0, 1] and the normal map in [0, 1]^3).  All maps are device arrays
+ * of one size Ht x Wt, HWC float32, sampled bilinearly with the albedo's
+ * texture coordinates.
+ *
+ *   f_j = (1 - m) rho_j / pi + ks D G F_j / (4 cos_i cos_o),
+ *   F_j = F0_j + (1 - F0_j) (1 - wo.h)^5,  F0_j = (1 - m) f0 + m rho_j
+ *
+ * The normal map decodes to v = 2 Vn - 1 in the triangle's tangent frame
+ * (T = dp/du orthogonal to the geometric normal N turned towards the ray,
+ * B = N x T); the shading normal v / |v| replaces N in the BRDF, its
+ * sampling and both cosines, while N keeps the ray offsets and light or
+ * continuations below the geometric surface are dropped.  metallic == NULL
+ * means 0 everywhere; normal == NULL means (0.5, 0.5, 1), no perturbation.
+ * The caller owns every map.
+ */
+typedef struct dpcs_material {
+    const float *albedo;    /* Ht x Wt x 3 */
+    const float *rough;     /* Ht x Wt */
+    const float *metallic;  /* Ht x Wt or NULL */
+    const float *normal;    /* Ht x Wt x 3 or NULL */
+    int32_t Ht, Wt;
+} dpcs_material;
+
+/*
+ * dpcs_render_principled: dpcs_render with the principled material (same
+ * view, parameters, sampling, determinism and errors; the fused, kept-record
+ * and batched paths are not available for it).
+ *
+ * dpcs_render_backward_principled: its path-replay adjoint, as
+ * dpcs_render_backward, adding (+=) also dLoss/dmetallic (Ht x Wt) and
+ * dLoss/dnormal (Ht x Wt x 3); each output may be NULL, and asking for the
+ * gradient of a map the material does not have is DPCS_ERR_INVALID_ARG.
+ * Sampled directions and pdfs are held fixed (detached sampling), so the
+ * normal-map gradient, like roughness, is exact per seed only for one
+ * bounce and unbiased beyond.
+ */
+dpcs_status dpcs_render_principled(dpcs_ctx *ctx, dpcs_scene scene, const dpcs_material *mat, const float *Ip,
+                                   const dpcs_view *view, const dpcs_params *params, int32_t spp, int32_t bounces,
+                                   uint64_t seed, float *Ic, float *Ec, void *stream);
+dpcs_status dpcs_render_backward_principled(dpcs_ctx *ctx, dpcs_scene scene, const dpcs_material *mat,
+                                            const float *Ip, const dpcs_view *view, const dpcs_params *params,
+                                            int32_t spp, int32_t bounces, uint64_t seed, const float *Ec,
+                                            const float *Ic, const float *dIc, float *dIp, float *dAlbedo,
+                                            float *dRough, float *dMetallic, float *dNormal, float *dParams,
+                                            void *stream);
+
 typedef struct dpcs_denoise_params {
     int32_t radius;      /* window half-width r, 0..8 (0 = identity) */
     float sigma_s;       /* spatial width in pixels, > 0 */

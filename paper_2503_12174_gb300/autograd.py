@@ -2,14 +2,17 @@
 its path-replay adjoint as the backward, so that projector compensation
 (Eq. 13) and scene fitting (Eq. 9) can be written with torch optimisers.
 
-    Ic = render(ctx, scene, albedo, rough, Ip, view, params, spp, bounces, seed, pvec=None)
+    Ic = render(ctx, scene, albedo, rough, Ip, view, params, spp, bounces, seed, pvec=None,
+                metallic=None, normal=None)
 
 ``albedo`` (Ht x Wt x 3), ``rough`` (Ht x Wt) and ``Ip`` (Hp x Wp x 3) are
 device tensors; ``pvec`` (11 floats: gamma_p(3), Gp, gamma_c(3), Gc, w(3)),
 when given, replaces the response parameters of ``params`` and receives their
-gradient.  The backward asks the library only for the gradients autograd
-needs: without albedo or roughness gradients the replay skips the texture
-scatters.  Both passes run in the library's kernels; each call renders with
+gradient.  ``metallic`` (Ht x Wt) and ``normal`` (Ht x Wt x 3), when either
+is given, select the principled material of Sec. 3.2
+(dpcs_render_principled) and receive their gradients too.  The backward
+asks the library only for the gradients autograd needs: without albedo or
+roughness gradients the replay skips the texture scatters.  Both passes run in the library's kernels; each call renders with
 Philox key ``seed``, and the backward re-traces the same paths.
 """
 from __future__ import annotations
@@ -38,27 +41,39 @@ def _function():
 
     class DPCSRender(torch.autograd.Function):
         @staticmethod
-        def forward(fctx, albedo, rough, Ip, pvec, ctx, scene, view, params, spp, bounces, seed):
+        def forward(fctx, albedo, rough, Ip, pvec, metallic, normal, ctx, scene, view, params, spp, bounces, seed):
             p = params if pvec is None else with_vector(params, pvec.detach().cpu().tolist())
             Ec = torch.empty((view.Hc, view.Wc, 3), dtype=torch.float32, device=ctx.device)
-            Ic, _ = ctx.render(scene, albedo, rough, Ip, view, p, spp, bounces, seed, Ec=Ec)
-            fctx.save_for_backward(albedo, rough, Ip, Ec, Ic)
-            fctx.meta = (ctx, scene, view, p, spp, bounces, seed, pvec is not None)
+            principled = metallic is not None or normal is not None
+            if principled:
+                Ic, _ = ctx.render_principled(scene, albedo, rough, metallic, normal, Ip, view, p, spp, bounces, seed,
+                                              Ec=Ec)
+            else:
+                Ic, _ = ctx.render(scene, albedo, rough, Ip, view, p, spp, bounces, seed, Ec=Ec)
+            fctx.save_for_backward(albedo, rough, Ip, Ec, Ic, metallic, normal)
+            fctx.meta = (ctx, scene, view, p, spp, bounces, seed, pvec is not None, principled)
             return Ic
 
         @staticmethod
         def backward(fctx, dIc):
-            albedo, rough, Ip, Ec, Ic = fctx.saved_tensors
-            ctx, scene, view, p, spp, bounces, seed, has_pvec = fctx.meta
+            albedo, rough, Ip, Ec, Ic, metallic, normal = fctx.saved_tensors
+            ctx, scene, view, p, spp, bounces, seed, has_pvec, principled = fctx.meta
             need = fctx.needs_input_grad
             dA = torch.zeros_like(albedo) if need[0] else None
             dR = torch.zeros_like(rough) if need[1] else None
             dIp = torch.zeros_like(Ip) if need[2] else None
             dP = torch.zeros(11, dtype=torch.float32, device=ctx.device) if has_pvec and need[3] else None
-            if any(x is not None for x in (dA, dR, dIp, dP)):
-                ctx.render_backward(scene, albedo, rough, Ip, view, p, spp, bounces, seed, Ec, Ic,
-                                    dIc.to(torch.float32).contiguous(), dIp=dIp, dAlbedo=dA, dRough=dR, dParams=dP)
-            return dA, dR, dIp, dP, None, None, None, None, None, None, None
+            dM = torch.zeros_like(metallic) if metallic is not None and need[4] else None
+            dN = torch.zeros_like(normal) if normal is not None and need[5] else None
+            g = dIc.to(torch.float32).contiguous()
+            if principled and any(x is not None for x in (dA, dR, dIp, dP, dM, dN)):
+                ctx.render_backward_principled(scene, albedo, rough, metallic, normal, Ip, view, p, spp, bounces, seed,
+                                               Ec, Ic, g, dIp=dIp, dAlbedo=dA, dRough=dR, dMetallic=dM, dNormal=dN,
+                                               dParams=dP)
+            elif any(x is not None for x in (dA, dR, dIp, dP)):
+                ctx.render_backward(scene, albedo, rough, Ip, view, p, spp, bounces, seed, Ec, Ic, g, dIp=dIp,
+                                    dAlbedo=dA, dRough=dR, dParams=dP)
+            return dA, dR, dIp, dP, dM, dN, None, None, None, None, None, None, None
 
     return DPCSRender
 
@@ -67,9 +82,10 @@ _DPCSRender = None
 
 
 def render(ctx: dpcs.Context, scene: int, albedo, rough, Ip, view: dpcs.DpcsView, params: dpcs.DpcsParams,
-           spp: int, bounces: int, seed: int, pvec=None):
+           spp: int, bounces: int, seed: int, pvec=None, metallic=None, normal=None):
     """Differentiable Ic = R(Ip, theta); see the module docstring."""
     global _DPCSRender
     if _DPCSRender is None:
         _DPCSRender = _function()
-    return _DPCSRender.apply(albedo, rough, Ip, pvec, ctx, scene, view, params, int(spp), int(bounces), int(seed))
+    return _DPCSRender.apply(albedo, rough, Ip, pvec, metallic, normal, ctx, scene, view, params, int(spp),
+                             int(bounces), int(seed))

@@ -50,6 +50,7 @@ struct dpcs_ctx {
     uint64_t next_scene = 1;
     // scratch
     Buf ep4, tex4, gE, dEp4, dtex4, acc, partial, build, upload, pix;  // pix: per-pixel dIc and Ec of the unfused loss path
+    Buf mat4, dmat4;  // principled material: (metallic, normal map) per texel and its gradient accumulators
     Buf kept;  // path records of the last dpcs_render_keep: 16-byte chunks (structure of arrays), then per-sample vertex counts
     struct {
         bool valid = false;
@@ -288,7 +289,7 @@ dpcs_status dpcs_destroy(dpcs_ctx *c) {
         cudaFree(s.order);
     }
     Buf *bufs[] = {&c->ep4, &c->tex4, &c->gE, &c->dEp4, &c->dtex4, &c->acc, &c->partial, &c->build, &c->upload, &c->pix,
-                   &c->kept};
+                   &c->kept, &c->mat4, &c->dmat4};
     for (Buf *b : bufs)
         if (b->p) cudaFree(b->p);
     cudaFree(c->status);
@@ -603,6 +604,88 @@ dpcs_status dpcs_render_backward(dpcs_ctx *c, dpcs_scene scene, const float *alb
     if (want_tex) nl += launch_tex_backward((const float4 *)c->dtex4.p, nt, dAlbedo, dRough, st);
     if (dParams) nl += launch_finalize_params(acc, dParams, st);
     return check_launch(c, nl, "render_backward");
+}
+
+dpcs_status dpcs_render_principled(dpcs_ctx *c, dpcs_scene scene, const dpcs_material *mat, const float *Ip,
+                                   const dpcs_view *view, const dpcs_params *params, int32_t spp, int32_t bounces,
+                                   uint64_t seed, float *Ic, float *Ec, void *stream) {
+    Range range("dpcs_render_principled");
+    if (!c) return DPCS_ERR_INVALID_ARG;
+    if (!mat) return fail(c, DPCS_ERR_INVALID_ARG, "null material");
+    RenderArgs a;
+    Scene *sc = nullptr;
+    dpcs_status s = prepare(c, scene, mat->albedo, mat->rough, mat->Ht, mat->Wt, Ip, view, params, spp, bounces, seed,
+                            a, &sc);
+    if (s) return s;
+    if (!Ic) return fail(c, DPCS_ERR_INVALID_ARG, "null Ic");
+    if ((s = set_device(c))) return s;
+    const int64_t np = (int64_t)view->Hp * view->Wp, nt = (int64_t)mat->Ht * mat->Wt;
+    if ((s = ensure(c, c->ep4, (size_t)np * 16, "Ep scratch")) ||
+        (s = ensure(c, c->tex4, (size_t)nt * 16, "texture scratch")) ||
+        (s = ensure(c, c->mat4, (size_t)nt * 16, "material scratch")))
+        return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    a.Ep = (const float4 *)c->ep4.p;
+    a.tex = (const float4 *)c->tex4.p;
+    a.Ic = Ic;
+    a.Ec = Ec;
+    int nl = launch_prf(Ip, np, params->gamma_p, params->gain_p, (float4 *)c->ep4.p, st);
+    nl += launch_pack_tex(mat->albedo, mat->rough, nt, (float4 *)c->tex4.p, st);
+    nl += launch_pack_mat(mat->metallic, mat->normal, nt, (float4 *)c->mat4.p, st);
+    nl += launch_render_pbr(a, (const float4 *)c->mat4.p, st);
+    return check_launch(c, nl, "render_principled");
+}
+
+dpcs_status dpcs_render_backward_principled(dpcs_ctx *c, dpcs_scene scene, const dpcs_material *mat, const float *Ip,
+                                            const dpcs_view *view, const dpcs_params *params, int32_t spp,
+                                            int32_t bounces, uint64_t seed, const float *Ec, const float *Ic,
+                                            const float *dIc, float *dIp, float *dAlbedo, float *dRough,
+                                            float *dMetallic, float *dNormal, float *dParams, void *stream) {
+    Range range("dpcs_render_backward_principled");
+    if (!c) return DPCS_ERR_INVALID_ARG;
+    if (!mat) return fail(c, DPCS_ERR_INVALID_ARG, "null material");
+    RenderArgs a;
+    Scene *sc = nullptr;
+    dpcs_status s = prepare(c, scene, mat->albedo, mat->rough, mat->Ht, mat->Wt, Ip, view, params, spp, bounces, seed,
+                            a, &sc);
+    if (s) return s;
+    if (!Ec || !Ic || !dIc) return fail(c, DPCS_ERR_INVALID_ARG, "null Ec, Ic or dIc");
+    if (dMetallic && !mat->metallic) return fail(c, DPCS_ERR_INVALID_ARG, "dMetallic given without a metallic map");
+    if (dNormal && !mat->normal) return fail(c, DPCS_ERR_INVALID_ARG, "dNormal given without a normal map");
+    if ((s = set_device(c))) return s;
+    const int64_t np = (int64_t)view->Hp * view->Wp, nt = (int64_t)mat->Ht * mat->Wt;
+    const int64_t npix = (int64_t)view->Hc * view->Wc;
+    if ((s = ensure(c, c->ep4, (size_t)np * 16, "Ep scratch")) ||
+        (s = ensure(c, c->tex4, (size_t)nt * 16, "texture scratch")) ||
+        (s = ensure(c, c->mat4, (size_t)nt * 16, "material scratch")) ||
+        (s = ensure(c, c->gE, (size_t)npix * 12, "dEc scratch")) ||
+        (s = ensure(c, c->dEp4, (size_t)np * 16, "dEp scratch")) ||
+        (s = ensure(c, c->acc, 16 * sizeof(double), "parameter accumulators")))
+        return s;
+    const bool want_tex = dAlbedo || dRough, want_mat = dMetallic || dNormal;
+    if (want_tex && (s = ensure(c, c->dtex4, (size_t)nt * 16, "dtex scratch"))) return s;
+    if (want_mat && (s = ensure(c, c->dmat4, (size_t)nt * 16, "dmat scratch"))) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    double *acc = (double *)c->acc.p;
+    cudaMemsetAsync(acc, 0, 16 * sizeof(double), st);
+    cudaMemsetAsync(c->dEp4.p, 0, (size_t)np * 16, st);
+    if (want_tex) cudaMemsetAsync(c->dtex4.p, 0, (size_t)nt * 16, st);
+    if (want_mat) cudaMemsetAsync(c->dmat4.p, 0, (size_t)nt * 16, st);
+    int nl = launch_prf(Ip, np, params->gamma_p, params->gain_p, (float4 *)c->ep4.p, st);
+    nl += launch_pack_tex(mat->albedo, mat->rough, nt, (float4 *)c->tex4.p, st);
+    nl += launch_pack_mat(mat->metallic, mat->normal, nt, (float4 *)c->mat4.p, st);
+    nl += launch_crf_backward(dIc, Ec, Ic, npix, params->gamma_c, params->gain_c, params->wb, (float *)c->gE.p, acc, st);
+    a.Ep = (const float4 *)c->ep4.p;
+    a.tex = (const float4 *)c->tex4.p;
+    a.gE = (const float *)c->gE.p;
+    a.dEp = (float4 *)c->dEp4.p;
+    a.dtex = want_tex ? (float4 *)c->dtex4.p : nullptr;
+    nl += launch_replay_pbr(a, (const float4 *)c->mat4.p, want_mat ? (float4 *)c->dmat4.p : nullptr, st);
+    nl += launch_prf_backward(Ip, (const float4 *)c->dEp4.p, np, params->gamma_p, params->gain_p, dIp, acc, st);
+    if (want_tex) nl += launch_tex_backward((const float4 *)c->dtex4.p, nt, dAlbedo, dRough, st);
+    if (want_mat) nl += launch_mat_backward((const float4 *)c->dmat4.p, nt, dMetallic, dNormal, st);
+    if (dParams) nl += launch_finalize_params(acc, dParams, st);
+    return check_launch(c, nl, "render_backward_principled");
 }
 
 dpcs_status dpcs_render_keep(dpcs_ctx *c, dpcs_scene scene, const float *albedo, const float *rough, int32_t Ht,

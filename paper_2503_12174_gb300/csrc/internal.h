@@ -111,6 +111,11 @@ int launch_crf_backward(const float *dIc, const float *Ec, const float *Ic, int6
 int launch_replay(const RenderArgs &a, cudaStream_t st);
 int launch_render_grad(const RenderArgs &a, const LossArgs &l, cudaStream_t st);
 int launch_pixel_loss(const float *Ic, int64_t n, const LossArgs &l, float *dIc, cudaStream_t st);
+// principled material (principled.cu)
+int launch_pack_mat(const float *metallic, const float *normal, int64_t ntex, float4 *mat, cudaStream_t st);
+int launch_render_pbr(const RenderArgs &a, const float4 *mat, cudaStream_t st);
+int launch_replay_pbr(const RenderArgs &a, const float4 *mat, float4 *dmat, cudaStream_t st);
+int launch_mat_backward(const float4 *dmat, int64_t ntex, float *dMetallic, float *dNormal, cudaStream_t st);
 int launch_render_keep(const RenderArgs &a, void *chunks, uint8_t *nvs, cudaStream_t st);
 int launch_sweep_kept(const RenderArgs &a, const void *chunks, const uint8_t *nvs, cudaStream_t st);
 constexpr int kRecWordsHost = 24;  // 32-bit words of one kept vertex record (VRec)

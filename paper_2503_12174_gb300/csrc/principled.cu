@@ -1,0 +1,552 @@
+// principled.cu -- the principled material of Sec. 3.2 on the GPU: the
+// scene parameters m (a BRDF with a metallic map) and Vn (a normal map) on
+// top of the Lambert + GGX path tracer, forward and path-replay adjoint.
+//
+// Material (Burley 2012's metallic workflow; the normal map in Mitsuba's
+// convention, the paper's stated reference):
+//   f_j = (1 - m) rho_j / pi + S F_j,  S = ks D G / (4 ci co),
+//   F_j = F0_j + (1 - F0_j) (1 - wo.h)^5,  F0_j = (1 - m) f0 + m rho_j;
+//   v = 2 Vn - 1 in the triangle's tangent frame (T = dp/du made orthogonal
+//   to the geometric normal N, B = N x T), shading normal ns = v / |v|.
+// ns replaces N in the BRDF, its sampling and pdf, cos_s of the NEE and
+// cos_i of the continuation; N keeps the ray offsets, and light or
+// continuations below the geometric surface are dropped.  metallic 0 and
+// Vn = (0.5, 0.5, 1) give the plain material.
+//
+// Kernels: k_pack_mat interleaves (metallic, Vn) into one float4 per texel;
+// k_render_pbr is k_render's loop (same thread mapping, same sample rounds,
+// same xor-shuffle pixel sum) with this material; k_replay_pbr re-traces the
+// paths, records each vertex and runs the reverse sweep with the material's
+// derivatives (detached sampling: sampled directions and pdfs fixed);
+// k_mat_backward adds the metallic and normal-map gradients to the caller's
+// buffers.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "device.cuh"
+#include "internal.h"
+
+namespace dpcs {
+
+namespace {
+
+constexpr int kPBlock = 128;
+#ifndef DPCS_YIELD_MIN
+#define DPCS_YIELD_MIN 0  // as in render.cu: traversal does not yield
+#endif
+#ifndef DPCS_PBR_MINB
+#define DPCS_PBR_MINB 8  // resident blocks per SM asked of ptxas (64 registers)
+#endif
+
+__device__ __forceinline__ void atomic_add4p(float4 *p, float4 v) { atomicAdd(p, v); }
+
+// GGX lobe of the principled BRDF at shading normal n, with its partial
+// derivatives in roughness and in n (wo, wi and h held fixed):
+//   d ln S / dn = (d ln D / d ch) h + (d ln G1(co) / d co - 1/co) wo
+//               + (d ln G1(ci) / d ci - 1/ci) wi.
+struct PLobe {
+    float on;   // 1 when wo and wi are both above the shading hemisphere, else 0 (the whole BRDF is 0)
+    float S;    // ks D G / (4 ci co)
+    float dSr;  // dS / d roughness
+    float s5;   // (1 - wo.h)^5 of Schlick's Fresnel
+    f3 dSn;     // dS / dn
+};
+__device__ __forceinline__ void plobe(f3 n, f3 wo, f3 wi, float r, float ks, PLobe &L) {
+    L.on = L.S = L.dSr = L.s5 = 0.0f;
+    L.dSn = mk3(0.f, 0.f, 0.f);
+    const float co = dot(n, wo), ci = dot(n, wi);
+    if (co <= 0.0f || ci <= 0.0f) return;
+    L.on = 1.0f;
+    if (ks <= 0.0f) return;
+    float dadr;
+    const float a = alpha_of(r, dadr);
+    const f3 h = normalize(wo + wi);
+    const float ch = dot(n, h), a2 = a * a;
+    const float t = sin2(n, h) + a2 * ch * ch;
+    const float D = a2 / (DPCS_PI_F * t * t);
+    const float si = sqrtf(a2 + (1.0f - a2) * ci * ci), so = sqrtf(a2 + (1.0f - a2) * co * co);
+    const float G = (2.0f * ci / (ci + si)) * (2.0f * co / (co + so));
+    const float S = ks * D * G / (4.0f * ci * co);
+    const float dlnD = 2.0f / a - 4.0f * a * ch * ch / t;
+    const float dlnG = -(a * (1.0f - ci * ci) / si) / (ci + si) - (a * (1.0f - co * co) / so) / (co + so);
+    L.S = S;
+    L.dSr = S * (dlnD + dlnG) * dadr;
+    const float kh = -4.0f * ch * (a2 - 1.0f) / t;
+    const float ko = -(1.0f + (1.0f - a2) * co / so) / (co + so);
+    const float ki = -(1.0f + (1.0f - a2) * ci / si) / (ci + si);
+    L.dSn = (h * kh + wo * ko + wi * ki) * S;
+    const float m = fmaxf(0.0f, 1.0f - dot(wo, h));
+    const float m2 = m * m;
+    L.s5 = m2 * m2 * m;
+}
+
+// Schlick F_j for F0_j = (1 - m) f0 + m rho_j
+__device__ __forceinline__ float pfresnel(float rho, float m, float f0, float s5) {
+    const float F0 = (1.0f - m) * f0 + m * rho;
+    return F0 + (1.0f - F0) * s5;
+}
+
+// f per channel from a lobe
+__device__ __forceinline__ f3 pbrdf(f3 rho, float m, float f0, const PLobe &L) {
+    const float kd = L.on * (1.0f - m) * DPCS_INV_PI_F;
+    return mk3(kd * rho.x + L.S * pfresnel(rho.x, m, f0, L.s5), kd * rho.y + L.S * pfresnel(rho.y, m, f0, L.s5),
+               kd * rho.z + L.S * pfresnel(rho.z, m, f0, L.s5));
+}
+
+// surface interaction with the principled maps
+struct PSurf {
+    f3 x, n, ns, wo, rho;  // n: geometric normal turned towards the incoming ray
+    float rough, m;
+    f3 T, B;               // tangent frame of the normal map
+    float inv_ulen;        // 1 / |v| of the decoded normal-map vector (0: unperturbed)
+    Bilin tb;
+};
+__device__ __forceinline__ PSurf psurface_at(const RenderArgs &a, const float4 *__restrict__ mat, const Hit &h, f3 d) {
+    PSurf S;
+    const float4 A = __ldg(a.tris + 3 * h.pos + 0);
+    const float4 E1 = __ldg(a.tris + 3 * h.pos + 1);
+    const float4 E2 = __ldg(a.tris + 3 * h.pos + 2);
+    const f3 e1 = xyz(E1), e2 = xyz(E2);
+    S.x = xyz(A) + e1 * h.u + e2 * h.v;
+    S.n = normalize(cross(e1, e2));
+    if (dot(S.n, d) > 0.0f) S.n = S.n * -1.0f;
+    const float2 t0 = __ldg(a.tuv + 3 * h.pos + 0), t1 = __ldg(a.tuv + 3 * h.pos + 1),
+                 t2 = __ldg(a.tuv + 3 * h.pos + 2);
+    const float w0 = 1.0f - h.u - h.v;
+    const float su = w0 * t0.x + h.u * t1.x + h.v * t2.x;
+    const float sv = w0 * t0.y + h.u * t1.y + h.v * t2.y;
+    S.tb = bilin_setup(su * (float)a.Wt, sv * (float)a.Ht, a.Wt, a.Ht);
+    const float4 tex = bilin_fetch(a.tex, S.tb, a.Wt, a.Ht);
+    const float4 mt = bilin_fetch(mat, S.tb, a.Wt, a.Ht);
+    S.rho = mk3(tex.x, tex.y, tex.z);
+    S.rough = tex.w;
+    S.m = mt.x;
+    S.wo = d * -1.0f;
+    // tangent: dp/du from e1 = dp/du du1 + dp/dv dv1 and e2 likewise
+    const float du1 = t1.x - t0.x, dv1 = t1.y - t0.y, du2 = t2.x - t0.x, dv2 = t2.y - t0.y;
+    const float det = du1 * dv2 - du2 * dv1;
+    bool ok = false;
+    if (det != 0.0f) {
+        const f3 dpdu = (e1 * dv2 - e2 * dv1) * (1.0f / det);
+        const f3 t = dpdu - S.n * dot(S.n, dpdu);
+        const float l2 = dot(t, t);
+        if (l2 > 1e-12f * dot(dpdu, dpdu)) {
+            S.T = t * rsqrtf(l2);
+            ok = true;
+        }
+    }
+    if (!ok) {
+        f3 b;
+        onb(S.n, S.T, b);
+    }
+    S.B = cross(S.n, S.T);
+    const f3 u = S.T * (2.0f * mt.y - 1.0f) + S.B * (2.0f * mt.z - 1.0f) + S.n * (2.0f * mt.w - 1.0f);
+    const float ul2 = dot(u, u);
+    if (ul2 > 1e-24f) {
+        S.inv_ulen = rsqrtf(ul2);
+        S.ns = u * S.inv_ulen;
+    } else {
+        S.inv_ulen = 0.0f;
+        S.ns = S.n;
+    }
+    return S;
+}
+
+// next-event estimation to the projector with the principled material
+struct PNee {
+    f3 so, sdir;
+    float smax;
+    Bilin pb;
+    float4 ep;
+    float G;
+    PLobe L;
+    f3 fp, wp_cs;
+};
+__device__ __forceinline__ bool pnee_prepare(const RenderArgs &a, const PSurf &S, PNee &N) {
+    const f3 cp = mk3(a.cp[0], a.cp[1], a.cp[2]);
+    const f3 X = mat3v(a.Rp, S.x) + mk3(a.tp[0], a.tp[1], a.tp[2]);
+    const f3 q = mat3v(a.Kp, X);
+    if (!(q.z > 0.0f && X.z > 0.0f)) return false;
+    const float up = q.x / q.z, vp = q.y / q.z;
+    if (!(up >= 0.0f && up < (float)a.Wp && vp >= 0.0f && vp < (float)a.Hp)) return false;
+    const f3 v = cp - S.x;
+    const float r2 = dot(v, v), dist = sqrtf(r2);
+    const f3 wp = v * (1.0f / dist);
+    const float cs = dot(S.ns, wp);
+    if (!(cs > 0.0f && dot(S.n, wp) > 0.0f)) return false;
+    const float cpz = X.z / sqrtf(dot(X, X));
+    N.so = S.x + S.n * kRayEps;
+    const f3 sv = cp - N.so;
+    const float sd = sqrtf(dot(sv, sv));
+    N.sdir = sv * (1.0f / sd);
+    N.smax = sd - kRayEps;
+    N.pb = bilin_setup(up, vp, a.Wp, a.Hp);
+    N.ep = bilin_fetch(a.Ep, N.pb, a.Wp, a.Hp);
+    N.G = a.k_proj * cpz * cs / r2;
+    plobe(S.ns, S.wo, wp, S.rough, a.ks, N.L);
+    N.fp = pbrdf(S.rho, S.m, a.f0, N.L);
+    N.wp_cs = wp * (1.0f / cs);
+    return true;
+}
+
+// continuation: BRDF sampling around ns, throughput, Russian roulette
+struct PCont {
+    f3 wi, w, wi_ci;
+    float cw;
+    PLobe L;
+};
+__device__ __forceinline__ bool pcontinue_prepare(const RenderArgs &a, uint32_t pix, uint32_t s, int b,
+                                                  const PSurf &S, PCont &C) {
+    float u[4];
+    rand4(a.key0, a.key1, pix, s, (uint32_t)b, u);
+    if (!bsdf_sample(S.ns, S.wo, S.rough, a.ks, u[0], u[1], u[2], C.wi)) return false;
+    if (!(dot(S.n, C.wi) > 0.0f)) return false;  // below the geometric surface
+    const float pdf = bsdf_pdf(S.ns, S.wo, C.wi, S.rough, a.ks);
+    if (!(pdf > 0.0f)) return false;
+    float qrr = 1.0f;
+    if (a.rr_start > 0 && b >= a.rr_start) {
+        if (u[3] >= a.rr_q) return false;
+        qrr = a.rr_q;
+    }
+    plobe(S.ns, S.wo, C.wi, S.rough, a.ks, C.L);
+    const float ci = dot(S.ns, C.wi);
+    C.cw = ci / (pdf * qrr);
+    C.wi_ci = C.wi * (1.0f / ci);
+    C.w = pbrdf(S.rho, S.m, a.f0, C.L) * C.cw;
+    return true;
+}
+
+// what the principled sweep needs of one vertex (52 words)
+struct PRec {
+    Bilin tb, pb;
+    float beta[3], Ep[3], G;
+    float rho[3], m;
+    unsigned unc;  // bits 0-2: channel j not clipped; bit 3 / 4: the NEE / continuation BRDF is on
+    float cw;
+    float Sp, dSrp, s5p;
+    f3 dSnp, wp_cs;
+    float Si, dSri, s5i;
+    f3 dSni, wi_ci;
+    f3 T, B, N, ns;
+    float inv_ulen;
+};
+
+// reverse sweep of one recorded path (the replay's recursion A_c = [lit]
+// f(wp) Ep G + f(wi) cw A_{c+1}) with the principled derivatives:
+//   d/d rho_j: (1 - m)/pi + S (1 - s5) m            (per lobe)
+//   d/d m:     -rho_j/pi + S (1 - s5) (rho_j - f0)
+//   d/d r:     dS/dr F_j
+//   d/d ns:    ln_e (F_j dS/dn + f_j wp / cs) + cont (F_j dS/dn + f_j wi / ci),
+// then ns = u / |u|, u = v_x T + v_y B + v_z N, v = 2 Vn - 1.
+__device__ __forceinline__ void psweep(const RenderArgs &a, float4 *__restrict__ dmat, const PRec *rec, int nv,
+                                       const float gb_in[3]) {
+    float A[3] = {0.f, 0.f, 0.f};
+    for (int c = nv - 1; c >= 0; --c) {
+        const PRec &R = rec[c];
+        float ga[3], dEp[3];
+        float dr = 0.0f, dm = 0.0f;
+        f3 gn = mk3(0.f, 0.f, 0.f);
+        const float kdp = (R.unc & 8u) ? (1.0f - R.m) * DPCS_INV_PI_F : 0.0f;
+        const float kdi = (R.unc & 16u) ? (1.0f - R.m) * DPCS_INV_PI_F : 0.0f;
+        const float onp = (R.unc & 8u) ? 1.0f : 0.0f, oni = (R.unc & 16u) ? 1.0f : 0.0f;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const float An = A[j];
+            const float gb = gb_in[j] * R.beta[j];
+            const bool lit = R.G > 0.0f && ((R.unc >> j) & 1u);
+            const float ln_e = lit ? R.Ep[j] * R.G : 0.0f;
+            const float cont = R.cw * An;
+            const float Fp = pfresnel(R.rho[j], R.m, a.f0, R.s5p), Fi = pfresnel(R.rho[j], R.m, a.f0, R.s5i);
+            const float fp = kdp * R.rho[j] + R.Sp * Fp, fi = kdi * R.rho[j] + R.Si * Fi;
+            dEp[j] = lit ? gb * fp * R.G : 0.0f;
+            ga[j] = gb * (ln_e * (kdp + R.Sp * (1.0f - R.s5p) * R.m) + cont * (kdi + R.Si * (1.0f - R.s5i) * R.m));
+            dr += gb * (R.dSrp * Fp * ln_e + R.dSri * Fi * cont);
+            dm += gb * (ln_e * (-onp * R.rho[j] * DPCS_INV_PI_F + R.Sp * (1.0f - R.s5p) * (R.rho[j] - a.f0)) +
+                        cont * (-oni * R.rho[j] * DPCS_INV_PI_F + R.Si * (1.0f - R.s5i) * (R.rho[j] - a.f0)));
+            gn = gn + (R.dSnp * Fp + R.wp_cs * fp) * (gb * ln_e) + (R.dSni * Fi + R.wi_ci * fi) * (gb * cont);
+            A[j] = fp * ln_e + fi * cont;
+        }
+        int idx[4];
+        float w[4];
+        bilin_taps(R.tb, a.Wt, a.Ht, idx, w);
+        if (a.dtex) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                atomic_add4p(a.dtex + idx[k], make_float4(ga[0] * w[k], ga[1] * w[k], ga[2] * w[k], dr * w[k]));
+        }
+        if (dmat) {
+            f3 gv = mk3(0.f, 0.f, 0.f);
+            if (R.inv_ulen > 0.0f) {
+                const f3 gu = (gn - R.ns * dot(R.ns, gn)) * R.inv_ulen;
+                gv = mk3(2.0f * dot(R.T, gu), 2.0f * dot(R.B, gu), 2.0f * dot(R.N, gu));
+            }
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                atomic_add4p(dmat + idx[k], make_float4(dm * w[k], gv.x * w[k], gv.y * w[k], gv.z * w[k]));
+        }
+        if (R.G > 0.0f && (dEp[0] != 0.0f || dEp[1] != 0.0f || dEp[2] != 0.0f)) {
+            bilin_taps(R.pb, a.Wp, a.Hp, idx, w);
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                atomic_add4p(a.dEp + idx[k], make_float4(dEp[0] * w[k], dEp[1] * w[k], dEp[2] * w[k], 0.0f));
+        }
+    }
+}
+
+__device__ __forceinline__ void prec_vertex(PRec &R, const PSurf &S, f3 beta) {
+    R.tb = S.tb;
+    R.pb.x0 = R.pb.y0 = 0;
+    R.pb.fx = R.pb.fy = 0.0f;
+    R.beta[0] = beta.x; R.beta[1] = beta.y; R.beta[2] = beta.z;
+    R.Ep[0] = R.Ep[1] = R.Ep[2] = 0.0f;
+    R.G = 0.0f;
+    R.rho[0] = S.rho.x; R.rho[1] = S.rho.y; R.rho[2] = S.rho.z;
+    R.m = S.m;
+    R.unc = 0u;
+    R.cw = 0.0f;
+    R.Sp = R.dSrp = R.s5p = R.Si = R.dSri = R.s5i = 0.0f;
+    R.dSnp = R.wp_cs = R.dSni = R.wi_ci = mk3(0.f, 0.f, 0.f);
+    R.T = S.T;
+    R.B = S.B;
+    R.N = S.n;
+    R.ns = S.ns;
+    R.inv_ulen = S.inv_ulen;
+}
+
+// One warp-synchronous pass over a lane's samples, as k_render and k_replay
+// run them: each iteration traces one ray (extension or shadow) per lane,
+// and the warp starts its next samples together.  kReplay = false: sum the
+// lit contributions and write Ec / Ic; true: record the vertices and sweep.
+template <bool kReplay>
+__device__ __forceinline__ void pbr_lanes(const RenderArgs &a, const float4 *__restrict__ mat,
+                                          float4 *__restrict__ dmat, int64_t pix, int sl, bool valid) {
+    const int L = 1 << a.log2L;
+    Cnt cnt;
+    f3 sum = mk3(0.f, 0.f, 0.f);
+    float gb_in[3] = {0.f, 0.f, 0.f};
+    bool any = true;
+    if (kReplay) {
+        const float inv = 1.0f / (float)a.spp;
+        if (valid) {
+            gb_in[0] = a.gE[3 * pix] * inv;
+            gb_in[1] = a.gE[3 * pix + 1] * inv;
+            gb_in[2] = a.gE[3 * pix + 2] * inv;
+        }
+        any = gb_in[0] != 0.0f || gb_in[1] != 0.0f || gb_in[2] != 0.0f;
+    }
+    int s = (valid && any) ? sl : a.spp;
+    int b = 1, nv = 0;
+    bool shadow = false, has_ext = false, pending = false;
+    f3 beta = mk3(0.f, 0.f, 0.f), c = beta, ed = beta;
+    Ray ray;
+    ray.o = ray.d = ray.inv = beta;
+    float tmax = INFINITY;
+    Trav st;
+    int stack[kStack];
+    PRec rec[kReplay ? DPCS_MAX_BOUNCES : 1];
+    if (s < a.spp && a.bounces > 0) {
+        f3 o, d;
+        camera_ray(a, (uint32_t)pix, (uint32_t)s, o, d);
+        ray = make_ray(o, d);
+        beta = mk3(1.f, 1.f, 1.f);
+        cnt.add(kCntPath);
+    } else {
+        s = a.spp;
+    }
+    const int64_t max_iter = ((int64_t)(a.spp / L + 1) * (2 * a.bounces + 1)) * (2 * (int64_t)a.T + 18);
+    int64_t iter = 0;
+    while (s < a.spp) {
+        while (true) {
+            if (++iter > max_iter) {
+                atomicOr(a.status, kStatusTraversalLimit);
+                s = a.spp;
+                nv = 0;
+                break;
+            }
+            if (!pending) {
+                cnt.add(shadow ? kCntShadow : kCntRay);
+                trav_begin(st, a.root, shadow ? tmax : INFINITY, shadow);
+                pending = true;
+            }
+            // the min_active argument in the form render.cu's kernels pass it:
+            // there a literal 0 (the same value) cost a 3.2x slowdown
+            const int alive = DPCS_YIELD_MIN > 0 ? __popc(__activemask()) : 0;
+            if (!trav_resume(a.nodes, a.tris, a.root, a.T, ray, st, stack, a.status, cnt, min(DPCS_YIELD_MIN, alive),
+                             a.visit_cap))
+                continue;
+            pending = false;
+            const bool hit = st.h.pos >= 0;
+            bool end = false;
+            if (shadow) {
+                if (hit) {
+                    if (kReplay) rec[nv - 1].G = 0.0f;  // occluded
+                } else {
+                    if (!kReplay) sum = sum + c;
+                    cnt.add(kCntLit);
+                }
+                shadow = false;
+                if (has_ext) {
+                    ray = make_ray(ray.o, ed);
+                    ++b;
+                } else {
+                    end = true;
+                }
+            } else if (!hit) {
+                end = true;
+            } else {
+                cnt.add(kCntVert);
+                const PSurf S = psurface_at(a, mat, st.h, ray.d);
+                PRec *R = kReplay ? &rec[nv++] : nullptr;
+                if (kReplay) prec_vertex(*R, S, beta);
+                PNee N;
+                const bool cand = pnee_prepare(a, S, N);
+                if (cand) {
+                    c = beta * N.fp * mk3(N.ep.x, N.ep.y, N.ep.z) * N.G;
+                    unsigned unc = 7u;
+                    if (a.clip > 0.0f) {
+                        if (c.x > a.clip) { c.x = a.clip; unc &= ~1u; }
+                        if (c.y > a.clip) { c.y = a.clip; unc &= ~2u; }
+                        if (c.z > a.clip) { c.z = a.clip; unc &= ~4u; }
+                    }
+                    if (kReplay) {
+                        R->pb = N.pb;
+                        R->Ep[0] = N.ep.x; R->Ep[1] = N.ep.y; R->Ep[2] = N.ep.z;
+                        R->G = N.G;
+                        R->unc = unc | (N.L.on > 0.0f ? 8u : 0u);
+                        R->Sp = N.L.S; R->dSrp = N.L.dSr; R->s5p = N.L.s5; R->dSnp = N.L.dSn;
+                        R->wp_cs = N.wp_cs;
+                    }
+                }
+                has_ext = false;
+                if (b < a.bounces) {
+                    PCont C;
+                    if (pcontinue_prepare(a, (uint32_t)pix, (uint32_t)s, b, S, C)) {
+                        cnt.add(kCntCont);
+                        beta = beta * C.w;
+                        ed = C.wi;
+                        has_ext = true;
+                        if (kReplay) {
+                            R->cw = C.cw;
+                            R->unc |= C.L.on > 0.0f ? 16u : 0u;
+                            R->Si = C.L.S; R->dSri = C.L.dSr; R->s5i = C.L.s5; R->dSni = C.L.dSn;
+                            R->wi_ci = C.wi_ci;
+                        }
+                    }
+                }
+                if (cand) {
+                    shadow = true;
+                    ray = make_ray(N.so, N.sdir);
+                    tmax = N.smax;
+                } else if (has_ext) {
+                    ray = make_ray(S.x + S.n * kRayEps, ed);
+                    ++b;
+                } else {
+                    end = true;
+                }
+            }
+            if (end) break;
+        }
+        if (kReplay) psweep(a, dmat, rec, nv, gb_in);
+        nv = 0;
+        s += L;
+        if (s < a.spp) {
+            f3 o, d;
+            camera_ray(a, (uint32_t)pix, (uint32_t)s, o, d);
+            ray = make_ray(o, d);
+            beta = mk3(1.f, 1.f, 1.f);
+            b = 1;
+            shadow = false;
+            has_ext = false;
+            cnt.add(kCntPath);
+        }
+    }
+    cnt.flush(a.counters);
+    if (!kReplay) {
+        for (int off = L >> 1; off > 0; off >>= 1) {
+            sum.x += __shfl_xor_sync(0xffffffffu, sum.x, off);
+            sum.y += __shfl_xor_sync(0xffffffffu, sum.y, off);
+            sum.z += __shfl_xor_sync(0xffffffffu, sum.z, off);
+        }
+        if (valid && sl == 0) {
+            const float inv = 1.0f / (float)a.spp;
+            const float ex = sum.x * inv, ey = sum.y * inv, ez = sum.z * inv;
+            if (a.Ec) {
+                a.Ec[3 * pix] = ex;
+                a.Ec[3 * pix + 1] = ey;
+                a.Ec[3 * pix + 2] = ez;
+            }
+            const float e3[3] = {ex, ey, ez};
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const float v = a.gain_c * a.wb[j] * e3[j];
+                a.Ic[3 * pix + j] = v > 0.0f ? powf(v, a.gamma_c[j]) : 0.0f;
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kPBlock, DPCS_PBR_MINB) k_render_pbr(const RenderArgs a, const float4 *__restrict__ mat) {
+    const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t pix = gt >> a.log2L;
+    pbr_lanes<false>(a, mat, nullptr, pix, (int)(gt & ((1 << a.log2L) - 1)), pix < (int64_t)a.Hc * a.Wc);
+}
+
+__global__ void __launch_bounds__(kPBlock, DPCS_PBR_MINB) k_replay_pbr(const RenderArgs a, const float4 *__restrict__ mat,
+                                                        float4 *__restrict__ dmat) {
+    const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t pix = gt >> a.log2L;
+    pbr_lanes<true>(a, mat, dmat, pix, (int)(gt & ((1 << a.log2L) - 1)), pix < (int64_t)a.Hc * a.Wc);
+}
+
+__global__ void k_pack_mat(const float *__restrict__ metallic, const float *__restrict__ normal, int64_t ntex,
+                           float4 *__restrict__ mat) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= ntex) return;
+    mat[t] = make_float4(metallic ? metallic[t] : 0.0f, normal ? normal[3 * t] : 0.5f, normal ? normal[3 * t + 1] : 0.5f,
+                         normal ? normal[3 * t + 2] : 1.0f);
+}
+
+__global__ void k_mat_backward(const float4 *__restrict__ dmat, int64_t ntex, float *__restrict__ dMetallic,
+                               float *__restrict__ dNormal) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= ntex) return;
+    const float4 g = dmat[t];
+    if (dMetallic) dMetallic[t] += g.x;
+    if (dNormal) {
+        dNormal[3 * t] += g.y;
+        dNormal[3 * t + 1] += g.z;
+        dNormal[3 * t + 2] += g.w;
+    }
+}
+
+inline unsigned grid1(int64_t n, int block) { return (unsigned)((n + block - 1) / block); }
+
+}  // namespace
+
+int launch_pack_mat(const float *metallic, const float *normal, int64_t ntex, float4 *mat, cudaStream_t st) {
+    if (ntex <= 0) return 0;
+    k_pack_mat<<<grid1(ntex, 256), 256, 0, st>>>(metallic, normal, ntex, mat);
+    return 1;
+}
+
+int launch_render_pbr(const RenderArgs &a, const float4 *mat, cudaStream_t st) {
+    const int64_t threads = ((int64_t)a.Hc * a.Wc) << a.log2L;
+    if (threads <= 0) return 0;
+    k_render_pbr<<<grid1(threads, kPBlock), kPBlock, 0, st>>>(a, mat);
+    return 1;
+}
+
+int launch_replay_pbr(const RenderArgs &a, const float4 *mat, float4 *dmat, cudaStream_t st) {
+    const int64_t threads = ((int64_t)a.Hc * a.Wc) << a.log2L;
+    if (threads <= 0) return 0;
+    k_replay_pbr<<<grid1(threads, kPBlock), kPBlock, 0, st>>>(a, mat, dmat);
+    return 1;
+}
+
+int launch_mat_backward(const float4 *dmat, int64_t ntex, float *dMetallic, float *dNormal, cudaStream_t st) {
+    if (ntex <= 0 || (!dMetallic && !dNormal)) return 0;
+    k_mat_backward<<<grid1(ntex, 256), 256, 0, st>>>(dmat, ntex, dMetallic, dNormal);
+    return 1;
+}
+
+}  // namespace dpcs

@@ -35,7 +35,7 @@ EXPORTED = [
     "dpcs_serve_submit", "dpcs_serve_step", "dpcs_serve_query", "dpcs_serve_drain", "dpcs_serve_stats_get",
     "dpcs_probe_l2_load", "dpcs_probe_atomic4", "dpcs_gbuffer", "dpcs_denoise", "dpcs_denoise_backward",
     "dpcs_l1_loss", "dpcs_tv_loss", "dpcs_scene_update", "dpcs_render_loss_backward", "dpcs_render_keep",
-    "dpcs_render_backward_kept",
+    "dpcs_render_backward_kept", "dpcs_render_principled", "dpcs_render_backward_principled",
 ]
 
 DPCS_REQ_RELIGHT = 0
@@ -59,6 +59,12 @@ class DpcsParams(ctypes.Structure):
                 ("ks", ctypes.c_float), ("f0", ctypes.c_float),
                 ("rr_start", ctypes.c_int32), ("rr_q", ctypes.c_float),
                 ("clip", ctypes.c_float), ("jitter", ctypes.c_int32)]
+
+
+class DpcsMaterial(ctypes.Structure):
+    """dpcs_material: device pointers of the principled maps (NULL = absent)."""
+    _fields_ = [("albedo", ctypes.c_void_p), ("rough", ctypes.c_void_p), ("metallic", ctypes.c_void_p),
+                ("normal", ctypes.c_void_p), ("Ht", ctypes.c_int32), ("Wt", ctypes.c_int32)]
 
 
 class DpcsView(ctypes.Structure):
@@ -133,6 +139,13 @@ _SIGS = {
                                                    ctypes.POINTER(DpcsView), ctypes.POINTER(DpcsParams),
                                                    ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, _P, ctypes.c_int32,
                                                    ctypes.c_float, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "dpcs_render_principled": (ctypes.c_int32, [_P, ctypes.c_uint64, ctypes.POINTER(DpcsMaterial), _P,
+                                                ctypes.POINTER(DpcsView), ctypes.POINTER(DpcsParams), ctypes.c_int32,
+                                                ctypes.c_int32, ctypes.c_uint64, _P, _P, _P]),
+    "dpcs_render_backward_principled": (ctypes.c_int32, [_P, ctypes.c_uint64, ctypes.POINTER(DpcsMaterial), _P,
+                                                         ctypes.POINTER(DpcsView), ctypes.POINTER(DpcsParams),
+                                                         ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, _P, _P, _P,
+                                                         _P, _P, _P, _P, _P, _P, _P]),
     "dpcs_timing_enable": (ctypes.c_int32, [_P, ctypes.c_int32]),
     "dpcs_timing_read": (ctypes.c_int32, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_int64)]),
@@ -564,6 +577,61 @@ class Context:
             _ptr(dRough, "dRough", (Ht, Wt), f32, self.device, allow_none=True),
             _ptr(dParams, "dParams", (11,), f32, self.device, allow_none=True), _stream(stream))
         self.check(st, "render_backward")
+
+    # -- principled material (metallic and normal maps) --------------------------
+    def _material(self, albedo, rough, metallic, normal):
+        import torch
+
+        Ht, Wt = albedo.shape[0], albedo.shape[1]
+        f32 = torch.float32
+        m = DpcsMaterial()
+        m.albedo = _ptr(albedo, "albedo", (Ht, Wt, 3), f32, self.device)
+        m.rough = _ptr(rough, "rough", (Ht, Wt), f32, self.device)
+        m.metallic = _ptr(metallic, "metallic", (Ht, Wt), f32, self.device, allow_none=True)
+        m.normal = _ptr(normal, "normal", (Ht, Wt, 3), f32, self.device, allow_none=True)
+        m.Ht, m.Wt = Ht, Wt
+        return m
+
+    def render_principled(self, scene: int, albedo, rough, metallic, normal, Ip, view: DpcsView,
+                          params: DpcsParams, spp: int, bounces: int, seed: int, Ic=None, Ec=None, stream=None):
+        """dpcs_render_principled: render with metallic (Ht, Wt) and normal (Ht, Wt, 3) maps (either None)."""
+        import torch
+
+        f32 = torch.float32
+        mat = self._material(albedo, rough, metallic, normal)
+        if Ic is None:
+            Ic = torch.empty((view.Hc, view.Wc, 3), dtype=f32, device=self.device)
+        st = self.lib.dpcs_render_principled(
+            self.handle, scene, ctypes.byref(mat), _ptr(Ip, "Ip", (view.Hp, view.Wp, 3), f32, self.device),
+            ctypes.byref(view), ctypes.byref(params), int(spp), int(bounces), int(seed) & (2**64 - 1),
+            _ptr(Ic, "Ic", (view.Hc, view.Wc, 3), f32, self.device),
+            _ptr(Ec, "Ec", (view.Hc, view.Wc, 3), f32, self.device, allow_none=True), _stream(stream))
+        self.check(st, "render_principled")
+        return Ic, Ec
+
+    def render_backward_principled(self, scene: int, albedo, rough, metallic, normal, Ip, view: DpcsView,
+                                   params: DpcsParams, spp: int, bounces: int, seed: int, Ec, Ic, dIc, dIp=None,
+                                   dAlbedo=None, dRough=None, dMetallic=None, dNormal=None, dParams=None,
+                                   stream=None):
+        """dpcs_render_backward_principled: the adjoint, accumulating into the given gradient buffers."""
+        import torch
+
+        f32 = torch.float32
+        mat = self._material(albedo, rough, metallic, normal)
+        Ht, Wt = mat.Ht, mat.Wt
+        img = (view.Hc, view.Wc, 3)
+        st = self.lib.dpcs_render_backward_principled(
+            self.handle, scene, ctypes.byref(mat), _ptr(Ip, "Ip", (view.Hp, view.Wp, 3), f32, self.device),
+            ctypes.byref(view), ctypes.byref(params), int(spp), int(bounces), int(seed) & (2**64 - 1),
+            _ptr(Ec, "Ec", img, f32, self.device), _ptr(Ic, "Ic", img, f32, self.device),
+            _ptr(dIc, "dIc", img, f32, self.device),
+            _ptr(dIp, "dIp", (view.Hp, view.Wp, 3), f32, self.device, allow_none=True),
+            _ptr(dAlbedo, "dAlbedo", (Ht, Wt, 3), f32, self.device, allow_none=True),
+            _ptr(dRough, "dRough", (Ht, Wt), f32, self.device, allow_none=True),
+            _ptr(dMetallic, "dMetallic", (Ht, Wt), f32, self.device, allow_none=True),
+            _ptr(dNormal, "dNormal", (Ht, Wt, 3), f32, self.device, allow_none=True),
+            _ptr(dParams, "dParams", (11,), f32, self.device, allow_none=True), _stream(stream))
+        self.check(st, "render_backward_principled")
 
     def gbuffer(self, scene: int, albedo, rough, view: DpcsView, guide=None, stream=None):
         """Guide features (Hc, Wc, 8) of the first hit through each pixel centre."""

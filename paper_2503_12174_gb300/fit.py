@@ -4,21 +4,25 @@
     theta* = argmin (1/K) sum_i |D(R(Ip_i, theta)) - Ic_i| + lambda L(m),
 
 with |.| the L1 norm (a mean over the pixels and channels of the K pairs),
-L(m) the total variation of the albedo and roughness maps, and D the
-optional cross-bilateral denoiser of Eq. 11.  theta = albedo, roughness,
-gamma_p, gamma_c and the white balance w; the gains Gp and Gc stay at their
-given constants (Sec. 3.2).  Each step renders every pair with a fresh
+L(m) the total variation of the BRDF maps (albedo, roughness and, with the
+principled material, metallic), and D the optional cross-bilateral
+denoiser of Eq. 11.  theta = albedo, roughness, gamma_p, gamma_c and the
+white balance w, plus the metallic map and the normal map Vn when they are
+given (the principled material of Sec. 3.2); the gains Gp and Gc stay at
+their given constants (Sec. 3.2).  Each step renders every pair with a fresh
 Philox key, accumulates the path-replay gradients of all pairs, adds the
 total-variation gradient and takes one Adam step per parameter group, each
 followed by the clamp to the group's range: albedo [0, 1], roughness
-[0.01, 1], gamma_p [2, 3], gamma_c [1/3, 1], w [0.2, 2.5] (Sec. 3.2).
+[0.01, 1], metallic [0, 1], normal map [0, 1]^3 (Sec. 4.3), gamma_p [2, 3],
+gamma_c [1/3, 1], w [0.2, 2.5] (Sec. 3.2).
 
 Without the denoiser each pair's render, L1 term and adjoint are one call
 that traces its paths once (``Context.render_loss_backward``); with it, the
 render keeps its path records and the adjoint sweeps them.  ``fused=False``
-makes separate calls that trace twice.  Every step runs in the library's kernels; the only
-host traffic per step is reading back the 11 response parameters the next
-renders take by value.
+makes separate calls that trace twice, and so does the principled material
+(dpcs_render_principled, then dpcs_render_backward_principled).  Every step
+runs in the library's kernels; the only host traffic per step is reading
+back the 11 response parameters the next renders take by value.
 """
 from __future__ import annotations
 
@@ -37,7 +41,7 @@ class SceneFit:
     def __init__(self, ctx: dpcs.Context, scene: int, view: dpcs.DpcsView, params0: dpcs.DpcsParams, albedo0, rough0,
                  pairs, spp: int, bounces: int, lr_tex: float = 2e-2, lr_params: float = 1e-2, tv_weight: float = 0.0,
                  denoise: dpcs.DpcsDenoiseParams | None = None, fit_params: bool = True, seed: int = 0,
-                 fused: bool = True):
+                 fused: bool = True, metallic0=None, normal0=None):
         import torch
 
         self.ctx, self.scene, self.view = ctx, scene, view
@@ -50,6 +54,16 @@ class SceneFit:
         f32 = torch.float32
         self.albedo = albedo0.clone().contiguous()
         self.rough = rough0.clone().contiguous()
+        # principled material: metallic (Ht, Wt) and normal map (Ht, Wt, 3), each optional
+        self.principled = metallic0 is not None or normal0 is not None
+        self.metallic = None if metallic0 is None else metallic0.clone().contiguous()
+        self.normal = None if normal0 is None else normal0.clone().contiguous()
+        self.gM = None if self.metallic is None else torch.zeros_like(self.metallic)
+        self.gN = None if self.normal is None else torch.zeros_like(self.normal)
+        if self.metallic is not None:
+            self.mM, self.vM = torch.zeros_like(self.metallic), torch.zeros_like(self.metallic)
+        if self.normal is not None:
+            self.mN, self.vN = torch.zeros_like(self.normal), torch.zeros_like(self.normal)
         self.params = params0
         self.pvec = torch.tensor(params_vector(params0), dtype=f32, device=dev)
         self.gA, self.gR = torch.zeros_like(self.albedo), torch.zeros_like(self.rough)
@@ -64,7 +78,8 @@ class SceneFit:
             self.guide = torch.empty((view.Hc, view.Wc, 8), dtype=f32, device=dev)
             self.D, self.dD = torch.empty(img, dtype=f32, device=dev), torch.empty(img, dtype=f32, device=dev)
             self.wsum = torch.empty((view.Hc, view.Wc), dtype=f32, device=dev)
-        self.losses = torch.zeros(self.K + 2, dtype=f32, device=dev)  # K data terms, TV(albedo), TV(rough)
+        # K data terms, TV(albedo), TV(rough) [, TV(metallic)]
+        self.losses = torch.zeros(self.K + 2 + (self.metallic is not None), dtype=f32, device=dev)
         self.scale = 1.0 / (self.K * view.Hc * view.Wc * 3)
         self.k = 0
 
@@ -75,10 +90,16 @@ class SceneFit:
         self.gA.zero_()
         self.gR.zero_()
         self.gP.zero_()
+        for g in (self.gM, self.gN):
+            if g is not None:
+                g.zero_()
         if self.denoise is not None:  # the guide follows the current albedo; its weights are not differentiated
             c.gbuffer(self.scene, self.albedo, self.rough, self.view, guide=self.guide)
         for i, (Ip, target) in enumerate(self.pairs):
             s = self.seed + (self.k - 1) * self.K + i
+            if self.principled:
+                self._pair_principled(Ip, target, s, i)
+                continue
             if self.denoise is None and self.fused:  # render, L1 term and adjoint in one trace of the paths
                 c.render_loss_backward(self.scene, self.albedo, self.rough, Ip, self.view, self.params, self.spp,
                                        self.bounces, s, target, self.losses[i:i + 1], loss_kind=1, scale=self.scale,
@@ -101,13 +122,36 @@ class SceneFit:
         K = self.K
         c.tv_loss(self.albedo, self.gA, self.losses[K:K + 1], self.tv_weight)
         c.tv_loss(self.rough, self.gR, self.losses[K + 1:K + 2], self.tv_weight)
+        if self.metallic is not None:
+            c.tv_loss(self.metallic, self.gM, self.losses[K + 2:K + 3], self.tv_weight)
         c.adam(self.albedo, self.gA, self.mA, self.vA, self.k, lr=self.lr_tex, lo=0.0, hi=1.0)
         c.adam(self.rough, self.gR, self.mR, self.vR, self.k, lr=self.lr_tex, lo=ROUGH_MIN, hi=1.0)
+        if self.metallic is not None:
+            c.adam(self.metallic, self.gM, self.mM, self.vM, self.k, lr=self.lr_tex, lo=0.0, hi=1.0)
+        if self.normal is not None:
+            c.adam(self.normal, self.gN, self.mN, self.vN, self.k, lr=self.lr_tex, lo=0.0, hi=1.0)
         if self.fit_params:
             for sl, lo, hi in PARAM_RANGES.values():
                 c.adam(self.pvec[sl], self.gP[sl], self.mP[sl], self.vP[sl], self.k, lr=self.lr_params, lo=lo, hi=hi)
             self.params = with_vector(self.params, self.pvec.cpu().tolist())
         return self.losses
+
+    def _pair_principled(self, Ip, target, s, i):
+        """One pair with the principled material: render, (D,) L1, adjoint with every map's gradient."""
+        c = self.ctx
+        c.render_principled(self.scene, self.albedo, self.rough, self.metallic, self.normal, Ip, self.view,
+                            self.params, self.spp, self.bounces, s, Ic=self.Ic, Ec=self.Ec)
+        if self.denoise is None:
+            c.l1_loss(self.Ic, target, self.dIc, self.losses[i:i + 1], scale=self.scale)
+        else:
+            c.denoise(self.Ic, self.guide, self.denoise, out=self.D, wsum=self.wsum)
+            c.l1_loss(self.D, target, self.dD, self.losses[i:i + 1], scale=self.scale)
+            self.dIc.zero_()
+            c.denoise_backward(self.dD, self.guide, self.wsum, self.denoise, dIc=self.dIc)
+        c.render_backward_principled(self.scene, self.albedo, self.rough, self.metallic, self.normal, Ip, self.view,
+                                     self.params, self.spp, self.bounces, s, self.Ec, self.Ic, self.dIc,
+                                     dAlbedo=self.gA, dRough=self.gR, dMetallic=self.gM, dNormal=self.gN,
+                                     dParams=self.gP if self.fit_params else None)
 
     def run(self, steps: int):
         """`steps` Adam steps; returns the per-step total loss (host list)."""

@@ -115,3 +115,57 @@ def test_fit_lowers_loss_and_albedo_error(orc, denoise):
     c0 = np.corrcoef(albedo0.ravel(), true.ravel())[0, 1]
     c1 = np.corrcoef(A.ravel(), true.ravel())[0, 1]
     assert c1 > c0 + 0.1, (c0, c1)
+
+
+def test_principled_fit_step_matches_oracle(orc):
+    """Eq. 9 with the principled material: one step's L1 terms, the albedo,
+    roughness, metallic, normal-map and response gradients and the TV terms
+    (albedo, roughness, metallic) against the oracle's chain, then a short
+    fit that lowers the loss."""
+    torch = need_cuda()
+    sc = scenes.with_principled(scenes.corner(res=20, tex=16, spp=4, bounces=2, seed=3), seed=12)
+    albedo0, rough0, params0 = _start(sc)
+    rng = np.random.default_rng(13)
+    metal0 = np.clip(sc.metallic + 0.2 * rng.uniform(-1, 1, sc.metallic.shape), 0, 1).astype(np.float32)
+    normal0 = np.clip(sc.normal + 0.05 * rng.uniform(-1, 1, sc.normal.shape), 0, 1).astype(np.float32)
+    K, tv_w, lr = 2, 1e-4, 2e-2
+    Ips = [rng.uniform(size=sc.Ip.shape) for _ in range(K)]
+    maps = dict(albedo=albedo0, rough=rough0, params=params0, metallic=metal0, normal=normal0)
+    targets = []
+    for i in range(K):
+        _, Ic = orc.render(sc, Ip=Ips[i], seed=sc.seed + i, **maps)
+        targets.append(Ic + 0.1 * rng.choice([-1.0, 1.0], size=Ic.shape))
+    g = GpuScene(sc)
+    try:
+        pairs = [(torch.from_numpy(Ips[i].astype(np.float32)).cuda(),
+                  torch.from_numpy(targets[i].astype(np.float32)).cuda()) for i in range(K)]
+        f = fit.SceneFit(g.ctx, g.handle, g.view, dpcs.make_params(params0), torch.from_numpy(albedo0).cuda(),
+                         torch.from_numpy(rough0).cuda(), pairs, sc.spp, sc.bounces, lr_tex=lr, lr_params=lr,
+                         tv_weight=tv_w, seed=sc.seed, metallic0=torch.from_numpy(metal0).cuda(),
+                         normal0=torch.from_numpy(normal0).cuda())
+        losses = f.step().cpu().numpy().astype(np.float64)
+        g.ctx.sync()
+        got = {k: x.cpu().numpy().astype(np.float64) for k, x in (("dalbedo", f.gA), ("drough", f.gR),
+                                                                   ("dmetallic", f.gM), ("dnormal", f.gN),
+                                                                   ("dparams", f.gP))}
+        hist = f.run(20)
+    finally:
+        g.close()
+    scale = 1.0 / (K * sc.Hc * sc.Wc * 3)
+    ref = {k: 0.0 for k in got}
+    rl = []
+    for i in range(K):
+        _, Ic = orc.render(sc, Ip=Ips[i], seed=sc.seed + i, **maps)
+        l, dIc = orc.l1_loss(Ic, targets[i], scale)
+        rl.append(l)
+        gr = orc.render_backward(sc, dIc, Ip=Ips[i], seed=sc.seed + i, **maps)
+        for k in ref:
+            ref[k] = ref[k] + gr[k]
+    tv = [orc.tv_loss(x, tv_w) for x in (albedo0, rough0, metal0)]
+    for k, (_, t) in zip(("dalbedo", "drough", "dmetallic"), tv):
+        ref[k] = ref[k] + t
+    np.testing.assert_allclose(losses, rl + [t[0] for t in tv], rtol=1e-4)
+    for k in ("dalbedo", "drough", "dmetallic", "dnormal"):
+        np.testing.assert_allclose(got[k], ref[k], rtol=1e-3, atol=2e-5 * np.abs(ref[k]).max(), err_msg=k)
+    np.testing.assert_allclose(got["dparams"], ref["dparams"], rtol=1e-3, atol=1e-6 * np.abs(ref["dparams"]).max())
+    assert np.mean(hist[-3:]) < np.mean(hist[:2])
