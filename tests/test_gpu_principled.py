@@ -149,3 +149,25 @@ def test_principled_backward_refuses_a_gradient_without_its_map():
         g.ctx.sync()
     finally:
         g.close()
+
+
+def test_principled_full_size_sampled_pixels(orc):
+    """The forward workload's size and launch shape (corner 256^2, 64 spp,
+    3 bounces, 32 lanes per pixel) with both maps: 300 random pixels against
+    the oracle run on those pixels alone."""
+    torch = need_cuda()
+    sc = scenes.with_principled(scenes.corner(res=256, spp=64, bounces=3, seed=1000), seed=4000)
+    g = GpuScene(sc)
+    try:
+        m, n = _maps(g, sc)
+        Ec, Ic = _render(g, sc, m, n)
+        Ec, Ic = Ec.cpu().numpy().reshape(-1, 3), Ic.cpu().numpy().reshape(-1, 3)
+    finally:
+        g.close()
+    px = np.random.default_rng(11).choice(sc.Hc * sc.Wc, 300, replace=False)
+    rEc, rIc = orc.render(sc, pixels=px)
+    assert rEc.max() > 0
+    ok, info = pixel_parity(Ec[px], rEc)
+    assert ok, info
+    ok, info = pixel_parity(Ic[px], rIc, atol=crf_atol(sc, rEc))
+    assert ok, info
