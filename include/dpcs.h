@@ -197,6 +197,21 @@ dpcs_status dpcs_scene_upload(dpcs_ctx *ctx, const float *verts, int32_t V, cons
  */
 dpcs_status dpcs_scene_update(dpcs_ctx *ctx, dpcs_scene scene, const float *verts, int32_t V, void *stream);
 
+/*
+ * Rigid transform of an uploaded scene, for the camera pose (Rc, tc) of
+ * Sec. 3.2's scene parameters: renders take the camera at the origin
+ * (Eq. 6), and a camera at pose (Rc, tc) sees each world point x at
+ * Rc x + tc, so a pose refinement moves the mesh by (R, t) = (Rc, tc) and
+ * the projector extrinsics by Rp' = Rp R^T, tp' = tp - Rp' t (the caller
+ * passes those in the view).  Every vertex of the scene's last upload or
+ * update goes to R v + t (R host, row-major 3 x 3; t host, 3 floats) and the
+ * tree is refitted as by dpcs_scene_update.  The stored positions are not
+ * changed, so transforms do not compound: each call maps the same positions.
+ * DPCS_ERR_INVALID_ARG for a null or non-finite R or t; DPCS_ERR_NOT_FOUND
+ * for an unknown scene.
+ */
+dpcs_status dpcs_scene_transform(dpcs_ctx *ctx, dpcs_scene scene, const float R[9], const float t[3], void *stream);
+
 /* Release a scene's device memory. */
 dpcs_status dpcs_scene_free(dpcs_ctx *ctx, dpcs_scene scene);
 

@@ -287,6 +287,9 @@ dpcs_status dpcs_destroy(dpcs_ctx *c) {
         cudaFree(s.tuv);
         cudaFree(s.codes);
         cudaFree(s.order);
+        cudaFree(s.vidx);
+        cudaFree(s.uv);
+        cudaFree(s.base);
     }
     Buf *bufs[] = {&c->ep4, &c->tex4, &c->gE, &c->dEp4, &c->dtex4, &c->acc, &c->partial, &c->build, &c->upload, &c->pix,
                    &c->kept, &c->mat4, &c->dmat4};
@@ -399,20 +402,22 @@ dpcs_status dpcs_scene_upload(dpcs_ctx *c, const float *verts, int32_t V, const 
     const size_t nn = (size_t)(T > 1 ? T - 1 : 1);
     const size_t nv = (size_t)(V > 0 ? V : 1);
     sc.V = V;
-    sc.bytes = nn * 64 + n * 48 + n * 24 + n * 8 + n * 12 + nv * 8;
+    sc.bytes = nn * 64 + n * 48 + n * 24 + n * 8 + n * 12 + nv * 8 + nv * 12;
     if ((s = dev_alloc(c, (void **)&sc.nodes, nn * 64, "scene nodes")) ||
         (s = dev_alloc(c, (void **)&sc.tris, n * 48, "scene triangles")) ||
         (s = dev_alloc(c, (void **)&sc.tuv, n * 24, "scene uv")) ||
         (s = dev_alloc(c, (void **)&sc.codes, n * 4, "scene codes")) ||
         (s = dev_alloc(c, (void **)&sc.order, n * 4, "scene order")) ||
         (s = dev_alloc(c, (void **)&sc.vidx, n * 12, "scene vertex indices")) ||
-        (s = dev_alloc(c, (void **)&sc.uv, nv * 8, "scene vertex uv"))) {
+        (s = dev_alloc(c, (void **)&sc.uv, nv * 8, "scene vertex uv")) ||
+        (s = dev_alloc(c, (void **)&sc.base, nv * 12, "scene vertex positions"))) {
         dev_free(c, sc.nodes, sc.nodes ? nn * 64 : 0);
         dev_free(c, sc.tris, sc.tris ? n * 48 : 0);
         dev_free(c, sc.tuv, sc.tuv ? n * 24 : 0);
         dev_free(c, sc.codes, sc.codes ? n * 4 : 0);
         dev_free(c, sc.order, sc.order ? n * 4 : 0);
         dev_free(c, sc.vidx, sc.vidx ? n * 12 : 0);
+        dev_free(c, sc.uv, sc.uv ? nv * 8 : 0);
         return s;
     }
     if (T > 0) {
@@ -433,6 +438,7 @@ dpcs_status dpcs_scene_upload(dpcs_ctx *c, const float *verts, int32_t V, const 
         if ((s = check_launch(c, nl, "LBVH build"))) return s;
         e = cudaMemcpyAsync(sc.vidx, dt, tb, cudaMemcpyDeviceToDevice, st);  // kept for dpcs_scene_update
         if (e == cudaSuccess) e = cudaMemcpyAsync(sc.uv, du, ub, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(sc.base, dv, vb, cudaMemcpyDeviceToDevice, st);  // rigid transforms
         if (e != cudaSuccess) return cuda_fail(c, e, "scene upload");
         e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return cuda_fail(c, e, "LBVH build");
@@ -460,6 +466,7 @@ dpcs_status dpcs_scene_free(dpcs_ctx *c, dpcs_scene scene) {
     dev_free(c, s.order, n * 4);
     dev_free(c, s.vidx, n * 12);
     dev_free(c, s.uv, (size_t)(s.V > 0 ? s.V : 1) * 8);
+    dev_free(c, s.base, (size_t)(s.V > 0 ? s.V : 1) * 12);
     c->scenes.erase(it);
     return DPCS_OK;
 }
@@ -483,9 +490,31 @@ dpcs_status dpcs_scene_update(dpcs_ctx *c, dpcs_scene scene, const float *verts,
         (s = ensure(c, c->build, lbvh_refit_scratch_bytes(sc.T), "refit scratch")))
         return s;
     cudaError_t e = cudaMemcpyAsync(c->upload.p, verts, vb, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sc.base, c->upload.p, vb, cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return cuda_fail(c, e, "scene_update upload");
     return check_launch(c, launch_lbvh_refit((const float *)c->upload.p, sc, c->build.p, c->build.n, st),
                         "LBVH refit");
+}
+
+dpcs_status dpcs_scene_transform(dpcs_ctx *c, dpcs_scene scene, const float R[9], const float t[3], void *stream) {
+    Range range("dpcs_scene_transform");
+    if (!c) return DPCS_ERR_INVALID_ARG;
+    auto it = c->scenes.find(scene);
+    if (it == c->scenes.end()) return fail(c, DPCS_ERR_NOT_FOUND, "unknown scene handle");
+    if (!R || !t || !finite_all(R, 9) || !finite_all(t, 3))
+        return fail(c, DPCS_ERR_INVALID_ARG, "scene_transform: null or non-finite R or t");
+    Scene &sc = it->second;
+    if (sc.T <= 0) return DPCS_OK;
+    dpcs_status s = set_device(c);
+    if (s) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((s = ensure(c, c->upload, (size_t)sc.V * 12, "upload staging")) ||
+        (s = ensure(c, c->build, lbvh_refit_scratch_bytes(sc.T), "refit scratch")))
+        return s;
+    int nl = launch_rigid_transform(sc.base, sc.V, R, t, (float *)c->upload.p, st);
+    const int nr = launch_lbvh_refit((const float *)c->upload.p, sc, c->build.p, c->build.n, st);
+    if (nr < 0) return check_launch(c, nr, "LBVH refit");
+    return check_launch(c, nl + nr, "scene_transform");
 }
 
 dpcs_status dpcs_scene_export(dpcs_ctx *c, dpcs_scene scene, uint32_t *codes, int32_t *order, int32_t *child,

@@ -30,6 +30,7 @@ struct Scene {
     int32_t V = 0;             // vertex count the mesh was uploaded with
     int32_t *vidx = nullptr;   // triangle vertex indices, 3 x T (kept for refits)
     float *uv = nullptr;       // per-vertex texture coordinates, 2 x V (kept for refits)
+    float *base = nullptr;     // vertex positions of the last upload or update, 3 x V (rigid transforms start here)
     size_t bytes = 0;
 };
 constexpr int32_t kEmptyRoot = (int32_t)0x80000000;
@@ -95,6 +96,8 @@ size_t lbvh_scratch_bytes(int32_t T);
 // the existing tree (topology and leaf order kept).  d_verts holds sc.V
 // vertices.  Returns the kernels enqueued or a negative dpcs_status.
 int launch_lbvh_refit(const float *d_verts, Scene &sc, void *scratch, size_t scratch_bytes, cudaStream_t st);
+// out[v] = R in[v] + t for V points (R row-major)
+int launch_rigid_transform(const float *in, int32_t V, const float R[9], const float t[3], float *out, cudaStream_t st);
 size_t lbvh_refit_scratch_bytes(int32_t T);
 
 int launch_prf(const float *Ip, int64_t ntex, const float gamma_p[3], float gain_p, float4 *Ep, cudaStream_t st);

@@ -280,6 +280,30 @@ int launch_lbvh_refit(const float *d_verts, Scene &sc, void *scratch, size_t scr
     return launches + 1;
 }
 
+namespace {
+struct Rigid {
+    float R[9], t[3];
+};
+__global__ void k_rigid(const float *__restrict__ in, int32_t V, const Rigid m, float *__restrict__ out) {
+    const int32_t v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= V) return;
+    const float x = in[3 * v], y = in[3 * v + 1], z = in[3 * v + 2];
+    out[3 * v] = m.R[0] * x + m.R[1] * y + m.R[2] * z + m.t[0];
+    out[3 * v + 1] = m.R[3] * x + m.R[4] * y + m.R[5] * z + m.t[1];
+    out[3 * v + 2] = m.R[6] * x + m.R[7] * y + m.R[8] * z + m.t[2];
+}
+}  // namespace
+
+int launch_rigid_transform(const float *in, int32_t V, const float R[9], const float t[3], float *out,
+                           cudaStream_t st) {
+    if (V <= 0) return 0;
+    Rigid m;
+    for (int i = 0; i < 9; ++i) m.R[i] = R[i];
+    for (int i = 0; i < 3; ++i) m.t[i] = t[i];
+    k_rigid<<<(V + 255) / 256, 256, 0, st>>>(in, V, m, out);
+    return 1;
+}
+
 int launch_lbvh_build(const float *d_verts, int32_t V, const int32_t *d_tris, int32_t T, const float *d_uv,
                       Scene &sc, void *scratch, size_t scratch_bytes, cudaStream_t st) {
     (void)V;

@@ -36,6 +36,7 @@ EXPORTED = [
     "dpcs_probe_l2_load", "dpcs_probe_atomic4", "dpcs_gbuffer", "dpcs_denoise", "dpcs_denoise_backward",
     "dpcs_l1_loss", "dpcs_tv_loss", "dpcs_scene_update", "dpcs_render_loss_backward", "dpcs_render_keep",
     "dpcs_render_backward_kept", "dpcs_render_principled", "dpcs_render_backward_principled",
+    "dpcs_scene_transform",
 ]
 
 DPCS_REQ_RELIGHT = 0
@@ -117,6 +118,7 @@ _SIGS = {
                                            ctypes.POINTER(ctypes.c_uint64)]),
     "dpcs_scene_free": (ctypes.c_int32, [_P, ctypes.c_uint64]),
     "dpcs_scene_update": (ctypes.c_int32, [_P, ctypes.c_uint64, _P, ctypes.c_int32, _P]),
+    "dpcs_scene_transform": (ctypes.c_int32, [_P, ctypes.c_uint64, _P, _P, _P]),
     "dpcs_scene_export": (ctypes.c_int32, [_P, ctypes.c_uint64, _P, _P, _P, _P]),
     "dpcs_trace": (ctypes.c_int32, [_P, ctypes.c_uint64, _P, _P, ctypes.c_int64, _P, _P, _P]),
     "dpcs_render": (ctypes.c_int32, [_P, ctypes.c_uint64, _P, _P, ctypes.c_int32, ctypes.c_int32, _P,
@@ -510,6 +512,15 @@ class Context:
         verts = np.ascontiguousarray(verts, np.float32)
         st = self.lib.dpcs_scene_update(self.handle, scene, verts.ctypes.data_as(_P), len(verts), _stream(stream))
         self.check(st, "scene_update")
+
+    def transform(self, scene: int, R, t, stream=None):
+        """dpcs_scene_transform: the scene's stored vertex positions mapped by
+        v -> R v + t (3 x 3 and 3-vector, rounded to float32), tree refitted."""
+        Rf = np.ascontiguousarray(np.asarray(R, np.float64).reshape(3, 3), np.float32)
+        tf = np.ascontiguousarray(np.asarray(t, np.float64).reshape(3), np.float32)
+        st = self.lib.dpcs_scene_transform(self.handle, scene, Rf.ctypes.data_as(_P), tf.ctypes.data_as(_P),
+                                           _stream(stream))
+        self.check(st, "scene_transform")
 
     def free(self, scene: int):
         self.check(self.lib.dpcs_scene_free(self.handle, scene), "scene_free")

@@ -1,0 +1,145 @@
+"""Camera-pose refinement: the rotation Rc and translation tc that Sec. 3.2
+lists among the scene parameters theta of Eq. 9 and refines slightly.
+
+Renders put the camera at the origin (Eq. 6).  A camera at pose (Rc, tc)
+sees a world point x at Rc x + tc, so the pose is applied to the scene: the
+mesh moves by ``dpcs_scene_transform`` and the projector extrinsics become
+Rp' = Rp Rc^T, tp' = tp - Rp' tc (``posed_view``).
+
+The pose is xi = (omega, delta) around a starting pose (R0, t0):
+Rc = exp([omega]x) R0 (Rodrigues), tc = t0 + delta.  Its gradient is taken
+by central differences with common random numbers: every evaluation renders
+with the same Philox keys, so the difference sees only the pose change.  Six
+parameters cost twelve renders per pair, and the differences include what
+the image does where silhouettes and shadow edges cross pixels -- the
+visibility terms that path replay with detached sampling (the adjoint of
+every other parameter) leaves out.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import dpcs
+
+
+def rotation(omega) -> np.ndarray:
+    """exp([omega]x): rotation by |omega| about omega / |omega| (Rodrigues)."""
+    w = np.asarray(omega, np.float64).reshape(3)
+    th = float(np.linalg.norm(w))
+    K = np.array([[0.0, -w[2], w[1]], [w[2], 0.0, -w[0]], [-w[1], w[0], 0.0]])
+    if th < 1e-8:  # series to second order
+        return np.eye(3) + K + 0.5 * (K @ K)
+    return np.eye(3) + (math.sin(th) / th) * K + ((1.0 - math.cos(th)) / (th * th)) * (K @ K)
+
+
+def pose_of(xi, R0=None, t0=None):
+    """(Rc, tc) of pose parameters xi = (omega, delta) around (R0, t0)."""
+    xi = np.asarray(xi, np.float64).reshape(6)
+    R0 = np.eye(3) if R0 is None else np.asarray(R0, np.float64)
+    t0 = np.zeros(3) if t0 is None else np.asarray(t0, np.float64)
+    return rotation(xi[:3]) @ R0, t0 + xi[3:]
+
+
+def posed_extrinsics(Rp, tp, R, t):
+    """Projector extrinsics seen from a camera at pose (R, t): (Rp R^T, tp - Rp R^T t)."""
+    Rp2 = np.asarray(Rp, np.float64).reshape(3, 3) @ np.asarray(R, np.float64).T
+    return Rp2, np.asarray(tp, np.float64).reshape(3) - Rp2 @ np.asarray(t, np.float64).reshape(3)
+
+
+def posed_view(view: dpcs.DpcsView, R, t) -> dpcs.DpcsView:
+    """``view`` with its projector extrinsics moved for a camera at pose (R, t)."""
+    Rp2, tp2 = posed_extrinsics(np.array(view.Rp[:]), np.array(view.tp[:]), R, t)
+    return dpcs.make_view(np.array(view.Kc[:]).reshape(3, 3), view.Hc, view.Wc,
+                          np.array(view.Kp[:]).reshape(3, 3), Rp2, tp2, view.Hp, view.Wp)
+
+
+def central_differences(loss, xi, h):
+    """Gradient of ``loss`` (a callable on 6-vectors returning a float) at xi
+    by central differences with steps h (6 values): 12 evaluations."""
+    xi = np.asarray(xi, np.float64).reshape(6)
+    h = np.broadcast_to(np.asarray(h, np.float64), (6,))
+    g = np.zeros(6)
+    for k in range(6):
+        e = np.zeros(6)
+        e[k] = h[k]
+        g[k] = (loss(xi + e) - loss(xi - e)) / (2.0 * h[k])
+    return g
+
+
+class PoseRefine:
+    """Refines the camera pose against K projector/capture pairs by Adam on
+    the central-difference gradient of the Eq. 9 data term (the mean L1
+    error; the other scene parameters stay fixed).  ``pairs`` is a list of
+    (Ip, Ic) device tensors; ``metallic`` / ``normal`` select the principled
+    material.  Each step: twelve pose evaluations, each a scene transform,
+    K renders and K L1 terms, then one Adam step on xi."""
+
+    def __init__(self, ctx: dpcs.Context, scene: int, view: dpcs.DpcsView, params: dpcs.DpcsParams, albedo, rough,
+                 pairs, spp: int, bounces: int, seed: int = 0, xi0=None, R0=None, t0=None, h_rot: float = 1e-3,
+                 h_trans: float = 1e-3, lr: float = 1e-3, metallic=None, normal=None):
+        import torch
+
+        self.ctx, self.scene, self.view, self.params = ctx, scene, view, params
+        self.albedo, self.rough, self.metallic, self.normal = albedo, rough, metallic, normal
+        self.pairs = list(pairs)
+        self.K = len(self.pairs)
+        self.spp, self.bounces, self.seed = int(spp), int(bounces), int(seed)
+        self.R0 = np.eye(3) if R0 is None else np.asarray(R0, np.float64)
+        self.t0 = np.zeros(3) if t0 is None else np.asarray(t0, np.float64)
+        self.h = np.array([h_rot] * 3 + [h_trans] * 3)
+        self.lr = float(lr)
+        dev = ctx.device
+        f32 = torch.float32
+        self.xi = torch.tensor(np.zeros(6) if xi0 is None else np.asarray(xi0, np.float64), dtype=f32, device=dev)
+        self.g = torch.zeros(6, dtype=f32, device=dev)
+        self.m, self.v = torch.zeros(6, dtype=f32, device=dev), torch.zeros(6, dtype=f32, device=dev)
+        img = (view.Hc, view.Wc, 3)
+        self.Ic = torch.empty(img, dtype=f32, device=dev)
+        self.dIc = torch.empty(img, dtype=f32, device=dev)
+        self.terms = torch.zeros((13, self.K), dtype=f32, device=dev)  # per evaluation and pair
+        self.scale = 1.0 / (self.K * view.Hc * view.Wc * 3)
+        self.k = 0
+
+    def apply(self, xi):
+        """Move the scene to pose xi; returns the matching view."""
+        R, t = pose_of(xi, self.R0, self.t0)
+        self.ctx.transform(self.scene, R, t)
+        return posed_view(self.view, R, t)
+
+    def _evaluate(self, xi, row: int):
+        c = self.ctx
+        v = self.apply(xi)
+        for i, (Ip, target) in enumerate(self.pairs):
+            s = self.seed + (self.k - 1) * self.K + i  # the same keys for every evaluation of a step
+            if self.metallic is not None or self.normal is not None:
+                c.render_principled(self.scene, self.albedo, self.rough, self.metallic, self.normal, Ip, v,
+                                    self.params, self.spp, self.bounces, s, Ic=self.Ic)
+            else:
+                c.render(self.scene, self.albedo, self.rough, Ip, v, self.params, self.spp, self.bounces, s,
+                         Ic=self.Ic)
+            c.l1_loss(self.Ic, target, self.dIc, self.terms[row, i:i + 1], scale=self.scale)
+
+    def step(self) -> float:
+        """One Adam step on the pose; returns the data term at the pose the step started from."""
+        import torch
+
+        self.k += 1
+        xi = self.xi.cpu().numpy().astype(np.float64)
+        self._evaluate(xi, 12)
+        for k in range(6):
+            e = np.zeros(6)
+            e[k] = self.h[k]
+            self._evaluate(xi + e, 2 * k)
+            self._evaluate(xi - e, 2 * k + 1)
+        L = self.terms.sum(dim=1).cpu().numpy().astype(np.float64)
+        g = (L[0:12:2] - L[1:12:2]) / (2.0 * self.h)
+        self.g.copy_(torch.from_numpy(g.astype(np.float32)))
+        self.ctx.adam(self.xi, self.g, self.m, self.v, self.k, lr=self.lr, lo=-1.0, hi=1.0)
+        self.apply(self.xi.cpu().numpy().astype(np.float64))
+        return float(L[12])
+
+    def pose(self):
+        """Current (Rc, tc)."""
+        return pose_of(self.xi.cpu().numpy().astype(np.float64), self.R0, self.t0)
