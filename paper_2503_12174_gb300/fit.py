@@ -8,11 +8,13 @@ L(m) the total variation of the BRDF maps (albedo, roughness and, with the
 principled material, metallic), and D the optional cross-bilateral
 denoiser of Eq. 11.  theta = albedo, roughness, gamma_p, gamma_c and the
 white balance w, plus the metallic map and the normal map Vn when they are
-given (the principled material of Sec. 3.2); the gains Gp and Gc stay at
-their given constants (Sec. 3.2).  Each step renders every pair with a fresh
-Philox key, accumulates the path-replay gradients of all pairs, adds the
-total-variation gradient and takes one Adam step per parameter group, each
-followed by the clamp to the group's range: albedo [0, 1], roughness
+given (the principled material of Sec. 3.2), and the camera pose Rc, tc
+when a starting pose is given (``pose.PoseRefine``: one central-difference
+Adam step on the pose after each step on the other parameters); the gains
+Gp and Gc stay at their given constants (Sec. 3.2).  Each step renders
+every pair with a fresh Philox key, accumulates the path-replay gradients
+of all pairs, adds the total-variation gradient and takes one Adam step per
+parameter group, each followed by the clamp to the group's range: albedo [0, 1], roughness
 [0.01, 1], metallic [0, 1], normal map [0, 1]^3 (Sec. 4.3), gamma_p [2, 3],
 gamma_c [1/3, 1], w [0.2, 2.5] (Sec. 3.2).
 
@@ -22,7 +24,8 @@ render keeps its path records and the adjoint sweeps them.  ``fused=False``
 makes separate calls that trace twice, and so does the principled material
 (dpcs_render_principled, then dpcs_render_backward_principled).  Every step
 runs in the library's kernels; the only host traffic per step is reading
-back the 11 response parameters the next renders take by value.
+back the 11 response parameters the next renders take by value (and, with
+the pose, the 13 K data terms of its differences).
 """
 from __future__ import annotations
 
@@ -41,7 +44,7 @@ class SceneFit:
     def __init__(self, ctx: dpcs.Context, scene: int, view: dpcs.DpcsView, params0: dpcs.DpcsParams, albedo0, rough0,
                  pairs, spp: int, bounces: int, lr_tex: float = 2e-2, lr_params: float = 1e-2, tv_weight: float = 0.0,
                  denoise: dpcs.DpcsDenoiseParams | None = None, fit_params: bool = True, seed: int = 0,
-                 fused: bool = True, metallic0=None, normal0=None):
+                 fused: bool = True, metallic0=None, normal0=None, pose_xi0=None, pose_lr: float = 1e-3):
         import torch
 
         self.ctx, self.scene, self.view = ctx, scene, view
@@ -78,6 +81,17 @@ class SceneFit:
             self.guide = torch.empty((view.Hc, view.Wc, 8), dtype=f32, device=dev)
             self.D, self.dD = torch.empty(img, dtype=f32, device=dev), torch.empty(img, dtype=f32, device=dev)
             self.wsum = torch.empty((view.Hc, view.Wc), dtype=f32, device=dev)
+        # camera pose (Rc, tc): when pose_xi0 is given, every step ends with one
+        # pose step (pose.PoseRefine) on the updated maps, and the renders use
+        # the scene moved to the current pose with the matching view
+        self.pose = None
+        if pose_xi0 is not None:
+            from .pose import PoseRefine
+
+            self.pose = PoseRefine(ctx, scene, view, params0, self.albedo, self.rough, self.pairs, spp, bounces,
+                                   seed=seed + 7919, xi0=pose_xi0, lr=pose_lr, metallic=self.metallic,
+                                   normal=self.normal)
+            self.view = self.pose.apply(pose_xi0)
         # K data terms, TV(albedo), TV(rough) [, TV(metallic)]
         self.losses = torch.zeros(self.K + 2 + (self.metallic is not None), dtype=f32, device=dev)
         self.scale = 1.0 / (self.K * view.Hc * view.Wc * 3)
@@ -134,6 +148,12 @@ class SceneFit:
             for sl, lo, hi in PARAM_RANGES.values():
                 c.adam(self.pvec[sl], self.gP[sl], self.mP[sl], self.vP[sl], self.k, lr=self.lr_params, lo=lo, hi=hi)
             self.params = with_vector(self.params, self.pvec.cpu().tolist())
+        if self.pose is not None:
+            from .pose import posed_view
+
+            self.pose.params = self.params
+            self.pose.step()
+            self.view = posed_view(self.pose.view, *self.pose.pose())
         return self.losses
 
     def _pair_principled(self, Ip, target, s, i):
