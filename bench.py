@@ -81,6 +81,7 @@ LOAD_BYTES = {"node_visits": 64, "tri_tests": 48, "vertices": 24 + 4 * 16, "lit"
 DENOISE_PARAMS = {"radius": 5, "sigma_s": 2.0, "sigma_albedo": 0.1, "sigma_normal": 0.3, "sigma_depth": 0.1}
 DENOISE_FLOP_PER_TAP = 34
 FIT_PAIRS = 15  # the paper's training set size K
+POSE_PAIRS = 3  # pairs per pose evaluation (13 evaluations per pose step)
 
 
 def denoise_taps(H: int, W: int, r: int) -> int:
@@ -629,7 +630,38 @@ def main():
             "albedo_mae_start": float((half.double() - true_alb).abs().mean()),
             "albedo_mae_end": float((fobj.albedo.double() - true_alb).abs().mean()),
         }
-        del fobj, pairs
+        # camera-pose refinement on the same scene: central-difference Adam
+        # steps on the pose (13 evaluations of the data term, each a rigid
+        # transform + refit and POSE_PAIRS renders), from a pose off by ~1 degree
+        from paper_2503_12174_gb300 import pose as pose_mod
+
+        xi0 = np.array([0.01, -0.008, 0.006, 0.01, -0.01, 0.015])
+        pr = pose_mod.PoseRefine(ctx, fh, fview, fprm, f_alb, f_rough, pairs[:POSE_PAIRS], fs.spp, fs.bounces,
+                                 seed=6400 + rank, xi0=xi0, lr=2e-3)
+        pr.step()  # warm-up
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        e0.record(stream)
+        phist = [pr.step() for _ in range(args.fit_steps)]
+        e1.record(stream)
+        e1.synchronize()
+        pose_wall_ms = (time.perf_counter() - t0) * 1e3
+        barrier()
+        pose_ms = max_over_ranks(e0.elapsed_time(e1))
+        xi_end = pr.xi.cpu().numpy().astype(np.float64)
+        ctx.transform(fh, np.eye(3), np.zeros(3))
+        fit_out["pose"] = {
+            "workload": f"camera-pose refinement, same scene and renders, {POSE_PAIRS} pairs: 13 evaluations of "
+                        "the mean L1 data term per step (transform + refit, renders, L1 terms), then Adam on the pose",
+            "steps": args.fit_steps, "ms_per_step": pose_ms / args.fit_steps,
+            "wall_ms_per_step": pose_wall_ms / args.fit_steps,
+            "Msamples_per_s": 13 * POSE_PAIRS * fs.n_samples * args.fit_steps * ws / (pose_ms / 1e3) / 1e6,
+            "loss_first": float(phist[0]), "loss_last": float(phist[-1]),
+            "pose_error_start": [float(np.linalg.norm(xi0[:3])), float(np.linalg.norm(xi0[3:]))],
+            "pose_error_end": [float(np.linalg.norm(xi_end[:3])), float(np.linalg.norm(xi_end[3:]))],
+        }
+        del fobj, pairs, pr
         ctx.free(fh)
 
     # ------------------------------------------------------------ large displaced surface (T = 199,712)
@@ -699,9 +731,18 @@ def main():
         hh2 = ctx.upload(frames[-1], hs.tris, hs.uv)
         rebuild_ms = (time.perf_counter() - t0) * 1e3
         ctx.free(hh2)
+        # a rigid move of the whole surface (camera-pose refinement): transform + refit on the device
+        evt = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(5)]
+        from paper_2503_12174_gb300 import pose as pose_mod
+        for k, (a, b) in enumerate(evt):
+            a.record(stream)
+            ctx.transform(hh, pose_mod.rotation([0.001 * k, 0.0, 0.002]), np.array([0.0, 0.001 * k, 0.0]))
+            b.record(stream)
+        torch.cuda.synchronize()
+        transform_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evt[1:]) / (len(evt) - 1))
         res["morph"] = {"workload": "heightfield vertices moved every frame, then rendered at 16 spp",
                         "update_ms": upd_ms, "frame_ms": frame_ms, "full_upload_ms": rebuild_ms,
-                        "frames": nfr - 1}
+                        "rigid_transform_ms": transform_ms, "frames": nfr - 1}
         ctx.sync()
         ctx.free(hh)
         hf_out = {"workload": f"heightfield T={hs.T}, camera {hs.Hc}x{hs.Wc}, projector {hs.Wp}x{hs.Hp}, "
