@@ -367,6 +367,22 @@ dpcs_status dpcs_render_backward_principled(dpcs_ctx *ctx, dpcs_scene scene, con
                                             float *dRough, float *dMetallic, float *dNormal, float *dParams,
                                             void *stream);
 
+/*
+ * dpcs_render_loss_backward_principled: dpcs_render_loss_backward (render,
+ * per-pixel L2 / L1 loss and adjoint; same arguments, loss kinds, scale,
+ * outputs and record limits, one trace of each path when
+ * ceil(spp / L) <= 4 and ceil(spp / L) * bounces <= 12, otherwise render,
+ * loss, Eq. 5 adjoint and replay) with the principled material, adding (+=)
+ * also dLoss/dmetallic and dLoss/dnormal when given (each needs its map:
+ * DPCS_ERR_INVALID_ARG otherwise).
+ */
+dpcs_status dpcs_render_loss_backward_principled(dpcs_ctx *ctx, dpcs_scene scene, const dpcs_material *mat,
+                                                 const float *Ip, const dpcs_view *view, const dpcs_params *params,
+                                                 int32_t spp, int32_t bounces, uint64_t seed, const float *target,
+                                                 int32_t loss_kind, float scale, float *Ic, float *Ec, float *loss,
+                                                 float *dIp, float *dAlbedo, float *dRough, float *dMetallic,
+                                                 float *dNormal, float *dParams, void *stream);
+
 typedef struct dpcs_denoise_params {
     int32_t radius;      /* window half-width r, 0..8 (0 = identity) */
     float sigma_s;       /* spatial width in pixels, > 0 */

@@ -15,6 +15,10 @@ the denoised image D(Ic) of Eq. 11 instead, and dL/dD is carried back to
 dL/dIc by the filter's adjoint before the replay.  The filter's guide is the
 scene's first hit through each pixel centre, computed once.
 
+With ``metallic`` / ``normal`` maps the scene uses the principled material
+of Sec. 3.2: the one-trace step is ``render_loss_backward_principled``, and
+with the denoiser the render and the replay are separate traces.
+
 With ``graph=True`` the whole loop is captured once as a CUDA graph and then
 replayed.  The steps are unrolled in the graph, so every step keeps its own
 seed and Adam step number, and one replay runs the full compensation.  The
@@ -31,10 +35,13 @@ class Compensation:
 
     def __init__(self, ctx: dpcs.Context, scene: int, albedo, rough, view: dpcs.DpcsView, params: dpcs.DpcsParams,
                  spp: int, bounces: int, steps: int, lr: float = 1e-2, seed: int = 0, graph: bool = True,
-                 denoise: dpcs.DpcsDenoiseParams | None = None, guide=None, fused: bool = True):
+                 denoise: dpcs.DpcsDenoiseParams | None = None, guide=None, fused: bool = True, metallic=None,
+                 normal=None):
         import torch
 
         self.ctx, self.scene, self.albedo, self.rough = ctx, scene, albedo, rough
+        self.metallic, self.normal = metallic, normal
+        self.principled = metallic is not None or normal is not None
         self.view, self.params, self.spp, self.bounces = view, params, int(spp), int(bounces)
         self.steps, self.lr, self.seed = int(steps), float(lr), int(seed)
         dev = ctx.device
@@ -66,6 +73,9 @@ class Compensation:
     def _step(self, k: int):
         c = self.ctx
         s = self.seed + k
+        if self.principled:
+            self._step_principled(k, s)
+            return
         if self.denoise is None and self.fused:  # render, loss and adjoint in one trace of the paths
             self.G.zero_()
             c.render_loss_backward(self.scene, self.albedo, self.rough, self.P, self.view, self.params, self.spp,
@@ -88,6 +98,29 @@ class Compensation:
         self.G.zero_()
         c.render_backward(self.scene, self.albedo, self.rough, self.P, self.view, self.params, self.spp, self.bounces, s,
                           self.Ec, self.Ic, self.dIc, dIp=self.G, kept=keep)
+        c.adam(self.P, self.G, self.M, self.V, k + 1, lr=self.lr, lo=0.0, hi=1.0)
+
+    def _step_principled(self, k: int, s: int):
+        c = self.ctx
+        self.G.zero_()
+        if self.denoise is None and self.fused:  # one trace of the paths
+            c.render_loss_backward_principled(self.scene, self.albedo, self.rough, self.metallic, self.normal, self.P,
+                                              self.view, self.params, self.spp, self.bounces, s, self.target,
+                                              self.loss, loss_kind=0, Ic=self.Ic, Ec=self.Ec, dIp=self.G)
+        else:
+            c.render_principled(self.scene, self.albedo, self.rough, self.metallic, self.normal, self.P, self.view,
+                                self.params, self.spp, self.bounces, s, Ic=self.Ic, Ec=self.Ec)
+            if self.denoise is None:
+                c.l2_loss(self.Ic, self.target, self.dIc, self.loss)
+            else:
+                c.denoise(self.Ic, self.guide, self.denoise, out=self.D, wsum=self.wsum)
+                c.l2_loss(self.D, self.target, self.dD, self.loss)
+                self.dIc.zero_()
+                c.denoise_backward(self.dD, self.guide, self.wsum, self.denoise, dIc=self.dIc)
+            c.render_backward_principled(self.scene, self.albedo, self.rough, self.metallic, self.normal, self.P,
+                                         self.view, self.params, self.spp, self.bounces, s, self.Ec, self.Ic,
+                                         self.dIc, dIp=self.G)
+        self.history[k].copy_(self.loss[0])
         c.adam(self.P, self.G, self.M, self.V, k + 1, lr=self.lr, lo=0.0, hi=1.0)
 
     def _loop(self):

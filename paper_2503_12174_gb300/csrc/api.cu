@@ -872,6 +872,80 @@ dpcs_status dpcs_render_loss_backward(dpcs_ctx *c, dpcs_scene scene, const float
     return check_launch(c, nl, "render_loss_backward");
 }
 
+dpcs_status dpcs_render_loss_backward_principled(dpcs_ctx *c, dpcs_scene scene, const dpcs_material *mat,
+                                                 const float *Ip, const dpcs_view *view, const dpcs_params *params,
+                                                 int32_t spp, int32_t bounces, uint64_t seed, const float *target,
+                                                 int32_t loss_kind, float scale, float *Ic, float *Ec, float *loss,
+                                                 float *dIp, float *dAlbedo, float *dRough, float *dMetallic,
+                                                 float *dNormal, float *dParams, void *stream) {
+    Range range("dpcs_render_loss_backward_principled");
+    if (!c) return DPCS_ERR_INVALID_ARG;
+    if (!mat) return fail(c, DPCS_ERR_INVALID_ARG, "null material");
+    RenderArgs a;
+    Scene *sc = nullptr;
+    dpcs_status s = prepare(c, scene, mat->albedo, mat->rough, mat->Ht, mat->Wt, Ip, view, params, spp, bounces, seed,
+                            a, &sc);
+    if (s) return s;
+    if (!target || !Ic || !loss) return fail(c, DPCS_ERR_INVALID_ARG, "null target, Ic or loss");
+    if ((loss_kind != 0 && loss_kind != 1) || !(scale > 0.0f))
+        return fail(c, DPCS_ERR_INVALID_ARG, "loss_kind must be 0 (L2) or 1 (L1) and scale > 0");
+    if (dMetallic && !mat->metallic) return fail(c, DPCS_ERR_INVALID_ARG, "dMetallic given without a metallic map");
+    if (dNormal && !mat->normal) return fail(c, DPCS_ERR_INVALID_ARG, "dNormal given without a normal map");
+    if ((s = set_device(c))) return s;
+    const int64_t np = (int64_t)view->Hp * view->Wp, nt = (int64_t)mat->Ht * mat->Wt;
+    const int64_t npix = (int64_t)view->Hc * view->Wc;
+    const int L = 1 << a.log2L;
+    const int spl = (spp + L - 1) / L;  // samples per lane
+    const bool fused = spl <= kFusedSamples && spl * bounces <= kFusedRecs;
+    const bool want_tex = dAlbedo || dRough, want_mat = dMetallic || dNormal;
+    if ((s = ensure(c, c->ep4, (size_t)np * 16, "Ep scratch")) ||
+        (s = ensure(c, c->tex4, (size_t)nt * 16, "texture scratch")) ||
+        (s = ensure(c, c->mat4, (size_t)nt * 16, "material scratch")) ||
+        (s = ensure(c, c->dEp4, (size_t)np * 16, "dEp scratch")) ||
+        (s = ensure(c, c->acc, 16 * sizeof(double), "parameter accumulators")) ||
+        (want_tex && (s = ensure(c, c->dtex4, (size_t)nt * 16, "dtex scratch"))) ||
+        (want_mat && (s = ensure(c, c->dmat4, (size_t)nt * 16, "dmat scratch"))) ||
+        (!fused && ((s = ensure(c, c->gE, (size_t)npix * 12, "dEc scratch")) ||
+                    (s = ensure(c, c->pix, (size_t)npix * 24, "per-pixel loss scratch")))))
+        return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    double *acc = (double *)c->acc.p;
+    cudaMemsetAsync(acc, 0, 16 * sizeof(double), st);
+    cudaMemsetAsync(c->dEp4.p, 0, (size_t)np * 16, st);
+    if (want_tex) cudaMemsetAsync(c->dtex4.p, 0, (size_t)nt * 16, st);
+    if (want_mat) cudaMemsetAsync(c->dmat4.p, 0, (size_t)nt * 16, st);
+    int nl = launch_prf(Ip, np, params->gamma_p, params->gain_p, (float4 *)c->ep4.p, st);
+    nl += launch_pack_tex(mat->albedo, mat->rough, nt, (float4 *)c->tex4.p, st);
+    nl += launch_pack_mat(mat->metallic, mat->normal, nt, (float4 *)c->mat4.p, st);
+    a.Ep = (const float4 *)c->ep4.p;
+    a.tex = (const float4 *)c->tex4.p;
+    a.Ic = Ic;
+    a.dEp = (float4 *)c->dEp4.p;
+    a.dtex = want_tex ? (float4 *)c->dtex4.p : nullptr;
+    const float4 *m4 = (const float4 *)c->mat4.p;
+    float4 *dm4 = want_mat ? (float4 *)c->dmat4.p : nullptr;
+    const LossArgs l{target, scale, loss_kind, acc};
+    if (fused) {
+        a.Ec = Ec;
+        nl += launch_render_grad_pbr(a, m4, dm4, l, st);
+    } else {  // render, per-pixel loss, Eq. 5 adjoint, replay
+        float *dIc = (float *)c->pix.p, *ec = Ec ? Ec : (float *)c->pix.p + 3 * npix;
+        a.Ec = ec;
+        nl += launch_render_pbr(a, m4, st);
+        nl += launch_pixel_loss(Ic, npix * 3, l, dIc, st);
+        nl += launch_crf_backward(dIc, ec, Ic, npix, params->gamma_c, params->gain_c, params->wb, (float *)c->gE.p,
+                                  acc, st);
+        a.gE = (const float *)c->gE.p;
+        nl += launch_replay_pbr(a, m4, dm4, st);
+    }
+    nl += launch_loss_out(acc, loss, st);
+    nl += launch_prf_backward(Ip, (const float4 *)c->dEp4.p, np, params->gamma_p, params->gain_p, dIp, acc, st);
+    if (want_tex) nl += launch_tex_backward((const float4 *)c->dtex4.p, nt, dAlbedo, dRough, st);
+    if (want_mat) nl += launch_mat_backward((const float4 *)c->dmat4.p, nt, dMetallic, dNormal, st);
+    if (dParams) nl += launch_finalize_params(acc, dParams, st);
+    return check_launch(c, nl, "render_loss_backward_principled");
+}
+
 dpcs_status dpcs_l2_loss(dpcs_ctx *c, const float *Ic, const float *target, int64_t n, float *dIc, float *loss,
                          void *stream) {
     if (!c) return DPCS_ERR_INVALID_ARG;

@@ -119,6 +119,7 @@ int launch_pack_mat(const float *metallic, const float *normal, int64_t ntex, fl
 int launch_render_pbr(const RenderArgs &a, const float4 *mat, cudaStream_t st);
 int launch_replay_pbr(const RenderArgs &a, const float4 *mat, float4 *dmat, cudaStream_t st);
 int launch_mat_backward(const float4 *dmat, int64_t ntex, float *dMetallic, float *dNormal, cudaStream_t st);
+int launch_render_grad_pbr(const RenderArgs &a, const float4 *mat, float4 *dmat, const LossArgs &l, cudaStream_t st);
 int launch_render_keep(const RenderArgs &a, void *chunks, uint8_t *nvs, cudaStream_t st);
 int launch_sweep_kept(const RenderArgs &a, const void *chunks, const uint8_t *nvs, cudaStream_t st);
 constexpr int kRecWordsHost = 24;  // 32-bit words of one kept vertex record (VRec)

@@ -18,8 +18,10 @@
 // same xor-shuffle pixel sum) with this material; k_replay_pbr re-traces the
 // paths, records each vertex and runs the reverse sweep with the material's
 // derivatives (detached sampling: sampled directions and pdfs fixed);
-// k_mat_backward adds the metallic and normal-map gradients to the caller's
-// buffers.
+// k_render_grad_pbr traces once for losses that act on each pixel alone (as
+// k_render_grad does for the plain material): forward with records, the
+// pixel's loss gradient through Eq. 5, then the sweeps; k_mat_backward adds
+// the metallic and normal-map gradients to the caller's buffers.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -313,19 +315,51 @@ __device__ __forceinline__ void prec_vertex(PRec &R, const PSurf &S, f3 beta) {
     R.inv_ulen = S.inv_ulen;
 }
 
+// NV floats summed over the block into FP64 accumulators
+template <int NV>
+__device__ __forceinline__ void pblock_reduce_add(float (&v)[NV], double *acc) {
+    __shared__ float red[NV][kPBlock / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k)
+        for (int off = 16; off; off >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], off);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < NV; ++k) red[k][w] = v[k];
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        float s = 0.0f;
+        for (int j = 0; j < (int)(blockDim.x >> 5); ++j) s += red[threadIdx.x][j];
+        if (s != 0.0f) atomicAdd(acc + threadIdx.x, (double)s);
+    }
+}
+
+__device__ __forceinline__ float pcrf(float ec, float gain, float wb, float gamma) {
+    const float v = gain * wb * ec;
+    return v > 0.0f ? powf(v, gamma) : 0.0f;
+}
+
 // One warp-synchronous pass over a lane's samples, as k_render and k_replay
 // run them: each iteration traces one ray (extension or shadow) per lane,
-// and the warp starts its next samples together.  kReplay = false: sum the
-// lit contributions and write Ec / Ic; true: record the vertices and sweep.
-template <bool kReplay>
+// and the warp starts its next samples together.  kMode 0: sum the lit
+// contributions and write Ec / Ic; 1: record the vertices and sweep each
+// path with the pixel's dLoss/dEc from a.gE; 2: record the vertices of up to
+// kFusedSamples samples, then form the pixel's loss gradient (loss l) and
+// sweep them all.
+constexpr int kModeRender = 0, kModeReplay = 1, kModeFused = 2;
+template <int kMode>
 __device__ __forceinline__ void pbr_lanes(const RenderArgs &a, const float4 *__restrict__ mat,
-                                          float4 *__restrict__ dmat, int64_t pix, int sl, bool valid) {
+                                          float4 *__restrict__ dmat, int64_t pix, int sl, bool valid,
+                                          const LossArgs *l) {
+    constexpr bool kReplay = kMode != kModeRender;
     const int L = 1 << a.log2L;
     Cnt cnt;
     f3 sum = mk3(0.f, 0.f, 0.f);
     float gb_in[3] = {0.f, 0.f, 0.f};
     bool any = true;
-    if (kReplay) {
+    int k = 0;  // samples this lane has finished (kModeFused)
+    int nvs[kMode == kModeFused ? kFusedSamples : 1];
+    if (kMode == kModeReplay) {
         const float inv = 1.0f / (float)a.spp;
         if (valid) {
             gb_in[0] = a.gE[3 * pix] * inv;
@@ -343,7 +377,7 @@ __device__ __forceinline__ void pbr_lanes(const RenderArgs &a, const float4 *__r
     float tmax = INFINITY;
     Trav st;
     int stack[kStack];
-    PRec rec[kReplay ? DPCS_MAX_BOUNCES : 1];
+    PRec rec[kMode == kModeRender ? 1 : (kMode == kModeReplay ? DPCS_MAX_BOUNCES : kFusedRecs)];
     if (s < a.spp && a.bounces > 0) {
         f3 o, d;
         camera_ray(a, (uint32_t)pix, (uint32_t)s, o, d);
@@ -356,6 +390,7 @@ __device__ __forceinline__ void pbr_lanes(const RenderArgs &a, const float4 *__r
     const int64_t max_iter = ((int64_t)(a.spp / L + 1) * (2 * a.bounces + 1)) * (2 * (int64_t)a.T + 18);
     int64_t iter = 0;
     while (s < a.spp) {
+        PRec *rs = rec + (kMode == kModeFused ? k * a.bounces : 0);  // this sample's records
         while (true) {
             if (++iter > max_iter) {
                 atomicOr(a.status, kStatusTraversalLimit);
@@ -379,9 +414,9 @@ __device__ __forceinline__ void pbr_lanes(const RenderArgs &a, const float4 *__r
             bool end = false;
             if (shadow) {
                 if (hit) {
-                    if (kReplay) rec[nv - 1].G = 0.0f;  // occluded
+                    if (kReplay) rs[nv - 1].G = 0.0f;  // occluded
                 } else {
-                    if (!kReplay) sum = sum + c;
+                    if (kMode != kModeReplay) sum = sum + c;
                     cnt.add(kCntLit);
                 }
                 shadow = false;
@@ -396,7 +431,7 @@ __device__ __forceinline__ void pbr_lanes(const RenderArgs &a, const float4 *__r
             } else {
                 cnt.add(kCntVert);
                 const PSurf S = psurface_at(a, mat, st.h, ray.d);
-                PRec *R = kReplay ? &rec[nv++] : nullptr;
+                PRec *R = kReplay ? &rs[nv++] : nullptr;
                 if (kReplay) prec_vertex(*R, S, beta);
                 PNee N;
                 const bool cand = pnee_prepare(a, S, N);
@@ -446,7 +481,9 @@ __device__ __forceinline__ void pbr_lanes(const RenderArgs &a, const float4 *__r
             }
             if (end) break;
         }
-        if (kReplay) psweep(a, dmat, rec, nv, gb_in);
+        if (kMode == kModeReplay) psweep(a, dmat, rec, nv, gb_in);
+        if (kMode == kModeFused) nvs[k < kFusedSamples ? k : kFusedSamples - 1] = nv;
+        ++k;
         nv = 0;
         s += L;
         if (s < a.spp) {
@@ -461,6 +498,43 @@ __device__ __forceinline__ void pbr_lanes(const RenderArgs &a, const float4 *__r
         }
     }
     cnt.flush(a.counters);
+    if (kMode == kModeFused) {
+        // every lane of a pixel ends with the pixel's sum (the tree below)
+        for (int off = L >> 1; off > 0; off >>= 1) {
+            sum.x += __shfl_xor_sync(0xffffffffu, sum.x, off);
+            sum.y += __shfl_xor_sync(0xffffffffu, sum.y, off);
+            sum.z += __shfl_xor_sync(0xffffffffu, sum.z, off);
+        }
+        const float inv = 1.0f / (float)a.spp;
+        const float ec[3] = {sum.x * inv, sum.y * inv, sum.z * inv};
+        float v[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // gamma_c(3), Gc, wb(3), loss
+        if (valid) {
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                const float ic = pcrf(ec[j], a.gain_c, a.wb[j], a.gamma_c[j]);
+                if (sl == 0) {
+                    if (a.Ec) a.Ec[3 * pix + j] = ec[j];
+                    a.Ic[3 * pix + j] = ic;
+                }
+                const float d = ic - l->target[3 * pix + j];
+                const float g = l->kind == 0 ? l->scale * d : (d > 0.0f ? l->scale : (d < 0.0f ? -l->scale : 0.0f));
+                const float w = a.gain_c * a.wb[j] * ec[j];
+                if (w > 0.0f) {
+                    const float da = a.gamma_c[j] * powf(w, a.gamma_c[j] - 1.0f);
+                    gb_in[j] = g * da * a.gain_c * a.wb[j] * inv;
+                    if (sl == 0) {
+                        v[j] += g * ic * logf(w);
+                        v[3] += g * da * a.wb[j] * ec[j];
+                        v[4 + j] += g * da * a.gain_c * ec[j];
+                    }
+                }
+                if (sl == 0) v[7] += l->kind == 0 ? 0.5f * l->scale * d * d : l->scale * fabsf(d);
+            }
+        }
+        pblock_reduce_add<8>(v, l->acc + 4);  // acc[4..10]: gamma_c, Gc, wb; acc[11]: the loss
+        if (gb_in[0] != 0.0f || gb_in[1] != 0.0f || gb_in[2] != 0.0f)
+            for (int i = 0; i < k && i < kFusedSamples; ++i) psweep(a, dmat, rec + i * a.bounces, nvs[i], gb_in);
+    }
     if (!kReplay) {
         for (int off = L >> 1; off > 0; off >>= 1) {
             sum.x += __shfl_xor_sync(0xffffffffu, sum.x, off);
@@ -488,14 +562,26 @@ __device__ __forceinline__ void pbr_lanes(const RenderArgs &a, const float4 *__r
 __global__ void __launch_bounds__(kPBlock, DPCS_PBR_MINB) k_render_pbr(const RenderArgs a, const float4 *__restrict__ mat) {
     const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t pix = gt >> a.log2L;
-    pbr_lanes<false>(a, mat, nullptr, pix, (int)(gt & ((1 << a.log2L) - 1)), pix < (int64_t)a.Hc * a.Wc);
+    pbr_lanes<kModeRender>(a, mat, nullptr, pix, (int)(gt & ((1 << a.log2L) - 1)), pix < (int64_t)a.Hc * a.Wc,
+                           nullptr);
+}
+
+// render + per-pixel loss + adjoint in one trace; the host calls it only
+// when ceil(spp / L) <= kFusedSamples and ceil(spp / L) * bounces <= kFusedRecs
+__global__ void __launch_bounds__(kPBlock, DPCS_PBR_MINB)
+    k_render_grad_pbr(const RenderArgs a, const float4 *__restrict__ mat, float4 *__restrict__ dmat,
+                      const LossArgs l) {
+    const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t pix = gt >> a.log2L;
+    pbr_lanes<kModeFused>(a, mat, dmat, pix, (int)(gt & ((1 << a.log2L) - 1)), pix < (int64_t)a.Hc * a.Wc, &l);
 }
 
 __global__ void __launch_bounds__(kPBlock, DPCS_PBR_MINB) k_replay_pbr(const RenderArgs a, const float4 *__restrict__ mat,
                                                         float4 *__restrict__ dmat) {
     const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t pix = gt >> a.log2L;
-    pbr_lanes<true>(a, mat, dmat, pix, (int)(gt & ((1 << a.log2L) - 1)), pix < (int64_t)a.Hc * a.Wc);
+    pbr_lanes<kModeReplay>(a, mat, dmat, pix, (int)(gt & ((1 << a.log2L) - 1)), pix < (int64_t)a.Hc * a.Wc,
+                           nullptr);
 }
 
 __global__ void k_pack_mat(const float *__restrict__ metallic, const float *__restrict__ normal, int64_t ntex,
@@ -540,6 +626,14 @@ int launch_replay_pbr(const RenderArgs &a, const float4 *mat, float4 *dmat, cuda
     const int64_t threads = ((int64_t)a.Hc * a.Wc) << a.log2L;
     if (threads <= 0) return 0;
     k_replay_pbr<<<grid1(threads, kPBlock), kPBlock, 0, st>>>(a, mat, dmat);
+    return 1;
+}
+
+int launch_render_grad_pbr(const RenderArgs &a, const float4 *mat, float4 *dmat, const LossArgs &l,
+                           cudaStream_t st) {
+    const int64_t threads = ((int64_t)a.Hc * a.Wc) << a.log2L;
+    if (threads <= 0) return 0;
+    k_render_grad_pbr<<<grid1(threads, kPBlock), kPBlock, 0, st>>>(a, mat, dmat, l);
     return 1;
 }
 

@@ -36,7 +36,7 @@ EXPORTED = [
     "dpcs_probe_l2_load", "dpcs_probe_atomic4", "dpcs_gbuffer", "dpcs_denoise", "dpcs_denoise_backward",
     "dpcs_l1_loss", "dpcs_tv_loss", "dpcs_scene_update", "dpcs_render_loss_backward", "dpcs_render_keep",
     "dpcs_render_backward_kept", "dpcs_render_principled", "dpcs_render_backward_principled",
-    "dpcs_scene_transform",
+    "dpcs_scene_transform", "dpcs_render_loss_backward_principled",
 ]
 
 DPCS_REQ_RELIGHT = 0
@@ -148,6 +148,11 @@ _SIGS = {
                                                          ctypes.POINTER(DpcsView), ctypes.POINTER(DpcsParams),
                                                          ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, _P, _P, _P,
                                                          _P, _P, _P, _P, _P, _P, _P]),
+    "dpcs_render_loss_backward_principled": (ctypes.c_int32, [_P, ctypes.c_uint64, ctypes.POINTER(DpcsMaterial), _P,
+                                                              ctypes.POINTER(DpcsView), ctypes.POINTER(DpcsParams),
+                                                              ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, _P,
+                                                              ctypes.c_int32, ctypes.c_float, _P, _P, _P, _P, _P, _P,
+                                                              _P, _P, _P, _P]),
     "dpcs_timing_enable": (ctypes.c_int32, [_P, ctypes.c_int32]),
     "dpcs_timing_read": (ctypes.c_int32, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_int64)]),
@@ -715,6 +720,35 @@ class Context:
             _ptr(dRough, "dRough", (Ht, Wt), f32, self.device, allow_none=True),
             _ptr(dParams, "dParams", (11,), f32, self.device, allow_none=True), _stream(stream))
         self.check(st, "render_loss_backward")
+        return Ic
+
+    def render_loss_backward_principled(self, scene: int, albedo, rough, metallic, normal, Ip, view: DpcsView,
+                                        params: DpcsParams, spp: int, bounces: int, seed: int, target, loss,
+                                        loss_kind: int = 0, scale: float = 1.0, Ic=None, Ec=None, dIp=None,
+                                        dAlbedo=None, dRough=None, dMetallic=None, dNormal=None, dParams=None,
+                                        stream=None):
+        """render_loss_backward with the principled material (metallic / normal maps, either None); returns Ic."""
+        import torch
+
+        f32 = torch.float32
+        mat = self._material(albedo, rough, metallic, normal)
+        Ht, Wt = mat.Ht, mat.Wt
+        img = (view.Hc, view.Wc, 3)
+        if Ic is None:
+            Ic = torch.empty(img, dtype=f32, device=self.device)
+        st = self.lib.dpcs_render_loss_backward_principled(
+            self.handle, scene, ctypes.byref(mat), _ptr(Ip, "Ip", (view.Hp, view.Wp, 3), f32, self.device),
+            ctypes.byref(view), ctypes.byref(params), int(spp), int(bounces), int(seed) & (2**64 - 1),
+            _ptr(target, "target", img, f32, self.device), int(loss_kind), float(scale),
+            _ptr(Ic, "Ic", img, f32, self.device), _ptr(Ec, "Ec", img, f32, self.device, allow_none=True),
+            _ptr(loss, "loss", (1,), f32, self.device),
+            _ptr(dIp, "dIp", (view.Hp, view.Wp, 3), f32, self.device, allow_none=True),
+            _ptr(dAlbedo, "dAlbedo", (Ht, Wt, 3), f32, self.device, allow_none=True),
+            _ptr(dRough, "dRough", (Ht, Wt), f32, self.device, allow_none=True),
+            _ptr(dMetallic, "dMetallic", (Ht, Wt), f32, self.device, allow_none=True),
+            _ptr(dNormal, "dNormal", (Ht, Wt, 3), f32, self.device, allow_none=True),
+            _ptr(dParams, "dParams", (11,), f32, self.device, allow_none=True), _stream(stream))
+        self.check(st, "render_loss_backward_principled")
         return Ic
 
     def l1_loss(self, Ic, target, dIc, loss, scale: float = 1.0, stream=None):

@@ -21,8 +21,9 @@ gamma_c [1/3, 1], w [0.2, 2.5] (Sec. 3.2).
 Without the denoiser each pair's render, L1 term and adjoint are one call
 that traces its paths once (``Context.render_loss_backward``); with it, the
 render keeps its path records and the adjoint sweeps them.  ``fused=False``
-makes separate calls that trace twice, and so does the principled material
-(dpcs_render_principled, then dpcs_render_backward_principled).  Every step
+makes separate calls that trace twice.  The principled material takes the
+same route without the denoiser (``render_loss_backward_principled``) and
+separate calls with it (render, D, L1, D^T, replay).  Every step
 runs in the library's kernels; the only host traffic per step is reading
 back the 11 response parameters the next renders take by value (and, with
 the pose, the 13 K data terms of its differences).
@@ -159,6 +160,13 @@ class SceneFit:
     def _pair_principled(self, Ip, target, s, i):
         """One pair with the principled material: render, (D,) L1, adjoint with every map's gradient."""
         c = self.ctx
+        if self.denoise is None and self.fused:  # one trace of the paths
+            c.render_loss_backward_principled(self.scene, self.albedo, self.rough, self.metallic, self.normal, Ip,
+                                              self.view, self.params, self.spp, self.bounces, s, target,
+                                              self.losses[i:i + 1], loss_kind=1, scale=self.scale, Ic=self.Ic,
+                                              Ec=self.Ec, dAlbedo=self.gA, dRough=self.gR, dMetallic=self.gM,
+                                              dNormal=self.gN, dParams=self.gP if self.fit_params else None)
+            return
         c.render_principled(self.scene, self.albedo, self.rough, self.metallic, self.normal, Ip, self.view,
                             self.params, self.spp, self.bounces, s, Ic=self.Ic, Ec=self.Ec)
         if self.denoise is None:

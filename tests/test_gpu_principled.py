@@ -171,3 +171,45 @@ def test_principled_full_size_sampled_pixels(orc):
     assert ok, info
     ok, info = pixel_parity(Ic[px], rIc, atol=crf_atol(sc, rEc))
     assert ok, info
+
+
+def test_principled_degenerate_inputs(orc):
+    """No bounces, a dark projector, an empty scene and a one-pixel camera
+    with one sample: the principled calls return what the oracle returns
+    (zeros where nothing is lit) and their adjoints stay finite."""
+    torch = need_cuda()
+    sc = scenes.with_principled(scenes.corner(res=16, tex=16, spp=3, bounces=2, seed=4), seed=2)
+    g = GpuScene(sc)
+    try:
+        m, n = _maps(g, sc)
+        Ec, Ic = g.ctx.render_principled(g.handle, g.albedo, g.rough, m, n, g.Ip, g.view, g.params, 3, 0, 1,
+                                         Ec=torch.empty((sc.Hc, sc.Wc, 3), device=g.ctx.device))
+        g.ctx.sync()
+        assert not Ec.any() and not Ic.any()
+        Ec, Ic = g.ctx.render_principled(g.handle, g.albedo, g.rough, m, n, torch.zeros_like(g.Ip), g.view,
+                                         g.params, 3, 2, 1, Ec=torch.empty((sc.Hc, sc.Wc, 3), device=g.ctx.device))
+        dM, dN = torch.zeros_like(m), torch.zeros_like(n)
+        g.ctx.render_backward_principled(g.handle, g.albedo, g.rough, m, n, torch.zeros_like(g.Ip), g.view,
+                                         g.params, 3, 2, 1, Ec, Ic, torch.ones_like(Ic), dMetallic=dM, dNormal=dN)
+        g.ctx.sync()
+        assert not Ec.any() and not dM.any() and not dN.any()
+    finally:
+        g.close()
+    one = sc.replace(Hc=1, Wc=1, Kc=scenes.intrinsics(1, 1, 40.0), spp=1)
+    g = GpuScene(one)
+    try:
+        m, n = _maps(g, one)
+        Ec, Ic = _render(g, one, m, n)
+        rE, _ = orc.render(one)
+        np.testing.assert_allclose(Ec.cpu().numpy(), rE, rtol=1e-4, atol=1e-7)
+    finally:
+        g.close()
+    empty = sc.replace(verts=np.zeros((0, 3), np.float32), tris=np.zeros((0, 3), np.int32),
+                       uv=np.zeros((0, 2), np.float32))
+    g = GpuScene(empty)
+    try:
+        m, n = _maps(g, empty)
+        Ec, Ic = _render(g, empty, m, n)
+        assert not Ec.any()
+    finally:
+        g.close()
