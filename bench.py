@@ -777,6 +777,14 @@ def main():
                                            cs.seed + step_no[0], cEc, cIc, dIc, dIp=G)
             ctx.adam(P, G, M, V, step_no[0], lr=1e-2)
 
+        def pbr_step_fused():  # the same step in one trace: render, L2 loss and adjoint, then Adam
+            step_no[0] += 1
+            G.zero_()
+            ctx.render_loss_backward_principled(hc, calb, crough, cpm, cpn, P, cview, cprm, cs.spp, cs.bounces,
+                                                cs.seed + step_no[0], target, loss, loss_kind=0, Ic=cIc, Ec=cEc,
+                                                dIp=G)
+            ctx.adam(P, G, M, V, step_no[0], lr=1e-2)
+
         def pbr_all():  # one fitting pass: every material gradient (albedo, roughness, metallic, normal map)
             ctx.render_principled(hc, calb, crough, cpm, cpn, P, cview, cprm, cs.spp, cs.bounces, cs.seed,
                                   Ic=cIc, Ec=cEc)
@@ -785,6 +793,7 @@ def main():
 
         res = {}
         for name, fn, n_samp in (("fwd", pbr_fwd, sc.n_samples), ("fwd_bwd", pbr_step, cs.n_samples),
+                                 ("fwd_bwd_fused", pbr_step_fused, cs.n_samples),
                                  ("fwd_bwd_material", pbr_all, cs.n_samples)):
             for k in range(args.warmup):
                 flush(k)
@@ -803,7 +812,8 @@ def main():
             res[name] = {"value": n_samp * ws / (ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": ms}
         pbr_out = {"workload": f"principled material (metallic map + normal map): fwd = corner {sc.Hc}x{sc.Wc}, "
                                f"{sc.spp} spp, {sc.bounces} bounces; fwd_bwd = compensation step at {cs.Hc}x{cs.Wc}, "
-                               f"{cs.spp} spp (render, L2 loss, replay adjoint to Ip, Adam); fwd_bwd_material = "
+                               f"{cs.spp} spp (render, L2 loss, replay adjoint to Ip, Adam); fwd_bwd_fused = the same step "
+                               "in one trace (dpcs_render_loss_backward_principled); fwd_bwd_material = "
                                "render + replay with albedo, roughness, metallic and normal-map gradients",
                    **res}
 
