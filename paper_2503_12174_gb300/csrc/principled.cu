@@ -390,7 +390,8 @@ __device__ __forceinline__ void pbr_lanes(const RenderArgs &a, const float4 *__r
     const int64_t max_iter = ((int64_t)(a.spp / L + 1) * (2 * a.bounces + 1)) * (2 * (int64_t)a.T + 18);
     int64_t iter = 0;
     while (s < a.spp) {
-        PRec *rs = rec + (kMode == kModeFused ? k * a.bounces : 0);  // this sample's records
+        // this sample's records (the host keeps k < kFusedSamples and k * bounces + nv < kFusedRecs)
+        PRec *rs = rec + (kMode == kModeFused ? min(k, kFusedSamples - 1) * a.bounces : 0);
         while (true) {
             if (++iter > max_iter) {
                 atomicOr(a.status, kStatusTraversalLimit);
