@@ -48,6 +48,12 @@ L2_FLUSH_BYTES = 256 << 20
 # the kernel sources it was measured on; once they change, the roofline's
 # traffic is reported as null until a new capture is taken.
 RENDER_TRAFFIC = {"bytes": 36724736, "sources_sha256": "7e2cfcba363a44384f6a98b48b89053c847a717d32acc2def29ee65c2981c67d"}
+# Warp instructions one k_render launch of the forward workload issues, and
+# the active lanes per instruction, from the same ncu capture
+# (smsp__inst_executed.sum, smsp__thread_inst_executed_per_inst_executed);
+# reported while the kernel sources keep this hash.
+RENDER_ISSUE = {"warp_instructions": 1879286116, "lanes_per_instruction": 12.08,
+                "sources_sha256": "7e2cfcba363a44384f6a98b48b89053c847a717d32acc2def29ee65c2981c67d"}
 KERNEL_SOURCES = ("paper_2503_12174_gb300/csrc/render.cu", "paper_2503_12174_gb300/csrc/device.cuh",
                   "paper_2503_12174_gb300/csrc/internal.h")
 
@@ -503,6 +509,19 @@ def main():
                 "flops_per_launch": flops, "kernel_ms": kernel_ms,
                 "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 FLOP/FMA x {sm_max_mhz:.0f} MHz (max SM clock)",
                 "counts_per_launch": counts}
+    roof_issue = None
+    if RENDER_ISSUE["sources_sha256"] == kernel_sources_sha256():
+        # instruction issue: each SM sub-partition issues at most one warp
+        # instruction per cycle, four per SM
+        inst = RENDER_ISSUE["warp_instructions"]
+        issue_peak = 4 * sms * sm_max_mhz * 1e6 / 1e9
+        issue = inst / (kernel_ms / 1e3) / 1e9
+        roof_issue = {"bound": "issue", "kernel": "k_render", "achieved": issue, "peak": issue_peak,
+                      "unit": "G warp-instructions/s", "frac": issue / issue_peak, "kernel_ms": kernel_ms,
+                      "warp_instructions_per_launch": inst,
+                      "lanes_per_instruction": RENDER_ISSUE["lanes_per_instruction"],
+                      "peak_basis": f"{sms} SMs x 4 schedulers x 1 warp-instruction/cycle x {sm_max_mhz:.0f} MHz",
+                      "source": "instruction count of one launch from ncu (profiles/k_render_corner256.md)"}
 
     # ------------------------------------------------------------ full compensation (Eq. 13): eager vs CUDA graph
     comp_out = None
@@ -882,6 +901,7 @@ def main():
             "roofline": roof,
             "roofline_load": roof_load,
             "roofline_atomic": roof_atomic,
+            "roofline_issue": roof_issue,
             "compensation": comp_out,
             "denoise": den_out,
             "fit": fit_out,
