@@ -12,7 +12,9 @@ finite differences of the FP64 forward.
 * one bounce is affine in the metallic map, and a metal of albedo f0 is the
   specular lobe alone;
 * the adjoint's metallic, albedo, roughness and normal-map gradients match
-  central differences wherever those parameters do not move sampled paths.
+  central differences wherever those parameters do not move sampled paths;
+* the sampler's mean weight f cos / pdf equals the quadrature of f cos
+  with metallic on, and stays <= 1.
 """
 import math
 
@@ -228,3 +230,34 @@ def test_adjoint_normal_map_and_roughness_fd_direct_only(orc):
     _check(orc, sc, W, g, "normal", "dnormal", rng)
     _check(orc, sc, W, g, "rough", "drough", rng)
     _check(orc, sc, W, g, "metallic", "dmetallic", rng)
+
+
+@pytest.mark.parametrize("m", [0.5, 1.0])
+def test_principled_mean_weight_is_directional_albedo(orc, m):
+    """E[f cos / pdf] over the sampler's directions equals the quadrature of
+    f cos over the hemisphere (the sampler and pdf are the plain BRDF's; f
+    carries the metallic Fresnel), and a metal of albedo <= 0.9 reflects no
+    more than it receives."""
+    rng = np.random.default_rng(8)
+    n = np.array([0.0, 0.0, 1.0])
+    wo = np.array([0.4, -0.2, 0.85])
+    wo /= np.linalg.norm(wo)
+    rho, r = np.array([0.9, 0.6, 0.3]), 0.45
+    nt, nph = 300, 600
+    th = (np.arange(nt) + 0.5) * np.pi / nt
+    ph = (np.arange(nph) + 0.5) * 2 * np.pi / nph
+    T, P = np.meshgrid(th, ph, indexing="ij")
+    d = np.stack([np.sin(T) * np.cos(P), np.sin(T) * np.sin(P), np.cos(T)], -1).reshape(-1, 3)
+    w = (np.sin(T) * (np.pi / nt) * (2 * np.pi / nph)).ravel()
+    fq = np.array([orc.pbr_eval(n, wo, di, rho, r, m, 1.0, 0.04)["f"] for di in d])
+    albedo = (fq * np.maximum(d[:, 2], 0)[:, None] * w[:, None]).sum(0)
+    N = 20000
+    u = rng.random((N, 3))
+    acc = np.zeros((N, 3))
+    for i in range(N):
+        ok, wi = orc.bsdf_sample(n, wo, r, 1.0, *u[i])
+        if ok:
+            acc[i] = orc.pbr_eval(n, wo, wi, rho, r, m, 1.0, 0.04)["f"] * wi[2] / orc.bsdf_pdf(n, wo, wi, r, 1.0)
+    se = acc.std(0) / np.sqrt(N)
+    assert np.all(np.abs(acc.mean(0) - albedo) < 4 * se + 1e-3), (acc.mean(0), albedo)
+    assert np.all(albedo <= 1.0)
