@@ -346,8 +346,9 @@ typedef struct dpcs_material {
 
 /*
  * dpcs_render_principled: dpcs_render with the principled material (same
- * view, parameters, sampling, determinism and errors; the fused, kept-record
- * and batched paths are not available for it).
+ * view, parameters, sampling, determinism and errors; the one-trace loss
+ * step and the kept records have principled variants below, the batched
+ * serving render has none).
  *
  * dpcs_render_backward_principled: its path-replay adjoint, as
  * dpcs_render_backward, adding (+=) also dLoss/dmetallic (Ht x Wt) and
@@ -366,6 +367,23 @@ dpcs_status dpcs_render_backward_principled(dpcs_ctx *ctx, dpcs_scene scene, con
                                             const float *Ic, const float *dIc, float *dIp, float *dAlbedo,
                                             float *dRough, float *dMetallic, float *dNormal, float *dParams,
                                             void *stream);
+
+/*
+ * dpcs_render_keep_principled / dpcs_render_backward_kept_principled:
+ * dpcs_render_keep and dpcs_render_backward_kept (same arguments, checks,
+ * memory and errors) with the principled material; the records are 208 B
+ * per recorded vertex.  A kept plain render does not serve the principled
+ * adjoint, nor the other way round (DPCS_ERR_INVALID_ARG).
+ */
+dpcs_status dpcs_render_keep_principled(dpcs_ctx *ctx, dpcs_scene scene, const dpcs_material *mat, const float *Ip,
+                                        const dpcs_view *view, const dpcs_params *params, int32_t spp,
+                                        int32_t bounces, uint64_t seed, float *Ic, float *Ec, void *stream);
+dpcs_status dpcs_render_backward_kept_principled(dpcs_ctx *ctx, dpcs_scene scene, const dpcs_material *mat,
+                                                 const float *Ip, const dpcs_view *view, const dpcs_params *params,
+                                                 int32_t spp, int32_t bounces, uint64_t seed, const float *Ec,
+                                                 const float *Ic, const float *dIc, float *dIp, float *dAlbedo,
+                                                 float *dRough, float *dMetallic, float *dNormal, float *dParams,
+                                                 void *stream);
 
 /*
  * dpcs_render_loss_backward_principled: dpcs_render_loss_backward (render,

@@ -17,7 +17,7 @@ scene's first hit through each pixel centre, computed once.
 
 With ``metallic`` / ``normal`` maps the scene uses the principled material
 of Sec. 3.2: the one-trace step is ``render_loss_backward_principled``, and
-with the denoiser the render and the replay are separate traces.
+with the denoiser the principled render keeps its path records as well.
 
 With ``graph=True`` the whole loop is captured once as a CUDA graph and then
 replayed.  The steps are unrolled in the graph, so every step keeps its own
@@ -108,8 +108,9 @@ class Compensation:
                                               self.view, self.params, self.spp, self.bounces, s, self.target,
                                               self.loss, loss_kind=0, Ic=self.Ic, Ec=self.Ec, dIp=self.G)
         else:
+            keep = self.denoise is not None and self.fused  # the filter couples pixels: keep the paths
             c.render_principled(self.scene, self.albedo, self.rough, self.metallic, self.normal, self.P, self.view,
-                                self.params, self.spp, self.bounces, s, Ic=self.Ic, Ec=self.Ec)
+                                self.params, self.spp, self.bounces, s, Ic=self.Ic, Ec=self.Ec, keep=keep)
             if self.denoise is None:
                 c.l2_loss(self.Ic, self.target, self.dIc, self.loss)
             else:
@@ -119,7 +120,7 @@ class Compensation:
                 c.denoise_backward(self.dD, self.guide, self.wsum, self.denoise, dIc=self.dIc)
             c.render_backward_principled(self.scene, self.albedo, self.rough, self.metallic, self.normal, self.P,
                                          self.view, self.params, self.spp, self.bounces, s, self.Ec, self.Ic,
-                                         self.dIc, dIp=self.G)
+                                         self.dIc, dIp=self.G, kept=keep)
         self.history[k].copy_(self.loss[0])
         c.adam(self.P, self.G, self.M, self.V, k + 1, lr=self.lr, lo=0.0, hi=1.0)
 

@@ -56,6 +56,7 @@ struct dpcs_ctx {
         bool valid = false;
         uint64_t scene = 0, seed = 0;
         int32_t Hc = 0, Wc = 0, spp = 0, bounces = 0, log2L = 0;
+        bool principled = false;  // records of dpcs_render_keep_principled
     } kept_key;
     // measurement support
     unsigned long long *counters = nullptr;  // 8 totals (DPCS_COUNTERS build)
@@ -756,6 +757,7 @@ dpcs_status dpcs_render_keep(dpcs_ctx *c, dpcs_scene scene, const float *albedo,
     c->kept_key.spp = spp;
     c->kept_key.bounces = bounces;
     c->kept_key.log2L = a.log2L;
+    c->kept_key.principled = false;
     return DPCS_OK;
 }
 
@@ -771,8 +773,8 @@ dpcs_status dpcs_render_backward_kept(dpcs_ctx *c, dpcs_scene scene, const float
     if (s) return s;
     if (!Ec || !Ic || !dIc) return fail(c, DPCS_ERR_INVALID_ARG, "null Ec, Ic or dIc");
     const auto &k = c->kept_key;
-    if (!k.valid || k.scene != scene || k.seed != seed || k.Hc != view->Hc || k.Wc != view->Wc || k.spp != spp ||
-        k.bounces != bounces || k.log2L != a.log2L)
+    if (!k.valid || k.principled || k.scene != scene || k.seed != seed || k.Hc != view->Hc || k.Wc != view->Wc ||
+        k.spp != spp || k.bounces != bounces || k.log2L != a.log2L)
         return fail(c, DPCS_ERR_INVALID_ARG, "render_backward_kept: no kept render with these arguments");
     if ((s = set_device(c))) return s;
     const int64_t np = (int64_t)view->Hp * view->Wp, nt = (int64_t)Ht * Wt, npix = (int64_t)view->Hc * view->Wc;
@@ -870,6 +872,110 @@ dpcs_status dpcs_render_loss_backward(dpcs_ctx *c, dpcs_scene scene, const float
     if (want_tex) nl += launch_tex_backward((const float4 *)c->dtex4.p, nt, dAlbedo, dRough, st);
     if (dParams) nl += launch_finalize_params(acc, dParams, st);
     return check_launch(c, nl, "render_loss_backward");
+}
+
+dpcs_status dpcs_render_keep_principled(dpcs_ctx *c, dpcs_scene scene, const dpcs_material *mat, const float *Ip,
+                                        const dpcs_view *view, const dpcs_params *params, int32_t spp,
+                                        int32_t bounces, uint64_t seed, float *Ic, float *Ec, void *stream) {
+    Range range("dpcs_render_keep_principled");
+    if (!c) return DPCS_ERR_INVALID_ARG;
+    if (!mat) return fail(c, DPCS_ERR_INVALID_ARG, "null material");
+    RenderArgs a;
+    Scene *sc = nullptr;
+    dpcs_status s = prepare(c, scene, mat->albedo, mat->rough, mat->Ht, mat->Wt, Ip, view, params, spp, bounces, seed,
+                            a, &sc);
+    if (s) return s;
+    if (!Ic) return fail(c, DPCS_ERR_INVALID_ARG, "null Ic");
+    if ((s = set_device(c))) return s;
+    const int64_t np = (int64_t)view->Hp * view->Wp, nt = (int64_t)mat->Ht * mat->Wt;
+    const int64_t npix = (int64_t)view->Hc * view->Wc;
+    const int L = 1 << a.log2L;
+    const int64_t nthr = npix << a.log2L, spl = (spp + L - 1) / L;
+    const size_t words = (size_t)kPRecWordsHost * spl * bounces * nthr * 4, counts = (size_t)spl * nthr;
+    c->kept_key.valid = false;
+    if ((s = ensure(c, c->ep4, (size_t)np * 16, "Ep scratch")) ||
+        (s = ensure(c, c->tex4, (size_t)nt * 16, "texture scratch")) ||
+        (s = ensure(c, c->mat4, (size_t)nt * 16, "material scratch")) ||
+        (s = ensure(c, c->kept, ((words + 255) & ~size_t(255)) + counts, "kept path records")))
+        return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    int nl = launch_prf(Ip, np, params->gamma_p, params->gain_p, (float4 *)c->ep4.p, st);
+    nl += launch_pack_tex(mat->albedo, mat->rough, nt, (float4 *)c->tex4.p, st);
+    nl += launch_pack_mat(mat->metallic, mat->normal, nt, (float4 *)c->mat4.p, st);
+    a.Ep = (const float4 *)c->ep4.p;
+    a.tex = (const float4 *)c->tex4.p;
+    a.Ic = Ic;
+    a.Ec = Ec;
+    char *kp = (char *)c->kept.p;
+    nl += launch_render_keep_pbr(a, (const float4 *)c->mat4.p, kp, (uint8_t *)(kp + ((words + 255) & ~size_t(255))),
+                                 st);
+    if ((s = check_launch(c, nl, "render_keep_principled"))) return s;
+    c->kept_key.valid = true;
+    c->kept_key.scene = scene;
+    c->kept_key.seed = seed;
+    c->kept_key.Hc = view->Hc;
+    c->kept_key.Wc = view->Wc;
+    c->kept_key.spp = spp;
+    c->kept_key.bounces = bounces;
+    c->kept_key.log2L = a.log2L;
+    c->kept_key.principled = true;
+    return DPCS_OK;
+}
+
+dpcs_status dpcs_render_backward_kept_principled(dpcs_ctx *c, dpcs_scene scene, const dpcs_material *mat,
+                                                 const float *Ip, const dpcs_view *view, const dpcs_params *params,
+                                                 int32_t spp, int32_t bounces, uint64_t seed, const float *Ec,
+                                                 const float *Ic, const float *dIc, float *dIp, float *dAlbedo,
+                                                 float *dRough, float *dMetallic, float *dNormal, float *dParams,
+                                                 void *stream) {
+    Range range("dpcs_render_backward_kept_principled");
+    if (!c) return DPCS_ERR_INVALID_ARG;
+    if (!mat) return fail(c, DPCS_ERR_INVALID_ARG, "null material");
+    RenderArgs a;
+    Scene *sc = nullptr;
+    dpcs_status s = prepare(c, scene, mat->albedo, mat->rough, mat->Ht, mat->Wt, Ip, view, params, spp, bounces, seed,
+                            a, &sc);
+    if (s) return s;
+    if (!Ec || !Ic || !dIc) return fail(c, DPCS_ERR_INVALID_ARG, "null Ec, Ic or dIc");
+    if (dMetallic && !mat->metallic) return fail(c, DPCS_ERR_INVALID_ARG, "dMetallic given without a metallic map");
+    if (dNormal && !mat->normal) return fail(c, DPCS_ERR_INVALID_ARG, "dNormal given without a normal map");
+    const auto &k = c->kept_key;
+    if (!k.valid || !k.principled || k.scene != scene || k.seed != seed || k.Hc != view->Hc || k.Wc != view->Wc ||
+        k.spp != spp || k.bounces != bounces || k.log2L != a.log2L)
+        return fail(c, DPCS_ERR_INVALID_ARG, "render_backward_kept_principled: no kept principled render with these "
+                                             "arguments");
+    if ((s = set_device(c))) return s;
+    const int64_t np = (int64_t)view->Hp * view->Wp, nt = (int64_t)mat->Ht * mat->Wt;
+    const int64_t npix = (int64_t)view->Hc * view->Wc;
+    const int L = 1 << a.log2L;
+    const int64_t nthr = npix << a.log2L, spl = (spp + L - 1) / L;
+    const size_t words = (size_t)kPRecWordsHost * spl * bounces * nthr * 4;
+    const bool want_tex = dAlbedo || dRough, want_mat = dMetallic || dNormal;
+    if ((s = ensure(c, c->gE, (size_t)npix * 12, "dEc scratch")) ||
+        (s = ensure(c, c->dEp4, (size_t)np * 16, "dEp scratch")) ||
+        (s = ensure(c, c->acc, 16 * sizeof(double), "parameter accumulators")) ||
+        (want_tex && (s = ensure(c, c->dtex4, (size_t)nt * 16, "dtex scratch"))) ||
+        (want_mat && (s = ensure(c, c->dmat4, (size_t)nt * 16, "dmat scratch"))))
+        return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    double *acc = (double *)c->acc.p;
+    cudaMemsetAsync(acc, 0, 16 * sizeof(double), st);
+    cudaMemsetAsync(c->dEp4.p, 0, (size_t)np * 16, st);
+    if (want_tex) cudaMemsetAsync(c->dtex4.p, 0, (size_t)nt * 16, st);
+    if (want_mat) cudaMemsetAsync(c->dmat4.p, 0, (size_t)nt * 16, st);
+    int nl = launch_crf_backward(dIc, Ec, Ic, npix, params->gamma_c, params->gain_c, params->wb, (float *)c->gE.p, acc,
+                                 st);
+    a.gE = (const float *)c->gE.p;
+    a.dEp = (float4 *)c->dEp4.p;
+    a.dtex = want_tex ? (float4 *)c->dtex4.p : nullptr;
+    const char *kp = (const char *)c->kept.p;
+    nl += launch_sweep_kept_pbr(a, kp, (const uint8_t *)(kp + ((words + 255) & ~size_t(255))),
+                                want_mat ? (float4 *)c->dmat4.p : nullptr, st);
+    nl += launch_prf_backward(Ip, (const float4 *)c->dEp4.p, np, params->gamma_p, params->gain_p, dIp, acc, st);
+    if (want_tex) nl += launch_tex_backward((const float4 *)c->dtex4.p, nt, dAlbedo, dRough, st);
+    if (want_mat) nl += launch_mat_backward((const float4 *)c->dmat4.p, nt, dMetallic, dNormal, st);
+    if (dParams) nl += launch_finalize_params(acc, dParams, st);
+    return check_launch(c, nl, "render_backward_kept_principled");
 }
 
 dpcs_status dpcs_render_loss_backward_principled(dpcs_ctx *c, dpcs_scene scene, const dpcs_material *mat,

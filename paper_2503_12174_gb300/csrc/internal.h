@@ -120,6 +120,10 @@ int launch_render_pbr(const RenderArgs &a, const float4 *mat, cudaStream_t st);
 int launch_replay_pbr(const RenderArgs &a, const float4 *mat, float4 *dmat, cudaStream_t st);
 int launch_mat_backward(const float4 *dmat, int64_t ntex, float *dMetallic, float *dNormal, cudaStream_t st);
 int launch_render_grad_pbr(const RenderArgs &a, const float4 *mat, float4 *dmat, const LossArgs &l, cudaStream_t st);
+// kept principled records: kPRecWordsHost 32-bit words per vertex
+constexpr int kPRecWordsHost = 52;
+int launch_render_keep_pbr(const RenderArgs &a, const float4 *mat, void *chunks, uint8_t *nvs, cudaStream_t st);
+int launch_sweep_kept_pbr(const RenderArgs &a, const void *chunks, const uint8_t *nvs, float4 *dmat, cudaStream_t st);
 int launch_render_keep(const RenderArgs &a, void *chunks, uint8_t *nvs, cudaStream_t st);
 int launch_sweep_kept(const RenderArgs &a, const void *chunks, const uint8_t *nvs, cudaStream_t st);
 constexpr int kRecWordsHost = 24;  // 32-bit words of one kept vertex record (VRec)

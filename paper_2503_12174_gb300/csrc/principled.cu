@@ -20,8 +20,11 @@
 // derivatives (detached sampling: sampled directions and pdfs fixed);
 // k_render_grad_pbr traces once for losses that act on each pixel alone (as
 // k_render_grad does for the plain material): forward with records, the
-// pixel's loss gradient through Eq. 5, then the sweeps; k_mat_backward adds
-// the metallic and normal-map gradients to the caller's buffers.
+// pixel's loss gradient through Eq. 5, then the sweeps; k_render_keep_pbr and
+// k_sweep_kept_pbr keep the records in device memory for losses that couple
+// pixels (the Eq. 11 filter), as k_render_keep / k_sweep_kept do;
+// k_mat_backward adds the metallic and normal-map gradients to the caller's
+// buffers.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -345,13 +348,18 @@ __device__ __forceinline__ float pcrf(float ec, float gain, float wb, float gamm
 // contributions and write Ec / Ic; 1: record the vertices and sweep each
 // path with the pixel's dLoss/dEc from a.gE; 2: record the vertices of up to
 // kFusedSamples samples, then form the pixel's loss gradient (loss l) and
-// sweep them all.
-constexpr int kModeRender = 0, kModeReplay = 1, kModeFused = 2;
+// sweep them all; 3: as 0, and store every vertex record to the kept buffer
+// (kchunks, 16-byte chunks laid out as the plain kept records, kernel
+// k_sweep_kept_pbr) and each sample's vertex count to knvs.
+constexpr int kModeRender = 0, kModeReplay = 1, kModeFused = 2, kModeKeep = 3;
 template <int kMode>
 __device__ __forceinline__ void pbr_lanes(const RenderArgs &a, const float4 *__restrict__ mat,
                                           float4 *__restrict__ dmat, int64_t pix, int sl, bool valid,
-                                          const LossArgs *l) {
-    constexpr bool kReplay = kMode != kModeRender;
+                                          const LossArgs *l, uint4 *__restrict__ kchunks = nullptr,
+                                          uint8_t *__restrict__ knvs = nullptr) {
+    constexpr bool kReplay = kMode != kModeRender;  // vertices are recorded
+    constexpr int kPChunks = (int)(sizeof(PRec) / 16);
+    constexpr int kGChunk = (int)(offsetof(PRec, G) / 16), kGWord = (int)(offsetof(PRec, G) % 16) / 4;
     const int L = 1 << a.log2L;
     Cnt cnt;
     f3 sum = mk3(0.f, 0.f, 0.f);
@@ -377,7 +385,10 @@ __device__ __forceinline__ void pbr_lanes(const RenderArgs &a, const float4 *__r
     float tmax = INFINITY;
     Trav st;
     int stack[kStack];
-    PRec rec[kMode == kModeRender ? 1 : (kMode == kModeReplay ? DPCS_MAX_BOUNCES : kFusedRecs)];
+    PRec rec[(kMode == kModeRender || kMode == kModeKeep) ? 1
+                                                           : (kMode == kModeReplay ? DPCS_MAX_BOUNCES : kFusedRecs)];
+    const int64_t nthr = ((int64_t)a.Hc * a.Wc) << a.log2L, gt = (pix << a.log2L) + sl;  // kModeKeep
+    const int spl = (a.spp + L - 1) / L;
     if (s < a.spp && a.bounces > 0) {
         f3 o, d;
         camera_ray(a, (uint32_t)pix, (uint32_t)s, o, d);
@@ -415,7 +426,13 @@ __device__ __forceinline__ void pbr_lanes(const RenderArgs &a, const float4 *__r
             bool end = false;
             if (shadow) {
                 if (hit) {
-                    if (kReplay) rs[nv - 1].G = 0.0f;  // occluded
+                    if (kMode == kModeKeep) {  // occluded: clear G of the stored record
+                        if (valid)
+                            __stcs(reinterpret_cast<unsigned *>(kchunks + kept_chunk(kGChunk, k, nv - 1, spl, a.bounces,
+                                                                                     nthr, gt)) + kGWord, 0u);
+                    } else if (kReplay) {
+                        rs[nv - 1].G = 0.0f;  // occluded
+                    }
                 } else {
                     if (kMode != kModeReplay) sum = sum + c;
                     cnt.add(kCntLit);
@@ -432,7 +449,8 @@ __device__ __forceinline__ void pbr_lanes(const RenderArgs &a, const float4 *__r
             } else {
                 cnt.add(kCntVert);
                 const PSurf S = psurface_at(a, mat, st.h, ray.d);
-                PRec *R = kReplay ? &rs[nv++] : nullptr;
+                PRec *R = kReplay ? &rs[kMode == kModeKeep ? 0 : nv] : nullptr;
+                if (kReplay) ++nv;
                 if (kReplay) prec_vertex(*R, S, beta);
                 PNee N;
                 const bool cand = pnee_prepare(a, S, N);
@@ -469,6 +487,12 @@ __device__ __forceinline__ void pbr_lanes(const RenderArgs &a, const float4 *__r
                         }
                     }
                 }
+                if (kMode == kModeKeep && valid) {  // the record, complete but for a later occlusion
+                    const uint4 *src = reinterpret_cast<const uint4 *>(R);
+#pragma unroll
+                    for (int q = 0; q < kPChunks; ++q)
+                        __stcs(kchunks + kept_chunk(q, k, nv - 1, spl, a.bounces, nthr, gt), src[q]);
+                }
                 if (cand) {
                     shadow = true;
                     ray = make_ray(N.so, N.sdir);
@@ -482,6 +506,7 @@ __device__ __forceinline__ void pbr_lanes(const RenderArgs &a, const float4 *__r
             }
             if (end) break;
         }
+        if (kMode == kModeKeep && valid) knvs[(int64_t)k * nthr + gt] = (uint8_t)nv;
         if (kMode == kModeReplay) psweep(a, dmat, rec, nv, gb_in);
         if (kMode == kModeFused) nvs[k < kFusedSamples ? k : kFusedSamples - 1] = nv;
         ++k;
@@ -536,7 +561,7 @@ __device__ __forceinline__ void pbr_lanes(const RenderArgs &a, const float4 *__r
         if (gb_in[0] != 0.0f || gb_in[1] != 0.0f || gb_in[2] != 0.0f)
             for (int i = 0; i < k && i < kFusedSamples; ++i) psweep(a, dmat, rec + i * a.bounces, nvs[i], gb_in);
     }
-    if (!kReplay) {
+    if (kMode == kModeRender || kMode == kModeKeep) {
         for (int off = L >> 1; off > 0; off >>= 1) {
             sum.x += __shfl_xor_sync(0xffffffffu, sum.x, off);
             sum.y += __shfl_xor_sync(0xffffffffu, sum.y, off);
@@ -583,6 +608,43 @@ __global__ void __launch_bounds__(kPBlock, DPCS_PBR_MINB) k_replay_pbr(const Ren
     const int64_t pix = gt >> a.log2L;
     pbr_lanes<kModeReplay>(a, mat, dmat, pix, (int)(gt & ((1 << a.log2L) - 1)), pix < (int64_t)a.Hc * a.Wc,
                            nullptr);
+}
+
+// the render of k_render_pbr, keeping every vertex record for k_sweep_kept_pbr
+__global__ void __launch_bounds__(kPBlock, DPCS_PBR_MINB)
+    k_render_keep_pbr(const RenderArgs a, const float4 *__restrict__ mat, uint4 *__restrict__ chunks,
+                      uint8_t *__restrict__ nvs) {
+    const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t pix = gt >> a.log2L;
+    pbr_lanes<kModeKeep>(a, mat, nullptr, pix, (int)(gt & ((1 << a.log2L) - 1)), pix < (int64_t)a.Hc * a.Wc,
+                         nullptr, chunks, nvs);
+}
+
+// the principled adjoint from the kept records: the sweeps of k_replay_pbr
+// without tracing again
+__global__ void __launch_bounds__(kPBlock) k_sweep_kept_pbr(const RenderArgs a, const uint4 *__restrict__ chunks,
+                                                            const uint8_t *__restrict__ nvs, float4 *__restrict__ dmat) {
+    constexpr int kPChunks = (int)(sizeof(PRec) / 16);
+    const int L = 1 << a.log2L;
+    const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t pix = gt >> a.log2L;
+    const int64_t nthr = ((int64_t)a.Hc * a.Wc) << a.log2L;
+    if (pix >= (int64_t)a.Hc * a.Wc) return;
+    const float inv = 1.0f / (float)a.spp;
+    const float gb_in[3] = {a.gE[3 * pix] * inv, a.gE[3 * pix + 1] * inv, a.gE[3 * pix + 2] * inv};
+    if (gb_in[0] == 0.0f && gb_in[1] == 0.0f && gb_in[2] == 0.0f) return;
+    const int sl = (int)(gt & (L - 1));
+    const int spl = (a.spp + L - 1) / L;
+    PRec rec[DPCS_MAX_BOUNCES];
+    for (int k = 0; k < spl && sl + k * L < a.spp; ++k) {
+        const int nv = nvs[(int64_t)k * nthr + gt];
+        for (int v = 0; v < nv; ++v) {
+            uint4 *dst = reinterpret_cast<uint4 *>(&rec[v]);
+#pragma unroll
+            for (int q = 0; q < kPChunks; ++q) dst[q] = __ldcs(chunks + kept_chunk(q, k, v, spl, a.bounces, nthr, gt));
+        }
+        psweep(a, dmat, rec, nv, gb_in);
+    }
 }
 
 __global__ void k_pack_mat(const float *__restrict__ metallic, const float *__restrict__ normal, int64_t ntex,
@@ -635,6 +697,23 @@ int launch_render_grad_pbr(const RenderArgs &a, const float4 *mat, float4 *dmat,
     const int64_t threads = ((int64_t)a.Hc * a.Wc) << a.log2L;
     if (threads <= 0) return 0;
     k_render_grad_pbr<<<grid1(threads, kPBlock), kPBlock, 0, st>>>(a, mat, dmat, l);
+    return 1;
+}
+
+static_assert(sizeof(PRec) == 4 * kPRecWordsHost, "the host sizes kept principled records with kPRecWordsHost");
+static_assert(sizeof(PRec) % 16 == 0, "PRec must be whole 16-byte chunks");
+
+int launch_render_keep_pbr(const RenderArgs &a, const float4 *mat, void *chunks, uint8_t *nvs, cudaStream_t st) {
+    const int64_t threads = ((int64_t)a.Hc * a.Wc) << a.log2L;
+    if (threads <= 0) return 0;
+    k_render_keep_pbr<<<grid1(threads, kPBlock), kPBlock, 0, st>>>(a, mat, (uint4 *)chunks, nvs);
+    return 1;
+}
+
+int launch_sweep_kept_pbr(const RenderArgs &a, const void *chunks, const uint8_t *nvs, float4 *dmat, cudaStream_t st) {
+    const int64_t threads = ((int64_t)a.Hc * a.Wc) << a.log2L;
+    if (threads <= 0) return 0;
+    k_sweep_kept_pbr<<<grid1(threads, kPBlock), kPBlock, 0, st>>>(a, (const uint4 *)chunks, nvs, dmat);
     return 1;
 }
 

@@ -36,7 +36,8 @@ EXPORTED = [
     "dpcs_probe_l2_load", "dpcs_probe_atomic4", "dpcs_gbuffer", "dpcs_denoise", "dpcs_denoise_backward",
     "dpcs_l1_loss", "dpcs_tv_loss", "dpcs_scene_update", "dpcs_render_loss_backward", "dpcs_render_keep",
     "dpcs_render_backward_kept", "dpcs_render_principled", "dpcs_render_backward_principled",
-    "dpcs_scene_transform", "dpcs_render_loss_backward_principled",
+    "dpcs_scene_transform", "dpcs_render_loss_backward_principled", "dpcs_render_keep_principled",
+    "dpcs_render_backward_kept_principled",
 ]
 
 DPCS_REQ_RELIGHT = 0
@@ -153,6 +154,13 @@ _SIGS = {
                                                               ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, _P,
                                                               ctypes.c_int32, ctypes.c_float, _P, _P, _P, _P, _P, _P,
                                                               _P, _P, _P, _P]),
+    "dpcs_render_keep_principled": (ctypes.c_int32, [_P, ctypes.c_uint64, ctypes.POINTER(DpcsMaterial), _P,
+                                                     ctypes.POINTER(DpcsView), ctypes.POINTER(DpcsParams),
+                                                     ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, _P, _P, _P]),
+    "dpcs_render_backward_kept_principled": (ctypes.c_int32, [_P, ctypes.c_uint64, ctypes.POINTER(DpcsMaterial), _P,
+                                                              ctypes.POINTER(DpcsView), ctypes.POINTER(DpcsParams),
+                                                              ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, _P, _P,
+                                                              _P, _P, _P, _P, _P, _P, _P, _P]),
     "dpcs_timing_enable": (ctypes.c_int32, [_P, ctypes.c_int32]),
     "dpcs_timing_read": (ctypes.c_int32, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(ctypes.c_int64)]),
@@ -609,15 +617,18 @@ class Context:
         return m
 
     def render_principled(self, scene: int, albedo, rough, metallic, normal, Ip, view: DpcsView,
-                          params: DpcsParams, spp: int, bounces: int, seed: int, Ic=None, Ec=None, stream=None):
-        """dpcs_render_principled: render with metallic (Ht, Wt) and normal (Ht, Wt, 3) maps (either None)."""
+                          params: DpcsParams, spp: int, bounces: int, seed: int, Ic=None, Ec=None, stream=None,
+                          keep: bool = False):
+        """dpcs_render_principled: render with metallic (Ht, Wt) and normal (Ht, Wt, 3) maps (either None);
+        keep=True keeps the path records for render_backward_principled(kept=True)."""
         import torch
 
         f32 = torch.float32
         mat = self._material(albedo, rough, metallic, normal)
         if Ic is None:
             Ic = torch.empty((view.Hc, view.Wc, 3), dtype=f32, device=self.device)
-        st = self.lib.dpcs_render_principled(
+        fn = self.lib.dpcs_render_keep_principled if keep else self.lib.dpcs_render_principled
+        st = fn(
             self.handle, scene, ctypes.byref(mat), _ptr(Ip, "Ip", (view.Hp, view.Wp, 3), f32, self.device),
             ctypes.byref(view), ctypes.byref(params), int(spp), int(bounces), int(seed) & (2**64 - 1),
             _ptr(Ic, "Ic", (view.Hc, view.Wc, 3), f32, self.device),
@@ -628,15 +639,17 @@ class Context:
     def render_backward_principled(self, scene: int, albedo, rough, metallic, normal, Ip, view: DpcsView,
                                    params: DpcsParams, spp: int, bounces: int, seed: int, Ec, Ic, dIc, dIp=None,
                                    dAlbedo=None, dRough=None, dMetallic=None, dNormal=None, dParams=None,
-                                   stream=None):
-        """dpcs_render_backward_principled: the adjoint, accumulating into the given gradient buffers."""
+                                   stream=None, kept: bool = False):
+        """dpcs_render_backward_principled: the adjoint, accumulating into the given gradient buffers;
+        kept=True sweeps the records of the last keep=True render instead of re-tracing."""
         import torch
 
         f32 = torch.float32
         mat = self._material(albedo, rough, metallic, normal)
         Ht, Wt = mat.Ht, mat.Wt
         img = (view.Hc, view.Wc, 3)
-        st = self.lib.dpcs_render_backward_principled(
+        fn = self.lib.dpcs_render_backward_kept_principled if kept else self.lib.dpcs_render_backward_principled
+        st = fn(
             self.handle, scene, ctypes.byref(mat), _ptr(Ip, "Ip", (view.Hp, view.Wp, 3), f32, self.device),
             ctypes.byref(view), ctypes.byref(params), int(spp), int(bounces), int(seed) & (2**64 - 1),
             _ptr(Ec, "Ec", img, f32, self.device), _ptr(Ic, "Ic", img, f32, self.device),

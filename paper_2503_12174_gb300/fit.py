@@ -22,8 +22,8 @@ Without the denoiser each pair's render, L1 term and adjoint are one call
 that traces its paths once (``Context.render_loss_backward``); with it, the
 render keeps its path records and the adjoint sweeps them.  ``fused=False``
 makes separate calls that trace twice.  The principled material takes the
-same route without the denoiser (``render_loss_backward_principled``) and
-separate calls with it (render, D, L1, D^T, replay).  Every step
+same routes (``render_loss_backward_principled``; with the denoiser, the
+principled render keeps its records).  Every step
 runs in the library's kernels; the only host traffic per step is reading
 back the 11 response parameters the next renders take by value (and, with
 the pose, the 13 K data terms of its differences).
@@ -167,8 +167,9 @@ class SceneFit:
                                               Ec=self.Ec, dAlbedo=self.gA, dRough=self.gR, dMetallic=self.gM,
                                               dNormal=self.gN, dParams=self.gP if self.fit_params else None)
             return
+        keep = self.fused  # with the denoiser: keep the paths for the adjoint
         c.render_principled(self.scene, self.albedo, self.rough, self.metallic, self.normal, Ip, self.view,
-                            self.params, self.spp, self.bounces, s, Ic=self.Ic, Ec=self.Ec)
+                            self.params, self.spp, self.bounces, s, Ic=self.Ic, Ec=self.Ec, keep=keep)
         if self.denoise is None:
             c.l1_loss(self.Ic, target, self.dIc, self.losses[i:i + 1], scale=self.scale)
         else:
@@ -179,7 +180,7 @@ class SceneFit:
         c.render_backward_principled(self.scene, self.albedo, self.rough, self.metallic, self.normal, Ip, self.view,
                                      self.params, self.spp, self.bounces, s, self.Ec, self.Ic, self.dIc,
                                      dAlbedo=self.gA, dRough=self.gR, dMetallic=self.gM, dNormal=self.gN,
-                                     dParams=self.gP if self.fit_params else None)
+                                     dParams=self.gP if self.fit_params else None, kept=keep)
 
     def run(self, steps: int):
         """`steps` Adam steps; returns the per-step total loss (host list)."""

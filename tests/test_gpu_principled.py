@@ -213,3 +213,52 @@ def test_principled_degenerate_inputs(orc):
         assert not Ec.any()
     finally:
         g.close()
+
+
+@pytest.mark.parametrize("spp,bounces", [(16, 3), (64, 2)])
+def test_principled_kept_records_equal_the_replay(spp, bounces):
+    """dpcs_render_keep_principled renders what dpcs_render_principled
+    renders, bit for bit, and the adjoint from its records equals the
+    re-tracing replay (every material gradient) to atomic rounding, twice
+    from the same records; a kept plain render does not serve the principled
+    adjoint."""
+    torch = need_cuda()
+    sc = scenes.with_principled(scenes.corner(res=24, tex=16, spp=spp, bounces=bounces, seed=6), seed=8)
+    g = GpuScene(sc)
+    try:
+        c = g.ctx
+        m, n = torch.from_numpy(sc.metallic).cuda(), torch.from_numpy(sc.normal).cuda()
+        W = torch.from_numpy(np.random.default_rng(spp).normal(size=(sc.Hc, sc.Wc, 3)).astype(np.float32)).cuda()
+        args = (g.handle, g.albedo, g.rough, m, n, g.Ip, g.view, g.params, sc.spp, sc.bounces, sc.seed)
+
+        def grads():
+            return {"dIp": torch.zeros_like(g.Ip), "dA": torch.zeros_like(g.albedo), "dR": torch.zeros_like(g.rough),
+                    "dM": torch.zeros_like(m), "dN": torch.zeros_like(n), "dP": torch.zeros(11, device="cuda")}
+
+        def backward(Ec, Ic, gr, kept):
+            c.render_backward_principled(*args, Ec, Ic, W, dIp=gr["dIp"], dAlbedo=gr["dA"], dRough=gr["dR"],
+                                         dMetallic=gr["dM"], dNormal=gr["dN"], dParams=gr["dP"], kept=kept)
+
+        E0 = torch.empty_like(W)
+        I0, _ = c.render_principled(*args, Ec=E0)
+        g0 = grads()
+        backward(E0, I0, g0, False)
+        E1 = torch.empty_like(W)
+        I1, _ = c.render_principled(*args, Ec=E1, keep=True)
+        g1, g2 = grads(), grads()
+        backward(E1, I1, g1, True)
+        backward(E1, I1, g2, True)
+        c.sync()
+        assert torch.equal(E0, E1) and torch.equal(I0, I1)
+        for gk in (g1, g2):
+            for k in g0:
+                a, b = g0[k].cpu().numpy(), gk[k].cpu().numpy()
+                assert np.abs(a).max() > 0, k
+                np.testing.assert_allclose(b, a, rtol=1e-4, atol=1e-6 * np.abs(a).max(), err_msg=k)
+        c.render(g.handle, g.albedo, g.rough, g.Ip, g.view, g.params, sc.spp, sc.bounces, sc.seed, keep=True)
+        with pytest.raises(dpcs.DPCSError) as e:
+            backward(E1, I1, grads(), True)
+        assert e.value.status == dpcs.DPCS_ERR_INVALID_ARG
+        c.sync()
+    finally:
+        g.close()
