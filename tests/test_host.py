@@ -1,0 +1,49 @@
+"""Host-side logic that needs no GPU: the response-parameter vector of the
+autograd wrapper and the fit, the posed projector extrinsics written into a
+dpcs_view, and the seeded principled maps."""
+import numpy as np
+
+from paper_2503_12174_gb300 import autograd, dpcs, pose, scenes
+
+
+def test_params_vector_round_trip():
+    p = dpcs.make_params(scenes.corner(res=8, spp=1).params)
+    v = [2.1, 2.2, 2.3, 1.4, 0.5, 0.6, 0.7, 1.8, 0.9, 1.1, 1.2]
+    q = autograd.with_vector(p, v)
+    np.testing.assert_allclose(autograd.params_vector(q), v, rtol=1e-7)
+    # the other fields are copied, and p itself is untouched
+    assert q.k_proj == p.k_proj and q.ks == p.ks and q.rr_start == p.rr_start
+    np.testing.assert_allclose(autograd.params_vector(p), autograd.params_vector(
+        dpcs.make_params(scenes.corner(res=8, spp=1).params)))
+
+
+def test_posed_view_writes_the_posed_extrinsics():
+    sc = scenes.corner(res=16, spp=1)
+    v = dpcs.view_of(sc)
+    R, t = pose.rotation([0.02, -0.05, 0.1]), np.array([0.01, 0.03, -0.02])
+    pv = pose.posed_view(v, R, t)
+    Rp2, tp2 = pose.posed_extrinsics(sc.Rp, sc.tp, R, t)
+    np.testing.assert_allclose(np.array(pv.Rp[:]).reshape(3, 3), Rp2, atol=1e-7)
+    np.testing.assert_allclose(np.array(pv.tp[:]), tp2, atol=1e-7)
+    assert list(pv.Kc[:]) == list(v.Kc[:]) and list(pv.Kp[:]) == list(v.Kp[:])
+    assert (pv.Hc, pv.Wc, pv.Hp, pv.Wp) == (v.Hc, v.Wc, v.Hp, v.Wp)
+    # the projector centre -Rp'^T tp' is the moved centre R cp + t
+    cp = -np.asarray(sc.Rp, np.float64).T @ np.asarray(sc.tp, np.float64)
+    np.testing.assert_allclose(-Rp2.T @ tp2, R @ cp + t, atol=1e-12)
+    # the identity pose changes nothing
+    pv0 = pose.posed_view(v, np.eye(3), np.zeros(3))
+    np.testing.assert_array_equal(np.array(pv0.Rp[:]), np.array(v.Rp[:]))
+    np.testing.assert_array_equal(np.array(pv0.tp[:]), np.array(v.tp[:]))
+
+
+def test_principled_maps_are_seeded_and_in_range():
+    a = scenes.principled_maps(np.random.default_rng(3), 24, 20)
+    b = scenes.principled_maps(np.random.default_rng(3), 24, 20)
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(x, y)
+    metallic, normal = a
+    assert metallic.shape == (24, 20) and normal.shape == (24, 20, 3)
+    assert metallic.min() >= 0.0 and metallic.max() <= 0.8 + 1e-6
+    n = 2.0 * normal.astype(np.float64) - 1.0
+    np.testing.assert_allclose(np.linalg.norm(n, axis=-1), 1.0, atol=1e-6)  # unit tangent-space normals
+    assert n[..., 2].min() > 0.5  # tilted, but facing out of the surface
