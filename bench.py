@@ -13,6 +13,14 @@ The same JSON line also carries
               image uploaded from pinned host memory and Ic read back every step;
   roofline  : the render kernel's FP32 arithmetic rate against the GPU's FP32
               peak (algorithmic FLOPs counted by the DPCS_COUNTERS build);
+  roofline_load / roofline_atomic / roofline_issue : the render kernel's
+              node, triangle and texel loads against the measured L2 load
+              rate, the replay's float4 atomics against the measured atomic
+              rate, and the render kernel's warp instructions against the
+              SMs' issue rate;
+  compensation, denoise, fit (with a camera-pose step), heightfield (with
+              the morphing and rigidly moved surface), principled (metallic
+              and normal maps) and serving : the other workloads of the path;
   cpu_baseline : the FP64 oracle on the host cores over a bounded pixel sample.
 
 ``--impl reference`` times the oracle alone (the reference arm).  Under
