@@ -127,3 +127,26 @@ def test_pixel_list_matches_full_image(orc):
     Ep, Ipx = orc.render(sc, pixels=px)
     np.testing.assert_array_equal(Ep, Ef.reshape(-1, 3)[px])
     np.testing.assert_array_equal(Ipx, If.reshape(-1, 3)[px])
+
+
+def _with(p, **kw):
+    d = {f: getattr(p, f) for f in p.__dataclass_fields__}
+    d.update(kw)
+    return scenes.Params(**d)
+
+
+def test_russian_roulette_is_unbiased(orc):
+    """Russian roulette from vertex 2 with survival q: survivors carry 1/q,
+    so q = 1 is exactly the renderer without roulette, and q = 0.75 has the
+    same expectation (image mean within 4 standard errors over 64 x 128
+    paths, in a closed sphere where every path would continue)."""
+    sc = scenes.sphere(subdiv=2, res=8, spp=128, bounces=5, seed=2)
+    E0, _ = orc.render(sc)
+    E1, _ = orc.render(sc.replace(params=_with(sc.params, rr_start=2, rr_q=1.0)))
+    np.testing.assert_array_equal(E1, E0)
+    Eq, _ = orc.render(sc.replace(params=_with(sc.params, rr_start=2, rr_q=0.75)))
+    assert np.abs(Eq - E0).max() > 0  # roulette changed individual paths
+    # per-pixel differences are independent across pixels: compare the image means
+    d = (Eq - E0).mean(axis=-1).ravel()
+    se = d.std(ddof=1) / np.sqrt(d.size)
+    assert abs(d.mean()) < 4 * se + 1e-12, (d.mean(), se)
