@@ -150,3 +150,18 @@ def test_russian_roulette_is_unbiased(orc):
     d = (Eq - E0).mean(axis=-1).ravel()
     se = d.std(ddof=1) / np.sqrt(d.size)
     assert abs(d.mean()) < 4 * se + 1e-12, (d.mean(), se)
+
+
+def test_radiance_clipping_bounds(orc):
+    """Eq. 12 clamps each per-vertex contribution per channel: a clip above
+    every contribution changes nothing, clipping never brightens a pixel, and
+    a pixel's mean over samples is at most (vertices per path) x clip."""
+    sc = scenes.corner(res=16, tex=16, spp=8, bounces=3, seed=6)
+    E0, _ = orc.render(sc)
+    Ebig, _ = orc.render(sc.replace(params=_with(sc.params, clip=1e6)))
+    np.testing.assert_array_equal(Ebig, E0)
+    for clip in (0.05, 0.005):
+        Ec, _ = orc.render(sc.replace(params=_with(sc.params, clip=clip)))
+        assert np.all(Ec <= E0 + 1e-15)
+        assert np.all(Ec <= sc.bounces * clip * (1 + 1e-12))
+        assert (Ec < E0 - 1e-9).any()  # the clip was active somewhere
