@@ -258,22 +258,25 @@ dpcs_status dpcs_render(dpcs_ctx *ctx, dpcs_scene scene, const float *albedo, co
                         int32_t bounces, uint64_t seed, float *Ic, float *Ec, void *stream);
 
 /*
- * dpcs_render without any device allocation, for callers that cannot call
- * cudaMalloc when they render: code recording a CUDA stream capture, host
- * programs that give the GPU a fixed memory budget up front, and loops that
- * cannot absorb an allocation's latency or failure.  Arguments, results and
- * error codes are those of dpcs_render (the same kernels run; Ic and Ec are
- * identical).  The PRF-mapped projector image and the packed textures live
- * in one fixed array compiled into the library instead of context scratch:
+ * dpcs_render without any device allocation.  It is for callers that cannot
+ * call cudaMalloc when they render: host applications that give the GPU a
+ * fixed memory budget up front and own every allocation in it, and real-time
+ * loops that cannot absorb an allocation's latency, or its failure, part-way
+ * through a frame.  Arguments, results and error codes are those of
+ * dpcs_render: the same kernels run, and Ic and Ec are bit-identical to
+ * dpcs_render's.  The PRF-mapped projector image and the packed textures
+ * live in one fixed array compiled into the library instead of context
+ * scratch:
  *  - limit: Hp*Wp + Ht*Wt <= 524288 texels (8 MiB); larger sizes return
  *    DPCS_ERR_INVALID_ARG without launching anything;
  *  - every GPU that loads the library holds the 8 MiB until the process exits;
  *  - the first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress), so make that first call before any stream
- *    capture begins;
- *  - all calls share the array: calls that overlap on the GPU (other
- *    streams, other host threads) race and must be serialised by the caller.
- * The paper has no counterpart; this is a deployment variant of Eq. 7.
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture begins;
+ *  - all calls share the array and every call overwrites the part it uses:
+ *    calls that overlap on the GPU (other streams, other host threads) race
+ *    and must be serialised by the caller.
+ * The paper has no counterpart.
  */
 dpcs_status dpcs_render_noalloc(dpcs_ctx *ctx, dpcs_scene scene, const float *albedo, const float *rough,
                                 int32_t Ht, int32_t Wt, const float *Ip, const dpcs_view *view,

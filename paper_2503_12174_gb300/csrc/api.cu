@@ -8,6 +8,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <atomic>
 #include <map>
 #include <string>
 #include <vector>
@@ -1106,15 +1107,15 @@ dpcs_status dpcs_adam(dpcs_ctx *c, float *p, const float *g, float *m, float *v,
 // Rendering without allocation.
 //
 // dpcs_render keeps the PRF-mapped projector image and the packed textures in
-// context scratch that grows with cudaMalloc on first use.  Callers that may
-// not allocate device memory at render time -- code recording a CUDA stream
-// capture (cudaMalloc is not permitted while a capture is active), host
-// applications that hand the GPU a fixed memory budget up front, real-time
-// loops that cannot absorb an allocation's latency or failure -- use
-// dpcs_render_noalloc instead.  Its scratch is the fixed array below,
-// compiled into the library: every GPU that loads the library holds these
-// 8 MiB until the process exits.  All calls share it, so calls that overlap
-// on the GPU (different streams, or different host threads) race.
+// context scratch that grows with cudaMalloc on first use.  Some callers may
+// not allocate device memory when they render: host applications that hand
+// the GPU a fixed memory budget up front and own every allocation in it, and
+// real-time loops that cannot absorb an allocation's latency or its failure
+// part-way through a frame.  They use dpcs_render_noalloc instead.  Its
+// scratch is the fixed array below, compiled into the library: every GPU that
+// loads the library holds these 8 MiB until the process exits.  All calls
+// share it, so calls that overlap on the GPU (different streams, or different
+// host threads) race.
 // ---------------------------------------------------------------------------
 namespace {
 
@@ -1122,18 +1123,21 @@ constexpr int64_t kNoAllocTexels = int64_t(1) << 19;  // 524,288 float4 = 8 MiB
 static __device__ __align__(256) float4 g_noalloc_scratch[kNoAllocTexels];
 
 constexpr int kMaxDevices = 64;
-void *g_noalloc_ptr[kMaxDevices] = {nullptr};
+// device address of the array per device; host threads may race on the first
+// lookup, so the entries are atomics (both writers store the same address)
+std::atomic<void *> g_noalloc_ptr[kMaxDevices];
 
-// device address of the array for the current device, resolved once per device
+// device address of the array for the current device, resolved once per
+// device with that device current (the caller has made it current)
 dpcs_status noalloc_scratch(dpcs_ctx *c, float4 **out) {
     if (c->device < 0 || c->device >= kMaxDevices) return fail(c, DPCS_ERR_INVALID_ARG, "device index too large");
-    if (!g_noalloc_ptr[c->device]) {
-        void *p = nullptr;
+    void *p = g_noalloc_ptr[c->device].load(std::memory_order_acquire);
+    if (!p) {
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) return cuda_fail(c, e, "cudaGetSymbolAddress(no-alloc scratch)");
-        g_noalloc_ptr[c->device] = p;
+        g_noalloc_ptr[c->device].store(p, std::memory_order_release);
     }
-    *out = (float4 *)g_noalloc_ptr[c->device];
+    *out = (float4 *)p;
     return DPCS_OK;
 }
 
