@@ -54,7 +54,9 @@
  *
  * Everything else is FP64.  Ray-triangle tests are brute force over all
  * triangles in their original order (Moller-Trumbore 1997); ties in t go to the
- * lowest triangle index.
+ * lowest triangle index.  A timing mode (or_set_accel(1)) tests only the
+ * triangles whose padded boxes a median-split BVH cannot cull; it returns the
+ * same hits, so its images equal the brute-force ones bit for bit.
  */
 #include <math.h>
 #include <stdint.h>
@@ -160,11 +162,27 @@ typedef struct {
     double Kp[9], Rp[9], tp[3]; int32_t Hp, Wp;   /* projector (Eq. 6) */
 } or_view;
 
+/* timing-mode acceleration: a median-split BVH over the same FP64 triangles */
+typedef struct {
+    double lo[3], hi[3];  /* box, padded outwards so that culling is conservative */
+    int left, right;      /* children, or -1 for a leaf */
+    int first, count;     /* leaf: range of bvh_idx */
+} bnode;
+
 typedef struct {
     int T;
     d3 *v0, *e1, *e2; /* FP64 copies of the FP32 input: differences are exact */
     double *uv;       /* 6 per triangle */
+    bnode *nodes;     /* NULL in parity mode (brute force) */
+    int *bvh_idx;     /* triangle indices in leaf order */
+    int nnodes;
 } dscene;
+
+/* 0 = parity mode (brute force), 1 = timing mode (BVH); set by the caller
+ * before a render, read by scene_make */
+static int g_accel = 0;
+void or_set_accel(int on) { g_accel = on ? 1 : 0; }
+static void bvh_build(dscene *S);
 
 static void scene_make(dscene *S, const float *verts, const int32_t *tris, int32_t T, const float *uv)
 {
@@ -182,8 +200,14 @@ static void scene_make(dscene *S, const float *verts, const int32_t *tris, int32
             S->uv[6 * i + 2 * k + 1] = uv[2 * tris[3 * i + k] + 1];
         }
     }
+    S->nodes = NULL; S->bvh_idx = NULL; S->nnodes = 0;
+    if (g_accel && T > 0) bvh_build(S);
 }
-static void scene_free(dscene *S) { free(S->v0); free(S->e1); free(S->e2); free(S->uv); }
+static void scene_free(dscene *S)
+{
+    free(S->v0); free(S->e1); free(S->e2); free(S->uv);
+    free(S->nodes); free(S->bvh_idx);
+}
 
 /* Moller-Trumbore (1997), two-sided, t in (tmin, tmax) */
 static int isect(const dscene *S, int i, d3 o, d3 d, double tmin, double tmax, double *t, double *bu, double *bv)
@@ -205,7 +229,7 @@ static int isect(const dscene *S, int i, d3 o, d3 d, double tmin, double tmax, d
 }
 
 /* brute-force closest hit; strict '<' keeps the lowest index on ties */
-static int closest(const dscene *S, d3 o, d3 d, double tmax, double *t, double *bu, double *bv)
+static int closest_brute(const dscene *S, d3 o, d3 d, double tmax, double *t, double *bu, double *bv)
 {
     int best = -1;
     double bt = tmax, tu = 0, tv = 0;
@@ -217,13 +241,181 @@ static int closest(const dscene *S, d3 o, d3 d, double tmax, double *t, double *
     return best;
 }
 
-static int occluded(const dscene *S, d3 o, d3 d, double tmax)
+static int occluded_brute(const dscene *S, d3 o, d3 d, double tmax)
 {
     for (int i = 0; i < S->T; ++i) {
         double tt, uu, vv;
         if (isect(S, i, o, d, 0.0, tmax, &tt, &uu, &vv)) return 1;
     }
     return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Timing mode: a median-split BVH (longest centroid axis, leaves of <= 4     */
+/* triangles).  It changes which triangles are tested, never how: each test   */
+/* is isect() above, and the closest hit is the lexicographic minimum of      */
+/* (t, triangle index), which is what the brute-force loop returns.  Boxes    */
+/* are padded and the slab test widened, so a box is culled only when no     */
+/* point of it can lie on the ray within the current bound.                   */
+/* ------------------------------------------------------------------------- */
+typedef struct { const dscene *S; double *cen; int *idx; } bvh_ctx;
+
+static void tri_box(const dscene *S, int i, double lo[3], double hi[3])
+{
+    d3 a = S->v0[i], b = add(S->v0[i], S->e1[i]), c = add(S->v0[i], S->e2[i]);
+    double pa[3] = {a.x, a.y, a.z}, pb[3] = {b.x, b.y, b.z}, pc[3] = {c.x, c.y, c.z};
+    for (int k = 0; k < 3; ++k) {
+        lo[k] = fmin(pa[k], fmin(pb[k], pc[k]));
+        hi[k] = fmax(pa[k], fmax(pb[k], pc[k]));
+    }
+}
+
+/* partial sort of idx[first, last) so that position mid holds the element of
+ * rank mid by centroid coordinate `axis` (Hoare's selection) */
+static void select_mid(bvh_ctx *B, int first, int last, int mid, int axis)
+{
+    int *v = B->idx;
+    while (last - first > 1) {
+        double piv = B->cen[3 * v[(first + last) / 2] + axis];
+        int i = first, j = last - 1;
+        while (i <= j) {
+            while (B->cen[3 * v[i] + axis] < piv) ++i;
+            while (B->cen[3 * v[j] + axis] > piv) --j;
+            if (i <= j) { int t = v[i]; v[i] = v[j]; v[j] = t; ++i; --j; }
+        }
+        if (mid <= j) last = j + 1;
+        else if (mid >= i) first = i;
+        else return;
+    }
+}
+
+static int bvh_node(bvh_ctx *B, dscene *S, int first, int last)
+{
+    int id = S->nnodes++;
+    bnode *N = &S->nodes[id];
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    double clo[3] = {INFINITY, INFINITY, INFINITY}, chi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int k = first; k < last; ++k) {
+        double tl[3], th[3];
+        tri_box(S, B->idx[k], tl, th);
+        for (int a = 0; a < 3; ++a) {
+            lo[a] = fmin(lo[a], tl[a]); hi[a] = fmax(hi[a], th[a]);
+            clo[a] = fmin(clo[a], B->cen[3 * B->idx[k] + a]); chi[a] = fmax(chi[a], B->cen[3 * B->idx[k] + a]);
+        }
+    }
+    for (int a = 0; a < 3; ++a) {  /* pad: far above FP64 rounding of the hit point */
+        double pad = 1e-9 * (fabs(lo[a]) + fabs(hi[a]) + (hi[a] - lo[a])) + 1e-12;
+        N->lo[a] = lo[a] - pad; N->hi[a] = hi[a] + pad;
+    }
+    if (last - first <= 4) {
+        N->left = N->right = -1; N->first = first; N->count = last - first;
+        return id;
+    }
+    int axis = 0;
+    for (int a = 1; a < 3; ++a)
+        if (chi[a] - clo[a] > chi[axis] - clo[axis]) axis = a;
+    int mid = (first + last) / 2;
+    select_mid(B, first, last, mid, axis);
+    N->first = first; N->count = 0;
+    int l = bvh_node(B, S, first, mid);
+    int r = bvh_node(B, S, mid, last);
+    S->nodes[id].left = l;
+    S->nodes[id].right = r;
+    return id;
+}
+
+static void bvh_build(dscene *S)
+{
+    int T = S->T;
+    S->nodes = (bnode *)malloc(sizeof(bnode) * (size_t)(2 * T));
+    S->bvh_idx = (int *)malloc(sizeof(int) * (size_t)T);
+    double *cen = (double *)malloc(sizeof(double) * 3 * (size_t)T);
+    for (int i = 0; i < T; ++i) {
+        d3 c = add(S->v0[i], scl(add(S->e1[i], S->e2[i]), 1.0 / 3.0));
+        cen[3 * i] = c.x; cen[3 * i + 1] = c.y; cen[3 * i + 2] = c.z;
+        S->bvh_idx[i] = i;
+    }
+    bvh_ctx B = {S, cen, S->bvh_idx};
+    S->nnodes = 0;
+    bvh_node(&B, S, 0, T);
+    free(cen);
+}
+
+/* ray-box overlap within [0, tmax], conservative (the far bound is widened) */
+static int box_hit(const bnode *N, d3 o, d3 d, double tmax, double *tnear)
+{
+    double oo[3] = {o.x, o.y, o.z}, dd[3] = {d.x, d.y, d.z};
+    double tn = 0.0, tf = tmax;
+    for (int a = 0; a < 3; ++a) {
+        if (dd[a] == 0.0) {
+            if (oo[a] < N->lo[a] || oo[a] > N->hi[a]) return 0;
+            continue;
+        }
+        double t0 = (N->lo[a] - oo[a]) / dd[a], t1 = (N->hi[a] - oo[a]) / dd[a];
+        if (t0 > t1) { double t = t0; t0 = t1; t1 = t; }
+        if (t0 > tn) tn = t0;
+        if (t1 < tf) tf = t1;
+    }
+    *tnear = tn;
+    return tn <= tf * (1.0 + 1e-12) + 1e-300;
+}
+
+static int closest_bvh(const dscene *S, d3 o, d3 d, double tmax, double *t, double *bu, double *bv)
+{
+    int best = -1;
+    double bt = tmax, tu = 0, tv = 0;
+    int stack[128], sp = 0;
+    stack[sp++] = 0;
+    while (sp > 0) {
+        const bnode *N = &S->nodes[stack[--sp]];
+        double tn;
+        if (!box_hit(N, o, d, bt, &tn)) continue;
+        if (N->left < 0) {
+            for (int k = N->first; k < N->first + N->count; ++k) {
+                int i = S->bvh_idx[k];
+                double tt, uu, vv;
+                if (isect(S, i, o, d, 0.0, tmax, &tt, &uu, &vv) && (tt < bt || (tt == bt && best >= 0 && i < best))) {
+                    bt = tt; best = i; tu = uu; tv = vv;
+                }
+            }
+        } else {
+            stack[sp++] = N->right;
+            stack[sp++] = N->left;
+        }
+    }
+    if (best >= 0) { *t = bt; *bu = tu; *bv = tv; }
+    return best;
+}
+
+static int occluded_bvh(const dscene *S, d3 o, d3 d, double tmax)
+{
+    int stack[128], sp = 0;
+    stack[sp++] = 0;
+    while (sp > 0) {
+        const bnode *N = &S->nodes[stack[--sp]];
+        double tn;
+        if (!box_hit(N, o, d, tmax, &tn)) continue;
+        if (N->left < 0) {
+            for (int k = N->first; k < N->first + N->count; ++k) {
+                double tt, uu, vv;
+                if (isect(S, S->bvh_idx[k], o, d, 0.0, tmax, &tt, &uu, &vv)) return 1;
+            }
+        } else {
+            stack[sp++] = N->right;
+            stack[sp++] = N->left;
+        }
+    }
+    return 0;
+}
+
+static int closest(const dscene *S, d3 o, d3 d, double tmax, double *t, double *bu, double *bv)
+{
+    return S->nodes ? closest_bvh(S, o, d, tmax, t, bu, bv) : closest_brute(S, o, d, tmax, t, bu, bv);
+}
+
+static int occluded(const dscene *S, d3 o, d3 d, double tmax)
+{
+    return S->nodes ? occluded_bvh(S, o, d, tmax) : occluded_brute(S, o, d, tmax);
 }
 
 void or_closest(const float *verts, int32_t V, const int32_t *tris, int32_t T, const float *uv,

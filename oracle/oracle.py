@@ -140,15 +140,18 @@ def lbvh(verts, tris):
     return codes, order, child, box
 
 
-def closest(verts, tris, o, d):
+def closest(verts, tris, o, d, accel: bool = False):
+    """FP64 closest hit (t, triangle) of each ray; brute force, or the BVH of
+    the timing mode (``accel``)."""
     verts, tris = _c(verts, np.float32), _c(tris, np.int32)
     o, d = _c(o, np.float64).reshape(-1, 3), _c(d, np.float64).reshape(-1, 3)
     n = len(o)
     t = np.empty(n, np.float64)
     tri = np.empty(n, np.int32)
     uv = np.zeros((max(len(verts), 1), 2), np.float32)
-    load().or_closest(_p(verts), ctypes.c_int32(len(verts)), _p(tris), ctypes.c_int32(len(tris)), _p(uv),
-                      _p(o), _p(d), ctypes.c_int64(n), _p(t), _p(tri))
+    with _Accel(accel):
+        load().or_closest(_p(verts), ctypes.c_int32(len(verts)), _p(tris), ctypes.c_int32(len(tris)), _p(uv),
+                          _p(o), _p(d), ctypes.c_int64(n), _p(t), _p(tri))
     return t, tri
 
 
@@ -218,11 +221,26 @@ def _maps(sc, metallic, normal, Ht, Wt):
     return m, nm
 
 
+class _Accel:
+    """Timing mode for the duration of one call: the C oracle tests only the
+    triangles a median-split BVH cannot cull (same hits as brute force)."""
+
+    def __init__(self, on: bool):
+        self.on = bool(on)
+
+    def __enter__(self):
+        load().or_set_accel(ctypes.c_int(1 if self.on else 0))
+
+    def __exit__(self, *exc):
+        load().or_set_accel(ctypes.c_int(0))
+
+
 def render(sc, pixels=None, *, albedo=None, rough=None, Ip=None, params=None, spp=None, bounces=None,
-           seed=None, nthreads: int = 0, metallic=_SCENE, normal=_SCENE):
+           seed=None, nthreads: int = 0, metallic=_SCENE, normal=_SCENE, accel: bool = False):
     """FP64 forward render.  Returns (Ec, Ic), each (npix, 3) for a pixel list
     or (Hc, Wc, 3) for the full image.  ``metallic`` (Ht, Wt) and ``normal``
-    (Ht, Wt, 3) default to the scene's maps; None = metallic 0 / no normal map."""
+    (Ht, Wt, 3) default to the scene's maps; None = metallic 0 / no normal map.
+    ``accel`` = timing mode (BVH; identical results)."""
     verts, tris, uv, albedo, rough, Ip = _scene_args(sc, albedo, rough, Ip)
     m, nm = _maps(sc, metallic, normal, albedo.shape[0], albedo.shape[1])
     P = make_params(params or sc.params)
@@ -232,13 +250,14 @@ def render(sc, pixels=None, *, albedo=None, rough=None, Ip=None, params=None, sp
     n = sc.Hc * sc.Wc if full else len(px)
     Ec = np.zeros((n, 3))
     Ic = np.zeros((n, 3))
-    rc = load().or_render_m(_p(verts), _p(tris), ctypes.c_int32(len(tris)), _p(uv), _p(albedo), _p(rough),
-                            None if m is None else _p(m), None if nm is None else _p(nm),
-                            ctypes.c_int32(albedo.shape[0]), ctypes.c_int32(albedo.shape[1]), _p(Ip),
-                            ctypes.byref(V), ctypes.byref(P), ctypes.c_int32(spp or sc.spp),
-                            ctypes.c_int32(sc.bounces if bounces is None else bounces),
-                            ctypes.c_uint64(sc.seed if seed is None else seed),
-                            None if full else _p(px), ctypes.c_int64(n), _p(Ec), _p(Ic), ctypes.c_int32(nthreads))
+    with _Accel(accel):
+        rc = load().or_render_m(_p(verts), _p(tris), ctypes.c_int32(len(tris)), _p(uv), _p(albedo), _p(rough),
+                                None if m is None else _p(m), None if nm is None else _p(nm),
+                                ctypes.c_int32(albedo.shape[0]), ctypes.c_int32(albedo.shape[1]), _p(Ip),
+                                ctypes.byref(V), ctypes.byref(P), ctypes.c_int32(spp or sc.spp),
+                                ctypes.c_int32(sc.bounces if bounces is None else bounces),
+                                ctypes.c_uint64(sc.seed if seed is None else seed),
+                                None if full else _p(px), ctypes.c_int64(n), _p(Ec), _p(Ic), ctypes.c_int32(nthreads))
     if rc != 0:
         raise ValueError("oracle render: invalid arguments")
     if full:
@@ -247,10 +266,10 @@ def render(sc, pixels=None, *, albedo=None, rough=None, Ip=None, params=None, sp
 
 
 def render_backward(sc, dIc, pixels=None, *, albedo=None, rough=None, Ip=None, params=None, spp=None,
-                    bounces=None, seed=None, nthreads: int = 0, metallic=_SCENE, normal=_SCENE):
+                    bounces=None, seed=None, nthreads: int = 0, metallic=_SCENE, normal=_SCENE, accel: bool = False):
     """FP64 adjoint.  ``dIc`` is (npix, 3) for a pixel list or (Hc, Wc, 3).
     Returns dict(dIp, dalbedo, drough, dparams[11]) plus dmetallic / dnormal
-    where those maps are used (see ``render``)."""
+    where those maps are used (see ``render``).  ``accel`` = timing mode."""
     verts, tris, uv, albedo, rough, Ip = _scene_args(sc, albedo, rough, Ip)
     m, nm = _maps(sc, metallic, normal, albedo.shape[0], albedo.shape[1])
     P = make_params(params or sc.params)
@@ -265,14 +284,15 @@ def render_backward(sc, dIc, pixels=None, *, albedo=None, rough=None, Ip=None, p
     dM = None if m is None else np.zeros(m.shape)
     dN = None if nm is None else np.zeros(nm.shape)
     dP = np.zeros(11)
-    rc = load().or_render_backward_m(
-        _p(verts), _p(tris), ctypes.c_int32(len(tris)), _p(uv), _p(albedo), _p(rough),
-        None if m is None else _p(m), None if nm is None else _p(nm),
-        ctypes.c_int32(albedo.shape[0]), ctypes.c_int32(albedo.shape[1]), _p(Ip), ctypes.byref(V),
-        ctypes.byref(P), ctypes.c_int32(spp or sc.spp), ctypes.c_int32(sc.bounces if bounces is None else bounces),
-        ctypes.c_uint64(sc.seed if seed is None else seed), None if full else _p(px), ctypes.c_int64(n), _p(dIc),
-        _p(dIp), _p(dA), _p(dR), None if dM is None else _p(dM), None if dN is None else _p(dN), _p(dP),
-        ctypes.c_int32(nthreads))
+    with _Accel(accel):
+        rc = load().or_render_backward_m(
+            _p(verts), _p(tris), ctypes.c_int32(len(tris)), _p(uv), _p(albedo), _p(rough),
+            None if m is None else _p(m), None if nm is None else _p(nm),
+            ctypes.c_int32(albedo.shape[0]), ctypes.c_int32(albedo.shape[1]), _p(Ip), ctypes.byref(V),
+            ctypes.byref(P), ctypes.c_int32(spp or sc.spp), ctypes.c_int32(sc.bounces if bounces is None else bounces),
+            ctypes.c_uint64(sc.seed if seed is None else seed), None if full else _p(px), ctypes.c_int64(n), _p(dIc),
+            _p(dIp), _p(dA), _p(dR), None if dM is None else _p(dM), None if dN is None else _p(dN), _p(dP),
+            ctypes.c_int32(nthreads))
     if rc != 0:
         raise ValueError("oracle render_backward: invalid arguments")
     out = {"dIp": dIp, "dalbedo": dA, "drough": dR, "dparams": dP}
