@@ -48,13 +48,14 @@ METRIC = "Msamples/s fwd and fwd+bwd; relight p50/p99 ms under load vs per-call 
 UNIT = "Msamples/s"
 WORKLOAD = "corner scene T=1026, camera/projector/textures 256x256, 64 spp, 3 bounces, forward render"
 FWD_BWD_WORKLOAD = "corner scene T=1026 at 512x512 (camera, projector, textures), 16 spp, 3 bounces: " \
-                   "render + L2 loss + path adjoint (one fused trace) + Adam on Ip"
+                   "render + L2 loss + path adjoint (one fused trace) with the gradients of Ip, albedo, roughness " \
+                   "and the 11 PRF/CRF/white-balance parameters + Adam on Ip"
 L2_FLUSH_BYTES = 256 << 20
 
-# DRAM bytes (read + write) of one k_render launch of this workload, from the
-# ncu capture summarised in profiles/k_render_corner256.md.  It holds only for
-# the kernel sources it was measured on; once they change, the roofline's
-# traffic is reported as null until a new capture is taken.
+# DRAM bytes (read + write) of one k_render launch of this workload, from an
+# ncu capture of the same command.  It holds only for the kernel sources it
+# was measured on; once they change, the roofline's traffic is reported as
+# null until a new capture is taken.
 RENDER_TRAFFIC = {"bytes": 36724736, "sources_sha256": "7e2cfcba363a44384f6a98b48b89053c847a717d32acc2def29ee65c2981c67d"}
 # Warp instructions one k_render launch of the forward workload issues, and
 # the active lanes per instruction, from the same ncu capture
@@ -62,6 +63,10 @@ RENDER_TRAFFIC = {"bytes": 36724736, "sources_sha256": "7e2cfcba363a44384f6a98b4
 # reported while the kernel sources keep this hash.
 RENDER_ISSUE = {"warp_instructions": 1879286116, "lanes_per_instruction": 12.08,
                 "sources_sha256": "7e2cfcba363a44384f6a98b48b89053c847a717d32acc2def29ee65c2981c67d"}
+# The same two figures for one k_render_grad launch of the compensation step
+# with every gradient requested.
+FWD_BWD_TRAFFIC = {"bytes": None, "sources_sha256": ""}
+FWD_BWD_ISSUE = {"warp_instructions": None, "lanes_per_instruction": None, "sources_sha256": ""}
 KERNEL_SOURCES = ("paper_2503_12174_gb300/csrc/render.cu", "paper_2503_12174_gb300/csrc/device.cuh",
                   "paper_2503_12174_gb300/csrc/internal.h")
 
@@ -85,6 +90,11 @@ FLOP = {
     "lit": 160,            # bilinear Ep, geometry term, GGX evaluation with roughness derivative, contribution
     "continuations": 230,  # frame, lobe sample (cosine or visible-normal GGX), pdf, BRDF, throughput
 }
+# the adjoint's reverse sweep per recorded vertex: per channel the path
+# throughput, the BRDF values, dEp, dalbedo, the roughness term and the
+# suffix A (about 20), two sets of bilinear weights (16) and the scattered
+# products (16 for albedo + roughness, 12 for Ep)
+SWEEP_FLOP_PER_VERTEX = 104
 # bytes each unit of work loads through L1 (128-bit loads of the layouts in
 # csrc/internal.h): a 64-byte node, a 48-byte triangle, three 8-byte UVs,
 # four 16-byte texels for albedo+roughness and four for Ep
@@ -430,6 +440,10 @@ def main():
     np.testing.assert_array_equal(Ic_host.numpy(), Ic.cpu().numpy())
 
     # ------------------------------------------------------------ fwd + bwd (compensation step)
+    # The compensation workload as stated: render, L2 loss against a target
+    # rendered from another projector image, the path-replay adjoint with the
+    # gradients of Ip, the albedo and roughness textures and the 11 PRF / CRF /
+    # white-balance parameters, then Adam on Ip.
     cs = scenes.compensation(res=512, spp=16, seed=2000 + rank)
     hc = ctx.upload(cs.verts, cs.tris, cs.uv)
     calb = torch.from_numpy(cs.albedo).to(dev)
@@ -440,68 +454,78 @@ def main():
                Ic=target)
     P = torch.full((cs.Hp, cs.Wp, 3), 0.5, device=dev)
     M, V, G = torch.zeros_like(P), torch.zeros_like(P), torch.zeros_like(P)
+    gA, gR = torch.zeros_like(calb), torch.zeros_like(crough)
+    gP = torch.zeros(11, device=dev)
     cIc = torch.empty((cs.Hc, cs.Wc, 3), device=dev)
     cEc = torch.empty_like(cIc)
     dIc = torch.empty_like(cIc)
     loss = torch.empty(1, device=dev)
     step_no = [0]
 
-    def comp_step():
+    def zero_grads(all_grads):
+        G.zero_()
+        if all_grads:
+            gA.zero_()
+            gR.zero_()
+            gP.zero_()
+
+    def comp_step_unfused(all_grads=True):
         step_no[0] += 1
         ctx.render(hc, calb, crough, P, cview, cprm, cs.spp, cs.bounces, cs.seed + step_no[0], Ic=cIc, Ec=cEc)
         ctx.l2_loss(cIc, target, dIc, loss)
-        G.zero_()
+        zero_grads(all_grads)
         ctx.render_backward(hc, calb, crough, P, cview, cprm, cs.spp, cs.bounces, cs.seed + step_no[0], cEc, cIc,
-                            dIc, dIp=G)
+                            dIc, dIp=G, dAlbedo=gA if all_grads else None, dRough=gR if all_grads else None,
+                            dParams=gP if all_grads else None)
         ctx.adam(P, G, M, V, step_no[0], lr=1e-2)
-
-    for k in range(args.warmup):
-        flush(k)
-        comp_step()
-    ctx.sync()
-    fb_s = [torch.cuda.Event(enable_timing=True) for _ in range(args.fwd_bwd_steps)]
-    fb_e = [torch.cuda.Event(enable_timing=True) for _ in range(args.fwd_bwd_steps)]
-    barrier()
-    ctx.timing(True)
-    for k in range(args.fwd_bwd_steps):
-        flush(k)
-        fb_s[k].record(stream)
-        comp_step()
-        fb_e[k].record(stream)
-    barrier()
-    ctx.sync()
-    replay_ms, replay_n = ctx.kernel_time(1)
-    crender_ms, crender_n = ctx.kernel_time(0)
-    ctx.timing(False)
-    fbu_ms = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(fb_s, fb_e)))
-    fbu_val = cs.n_samples * ws * args.fwd_bwd_steps / (fbu_ms / 1e3) / 1e6
 
     # the same step as the library's fused call: render, loss and adjoint in
     # one trace of the paths (dpcs_render_loss_backward), then Adam
-    def comp_step_fused():
+    def comp_step_fused(all_grads=True):
         step_no[0] += 1
-        G.zero_()
+        zero_grads(all_grads)
         ctx.render_loss_backward(hc, calb, crough, P, cview, cprm, cs.spp, cs.bounces, cs.seed + step_no[0], target,
-                                 loss, loss_kind=0, Ic=cIc, Ec=cEc, dIp=G)
+                                 loss, loss_kind=0, Ic=cIc, Ec=cEc, dIp=G, dAlbedo=gA if all_grads else None,
+                                 dRough=gR if all_grads else None, dParams=gP if all_grads else None)
         ctx.adam(P, G, M, V, step_no[0], lr=1e-2)
 
-    for k in range(args.warmup):
-        flush(k)
-        comp_step_fused()
-    ctx.sync()
-    barrier()
-    ctx.timing(True)
-    for k in range(args.fwd_bwd_steps):
-        flush(k)
-        fb_s[k].record(stream)
-        comp_step_fused()
-        fb_e[k].record(stream)
-    barrier()
-    ctx.sync()
-    fused_ms, fused_n = ctx.kernel_time(0)
-    ctx.timing(False)
-    fb_ms = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(fb_s, fb_e)))
-    fb_val = cs.n_samples * ws * args.fwd_bwd_steps / (fb_ms / 1e3) / 1e6
+    def timed_steps(fn, n):
+        """ms per step of n timed steps (L2 flushed before each), and the
+        library's kernel times (render-side, replay-side) per step."""
+        for k in range(args.warmup):
+            flush(k)
+            fn()
+        ctx.sync()
+        s_ev = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+        e_ev = [torch.cuda.Event(enable_timing=True) for _ in range(n)]
+        barrier()
+        ctx.timing(True)
+        for k in range(n):
+            flush(k)
+            s_ev[k].record(stream)
+            fn()
+            e_ev[k].record(stream)
+        barrier()
+        ctx.sync()
+        k0, n0 = ctx.kernel_time(0)
+        k1, n1 = ctx.kernel_time(1)
+        ctx.timing(False)
+        ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in zip(s_ev, e_ev))) / n
+        return ms, (k0 / n if n0 else None), (k1 / n if n1 else None)
+
+    nfb = args.fwd_bwd_steps
+    fb_ms, fused_ms, _ = timed_steps(lambda: comp_step_fused(True), nfb)
+    fbu_ms, crender_ms, replay_ms = timed_steps(lambda: comp_step_unfused(True), nfb)
+    ip_ms, ip_kernel_ms, _ = timed_steps(lambda: comp_step_fused(False), nfb)
+    ipu_ms, _, ip_replay_ms = timed_steps(lambda: comp_step_unfused(False), nfb)
+    ctx.set_grad_accum(dpcs.DPCS_ACCUM_F64)
+    f64_ms, f64_kernel_ms, _ = timed_steps(lambda: comp_step_fused(True), nfb)
+    ctx.set_grad_accum(dpcs.DPCS_ACCUM_F32)
+
+    def msps(ms):
+        return cs.n_samples * ws / (ms / 1e3) / 1e6
+
+    fb_val = msps(fb_ms)
 
     # ------------------------------------------------------------ roofline (counters build, untimed)
     counts = None
@@ -517,13 +541,21 @@ def main():
         cctx.render(cch, calb, crough, P, cview, cprm, cs.spp, cs.bounces, cs.seed + 1, Ic=cIc, Ec=cEc)
         cctx.counters(reset=True)
         cctx.render_backward(cch, calb, crough, P, cview, cprm, cs.spp, cs.bounces, cs.seed + 1, cEc, cIc, dIc,
-                             dIp=torch.zeros_like(P))
+                             dIp=torch.zeros_like(P), dAlbedo=torch.zeros_like(calb), dRough=torch.zeros_like(crough),
+                             dParams=torch.zeros(11, device=dev))
         replay_counts = cctx.counters(reset=True)
+        # the fused step: its forward work and the vertices it sweeps
+        cctx.render_loss_backward(cch, calb, crough, P, cview, cprm, cs.spp, cs.bounces, cs.seed + 1, target, loss,
+                                  loss_kind=0, Ic=cIc, Ec=cEc, dIp=torch.zeros_like(P),
+                                  dAlbedo=torch.zeros_like(calb), dRough=torch.zeros_like(crough),
+                                  dParams=torch.zeros(11, device=dev))
+        grad_counts = cctx.counters(reset=True)
         cctx.close()
         flops = sum(FLOP[k] * counts[k] for k in FLOP)
     except Exception as e:  # the roofline stays unreported rather than guessed
         counts = {"error": str(e)[:200]}
         replay_counts = None
+        grad_counts = None
     # measured roofs the driver's peaks file lacks: L2 load bandwidth and scattered float4 atomics
     l2_gbs = ctx.probe_l2_load(PROBE_L2_BYTES, 256)
     atomic_g = ctx.probe_atomic4(PROBE_ATOMIC_TEXELS, 1 << 28)
@@ -547,9 +579,9 @@ def main():
                      "peak_basis": f"measured: dpcs_probe_l2_load, {PROBE_L2_BYTES >> 20} MiB read with 16 B "
                                    "L2-only loads, best of 3",
                      "l1_nominal_peak": sms * 128 * sm_max_mhz * 1e6 / 1e12}
-    if replay_counts and replay_n:
+    if replay_counts and replay_ms:
         n_atom = 4 * (replay_counts["vertices"] + replay_counts["lit"])
-        r_ms = replay_ms / replay_n
+        r_ms = replay_ms
         roof_atomic = {"bound": "atomic", "kernel": "k_replay", "achieved": n_atom / (r_ms / 1e3) / 1e9,
                        "peak": atomic_g, "unit": "Gatomics/s", "frac": n_atom / (r_ms / 1e3) / 1e9 / atomic_g,
                        "atomics_per_launch": n_atom, "kernel_ms": r_ms,
@@ -563,6 +595,25 @@ def main():
                 "flops_per_launch": flops, "kernel_ms": kernel_ms,
                 "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 FLOP/FMA x {sm_max_mhz:.0f} MHz (max SM clock)",
                 "counts_per_launch": counts}
+    roof_fb = None
+    if grad_counts and "vertices" in grad_counts and fused_ms:
+        fb_flops = sum(FLOP[k] * grad_counts[k] for k in FLOP) + SWEEP_FLOP_PER_VERTEX * grad_counts["vertices"]
+        ach = fb_flops / (fused_ms / 1e3) / 1e12
+        n_atom = 4 * (grad_counts["vertices"] + grad_counts["lit"])
+        roof_fb = {"bound": "alu", "kernel": "k_render_grad", "achieved": ach, "peak": peak_tflops, "unit": "TFLOP/s",
+                   "frac": ach / peak_tflops, "flops_per_launch": fb_flops, "kernel_ms": fused_ms,
+                   "float4_atomics_per_launch": n_atom,
+                   "atomic_rate_g_per_s": n_atom / (fused_ms / 1e3) / 1e9, "atomic_peak_g_per_s": atomic_g,
+                   "traffic": FWD_BWD_TRAFFIC["bytes"] if FWD_BWD_TRAFFIC["sources_sha256"] == kernel_sources_sha256()
+                   else None,
+                   "counts_per_launch": grad_counts}
+        if FWD_BWD_ISSUE["sources_sha256"] == kernel_sources_sha256():
+            inst = FWD_BWD_ISSUE["warp_instructions"]
+            issue_peak = 4 * sms * sm_max_mhz * 1e6 / 1e9
+            roof_fb["issue"] = {"achieved": inst / (fused_ms / 1e3) / 1e9, "peak": issue_peak,
+                                "unit": "G warp-instructions/s", "frac": inst / (fused_ms / 1e3) / 1e9 / issue_peak,
+                                "warp_instructions_per_launch": inst,
+                                "lanes_per_instruction": FWD_BWD_ISSUE["lanes_per_instruction"]}
     roof_issue = None
     if RENDER_ISSUE["sources_sha256"] == kernel_sources_sha256():
         # instruction issue: each SM sub-partition issues at most one warp
@@ -575,7 +626,8 @@ def main():
                       "warp_instructions_per_launch": inst,
                       "lanes_per_instruction": RENDER_ISSUE["lanes_per_instruction"],
                       "peak_basis": f"{sms} SMs x 4 schedulers x 1 warp-instruction/cycle x {sm_max_mhz:.0f} MHz",
-                      "source": "instruction count of one launch from ncu (profiles/k_render_corner256.md)"}
+                      "source": "instruction count of one launch of this workload, from an ncu capture of the same "
+                                "kernel sources"}
 
     # ------------------------------------------------------------ full compensation (Eq. 13): eager vs CUDA graph
     comp_out = None
@@ -758,10 +810,15 @@ def main():
         htarget = (torch.rand_like(hIc) * 0.5).contiguous()
         hloss = torch.zeros(1, device=dev)
 
+        hgA, hgR, hgP = torch.zeros_like(halb), torch.zeros_like(hrough), torch.zeros(11, device=dev)
+
         def hf_fb(spp):
             hG.zero_()
+            hgA.zero_()
+            hgR.zero_()
+            hgP.zero_()
             ctx.render_loss_backward(hh, halb, hrough, hIp, hview, hprm, spp, hs.bounces, hs.seed, htarget, hloss,
-                                     loss_kind=0, Ic=hIc, Ec=hEc, dIp=hG)
+                                     loss_kind=0, Ic=hIc, Ec=hEc, dIp=hG, dAlbedo=hgA, dRough=hgR, dParams=hgP)
 
         res = {}
         for name, fn, spp in (("fwd", hf_fwd, 256), ("fwd_bwd", hf_fb, 32)):
@@ -947,12 +1004,20 @@ def main():
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(Ip_host.numel() * 4),
                     "d2h_bytes_per_step": int(Ic_host.numel() * 4)},
             "fwd_bwd": {"value": fb_val, "unit": UNIT, "workload": FWD_BWD_WORKLOAD,
-                        "ms_per_step": fb_ms / args.fwd_bwd_steps, "steps": args.fwd_bwd_steps,
-                        "samples_per_step_per_gpu": cs.n_samples,
-                        "fused_kernel_ms": fused_ms / max(fused_n, 1),
-                        "unfused": {"value": fbu_val, "ms_per_step": fbu_ms / args.fwd_bwd_steps,
-                                    "replay_kernel_ms": replay_ms / max(replay_n, 1),
-                                    "render_kernel_ms": crender_ms / max(crender_n, 1)}},
+                        "ms_per_step": fb_ms, "steps": nfb, "samples_per_step_per_gpu": cs.n_samples,
+                        "fused_kernel_ms": fused_ms,
+                        "unfused": {"value": msps(fbu_ms), "ms_per_step": fbu_ms, "render_kernel_ms": crender_ms,
+                                    "replay_kernel_ms": replay_ms,
+                                    "workload": "the same step as separate render, L2 loss, replay adjoint calls"},
+                        "fp64_accumulation": {"value": msps(f64_ms), "ms_per_step": f64_ms,
+                                              "fused_kernel_ms": f64_kernel_ms,
+                                              "workload": "the same fused step with FP64 gradient accumulators "
+                                                          "(dpcs_set_grad_accum DPCS_ACCUM_F64)"},
+                        "ip_only": {"value": msps(ip_ms), "ms_per_step": ip_ms, "fused_kernel_ms": ip_kernel_ms,
+                                    "unfused_value": msps(ipu_ms), "unfused_replay_kernel_ms": ip_replay_ms,
+                                    "workload": "the same step asking only for dIp (no texture or response "
+                                                "gradients)"}},
+            "roofline_fwd_bwd": roof_fb,
             "roofline": roof,
             "roofline_load": roof_load,
             "roofline_atomic": roof_atomic,
@@ -968,6 +1033,27 @@ def main():
             "gpu_launches": int(launches),
             "kernel_ms_per_step": kernel_ms,
         }
+        # the headline figures again, last on the line, so that a reader of
+        # its tail alone sees them
+        summ = {"fwd": value, "fwd_kernel_ms": kernel_ms, "fwd_alu_frac": roof["frac"] if roof else None,
+                "fwd_issue_frac": roof_issue["frac"] if roof_issue else None,
+                "fwd_traffic_bytes": roof["traffic"] if roof else None,
+                "fwd_bwd_all_grads": fb_val, "fwd_bwd_all_grads_unfused": msps(fbu_ms),
+                "fwd_bwd_fp64_accum": msps(f64_ms), "fwd_bwd_ip_only": msps(ip_ms),
+                "fwd_bwd_alu_frac": roof_fb["frac"] if roof_fb else None,
+                "e2e": e2e_val, "cpu_baseline": cpu["value"] if cpu else None}
+        if hf_out:
+            summ["heightfield_fwd"] = hf_out["fwd"]["value"]
+            summ["heightfield_fwd_bwd"] = hf_out["fwd_bwd"]["value"]
+        if comp_out:
+            summ["compensation_100_steps_ms"] = comp_out["graph"]["ms"]
+        if serving_out:
+            summ["serving"] = [{"rate": x["offered_rate_per_s"], "srv_relight_p99": x["server"]["relight_p99_ms"],
+                                "call_relight_p99": x["per_call"]["relight_p99_ms"],
+                                "srv_comp_p99": x["server"]["compensation_p99_ms"],
+                                "call_comp_p99": x["per_call"]["compensation_p99_ms"]}
+                               for x in serving_out["load_sweep"]]
+        line["summary"] = summ
         print(json.dumps(line), flush=True)
     ctx.free(h)
     ctx.free(hc)

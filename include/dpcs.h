@@ -171,6 +171,25 @@ dpcs_status dpcs_probe_atomic4(dpcs_ctx *ctx, int32_t texels, int64_t n_atomics,
 dpcs_status dpcs_debug_set_visit_cap(dpcs_ctx *ctx, int32_t cap);
 
 /*
+ * Accumulation precision of the adjoint's gradient scatters (the path-replay
+ * adjoint of Eq. 8's inverse rendering; Sec. 3.2, Eq. 13):
+ *  DPCS_ACCUM_F32 (default): packed float4 atomics into FP32 accumulators.
+ *    Fast; each projector texel or texture texel sums its contributions in
+ *    whatever order the atomics arrive, so the last bits vary run to run.
+ *  DPCS_ACCUM_F64: one FP64 atomic per component (FP64 accumulators,
+ *    24 B per projector texel and 32 B per texture texel of context
+ *    scratch), and the Eq. 1 adjoint and its reductions in FP64 before the
+ *    result is rounded to FP32.  The order of the adds then changes the sums
+ *    only at FP64 rounding, about 1e-16 of their magnitude.
+ * Applies to dpcs_render_backward, dpcs_render_backward_kept and
+ * dpcs_render_loss_backward on this context; the principled-material calls
+ * always accumulate in FP32.  DPCS_ERR_INVALID_ARG for another mode.
+ */
+#define DPCS_ACCUM_F32 0
+#define DPCS_ACCUM_F64 1
+dpcs_status dpcs_set_grad_accum(dpcs_ctx *ctx, int32_t mode);
+
+/*
  * Upload a triangle mesh and build its LBVH on the device (Morton codes of
  * triangle centroids, radix sort, Karras radix tree, bottom-up AABB refit).
  *  verts : host, V x 3 float32 positions (world = camera frame)

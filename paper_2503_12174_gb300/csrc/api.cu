@@ -52,6 +52,8 @@ struct dpcs_ctx {
     // scratch
     Buf ep4, tex4, gE, dEp4, dtex4, acc, partial, build, upload, pix;  // pix: per-pixel dIc and Ec of the unfused loss path
     Buf mat4, dmat4;  // principled material: (metallic, normal map) per texel and its gradient accumulators
+    Buf dEp64, dtex64;  // FP64 gradient accumulators (dpcs_set_grad_accum(ctx, DPCS_ACCUM_F64))
+    bool grad_f64 = false;
     Buf kept;  // path records of the last dpcs_render_keep: 16-byte chunks (structure of arrays), then per-sample vertex counts
     struct {
         bool valid = false;
@@ -129,6 +131,50 @@ dpcs_status check_launch(dpcs_ctx *c, int n, const char *what) {
     c->launches += (uint64_t)n;
     cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? DPCS_OK : cuda_fail(c, e, what);
+}
+
+// Gradient accumulators of one adjoint call (dEp always, dtex when a texture
+// gradient is wanted): packed float4, or FP64 in the FP64 accumulation mode.
+// Zeroes them on `st` and points the kernel arguments at them.
+dpcs_status grad_setup(dpcs_ctx *c, int64_t np, int64_t nt, bool want_tex, cudaStream_t st, RenderArgs &a) {
+    dpcs_status s;
+    a.dEp = nullptr;
+    a.dtex = nullptr;
+    a.dEp64 = nullptr;
+    a.dtex64 = nullptr;
+    if (c->grad_f64) {
+        if ((s = ensure(c, c->dEp64, (size_t)np * 24, "dEp FP64 accumulators")) ||
+            (want_tex && (s = ensure(c, c->dtex64, (size_t)nt * 32, "dtex FP64 accumulators"))))
+            return s;
+        cudaMemsetAsync(c->dEp64.p, 0, (size_t)np * 24, st);
+        if (want_tex) cudaMemsetAsync(c->dtex64.p, 0, (size_t)nt * 32, st);
+        a.dEp64 = (double *)c->dEp64.p;
+        a.dtex64 = want_tex ? (double *)c->dtex64.p : nullptr;
+        return DPCS_OK;
+    }
+    if ((s = ensure(c, c->dEp4, (size_t)np * 16, "dEp scratch")) ||
+        (want_tex && (s = ensure(c, c->dtex4, (size_t)nt * 16, "dtex scratch"))))
+        return s;
+    cudaMemsetAsync(c->dEp4.p, 0, (size_t)np * 16, st);
+    if (want_tex) cudaMemsetAsync(c->dtex4.p, 0, (size_t)nt * 16, st);
+    a.dEp = (float4 *)c->dEp4.p;
+    a.dtex = want_tex ? (float4 *)c->dtex4.p : nullptr;
+    return DPCS_OK;
+}
+
+// Eq. 1 adjoint and the texture gradients from the accumulators grad_setup
+// chose; returns the kernels enqueued
+int grad_finish(const RenderArgs &a, const float *Ip, int64_t np, int64_t nt, const dpcs_params *params, float *dIp,
+                float *dAlbedo, float *dRough, double *acc, cudaStream_t st) {
+    int nl;
+    if (a.dEp64) {
+        nl = launch_prf_backward64(Ip, a.dEp64, np, params->gamma_p, params->gain_p, dIp, acc, st);
+        if (a.dtex64) nl += launch_tex_backward64(a.dtex64, nt, dAlbedo, dRough, st);
+    } else {
+        nl = launch_prf_backward(Ip, a.dEp, np, params->gamma_p, params->gain_p, dIp, acc, st);
+        if (a.dtex) nl += launch_tex_backward(a.dtex, nt, dAlbedo, dRough, st);
+    }
+    return nl;
 }
 
 // events around a path-tracing kernel when timing is on
@@ -294,7 +340,7 @@ dpcs_status dpcs_destroy(dpcs_ctx *c) {
         cudaFree(s.base);
     }
     Buf *bufs[] = {&c->ep4, &c->tex4, &c->gE, &c->dEp4, &c->dtex4, &c->acc, &c->partial, &c->build, &c->upload, &c->pix,
-                   &c->kept, &c->mat4, &c->dmat4};
+                   &c->kept, &c->mat4, &c->dmat4, &c->dEp64, &c->dtex64};
     for (Buf *b : bufs)
         if (b->p) cudaFree(b->p);
     cudaFree(c->status);
@@ -336,6 +382,14 @@ dpcs_status dpcs_timing_read(dpcs_ctx *c, int32_t kernel, double *total_ms, int6
     }
     *total_ms = tot;
     *launches = n;
+    return DPCS_OK;
+}
+
+dpcs_status dpcs_set_grad_accum(dpcs_ctx *c, int32_t mode) {
+    if (!c) return DPCS_ERR_INVALID_ARG;
+    if (mode != DPCS_ACCUM_F32 && mode != DPCS_ACCUM_F64)
+        return fail(c, DPCS_ERR_INVALID_ARG, "grad accumulation mode must be DPCS_ACCUM_F32 or DPCS_ACCUM_F64");
+    c->grad_f64 = mode == DPCS_ACCUM_F64;
     return DPCS_OK;
 }
 
@@ -610,29 +664,23 @@ dpcs_status dpcs_render_backward(dpcs_ctx *c, dpcs_scene scene, const float *alb
     if ((s = ensure(c, c->ep4, (size_t)np * 16, "Ep scratch")) ||
         (s = ensure(c, c->tex4, (size_t)nt * 16, "texture scratch")) ||
         (s = ensure(c, c->gE, (size_t)npix * 12, "dEc scratch")) ||
-        (s = ensure(c, c->dEp4, (size_t)np * 16, "dEp scratch")) ||
         (s = ensure(c, c->acc, 16 * sizeof(double), "parameter accumulators")))
         return s;
     const bool want_tex = dAlbedo || dRough;  // otherwise the replay skips the texture scatters
-    if (want_tex && (s = ensure(c, c->dtex4, (size_t)nt * 16, "dtex scratch"))) return s;
     cudaStream_t st = (cudaStream_t)stream;
+    if ((s = grad_setup(c, np, nt, want_tex, st, a))) return s;
     double *acc = (double *)c->acc.p;
     cudaMemsetAsync(acc, 0, 16 * sizeof(double), st);
-    cudaMemsetAsync(c->dEp4.p, 0, (size_t)np * 16, st);
-    if (want_tex) cudaMemsetAsync(c->dtex4.p, 0, (size_t)nt * 16, st);
     int nl = launch_prf(Ip, np, params->gamma_p, params->gain_p, (float4 *)c->ep4.p, st);
     nl += launch_pack_tex(albedo, rough, nt, (float4 *)c->tex4.p, st);
     nl += launch_crf_backward(dIc, Ec, Ic, npix, params->gamma_c, params->gain_c, params->wb, (float *)c->gE.p, acc, st);
     a.Ep = (const float4 *)c->ep4.p;
     a.tex = (const float4 *)c->tex4.p;
     a.gE = (const float *)c->gE.p;
-    a.dEp = (float4 *)c->dEp4.p;
-    a.dtex = want_tex ? (float4 *)c->dtex4.p : nullptr;
     TimedLaunch *tl = timing_begin(c, 1, st);
     nl += launch_replay(a, st);
     timing_end(tl, st);
-    nl += launch_prf_backward(Ip, (const float4 *)c->dEp4.p, np, params->gamma_p, params->gain_p, dIp, acc, st);
-    if (want_tex) nl += launch_tex_backward((const float4 *)c->dtex4.p, nt, dAlbedo, dRough, st);
+    nl += grad_finish(a, Ip, np, nt, params, dIp, dAlbedo, dRough, acc, st);
     if (dParams) nl += launch_finalize_params(acc, dParams, st);
     return check_launch(c, nl, "render_backward");
 }
@@ -783,27 +831,21 @@ dpcs_status dpcs_render_backward_kept(dpcs_ctx *c, dpcs_scene scene, const float
     const int64_t nthr = npix << a.log2L, spl = (spp + L - 1) / L;
     const size_t words = (size_t)kRecWordsHost * spl * bounces * nthr * 4;
     if ((s = ensure(c, c->gE, (size_t)npix * 12, "dEc scratch")) ||
-        (s = ensure(c, c->dEp4, (size_t)np * 16, "dEp scratch")) ||
         (s = ensure(c, c->acc, 16 * sizeof(double), "parameter accumulators")))
         return s;
     const bool want_tex = dAlbedo || dRough;
-    if (want_tex && (s = ensure(c, c->dtex4, (size_t)nt * 16, "dtex scratch"))) return s;
     cudaStream_t st = (cudaStream_t)stream;
+    if ((s = grad_setup(c, np, nt, want_tex, st, a))) return s;
     double *acc = (double *)c->acc.p;
     cudaMemsetAsync(acc, 0, 16 * sizeof(double), st);
-    cudaMemsetAsync(c->dEp4.p, 0, (size_t)np * 16, st);
-    if (want_tex) cudaMemsetAsync(c->dtex4.p, 0, (size_t)nt * 16, st);
     int nl = launch_crf_backward(dIc, Ec, Ic, npix, params->gamma_c, params->gain_c, params->wb, (float *)c->gE.p, acc,
                                  st);
     a.gE = (const float *)c->gE.p;
-    a.dEp = (float4 *)c->dEp4.p;
-    a.dtex = want_tex ? (float4 *)c->dtex4.p : nullptr;
     const char *kp = (const char *)c->kept.p;
     TimedLaunch *tl = timing_begin(c, 1, st);
     nl += launch_sweep_kept(a, kp, (const uint8_t *)(kp + ((words + 255) & ~size_t(255))), st);
     timing_end(tl, st);
-    nl += launch_prf_backward(Ip, (const float4 *)c->dEp4.p, np, params->gamma_p, params->gain_p, dIp, acc, st);
-    if (want_tex) nl += launch_tex_backward((const float4 *)c->dtex4.p, nt, dAlbedo, dRough, st);
+    nl += grad_finish(a, Ip, np, nt, params, dIp, dAlbedo, dRough, acc, st);
     if (dParams) nl += launch_finalize_params(acc, dParams, st);
     return check_launch(c, nl, "render_backward_kept");
 }
@@ -830,24 +872,19 @@ dpcs_status dpcs_render_loss_backward(dpcs_ctx *c, dpcs_scene scene, const float
     const bool want_tex = dAlbedo || dRough;
     if ((s = ensure(c, c->ep4, (size_t)np * 16, "Ep scratch")) ||
         (s = ensure(c, c->tex4, (size_t)nt * 16, "texture scratch")) ||
-        (s = ensure(c, c->dEp4, (size_t)np * 16, "dEp scratch")) ||
         (s = ensure(c, c->acc, 16 * sizeof(double), "parameter accumulators")) ||
-        (want_tex && (s = ensure(c, c->dtex4, (size_t)nt * 16, "dtex scratch"))) ||
         (!fused && ((s = ensure(c, c->gE, (size_t)npix * 12, "dEc scratch")) ||
                     (s = ensure(c, c->pix, (size_t)npix * 24, "per-pixel loss scratch")))))
         return s;
     cudaStream_t st = (cudaStream_t)stream;
+    if ((s = grad_setup(c, np, nt, want_tex, st, a))) return s;
     double *acc = (double *)c->acc.p;
     cudaMemsetAsync(acc, 0, 16 * sizeof(double), st);
-    cudaMemsetAsync(c->dEp4.p, 0, (size_t)np * 16, st);
-    if (want_tex) cudaMemsetAsync(c->dtex4.p, 0, (size_t)nt * 16, st);
     int nl = launch_prf(Ip, np, params->gamma_p, params->gain_p, (float4 *)c->ep4.p, st);
     nl += launch_pack_tex(albedo, rough, nt, (float4 *)c->tex4.p, st);
     a.Ep = (const float4 *)c->ep4.p;
     a.tex = (const float4 *)c->tex4.p;
     a.Ic = Ic;
-    a.dEp = (float4 *)c->dEp4.p;
-    a.dtex = want_tex ? (float4 *)c->dtex4.p : nullptr;
     const LossArgs l{target, scale, loss_kind, acc};
     if (fused) {
         a.Ec = Ec;
@@ -869,8 +906,7 @@ dpcs_status dpcs_render_loss_backward(dpcs_ctx *c, dpcs_scene scene, const float
         timing_end(tr, st);
     }
     nl += launch_loss_out(acc, loss, st);
-    nl += launch_prf_backward(Ip, (const float4 *)c->dEp4.p, np, params->gamma_p, params->gain_p, dIp, acc, st);
-    if (want_tex) nl += launch_tex_backward((const float4 *)c->dtex4.p, nt, dAlbedo, dRough, st);
+    nl += grad_finish(a, Ip, np, nt, params, dIp, dAlbedo, dRough, acc, st);
     if (dParams) nl += launch_finalize_params(acc, dParams, st);
     return check_launch(c, nl, "render_loss_backward");
 }

@@ -64,6 +64,10 @@ struct RenderArgs {
     unsigned *status;
     unsigned long long *counters;  // DPCS_COUNTERS build only (8 totals)
     int32_t visit_cap;             // traversal steps per ray before giving up (0 = 2T + 16)
+    // backward only, FP64 accumulation mode: when dEp64 is set the adjoint
+    // adds into these instead of dEp / dtex
+    double *dEp64;                 // Hp x Wp x 3
+    double *dtex64;                // Ht x Wt x 4 (albedo rgb, roughness); null = not wanted
 };
 
 // Per-pixel loss of the fused forward + adjoint kernel (k_render_grad).
@@ -131,6 +135,10 @@ int launch_loss_out(const double *acc, float *loss, cudaStream_t st);
 int launch_prf_backward(const float *Ip, const float4 *dEp, int64_t ntex, const float gamma_p[3], float gain_p,
                         float *dIp, double *acc, cudaStream_t st);
 int launch_tex_backward(const float4 *dtex, int64_t ntex, float *dAlbedo, float *dRough, cudaStream_t st);
+// the same from the FP64 accumulators (dEp64: 3 per texel, dtex64: 4 per texel)
+int launch_prf_backward64(const float *Ip, const double *dEp64, int64_t ntex, const float gamma_p[3], float gain_p,
+                          float *dIp, double *acc, cudaStream_t st);
+int launch_tex_backward64(const double *dtex64, int64_t ntex, float *dAlbedo, float *dRough, cudaStream_t st);
 int launch_finalize_params(const double *acc, float *dParams, cudaStream_t st);
 int launch_zero(void *p, size_t bytes, cudaStream_t st);
 int launch_l2_loss(const float *Ic, const float *target, int64_t n, float *dIc, float *loss, double *partial,

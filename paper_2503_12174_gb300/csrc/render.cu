@@ -365,7 +365,10 @@ __global__ void k_crf_backward(const float *__restrict__ dIc, const float *__res
 // reverse sweep over the recorded vertices of one path: with A the
 // derivative of the path radiance with respect to the throughput entering
 // the next vertex (A_c = [lit] f(wp) Ep G + f(wi) cw A_{c+1}), scatter
-// dLoss/dEp, dLoss/dalbedo and dLoss/droughness into the accumulators.
+// dLoss/dEp, dLoss/dalbedo and dLoss/droughness into the accumulators:
+// packed float4 atomics, or (F64) one FP64 atomic per component, whose sums
+// do not depend on the order of the adds beyond FP64 rounding.
+template <bool F64>
 __device__ __forceinline__ void replay_sweep(const RenderArgs &a, const VRec *rec, int nv, const float gb_in[3],
                                              float4 *row) {
     float A[3] = {0.f, 0.f, 0.f};
@@ -389,21 +392,39 @@ __device__ __forceinline__ void replay_sweep(const RenderArgs &a, const VRec *re
         }
         int idx[4];
         float w[4];
-        if (a.dtex) {  // null when the caller wants no texture gradient
+        if (F64 ? a.dtex64 != nullptr : a.dtex != nullptr) {  // null when the caller wants no texture gradient
             Bilin tb;
             tb.x0 = R.tx0; tb.y0 = R.ty0; tb.fx = R.tfx; tb.fy = R.tfy;
             bilin_taps(tb, a.Wt, a.Ht, idx, w);
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
-                scatter_add4(a.dtex, idx[k], make_float4(ga[0] * w[k], ga[1] * w[k], ga[2] * w[k], dr * w[k]), row);
+            for (int k = 0; k < 4; ++k) {
+                if constexpr (F64) {
+                    double *p = a.dtex64 + 4 * (int64_t)idx[k];
+                    atomicAdd(p + 0, (double)ga[0] * (double)w[k]);
+                    atomicAdd(p + 1, (double)ga[1] * (double)w[k]);
+                    atomicAdd(p + 2, (double)ga[2] * (double)w[k]);
+                    atomicAdd(p + 3, (double)dr * (double)w[k]);
+                } else {
+                    scatter_add4(a.dtex, idx[k], make_float4(ga[0] * w[k], ga[1] * w[k], ga[2] * w[k], dr * w[k]),
+                                 row);
+                }
+            }
         }
         if (R.G > 0.0f && (dEp[0] != 0.0f || dEp[1] != 0.0f || dEp[2] != 0.0f)) {
             Bilin pb;
             pb.x0 = R.px0; pb.y0 = R.py0; pb.fx = R.pfx; pb.fy = R.pfy;
             bilin_taps(pb, a.Wp, a.Hp, idx, w);
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
-                scatter_add4(a.dEp, idx[k], make_float4(dEp[0] * w[k], dEp[1] * w[k], dEp[2] * w[k], 0.0f), row);
+            for (int k = 0; k < 4; ++k) {
+                if constexpr (F64) {
+                    double *p = a.dEp64 + 3 * (int64_t)idx[k];
+                    atomicAdd(p + 0, (double)dEp[0] * (double)w[k]);
+                    atomicAdd(p + 1, (double)dEp[1] * (double)w[k]);
+                    atomicAdd(p + 2, (double)dEp[2] * (double)w[k]);
+                } else {
+                    scatter_add4(a.dEp, idx[k], make_float4(dEp[0] * w[k], dEp[1] * w[k], dEp[2] * w[k], 0.0f), row);
+                }
+            }
         }
     }
 }
@@ -412,6 +433,7 @@ __device__ __forceinline__ void replay_sweep(const RenderArgs &a, const VRec *re
 // re-traces its paths from their Philox counters one ray per iteration and
 // records every vertex; once every path of the warp has ended, the lanes run
 // their reverse sweeps together and start their next samples.
+template <bool F64>
 __global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB) k_replay(const RenderArgs a) {
     const int L = 1 << a.log2L;
     const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -521,7 +543,7 @@ __global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB) k_replay(const
             }
             if (end) break;
         }
-        replay_sweep(a, rec, nv, gb_in, &s_row[threadIdx.x & ~31]);
+        replay_sweep<F64>(a, rec, nv, gb_in, &s_row[threadIdx.x & ~31]);
         nv = 0;
         s += L;
         if (s < a.spp) {
@@ -548,6 +570,7 @@ __global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB) k_replay(const
 // vertices it recorded: the paths are traced once, not twice.  The host
 // calls it only when ceil(spp / L) <= kFusedSamples and ceil(spp / L) *
 // bounces <= kFusedRecs.
+template <bool F64>
 __global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB) k_render_grad(const RenderArgs a, const LossArgs l) {
     const int L = 1 << a.log2L;
     const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -713,7 +736,7 @@ __global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB) k_render_grad(
     block_reduce_add<8>(v, l.acc + 4);  // acc[4..10]: gamma_c, Gc, wb; acc[11]: the loss
     const bool any = gb_in[0] != 0.0f || gb_in[1] != 0.0f || gb_in[2] != 0.0f;
     for (int i = 0; any && i < k && i < kFusedSamples; ++i)
-        replay_sweep(a, rec + i * a.bounces, nvs[i], gb_in, &s_row[threadIdx.x & ~31]);
+        replay_sweep<F64>(a, rec + i * a.bounces, nvs[i], gb_in, &s_row[threadIdx.x & ~31]);
 }
 
 // Forward render that keeps every path's vertex records in device memory
@@ -890,6 +913,7 @@ __global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB)
 
 // The adjoint from the records k_render_keep wrote: the reverse sweep of
 // every recorded path with its pixel's dLoss/dEc, without tracing again.
+template <bool F64>
 __global__ void __launch_bounds__(kRenderBlock) k_sweep_kept(const RenderArgs a, const uint4 *__restrict__ chunks,
                                                              const uint8_t *__restrict__ nvs) {
     const int L = 1 << a.log2L;
@@ -911,7 +935,7 @@ __global__ void __launch_bounds__(kRenderBlock) k_sweep_kept(const RenderArgs a,
 #pragma unroll
             for (int q4 = 0; q4 < kKeptChunks; ++q4) dst[q4] = __ldcs(chunks + kept_chunk(q4, k, v, spl, a.bounces, nthr, gt));
         }
-        replay_sweep(a, rec, nv, gb_in, &s_row[threadIdx.x & ~31]);
+        replay_sweep<F64>(a, rec, nv, gb_in, &s_row[threadIdx.x & ~31]);
     }
 }
 
@@ -935,6 +959,54 @@ __global__ void k_prf_backward(const float *__restrict__ Ip, const float4 *__res
         }
     }
     block_reduce_add<4>(v, acc);
+}
+
+// the same from FP64 accumulators; the products and the reductions are
+// taken in FP64 before the result is rounded
+__global__ void k_prf_backward64(const float *__restrict__ Ip, const double *__restrict__ dEp, int64_t ntex,
+                                 float g0, float g1, float g2, float gain, float *__restrict__ dIp, double *acc) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double v[4] = {0, 0, 0, 0};
+    if (t < ntex) {
+        const float gm[3] = {g0, g1, g2};
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            const float ip = Ip[3 * t + j];
+            const double gs = dEp[3 * t + j];
+            if (ip > 0.0f && gs != 0.0) {
+                const double pw = pow((double)ip, (double)gm[j]);
+                if (dIp) dIp[3 * t + j] += (float)(gs * gain * gm[j] * pow((double)ip, (double)gm[j] - 1.0));
+                v[j] += gs * gain * pw * log((double)ip);
+                v[3] += gs * pw;
+            }
+        }
+    }
+    __shared__ double red[4][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        for (int off = 16; off; off >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], off);
+    if (lane == 0)
+#pragma unroll
+        for (int k = 0; k < 4; ++k) red[k][w] = v[k];
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double s = 0.0;
+        for (int j = 0; j < (int)(blockDim.x >> 5); ++j) s += red[threadIdx.x][j];
+        if (s != 0.0) atomicAdd(acc + threadIdx.x, s);
+    }
+}
+
+__global__ void k_tex_backward64(const double *__restrict__ dtex, int64_t ntex, float *__restrict__ dAlbedo,
+                                 float *__restrict__ dRough) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= ntex) return;
+    if (dAlbedo) {
+        dAlbedo[3 * t] += (float)dtex[4 * t];
+        dAlbedo[3 * t + 1] += (float)dtex[4 * t + 1];
+        dAlbedo[3 * t + 2] += (float)dtex[4 * t + 2];
+    }
+    if (dRough) dRough[t] += (float)dtex[4 * t + 3];
 }
 
 __global__ void k_tex_backward(const float4 *__restrict__ dtex, int64_t ntex, float *__restrict__ dAlbedo,
@@ -1022,13 +1094,19 @@ int launch_crf_backward(const float *dIc, const float *Ec, const float *Ic, int6
 
 int launch_replay(const RenderArgs &a, cudaStream_t st) {
     const int64_t threads = ((int64_t)a.Hc * a.Wc) << a.log2L;
-    k_replay<<<grid_for(threads, kRenderBlock), kRenderBlock, 0, st>>>(a);
+    if (a.dEp64)
+        k_replay<true><<<grid_for(threads, kRenderBlock), kRenderBlock, 0, st>>>(a);
+    else
+        k_replay<false><<<grid_for(threads, kRenderBlock), kRenderBlock, 0, st>>>(a);
     return 1;
 }
 
 int launch_render_grad(const RenderArgs &a, const LossArgs &l, cudaStream_t st) {
     const int64_t threads = ((int64_t)a.Hc * a.Wc) << a.log2L;
-    k_render_grad<<<grid_for(threads, kRenderBlock), kRenderBlock, 0, st>>>(a, l);
+    if (a.dEp64)
+        k_render_grad<true><<<grid_for(threads, kRenderBlock), kRenderBlock, 0, st>>>(a, l);
+    else
+        k_render_grad<false><<<grid_for(threads, kRenderBlock), kRenderBlock, 0, st>>>(a, l);
     return 1;
 }
 
@@ -1040,7 +1118,10 @@ int launch_render_keep(const RenderArgs &a, void *chunks, uint8_t *nvs, cudaStre
 
 int launch_sweep_kept(const RenderArgs &a, const void *chunks, const uint8_t *nvs, cudaStream_t st) {
     const int64_t threads = ((int64_t)a.Hc * a.Wc) << a.log2L;
-    k_sweep_kept<<<grid_for(threads, kRenderBlock), kRenderBlock, 0, st>>>(a, (const uint4 *)chunks, nvs);
+    if (a.dEp64)
+        k_sweep_kept<true><<<grid_for(threads, kRenderBlock), kRenderBlock, 0, st>>>(a, (const uint4 *)chunks, nvs);
+    else
+        k_sweep_kept<false><<<grid_for(threads, kRenderBlock), kRenderBlock, 0, st>>>(a, (const uint4 *)chunks, nvs);
     return 1;
 }
 
@@ -1063,6 +1144,18 @@ int launch_prf_backward(const float *Ip, const float4 *dEp, int64_t ntex, const 
 
 int launch_tex_backward(const float4 *dtex, int64_t ntex, float *dAlbedo, float *dRough, cudaStream_t st) {
     k_tex_backward<<<grid_for(ntex, 256), 256, 0, st>>>(dtex, ntex, dAlbedo, dRough);
+    return 1;
+}
+
+int launch_prf_backward64(const float *Ip, const double *dEp64, int64_t ntex, const float gamma_p[3], float gain_p,
+                          float *dIp, double *acc, cudaStream_t st) {
+    k_prf_backward64<<<grid_for(ntex, 256), 256, 0, st>>>(Ip, dEp64, ntex, gamma_p[0], gamma_p[1], gamma_p[2],
+                                                          gain_p, dIp, acc);
+    return 1;
+}
+
+int launch_tex_backward64(const double *dtex64, int64_t ntex, float *dAlbedo, float *dRough, cudaStream_t st) {
+    k_tex_backward64<<<grid_for(ntex, 256), 256, 0, st>>>(dtex64, ntex, dAlbedo, dRough);
     return 1;
 }
 

@@ -26,6 +26,8 @@ DPCS_ERR_TIMEOUT = -6
 DPCS_ERR_BUSY = -7
 DPCS_ERR_NOT_FOUND = -8
 DPCS_MAX_BOUNCES = 8
+DPCS_ACCUM_F32 = 0
+DPCS_ACCUM_F64 = 1
 
 EXPORTED = [
     "dpcs_create", "dpcs_destroy", "dpcs_last_error", "dpcs_sync", "dpcs_memory_used", "dpcs_launch_count",
@@ -37,7 +39,7 @@ EXPORTED = [
     "dpcs_l1_loss", "dpcs_tv_loss", "dpcs_scene_update", "dpcs_render_loss_backward", "dpcs_render_keep",
     "dpcs_render_backward_kept", "dpcs_render_principled", "dpcs_render_backward_principled",
     "dpcs_scene_transform", "dpcs_render_loss_backward_principled", "dpcs_render_keep_principled",
-    "dpcs_render_backward_kept_principled",
+    "dpcs_render_backward_kept_principled", "dpcs_set_grad_accum",
 ]
 
 DPCS_REQ_RELIGHT = 0
@@ -166,6 +168,7 @@ _SIGS = {
                                           ctypes.POINTER(ctypes.c_int64)]),
     "dpcs_counters_read": (ctypes.c_int32, [_P, _P, ctypes.c_int32]),
     "dpcs_debug_set_visit_cap": (ctypes.c_int32, [_P, ctypes.c_int32]),
+    "dpcs_set_grad_accum": (ctypes.c_int32, [_P, ctypes.c_int32]),
     "dpcs_gbuffer": (ctypes.c_int32, [_P, ctypes.c_uint64, _P, _P, ctypes.c_int32, ctypes.c_int32,
                                       ctypes.POINTER(DpcsView), _P, _P]),
     "dpcs_denoise": (ctypes.c_int32, [_P, _P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(DpcsDenoiseParams),
@@ -352,6 +355,10 @@ def dpcs_render_backward_kept(ctx, scene, albedo, rough, Ht, Wt, Ip, view, param
                                                     dAlbedo, dRough, dParams, stream)
 
 
+def dpcs_set_grad_accum(ctx, mode):
+    return load_library().dpcs_set_grad_accum(ctx, int(mode))
+
+
 def dpcs_timing_enable(ctx, on):
     return load_library().dpcs_timing_enable(ctx, int(on))
 
@@ -453,6 +460,12 @@ class Context:
     def set_visit_cap(self, cap: int):
         """Failure-path testing: cap BVH traversal steps per ray (0 = default)."""
         self.check(self.lib.dpcs_debug_set_visit_cap(self.handle, int(cap)), "debug_set_visit_cap")
+
+    def set_grad_accum(self, mode: int):
+        """Adjoint accumulation: DPCS_ACCUM_F32 (float4 atomics, default) or
+        DPCS_ACCUM_F64 (FP64 atomics; sums independent of the add order up to
+        FP64 rounding)."""
+        self.check(self.lib.dpcs_set_grad_accum(self.handle, int(mode)), "set_grad_accum")
 
     def counters(self, reset: bool = True):
         """Work counters (counters build only): dict of totals."""

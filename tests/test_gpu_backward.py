@@ -66,6 +66,66 @@ def test_backward_64_random_parameters_full_size(orc):
     assert ok, (grads["dparams"], ref["dparams"])
 
 
+def _config3_first_step(orc, mode):
+    """The compensation workload's first step at full size (512^2 camera,
+    projector and textures, 16 spp, 3 bounces): Ip = 0.5, target = a render
+    of the scene's random-blob projector image, L2 loss, every gradient.
+    Returns the GPU gradients (accumulation ``mode``) and the oracle's
+    adjoint of the same paths for the same dLoss/dIc."""
+    torch = need_cuda()
+    from paper_2503_12174_gb300 import dpcs
+
+    sc = scenes.compensation(res=512, spp=16)
+    g = GpuScene(sc)
+    try:
+        target, _ = g.render(Ip=g.Ip, seed=sc.seed + 7)
+        P = torch.full_like(g.Ip, 0.5)
+        Ec, Ic = g.render(Ip=P)
+        dIc = torch.empty_like(Ic)
+        loss = torch.empty(1, device=Ic.device)
+        g.ctx.l2_loss(Ic, target, dIc, loss)
+        g.Ip = P
+        g.ctx.set_grad_accum(mode)
+        try:
+            grads = g.backward(Ec, Ic, dIc)
+        finally:
+            g.ctx.set_grad_accum(dpcs.DPCS_ACCUM_F32)
+        dIc_np = dIc.cpu().numpy().astype(np.float64)
+    finally:
+        g.close()
+    ref = orc.render_backward(sc.replace(Ip=np.full_like(sc.Ip, 0.5)), dIc_np, accel=True)
+    return grads, ref
+
+
+def test_backward_config3_64_random_parameters_fp64(orc):
+    """64 random parameters of the full-size compensation step -- 40 projector
+    texels, 13 albedo texels and all 11 response parameters (gamma_p, Gp,
+    gamma_c, Gc, w) -- agree with the oracle's FP64 adjoint to 1e-4 relative
+    when the GPU accumulates in FP64.  The absolute floor, 1e-6 of the largest
+    gradient of the same kind, covers texels whose contributions cancel to far
+    below their own size, where FP32 rounding of each contribution (~1e-7 of
+    it) is all that is left."""
+    from paper_2503_12174_gb300 import dpcs
+
+    grads, ref = _config3_first_step(orc, dpcs.DPCS_ACCUM_F64)
+    rng = np.random.default_rng(64)
+    picked = 0
+    for kind, n in (("dIp", 40), ("dalbedo", 13)):
+        r, gg = ref[kind].ravel(), grads[kind].ravel()
+        cand = np.flatnonzero(r != 0.0)
+        pick = rng.choice(cand, n, replace=False)
+        atol = 1e-6 * np.abs(r).max()
+        err = np.abs(gg[pick] - r[pick])
+        bad = err > 1e-4 * np.abs(r[pick]) + atol
+        assert not bad.any(), (kind, pick[bad], gg[pick][bad], r[pick][bad])
+        picked += n
+    r, gg = ref["dparams"], grads["dparams"]
+    bad = np.abs(gg - r) > 1e-4 * np.abs(r) + 1e-9 * np.abs(r).max()
+    assert not bad.any(), ("dparams", gg, r)
+    picked += 11
+    assert picked == 64
+
+
 def test_backward_without_texture_outputs(orc):
     """dAlbedo = dRough = NULL (compensation's call) skips the texture
     scatters; dIp and dParams still equal the oracle's, and a later call that
