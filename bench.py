@@ -590,11 +590,16 @@ def main():
                        "counts_per_launch": replay_counts}
         achieved = flops / (kernel_ms / 1e3) / 1e12
         traffic = RENDER_TRAFFIC["bytes"] if RENDER_TRAFFIC["sources_sha256"] == kernel_sources_sha256() else None
+        simt = {}
+        if counts.get("trav_warp_iters"):
+            simt["traversal"] = (counts["node_visits"] + counts["tri_tests"]) / (32.0 * counts["trav_warp_iters"])
+        if counts.get("path_warp_iters"):
+            simt["path_loop"] = (counts["rays"] + counts["shadow_rays"]) / (32.0 * counts["path_warp_iters"])
         roof = {"bound": "alu", "kernel": "k_render", "achieved": achieved, "peak": peak_tflops,
                 "unit": "TFLOP/s", "frac": achieved / peak_tflops, "traffic": traffic,
                 "flops_per_launch": flops, "kernel_ms": kernel_ms,
                 "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 FLOP/FMA x {sm_max_mhz:.0f} MHz (max SM clock)",
-                "counts_per_launch": counts}
+                "simt_efficiency": simt, "counts_per_launch": counts}
     roof_fb = None
     if grad_counts and "vertices" in grad_counts and fused_ms:
         fb_flops = sum(FLOP[k] * grad_counts[k] for k in FLOP) + SWEEP_FLOP_PER_VERTEX * grad_counts["vertices"]

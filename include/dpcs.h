@@ -128,12 +128,16 @@ dpcs_status dpcs_timing_enable(dpcs_ctx *ctx, int32_t on);
 dpcs_status dpcs_timing_read(dpcs_ctx *ctx, int32_t kernel, double *total_ms, int64_t *launches);
 
 /*
- * Work counters of a library built with DPCS_COUNTERS: out[0..7] = BVH node
+ * Work counters of a library built with DPCS_COUNTERS: out[0..9] = BVH node
  * visits, triangle tests, closest-hit rays, shadow rays, path vertices,
- * vertices lit by the projector, BRDF continuations, camera paths, summed
- * over every render / replay launch since the last reset (reset != 0 clears
- * them after reading).  Synchronous.  Returns DPCS_ERR_INVALID_ARG in a
- * library built without counters.  Measurement support for the roofline.
+ * vertices lit by the projector, BRDF continuations, camera paths, warp
+ * iterations of the traversal loop and warp iterations of the path loop
+ * (one ray per lane and iteration), summed over every render / replay launch
+ * since the last reset (reset != 0 clears them after reading).  The last two
+ * give SIMT efficiencies: (node visits + triangle tests) / (32 x traversal
+ * warp iterations) and rays / (32 x path warp iterations).  `out` holds 10
+ * values.  Synchronous.  Returns DPCS_ERR_INVALID_ARG in a library built
+ * without counters.  Measurement support for the roofline.
  */
 dpcs_status dpcs_counters_read(dpcs_ctx *ctx, uint64_t *out, int32_t reset);
 
@@ -169,6 +173,24 @@ dpcs_status dpcs_probe_atomic4(dpcs_ctx *ctx, int32_t texels, int64_t n_atomics,
  * Not part of the paper's method.
  */
 dpcs_status dpcs_debug_set_visit_cap(dpcs_ctx *ctx, int32_t cap);
+
+/*
+ * How dpcs_render traces its paths (the same estimator, Eqs. 3, 10; the same
+ * images bit for bit):
+ *  DPCS_PATH_MEGAKERNEL (default): one kernel; each lane runs its paths from
+ *    the camera to their last vertex.
+ *  DPCS_PATH_WAVEFRONT: per bounce, a closest-hit pass over the extension
+ *    rays of every live path and a shading pass (next-event estimation with
+ *    its shadow ray, BRDF continuation) that appends the paths that go on to
+ *    the next bounce's queue.  Paths run in chunks of `chunk` paths (0 keeps
+ *    the current value, 2^20 at creation; else a multiple of 32 in
+ *    [4096, 2^28]), whose state (64 B per path) is context scratch, plus 16 B
+ *    of running sum per (pixel, lane).
+ * DPCS_ERR_INVALID_ARG for another path or chunk.
+ */
+#define DPCS_PATH_MEGAKERNEL 0
+#define DPCS_PATH_WAVEFRONT 1
+dpcs_status dpcs_set_render_path(dpcs_ctx *ctx, int32_t path, int64_t chunk);
 
 /*
  * Accumulation precision of the adjoint's gradient scatters (the path-replay
@@ -576,7 +598,22 @@ typedef struct dpcs_serve_config {
     int32_t max_inflight;           /* batched iterations queued on the GPU at once (1..4) */
     int64_t samples_per_iteration;  /* camera samples one batched iteration aims at */
     int64_t quantum_samples;        /* samples every active relighting request gets first */
+    /* How the rest of an iteration is shared (after every relighting request's
+     * quantum).  DPCS_SERVE_DEADLINE: by earliest deadline, a request's
+     * deadline being its arrival plus slack x its work / est_samples_per_s
+     * (a compensation step counts its samples x 1.4 for the adjoint);
+     * DPCS_SERVE_FIXED_SHARE: one compensation step per request within
+     * compensation_share of the iteration, the rest to relighting in arrival
+     * order, and what relighting leaves to further compensation steps. */
+    int32_t policy;
+    int32_t pad;
+    double relight_slack;           /* deadline policy, > 0 */
+    double compensation_slack;      /* deadline policy, > 0 */
+    double est_samples_per_s;       /* deadline policy, > 0: the throughput the deadlines assume */
+    double compensation_share;      /* fixed-share policy, in (0, 1] */
 } dpcs_serve_config;
+#define DPCS_SERVE_DEADLINE 0
+#define DPCS_SERVE_FIXED_SHARE 1
 
 #define DPCS_REQ_RELIGHT 0
 #define DPCS_REQ_COMPENSATE 1

@@ -182,6 +182,16 @@ typedef struct {
  * before a render, read by scene_make */
 static int g_accel = 0;
 void or_set_accel(int on) { g_accel = on ? 1 : 0; }
+
+/* Adjoint diagnostics: 1 = scatter every projector and albedo contribution
+ * to its four bilinear taps with weight 1 instead of the tap's weight.  With
+ * dLoss/dIc replaced by its absolute value, every such contribution is
+ * nonnegative, and the result is, per texel, the total size of the
+ * contributions that reach it through any tap -- the scale by which rounding
+ * of a tap's weight (the FP32 position of the hit point in texel units) can
+ * move that texel's gradient.  Off in every parity computation. */
+static int g_unit_taps = 0;
+void or_set_unit_taps(int on) { g_unit_taps = on ? 1 : 0; }
 static void bvh_build(dscene *S);
 
 static void scene_make(dscene *S, const float *verts, const int32_t *tris, int32_t T, const float *uv)
@@ -1154,9 +1164,10 @@ int or_render_backward_m(const float *verts, const int32_t *tris, int32_t T, con
                         double cont = R->cont ? R->cw * An[j] : 0.0;                       /* w / f * A */
                         if (R->nee && R->unclipped[j])
                             for (int k = 0; k < 4; ++k)
-                                gEp[3 * R->proj_idx[k] + j] += gb * R->fp.f[j] * R->G * R->proj_w[k];
+                                gEp[3 * R->proj_idx[k] + j] +=
+                                    gb * R->fp.f[j] * R->G * (g_unit_taps ? 1.0 : R->proj_w[k]);
                         double ga = gb * (R->fp.drho[j] * ln_e + R->fi.drho[j] * cont);
-                        for (int k = 0; k < 4; ++k) gA[3 * R->tex_idx[k] + j] += ga * R->tex_w[k];
+                        for (int k = 0; k < 4; ++k) gA[3 * R->tex_idx[k] + j] += ga * (g_unit_taps ? 1.0 : R->tex_w[k]);
                         dr += gb * (R->fp.dr[j] * ln_e + R->fi.dr[j] * cont);
                         dm += gb * (R->fp.dm[j] * ln_e + R->fi.dm[j] * cont);
                         /* the normal enters f and cos_s (NEE), f and cos_i (continuation) */

@@ -266,10 +266,13 @@ def render(sc, pixels=None, *, albedo=None, rough=None, Ip=None, params=None, sp
 
 
 def render_backward(sc, dIc, pixels=None, *, albedo=None, rough=None, Ip=None, params=None, spp=None,
-                    bounces=None, seed=None, nthreads: int = 0, metallic=_SCENE, normal=_SCENE, accel: bool = False):
+                    bounces=None, seed=None, nthreads: int = 0, metallic=_SCENE, normal=_SCENE, accel: bool = False,
+                    unit_taps: bool = False):
     """FP64 adjoint.  ``dIc`` is (npix, 3) for a pixel list or (Hc, Wc, 3).
     Returns dict(dIp, dalbedo, drough, dparams[11]) plus dmetallic / dnormal
-    where those maps are used (see ``render``).  ``accel`` = timing mode."""
+    where those maps are used (see ``render``).  ``accel`` = timing mode.
+    ``unit_taps`` (a diagnostic, not the adjoint): projector and albedo
+    contributions reach each of their four bilinear taps with weight 1."""
     verts, tris, uv, albedo, rough, Ip = _scene_args(sc, albedo, rough, Ip)
     m, nm = _maps(sc, metallic, normal, albedo.shape[0], albedo.shape[1])
     P = make_params(params or sc.params)
@@ -284,15 +287,19 @@ def render_backward(sc, dIc, pixels=None, *, albedo=None, rough=None, Ip=None, p
     dM = None if m is None else np.zeros(m.shape)
     dN = None if nm is None else np.zeros(nm.shape)
     dP = np.zeros(11)
-    with _Accel(accel):
-        rc = load().or_render_backward_m(
-            _p(verts), _p(tris), ctypes.c_int32(len(tris)), _p(uv), _p(albedo), _p(rough),
-            None if m is None else _p(m), None if nm is None else _p(nm),
-            ctypes.c_int32(albedo.shape[0]), ctypes.c_int32(albedo.shape[1]), _p(Ip), ctypes.byref(V),
-            ctypes.byref(P), ctypes.c_int32(spp or sc.spp), ctypes.c_int32(sc.bounces if bounces is None else bounces),
-            ctypes.c_uint64(sc.seed if seed is None else seed), None if full else _p(px), ctypes.c_int64(n), _p(dIc),
-            _p(dIp), _p(dA), _p(dR), None if dM is None else _p(dM), None if dN is None else _p(dN), _p(dP),
-            ctypes.c_int32(nthreads))
+    load().or_set_unit_taps(ctypes.c_int(1 if unit_taps else 0))
+    try:
+        with _Accel(accel):
+            rc = load().or_render_backward_m(
+                _p(verts), _p(tris), ctypes.c_int32(len(tris)), _p(uv), _p(albedo), _p(rough),
+                None if m is None else _p(m), None if nm is None else _p(nm),
+                ctypes.c_int32(albedo.shape[0]), ctypes.c_int32(albedo.shape[1]), _p(Ip), ctypes.byref(V),
+                ctypes.byref(P), ctypes.c_int32(spp or sc.spp), ctypes.c_int32(sc.bounces if bounces is None else bounces),
+                ctypes.c_uint64(sc.seed if seed is None else seed), None if full else _p(px), ctypes.c_int64(n), _p(dIc),
+                _p(dIp), _p(dA), _p(dR), None if dM is None else _p(dM), None if dN is None else _p(dN), _p(dP),
+                ctypes.c_int32(nthreads))
+    finally:
+        load().or_set_unit_taps(ctypes.c_int(0))
     if rc != 0:
         raise ValueError("oracle render_backward: invalid arguments")
     out = {"dIp": dIp, "dalbedo": dA, "drough": dR, "dparams": dP}

@@ -27,6 +27,7 @@ using namespace dpcs;
 namespace {
 
 constexpr int kMinSamplesPerLane = DPCS_MIN_SAMPLES_PER_LANE;
+constexpr int kCounters = 10;  // totals dpcs_counters_read returns
 
 struct Buf {
     void *p = nullptr;
@@ -54,6 +55,9 @@ struct dpcs_ctx {
     Buf mat4, dmat4;  // principled material: (metallic, normal map) per texel and its gradient accumulators
     Buf dEp64, dtex64;  // FP64 gradient accumulators (dpcs_set_grad_accum(ctx, DPCS_ACCUM_F64))
     bool grad_f64 = false;
+    Buf wf;  // wavefront render: lane sums, per-chunk path state, queues
+    int32_t render_path = DPCS_PATH_MEGAKERNEL;
+    int64_t wf_chunk = int64_t(1) << 20;
     Buf kept;  // path records of the last dpcs_render_keep: 16-byte chunks (structure of arrays), then per-sample vertex counts
     struct {
         bool valid = false;
@@ -62,7 +66,7 @@ struct dpcs_ctx {
         bool principled = false;  // records of dpcs_render_keep_principled
     } kept_key;
     // measurement support
-    unsigned long long *counters = nullptr;  // 8 totals (DPCS_COUNTERS build)
+    unsigned long long *counters = nullptr;  // kCounters totals (DPCS_COUNTERS build)
     bool timing = false;
     int32_t visit_cap = 0;  // debug override of the traversal visit cap
     std::vector<TimedLaunch> timed;
@@ -314,8 +318,9 @@ dpcs_status dpcs_create(int device, size_t hbm_budget_bytes, dpcs_ctx **out) {
     dpcs_status s = set_device(c);
     if (s == DPCS_OK) s = dev_alloc(c, (void **)&c->status, sizeof(unsigned), "status word");
     if (s == DPCS_OK && cudaMemset(c->status, 0, sizeof(unsigned)) != cudaSuccess) s = DPCS_ERR_CUDA;
-    if (s == DPCS_OK) s = dev_alloc(c, (void **)&c->counters, 8 * sizeof(unsigned long long), "counters");
-    if (s == DPCS_OK && cudaMemset(c->counters, 0, 8 * sizeof(unsigned long long)) != cudaSuccess) s = DPCS_ERR_CUDA;
+    if (s == DPCS_OK) s = dev_alloc(c, (void **)&c->counters, kCounters * sizeof(unsigned long long), "counters");
+    if (s == DPCS_OK && cudaMemset(c->counters, 0, kCounters * sizeof(unsigned long long)) != cudaSuccess)
+        s = DPCS_ERR_CUDA;
     if (s != DPCS_OK) {
         delete c;
         return s;
@@ -340,7 +345,7 @@ dpcs_status dpcs_destroy(dpcs_ctx *c) {
         cudaFree(s.base);
     }
     Buf *bufs[] = {&c->ep4, &c->tex4, &c->gE, &c->dEp4, &c->dtex4, &c->acc, &c->partial, &c->build, &c->upload, &c->pix,
-                   &c->kept, &c->mat4, &c->dmat4, &c->dEp64, &c->dtex64};
+                   &c->kept, &c->mat4, &c->dmat4, &c->dEp64, &c->dtex64, &c->wf};
     for (Buf *b : bufs)
         if (b->p) cudaFree(b->p);
     cudaFree(c->status);
@@ -385,6 +390,17 @@ dpcs_status dpcs_timing_read(dpcs_ctx *c, int32_t kernel, double *total_ms, int6
     return DPCS_OK;
 }
 
+dpcs_status dpcs_set_render_path(dpcs_ctx *c, int32_t path, int64_t chunk) {
+    if (!c) return DPCS_ERR_INVALID_ARG;
+    if (path != DPCS_PATH_MEGAKERNEL && path != DPCS_PATH_WAVEFRONT)
+        return fail(c, DPCS_ERR_INVALID_ARG, "render path must be DPCS_PATH_MEGAKERNEL or DPCS_PATH_WAVEFRONT");
+    if (chunk != 0 && (chunk < 4096 || chunk > (int64_t(1) << 28) || chunk % 32 != 0))
+        return fail(c, DPCS_ERR_INVALID_ARG, "wavefront chunk must be 0 or a multiple of 32 in [4096, 2^28]");
+    c->render_path = path;
+    if (chunk) c->wf_chunk = chunk;
+    return DPCS_OK;
+}
+
 dpcs_status dpcs_set_grad_accum(dpcs_ctx *c, int32_t mode) {
     if (!c) return DPCS_ERR_INVALID_ARG;
     if (mode != DPCS_ACCUM_F32 && mode != DPCS_ACCUM_F64)
@@ -408,8 +424,8 @@ dpcs_status dpcs_counters_read(dpcs_ctx *c, uint64_t *out, int32_t reset) {
     dpcs_status s = set_device(c);
     if (s) return s;
     cudaError_t e = cudaDeviceSynchronize();
-    if (e == cudaSuccess) e = cudaMemcpy(out, c->counters, 8 * sizeof(uint64_t), cudaMemcpyDeviceToHost);
-    if (e == cudaSuccess && reset) e = cudaMemset(c->counters, 0, 8 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemcpy(out, c->counters, kCounters * sizeof(uint64_t), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && reset) e = cudaMemset(c->counters, 0, kCounters * sizeof(unsigned long long));
     return e == cudaSuccess ? DPCS_OK : cuda_fail(c, e, "counters_read");
 #endif
 }
@@ -635,6 +651,9 @@ dpcs_status dpcs_render(dpcs_ctx *c, dpcs_scene scene, const float *albedo, cons
     const int64_t np = (int64_t)view->Hp * view->Wp, nt = (int64_t)Ht * Wt;
     if ((s = ensure(c, c->ep4, (size_t)np * 16, "Ep scratch")) || (s = ensure(c, c->tex4, (size_t)nt * 16, "texture scratch")))
         return s;
+    const bool wf = c->render_path == DPCS_PATH_WAVEFRONT;
+    const size_t wf_bytes = wf ? wavefront_scratch_bytes(a, c->wf_chunk) : 0;
+    if (wf && (s = ensure(c, c->wf, wf_bytes, "wavefront scratch"))) return s;
     cudaStream_t st = (cudaStream_t)stream;
     a.Ep = (const float4 *)c->ep4.p;
     a.tex = (const float4 *)c->tex4.p;
@@ -643,7 +662,7 @@ dpcs_status dpcs_render(dpcs_ctx *c, dpcs_scene scene, const float *albedo, cons
     int nl = launch_prf(Ip, np, params->gamma_p, params->gain_p, (float4 *)c->ep4.p, st);
     nl += launch_pack_tex(albedo, rough, nt, (float4 *)c->tex4.p, st);
     TimedLaunch *tl = timing_begin(c, 0, st);
-    nl += launch_render(a, st);
+    nl += wf ? launch_render_wavefront(a, c->wf_chunk, c->wf.p, st) : launch_render(a, st);
     timing_end(tl, st);
     return check_launch(c, nl, "render");
 }

@@ -17,9 +17,12 @@ constexpr float kRayEps = 1e-4f;   // origin offset along the shading normal
 constexpr int kStack = 64;         // traversal stack depth
 
 // Work counters of the DPCS_COUNTERS build (node visits, triangle tests,
-// closest rays, shadow rays, vertices, lit NEE, continuations, paths); in
-// the normal build every increment compiles away.
-enum { kCntNode = 0, kCntTri, kCntRay, kCntShadow, kCntVert, kCntLit, kCntCont, kCntPath, kCntN };
+// closest rays, shadow rays, vertices, lit NEE, continuations, paths, and
+// two SIMT-efficiency counts: warp iterations of the traversal loop and of
+// the one-ray-per-iteration path loop, each counted once per warp); in the
+// normal build every increment compiles away.
+enum { kCntNode = 0, kCntTri, kCntRay, kCntShadow, kCntVert, kCntLit, kCntCont, kCntPath, kCntTravWarpIter,
+       kCntPathWarpIter, kCntN };
 struct Cnt {
 #ifdef DPCS_COUNTERS
     uint32_t v[kCntN];
@@ -27,6 +30,10 @@ struct Cnt {
         for (int i = 0; i < kCntN; ++i) v[i] = 0u;
     }
     __device__ __forceinline__ void add(int i, uint32_t k = 1u) { v[i] += k; }
+    // once per warp: the lowest active lane counts
+    __device__ __forceinline__ void add_warp(int i) {
+        if ((int)(threadIdx.x & 31) == __ffs(__activemask()) - 1) v[i] += 1u;
+    }
     __device__ __forceinline__ void flush(unsigned long long *out) {
         if (!out) return;
         for (int i = 0; i < kCntN; ++i) {
@@ -37,6 +44,7 @@ struct Cnt {
     }
 #else
     __device__ __forceinline__ void add(int, uint32_t = 1u) {}
+    __device__ __forceinline__ void add_warp(int) {}
     __device__ __forceinline__ void flush(unsigned long long *) {}
 #endif
 };
@@ -260,7 +268,7 @@ __device__ __forceinline__ float4 bilin_fetch(const float4 *__restrict__ img, co
 // BVH traversal.  Node = 4 float4: (l.lo.x, l.hi.x, l.lo.y, l.hi.y),
 // (r.lo.x, r.hi.x, r.lo.y, r.hi.y), (l.lo.z, l.hi.z, r.lo.z, r.hi.z),
 // (left ref, right ref, -, -) with refs >= 0 internal, < 0 leaf ~position.
-// Triangle = 3 float4: (v0, original index), e1, e2.
+// Triangle = 3 float4: (v0, original index), v1, v2.
 // ---------------------------------------------------------------------------
 #ifndef DPCS_SLAB_FMA
 #define DPCS_SLAB_FMA 1  // slab distances as fma(lo, 1/d, -o/d) with a per-ray absolute error margin
@@ -336,21 +344,111 @@ __device__ __forceinline__ bool slab(const Ray &r, float lx, float hx, float ly,
 #endif
 }
 
+#ifndef DPCS_WATERTIGHT
+// 1: Moller-Trumbore, with the watertight test deciding every ray that MT
+//    finds within rounding of an edge of the triangle (crack-free);
+// 2: the watertight test for every triangle; 0: Moller-Trumbore alone
+#define DPCS_WATERTIGHT 1
+#endif
+
+// component k of v, by selects (no local-memory array)
+__device__ __forceinline__ float comp(f3 v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
+
+// Watertight ray-triangle test (Woop, Benthin, Wald, JCGT 2013), two-sided,
+// t in (0, tmax].  The ray is sheared so that it runs along +z through the
+// origin; the three 2-D edge functions of the sheared vertices then decide
+// containment.  A vertex shared by two triangles is sheared identically in
+// both, and each edge function is a difference of two separately rounded
+// products (no FMA contraction), so the function of a shared edge in one
+// triangle is the exact negative of its function in the other: a ray
+// through an edge hits at least one of the two triangles, never neither.
+// When an edge function is exactly 0 it is recomputed in FP64, as the paper
+// prescribes.  u, v are the barycentric weights of v1 and v2.
+__device__ __forceinline__ bool tri_isect_wt(const Ray &r, f3 v0, f3 v1, f3 v2, float tmax, float &t, float &u,
+                                             float &v) {
+    const float ax = fabsf(r.d.x), ay = fabsf(r.d.y), az = fabsf(r.d.z);
+    const int kz = ax > ay ? (ax > az ? 0 : 2) : (ay > az ? 1 : 2);
+    int kx = kz == 2 ? 0 : kz + 1, ky = kx == 2 ? 0 : kx + 1;
+    if (comp(r.d, kz) < 0.0f) {
+        const int tmp = kx;
+        kx = ky;
+        ky = tmp;
+    }
+    const float sz = 1.0f / comp(r.d, kz);
+    const float sx = comp(r.d, kx) * sz, sy = comp(r.d, ky) * sz;
+    const f3 A = v0 - r.o, B = v1 - r.o, C = v2 - r.o;
+    const float Az = comp(A, kz), Bz = comp(B, kz), Cz = comp(C, kz);
+    const float Ax = __fsub_rn(comp(A, kx), __fmul_rn(sx, Az)), Ay = __fsub_rn(comp(A, ky), __fmul_rn(sy, Az));
+    const float Bx = __fsub_rn(comp(B, kx), __fmul_rn(sx, Bz)), By = __fsub_rn(comp(B, ky), __fmul_rn(sy, Bz));
+    const float Cx = __fsub_rn(comp(C, kx), __fmul_rn(sx, Cz)), Cy = __fsub_rn(comp(C, ky), __fmul_rn(sy, Cz));
+    float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
+    float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
+    float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
+    if (U == 0.0f || V == 0.0f || W == 0.0f) {
+        U = (float)__dsub_rn(__dmul_rn((double)Cx, (double)By), __dmul_rn((double)Cy, (double)Bx));
+        V = (float)__dsub_rn(__dmul_rn((double)Ax, (double)Cy), __dmul_rn((double)Ay, (double)Cx));
+        W = (float)__dsub_rn(__dmul_rn((double)Bx, (double)Ay), __dmul_rn((double)By, (double)Ax));
+    }
+    if ((U < 0.0f || V < 0.0f || W < 0.0f) && (U > 0.0f || V > 0.0f || W > 0.0f)) return false;
+    const float det = U + V + W;
+    if (det == 0.0f) return false;
+    const float T = U * (sz * Az) + V * (sz * Bz) + W * (sz * Cz);
+    const float inv = 1.0f / det;
+    t = T * inv;
+    u = V * inv;
+    v = W * inv;
+    return t > 0.0f && t <= tmax;
+}
+
+// out of line: the rare edge cases stay out of the traversal loop's code
+static __device__ __noinline__ bool tri_isect_wt_call(const Ray &r, f3 v0, f3 v1, f3 v2, float tmax, float &t,
+                                                      float &u, float &v) {
+    return tri_isect_wt(r, v0, v1, v2, tmax, t, u, v);
+}
+
 // Moller-Trumbore, two-sided, t in (0, tmax]
-__device__ __forceinline__ bool tri_isect(const Ray &r, f3 v0, f3 e1, f3 e2, float tmax, float &t, float &u,
-                                          float &v) {
+__device__ __forceinline__ bool tri_isect_mt(const Ray &r, f3 v0, f3 v1, f3 v2, float tmax, float &t, float &u,
+                                             float &v, bool &near_edge) {
+    const f3 e1 = v1 - v0, e2 = v2 - v0;
     const f3 p = cross(r.d, e2);
     const float det = dot(e1, p);
-    if (det == 0.0f) return false;
+    near_edge = false;
+    // a ray within rounding of an edge: its barycentric is within kEdgeTol of
+    // the edge's line.  MT's barycentrics carry an absolute error of a few
+    // ulps times |o - v0| / (edge length): about 2e-5 for the 200k-triangle
+    // heightfield seen from the camera, so 1e-4 leaves a margin of five.
+    // det near 0 is a ray in or near the triangle's plane.
+    constexpr float kEdgeTol = 1e-4f;
+    if (fabsf(det) <= 1e-12f * dot(e1, e1) * sqrtf(dot(e2, e2))) {
+        near_edge = true;
+        return false;
+    }
     const float inv = 1.0f / det;
     const f3 s = r.o - v0;
     u = dot(s, p) * inv;
-    if (u < 0.0f || u > 1.0f) return false;
     const f3 q = cross(s, e1);
     v = dot(r.d, q) * inv;
-    if (v < 0.0f || u + v > 1.0f) return false;
+    const float w = 1.0f - u - v;
+    if (u < 0.0f || v < 0.0f || w < 0.0f) {
+        near_edge = u > -kEdgeTol && v > -kEdgeTol && w > -kEdgeTol;
+        return false;
+    }
     t = dot(e2, q) * inv;
     return t > 0.0f && t <= tmax;
+}
+
+__device__ __forceinline__ bool tri_isect(const Ray &r, f3 v0, f3 v1, f3 v2, float tmax, float &t, float &u,
+                                          float &v) {
+#if DPCS_WATERTIGHT == 2
+    return tri_isect_wt(r, v0, v1, v2, tmax, t, u, v);
+#elif DPCS_WATERTIGHT == 1
+    bool near_edge;
+    if (tri_isect_mt(r, v0, v1, v2, tmax, t, u, v, near_edge)) return true;
+    return near_edge && tri_isect_wt_call(r, v0, v1, v2, tmax, t, u, v);
+#else
+    bool near_edge;
+    return tri_isect_mt(r, v0, v1, v2, tmax, t, u, v, near_edge);
+#endif
 }
 
 struct Hit {
@@ -362,7 +460,7 @@ struct Hit {
 // BVH traversal.  Node = 4 float4: (l.lo.x, l.hi.x, l.lo.y, l.hi.y),
 // (r.lo.x, r.hi.x, r.lo.y, r.hi.y), (l.lo.z, l.hi.z, r.lo.z, r.hi.z),
 // (left ref, right ref, -, -) with refs >= 0 internal, < 0 leaf ~position.
-// Triangle = 3 float4: (v0, original index), e1, e2.  Both children's boxes
+// Triangle = 3 float4: (v0, original index), v1, v2.  Both children's boxes
 // are tested; the nearer hit child is visited next and the other pushed.
 // any = true stops at the first hit with t < tmax (shadow rays); otherwise
 // the closest hit is kept, ties in t to the lowest original triangle index.
@@ -401,6 +499,7 @@ __device__ __forceinline__ bool trav_resume(const float4 *__restrict__ nodes, co
     while (true) {
         if (min_active > 0 && !first && __popc(__activemask()) < min_active) return false;
         first = false;
+        cnt.add_warp(kCntTravWarpIter);
         if (++st.visits > cap) {
             atomicOr(status, kStatusTraversalLimit);
             st.h.pos = -1;
@@ -526,9 +625,9 @@ struct Surf {
 __device__ __forceinline__ Surf surface_at(const RenderArgs &a, const Hit &h, f3 d) {
     Surf S;
     const float4 A = __ldg(a.tris + 3 * h.pos + 0);
-    const float4 E1 = __ldg(a.tris + 3 * h.pos + 1);
-    const float4 E2 = __ldg(a.tris + 3 * h.pos + 2);
-    const f3 e1 = xyz(E1), e2 = xyz(E2);
+    const float4 V1 = __ldg(a.tris + 3 * h.pos + 1);
+    const float4 V2 = __ldg(a.tris + 3 * h.pos + 2);
+    const f3 e1 = xyz(V1) - xyz(A), e2 = xyz(V2) - xyz(A);
     S.x = xyz(A) + e1 * h.u + e2 * h.v;
     S.n = normalize(cross(e1, e2));
     if (dot(S.n, d) > 0.0f) S.n = S.n * -1.0f;

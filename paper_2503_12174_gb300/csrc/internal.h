@@ -17,7 +17,7 @@ enum : unsigned {
 };
 
 // Resident scene: LBVH nodes (64 B: two child boxes and two child references),
-// triangles in leaf order (48 B: v0 with the original index in .w, e1, e2)
+// triangles in leaf order (48 B: v0 with the original index in .w, v1, v2)
 // and their per-corner texture coordinates.
 struct Scene {
     int32_t T = 0;
@@ -82,6 +82,24 @@ struct LossArgs {
 constexpr int kFusedSamples = 4;
 constexpr int kFusedRecs = 12;
 
+// One pass of the wavefront render (wavefront.cu): bounce b of the paths
+// [path0, path0 + nchunk) of wave `wave`.  Path state arrays are indexed by
+// the chunk-local path, the lane sums by the global path.
+struct WfPass {
+    RenderArgs r;
+    int64_t path0;
+    int32_t nchunk, wave, b;
+    const int32_t *qin;   // paths of this bounce (null: every path of the chunk, bounce 1)
+    const int32_t *nin;   // length of qin
+    int32_t *qout;        // paths that continue to bounce b + 1
+    int32_t *nout;        // length of qout (zeroed before the pass)
+    float4 *hit;          // (leaf position as int bits, u, v, -) of the last traced ray
+    float4 *ro, *rd;      // origin and direction of the next extension ray
+    float4 *beta;         // throughput entering the next vertex
+    float4 *sum;          // lane sums (xyz) per global path
+    int32_t *fetch;       // rays taken from the pass's queue (persistent trace)
+};
+
 // One pixel range of one request in a batched render launch.
 struct BatchSeg {
     int64_t vb_begin;   // first virtual block of the segment
@@ -107,6 +125,10 @@ size_t lbvh_refit_scratch_bytes(int32_t T);
 int launch_prf(const float *Ip, int64_t ntex, const float gamma_p[3], float gain_p, float4 *Ep, cudaStream_t st);
 int launch_pack_tex(const float *albedo, const float *rough, int64_t ntex, float4 *tex, cudaStream_t st);
 int launch_render(const RenderArgs &a, cudaStream_t st);
+// the same render as a wavefront of trace and shade passes over path queues
+// in chunks of `chunk` paths; scratch of wavefront_scratch_bytes(a, chunk)
+size_t wavefront_scratch_bytes(const RenderArgs &a, int64_t chunk);
+int launch_render_wavefront(const RenderArgs &a, int64_t chunk, void *scratch, cudaStream_t st);
 int launch_render_batch(const RenderArgs *descs, const BatchSeg *segs, int nseg, int64_t total_vb,
                         unsigned long long *counter, int grid, cudaStream_t st);
 int render_batch_grid(int device);

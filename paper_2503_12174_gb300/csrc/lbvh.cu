@@ -204,9 +204,11 @@ __global__ void k_refit(const float *__restrict__ verts, const int32_t *__restri
     const float x0 = verts[3 * i0], y0 = verts[3 * i0 + 1], z0 = verts[3 * i0 + 2];
     const float x1 = verts[3 * i1], y1 = verts[3 * i1 + 1], z1 = verts[3 * i1 + 2];
     const float x2 = verts[3 * i2], y2 = verts[3 * i2 + 1], z2 = verts[3 * i2 + 2];
+    // the three vertices as uploaded: a vertex shared by two triangles has
+    // the same bits in both, which the watertight hit test relies on
     tout[3 * p + 0] = make_float4(x0, y0, z0, __int_as_float(t));
-    tout[3 * p + 1] = make_float4(x1 - x0, y1 - y0, z1 - z0, 0.0f);
-    tout[3 * p + 2] = make_float4(x2 - x0, y2 - y0, z2 - z0, 0.0f);
+    tout[3 * p + 1] = make_float4(x1, y1, z1, 0.0f);
+    tout[3 * p + 2] = make_float4(x2, y2, z2, 0.0f);
     tuv[3 * p + 0] = make_float2(uv[2 * i0], uv[2 * i0 + 1]);
     tuv[3 * p + 1] = make_float2(uv[2 * i1], uv[2 * i1 + 1]);
     tuv[3 * p + 2] = make_float2(uv[2 * i2], uv[2 * i2 + 1]);

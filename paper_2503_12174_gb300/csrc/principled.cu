@@ -109,9 +109,9 @@ struct PSurf {
 __device__ __forceinline__ PSurf psurface_at(const RenderArgs &a, const float4 *__restrict__ mat, const Hit &h, f3 d) {
     PSurf S;
     const float4 A = __ldg(a.tris + 3 * h.pos + 0);
-    const float4 E1 = __ldg(a.tris + 3 * h.pos + 1);
-    const float4 E2 = __ldg(a.tris + 3 * h.pos + 2);
-    const f3 e1 = xyz(E1), e2 = xyz(E2);
+    const float4 V1 = __ldg(a.tris + 3 * h.pos + 1);
+    const float4 V2 = __ldg(a.tris + 3 * h.pos + 2);
+    const f3 e1 = xyz(V1) - xyz(A), e2 = xyz(V2) - xyz(A);
     S.x = xyz(A) + e1 * h.u + e2 * h.v;
     S.n = normalize(cross(e1, e2));
     if (dot(S.n, d) > 0.0f) S.n = S.n * -1.0f;

@@ -164,6 +164,7 @@ __device__ __forceinline__ void render_lanes(const RenderArgs &a, int64_t pix, i
                 s = a.spp;
                 break;
             }
+            cnt.add_warp(kCntPathWarpIter);
             // yield only while some live lane of the warp could take a new ray
             const int alive = DPCS_YIELD_MIN > 0 ? __popc(__activemask()) : 0;
             if (!pending) {

@@ -8,11 +8,12 @@
 //   2. admit waiting requests in arrival order while their device memory
 //      fits the HBM budget and fewer than max_active are admitted;
 //   3. plan about samples_per_iteration samples of work: every relighting
-//      request first gets quantum_samples; then one compensation step per
-//      request (a full image) within half of the iteration's samples; the
-//      rest goes to relighting requests in arrival order, and what
-//      relighting leaves unused runs further consecutive compensation
-//      steps, still within that half;
+//      request first gets quantum_samples; then (fixed-share policy) one
+//      compensation step per request (a full image) within
+//      compensation_share of the iteration; the rest goes to relighting
+//      requests in arrival order, and what relighting leaves unused runs
+//      further consecutive compensation steps, still within that share; or
+//      (deadline policy) the rest goes to requests in order of deadline;
 //   4. enqueue on the server stream: the batch descriptors, one persistent
 //      k_render_batch launch over the relighting pixels, each compensation
 //      request's step: render, loss and path adjoint in one trace
@@ -305,6 +306,12 @@ dpcs_status queue_result_copy(dpcs_server *s, Req *q) {
     return DPCS_OK;
 }
 
+void plan_fixed_share(dpcs_server *s, const std::vector<Req *> &relight, const std::vector<Req *> &comp,
+                      std::vector<int64_t> &give, int64_t &budget, int64_t total_budget, Batch &b);
+void plan_by_deadline(dpcs_server *s, const std::vector<Req *> &relight, const std::vector<Req *> &comp,
+                      std::vector<int64_t> &give, int64_t &budget, Batch &b);
+dpcs_status enqueue_iteration(dpcs_server *s, Batch &b, int nseg, int64_t vb);
+
 dpcs_status launch_iteration(dpcs_server *s, Batch &b) {
     std::vector<Req *> comp, relight;
     for (Req *q : s->active) {
@@ -339,9 +346,28 @@ dpcs_status launch_iteration(dpcs_server *s, Batch &b) {
         give[i] = std::min(q->npix - q->next_pix, std::max<int64_t>(1, s->cfg.quantum_samples / q->r.spp));
         budget -= give[i] * q->r.spp;
     }
-    // 2) one compensation step per request in arrival order (a full image)
-    //    within half of the iteration's samples;
-    const int64_t comp_cap = total_budget / 2;
+    if (s->cfg.policy == DPCS_SERVE_DEADLINE) {
+        plan_by_deadline(s, relight, comp, give, budget, b);
+    } else {
+        plan_fixed_share(s, relight, comp, give, budget, total_budget, b);
+    }
+    for (size_t i = 0; i < relight.size(); ++i) {
+        if (give[i] <= 0) continue;
+        Req *q = relight[i];
+        add_seg(q, q->next_pix, give[i]);
+        b.pixels.push_back({q, give[i]});
+        q->next_pix += give[i];
+    }
+    return enqueue_iteration(s, b, nseg, vb);
+}
+
+// The fixed-share plan: 2) one compensation step per request in arrival
+// order (a full image) within compensation_share of the iteration; 3) the rest
+// to relighting requests in arrival order; 4) what relighting leaves unused
+// runs further consecutive steps of the same compensation requests.
+void plan_fixed_share(dpcs_server *s, const std::vector<Req *> &relight, const std::vector<Req *> &comp,
+                      std::vector<int64_t> &give, int64_t &budget, int64_t total_budget, Batch &b) {
+    const int64_t comp_cap = (int64_t)(s->cfg.compensation_share * (double)total_budget);
     int64_t comp_used = 0;
     for (Req *q : comp) {
         const int64_t need = q->npix * q->r.spp;
@@ -361,7 +387,7 @@ dpcs_status launch_iteration(dpcs_server *s, Batch &b) {
         }
     }
     // 4) budget that relighting left unused runs further consecutive steps of
-    //    the same compensation requests, in rounds, still within half of the
+    //    the same compensation requests, in rounds, still within that share of the
     //    iteration (rounds keep each request's steps in order on the stream).
     const size_t n_first = b.steps.size();
     std::vector<int> planned(n_first, 1);
@@ -378,13 +404,55 @@ dpcs_status launch_iteration(dpcs_server *s, Batch &b) {
             more = true;
         }
     }
+}
+
+// The deadline plan: every request (after the relighting quanta) has a
+// deadline, its arrival plus its slack times the time its remaining work
+// would take alone at est_samples_per_s; the iteration's remaining budget
+// goes to requests in deadline order -- relighting pixels, or consecutive
+// compensation steps (a step counts its samples x kStepCost).  Small
+// requests therefore pass large ones, and a large request's deadline comes
+// up as it waits.
+void plan_by_deadline(dpcs_server *s, const std::vector<Req *> &relight, const std::vector<Req *> &comp,
+                      std::vector<int64_t> &give, int64_t &budget, Batch &b) {
+    constexpr double kStepCost = 1.4;  // a fused render + adjoint step, in forward samples
+    struct Claim {
+        double deadline;
+        int relight;  // index into relight, or -1
+        Req *q;
+    };
+    std::vector<Claim> claims;
+    const double R = s->cfg.est_samples_per_s;
     for (size_t i = 0; i < relight.size(); ++i) {
-        if (give[i] <= 0) continue;
         Req *q = relight[i];
-        add_seg(q, q->next_pix, give[i]);
-        b.pixels.push_back({q, give[i]});
-        q->next_pix += give[i];
+        const double work = (double)q->npix * q->r.spp;
+        claims.push_back({q->t_submit + s->cfg.relight_slack * work / R, (int)i, q});
     }
+    for (Req *q : comp) {
+        const double work = kStepCost * (double)q->r.steps * q->npix * q->r.spp;
+        claims.push_back({q->t_submit + s->cfg.compensation_slack * work / R, -1, q});
+    }
+    std::stable_sort(claims.begin(), claims.end(), [](const Claim &x, const Claim &y) { return x.deadline < y.deadline; });
+    for (const Claim &c : claims) {
+        if (budget <= 0) break;
+        Req *q = c.q;
+        if (c.relight >= 0) {
+            const int64_t extra = std::min(q->npix - q->next_pix - give[c.relight], budget / q->r.spp);
+            if (extra > 0) {
+                give[c.relight] += extra;
+                budget -= extra * q->r.spp;
+            }
+        } else {
+            const int64_t need = (int64_t)(kStepCost * (double)q->npix * q->r.spp);
+            for (int k = q->steps_issued; k < q->r.steps && (need <= budget || b.steps.empty()); ++k) {
+                b.steps.push_back(q);
+                budget -= need;
+            }
+        }
+    }
+}
+
+dpcs_status enqueue_iteration(dpcs_server *s, Batch &b, int nseg, int64_t vb) {
     cudaStream_t st = s->stream;
     cudaError_t e = cudaSuccess;
     int n = 0;
@@ -448,7 +516,11 @@ dpcs_status dpcs_serve_create(dpcs_ctx *ctx, const dpcs_serve_config *cfg, dpcs_
     if (!ctx || !cfg || !out) return DPCS_ERR_INVALID_ARG;
     *out = nullptr;
     if (cfg->max_active < 1 || cfg->max_active > 1024 || cfg->max_inflight < 1 || cfg->max_inflight > 4 ||
-        cfg->samples_per_iteration < 1 || cfg->quantum_samples < 1)
+        cfg->samples_per_iteration < 1 || cfg->quantum_samples < 1 ||
+        (cfg->policy != DPCS_SERVE_DEADLINE && cfg->policy != DPCS_SERVE_FIXED_SHARE) ||
+        (cfg->policy == DPCS_SERVE_DEADLINE &&
+         !(cfg->relight_slack > 0.0 && cfg->compensation_slack > 0.0 && cfg->est_samples_per_s > 0.0)) ||
+        (cfg->policy == DPCS_SERVE_FIXED_SHARE && !(cfg->compensation_share > 0.0 && cfg->compensation_share <= 1.0)))
         return ctx_fail(ctx, DPCS_ERR_INVALID_ARG, "serve: bad config");
     dpcs_server *s = new dpcs_server();
     s->ctx = ctx;

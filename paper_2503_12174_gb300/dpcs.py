@@ -28,6 +28,8 @@ DPCS_ERR_NOT_FOUND = -8
 DPCS_MAX_BOUNCES = 8
 DPCS_ACCUM_F32 = 0
 DPCS_ACCUM_F64 = 1
+DPCS_PATH_MEGAKERNEL = 0
+DPCS_PATH_WAVEFRONT = 1
 
 EXPORTED = [
     "dpcs_create", "dpcs_destroy", "dpcs_last_error", "dpcs_sync", "dpcs_memory_used", "dpcs_launch_count",
@@ -39,7 +41,7 @@ EXPORTED = [
     "dpcs_l1_loss", "dpcs_tv_loss", "dpcs_scene_update", "dpcs_render_loss_backward", "dpcs_render_keep",
     "dpcs_render_backward_kept", "dpcs_render_principled", "dpcs_render_backward_principled",
     "dpcs_scene_transform", "dpcs_render_loss_backward_principled", "dpcs_render_keep_principled",
-    "dpcs_render_backward_kept_principled", "dpcs_set_grad_accum",
+    "dpcs_render_backward_kept_principled", "dpcs_set_grad_accum", "dpcs_set_render_path",
 ]
 
 DPCS_REQ_RELIGHT = 0
@@ -79,7 +81,14 @@ class DpcsView(ctypes.Structure):
 
 class DpcsServeConfig(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_size_t), ("max_active", ctypes.c_int32), ("max_inflight", ctypes.c_int32),
-                ("samples_per_iteration", ctypes.c_int64), ("quantum_samples", ctypes.c_int64)]
+                ("samples_per_iteration", ctypes.c_int64), ("quantum_samples", ctypes.c_int64),
+                ("policy", ctypes.c_int32), ("pad", ctypes.c_int32), ("relight_slack", ctypes.c_double),
+                ("compensation_slack", ctypes.c_double), ("est_samples_per_s", ctypes.c_double),
+                ("compensation_share", ctypes.c_double)]
+
+
+DPCS_SERVE_DEADLINE = 0
+DPCS_SERVE_FIXED_SHARE = 1
 
 
 class DpcsRequest(ctypes.Structure):
@@ -169,6 +178,7 @@ _SIGS = {
     "dpcs_counters_read": (ctypes.c_int32, [_P, _P, ctypes.c_int32]),
     "dpcs_debug_set_visit_cap": (ctypes.c_int32, [_P, ctypes.c_int32]),
     "dpcs_set_grad_accum": (ctypes.c_int32, [_P, ctypes.c_int32]),
+    "dpcs_set_render_path": (ctypes.c_int32, [_P, ctypes.c_int32, ctypes.c_int64]),
     "dpcs_gbuffer": (ctypes.c_int32, [_P, ctypes.c_uint64, _P, _P, ctypes.c_int32, ctypes.c_int32,
                                       ctypes.POINTER(DpcsView), _P, _P]),
     "dpcs_denoise": (ctypes.c_int32, [_P, _P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(DpcsDenoiseParams),
@@ -359,6 +369,10 @@ def dpcs_set_grad_accum(ctx, mode):
     return load_library().dpcs_set_grad_accum(ctx, int(mode))
 
 
+def dpcs_set_render_path(ctx, path, chunk):
+    return load_library().dpcs_set_render_path(ctx, int(path), int(chunk))
+
+
 def dpcs_timing_enable(ctx, on):
     return load_library().dpcs_timing_enable(ctx, int(on))
 
@@ -467,11 +481,18 @@ class Context:
         FP64 rounding)."""
         self.check(self.lib.dpcs_set_grad_accum(self.handle, int(mode)), "set_grad_accum")
 
+    def set_render_path(self, path: int, chunk: int = 0):
+        """dpcs_render's kernels: DPCS_PATH_MEGAKERNEL (one kernel) or
+        DPCS_PATH_WAVEFRONT (trace and shade passes over path queues, in chunks
+        of ``chunk`` paths; 0 keeps the current size)."""
+        self.check(self.lib.dpcs_set_render_path(self.handle, int(path), int(chunk)), "set_render_path")
+
     def counters(self, reset: bool = True):
         """Work counters (counters build only): dict of totals."""
-        out = (ctypes.c_uint64 * 8)()
+        out = (ctypes.c_uint64 * 10)()
         self.check(self.lib.dpcs_counters_read(self.handle, out, 1 if reset else 0), "counters_read")
-        keys = ("node_visits", "tri_tests", "rays", "shadow_rays", "vertices", "lit", "continuations", "paths")
+        keys = ("node_visits", "tri_tests", "rays", "shadow_rays", "vertices", "lit", "continuations", "paths",
+                "trav_warp_iters", "path_warp_iters")
         return dict(zip(keys, [int(x) for x in out]))
 
     def probe_l2_load(self, nbytes: int = 32 << 20, passes: int = 64) -> float:
@@ -829,11 +850,14 @@ class Server:
     handed to submit() are kept alive here until the request is done."""
 
     def __init__(self, ctx: Context, hbm_budget_bytes: int = 0, max_active: int = 64, max_inflight: int = 2,
-                 samples_per_iteration: int = 48 << 20, quantum_samples: int = 2 << 20):
+                 samples_per_iteration: int = 48 << 20, quantum_samples: int = 2 << 20,
+                 policy: int = DPCS_SERVE_FIXED_SHARE, relight_slack: float = 4.0, compensation_slack: float = 1.0,
+                 est_samples_per_s: float = 2e9, compensation_share: float = 0.5):
         self.ctx = ctx
         self.lib = ctx.lib
         cfg = DpcsServeConfig(int(hbm_budget_bytes), int(max_active), int(max_inflight), int(samples_per_iteration),
-                              int(quantum_samples))
+                              int(quantum_samples), int(policy), 0, float(relight_slack), float(compensation_slack),
+                              float(est_samples_per_s), float(compensation_share))
         h = _P()
         ctx.check(self.lib.dpcs_serve_create(ctx.handle, ctypes.byref(cfg), ctypes.byref(h)), "serve_create")
         self.handle = h

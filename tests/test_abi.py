@@ -45,11 +45,12 @@ def test_struct_layout_matches_header():
 #include <stddef.h>
 #include "dpcs.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(dpcs_params), offsetof(dpcs_params, rr_start),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(dpcs_params), offsetof(dpcs_params, rr_start),
          offsetof(dpcs_params, jitter), sizeof(dpcs_view), offsetof(dpcs_view, Kp), offsetof(dpcs_view, Hp),
          sizeof(dpcs_request), offsetof(dpcs_request, seed), offsetof(dpcs_request, Ip_out),
          sizeof(dpcs_serve_config), offsetof(dpcs_serve_config, quantum_samples), sizeof(dpcs_serve_stats),
-         sizeof(dpcs_denoise_params), offsetof(dpcs_denoise_params, sigma_depth));
+         sizeof(dpcs_denoise_params), offsetof(dpcs_denoise_params, sigma_depth),
+         offsetof(dpcs_serve_config, est_samples_per_s), offsetof(dpcs_serve_config, compensation_share));
   return 0;
 }
 """
@@ -63,4 +64,5 @@ int main(void) {
     assert out == [ctypes.sizeof(P), P.rr_start.offset, P.jitter.offset, ctypes.sizeof(V), V.Kp.offset, V.Hp.offset,
                    ctypes.sizeof(R), R.seed.offset, R.Ip_out.offset, ctypes.sizeof(C), C.quantum_samples.offset,
                    ctypes.sizeof(dpcs.DpcsServeStats), ctypes.sizeof(dpcs.DpcsDenoiseParams),
-                   dpcs.DpcsDenoiseParams.sigma_depth.offset]
+                   dpcs.DpcsDenoiseParams.sigma_depth.offset, C.est_samples_per_s.offset,
+                   C.compensation_share.offset]

@@ -32,10 +32,12 @@ def test_gbuffer_matches_oracle(orc):
     ref = orc.gbuffer(sc)
     same_hit = got[..., 7] == ref[..., 7]
     # The corner's seams project onto the image diagonals, through pixel
-    # centres: those rays run exactly along an edge shared by two triangles,
-    # and the FP32 hit test can miss both (a crack) where FP64 hits one.
-    assert same_hit.mean() >= 0.99
-    assert np.all(ref[~same_hit][:, 7] == 1.0)  # only misses of the FP32 side
+    # centres: those rays run exactly along an edge shared by two triangles.
+    # A plain FP32 hit test can miss both triangles there (a crack); the
+    # library's test is watertight near edges, so the GPU misses no pixel
+    # that the FP64 oracle hits.
+    assert not np.any((ref[..., 7] == 1.0) & (got[..., 7] == 0.0))
+    assert same_hit.all()
     both = same_hit & (ref[..., 7] == 1.0)
     # a different triangle at a shared edge (FP32 vs FP64 hit tests) changes the normal
     agree = both & (np.abs(got[..., 3:6] - ref[..., 3:6]).max(axis=-1) < 1e-4)

@@ -29,15 +29,7 @@ def _small_workload(n=14, steps=4):
                                  sides=(64, 96, 128), spp_range=(4, 40), pool=3)
 
 
-def test_results_same_alone_and_in_mix(env):
-    torch = need_cuda()
-    c, gs, host = env
-    wl = _small_workload()
-    assert any(r.kind == dpcs.DPCS_REQ_COMPENSATE for r in wl) and any(r.kind == dpcs.DPCS_REQ_RELIGHT for r in wl)
-    summary, outs = serving.run_server(c, gs, host, wl, keep_outputs=True, max_active=8, samples_per_iteration=1 << 18,
-                                       quantum_samples=1 << 16)
-    assert summary["requests"] == len(wl)
-    assert summary["server"]["iterations"] > 2  # requests really were interleaved over several iterations
+def _check_against_alone(c, gs, host, wl, outs):
     for k, rq in enumerate(wl):
         sc = gs.scs[rq.scene]
         Ic_mix, Ip_mix = outs[k]
@@ -54,6 +46,65 @@ def test_results_same_alone_and_in_mix(env):
             # gradients are summed with float atomics, so the Adam iterates agree to rounding only
             np.testing.assert_allclose(Ip_mix, P.cpu().numpy(), rtol=0, atol=2e-3, err_msg=f"compensation {k}")
             np.testing.assert_allclose(Ic_mix, Ic.cpu().numpy(), rtol=2e-3, atol=2e-4, err_msg=f"compensation {k}")
+
+
+@pytest.mark.parametrize("policy", [dpcs.DPCS_SERVE_DEADLINE, dpcs.DPCS_SERVE_FIXED_SHARE])
+def test_results_same_alone_and_in_mix(env, policy):
+    need_cuda()
+    c, gs, host = env
+    wl = _small_workload()
+    assert any(r.kind == dpcs.DPCS_REQ_COMPENSATE for r in wl) and any(r.kind == dpcs.DPCS_REQ_RELIGHT for r in wl)
+    summary, outs = serving.run_server(c, gs, host, wl, keep_outputs=True, max_active=8, samples_per_iteration=1 << 18,
+                                       quantum_samples=1 << 16, policy=policy)
+    assert summary["requests"] == len(wl)
+    assert summary["server"]["iterations"] > 2  # requests really were interleaved over several iterations
+    _check_against_alone(c, gs, host, wl, outs)
+
+
+def test_requests_admitted_while_others_run(env):
+    """Continuous batching: a second wave of requests is submitted while the
+    first wave's iterations are still on the GPU; the server admits them as
+    slots free up, their work shares iterations with the first wave's, and
+    every result equals the request run alone."""
+    torch = need_cuda()
+    c, gs, host = env
+    wl = serving.make_workload(10, rate=0.0, seed=21, comp_frac=0.3, comp_steps=4, comp_spp=4, sides=(96, 128, 160),
+                               spp_range=(8, 64), pool=3)
+    assert any(r.kind == dpcs.DPCS_REQ_COMPENSATE for r in wl[5:])
+    srv = dpcs.Server(c, max_active=4, max_inflight=2, samples_per_iteration=1 << 18, quantum_samples=1 << 16)
+    slots = [srv.add_scene(gs.handles[i], gs.alb[i], gs.rough[i], dpcs.view_of(sc), gs.params[i], sc.bounces)
+             for i, sc in enumerate(gs.scs)]
+    outs = serving._result_buffers(gs, host, wl)
+    ids = {}
+
+    def submit(k):
+        rq = wl[k]
+        Ic, Ipo = outs[k]
+        tgt = host.target(rq.scene, rq.side) if rq.kind == dpcs.DPCS_REQ_COMPENSATE else None
+        ids[k] = srv.submit(rq.kind, slots[rq.scene], rq.side, rq.side, rq.spp, rq.seed, host.ips[rq.scene][rq.ip_idx],
+                            Ic, target=tgt, Ip_out=Ipo, steps=rq.steps, lr=1e-2)
+
+    try:
+        for k in range(5):
+            submit(k)
+        srv.step()
+        srv.step()
+        st = srv.stats()
+        assert st["active"] > 0 and st["completed"] < 5  # the first wave is still on the GPU
+        for k in range(5, 10):  # the second wave arrives while the first runs
+            submit(k)
+        assert srv.stats()["waiting"] > 0  # more requests than slots: some wait for admission
+        srv.drain(60.0)
+        st = srv.stats()
+        assert st["completed"] == 10 and st["failed"] == 0 and st["memory_used"] == 0
+        for k in range(10):
+            state, _ = srv.query(ids[k])
+            assert state == dpcs.DPCS_REQ_DONE
+        got = {k: (outs[k][0].numpy().copy(), None if outs[k][1] is None else outs[k][1].numpy().copy())
+               for k in range(10)}
+    finally:
+        srv.close()
+    _check_against_alone(c, gs, host, wl, got)
 
 
 def test_admission_respects_hbm_budget(env):

@@ -127,3 +127,30 @@ def test_adjoint_roughness_unbiased_multi_bounce(orc):
         se = np.sqrt(adj.var() / n + fd.var() / n)
         assert abs(adj.mean()) > 10 * se  # the gradient is resolved, not noise
         assert abs(adj.mean() - fd.mean()) < 4 * se, (B, adj.mean(), fd.mean(), se)
+
+
+def test_unit_tap_diagnostic_counts_each_contribution_once_per_tap(orc):
+    """The unit-tap diagnostic (used to bound how far FP32 rounding of a hit
+    point's texel position can move a texel's gradient): with dLoss/dIc >= 0
+    every projector and albedo contribution is nonnegative; each reaches its
+    four bilinear taps with weight 1 instead of weights that sum to 1, so the
+    totals are exactly four times the adjoint's, and no texel gets less than
+    its share under the real weights."""
+    import numpy as np
+
+    from paper_2503_12174_gb300 import scenes
+
+    sc = scenes.corner(res=20, tex=16, spp=3, bounces=3, seed=5)
+    p = sc.params
+    sc = sc.replace(params=scenes.Params(gamma_p=(1.0, 1.0, 1.0), gain_p=1.0, gamma_c=p.gamma_c, gain_c=p.gain_c,
+                                         wb=p.wb, k_proj=p.k_proj, ks=p.ks, f0=p.f0))
+    W = np.random.default_rng(8).uniform(0.1, 1.0, size=(sc.Hc, sc.Wc, 3))
+    g = orc.render_backward(sc, W)
+    u = orc.render_backward(sc, W, unit_taps=True)
+    for k in ("dIp", "dalbedo"):
+        assert g[k].min() >= 0.0 and g[k].sum() > 0
+        np.testing.assert_allclose(u[k].sum(), 4.0 * g[k].sum(), rtol=1e-12)
+        assert np.all(u[k] >= g[k] * (1 - 1e-12))
+    # the diagnostic is off again for the next call
+    g2 = orc.render_backward(sc, W)
+    np.testing.assert_allclose(g2["dIp"], g["dIp"], rtol=1e-12)
