@@ -345,6 +345,7 @@ def main():
     if rank == 0:  # one rank compiles; the others load what it built
         _build.build()
         _build.build(variant="_counters", defines=("DPCS_COUNTERS",))
+        _build.build_probe()
     if dist:
         dist.barrier()
     from paper_2503_12174_gb300 import dpcs, scenes
@@ -557,8 +558,10 @@ def main():
         replay_counts = None
         grad_counts = None
     # measured roofs the driver's peaks file lacks: L2 load bandwidth and scattered float4 atomics
-    l2_gbs = ctx.probe_l2_load(PROBE_L2_BYTES, 256)
-    atomic_g = ctx.probe_atomic4(PROBE_ATOMIC_TEXELS, 1 << 28)
+    from paper_2503_12174_gb300 import probe as _probe
+
+    l2_gbs = _probe.dpcs_probe_l2_load(local, PROBE_L2_BYTES, 256)
+    atomic_g = _probe.dpcs_probe_atomic4(local, PROBE_ATOMIC_TEXELS, 1 << 28)
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
     peaks = {}
@@ -576,7 +579,7 @@ def main():
         l_tbs = lbytes / (kernel_ms / 1e3) / 1e12
         roof_load = {"bound": "l2", "kernel": "k_render", "achieved": l_tbs, "peak": l2_gbs / 1e3, "unit": "TB/s",
                      "frac": l_tbs / (l2_gbs / 1e3), "bytes_per_launch": lbytes,
-                     "peak_basis": f"measured: dpcs_probe_l2_load, {PROBE_L2_BYTES >> 20} MiB read with 16 B "
+                     "peak_basis": f"measured: dpcs_probe_l2_load (measurement library), {PROBE_L2_BYTES >> 20} MiB read with 16 B "
                                    "L2-only loads, best of 3",
                      "l1_nominal_peak": sms * 128 * sm_max_mhz * 1e6 / 1e12}
     if replay_counts and replay_ms:

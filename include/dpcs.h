@@ -142,29 +142,6 @@ dpcs_status dpcs_timing_read(dpcs_ctx *ctx, int32_t kernel, double *total_ms, in
 dpcs_status dpcs_counters_read(dpcs_ctx *ctx, uint64_t *out, int32_t reset);
 
 /*
- * Roof probes: measurement helpers with no counterpart in the paper.  The
- * render and replay kernels load a scene and textures that stay resident in
- * L2, and the replay scatters gradients with float4 atomics; these calls
- * measure both rates on ctx's device so the kernels' rooflines can be stated
- * against them.  Each call allocates its own device buffer (outside the HBM
- * budget) for the call's duration, runs on the legacy default stream, times
- * the best of three launches after one warm-up with CUDA events, and
- * returns after synchronising.
- *
- * dpcs_probe_l2_load: reads a zeroed `bytes` buffer `passes` times with
- * 16-byte loads that cache in L2 only; *gbs = bytes * passes / time in GB/s.
- * bytes must be a positive multiple of 16 up to 64 MiB (so it stays in L2)
- * and passes in [1, 4096], else DPCS_ERR_INVALID_ARG.
- *
- * dpcs_probe_atomic4: about n_atomics float4 atomic adds (rounded up to a
- * whole number per thread) at pseudo-random texels of a `texels`-entry float4
- * buffer, so the lanes of a warp hit unrelated addresses; *gatomics = adds
- * per second / 1e9.  texels in [1, 2^24], n_atomics in [1, 2^34].
- */
-dpcs_status dpcs_probe_l2_load(dpcs_ctx *ctx, size_t bytes, int32_t passes, double *gbs);
-dpcs_status dpcs_probe_atomic4(dpcs_ctx *ctx, int32_t texels, int64_t n_atomics, double *gatomics);
-
-/*
  * Failure-path testing: cap every ray's BVH traversal at `cap` steps in the
  * render and replay calls that follow (0 restores the default, 2T + 16, which
  * a correct tree never reaches).  A ray that reaches the cap ends as a miss
@@ -598,13 +575,14 @@ typedef struct dpcs_serve_config {
     int32_t max_inflight;           /* batched iterations queued on the GPU at once (1..4) */
     int64_t samples_per_iteration;  /* camera samples one batched iteration aims at */
     int64_t quantum_samples;        /* samples every active relighting request gets first */
-    /* How the rest of an iteration is shared (after every relighting request's
-     * quantum).  DPCS_SERVE_DEADLINE: by earliest deadline, a request's
-     * deadline being its arrival plus slack x its work / est_samples_per_s
-     * (a compensation step counts its samples x 1.4 for the adjoint);
-     * DPCS_SERVE_FIXED_SHARE: one compensation step per request within
-     * compensation_share of the iteration, the rest to relighting in arrival
-     * order, and what relighting leaves to further compensation steps. */
+    /* How an iteration is shared.  DPCS_SERVE_FIXED_SHARE: every relighting
+     * request first gets quantum_samples, then one compensation step per
+     * request within compensation_share of the iteration, the rest to
+     * relighting in arrival order, and what relighting leaves to further
+     * compensation steps.  DPCS_SERVE_DEADLINE: by earliest deadline, a
+     * request's deadline being its arrival plus slack x its work /
+     * est_samples_per_s (a compensation step counts its samples x 1.4 for
+     * the adjoint); no quanta. */
     int32_t policy;
     int32_t pad;
     double relight_slack;           /* deadline policy, > 0 */

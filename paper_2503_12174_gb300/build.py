@@ -18,8 +18,9 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "lbvh.cu", "render.cu", "optim.cu", "serve.cu", "probe.cu", "denoise.cu", "principled.cu",
-           "wavefront.cu"]
+SOURCES = ["api.cu", "lbvh.cu", "render.cu", "optim.cu", "serve.cu", "denoise.cu", "principled.cu", "wavefront.cu"]
+# the measurement library (roof probes), used by the benchmark and its tests
+PROBE_SOURCES = ["probe.cu"]
 
 
 def nvcc() -> str:
@@ -33,19 +34,22 @@ def lib_path(variant: str = "") -> str:
     return os.path.join(OUT, f"libdpcs{variant}.so")
 
 
-def _deps():
-    return [os.path.join(CSRC, s) for s in SOURCES] + glob.glob(os.path.join(CSRC, "*.cuh")) + \
+def _deps(sources=SOURCES):
+    return [os.path.join(CSRC, s) for s in sources] + glob.glob(os.path.join(CSRC, "*.cuh")) + \
         glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(INCLUDE, "*.h")) + [os.path.abspath(__file__)]
 
 
-def build(force: bool = False, variant: str = "", defines=(), verbose: bool = False) -> str:
+def build(force: bool = False, variant: str = "", defines=(), verbose: bool = False, sources=None,
+          name: str = "libdpcs") -> str:
     """Compile and link; returns the library path.  ``variant`` names an
-    alternative build (e.g. "_counters" with defines=("DPCS_COUNTERS",))."""
+    alternative build (e.g. "_counters" with defines=("DPCS_COUNTERS",));
+    ``sources`` / ``name`` select another library (the probes)."""
     os.makedirs(OUT, exist_ok=True)
-    lib = lib_path(variant)
+    sources = SOURCES if sources is None else sources
+    lib = os.path.join(OUT, f"{name}{variant}.so")
     if not force and os.path.exists(lib):
         t = os.path.getmtime(lib)
-        if all(os.path.getmtime(d) <= t for d in _deps()):
+        if all(os.path.getmtime(d) <= t for d in _deps(sources)):
             return lib
     cc = nvcc()
     flags = ["-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
@@ -61,8 +65,8 @@ def build(force: bool = False, variant: str = "", defines=(), verbose: bool = Fa
             raise RuntimeError(f"nvcc failed for {src}:\n{p.stderr}")
         return obj, p.stderr
 
-    with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-        results = list(ex.map(compile_one, SOURCES))
+    with cf.ThreadPoolExecutor(max_workers=len(sources)) as ex:
+        results = list(ex.map(compile_one, sources))
     if verbose:
         for _, err in results:
             print(err)
@@ -73,6 +77,11 @@ def build(force: bool = False, variant: str = "", defines=(), verbose: bool = Fa
         raise RuntimeError(f"link failed:\n{p.stderr}")
     os.replace(tmp, lib)
     return lib
+
+
+def build_probe(force: bool = False) -> str:
+    """The measurement library libdpcs_probe.so (roof probes)."""
+    return build(force=force, sources=PROBE_SOURCES, name="libdpcs_probe")
 
 
 if __name__ == "__main__":

@@ -406,19 +406,19 @@ static __device__ __noinline__ bool tri_isect_wt_call(const Ray &r, f3 v0, f3 v1
     return tri_isect_wt(r, v0, v1, v2, tmax, t, u, v);
 }
 
-// Moller-Trumbore, two-sided, t in (0, tmax]
+// Moller-Trumbore, two-sided, t in (0, tmax].  near_edge reports a miss
+// within kEdgeTol (in barycentric units) of the triangle -- or a ray nearly
+// in its plane -- for the watertight test to decide.  MT's barycentrics
+// carry an absolute error of a few ulps times |o - v0| / (edge length):
+// about 2e-5 for the 200k-triangle heightfield seen from the camera, so
+// 1e-4 leaves a margin of five.
 __device__ __forceinline__ bool tri_isect_mt(const Ray &r, f3 v0, f3 v1, f3 v2, float tmax, float &t, float &u,
                                              float &v, bool &near_edge) {
+    constexpr float kEdgeTol = 1e-4f;
     const f3 e1 = v1 - v0, e2 = v2 - v0;
     const f3 p = cross(r.d, e2);
     const float det = dot(e1, p);
     near_edge = false;
-    // a ray within rounding of an edge: its barycentric is within kEdgeTol of
-    // the edge's line.  MT's barycentrics carry an absolute error of a few
-    // ulps times |o - v0| / (edge length): about 2e-5 for the 200k-triangle
-    // heightfield seen from the camera, so 1e-4 leaves a margin of five.
-    // det near 0 is a ray in or near the triangle's plane.
-    constexpr float kEdgeTol = 1e-4f;
     if (fabsf(det) <= 1e-12f * dot(e1, e1) * sqrtf(dot(e2, e2))) {
         near_edge = true;
         return false;
@@ -426,11 +426,12 @@ __device__ __forceinline__ bool tri_isect_mt(const Ray &r, f3 v0, f3 v1, f3 v2, 
     const float inv = 1.0f / det;
     const f3 s = r.o - v0;
     u = dot(s, p) * inv;
+    if (u < -kEdgeTol || u > 1.0f + kEdgeTol) return false;
     const f3 q = cross(s, e1);
     v = dot(r.d, q) * inv;
-    const float w = 1.0f - u - v;
-    if (u < 0.0f || v < 0.0f || w < 0.0f) {
-        near_edge = u > -kEdgeTol && v > -kEdgeTol && w > -kEdgeTol;
+    if (v < -kEdgeTol || u + v > 1.0f + kEdgeTol) return false;
+    if (u < 0.0f || v < 0.0f || u + v > 1.0f) {
+        near_edge = true;
         return false;
     }
     t = dot(e2, q) * inv;

@@ -1,14 +1,14 @@
-// probe.cu -- measured roofs for the rendering kernels.  The forward and the
-// adjoint read a scene and textures that stay resident in L2, and the adjoint
-// scatters its gradients with float4 atomics; neither rate is a published
-// figure, so these two kernels measure them on the device at hand.  They are
-// measurement helpers, not part of the method.
+// probe.cu -- measured roofs for the rendering kernels, built as a
+// measurement library of its own (libdpcs_probe.so; the product library does
+// not contain it).  The forward and the adjoint read a scene and textures
+// that stay resident in L2, and the adjoint scatters its gradients with
+// float4 atomics; neither rate is a published figure, so these two kernels
+// measure them on the device at hand.  They are measurement helpers, not
+// part of the method.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "internal.h"
-
-namespace dpcs {
+#include "dpcs_probe.h"
 
 namespace {
 
@@ -52,14 +52,16 @@ __global__ void __launch_bounds__(kProbeBlock, kAtomicBlocksPerSM)
     }
 }
 
+constexpr int32_t kOk = 0, kBadArg = -1, kOom = -2, kCuda = -3;
+
 // best of `reps` event-timed launches of fn on stream 0, in ms
 template <class F>
-dpcs_status time_best(dpcs_ctx *c, int reps, F fn, float *best) {
+int32_t time_best(int reps, F fn, float *best) {
     cudaEvent_t e0, e1;
-    if (cudaEventCreate(&e0) != cudaSuccess) return ctx_fail(c, DPCS_ERR_CUDA, "probe: cudaEventCreate");
+    if (cudaEventCreate(&e0) != cudaSuccess) return kCuda;
     if (cudaEventCreate(&e1) != cudaSuccess) {
         cudaEventDestroy(e0);
-        return ctx_fail(c, DPCS_ERR_CUDA, "probe: cudaEventCreate");
+        return kCuda;
     }
     *best = 0.0f;
     cudaError_t e = cudaSuccess;
@@ -75,8 +77,8 @@ dpcs_status time_best(dpcs_ctx *c, int reps, F fn, float *best) {
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    if (e != cudaSuccess) return ctx_fail(c, DPCS_ERR_CUDA, cudaGetErrorString(e));
-    return *best > 0.0f ? DPCS_OK : ctx_fail(c, DPCS_ERR_CUDA, "probe: zero kernel time");
+    if (e != cudaSuccess) return kCuda;
+    return *best > 0.0f ? kOk : kCuda;
 }
 
 struct DevBuf {
@@ -86,65 +88,60 @@ struct DevBuf {
     }
 };
 
-dpcs_status probe_setup(dpcs_ctx *c, int *sms) {
-    if (cudaSetDevice(ctx_device(c)) != cudaSuccess) return ctx_fail(c, DPCS_ERR_CUDA, "probe: cudaSetDevice");
-    if (cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, ctx_device(c)) != cudaSuccess)
-        return ctx_fail(c, DPCS_ERR_CUDA, "probe: SM count");
-    return DPCS_OK;
+int32_t probe_setup(int32_t device, int *sms) {
+    if (cudaSetDevice(device) != cudaSuccess) return kCuda;
+    if (cudaDeviceGetAttribute(sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) return kCuda;
+    return kOk;
 }
 
 }  // namespace
 
-}  // namespace dpcs
-
-using namespace dpcs;
-
 extern "C" {
 
-dpcs_status dpcs_probe_l2_load(dpcs_ctx *c, size_t bytes, int32_t passes, double *gbs) {
-    if (!c || !gbs) return DPCS_ERR_INVALID_ARG;
-    if (bytes == 0 || bytes % 16 != 0 || bytes > ((size_t)64 << 20) || passes < 1 || passes > 4096)
-        return ctx_fail(c, DPCS_ERR_INVALID_ARG, "probe_l2_load: bytes must be a positive multiple of 16 up to "
-                                                 "64 MiB and passes in [1, 4096]");
+int32_t dpcs_probe_l2_load(int32_t device, size_t bytes, int32_t passes, double *gbs) {
+    if (!gbs || bytes == 0 || bytes % 16 != 0 || bytes > ((size_t)64 << 20) || passes < 1 || passes > 4096)
+        return kBadArg;
     int sms = 0;
-    dpcs_status s = probe_setup(c, &sms);
+    int32_t s = probe_setup(device, &sms);
     if (s) return s;
     DevBuf buf, sink;
-    if (cudaMalloc(&buf.p, bytes) != cudaSuccess || cudaMalloc(&sink.p, 16) != cudaSuccess)
-        return ctx_fail(c, DPCS_ERR_OOM, "probe_l2_load: cudaMalloc");
-    if (cudaMemset(buf.p, 0, bytes) != cudaSuccess) return ctx_fail(c, DPCS_ERR_CUDA, "probe_l2_load: cudaMemset");
+    if (cudaMalloc(&buf.p, bytes) != cudaSuccess || cudaMalloc(&sink.p, 16) != cudaSuccess) {
+        cudaGetLastError();
+        return kOom;
+    }
+    if (cudaMemset(buf.p, 0, bytes) != cudaSuccess) return kCuda;
     const int64_t n4 = (int64_t)(bytes / 16);
     const int grid = sms * kLoadBlocksPerSM;
     float ms = 0.0f;
-    s = time_best(c, 3, [&] {
+    s = time_best(3, [&] {
         k_probe_l2_load<<<grid, kProbeBlock>>>((const uint4 *)buf.p, n4, passes, (unsigned *)sink.p);
     }, &ms);
     if (s) return s;
-    ctx_add_launches(c, 4);
     *gbs = (double)bytes * passes / (ms * 1e-3) / 1e9;
-    return DPCS_OK;
+    return kOk;
 }
 
-dpcs_status dpcs_probe_atomic4(dpcs_ctx *c, int32_t texels, int64_t n_atomics, double *gatomics) {
-    if (!c || !gatomics) return DPCS_ERR_INVALID_ARG;
-    if (texels < 1 || texels > (1 << 24) || n_atomics < 1 || n_atomics > ((int64_t)1 << 34))
-        return ctx_fail(c, DPCS_ERR_INVALID_ARG, "probe_atomic4: texels in [1, 2^24], n_atomics in [1, 2^34]");
+int32_t dpcs_probe_atomic4(int32_t device, int32_t texels, int64_t n_atomics, double *gatomics) {
+    if (!gatomics || texels < 1 || texels > (1 << 24) || n_atomics < 1 || n_atomics > ((int64_t)1 << 34))
+        return kBadArg;
     int sms = 0;
-    dpcs_status s = probe_setup(c, &sms);
+    int32_t s = probe_setup(device, &sms);
     if (s) return s;
     DevBuf buf;
     const size_t bytes = (size_t)texels * 16;
-    if (cudaMalloc(&buf.p, bytes) != cudaSuccess) return ctx_fail(c, DPCS_ERR_OOM, "probe_atomic4: cudaMalloc");
-    if (cudaMemset(buf.p, 0, bytes) != cudaSuccess) return ctx_fail(c, DPCS_ERR_CUDA, "probe_atomic4: cudaMemset");
+    if (cudaMalloc(&buf.p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return kOom;
+    }
+    if (cudaMemset(buf.p, 0, bytes) != cudaSuccess) return kCuda;
     const int grid = sms * kAtomicBlocksPerSM;
     const int64_t threads = (int64_t)grid * kProbeBlock;
     const int64_t per_thread = (n_atomics + threads - 1) / threads;
     float ms = 0.0f;
-    s = time_best(c, 3, [&] { k_probe_atomic4<<<grid, kProbeBlock>>>((float4 *)buf.p, texels, per_thread); }, &ms);
+    s = time_best(3, [&] { k_probe_atomic4<<<grid, kProbeBlock>>>((float4 *)buf.p, texels, per_thread); }, &ms);
     if (s) return s;
-    ctx_add_launches(c, 4);
     *gatomics = (double)(threads * per_thread) / (ms * 1e-3) / 1e9;
-    return DPCS_OK;
+    return kOk;
 }
 
 }  // extern "C"

@@ -34,6 +34,12 @@ constexpr int kRenderBlock = 128;
 #ifndef DPCS_BATCH_MINB
 #define DPCS_BATCH_MINB 8  // resident blocks per SM for the batched render: it reads its arguments from shared memory and needs the registers
 #endif
+#ifndef DPCS_ALIGN_SHADOW
+// 1: a vertex without projector light takes an empty shadow step, so the
+// lanes of a warp trace extension rays and shadow rays in the same
+// iterations and shade together; 0: it goes straight to its extension ray
+#define DPCS_ALIGN_SHADOW 1
+#endif
 #ifndef DPCS_RENDER_MINB
 #define DPCS_RENDER_MINB 10  // minimum resident blocks per SM requested from ptxas (48 registers; sweep: 9-12 within 3 %)
 #endif
@@ -135,7 +141,7 @@ __device__ __forceinline__ void render_lanes(const RenderArgs &a, int64_t pix, i
     Cnt cnt;
     int s = valid ? sl : a.spp;
     int b = 1;
-    bool shadow = false, has_ext = false, pending = false;
+    bool shadow = false, has_ext = false, pending = false, nulls = false;
     // throughput, pending NEE contribution, extension direction; each lit
     // vertex's contribution goes straight into the lane's pixel sum
     f3 beta = mk3(0.f, 0.f, 0.f), c = beta, ed = beta;
@@ -168,21 +174,22 @@ __device__ __forceinline__ void render_lanes(const RenderArgs &a, int64_t pix, i
             // yield only while some live lane of the warp could take a new ray
             const int alive = DPCS_YIELD_MIN > 0 ? __popc(__activemask()) : 0;
             if (!pending) {
-                cnt.add(shadow ? kCntShadow : kCntRay);
+                if (!nulls) cnt.add(shadow ? kCntShadow : kCntRay);
                 trav_begin(st, a.root, shadow ? tmax : INFINITY, shadow);
                 pending = true;
             }
-            if (!trav_resume(a.nodes, a.tris, a.root, a.T, ray, st, stack, a.status, cnt, min(DPCS_YIELD_MIN, alive), a.visit_cap))
+            if (!trav_resume(a.nodes, a.tris, nulls ? kEmptyRoot : a.root, a.T, ray, st, stack, a.status, cnt, min(DPCS_YIELD_MIN, alive), a.visit_cap))
                 continue;
             pending = false;
             const bool hit = st.h.pos >= 0;
             bool end = false;
             if (shadow) {
-                if (!hit) {
+                if (!hit && !nulls) {
                     sum = sum + c;
                     cnt.add(kCntLit);
                 }
                 shadow = false;
+                nulls = false;
                 if (has_ext) {  // the extension ray starts where the shadow ray did (x + n eps)
                     ray = make_ray(ray.o, ed);
                     ++b;
@@ -215,8 +222,16 @@ __device__ __forceinline__ void render_lanes(const RenderArgs &a, int64_t pix, i
                     ray = make_ray(N.so, N.sdir);
                     tmax = N.smax;
                 } else if (has_ext) {
+#if DPCS_ALIGN_SHADOW
+                    // no projector light here: an empty shadow step (no
+                    // traversal) keeps the lane in phase with the others
+                    shadow = true;
+                    nulls = true;
+                    ray.o = S.x + S.n * kRayEps;
+#else
                     ray = make_ray(S.x + S.n * kRayEps, ed);
                     ++b;
+#endif
                 } else {
                     end = true;
                 }
@@ -231,6 +246,7 @@ __device__ __forceinline__ void render_lanes(const RenderArgs &a, int64_t pix, i
             beta = mk3(1.f, 1.f, 1.f);
             b = 1;
             shadow = false;
+            nulls = false;
             has_ext = false;
             cnt.add(kCntPath);
         }
@@ -453,7 +469,7 @@ __global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB) k_replay(const
     __shared__ float4 s_row[kRenderBlock];  // per-warp rows for scatter_add4
     int s = (pix < npix && any) ? sl : a.spp;
     int b = 1, nv = 0;
-    bool shadow = false, has_ext = false, pending = false;
+    bool shadow = false, has_ext = false, pending = false, nulls = false;
     f3 beta = mk3(0.f, 0.f, 0.f), ed = beta;
     Ray ray;
     ray.o = ray.d = ray.inv = beta;
@@ -482,19 +498,20 @@ __global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB) k_replay(const
             }
             const int alive = DPCS_YIELD_MIN > 0 ? __popc(__activemask()) : 0;
             if (!pending) {
-                cnt.add(shadow ? kCntShadow : kCntRay);
+                if (!nulls) cnt.add(shadow ? kCntShadow : kCntRay);
                 trav_begin(st, a.root, shadow ? tmax : INFINITY, shadow);
                 pending = true;
             }
-            if (!trav_resume(a.nodes, a.tris, a.root, a.T, ray, st, stack, a.status, cnt, min(DPCS_YIELD_MIN, alive), a.visit_cap))
+            if (!trav_resume(a.nodes, a.tris, nulls ? kEmptyRoot : a.root, a.T, ray, st, stack, a.status, cnt, min(DPCS_YIELD_MIN, alive), a.visit_cap))
                 continue;
             pending = false;
             const bool hit = st.h.pos >= 0;
             bool end = false;
             if (shadow) {
                 if (hit) rec[nv - 1].G = 0.0f;  // occluded: no projector light at this vertex
-                else cnt.add(kCntLit);
+                else if (!nulls) cnt.add(kCntLit);
                 shadow = false;
+                nulls = false;
                 if (has_ext) {
                     ray = make_ray(ray.o, ed);
                     ++b;
@@ -536,8 +553,16 @@ __global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB) k_replay(const
                     ray = make_ray(N.so, N.sdir);
                     tmax = N.smax;
                 } else if (has_ext) {
+#if DPCS_ALIGN_SHADOW
+                    // no projector light here: an empty shadow step (no
+                    // traversal) keeps the lane in phase with the others
+                    shadow = true;
+                    nulls = true;
+                    ray.o = S.x + S.n * kRayEps;
+#else
                     ray = make_ray(S.x + S.n * kRayEps, ed);
                     ++b;
+#endif
                 } else {
                     end = true;
                 }
@@ -554,6 +579,7 @@ __global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB) k_replay(const
             beta = mk3(1.f, 1.f, 1.f);
             b = 1;
             shadow = false;
+            nulls = false;
             has_ext = false;
             cnt.add(kCntPath);
         }
@@ -582,7 +608,7 @@ __global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB) k_render_grad(
     __shared__ float4 s_row[kRenderBlock];  // per-warp rows for scatter_add4
     int s = valid ? sl : a.spp;
     int b = 1, nv = 0, k = 0;
-    bool shadow = false, has_ext = false, pending = false;
+    bool shadow = false, has_ext = false, pending = false, nulls = false;
     f3 sum = mk3(0.f, 0.f, 0.f);
     f3 beta = sum, c = sum, ed = sum;
     Ray ray;
@@ -615,14 +641,14 @@ __global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB) k_render_grad(
                 break;
             }
             if (!pending) {
-                cnt.add(shadow ? kCntShadow : kCntRay);
+                if (!nulls) cnt.add(shadow ? kCntShadow : kCntRay);
                 trav_begin(st, a.root, shadow ? tmax : INFINITY, shadow);
                 pending = true;
             }
             // the same call as in k_render and k_replay: passing a literal 0 for
             // min_active instead (the same value) made this kernel 3.2x slower
             const int alive = DPCS_YIELD_MIN > 0 ? __popc(__activemask()) : 0;
-            if (!trav_resume(a.nodes, a.tris, a.root, a.T, ray, st, stack, a.status, cnt, min(DPCS_YIELD_MIN, alive),
+            if (!trav_resume(a.nodes, a.tris, nulls ? kEmptyRoot : a.root, a.T, ray, st, stack, a.status, cnt, min(DPCS_YIELD_MIN, alive),
                              a.visit_cap))
                 continue;
             pending = false;
@@ -631,11 +657,12 @@ __global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB) k_render_grad(
             if (shadow) {
                 if (hit) {
                     rs[nv - 1].G = 0.0f;  // occluded: no projector light at this vertex
-                } else {
+                } else if (!nulls) {
                     sum = sum + c;
                     cnt.add(kCntLit);
                 }
                 shadow = false;
+                nulls = false;
                 if (has_ext) {
                     ray = make_ray(ray.o, ed);
                     ++b;
@@ -677,8 +704,16 @@ __global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB) k_render_grad(
                     ray = make_ray(N.so, N.sdir);
                     tmax = N.smax;
                 } else if (has_ext) {
+#if DPCS_ALIGN_SHADOW
+                    // no projector light here: an empty shadow step (no
+                    // traversal) keeps the lane in phase with the others
+                    shadow = true;
+                    nulls = true;
+                    ray.o = S.x + S.n * kRayEps;
+#else
                     ray = make_ray(S.x + S.n * kRayEps, ed);
                     ++b;
+#endif
                 } else {
                     end = true;
                 }
@@ -696,6 +731,7 @@ __global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB) k_render_grad(
             beta = mk3(1.f, 1.f, 1.f);
             b = 1;
             shadow = false;
+            nulls = false;
             has_ext = false;
             cnt.add(kCntPath);
         }
@@ -757,7 +793,7 @@ __global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB)
     const int64_t nthr = ((int64_t)a.Hc * a.Wc) << a.log2L;
     int s = valid ? sl : a.spp;
     int b = 1, nv = 0, k = 0;
-    bool shadow = false, has_ext = false, pending = false;
+    bool shadow = false, has_ext = false, pending = false, nulls = false;
     f3 sum = mk3(0.f, 0.f, 0.f);
     f3 beta = sum, c = sum, ed = sum;
     Ray ray;
@@ -786,14 +822,14 @@ __global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB)
                 break;
             }
             if (!pending) {
-                cnt.add(shadow ? kCntShadow : kCntRay);
+                if (!nulls) cnt.add(shadow ? kCntShadow : kCntRay);
                 trav_begin(st, a.root, shadow ? tmax : INFINITY, shadow);
                 pending = true;
             }
             // the same call as in k_render and k_replay: passing a literal 0 for
             // min_active instead (the same value) made this kernel 3.2x slower
             const int alive = DPCS_YIELD_MIN > 0 ? __popc(__activemask()) : 0;
-            if (!trav_resume(a.nodes, a.tris, a.root, a.T, ray, st, stack, a.status, cnt, min(DPCS_YIELD_MIN, alive),
+            if (!trav_resume(a.nodes, a.tris, nulls ? kEmptyRoot : a.root, a.T, ray, st, stack, a.status, cnt, min(DPCS_YIELD_MIN, alive),
                              a.visit_cap))
                 continue;
             pending = false;
@@ -807,11 +843,12 @@ __global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB)
                                                                                        a.bounces, nthr, gt));
                         __stcs(w + kKeptGWord, 0u);
                     }
-                } else {
+                } else if (!nulls) {
                     sum = sum + c;
                     cnt.add(kCntLit);
                 }
                 shadow = false;
+                nulls = false;
                 if (has_ext) {
                     ray = make_ray(ray.o, ed);
                     ++b;
@@ -869,8 +906,16 @@ __global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB)
                     ray = make_ray(N.so, N.sdir);
                     tmax = N.smax;
                 } else if (has_ext) {
+#if DPCS_ALIGN_SHADOW
+                    // no projector light here: an empty shadow step (no
+                    // traversal) keeps the lane in phase with the others
+                    shadow = true;
+                    nulls = true;
+                    ray.o = S.x + S.n * kRayEps;
+#else
                     ray = make_ray(S.x + S.n * kRayEps, ed);
                     ++b;
+#endif
                 } else {
                     end = true;
                 }
@@ -888,6 +933,7 @@ __global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB)
             beta = mk3(1.f, 1.f, 1.f);
             b = 1;
             shadow = false;
+            nulls = false;
             has_ext = false;
             cnt.add(kCntPath);
         }

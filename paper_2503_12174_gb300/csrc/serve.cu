@@ -338,10 +338,11 @@ dpcs_status launch_iteration(dpcs_server *s, Batch &b) {
         vb += render_batch_vblocks(npx, q->args.log2L);
         ++nseg;
     };
-    // `active` is in arrival order.  1) every relighting request gets a small
-    // quantum, so short requests finish within an iteration or two;
+    // `active` is in arrival order.  1) (fixed share) every relighting
+    // request gets a small quantum, so short requests finish within an
+    // iteration or two; under the deadline policy the deadlines order them
     std::vector<int64_t> give(relight.size(), 0);
-    for (size_t i = 0; i < relight.size() && budget > 0; ++i) {
+    for (size_t i = 0; s->cfg.policy == DPCS_SERVE_FIXED_SHARE && i < relight.size() && budget > 0; ++i) {
         Req *q = relight[i];
         give[i] = std::min(q->npix - q->next_pix, std::max<int64_t>(1, s->cfg.quantum_samples / q->r.spp));
         budget -= give[i] * q->r.spp;

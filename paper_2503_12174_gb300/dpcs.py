@@ -37,7 +37,7 @@ EXPORTED = [
     "dpcs_render_backward", "dpcs_l2_loss", "dpcs_adam", "dpcs_timing_enable", "dpcs_timing_read",
     "dpcs_counters_read", "dpcs_debug_set_visit_cap", "dpcs_render_noalloc", "dpcs_serve_create", "dpcs_serve_destroy", "dpcs_serve_add_scene",
     "dpcs_serve_submit", "dpcs_serve_step", "dpcs_serve_query", "dpcs_serve_drain", "dpcs_serve_stats_get",
-    "dpcs_probe_l2_load", "dpcs_probe_atomic4", "dpcs_gbuffer", "dpcs_denoise", "dpcs_denoise_backward",
+    "dpcs_gbuffer", "dpcs_denoise", "dpcs_denoise_backward",
     "dpcs_l1_loss", "dpcs_tv_loss", "dpcs_scene_update", "dpcs_render_loss_backward", "dpcs_render_keep",
     "dpcs_render_backward_kept", "dpcs_render_principled", "dpcs_render_backward_principled",
     "dpcs_scene_transform", "dpcs_render_loss_backward_principled", "dpcs_render_keep_principled",
@@ -185,8 +185,6 @@ _SIGS = {
                                       _P, _P, _P]),
     "dpcs_denoise_backward": (ctypes.c_int32, [_P, _P, _P, _P, ctypes.c_int32, ctypes.c_int32,
                                                ctypes.POINTER(DpcsDenoiseParams), _P, _P]),
-    "dpcs_probe_l2_load": (ctypes.c_int32, [_P, ctypes.c_size_t, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
-    "dpcs_probe_atomic4": (ctypes.c_int32, [_P, ctypes.c_int32, ctypes.c_int64, ctypes.POINTER(ctypes.c_double)]),
     "dpcs_serve_create": (ctypes.c_int32, [_P, ctypes.POINTER(DpcsServeConfig), ctypes.POINTER(_P)]),
     "dpcs_serve_destroy": (ctypes.c_int32, [_P]),
     "dpcs_serve_add_scene": (ctypes.c_int32, [_P, ctypes.c_uint64, _P, _P, ctypes.c_int32, ctypes.c_int32,
@@ -385,14 +383,6 @@ def dpcs_counters_read(ctx, out, reset):
     return load_library().dpcs_counters_read(ctx, out, int(reset))
 
 
-def dpcs_probe_l2_load(ctx, nbytes, passes, gbs):
-    return load_library().dpcs_probe_l2_load(ctx, nbytes, int(passes), gbs)
-
-
-def dpcs_probe_atomic4(ctx, texels, n_atomics, gatomics):
-    return load_library().dpcs_probe_atomic4(ctx, int(texels), int(n_atomics), gatomics)
-
-
 def dpcs_gbuffer(ctx, scene, albedo, rough, Ht, Wt, view, guide, stream):
     return load_library().dpcs_gbuffer(ctx, scene, albedo, rough, Ht, Wt, ctypes.byref(view), guide, stream)
 
@@ -494,20 +484,6 @@ class Context:
         keys = ("node_visits", "tri_tests", "rays", "shadow_rays", "vertices", "lit", "continuations", "paths",
                 "trav_warp_iters", "path_warp_iters")
         return dict(zip(keys, [int(x) for x in out]))
-
-    def probe_l2_load(self, nbytes: int = 32 << 20, passes: int = 64) -> float:
-        """Measured L2 load bandwidth in GB/s (16-byte loads that bypass L1)."""
-        out = ctypes.c_double()
-        self.check(self.lib.dpcs_probe_l2_load(self.handle, int(nbytes), int(passes), ctypes.byref(out)),
-                   "probe_l2_load")
-        return out.value
-
-    def probe_atomic4(self, texels: int = 512 * 512, n_atomics: int = 1 << 28) -> float:
-        """Measured scattered float4 atomic-add throughput in 1e9 adds per second."""
-        out = ctypes.c_double()
-        self.check(self.lib.dpcs_probe_atomic4(self.handle, int(texels), int(n_atomics), ctypes.byref(out)),
-                   "probe_atomic4")
-        return out.value
 
     def kernel_time(self, kernel: int):
         """(total ms, launches) of kernel 0 = render, 1 = replay since timing(True)."""

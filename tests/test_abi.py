@@ -66,3 +66,18 @@ int main(void) {
                    ctypes.sizeof(dpcs.DpcsServeStats), ctypes.sizeof(dpcs.DpcsDenoiseParams),
                    dpcs.DpcsDenoiseParams.sigma_depth.offset, C.est_samples_per_s.offset,
                    C.compensation_share.offset]
+
+
+def test_probe_library_exports_its_header_and_the_product_library_has_no_probes():
+    """The roof probes live in the measurement library (include/dpcs_probe.h),
+    not in libdpcs.so."""
+    from paper_2503_12174_gb300 import probe
+
+    src = open(os.path.join(ROOT, "include", "dpcs_probe.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = sorted(set(re.findall(r"\b(dpcs_[a-z0-9_]+)\s*\(", src)))
+    assert names == ["dpcs_probe_atomic4", "dpcs_probe_l2_load"]
+    plib = probe.load_library()
+    assert all(hasattr(plib, n) for n in names)
+    lib = dpcs.load_library()
+    assert not any(hasattr(lib, n) for n in names)

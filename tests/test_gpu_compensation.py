@@ -135,6 +135,39 @@ def test_checkpoint_and_resume(orc, tmp_path):
         g.close()
 
 
+def test_checkpoint_and_resume_is_exact_with_fp64_accumulation(orc, tmp_path):
+    """With FP64 gradient accumulation the adjoint's sums do not depend on the
+    order of its atomics (beyond FP64 rounding, far below the FP32 result), so
+    three steps, a checkpoint and three resumed steps reproduce six steps in
+    one go bit for bit."""
+    from paper_2503_12174_gb300 import dpcs
+
+    torch, sc, target = _setup(orc, res=20, steps=6)
+    g = GpuScene(sc)
+    g.ctx.set_grad_accum(dpcs.DPCS_ACCUM_F64)
+    try:
+        args = (g.ctx, g.handle, g.albedo, g.rough, g.view, g.params, sc.spp, sc.bounces, 6)
+        init, tgt = torch.full_like(g.Ip, 0.5), torch.from_numpy(target).cuda()
+        whole = compensate.Compensation(*args, lr=0.05, seed=7, graph=False)
+        whole.start(init, tgt)
+        Pw, hw = whole.advance(6)
+        Pw, hw = Pw.clone(), hw.clone()
+        first = compensate.Compensation(*args, lr=0.05, seed=7, graph=False)
+        first.start(init, tgt)
+        first.advance(3)
+        path = str(tmp_path / "comp64.npz")
+        first.save(path)
+        second = compensate.Compensation(*args, lr=0.05, seed=7, graph=False)
+        second.resume(path)
+        Pr, hr = second.advance(3)
+        g.ctx.sync()
+        np.testing.assert_array_equal(hr.cpu().numpy(), hw.cpu().numpy())
+        np.testing.assert_array_equal(Pr.cpu().numpy(), Pw.cpu().numpy())
+    finally:
+        g.ctx.set_grad_accum(dpcs.DPCS_ACCUM_F32)
+        g.close()
+
+
 @pytest.mark.parametrize("denoised", [False, True])
 def test_principled_compensation_follows_oracle(orc, denoised):
     """Compensation on a surface with metallic and normal maps: the one-trace
