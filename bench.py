@@ -132,7 +132,7 @@ def _args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="target oracle time for cpu_baseline")
     ap.add_argument("--serve-requests", type=int, default=120, help="requests per serving run (0 = skip)")
-    ap.add_argument("--serve-rates", default="5,8,11", help="Poisson arrival rates (requests/s) of the load sweep")
+    ap.add_argument("--serve-rates", default="3,8,14", help="Poisson arrival rates (requests/s) of the load sweep")
     ap.add_argument("--heightfield-steps", type=int, default=2, help="timed steps of the 200k-triangle workload (0 = skip)")
     ap.add_argument("--comp-steps", type=int, default=100, help="Adam steps of the full compensation run (0 = skip)")
     ap.add_argument("--fit-steps", type=int, default=10, help="timed steps of the Eq. 9 scene fit (0 = skip)")
@@ -969,13 +969,18 @@ def main():
         keep = ("requests_per_s", "relight_p50_ms", "relight_p99_ms", "compensation_p50_ms", "compensation_p99_ms",
                 "samples_per_s_M", "wall_s")
         sweep = []
+        deadline = dict(policy=dpcs.DPCS_SERVE_DEADLINE, relight_slack=4.0, compensation_slack=0.5)
         for rate in [float(x) for x in args.serve_rates.split(",") if x]:
             wl = serving.make_workload(args.serve_requests, rate=rate, seed=100 + rank)
             srv = serving.run_server(ctx, gs, host, wl)
             per = serving.run_per_call(ctx, gs, host, wl)
-            sweep.append({"offered_rate_per_s": rate, "server": {k: srv[k] for k in keep},
-                          "per_call": {k: per[k] for k in keep}, "server_iterations": srv["server"]["iterations"],
-                          "server_memory_high_water_bytes": srv["server"]["memory_high_water"]})
+            entry = {"offered_rate_per_s": rate, "server": {k: srv[k] for k in keep},
+                     "per_call": {k: per[k] for k in keep}, "server_iterations": srv["server"]["iterations"],
+                     "server_memory_high_water_bytes": srv["server"]["memory_high_water"]}
+            if rate >= 8.0:  # the deadline policy beside the default fixed share
+                dl = serving.run_server(ctx, gs, host, wl, **deadline)
+                entry["server_deadline_policy"] = {k: dl[k] for k in keep}
+            sweep.append(entry)
         sat = serving.make_workload(args.serve_requests, rate=0.0, seed=200 + rank)
         srv_sat = serving.run_server(ctx, gs, host, sat)
         per_sat = serving.run_per_call(ctx, gs, host, sat)
@@ -985,6 +990,8 @@ def main():
             "workload": f"{args.serve_requests} requests per run over 3 resident scenes (plane, corner256, corner512); "
                         "camera side in {128..1024 step 64}, spp log-uniform 16-256; 90% relight, "
                         "10% compensation (50 Adam steps, 16 spp); Poisson arrivals",
+            "policy": "server = fixed share (relighting quanta, compensation within half of each iteration); "
+                      "server_deadline_policy = earliest deadline first, slack 4 (relight) and 0.5 (compensation)",
             "load_sweep": sweep,
             "saturated": {"server_requests_per_s": srv_sat["requests_per_s"],
                           "per_call_requests_per_s": per_sat["requests_per_s"],
@@ -1059,7 +1066,9 @@ def main():
             summ["serving"] = [{"rate": x["offered_rate_per_s"], "srv_relight_p99": x["server"]["relight_p99_ms"],
                                 "call_relight_p99": x["per_call"]["relight_p99_ms"],
                                 "srv_comp_p99": x["server"]["compensation_p99_ms"],
-                                "call_comp_p99": x["per_call"]["compensation_p99_ms"]}
+                                "call_comp_p99": x["per_call"]["compensation_p99_ms"],
+                                "deadline_relight_p99": x.get("server_deadline_policy", {}).get("relight_p99_ms"),
+                                "deadline_comp_p99": x.get("server_deadline_policy", {}).get("compensation_p99_ms")}
                                for x in serving_out["load_sweep"]]
         line["summary"] = summ
         print(json.dumps(line), flush=True)

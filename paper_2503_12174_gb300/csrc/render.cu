@@ -41,7 +41,15 @@ constexpr int kRenderBlock = 128;
 #define DPCS_ALIGN_SHADOW 1
 #endif
 #ifndef DPCS_RENDER_MINB
-#define DPCS_RENDER_MINB 10  // minimum resident blocks per SM requested from ptxas (48 registers; sweep: 9-12 within 3 %)
+// minimum resident blocks per SM requested from ptxas for k_render: 8 (64
+// registers) against 10 (48 registers, with spills) measured 2 % faster on
+// the corner and 2 % slower on the 200k-triangle heightfield
+#define DPCS_RENDER_MINB 8
+#endif
+#ifndef DPCS_GRAD_MINB
+// the same for the kernels that keep vertex records (replay, fused step,
+// kept records): 8 blocks (64 registers) measured 3-5 % faster than 10
+#define DPCS_GRAD_MINB 8
 #endif
 
 __device__ __forceinline__ void atomic_add4(float4 *p, float4 v) {
@@ -451,7 +459,7 @@ __device__ __forceinline__ void replay_sweep(const RenderArgs &a, const VRec *re
 // records every vertex; once every path of the warp has ended, the lanes run
 // their reverse sweeps together and start their next samples.
 template <bool F64>
-__global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB) k_replay(const RenderArgs a) {
+__global__ void __launch_bounds__(kRenderBlock, DPCS_GRAD_MINB) k_replay(const RenderArgs a) {
     const int L = 1 << a.log2L;
     const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t pix = gt >> a.log2L;
@@ -598,7 +606,7 @@ __global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB) k_replay(const
 // calls it only when ceil(spp / L) <= kFusedSamples and ceil(spp / L) *
 // bounces <= kFusedRecs.
 template <bool F64>
-__global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB) k_render_grad(const RenderArgs a, const LossArgs l) {
+__global__ void __launch_bounds__(kRenderBlock, DPCS_GRAD_MINB) k_render_grad(const RenderArgs a, const LossArgs l) {
     const int L = 1 << a.log2L;
     const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t pix = gt >> a.log2L;
@@ -782,7 +790,7 @@ __global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB) k_render_grad(
 // writes them, so a later k_sweep_kept can run the adjoint of any loss,
 // including one that couples pixels (the Eq. 11 filter), without tracing
 // the paths again.
-__global__ void __launch_bounds__(kRenderBlock, DPCS_RENDER_MINB)
+__global__ void __launch_bounds__(kRenderBlock, DPCS_GRAD_MINB)
     k_render_keep(const RenderArgs a, uint4 *__restrict__ chunks, uint8_t *__restrict__ nvs) {
     const int L = 1 << a.log2L;
     const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
