@@ -56,17 +56,19 @@ L2_FLUSH_BYTES = 256 << 20
 # ncu capture of the same command.  It holds only for the kernel sources it
 # was measured on; once they change, the roofline's traffic is reported as
 # null until a new capture is taken.
-RENDER_TRAFFIC = {"bytes": 36724736, "sources_sha256": "7e2cfcba363a44384f6a98b48b89053c847a717d32acc2def29ee65c2981c67d"}
+RENDER_TRAFFIC = {"bytes": 23213568, "sources_sha256": "adfb480d3e287616f440b500cd7c94980f0d24b41814978db260480e0817b544"}
 # Warp instructions one k_render launch of the forward workload issues, and
 # the active lanes per instruction, from the same ncu capture
 # (smsp__inst_executed.sum, smsp__thread_inst_executed_per_inst_executed);
 # reported while the kernel sources keep this hash.
-RENDER_ISSUE = {"warp_instructions": 1879286116, "lanes_per_instruction": 12.08,
-                "sources_sha256": "7e2cfcba363a44384f6a98b48b89053c847a717d32acc2def29ee65c2981c67d"}
+RENDER_ISSUE = {"warp_instructions": 2012553153, "lanes_per_instruction": 11.69,
+                "sources_sha256": "adfb480d3e287616f440b500cd7c94980f0d24b41814978db260480e0817b544"}
 # The same two figures for one k_render_grad launch of the compensation step
 # with every gradient requested.
-FWD_BWD_TRAFFIC = {"bytes": None, "sources_sha256": ""}
-FWD_BWD_ISSUE = {"warp_instructions": None, "lanes_per_instruction": None, "sources_sha256": ""}
+FWD_BWD_TRAFFIC = {"bytes": 1907859200,
+                   "sources_sha256": "adfb480d3e287616f440b500cd7c94980f0d24b41814978db260480e0817b544"}
+FWD_BWD_ISSUE = {"warp_instructions": 2224721825, "lanes_per_instruction": 12.89,
+                 "sources_sha256": "adfb480d3e287616f440b500cd7c94980f0d24b41814978db260480e0817b544"}
 KERNEL_SOURCES = ("paper_2503_12174_gb300/csrc/render.cu", "paper_2503_12174_gb300/csrc/device.cuh",
                   "paper_2503_12174_gb300/csrc/internal.h")
 
@@ -885,7 +887,7 @@ def main():
         ctx.free(hh)
         hf_out = {"workload": f"heightfield T={hs.T}, camera {hs.Hc}x{hs.Wc}, projector {hs.Wp}x{hs.Hp}, "
                               f"textures 512x512, {hs.bounces} bounces, Russian roulette from vertex 2 (q=0.75); "
-                              "fwd_bwd = render + L2 loss + adjoint to Ip in one fused call",
+                              "fwd_bwd = render + L2 loss + adjoint to Ip, textures and response parameters in one fused call",
                   **res}
 
     # ------------------------------------------------------------ principled material (metallic + normal maps)
