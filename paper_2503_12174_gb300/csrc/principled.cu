@@ -33,6 +33,13 @@
 
 namespace dpcs {
 
+#ifndef DPCS_ALIGN_SHADOW
+// 1: a vertex without projector light takes an empty shadow step, so the
+// lanes of a warp trace extension rays and shadow rays in the same
+// iterations (as in render.cu)
+#define DPCS_ALIGN_SHADOW 1
+#endif
+
 namespace {
 
 constexpr int kPBlock = 128;
@@ -378,7 +385,7 @@ __device__ __forceinline__ void pbr_lanes(const RenderArgs &a, const float4 *__r
     }
     int s = (valid && any) ? sl : a.spp;
     int b = 1, nv = 0;
-    bool shadow = false, has_ext = false, pending = false;
+    bool shadow = false, has_ext = false, pending = false, nulls = false;
     f3 beta = mk3(0.f, 0.f, 0.f), c = beta, ed = beta;
     Ray ray;
     ray.o = ray.d = ray.inv = beta;
@@ -411,15 +418,15 @@ __device__ __forceinline__ void pbr_lanes(const RenderArgs &a, const float4 *__r
                 break;
             }
             if (!pending) {
-                cnt.add(shadow ? kCntShadow : kCntRay);
+                if (!nulls) cnt.add(shadow ? kCntShadow : kCntRay);
                 trav_begin(st, a.root, shadow ? tmax : INFINITY, shadow);
                 pending = true;
             }
             // the min_active argument in the form render.cu's kernels pass it:
             // there a literal 0 (the same value) cost a 3.2x slowdown
             const int alive = DPCS_YIELD_MIN > 0 ? __popc(__activemask()) : 0;
-            if (!trav_resume(a.nodes, a.tris, a.root, a.T, ray, st, stack, a.status, cnt, min(DPCS_YIELD_MIN, alive),
-                             a.visit_cap))
+            if (!trav_resume(a.nodes, a.tris, nulls ? kEmptyRoot : a.root, a.T, ray, st, stack, a.status, cnt,
+                             min(DPCS_YIELD_MIN, alive), a.visit_cap))
                 continue;
             pending = false;
             const bool hit = st.h.pos >= 0;
@@ -433,11 +440,12 @@ __device__ __forceinline__ void pbr_lanes(const RenderArgs &a, const float4 *__r
                     } else if (kReplay) {
                         rs[nv - 1].G = 0.0f;  // occluded
                     }
-                } else {
+                } else if (!nulls) {
                     if (kMode != kModeReplay) sum = sum + c;
                     cnt.add(kCntLit);
                 }
                 shadow = false;
+                nulls = false;
                 if (has_ext) {
                     ray = make_ray(ray.o, ed);
                     ++b;
@@ -498,8 +506,16 @@ __device__ __forceinline__ void pbr_lanes(const RenderArgs &a, const float4 *__r
                     ray = make_ray(N.so, N.sdir);
                     tmax = N.smax;
                 } else if (has_ext) {
+#if DPCS_ALIGN_SHADOW
+                    // no projector light here: an empty shadow step (no
+                    // traversal) keeps the lane in phase with the others
+                    shadow = true;
+                    nulls = true;
+                    ray.o = S.x + S.n * kRayEps;
+#else
                     ray = make_ray(S.x + S.n * kRayEps, ed);
                     ++b;
+#endif
                 } else {
                     end = true;
                 }
@@ -519,6 +535,7 @@ __device__ __forceinline__ void pbr_lanes(const RenderArgs &a, const float4 *__r
             beta = mk3(1.f, 1.f, 1.f);
             b = 1;
             shadow = false;
+            nulls = false;
             has_ext = false;
             cnt.add(kCntPath);
         }
