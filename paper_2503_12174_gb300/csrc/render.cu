@@ -1016,8 +1016,9 @@ __global__ void k_prf_backward(const float *__restrict__ Ip, const float4 *__res
     block_reduce_add<4>(v, acc);
 }
 
-// the same from FP64 accumulators; the products and the reductions are
-// taken in FP64 before the result is rounded
+// the same from FP64 accumulators: the per-texel factors Ip^gamma, its
+// derivative and ln Ip in FP32 (as k_prf_backward), the products and the
+// reductions in FP64 before the result is rounded
 __global__ void k_prf_backward64(const float *__restrict__ Ip, const double *__restrict__ dEp, int64_t ntex,
                                  float g0, float g1, float g2, float gain, float *__restrict__ dIp, double *acc) {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -1029,9 +1030,9 @@ __global__ void k_prf_backward64(const float *__restrict__ Ip, const double *__r
             const float ip = Ip[3 * t + j];
             const double gs = dEp[3 * t + j];
             if (ip > 0.0f && gs != 0.0) {
-                const double pw = pow((double)ip, (double)gm[j]);
-                if (dIp) dIp[3 * t + j] += (float)(gs * gain * gm[j] * pow((double)ip, (double)gm[j] - 1.0));
-                v[j] += gs * gain * pw * log((double)ip);
+                const double pw = (double)powf(ip, gm[j]);
+                if (dIp) dIp[3 * t + j] += (float)(gs * (double)(gain * gm[j] * powf(ip, gm[j] - 1.0f)));
+                v[j] += gs * (double)gain * pw * (double)logf(ip);
                 v[3] += gs * pw;
             }
         }
