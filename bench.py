@@ -56,19 +56,19 @@ L2_FLUSH_BYTES = 256 << 20
 # ncu capture of the same command.  It holds only for the kernel sources it
 # was measured on; once they change, the roofline's traffic is reported as
 # null until a new capture is taken.
-RENDER_TRAFFIC = {"bytes": 23213568, "sources_sha256": "adfb480d3e287616f440b500cd7c94980f0d24b41814978db260480e0817b544"}
+RENDER_TRAFFIC = {"bytes": 23004160, "sources_sha256": "868c983676ab5d1dbc76dfb730588b3b3b6e73744dbd106acb33d7a741dc076c"}
 # Warp instructions one k_render launch of the forward workload issues, and
 # the active lanes per instruction, from the same ncu capture
 # (smsp__inst_executed.sum, smsp__thread_inst_executed_per_inst_executed);
 # reported while the kernel sources keep this hash.
-RENDER_ISSUE = {"warp_instructions": 2012553153, "lanes_per_instruction": 11.69,
-                "sources_sha256": "adfb480d3e287616f440b500cd7c94980f0d24b41814978db260480e0817b544"}
+RENDER_ISSUE = {"warp_instructions": 1914933228, "lanes_per_instruction": 12.08,
+                "sources_sha256": "868c983676ab5d1dbc76dfb730588b3b3b6e73744dbd106acb33d7a741dc076c"}
 # The same two figures for one k_render_grad launch of the compensation step
 # with every gradient requested.
-FWD_BWD_TRAFFIC = {"bytes": 1907859200,
-                   "sources_sha256": "adfb480d3e287616f440b500cd7c94980f0d24b41814978db260480e0817b544"}
-FWD_BWD_ISSUE = {"warp_instructions": 2224721825, "lanes_per_instruction": 12.89,
-                 "sources_sha256": "adfb480d3e287616f440b500cd7c94980f0d24b41814978db260480e0817b544"}
+FWD_BWD_TRAFFIC = {"bytes": 1938776576,
+                   "sources_sha256": "868c983676ab5d1dbc76dfb730588b3b3b6e73744dbd106acb33d7a741dc076c"}
+FWD_BWD_ISSUE = {"warp_instructions": 2127931742, "lanes_per_instruction": 13.29,
+                 "sources_sha256": "868c983676ab5d1dbc76dfb730588b3b3b6e73744dbd106acb33d7a741dc076c"}
 KERNEL_SOURCES = ("paper_2503_12174_gb300/csrc/render.cu", "paper_2503_12174_gb300/csrc/device.cuh",
                   "paper_2503_12174_gb300/csrc/internal.h")
 

@@ -17,9 +17,11 @@ def _grad_close(g, r, rtol, scale_tol):
     return bool(np.all(err <= 0)), float(np.max(np.abs(g - r) / (np.abs(r) + 1e-30))), scale
 
 
+@pytest.mark.parametrize("accum", ["f32", "f64"])
 @pytest.mark.parametrize("res,spp,bounces,clip", [(24, 4, 3, 0.0), (31, 5, 2, 0.05), (20, 16, 1, 0.0)])
-def test_backward_matches_oracle(orc, res, spp, bounces, clip):
+def test_backward_matches_oracle(orc, res, spp, bounces, clip, accum):
     torch = need_cuda()
+    from paper_2503_12174_gb300 import dpcs
     sc = scenes.corner(res=res, tex=32, spp=spp, bounces=bounces, seed=3)
     p = sc.params
     sc = sc.replace(params=scenes.Params(gamma_p=p.gamma_p, gain_p=1.2, gamma_c=p.gamma_c, gain_c=p.gain_c,
@@ -29,7 +31,11 @@ def test_backward_matches_oracle(orc, res, spp, bounces, clip):
     W = rng.normal(size=(sc.Hc, sc.Wc, 3)).astype(np.float32)
     try:
         Ec, Ic = g.render()
-        grads = g.backward(Ec, Ic, torch.from_numpy(W).cuda())
+        g.ctx.set_grad_accum(dpcs.DPCS_ACCUM_F64 if accum == "f64" else dpcs.DPCS_ACCUM_F32)
+        try:
+            grads = g.backward(Ec, Ic, torch.from_numpy(W).cuda())
+        finally:
+            g.ctx.set_grad_accum(dpcs.DPCS_ACCUM_F32)
     finally:
         g.close()
     ref = orc.render_backward(sc, W.astype(np.float64))

@@ -20,8 +20,9 @@ def _backward(g, sc, Ec, Ic, dIc, spp, bounces, kept):
     return out
 
 
+@pytest.mark.parametrize("accum", ["f32", "f64"])
 @pytest.mark.parametrize("case", ["corner16", "corner64", "corner256", "heightfield_rr"])
-def test_kept_adjoint_equals_replay(case):
+def test_kept_adjoint_equals_replay(case, accum):
     torch = need_cuda()
     if case == "heightfield_rr":
         sc = scenes.heightfield(spp=8, cam=96, proj=(64, 80), tex=64, n_vert=41)
@@ -29,6 +30,7 @@ def test_kept_adjoint_equals_replay(case):
         spp = int(case[len("corner"):])
         sc = scenes.corner(res=40, tex=32, spp=spp, bounces=3, seed=2)
     g = GpuScene(sc)
+    g.ctx.set_grad_accum(dpcs.DPCS_ACCUM_F64 if accum == "f64" else dpcs.DPCS_ACCUM_F32)
     try:
         Ea = torch.empty((sc.Hc, sc.Wc, 3), device="cuda")
         Ia, _ = g.ctx.render(g.handle, g.albedo, g.rough, g.Ip, g.view, g.params, sc.spp, sc.bounces, sc.seed, Ec=Ea)
@@ -46,7 +48,10 @@ def test_kept_adjoint_equals_replay(case):
             a = ref[k].cpu().numpy()
             for o in (got, got2):
                 np.testing.assert_allclose(o[k].cpu().numpy(), a, rtol=1e-4, atol=1e-6 * np.abs(a).max(), err_msg=k)
+            if accum == "f64":  # order-independent sums: the second sweep repeats the first bit for bit
+                np.testing.assert_array_equal(got2[k].cpu().numpy(), got[k].cpu().numpy(), err_msg=k)
     finally:
+        g.ctx.set_grad_accum(dpcs.DPCS_ACCUM_F32)
         g.close()
 
 
