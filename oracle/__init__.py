@@ -18,6 +18,8 @@ from .oracle import (  # noqa: F401
     prf,
     render,
     render_backward,
+    crf_grad,
+    pose_backward,
     bsdf_eval,
     pbr_eval,
     bsdf_pdf,

@@ -866,6 +866,10 @@ typedef struct {
     double cw;                    /* cos_i / (pdf q) */
     pbr_f fi;                     /* f(wo, wi) and its partial derivatives */
     d3 wi_ci;                     /* wi / cos_i */
+    d3 x, wo;                     /* the vertex and the direction back along the incoming ray */
+    double r;                     /* roughness at the vertex */
+    d3 wp, wi;                    /* towards the projector (when nee) and the continuation (when cont) */
+    double c[3];                  /* this vertex's contribution to L (after clipping) */
 } vrec;
 
 typedef struct {
@@ -873,24 +877,21 @@ typedef struct {
     const double *albedo, *rough; int Ht, Wt;
     const double *metal, *nmap;   /* Ht x Wt and Ht x Wt x 3, or NULL */
     const double *Ep; int Hp, Wp;
-    double Kc_inv[9], Kp[9], Rp[9], tp[3], cp[3];
+    double Kc[9], Kc_inv[9], Kp[9], Rp[9], tp[3], cp[3];
     const or_params *P;
     int spp, bounces;
     uint64_t seed;
     int Wc;
 } rctx;
 
-/* returns path radiance (RGB) and the vertex records */
-static int trace_sample(const rctx *C, uint32_t pix, uint32_t s, double L[3], vrec *rec)
+/* The path that starts with the ray (o, d); continuation b draws its random
+ * numbers from counter (pix, s, b, 0).  Returns the number of vertices, the
+ * path radiance L (RGB) and the vertex records. */
+static int trace_ray(const rctx *C, d3 o, d3 d, uint32_t pix, uint32_t s, double L[3], vrec *rec)
 {
     const or_params *P = C->P;
     double u[4];
     L[0] = L[1] = L[2] = 0.0;
-    rand4(C->seed, pix, s, 0u, u);
-    double fx = (double)(pix % (uint32_t)C->Wc) + (P->jitter ? u[0] : 0.5);
-    double fy = (double)(pix / (uint32_t)C->Wc) + (P->jitter ? u[1] : 0.5);
-    d3 o = mk(0.0, 0.0, 0.0);
-    d3 d = nrm(mat3v(C->Kc_inv, mk(fx, fy, 1.0)));
     double beta[3] = {1.0, 1.0, 1.0};
     d3 cp = mk(C->cp[0], C->cp[1], C->cp[2]);
     int nv = 0;
@@ -935,6 +936,9 @@ static int trace_sample(const rctx *C, uint32_t pix, uint32_t s, double L[3], vr
         R->ns = ns;
         for (int j = 0; j < 3; ++j) R->beta[j] = beta[j];
         d3 wo = scl(d, -1.0);
+        R->x = x;
+        R->wo = wo;
+        R->r = r;
 
         /* next-event estimation to the pinhole projector (Eqs. 1, 2, 3, 6) */
         d3 X = add(mat3v(C->Rp, x), mk(C->tp[0], C->tp[1], C->tp[2]));
@@ -961,10 +965,12 @@ static int trace_sample(const rctx *C, uint32_t pix, uint32_t s, double L[3], vr
                         R->G = P->k_proj * cpz * cs / r2;
                         pbr_eval(ns, wo, wp, R->rho, r, R->m, P->ks, P->f0, &R->fp);
                         R->wp_cs = scl(wp, 1.0 / cs);
+                        R->wp = wp;
                         for (int j = 0; j < 3; ++j) {
                             double c = beta[j] * R->fp.f[j] * R->Ep[j] * R->G;
                             R->unclipped[j] = 1;
                             if (P->clip > 0.0 && c > P->clip) { c = P->clip; R->unclipped[j] = 0; }
+                            R->c[j] = c;
                             L[j] += c;
                         }
                     }
@@ -990,11 +996,23 @@ static int trace_sample(const rctx *C, uint32_t pix, uint32_t s, double L[3], vr
         double ci = dot(ns, wi);
         R->cw = ci / (pdf * qrr);
         R->wi_ci = scl(wi, 1.0 / ci);
+        R->wi = wi;
         for (int j = 0; j < 3; ++j) beta[j] *= R->fi.f[j] * R->cw;
         o = add(x, scl(n, OR_RAY_EPS));
         d = wi;
     }
     return nv;
+}
+
+/* camera sample s of pixel pix: the jittered ray of Eq. 6 with the Eq. 4 box
+ * filter, then trace_ray */
+static int trace_sample(const rctx *C, uint32_t pix, uint32_t s, double L[3], vrec *rec)
+{
+    double u[4];
+    rand4(C->seed, pix, s, 0u, u);
+    double fx = (double)(pix % (uint32_t)C->Wc) + (C->P->jitter ? u[0] : 0.5);
+    double fy = (double)(pix / (uint32_t)C->Wc) + (C->P->jitter ? u[1] : 0.5);
+    return trace_ray(C, mk(0.0, 0.0, 0.0), nrm(mat3v(C->Kc_inv, mk(fx, fy, 1.0))), pix, s, L, rec);
 }
 
 static void rctx_make(rctx *C, const dscene *S, const double *albedo, const double *rough, int Ht, int Wt,
@@ -1003,6 +1021,7 @@ static void rctx_make(rctx *C, const dscene *S, const double *albedo, const doub
     C->S = S; C->albedo = albedo; C->rough = rough; C->Ht = Ht; C->Wt = Wt;
     C->metal = NULL; C->nmap = NULL;
     C->Ep = Ep; C->Hp = Vw->Hp; C->Wp = Vw->Wp;
+    memcpy(C->Kc, Vw->Kc, sizeof C->Kc);
     inv3(Vw->Kc, C->Kc_inv);
     memcpy(C->Kp, Vw->Kp, sizeof C->Kp);
     memcpy(C->Rp, Vw->Rp, sizeof C->Rp);
@@ -1288,6 +1307,353 @@ int or_gbuffer(const float *verts, const int32_t *tris, int32_t T, const float *
         g[6] = t;
         g[7] = 1.0;
     }
+    scene_free(&S);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Camera-pose gradient.  Sec. 3.2 counts the camera pose (Rc, tc) among the  */
+/* scene parameters theta of Eq. 9.                                           */
+/* ------------------------------------------------------------------------- */
+/*
+ * Renders keep the camera at the origin, so a pose parameter moves the whole
+ * scene (mesh and projector) rigidly in the camera frame: a point y moves
+ * with velocity a x y + b (a "twist" (a, b) per parameter).  The pixel mean
+ * of Eq. 4 is I_P = integral over pixel P's unit square of the radiance
+ * L(u) that reaches image point u.  Written as an integral over the visible
+ * surface, the integrand L(x) J(x) (J = image area per unit surface area)
+ * travels with the surface, and so do the shadow edges and the projector
+ * frustum's border on it: relative to the scene only the camera moves.
+ * Differentiating each visible region's integral as its boundary moves
+ * (Reynolds transport) leaves three terms, g_P = dLoss/dEc_P:
+ *   interior    sum over camera samples of d/dtheta of the sample's
+ *               contribution with its first hit held on the surface and the
+ *               sampled directions held fixed: the BRDF at the first vertex
+ *               through its direction wo to the camera, plus the whole
+ *               contribution times d log J / dtheta (divided by spp);
+ *   pixel edges over every edge between pixels P and Q (normal n from P to
+ *               Q; outside the image g = 0), integral of L (V.n) (g_Q - g_P),
+ *               V the image velocity of the surface point seen there;
+ *   silhouettes where a nearer surface F hides a farther one B, B's visible
+ *               part ends at F's edge, which moves with F: integral over the
+ *               silhouette of g_P L_B (V_F - V_B).n_BF.
+ * Every derivative of a smooth quantity here (the BRDF along wo, log J, the
+ * image velocity, the silhouette's image speed) is taken by central
+ * differences in FP64; only the split into the three terms is analytic.
+ */
+static void pose_proj(const double *Kc, d3 y, double s[2])
+{
+    d3 q = mat3v(Kc, y);
+    s[0] = q.x / q.z;
+    s[1] = q.y / q.z;
+}
+
+static d3 pose_vel(const double *tw, d3 y) { return add(cross(mk(tw[0], tw[1], tw[2]), y), mk(tw[3], tw[4], tw[5])); }
+
+/* image velocity of the scene point y under twist tw */
+static void pose_img_vel(const double *Kc, const double *tw, d3 y, double V[2])
+{
+    const double h = 1e-5;
+    double sp[2], sm[2];
+    d3 v = pose_vel(tw, y);
+    pose_proj(Kc, add(y, scl(v, h)), sp);
+    pose_proj(Kc, sub(y, scl(v, h)), sm);
+    V[0] = (sp[0] - sm[0]) / (2.0 * h);
+    V[1] = (sp[1] - sm[1]) / (2.0 * h);
+}
+
+/* log of the image area per unit surface area at x (normal n), the scene
+ * moved by th along twist tw: the square of half-side e around x in the
+ * surface's plane maps to a quadrilateral (lines stay lines), whose area
+ * over the square's is J averaged over the square, J(x) + O(e^2) */
+static double pose_logJ(const double *Kc, const double *tw, d3 x, d3 n, double th)
+{
+    d3 t1, t2;
+    onb(n, &t1, &t2);
+    const double e = 1e-3 * len(x);
+    const double sg[4][2] = {{1, 1}, {-1, 1}, {-1, -1}, {1, -1}};
+    d3 c[4];
+    double s[4][2], s0[2];
+    for (int i = 0; i < 4; ++i) {
+        d3 p = add(x, add(scl(t1, e * sg[i][0]), scl(t2, e * sg[i][1])));
+        c[i] = add(p, scl(pose_vel(tw, p), th));
+    }
+    d3 xc = add(x, scl(pose_vel(tw, x), th));
+    pose_proj(Kc, xc, s0);
+    for (int i = 0; i < 4; ++i) {
+        pose_proj(Kc, c[i], s[i]);
+        s[i][0] -= s0[0];
+        s[i][1] -= s0[1];
+    }
+    double img = 0.0;
+    for (int i = 0; i < 4; ++i) img += s[i][0] * s[(i + 1) % 4][1] - s[(i + 1) % 4][0] * s[i][1];
+    img = 0.5 * fabs(img);
+    double surf = 0.5 * len(cross(sub(c[0], c[2]), sub(c[1], c[3])));
+    return log(img / surf);
+}
+
+static double pose_dlogJ(const double *Kc, const double *tw, d3 x, d3 n)
+{
+    const double h = 1e-5;
+    return (pose_logJ(Kc, tw, x, n, h) - pose_logJ(Kc, tw, x, n, -h)) / (2.0 * h);
+}
+
+/* directional derivative of the BRDF value f(wo, w) along dwo (tangent to wo) */
+static void pose_df(const vrec *R, d3 wo, d3 dwo, d3 w, const or_params *P, double df[3])
+{
+    const double h = 1e-6;
+    pbr_f fp, fm;
+    pbr_eval(R->ns, nrm(add(wo, scl(dwo, h))), w, R->rho, R->r, R->m, P->ks, P->f0, &fp);
+    pbr_eval(R->ns, nrm(sub(wo, scl(dwo, h))), w, R->rho, R->r, R->m, P->ks, P->f0, &fm);
+    for (int j = 0; j < 3; ++j) df[j] = (fp.f[j] - fm.f[j]) / (2.0 * h);
+}
+
+/* interior term of one path for twist tw, g = dLoss/dEc of its pixel / spp */
+static double pose_interior(const rctx *C, const vrec *rec, int nv, const double *tw, const double g[3])
+{
+    const vrec *R = &rec[0];
+    double rest[3] = {0, 0, 0}, restU[3] = {0, 0, 0};
+    for (int v = 1; v < nv; ++v)
+        for (int j = 0; j < 3; ++j) {
+            rest[j] += rec[v].c[j];
+            if (rec[v].unclipped[j]) restU[j] += rec[v].c[j];
+        }
+    d3 x = R->x, wo = R->wo, b = mk(tw[3], tw[4], tw[5]);
+    /* relative to the scene the camera centre moves by -b: wo turns by
+     * -(b - wo (wo.b)) / |x| */
+    d3 dwo = scl(sub(b, scl(wo, dot(wo, b))), -1.0 / len(x));
+    double term = 0.0, df[3];
+    if (R->nee) {
+        pose_df(R, wo, dwo, R->wp, C->P, df);
+        for (int j = 0; j < 3; ++j)
+            if (R->unclipped[j]) term += g[j] * df[j] * R->Ep[j] * R->G; /* throughput 1 at the first vertex */
+    }
+    if (R->cont) {
+        pose_df(R, wo, dwo, R->wi, C->P, df);
+        for (int j = 0; j < 3; ++j)
+            if (R->fi.f[j] > 0.0) term += g[j] * restU[j] * df[j] / R->fi.f[j];
+    }
+    const double dlj = pose_dlogJ(C->Kc, tw, x, R->N);
+    for (int j = 0; j < 3; ++j) term += g[j] * (R->c[j] + rest[j]) * dlj;
+    return term;
+}
+
+typedef struct { int32_t v0, v1, third[2], nthird; } pose_edge;
+
+static int pose_edge_cmp(const void *pa, const void *pb)
+{
+    const int32_t *a = (const int32_t *)pa, *b = (const int32_t *)pb;
+    for (int k = 0; k < 3; ++k)
+        if (a[k] != b[k]) return a[k] < b[k] ? -1 : 1;
+    return 0;
+}
+
+/* the mesh's edges in increasing (lower vertex, higher vertex) order, each
+ * with the third vertices of its triangles (nthird > 2: non-manifold) */
+static int64_t pose_edges(const int32_t *tris, int32_t T, pose_edge **out)
+{
+    int32_t *h = (int32_t *)malloc(sizeof(int32_t) * 9 * (size_t)(T > 0 ? T : 1));
+    for (int32_t i = 0; i < T; ++i)
+        for (int k = 0; k < 3; ++k) {
+            int32_t a = tris[3 * i + k], b = tris[3 * i + (k + 1) % 3], c = tris[3 * i + (k + 2) % 3];
+            int32_t *r = h + 3 * (3 * (int64_t)i + k);
+            r[0] = a < b ? a : b;
+            r[1] = a < b ? b : a;
+            r[2] = c;
+        }
+    qsort(h, (size_t)3 * T, 3 * sizeof(int32_t), pose_edge_cmp);
+    pose_edge *E = (pose_edge *)malloc(sizeof(pose_edge) * 3 * (size_t)(T > 0 ? T : 1));
+    int64_t n = 0;
+    for (int64_t i = 0; i < 3 * (int64_t)T; ++i) {
+        const int32_t *r = h + 3 * i;
+        if (n == 0 || E[n - 1].v0 != r[0] || E[n - 1].v1 != r[1]) {
+            E[n].v0 = r[0]; E[n].v1 = r[1]; E[n].nthird = 0;
+            ++n;
+        }
+        pose_edge *e = &E[n - 1];
+        if (e->nthird < 2) e->third[e->nthird] = r[2];
+        e->nthird++;
+    }
+    free(h);
+    *out = E;
+    return n;
+}
+
+static d3 vert_at(const float *verts, int32_t i) { return mk(verts[3 * i], verts[3 * i + 1], verts[3 * i + 2]); }
+
+/*
+ * Gradient of a loss with dLoss/dEc = dEc (Hc x Wc x 3) with respect to n_tw
+ * pose parameters, each given as the twist tw[6k..6k+5] = (a, b) of the
+ * scene's motion in the camera frame.  out (3 x n_tw) receives the interior,
+ * pixel-edge and silhouette terms; their sum is the gradient.  Random
+ * numbers: camera samples as the render; the pixel-edge sample j of edge e
+ * (vertical edges x = 0..Wc of row y first, e = y (Wc + 1) + x; then the
+ * horizontal ones, e = (Wc + 1) Hc + y Wc + x) uses counter
+ * (Hc Wc + e, j, vertex, 0) and places itself at (j + u0) / edge_spp along
+ * the edge; silhouette sample j of mesh edge k (pose_edges order) uses
+ * (Hc Wc + n_pixel_edges + k, j, vertex, 0) and sits at (j + u0) / sil_spp
+ * from the lower-numbered vertex.  Non-manifold edges are skipped.
+ * Returns 0, or -1 on bad arguments.
+ */
+int or_pose_backward(const float *verts, const int32_t *tris, int32_t T, const float *uv, const double *albedo,
+                     const double *rough, int32_t Ht, int32_t Wt, const double *Ip, const or_view *Vw,
+                     const or_params *P, int32_t spp, int32_t bounces, uint64_t seed, const double *dEc, int32_t n_tw,
+                     const double *tw, int32_t edge_spp, int32_t sil_spp, double *out, int32_t nthreads)
+{
+    if (spp <= 0 || bounces < 1 || bounces > OR_MAX_VERTS || Ht <= 0 || Wt <= 0 || Vw->Hp <= 0 || Vw->Wp <= 0 ||
+        n_tw < 1 || n_tw > 16 || edge_spp < 0 || sil_spp < 0)
+        return -1;
+    set_threads(nthreads);
+    dscene S;
+    scene_make(&S, verts, tris, T, uv);
+    int64_t ntex = (int64_t)Vw->Hp * Vw->Wp;
+    double *Ep = (double *)malloc(sizeof(double) * 3 * (size_t)ntex);
+    or_prf(Ip, ntex, P, Ep);
+    rctx C;
+    rctx_make(&C, &S, albedo, rough, Ht, Wt, Ep, Vw, P, spp, bounces, seed);
+    const int32_t Hc = Vw->Hc, Wc = Vw->Wc;
+    const int64_t npix = (int64_t)Hc * Wc;
+    const int64_t nev = (int64_t)(Wc + 1) * Hc, neh = (int64_t)Wc * (Hc + 1);
+    double acc[3][16];
+    memset(acc, 0, sizeof acc);
+
+    /* interior */
+#pragma omp parallel
+    {
+        double loc[16] = {0};
+        vrec rec[OR_MAX_VERTS];
+#pragma omp for schedule(dynamic, 4)
+        for (int64_t p = 0; p < npix; ++p) {
+            double g[3];
+            for (int j = 0; j < 3; ++j) g[j] = dEc[3 * p + j] / spp;
+            if (g[0] == 0.0 && g[1] == 0.0 && g[2] == 0.0) continue;
+            for (int s = 0; s < spp; ++s) {
+                double L[3];
+                int nv = trace_sample(&C, (uint32_t)p, (uint32_t)s, L, rec);
+                if (nv == 0) continue;
+                for (int k = 0; k < n_tw; ++k) loc[k] += pose_interior(&C, rec, nv, tw + 6 * k, g);
+            }
+        }
+#pragma omp critical
+        for (int k = 0; k < n_tw; ++k) acc[0][k] += loc[k];
+    }
+
+    /* pixel edges */
+    if (edge_spp > 0) {
+#pragma omp parallel
+        {
+            double loc[16] = {0};
+            vrec rec[OR_MAX_VERTS];
+#pragma omp for schedule(dynamic, 16)
+            for (int64_t e = 0; e < nev + neh; ++e) {
+                const int vert = e < nev;
+                int64_t x, y, pP, pQ;
+                if (vert) {
+                    x = e % (Wc + 1); y = e / (Wc + 1);
+                    pP = x > 0 ? y * Wc + x - 1 : -1;
+                    pQ = x < Wc ? y * Wc + x : -1;
+                } else {
+                    int64_t f = e - nev;
+                    x = f % Wc; y = f / Wc;
+                    pP = y > 0 ? (y - 1) * Wc + x : -1;
+                    pQ = y < Hc ? y * Wc + x : -1;
+                }
+                double dg[3];
+                for (int j = 0; j < 3; ++j) dg[j] = (pQ >= 0 ? dEc[3 * pQ + j] : 0.0) - (pP >= 0 ? dEc[3 * pP + j] : 0.0);
+                if (dg[0] == 0.0 && dg[1] == 0.0 && dg[2] == 0.0) continue;
+                const uint32_t vpix = (uint32_t)(npix + e);
+                for (int j = 0; j < edge_spp; ++j) {
+                    double u[4], L[3];
+                    rand4(seed, vpix, (uint32_t)j, 0u, u);
+                    double t = ((double)j + u[0]) / edge_spp;
+                    double sx = vert ? (double)x : (double)x + t, sy = vert ? (double)y + t : (double)y;
+                    d3 d = nrm(mat3v(C.Kc_inv, mk(sx, sy, 1.0)));
+                    int nv = trace_ray(&C, mk(0.0, 0.0, 0.0), d, vpix, (uint32_t)j, L, rec);
+                    if (nv == 0) continue;
+                    double gl = L[0] * dg[0] + L[1] * dg[1] + L[2] * dg[2];
+                    for (int k = 0; k < n_tw; ++k) {
+                        double V[2];
+                        pose_img_vel(C.Kc, tw + 6 * k, rec[0].x, V);
+                        loc[k] += gl * (vert ? V[0] : V[1]) / edge_spp;
+                    }
+                }
+            }
+#pragma omp critical
+            for (int k = 0; k < n_tw; ++k) acc[1][k] += loc[k];
+        }
+    }
+
+    /* silhouettes */
+    if (sil_spp > 0 && T > 0) {
+        pose_edge *E;
+        int64_t ne = pose_edges(tris, T, &E);
+        const int64_t vbase = npix + nev + neh;
+#pragma omp parallel
+        {
+            double loc[16] = {0};
+            vrec rec[OR_MAX_VERTS];
+#pragma omp for schedule(dynamic, 16)
+            for (int64_t k = 0; k < ne; ++k) {
+                const pose_edge *ed = &E[k];
+                if (ed->nthird > 2) continue;
+                d3 P0 = vert_at(verts, ed->v0), P1 = vert_at(verts, ed->v1);
+                d3 m = cross(P0, P1);
+                /* a silhouette when every adjacent triangle lies on one side
+                 * of the plane through the camera centre and the edge */
+                int sgn = 0, ok = 1;
+                for (int i = 0; i < ed->nthird; ++i) {
+                    double sd = dot(m, vert_at(verts, ed->third[i]));
+                    int si = sd > 0.0 ? 1 : (sd < 0.0 ? -1 : 0);
+                    if (si == 0 || (sgn != 0 && si != sgn)) ok = 0;
+                    sgn = si;
+                }
+                if (!ok) continue;
+                d3 P2 = vert_at(verts, ed->third[0]);
+                const uint32_t vpix = (uint32_t)(vbase + k);
+                for (int j = 0; j < sil_spp; ++j) {
+                    double u[4], L[3], s[2];
+                    rand4(seed, vpix, (uint32_t)j, 0u, u);
+                    double t = ((double)j + u[0]) / sil_spp;
+                    d3 p = add(P0, scl(sub(P1, P0), t));
+                    if (!(p.z > 0.0)) continue;
+                    pose_proj(C.Kc, p, s);
+                    if (!(s[0] >= 0.0 && s[0] < Wc && s[1] >= 0.0 && s[1] < Hc)) continue;
+                    double dist = len(p);
+                    d3 d = scl(p, 1.0 / dist);
+                    if (occluded(&S, mk(0.0, 0.0, 0.0), d, dist * (1.0 - 1e-4))) continue;
+                    int nv = trace_ray(&C, scl(d, dist * (1.0 + 1e-4)), d, vpix, (uint32_t)j, L, rec);
+                    if (nv == 0) continue;
+                    int64_t px = (int64_t)floor(s[1]) * Wc + (int64_t)floor(s[0]);
+                    double gl = L[0] * dEc[3 * px] + L[1] * dEc[3 * px + 1] + L[2] * dEc[3 * px + 2];
+                    if (gl == 0.0) continue;
+                    /* the silhouette's image tangent and speed, and its normal
+                     * turned towards F (a point just inside F's triangle) */
+                    const double dl = 1e-6;
+                    double sp[2], sm[2], sq[2];
+                    pose_proj(C.Kc, add(p, scl(sub(P1, P0), dl)), sp);
+                    pose_proj(C.Kc, sub(p, scl(sub(P1, P0), dl)), sm);
+                    double tx = sp[0] - sm[0], ty = sp[1] - sm[1];
+                    double tl = sqrt(tx * tx + ty * ty);
+                    double speed = tl / (2.0 * dl);
+                    double nx = -ty / tl, ny = tx / tl;
+                    pose_proj(C.Kc, add(p, scl(sub(P2, p), 1e-6)), sq);
+                    if (nx * (sq[0] - s[0]) + ny * (sq[1] - s[1]) < 0.0) { nx = -nx; ny = -ny; }
+                    for (int q = 0; q < n_tw; ++q) {
+                        double Vf[2], Vb[2];
+                        pose_img_vel(C.Kc, tw + 6 * q, p, Vf);
+                        pose_img_vel(C.Kc, tw + 6 * q, rec[0].x, Vb);
+                        loc[q] += gl * ((Vf[0] - Vb[0]) * nx + (Vf[1] - Vb[1]) * ny) * speed / sil_spp;
+                    }
+                }
+            }
+#pragma omp critical
+            for (int q = 0; q < n_tw; ++q) acc[2][q] += loc[q];
+        }
+        free(E);
+    }
+    for (int r = 0; r < 3; ++r)
+        for (int k = 0; k < n_tw; ++k) out[r * n_tw + k] = acc[r][k];
+    free(Ep);
     scene_free(&S);
     return 0;
 }

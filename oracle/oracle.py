@@ -66,6 +66,7 @@ def load():
                                      P, P, P, P, P]
         _lib.or_render_m.restype = ctypes.c_int
         _lib.or_render_backward_m.restype = ctypes.c_int
+        _lib.or_pose_backward.restype = ctypes.c_int
         _lib.or_gbuffer.restype = ctypes.c_int
         _lib.or_num_threads.restype = ctypes.c_int
         _lib.or_num_threads.argtypes = [ctypes.c_int]
@@ -308,6 +309,41 @@ def render_backward(sc, dIc, pixels=None, *, albedo=None, rough=None, Ip=None, p
     if dN is not None:
         out["dnormal"] = dN
     return out
+
+
+def crf_grad(Ec, params):
+    """dIc/dEc of Eq. 5, Ic_j = (Gc w_j Ec_j)^gamma_c,j (0 where Gc w_j Ec_j <= 0),
+    per pixel and channel; Ec is (..., 3)."""
+    Ec = np.asarray(Ec, np.float64)
+    gam = np.asarray(params.gamma_c, np.float64)
+    a = float(params.gain_c) * np.asarray(params.wb, np.float64)
+    x = a * Ec
+    return np.where(x > 0.0, gam * a * np.power(np.maximum(x, 1e-300), gam - 1.0), 0.0)
+
+
+def pose_backward(sc, dEc, twists, edge_spp, sil_spp, *, albedo=None, rough=None, Ip=None, params=None, spp=None,
+                  bounces=None, seed=None, nthreads: int = 0, accel: bool = False):
+    """FP64 gradient of a loss with dLoss/dEc = ``dEc`` (Hc, Wc, 3) with
+    respect to camera-pose parameters, each given by the twist (a, b) of the
+    scene's motion in the camera frame (a point y moves with a x y + b);
+    ``twists`` is (K, 6).  Returns (3, K): the interior, pixel-edge and
+    silhouette terms (their sum is the gradient).  Plain material only."""
+    verts, tris, uv, albedo, rough, Ip = _scene_args(sc, albedo, rough, Ip)
+    P = make_params(params or sc.params)
+    V = make_view(sc)
+    dEc = _c(dEc, np.float64).reshape(sc.Hc * sc.Wc, 3)
+    tw = _c(twists, np.float64).reshape(-1, 6)
+    out = np.zeros(3 * len(tw))
+    with _Accel(accel):
+        rc = load().or_pose_backward(
+            _p(verts), _p(tris), ctypes.c_int32(len(tris)), _p(uv), _p(albedo), _p(rough),
+            ctypes.c_int32(albedo.shape[0]), ctypes.c_int32(albedo.shape[1]), _p(Ip), ctypes.byref(V), ctypes.byref(P),
+            ctypes.c_int32(spp or sc.spp), ctypes.c_int32(sc.bounces if bounces is None else bounces),
+            ctypes.c_uint64(sc.seed if seed is None else seed), _p(dEc), ctypes.c_int32(len(tw)), _p(tw),
+            ctypes.c_int32(edge_spp), ctypes.c_int32(sil_spp), _p(out), ctypes.c_int32(nthreads))
+    if rc != 0:
+        raise ValueError("oracle pose_backward: invalid arguments")
+    return out.reshape(3, len(tw))
 
 
 def adam_step(p, g, m, v, step, lr=1e-2, b1=0.9, b2=0.999, eps=1e-8, lo=0.0, hi=1.0):

@@ -42,6 +42,35 @@ def pose_of(xi, R0=None, t0=None):
     return rotation(xi[:3]) @ R0, t0 + xi[3:]
 
 
+def left_jacobian(omega) -> np.ndarray:
+    """J with d/ds exp([omega + s e]x) = [J e]x exp([omega]x) at s = 0 (the
+    left Jacobian of the rotation-vector map)."""
+    w = np.asarray(omega, np.float64).reshape(3)
+    th = float(np.linalg.norm(w))
+    K = np.array([[0.0, -w[2], w[1]], [w[2], 0.0, -w[0]], [-w[1], w[0], 0.0]])
+    if th < 1e-5:  # series: 1/2 - th^2/24 and 1/6 - th^2/120
+        return np.eye(3) + (0.5 - th * th / 24.0) * K + (1.0 / 6.0 - th * th / 120.0) * (K @ K)
+    return np.eye(3) + ((1.0 - math.cos(th)) / (th * th)) * K + ((th - math.sin(th)) / (th ** 3)) * (K @ K)
+
+
+def twists(xi, R0=None, t0=None) -> np.ndarray:
+    """(6, 6): for each pose parameter, the motion (a, b) of the posed scene
+    in the camera frame at pose xi, a point y moving with a x y + b.  The
+    scene sits at y = exp([omega]x) R0 x + t0 + delta: rotation parameter k
+    turns it about t = t0 + delta with a = J(omega) e_k (b = -a x t);
+    translation parameter k moves it with a = 0, b = e_k."""
+    xi = np.asarray(xi, np.float64).reshape(6)
+    t = (np.zeros(3) if t0 is None else np.asarray(t0, np.float64)) + xi[3:]
+    J = left_jacobian(xi[:3])
+    out = np.zeros((6, 6))
+    for k in range(3):
+        a = J[:, k]
+        out[k, :3] = a
+        out[k, 3:] = -np.cross(a, t)
+        out[3 + k, 3 + k] = 1.0
+    return out
+
+
 def posed_extrinsics(Rp, tp, R, t):
     """Projector extrinsics seen from a camera at pose (R, t): (Rp R^T, tp - Rp R^T t)."""
     Rp2 = np.asarray(Rp, np.float64).reshape(3, 3) @ np.asarray(R, np.float64).T
