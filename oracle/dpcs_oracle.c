@@ -1331,9 +1331,14 @@ int or_gbuffer(const float *verts, const int32_t *tris, int32_t T, const float *
  *               sampled directions held fixed: the BRDF at the first vertex
  *               through its direction wo to the camera, plus the whole
  *               contribution times d log J / dtheta (divided by spp);
- *   pixel edges over every edge between pixels P and Q (normal n from P to
- *               Q; outside the image g = 0), integral of L (V.n) (g_Q - g_P),
- *               V the image velocity of the surface point seen there;
+ *   pixel edges for every pixel P, -g_P times the flux out of its square,
+ *               the integral over its four edges of L (V.n), n the outward
+ *               normal and V the image velocity of the surface point seen
+ *               there (the same sum, edge by edge, as L (V.n) (g_Q - g_P)
+ *               over the edges between pixels P and Q, g = 0 outside the
+ *               image, but estimated pixel by pixel: the four edges' paths
+ *               share their random numbers, so opposite edges give a
+ *               common-random-number difference across the pixel);
  *   silhouettes where a nearer surface F hides a farther one B, B's visible
  *               part ends at F's edge, which moves with F: integral over the
  *               silhouette of g_P L_B (V_F - V_B).n_BF.
@@ -1486,13 +1491,13 @@ static d3 vert_at(const float *verts, int32_t i) { return mk(verts[3 * i], verts
  * pose parameters, each given as the twist tw[6k..6k+5] = (a, b) of the
  * scene's motion in the camera frame.  out (3 x n_tw) receives the interior,
  * pixel-edge and silhouette terms; their sum is the gradient.  Random
- * numbers: camera samples as the render; the pixel-edge sample j of edge e
- * (vertical edges x = 0..Wc of row y first, e = y (Wc + 1) + x; then the
- * horizontal ones, e = (Wc + 1) Hc + y Wc + x) uses counter
- * (Hc Wc + e, j, vertex, 0) and places itself at (j + u0) / edge_spp along
- * the edge; silhouette sample j of mesh edge k (pose_edges order) uses
- * (Hc Wc + n_pixel_edges + k, j, vertex, 0) and sits at (j + u0) / sil_spp
- * from the lower-numbered vertex.  Non-manifold edges are skipped.
+ * numbers: camera samples as the render; pixel-edge sample j of pixel p
+ * (x0, y0) uses counter (Hc Wc + p, j, vertex, 0) for all four of its paths,
+ * which start at (x0 + 1, y0 + t), (x0, y0 + t), (x0 + t, y0 + 1) and
+ * (x0 + t, y0), t = (j + u0) / edge_spp; silhouette sample j of mesh edge k
+ * (pose_edges order) uses (2 Hc Wc + k, j, vertex, 0) and sits at
+ * (j + u0) / sil_spp from the lower-numbered vertex.  Non-manifold edges are
+ * skipped.
  * Returns 0, or -1 on bad arguments.
  */
 int or_pose_backward(const float *verts, const int32_t *tris, int32_t T, const float *uv, const double *albedo,
@@ -1513,7 +1518,6 @@ int or_pose_backward(const float *verts, const int32_t *tris, int32_t T, const f
     rctx_make(&C, &S, albedo, rough, Ht, Wt, Ep, Vw, P, spp, bounces, seed);
     const int32_t Hc = Vw->Hc, Wc = Vw->Wc;
     const int64_t npix = (int64_t)Hc * Wc;
-    const int64_t nev = (int64_t)(Wc + 1) * Hc, neh = (int64_t)Wc * (Hc + 1);
     double acc[3][16];
     memset(acc, 0, sizeof acc);
 
@@ -1538,48 +1542,43 @@ int or_pose_backward(const float *verts, const int32_t *tris, int32_t T, const f
         for (int k = 0; k < n_tw; ++k) acc[0][k] += loc[k];
     }
 
-    /* pixel edges */
+    /* pixel edges: -g_P times the flux out through P's right, left, bottom
+     * and top edges (outward normals +x, -x, +y, -y) */
     if (edge_spp > 0) {
 #pragma omp parallel
         {
             double loc[16] = {0};
             vrec rec[OR_MAX_VERTS];
 #pragma omp for schedule(dynamic, 16)
-            for (int64_t e = 0; e < nev + neh; ++e) {
-                const int vert = e < nev;
-                int64_t x, y, pP, pQ;
-                if (vert) {
-                    x = e % (Wc + 1); y = e / (Wc + 1);
-                    pP = x > 0 ? y * Wc + x - 1 : -1;
-                    pQ = x < Wc ? y * Wc + x : -1;
-                } else {
-                    int64_t f = e - nev;
-                    x = f % Wc; y = f / Wc;
-                    pP = y > 0 ? (y - 1) * Wc + x : -1;
-                    pQ = y < Hc ? y * Wc + x : -1;
-                }
-                double dg[3];
-                for (int j = 0; j < 3; ++j) dg[j] = (pQ >= 0 ? dEc[3 * pQ + j] : 0.0) - (pP >= 0 ? dEc[3 * pP + j] : 0.0);
-                if (dg[0] == 0.0 && dg[1] == 0.0 && dg[2] == 0.0) continue;
-                const uint32_t vpix = (uint32_t)(npix + e);
+            for (int64_t p = 0; p < npix; ++p) {
+                const double *g = dEc + 3 * p;
+                if (g[0] == 0.0 && g[1] == 0.0 && g[2] == 0.0) continue;
+                const double x0 = (double)(p % Wc), y0 = (double)(p / Wc);
+                const uint32_t vpix = (uint32_t)(npix + p);
                 for (int j = 0; j < edge_spp; ++j) {
-                    double u[4], L[3];
+                    double u[4];
                     rand4(seed, vpix, (uint32_t)j, 0u, u);
-                    double t = ((double)j + u[0]) / edge_spp;
-                    double sx = vert ? (double)x : (double)x + t, sy = vert ? (double)y + t : (double)y;
-                    d3 d = nrm(mat3v(C.Kc_inv, mk(sx, sy, 1.0)));
-                    int nv = trace_ray(&C, mk(0.0, 0.0, 0.0), d, vpix, (uint32_t)j, L, rec);
-                    if (nv == 0) continue;
-                    double gl = L[0] * dg[0] + L[1] * dg[1] + L[2] * dg[2];
-                    for (int k = 0; k < n_tw; ++k) {
-                        double V[2];
-                        pose_img_vel(C.Kc, tw + 6 * k, rec[0].x, V);
-                        loc[k] += gl * (vert ? V[0] : V[1]) / edge_spp;
+                    const double t = ((double)j + u[0]) / edge_spp;
+                    const double ex[4] = {x0 + 1.0, x0, x0 + t, x0 + t};
+                    const double ey[4] = {y0 + t, y0 + t, y0 + 1.0, y0};
+                    const int axis[4] = {0, 0, 1, 1};
+                    const double sgn[4] = {1.0, -1.0, 1.0, -1.0};
+                    for (int k = 0; k < 4; ++k) {
+                        double L[3];
+                        d3 d = nrm(mat3v(C.Kc_inv, mk(ex[k], ey[k], 1.0)));
+                        int nv = trace_ray(&C, mk(0.0, 0.0, 0.0), d, vpix, (uint32_t)j, L, rec);
+                        if (nv == 0) continue;
+                        double gl = L[0] * g[0] + L[1] * g[1] + L[2] * g[2];
+                        for (int q = 0; q < n_tw; ++q) {
+                            double V[2];
+                            pose_img_vel(C.Kc, tw + 6 * q, rec[0].x, V);
+                            loc[q] -= sgn[k] * gl * V[axis[k]] / edge_spp;
+                        }
                     }
                 }
             }
 #pragma omp critical
-            for (int k = 0; k < n_tw; ++k) acc[1][k] += loc[k];
+            for (int q = 0; q < n_tw; ++q) acc[1][q] += loc[q];
         }
     }
 
@@ -1587,7 +1586,7 @@ int or_pose_backward(const float *verts, const int32_t *tris, int32_t T, const f
     if (sil_spp > 0 && T > 0) {
         pose_edge *E;
         int64_t ne = pose_edges(tris, T, &E);
-        const int64_t vbase = npix + nev + neh;
+        const int64_t vbase = 2 * npix;
 #pragma omp parallel
         {
             double loc[16] = {0};
