@@ -119,9 +119,10 @@ uint64_t dpcs_launch_count(const dpcs_ctx *ctx);
 /*
  * Kernel timing with CUDA events recorded on the launching stream around the
  * path-tracing kernels: kernel 0 = forward render (k_render), 1 = path replay
- * (k_replay).  dpcs_timing_enable(ctx, 1) clears and starts recording,
- * (ctx, 0) stops it.  dpcs_timing_read waits for the recorded events and
- * returns the summed duration in milliseconds and the number of launches.
+ * (k_replay), 2 = the pose-gradient kernels (dpcs_pose_backward).
+ * dpcs_timing_enable(ctx, 1) clears and starts recording, (ctx, 0) stops it.
+ * dpcs_timing_read waits for the recorded events and returns the summed
+ * duration in milliseconds and the number of launches.
  * Measurement support, not part of the paper's method.
  */
 dpcs_status dpcs_timing_enable(dpcs_ctx *ctx, int32_t on);
@@ -322,6 +323,48 @@ dpcs_status dpcs_render_backward(dpcs_ctx *ctx, dpcs_scene scene, const float *a
                                  const dpcs_params *params, int32_t spp, int32_t bounces, uint64_t seed,
                                  const float *Ec, const float *Ic, const float *dIc, float *dIp, float *dAlbedo,
                                  float *dRough, float *dParams, void *stream);
+
+/*
+ * Gradient with respect to the camera pose (Rc, tc), which Sec. 3.2 counts
+ * among the scene parameters theta of Eq. 9.  Renders keep the camera at the
+ * origin (Eq. 6), so a pose parameter moves the whole scene (mesh and
+ * projector) rigidly in the camera frame: a point y moves with velocity
+ * a x y + b, the twist (a, b) of that parameter.  The call returns, for a
+ * loss with dLoss/dIc = dIc, the six numbers W = dLoss/d(a, b); the
+ * derivative for a parameter with twist (a, b) is a . W[0..2] + b . W[3..5].
+ * It differentiates the box-filtered pixel means of Eq. 4 with their
+ * visibility changes, as three Monte Carlo terms:
+ *   interior     every camera sample of the render (same Philox counters):
+ *                its first vertex's BRDF as the direction to the camera
+ *                turns, and the path contribution times the change of the
+ *                pixel footprint's area on the surface;
+ *   pixel edges  per pixel, edge_spp points on each of its four edges,
+ *                the paths through them weighted by the pixel's dLoss/dEc
+ *                and the image velocity out of the pixel (the four paths of
+ *                a sample share their random numbers, so that opposite
+ *                edges give a low-variance difference across the pixel);
+ *   silhouettes  sil_spp points on each mesh edge that is a silhouette from
+ *                the camera, in view and inside the image, weighted by the
+ *                radiance of the surface behind it and the relative image
+ *                velocity of the two surfaces across the edge.
+ * Inputs are those of dpcs_render_backward (the scene at the pose where the
+ * gradient is wanted, i.e. after dpcs_scene_transform, with the matching
+ * view) plus
+ *  edge_spp : samples per pixel edge, 0..65536 (0 drops the term)
+ *  sil_spp  : samples per mesh edge, 0..65536 (0 drops the term)
+ * Output, ACCUMULATED (+=):
+ *  wrench   : dev, 18 float64: interior, pixel-edge and silhouette terms,
+ *             each (W_a[3], W_b[3]); their sum is W.
+ * The plain material only (no metallic or normal map).  Kc's last row must
+ * be (0, 0, k) with k > 0.  The first call with sil_spp > 0 on a scene builds
+ * its edge table on the host (one stream synchronisation); later calls,
+ * updates and transforms reuse it.  Results repeat bit for bit for the same
+ * inputs on the same device.
+ */
+dpcs_status dpcs_pose_backward(dpcs_ctx *ctx, dpcs_scene scene, const float *albedo, const float *rough, int32_t Ht,
+                               int32_t Wt, const float *Ip, const dpcs_view *view, const dpcs_params *params,
+                               int32_t spp, int32_t bounces, uint64_t seed, const float *Ec, const float *Ic,
+                               const float *dIc, int32_t edge_spp, int32_t sil_spp, double *wrench, void *stream);
 
 /* ------------------------------------------------------------------------ */
 /* Denoiser of Eq. 11: Ic' = D(Ic), a differentiable cross-bilateral filter  */

@@ -18,7 +18,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(HERE, "_build")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "lbvh.cu", "render.cu", "optim.cu", "serve.cu", "denoise.cu", "principled.cu", "wavefront.cu"]
+SOURCES = ["api.cu", "lbvh.cu", "render.cu", "optim.cu", "serve.cu", "denoise.cu", "principled.cu", "wavefront.cu",
+           "pose.cu"]
 # the measurement library (roof probes), used by the benchmark and its tests
 PROBE_SOURCES = ["probe.cu"]
 

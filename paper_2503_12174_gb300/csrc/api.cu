@@ -8,6 +8,7 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 #include <map>
 #include <string>
@@ -17,6 +18,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include "internal.h"
+#include "pose.h"
 
 using namespace dpcs;
 
@@ -39,6 +41,12 @@ struct TimedLaunch {
     int kernel = 0;
 };
 
+// mesh edges of one scene for the pose gradient's silhouette term
+struct EdgeTable {
+    PoseEdge *d = nullptr;
+    int64_t n = 0;
+};
+
 }  // namespace
 
 struct dpcs_ctx {
@@ -58,6 +66,8 @@ struct dpcs_ctx {
     Buf wf;  // wavefront render: lane sums, per-chunk path state, queues
     int32_t render_path = DPCS_PATH_MEGAKERNEL;
     int64_t wf_chunk = int64_t(1) << 20;
+    Buf pose;  // per-block partial sums of the pose-gradient kernels
+    std::map<uint64_t, EdgeTable> edges;  // per scene, built by its first pose-gradient call with silhouettes
     Buf kept;  // path records of the last dpcs_render_keep: 16-byte chunks (structure of arrays), then per-sample vertex counts
     struct {
         bool valid = false;
@@ -300,6 +310,84 @@ dpcs_status prepare(dpcs_ctx *c, dpcs_scene scene, const float *albedo, const fl
     return DPCS_OK;
 }
 
+// The scene's mesh edges for the pose gradient's silhouette term, built on
+// the host at the first call that needs them (the edges depend only on the
+// triangles' vertex indices, which updates and rigid transforms keep).  Each
+// triangle adds its three edges as (lower vertex, higher vertex, third
+// vertex); sorted, each run of equal (lower, higher) is one edge, numbered in
+// that order.  Synchronises the stream once.
+dpcs_status pose_edges(dpcs_ctx *c, dpcs_scene scene, const Scene &sc, cudaStream_t st, const EdgeTable **out) {
+    auto it = c->edges.find(scene);
+    if (it != c->edges.end()) {
+        *out = &it->second;
+        return DPCS_OK;
+    }
+    const int64_t T = sc.T;
+    std::vector<int32_t> vidx((size_t)(3 * T)), order((size_t)T), pos((size_t)T);
+    cudaError_t e = cudaMemcpyAsync(vidx.data(), sc.vidx, (size_t)T * 12, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(order.data(), sc.order, (size_t)T * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "pose edges: reading the mesh");
+    for (int64_t p = 0; p < T; ++p) {
+        if (order[p] < 0 || order[p] >= T) return fail(c, DPCS_ERR_DEVICE_CHECK, "pose edges: corrupt leaf order");
+        pos[order[p]] = (int32_t)p;
+    }
+    struct Half {
+        int32_t lo, hi, third, tri;
+        int8_t clo, chi, cth;
+    };
+    std::vector<Half> h((size_t)(3 * T));
+    for (int64_t i = 0; i < T; ++i)
+        for (int k = 0; k < 3; ++k) {
+            const int ka = k, kb = (k + 1) % 3, kc = (k + 2) % 3;
+            const int32_t va = vidx[3 * i + ka], vb = vidx[3 * i + kb];
+            Half &r = h[(size_t)(3 * i + k)];
+            const bool sw = vb < va;
+            r.lo = sw ? vb : va;
+            r.hi = sw ? va : vb;
+            r.clo = (int8_t)(sw ? kb : ka);
+            r.chi = (int8_t)(sw ? ka : kb);
+            r.third = vidx[3 * i + kc];
+            r.cth = (int8_t)kc;
+            r.tri = (int32_t)i;
+        }
+    std::sort(h.begin(), h.end(), [](const Half &x, const Half &y) {
+        if (x.lo != y.lo) return x.lo < y.lo;
+        if (x.hi != y.hi) return x.hi < y.hi;
+        return x.third < y.third;
+    });
+    std::vector<PoseEdge> E;
+    E.reserve(h.size());
+    for (size_t g = 0; g < h.size();) {
+        size_t g1 = g + 1;
+        while (g1 < h.size() && h[g1].lo == h[g].lo && h[g1].hi == h[g].hi) ++g1;
+        PoseEdge r = make_int4(-1, 0, -1, 0);
+        if (g1 - g <= 2) {
+            const Half &A = h[g];
+            r.x = pos[A.tri];
+            r.y = A.clo | (A.chi << 2) | (A.cth << 4);
+            if (g1 - g == 2) {
+                r.z = pos[h[g + 1].tri];
+                r.w = h[g + 1].cth;
+            }
+        }
+        E.push_back(r);
+        g = g1;
+    }
+    EdgeTable tab;
+    tab.n = (int64_t)E.size();
+    const size_t bytes = (size_t)(tab.n > 0 ? tab.n : 1) * sizeof(PoseEdge);
+    dpcs_status s = dev_alloc(c, (void **)&tab.d, bytes, "pose edges");
+    if (s) return s;
+    e = tab.n > 0 ? cudaMemcpy(tab.d, E.data(), (size_t)tab.n * sizeof(PoseEdge), cudaMemcpyHostToDevice) : cudaSuccess;
+    if (e != cudaSuccess) {
+        dev_free(c, tab.d, bytes);
+        return cuda_fail(c, e, "pose edges: upload");
+    }
+    *out = &(c->edges[scene] = tab);
+    return DPCS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -344,8 +432,9 @@ dpcs_status dpcs_destroy(dpcs_ctx *c) {
         cudaFree(s.uv);
         cudaFree(s.base);
     }
+    for (auto &kv : c->edges) cudaFree(kv.second.d);
     Buf *bufs[] = {&c->ep4, &c->tex4, &c->gE, &c->dEp4, &c->dtex4, &c->acc, &c->partial, &c->build, &c->upload, &c->pix,
-                   &c->kept, &c->mat4, &c->dmat4, &c->dEp64, &c->dtex64, &c->wf};
+                   &c->kept, &c->mat4, &c->dmat4, &c->dEp64, &c->dtex64, &c->wf, &c->pose};
     for (Buf *b : bufs)
         if (b->p) cudaFree(b->p);
     cudaFree(c->status);
@@ -539,6 +628,11 @@ dpcs_status dpcs_scene_free(dpcs_ctx *c, dpcs_scene scene) {
     dev_free(c, s.vidx, n * 12);
     dev_free(c, s.uv, (size_t)(s.V > 0 ? s.V : 1) * 8);
     dev_free(c, s.base, (size_t)(s.V > 0 ? s.V : 1) * 12);
+    auto et = c->edges.find(scene);
+    if (et != c->edges.end()) {
+        dev_free(c, et->second.d, (size_t)(et->second.n > 0 ? et->second.n : 1) * sizeof(PoseEdge));
+        c->edges.erase(et);
+    }
     c->scenes.erase(it);
     return DPCS_OK;
 }
@@ -1154,6 +1248,59 @@ dpcs_status dpcs_adam(dpcs_ctx *c, float *p, const float *g, float *m, float *v,
     if (s) return s;
     return check_launch(c, launch_adam(p, g, m, v, n, lr, beta1, beta2, eps, step, lo, hi, (cudaStream_t)stream),
                         "adam");
+}
+
+dpcs_status dpcs_pose_backward(dpcs_ctx *c, dpcs_scene scene, const float *albedo, const float *rough, int32_t Ht,
+                               int32_t Wt, const float *Ip, const dpcs_view *view, const dpcs_params *params,
+                               int32_t spp, int32_t bounces, uint64_t seed, const float *Ec, const float *Ic,
+                               const float *dIc, int32_t edge_spp, int32_t sil_spp, double *wrench, void *stream) {
+    Range range("dpcs_pose_backward");
+    RenderArgs a;
+    Scene *sc = nullptr;
+    dpcs_status s = prepare(c, scene, albedo, rough, Ht, Wt, Ip, view, params, spp, bounces, seed, a, &sc);
+    if (s) return s;
+    if (!Ec || !Ic || !dIc || !wrench) return fail(c, DPCS_ERR_INVALID_ARG, "null Ec, Ic, dIc or wrench");
+    if (edge_spp < 0 || sil_spp < 0 || edge_spp > (1 << 16) || sil_spp > (1 << 16))
+        return fail(c, DPCS_ERR_INVALID_ARG, "edge_spp and sil_spp must be in [0, 65536]");
+    if (view->Kc[6] != 0.0f || view->Kc[7] != 0.0f || !(view->Kc[8] > 0.0f))
+        return fail(c, DPCS_ERR_INVALID_ARG, "pose gradient: Kc's last row must be (0, 0, k), k > 0");
+    if ((s = set_device(c))) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t np = (int64_t)view->Hp * view->Wp, nt = (int64_t)Ht * Wt, npix = (int64_t)view->Hc * view->Wc;
+    const EdgeTable *tab = nullptr;
+    if (sil_spp > 0 && sc->T > 0 && (s = pose_edges(c, scene, *sc, st, &tab))) return s;
+    // the Philox counters of pixel-edge and silhouette samples follow the
+    // pixels': every one must fit in 32 bits
+    if (2 * npix + (tab ? tab->n : 0) > (int64_t)0xffffffffLL)
+        return fail(c, DPCS_ERR_INVALID_ARG, "pose gradient: too many pixels and edges for 32-bit counters");
+    const int gmax = pose_grid(c->device);
+    if (gmax <= 0) return fail(c, DPCS_ERR_CUDA, "pose gradient: no multiprocessor count");
+    if ((s = ensure(c, c->ep4, (size_t)np * 16, "Ep scratch")) ||
+        (s = ensure(c, c->tex4, (size_t)nt * 16, "texture scratch")) ||
+        (s = ensure(c, c->gE, (size_t)npix * 12, "dEc scratch")) ||
+        (s = ensure(c, c->acc, 16 * sizeof(double), "parameter accumulators")) ||
+        (s = ensure(c, c->pose, (size_t)3 * gmax * 6 * sizeof(double), "pose partial sums")))
+        return s;
+    int nl = launch_prf(Ip, np, params->gamma_p, params->gain_p, (float4 *)c->ep4.p, st);
+    nl += launch_pack_tex(albedo, rough, nt, (float4 *)c->tex4.p, st);
+    // dLoss/dEc through Eq. 5 (the response-parameter sums it also forms are not used)
+    nl += launch_crf_backward(dIc, Ec, Ic, npix, params->gamma_c, params->gain_c, params->wb, (float *)c->gE.p,
+                              (double *)c->acc.p, st);
+    a.Ep = (const float4 *)c->ep4.p;
+    a.tex = (const float4 *)c->tex4.p;
+    a.gE = (const float *)c->gE.p;
+    PoseArgs p;
+    memcpy(p.Kc, view->Kc, sizeof p.Kc);
+    p.edge_spp = edge_spp;
+    p.sil_spp = tab ? sil_spp : 0;
+    p.edges = tab ? tab->d : nullptr;
+    p.nedges = tab ? tab->n : 0;
+    p.partial = (double *)c->pose.p;
+    TimedLaunch *tl = timing_begin(c, 2, st);
+    const int np2 = launch_pose(a, p, c->device, wrench, st);
+    timing_end(tl, st);
+    if (np2 < 0) return check_launch(c, np2, "pose_backward");
+    return check_launch(c, nl + np2, "pose_backward");
 }
 
 }  // extern "C"

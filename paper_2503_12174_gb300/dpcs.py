@@ -41,7 +41,7 @@ EXPORTED = [
     "dpcs_l1_loss", "dpcs_tv_loss", "dpcs_scene_update", "dpcs_render_loss_backward", "dpcs_render_keep",
     "dpcs_render_backward_kept", "dpcs_render_principled", "dpcs_render_backward_principled",
     "dpcs_scene_transform", "dpcs_render_loss_backward_principled", "dpcs_render_keep_principled",
-    "dpcs_render_backward_kept_principled", "dpcs_set_grad_accum", "dpcs_set_render_path",
+    "dpcs_render_backward_kept_principled", "dpcs_set_grad_accum", "dpcs_set_render_path", "dpcs_pose_backward",
 ]
 
 DPCS_REQ_RELIGHT = 0
@@ -149,6 +149,10 @@ _SIGS = {
     "dpcs_render_backward": (ctypes.c_int32, [_P, ctypes.c_uint64, _P, _P, ctypes.c_int32, ctypes.c_int32, _P,
                                               ctypes.POINTER(DpcsView), ctypes.POINTER(DpcsParams), ctypes.c_int32,
                                               ctypes.c_int32, ctypes.c_uint64, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "dpcs_pose_backward": (ctypes.c_int32, [_P, ctypes.c_uint64, _P, _P, ctypes.c_int32, ctypes.c_int32, _P,
+                                            ctypes.POINTER(DpcsView), ctypes.POINTER(DpcsParams), ctypes.c_int32,
+                                            ctypes.c_int32, ctypes.c_uint64, _P, _P, _P, ctypes.c_int32,
+                                            ctypes.c_int32, _P, _P]),
     "dpcs_render_loss_backward": (ctypes.c_int32, [_P, ctypes.c_uint64, _P, _P, ctypes.c_int32, ctypes.c_int32, _P,
                                                    ctypes.POINTER(DpcsView), ctypes.POINTER(DpcsParams),
                                                    ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, _P, ctypes.c_int32,
@@ -342,6 +346,13 @@ def dpcs_render_backward(ctx, scene, albedo, rough, Ht, Wt, Ip, view, params, sp
     return load_library().dpcs_render_backward(ctx, scene, albedo, rough, Ht, Wt, Ip, ctypes.byref(view),
                                                ctypes.byref(params), spp, bounces, seed, Ec, Ic, dIc, dIp, dAlbedo,
                                                dRough, dParams, stream)
+
+
+def dpcs_pose_backward(ctx, scene, albedo, rough, Ht, Wt, Ip, view, params, spp, bounces, seed, Ec, Ic, dIc,
+                       edge_spp, sil_spp, wrench, stream):
+    return load_library().dpcs_pose_backward(ctx, scene, albedo, rough, Ht, Wt, Ip, ctypes.byref(view),
+                                             ctypes.byref(params), spp, bounces, seed, Ec, Ic, dIc, edge_spp, sil_spp,
+                                             wrench, stream)
 
 
 def dpcs_render_loss_backward(ctx, scene, albedo, rough, Ht, Wt, Ip, view, params, spp, bounces, seed, target,
@@ -611,6 +622,29 @@ class Context:
             _ptr(dRough, "dRough", (Ht, Wt), f32, self.device, allow_none=True),
             _ptr(dParams, "dParams", (11,), f32, self.device, allow_none=True), _stream(stream))
         self.check(st, "render_backward")
+
+    def pose_backward(self, scene: int, albedo, rough, Ip, view: DpcsView, params: DpcsParams, spp: int,
+                      bounces: int, seed: int, Ec, Ic, dIc, edge_spp: int, sil_spp: int, wrench=None, stream=None):
+        """dLoss/d(a, b) of a rigid motion of the scene in the camera frame
+        (``dpcs_pose_backward``): returns ``wrench`` (3, 6) float64 on the
+        device, the interior, pixel-edge and silhouette terms, ADDED to the
+        tensor passed in (zeros when none is)."""
+        import torch
+
+        Ht, Wt = albedo.shape[0], albedo.shape[1]
+        f32 = torch.float32
+        img = (view.Hc, view.Wc, 3)
+        if wrench is None:
+            wrench = torch.zeros((3, 6), dtype=torch.float64, device=self.device)
+        st = self.lib.dpcs_pose_backward(
+            self.handle, scene, _ptr(albedo, "albedo", (Ht, Wt, 3), f32, self.device),
+            _ptr(rough, "rough", (Ht, Wt), f32, self.device), Ht, Wt,
+            _ptr(Ip, "Ip", (view.Hp, view.Wp, 3), f32, self.device), ctypes.byref(view), ctypes.byref(params),
+            int(spp), int(bounces), int(seed) & (2**64 - 1), _ptr(Ec, "Ec", img, f32, self.device),
+            _ptr(Ic, "Ic", img, f32, self.device), _ptr(dIc, "dIc", img, f32, self.device), int(edge_spp),
+            int(sil_spp), _ptr(wrench, "wrench", (3, 6), torch.float64, self.device), _stream(stream))
+        self.check(st, "pose_backward")
+        return wrench
 
     # -- principled material (metallic and normal maps) --------------------------
     def _material(self, albedo, rough, metallic, normal):

@@ -9,8 +9,9 @@ principled material, metallic), and D the optional cross-bilateral
 denoiser of Eq. 11.  theta = albedo, roughness, gamma_p, gamma_c and the
 white balance w, plus the metallic map and the normal map Vn when they are
 given (the principled material of Sec. 3.2), and the camera pose Rc, tc
-when a starting pose is given (``pose.PoseRefine``: one central-difference
-Adam step on the pose after each step on the other parameters); the gains
+when a starting pose is given (``pose.PoseRefine``: one Adam step on the
+pose after each step on the other parameters, its gradient from the pose
+adjoint, or from central differences with the principled material); the gains
 Gp and Gc stay at their given constants (Sec. 3.2).  Each step renders
 every pair with a fresh Philox key, accumulates the path-replay gradients
 of all pairs, adds the total-variation gradient and takes one Adam step per
@@ -26,7 +27,8 @@ same routes (``render_loss_backward_principled``; with the denoiser, the
 principled render keeps its records).  Every step
 runs in the library's kernels; the only host traffic per step is reading
 back the 11 response parameters the next renders take by value (and, with
-the pose, the 13 K data terms of its differences).
+the pose, its data terms and its 18-number gradient, or the 13 K data terms
+of its differences).
 """
 from __future__ import annotations
 
@@ -45,7 +47,8 @@ class SceneFit:
     def __init__(self, ctx: dpcs.Context, scene: int, view: dpcs.DpcsView, params0: dpcs.DpcsParams, albedo0, rough0,
                  pairs, spp: int, bounces: int, lr_tex: float = 2e-2, lr_params: float = 1e-2, tv_weight: float = 0.0,
                  denoise: dpcs.DpcsDenoiseParams | None = None, fit_params: bool = True, seed: int = 0,
-                 fused: bool = True, metallic0=None, normal0=None, pose_xi0=None, pose_lr: float = 1e-3):
+                 fused: bool = True, metallic0=None, normal0=None, pose_xi0=None, pose_lr: float = 1e-3,
+                 pose_gradient: str | None = None, pose_edge_spp: int = 16):
         import torch
 
         self.ctx, self.scene, self.view = ctx, scene, view
@@ -91,7 +94,7 @@ class SceneFit:
 
             self.pose = PoseRefine(ctx, scene, view, params0, self.albedo, self.rough, self.pairs, spp, bounces,
                                    seed=seed + 7919, xi0=pose_xi0, lr=pose_lr, metallic=self.metallic,
-                                   normal=self.normal)
+                                   normal=self.normal, gradient=pose_gradient, edge_spp=pose_edge_spp)
             self.view = self.pose.apply(pose_xi0)
         # K data terms, TV(albedo), TV(rough) [, TV(metallic)]
         self.losses = torch.zeros(self.K + 2 + (self.metallic is not None), dtype=f32, device=dev)

@@ -7,13 +7,16 @@ mesh moves by ``dpcs_scene_transform`` and the projector extrinsics become
 Rp' = Rp Rc^T, tp' = tp - Rp' tc (``posed_view``).
 
 The pose is xi = (omega, delta) around a starting pose (R0, t0):
-Rc = exp([omega]x) R0 (Rodrigues), tc = t0 + delta.  Its gradient is taken
-by central differences with common random numbers: every evaluation renders
-with the same Philox keys, so the difference sees only the pose change.  Six
-parameters cost twelve renders per pair, and the differences include what
-the image does where silhouettes and shadow edges cross pixels -- the
-visibility terms that path replay with detached sampling (the adjoint of
-every other parameter) leaves out.
+Rc = exp([omega]x) R0 (Rodrigues), tc = t0 + delta.  Each pose parameter
+moves the posed scene with a twist (a, b) (``twists``).  Its gradient comes
+either from the adjoint (``dpcs_pose_backward``: dLoss/d(a, b) with the
+interior, pixel-edge and silhouette terms of the box-filtered pixel means,
+one call per pair, projected on the six twists) or from central differences
+with common random numbers (every evaluation renders with the same Philox
+keys; six parameters cost twelve renders per pair).  Both include what the
+image does where silhouettes cross pixels -- the visibility terms that path
+replay with detached sampling (the adjoint of every other parameter) leaves
+out.
 """
 from __future__ import annotations
 
@@ -97,21 +100,56 @@ def central_differences(loss, xi, h):
     return g
 
 
+def adjoint_key(seed: int) -> int:
+    """Philox key of the pose adjoint's paths for a render with key ``seed``:
+    the same low word, the high word moved by one, so that the two sets of
+    samples are independent."""
+    return (int(seed) + (1 << 32)) & (2**64 - 1)
+
+
+def project(wrench, tw) -> np.ndarray:
+    """Gradient of each pose parameter from dLoss/d(a, b): ``wrench`` is the
+    (3, 6) or (6,) output of ``dpcs_pose_backward`` (its terms are summed),
+    ``tw`` the (K, 6) twists of the parameters."""
+    w = np.asarray(wrench, np.float64)
+    w = w.reshape(-1, 6).sum(axis=0)
+    return np.asarray(tw, np.float64).reshape(-1, 6) @ w
+
+
 class PoseRefine:
     """Refines the camera pose against K projector/capture pairs by Adam on
-    the central-difference gradient of the Eq. 9 data term (the mean L1
-    error; the other scene parameters stay fixed).  ``pairs`` is a list of
-    (Ip, Ic) device tensors; ``metallic`` / ``normal`` select the principled
-    material.  Each step: twelve pose evaluations, each a scene transform,
-    K renders and K L1 terms, then one Adam step on xi."""
+    the gradient of the Eq. 9 data term (the mean L1 error; the other scene
+    parameters stay fixed).  ``pairs`` is a list of (Ip, Ic) device tensors;
+    ``metallic`` / ``normal`` select the principled material.
+
+    ``gradient="adjoint"`` (the plain material's default): each step moves
+    the scene to the pose, and per pair renders, takes the L1 term and calls
+    ``dpcs_pose_backward`` (``edge_spp`` and ``sil_spp`` samples per pixel
+    edge and per silhouette edge), then one Adam step on xi.  Its noise
+    falls with the pixel count: small images want more edge samples (64 at
+    48 x 48 pixels recovers the pose about as central differences do at
+    higher cost; 16 suffices at 256 x 256).
+    ``gradient="differences"`` (the principled material's only choice):
+    thirteen pose evaluations per step, each a scene transform, K renders and
+    K L1 terms, at xi and at xi +- h e_k."""
 
     def __init__(self, ctx: dpcs.Context, scene: int, view: dpcs.DpcsView, params: dpcs.DpcsParams, albedo, rough,
                  pairs, spp: int, bounces: int, seed: int = 0, xi0=None, R0=None, t0=None, h_rot: float = 1e-3,
-                 h_trans: float = 1e-3, lr: float = 1e-3, metallic=None, normal=None):
+                 h_trans: float = 1e-3, lr: float = 1e-3, metallic=None, normal=None, gradient: str | None = None,
+                 edge_spp: int = 16, sil_spp: int = 16):
         import torch
 
         self.ctx, self.scene, self.view, self.params = ctx, scene, view, params
         self.albedo, self.rough, self.metallic, self.normal = albedo, rough, metallic, normal
+        principled = metallic is not None or normal is not None
+        if gradient is None:
+            gradient = "differences" if principled else "adjoint"
+        if gradient not in ("adjoint", "differences"):
+            raise ValueError("gradient must be 'adjoint' or 'differences'")
+        if gradient == "adjoint" and principled:
+            raise ValueError("the pose adjoint covers the plain material only")
+        self.gradient = gradient
+        self.edge_spp, self.sil_spp = int(edge_spp), int(sil_spp)
         self.pairs = list(pairs)
         self.K = len(self.pairs)
         self.spp, self.bounces, self.seed = int(spp), int(bounces), int(seed)
@@ -126,7 +164,9 @@ class PoseRefine:
         self.m, self.v = torch.zeros(6, dtype=f32, device=dev), torch.zeros(6, dtype=f32, device=dev)
         img = (view.Hc, view.Wc, 3)
         self.Ic = torch.empty(img, dtype=f32, device=dev)
+        self.Ec = torch.empty(img, dtype=f32, device=dev)
         self.dIc = torch.empty(img, dtype=f32, device=dev)
+        self.wrench = torch.zeros((3, 6), dtype=torch.float64, device=dev)
         self.terms = torch.zeros((13, self.K), dtype=f32, device=dev)  # per evaluation and pair
         self.scale = 1.0 / (self.K * view.Hc * view.Wc * 3)
         self.k = 0
@@ -137,11 +177,14 @@ class PoseRefine:
         self.ctx.transform(self.scene, R, t)
         return posed_view(self.view, R, t)
 
+    def _key(self, i: int) -> int:
+        return self.seed + (self.k - 1) * self.K + i  # the same keys for every evaluation of a step
+
     def _evaluate(self, xi, row: int):
         c = self.ctx
         v = self.apply(xi)
         for i, (Ip, target) in enumerate(self.pairs):
-            s = self.seed + (self.k - 1) * self.K + i  # the same keys for every evaluation of a step
+            s = self._key(i)
             if self.metallic is not None or self.normal is not None:
                 c.render_principled(self.scene, self.albedo, self.rough, self.metallic, self.normal, Ip, v,
                                     self.params, self.spp, self.bounces, s, Ic=self.Ic)
@@ -150,24 +193,50 @@ class PoseRefine:
                          Ic=self.Ic)
             c.l1_loss(self.Ic, target, self.dIc, self.terms[row, i:i + 1], scale=self.scale)
 
+    def _adjoint(self, xi):
+        """Data term and its pose gradient at xi by dpcs_pose_backward.  The
+        adjoint traces its paths under another Philox key than the render
+        whose L1 residual it weights: with the render's own samples the
+        interior term (each sample's value times the change of its pixel
+        footprint) would correlate with sign(Ic - target) and carry a bias of
+        about the loss itself times the mean footprint change, which does
+        not vanish at the true pose."""
+        c = self.ctx
+        v = self.apply(xi)
+        self.wrench.zero_()
+        for i, (Ip, target) in enumerate(self.pairs):
+            s = self._key(i)
+            c.render(self.scene, self.albedo, self.rough, Ip, v, self.params, self.spp, self.bounces, s, Ic=self.Ic,
+                     Ec=self.Ec)
+            c.l1_loss(self.Ic, target, self.dIc, self.terms[12, i:i + 1], scale=self.scale)
+            c.pose_backward(self.scene, self.albedo, self.rough, Ip, v, self.params, self.spp, self.bounces,
+                            adjoint_key(s), self.Ec, self.Ic, self.dIc, self.edge_spp, self.sil_spp,
+                            wrench=self.wrench)
+        g = project(self.wrench.cpu().numpy(), twists(xi, self.R0, self.t0))
+        return float(self.terms[12].sum().cpu()), g
+
     def step(self) -> float:
         """One Adam step on the pose; returns the data term at the pose the step started from."""
         import torch
 
         self.k += 1
         xi = self.xi.cpu().numpy().astype(np.float64)
-        self._evaluate(xi, 12)
-        for k in range(6):
-            e = np.zeros(6)
-            e[k] = self.h[k]
-            self._evaluate(xi + e, 2 * k)
-            self._evaluate(xi - e, 2 * k + 1)
-        L = self.terms.sum(dim=1).cpu().numpy().astype(np.float64)
-        g = (L[0:12:2] - L[1:12:2]) / (2.0 * self.h)
+        if self.gradient == "adjoint":
+            L0, g = self._adjoint(xi)
+        else:
+            self._evaluate(xi, 12)
+            for k in range(6):
+                e = np.zeros(6)
+                e[k] = self.h[k]
+                self._evaluate(xi + e, 2 * k)
+                self._evaluate(xi - e, 2 * k + 1)
+            L = self.terms.sum(dim=1).cpu().numpy().astype(np.float64)
+            g = (L[0:12:2] - L[1:12:2]) / (2.0 * self.h)
+            L0 = float(L[12])
         self.g.copy_(torch.from_numpy(g.astype(np.float32)))
         self.ctx.adam(self.xi, self.g, self.m, self.v, self.k, lr=self.lr, lo=-1.0, hi=1.0)
         self.apply(self.xi.cpu().numpy().astype(np.float64))
-        return float(L[12])
+        return L0
 
     def pose(self):
         """Current (Rc, tc)."""

@@ -171,10 +171,13 @@ def test_principled_fit_step_matches_oracle(orc):
     assert np.mean(hist[-3:]) < np.mean(hist[:2])
 
 
-def test_joint_fit_with_camera_pose(orc):
+@pytest.mark.parametrize("pose_gradient", ["adjoint", "differences"])
+def test_joint_fit_with_camera_pose(orc, pose_gradient):
     """Eq. 9 over albedo, roughness, responses and the camera pose at once,
     from maps and a pose that are both off: the pose error shrinks, and the
-    loss ends lower than the same fit with the pose held at its start."""
+    loss ends lower than the same fit with the pose held at its start; the
+    pose's gradient from the pose adjoint (64 samples per pixel edge at this
+    size) or from central differences."""
     torch = need_cuda()
 
     sc = scenes.corner(res=40, tex=16, spp=8, bounces=2, seed=2)
@@ -192,7 +195,8 @@ def test_joint_fit_with_camera_pose(orc):
                      for i in range(K)]
             f = fit.SceneFit(g.ctx, g.handle, g.view, dpcs.make_params(params0), torch.from_numpy(albedo0).cuda(),
                              torch.from_numpy(rough0).cuda(), pairs, sc.spp, sc.bounces, lr_tex=2e-2,
-                             lr_params=1e-2, tv_weight=1e-5, seed=5, pose_xi0=xi0, pose_lr=pose_lr)
+                             lr_params=1e-2, tv_weight=1e-5, seed=5, pose_xi0=xi0, pose_lr=pose_lr,
+                             pose_gradient=pose_gradient, pose_edge_spp=64)
             hist = f.run(40)
             out[pose_lr] = (hist, f.pose.xi.cpu().numpy().astype(np.float64))
         finally:

@@ -102,7 +102,7 @@ def test_pose_gradient_matches_oracle(orc):
         pairs = [(torch.from_numpy(Ips[i]).cuda(), torch.from_numpy(caps[i].astype(np.float32)).cuda())
                  for i in range(K)]
         pr = pose.PoseRefine(g.ctx, g.handle, g.view, g.params, g.albedo, g.rough, pairs, sc.spp, sc.bounces,
-                             seed=sc.seed, xi0=xi0, h_rot=2e-3, h_trans=2e-3, lr=0.0)
+                             seed=sc.seed, xi0=xi0, h_rot=2e-3, h_trans=2e-3, lr=0.0, gradient="differences")
         L0 = pr.step()
         g.ctx.sync()
         grad = pr.g.cpu().numpy().astype(np.float64)
@@ -122,8 +122,9 @@ def test_pose_gradient_matches_oracle(orc):
 
 
 def test_pose_refinement_recovers_the_pose(orc):
-    """Captures rendered at the true pose (the identity); Adam on the FD
-    gradient from a pose off by ~1 degree and ~2 cm shrinks the error."""
+    """Captures rendered at the true pose (the identity); Adam on the
+    central-difference gradient from a pose off by ~1 degree and ~2 cm
+    shrinks the error."""
     torch = need_cuda()
     sc = scenes.corner(res=48, tex=32, spp=8, bounces=2, seed=9)
     rng = np.random.default_rng(10)
@@ -135,7 +136,7 @@ def test_pose_refinement_recovers_the_pose(orc):
         pairs = [(torch.from_numpy(Ips[i]).cuda(), torch.from_numpy(caps[i].astype(np.float32)).cuda())
                  for i in range(K)]
         pr = pose.PoseRefine(g.ctx, g.handle, g.view, g.params, g.albedo, g.rough, pairs, sc.spp, sc.bounces,
-                             seed=3, xi0=xi0, h_rot=2e-3, h_trans=2e-3, lr=2e-3)
+                             seed=3, xi0=xi0, h_rot=2e-3, h_trans=2e-3, lr=2e-3, gradient="differences")
         hist = [pr.step() for _ in range(40)]
         xi = pr.xi.cpu().numpy().astype(np.float64)
     finally:
