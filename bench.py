@@ -107,7 +107,9 @@ LOAD_BYTES = {"node_visits": 64, "tri_tests": 48, "vertices": 24 + 4 * 16, "lit"
 DENOISE_PARAMS = {"radius": 5, "sigma_s": 2.0, "sigma_albedo": 0.1, "sigma_normal": 0.3, "sigma_depth": 0.1}
 DENOISE_FLOP_PER_TAP = 34
 FIT_PAIRS = 15  # the paper's training set size K
-POSE_PAIRS = 3  # pairs per pose evaluation (13 evaluations per pose step)
+POSE_PAIRS = 3  # pairs per pose step (13 evaluations each with central differences)
+POSE_EDGE_SPP = 16  # pose adjoint: samples per pixel edge
+POSE_SIL_SPP = 16   # pose adjoint: samples per silhouette edge
 
 
 def denoise_taps(H: int, W: int, r: int) -> int:
@@ -765,37 +767,50 @@ def main():
             "albedo_mae_start": float((half.double() - true_alb).abs().mean()),
             "albedo_mae_end": float((fobj.albedo.double() - true_alb).abs().mean()),
         }
-        # camera-pose refinement on the same scene: central-difference Adam
-        # steps on the pose (13 evaluations of the data term, each a rigid
-        # transform + refit and POSE_PAIRS renders), from a pose off by ~1 degree
+        # camera-pose refinement on the same scene, from a pose off by ~1
+        # degree: Adam steps on the pose with its gradient from the pose
+        # adjoint (per pair one render, L1 term and dpcs_pose_backward) and
+        # from central differences (13 evaluations of the data term, each a
+        # rigid transform + refit and POSE_PAIRS renders)
         from paper_2503_12174_gb300 import pose as pose_mod
 
         xi0 = np.array([0.01, -0.008, 0.006, 0.01, -0.01, 0.015])
-        pr = pose_mod.PoseRefine(ctx, fh, fview, fprm, f_alb, f_rough, pairs[:POSE_PAIRS], fs.spp, fs.bounces,
-                                 seed=6400 + rank, xi0=xi0, lr=2e-3)
-        pr.step()  # warm-up
-        torch.cuda.synchronize()
-        barrier()
-        t0 = time.perf_counter()
-        e0.record(stream)
-        phist = [pr.step() for _ in range(args.fit_steps)]
-        e1.record(stream)
-        e1.synchronize()
-        pose_wall_ms = (time.perf_counter() - t0) * 1e3
-        barrier()
-        pose_ms = max_over_ranks(e0.elapsed_time(e1))
-        xi_end = pr.xi.cpu().numpy().astype(np.float64)
-        ctx.transform(fh, np.eye(3), np.zeros(3))
-        fit_out["pose"] = {
-            "workload": f"camera-pose refinement, same scene and renders, {POSE_PAIRS} pairs: 13 evaluations of "
-                        "the mean L1 data term per step (transform + refit, renders, L1 terms), then Adam on the pose",
-            "steps": args.fit_steps, "ms_per_step": pose_ms / args.fit_steps,
-            "wall_ms_per_step": pose_wall_ms / args.fit_steps,
-            "Msamples_per_s": 13 * POSE_PAIRS * fs.n_samples * args.fit_steps * ws / (pose_ms / 1e3) / 1e6,
-            "loss_first": float(phist[0]), "loss_last": float(phist[-1]),
-            "pose_error_start": [float(np.linalg.norm(xi0[:3])), float(np.linalg.norm(xi0[3:]))],
-            "pose_error_end": [float(np.linalg.norm(xi_end[:3])), float(np.linalg.norm(xi_end[3:]))],
-        }
+        fit_out["pose"] = {}
+        for grad_kind in ("adjoint", "differences"):
+            pr = pose_mod.PoseRefine(ctx, fh, fview, fprm, f_alb, f_rough, pairs[:POSE_PAIRS], fs.spp, fs.bounces,
+                                     seed=6400 + rank, xi0=xi0, lr=2e-3, gradient=grad_kind,
+                                     edge_spp=POSE_EDGE_SPP, sil_spp=POSE_SIL_SPP)
+            pr.step()  # warm-up
+            torch.cuda.synchronize()
+            barrier()
+            t0 = time.perf_counter()
+            e0.record(stream)
+            phist = [pr.step() for _ in range(args.fit_steps)]
+            e1.record(stream)
+            e1.synchronize()
+            pose_wall_ms = (time.perf_counter() - t0) * 1e3
+            barrier()
+            pose_ms = max_over_ranks(e0.elapsed_time(e1))
+            xi_end = pr.xi.cpu().numpy().astype(np.float64)
+            ctx.transform(fh, np.eye(3), np.zeros(3))
+            if grad_kind == "adjoint":
+                work = (f"{POSE_PAIRS} pairs: per pair one render, the mean L1 term and the pose adjoint (interior "
+                        f"samples as the render, {POSE_EDGE_SPP} samples per pixel edge, {POSE_SIL_SPP} per "
+                        "silhouette edge), then Adam on the pose")
+                paths = POSE_PAIRS * fs.n_samples * (2 + 4 * POSE_EDGE_SPP / fs.spp)  # render + adjoint paths
+            else:
+                work = (f"{POSE_PAIRS} pairs: 13 evaluations of the mean L1 data term per step (transform + refit, "
+                        "renders, L1 terms), then Adam on the pose")
+                paths = 13 * POSE_PAIRS * fs.n_samples
+            fit_out["pose"][grad_kind] = {
+                "workload": "camera-pose refinement, same scene and renders, " + work,
+                "steps": args.fit_steps, "ms_per_step": pose_ms / args.fit_steps,
+                "wall_ms_per_step": pose_wall_ms / args.fit_steps,
+                "Mpaths_per_s": paths * args.fit_steps * ws / (pose_ms / 1e3) / 1e6,
+                "loss_first": float(phist[0]), "loss_last": float(phist[-1]),
+                "pose_error_start": [float(np.linalg.norm(xi0[:3])), float(np.linalg.norm(xi0[3:]))],
+                "pose_error_end": [float(np.linalg.norm(xi_end[:3])), float(np.linalg.norm(xi_end[3:]))],
+            }
         del fobj, pairs, pr
         ctx.free(fh)
 
@@ -1064,6 +1079,8 @@ def main():
             summ["heightfield_fwd_bwd"] = hf_out["fwd_bwd"]["value"]
         if comp_out:
             summ["compensation_100_steps_ms"] = comp_out["graph"]["ms"]
+        if fit_out and "pose" in fit_out:
+            summ["pose_step_ms"] = {k: v["ms_per_step"] for k, v in fit_out["pose"].items()}
         if serving_out:
             summ["serving"] = [{"rate": x["offered_rate_per_s"], "srv_relight_p99": x["server"]["relight_p99_ms"],
                                 "call_relight_p99": x["per_call"]["relight_p99_ms"],
