@@ -56,21 +56,22 @@ L2_FLUSH_BYTES = 256 << 20
 # ncu capture of the same command.  It holds only for the kernel sources it
 # was measured on; once they change, the roofline's traffic is reported as
 # null until a new capture is taken.
-RENDER_TRAFFIC = {"bytes": 23004160, "sources_sha256": "868c983676ab5d1dbc76dfb730588b3b3b6e73744dbd106acb33d7a741dc076c"}
+RENDER_TRAFFIC = {"bytes": 20629504, "sources_sha256": "508f75db6f855332a222fba620eb55bc1b90fe365e09b9af620bbc64d8698124"}
 # Warp instructions one k_render launch of the forward workload issues, and
 # the active lanes per instruction, from the same ncu capture
 # (smsp__inst_executed.sum, smsp__thread_inst_executed_per_inst_executed);
 # reported while the kernel sources keep this hash.
-RENDER_ISSUE = {"warp_instructions": 1914933228, "lanes_per_instruction": 12.08,
-                "sources_sha256": "868c983676ab5d1dbc76dfb730588b3b3b6e73744dbd106acb33d7a741dc076c"}
+RENDER_ISSUE = {"warp_instructions": 1192796769, "lanes_per_instruction": 13.54,
+                "sources_sha256": "508f75db6f855332a222fba620eb55bc1b90fe365e09b9af620bbc64d8698124"}
 # The same two figures for one k_render_grad launch of the compensation step
 # with every gradient requested.
-FWD_BWD_TRAFFIC = {"bytes": 1938776576,
-                   "sources_sha256": "868c983676ab5d1dbc76dfb730588b3b3b6e73744dbd106acb33d7a741dc076c"}
-FWD_BWD_ISSUE = {"warp_instructions": 2127931742, "lanes_per_instruction": 13.29,
-                 "sources_sha256": "868c983676ab5d1dbc76dfb730588b3b3b6e73744dbd106acb33d7a741dc076c"}
+FWD_BWD_TRAFFIC = {"bytes": 1898995712,
+                   "sources_sha256": "508f75db6f855332a222fba620eb55bc1b90fe365e09b9af620bbc64d8698124"}
+FWD_BWD_ISSUE = {"warp_instructions": 1407314884, "lanes_per_instruction": 15.14,
+                 "sources_sha256": "508f75db6f855332a222fba620eb55bc1b90fe365e09b9af620bbc64d8698124"}
+# the kernels' sources and the tree builder (its topology sets the node visits)
 KERNEL_SOURCES = ("paper_2503_12174_gb300/csrc/render.cu", "paper_2503_12174_gb300/csrc/device.cuh",
-                  "paper_2503_12174_gb300/csrc/internal.h")
+                  "paper_2503_12174_gb300/csrc/internal.h", "paper_2503_12174_gb300/csrc/lbvh.cu")
 
 
 def kernel_sources_sha256() -> str:

@@ -217,6 +217,25 @@ dpcs_status dpcs_scene_upload(dpcs_ctx *ctx, const float *verts, int32_t V, cons
 dpcs_status dpcs_scene_update(dpcs_ctx *ctx, dpcs_scene scene, const float *verts, int32_t V, void *stream);
 
 /*
+ * Tree topology of the scenes uploaded from now on (closest hits, and so
+ * every image and gradient, do not depend on it):
+ *  DPCS_BVH_PLOC (default): the radix tree over the Morton order is rebuilt
+ *    by agglomerative clustering (PLOC, Meister & Bittner 2018: mutual
+ *    nearest neighbours by union surface area within 16 clusters on either
+ *    side in Morton order), a tree of lower surface-area cost that rays
+ *    traverse with fewer node visits.  The upload then synchronises the
+ *    stream once per clustering round.  A tree deeper than the traversal
+ *    stack (64) is not taken: the radix tree stays.
+ *  DPCS_BVH_LBVH: the Karras radix tree itself.
+ * Codes, leaf order and the triangle records are the same for both; refits
+ * (dpcs_scene_update, dpcs_scene_transform) keep whichever topology the
+ * upload built.  Measurement and quality setting, not part of the paper.
+ */
+#define DPCS_BVH_LBVH 0
+#define DPCS_BVH_PLOC 1
+dpcs_status dpcs_set_bvh_builder(dpcs_ctx *ctx, int32_t builder);
+
+/*
  * Rigid transform of an uploaded scene, for the camera pose (Rc, tc) of
  * Sec. 3.2's scene parameters: renders take the camera at the origin
  * (Eq. 6), and a camera at pose (Rc, tc) sees each world point x at

@@ -66,6 +66,8 @@ struct dpcs_ctx {
     Buf wf;  // wavefront render: lane sums, per-chunk path state, queues
     int32_t render_path = DPCS_PATH_MEGAKERNEL;
     int64_t wf_chunk = int64_t(1) << 20;
+    int32_t bvh_builder = DPCS_BVH_PLOC;  // tree topology of the next uploads
+    Buf ploc;  // PLOC build scratch
     Buf pose;  // per-block partial sums of the pose-gradient kernels
     std::map<uint64_t, EdgeTable> edges;  // per scene, built by its first pose-gradient call with silhouettes
     Buf kept;  // path records of the last dpcs_render_keep: 16-byte chunks (structure of arrays), then per-sample vertex counts
@@ -434,7 +436,7 @@ dpcs_status dpcs_destroy(dpcs_ctx *c) {
     }
     for (auto &kv : c->edges) cudaFree(kv.second.d);
     Buf *bufs[] = {&c->ep4, &c->tex4, &c->gE, &c->dEp4, &c->dtex4, &c->acc, &c->partial, &c->build, &c->upload, &c->pix,
-                   &c->kept, &c->mat4, &c->dmat4, &c->dEp64, &c->dtex64, &c->wf, &c->pose};
+                   &c->kept, &c->mat4, &c->dmat4, &c->dEp64, &c->dtex64, &c->wf, &c->pose, &c->ploc};
     for (Buf *b : bufs)
         if (b->p) cudaFree(b->p);
     cudaFree(c->status);
@@ -495,6 +497,13 @@ dpcs_status dpcs_set_grad_accum(dpcs_ctx *c, int32_t mode) {
     if (mode != DPCS_ACCUM_F32 && mode != DPCS_ACCUM_F64)
         return fail(c, DPCS_ERR_INVALID_ARG, "grad accumulation mode must be DPCS_ACCUM_F32 or DPCS_ACCUM_F64");
     c->grad_f64 = mode == DPCS_ACCUM_F64;
+    return DPCS_OK;
+}
+
+dpcs_status dpcs_set_bvh_builder(dpcs_ctx *c, int32_t builder) {
+    if (!c) return DPCS_ERR_INVALID_ARG;
+    if (builder != DPCS_BVH_LBVH && builder != DPCS_BVH_PLOC) return fail(c, DPCS_ERR_INVALID_ARG, "unknown BVH builder");
+    c->bvh_builder = builder;
     return DPCS_OK;
 }
 
@@ -597,6 +606,12 @@ dpcs_status dpcs_scene_upload(dpcs_ctx *c, const float *verts, int32_t V, const 
         if (e != cudaSuccess) return cuda_fail(c, e, "scene upload");
         int nl = launch_lbvh_build(dv, V, dt, T, du, sc, c->build.p, c->build.n, st);
         if ((s = check_launch(c, nl, "LBVH build"))) return s;
+        if (c->bvh_builder == DPCS_BVH_PLOC && T >= 3) {
+            if ((s = ensure(c, c->ploc, ploc_scratch_bytes(T), "PLOC scratch"))) return s;
+            int32_t depth = 0;
+            if ((s = check_launch(c, launch_ploc(sc, c->ploc.p, c->ploc.n, kMaxTreeDepth, st, &depth), "PLOC build")))
+                return s;
+        }
         e = cudaMemcpyAsync(sc.vidx, dt, tb, cudaMemcpyDeviceToDevice, st);  // kept for dpcs_scene_update
         if (e == cudaSuccess) e = cudaMemcpyAsync(sc.uv, du, ub, cudaMemcpyDeviceToDevice, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(sc.base, dv, vb, cudaMemcpyDeviceToDevice, st);  // rigid transforms

@@ -121,6 +121,13 @@ int launch_lbvh_refit(const float *d_verts, Scene &sc, void *scratch, size_t scr
 // out[v] = R in[v] + t for V points (R row-major)
 int launch_rigid_transform(const float *in, int32_t V, const float R[9], const float t[3], float *out, cudaStream_t st);
 size_t lbvh_refit_scratch_bytes(int32_t T);
+// Rebuild of the tree's topology by agglomerative clustering (PLOC) over the
+// leaf order of the radix tree, for a lower surface-area cost: the nodes are
+// replaced only if the new tree is at most max_depth deep (depth_out gets
+// its depth).  Synchronises the stream once per clustering round.
+size_t ploc_scratch_bytes(int32_t T);
+int launch_ploc(Scene &sc, void *scratch, size_t scratch_bytes, int max_depth, cudaStream_t st, int32_t *depth_out);
+constexpr int kMaxTreeDepth = 64;  // internal nodes on a root-to-leaf path: the traversal stack's depth
 
 int launch_prf(const float *Ip, int64_t ntex, const float gamma_p[3], float gain_p, float4 *Ep, cudaStream_t st);
 int launch_pack_tex(const float *albedo, const float *rough, int64_t ntex, float4 *tex, cudaStream_t st);

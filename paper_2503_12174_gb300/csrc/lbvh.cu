@@ -250,7 +250,202 @@ __global__ void k_parents(const float4 *__restrict__ nodes, int T, int32_t *__re
 
 inline size_t align256(size_t n) { return (n + 255) & ~size_t(255); }
 
+// --- PLOC: agglomerative clustering over the Morton order -------------------
+// (Meister & Bittner, "Parallel Locally-Ordered Clustering for Bounding
+// Volume Hierarchy Construction", IEEE TVCG 2018.)  Clusters sit in Morton
+// order; each finds its nearest neighbour -- the one whose union with it has
+// the smallest surface area -- among the kPlocRadius clusters on either side;
+// mutual nearest neighbours merge into a new node, and the survivors are
+// compacted in order, until one cluster is left.  Ties go to the smaller
+// index, which orders every pair by (area, lower index, higher index): the
+// least pair of a round is always mutual, so every round merges.  New nodes
+// are numbered downwards from T - 2 by a prefix sum of the merge flags, so
+// the last merge (the root) is node 0 and the build is deterministic.
+#ifndef DPCS_PLOC_RADIUS
+#define DPCS_PLOC_RADIUS 16
+#endif
+constexpr int kPlocRadius = DPCS_PLOC_RADIUS;
+constexpr int kPlocBlock = 128;
+
+__device__ __forceinline__ float union_area(float4 alo, float4 ahi, float4 blo, float4 bhi) {
+    const float dx = fmaxf(ahi.x, bhi.x) - fminf(alo.x, blo.x);
+    const float dy = fmaxf(ahi.y, bhi.y) - fminf(alo.y, blo.y);
+    const float dz = fmaxf(ahi.z, bhi.z) - fminf(alo.z, blo.z);
+    return 2.0f * (dx * dy + dy * dz + dz * dx);
+}
+
+// leaf clusters: the boxes of the triangle records, in leaf order
+__global__ void k_ploc_init(const float4 *__restrict__ tris, int T, int32_t *__restrict__ cid,
+                            float4 *__restrict__ cbox) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= T) return;
+    const float4 a = tris[3 * p], b = tris[3 * p + 1], c = tris[3 * p + 2];
+    cid[p] = ~p;
+    cbox[2 * p] = make_float4(fminf(fminf(a.x, b.x), c.x), fminf(fminf(a.y, b.y), c.y), fminf(fminf(a.z, b.z), c.z), 0.f);
+    cbox[2 * p + 1] =
+        make_float4(fmaxf(fmaxf(a.x, b.x), c.x), fmaxf(fmaxf(a.y, b.y), c.y), fmaxf(fmaxf(a.z, b.z), c.z), 0.f);
+}
+
+// nearest neighbour of each of the n clusters within the radius; the block's
+// clusters and the radius on either side are staged in shared memory
+__global__ void __launch_bounds__(kPlocBlock) k_ploc_nn(const float4 *__restrict__ cbox, int n,
+                                                       int32_t *__restrict__ nn) {
+    __shared__ float4 sb[2 * (kPlocBlock + 2 * kPlocRadius)];
+    const int base = blockIdx.x * kPlocBlock - kPlocRadius;
+    for (int k = threadIdx.x; k < kPlocBlock + 2 * kPlocRadius; k += blockDim.x) {
+        const int j = base + k;
+        if (j >= 0 && j < n) {
+            sb[2 * k] = cbox[2 * j];
+            sb[2 * k + 1] = cbox[2 * j + 1];
+        }
+    }
+    __syncthreads();
+    const int i = blockIdx.x * kPlocBlock + threadIdx.x;
+    if (i >= n) return;
+    const int li = i - base;
+    const float4 lo = sb[2 * li], hi = sb[2 * li + 1];
+    float best = INFINITY;
+    int bj = i > 0 ? i - 1 : i + 1;
+    const int j0 = max(0, i - kPlocRadius), j1 = min(n - 1, i + kPlocRadius);
+    for (int j = j0; j <= j1; ++j) {
+        if (j == i) continue;
+        const float a = union_area(lo, hi, sb[2 * (j - base)], sb[2 * (j - base) + 1]);
+        if (a < best) {  // ascending j with a strict comparison: ties to the smaller index
+            best = a;
+            bj = j;
+        }
+    }
+    nn[i] = bj;
+}
+
+// merge flag (the lower of a mutual pair) and keep flag (not the higher one)
+__global__ void k_ploc_flags(const int32_t *__restrict__ nn, int n, uint32_t *__restrict__ mflag,
+                             uint32_t *__restrict__ kflag) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int j = nn[i];
+    const bool mutual = nn[j] == i;
+    mflag[i] = (mutual && i < j) ? 1u : 0u;
+    kflag[i] = (mutual && i > j) ? 0u : 1u;
+}
+
+// with mscan / kscan the exclusive prefix sums of the flags: write the new
+// nodes (ids next - 1 - mscan[i]) and the surviving clusters in order;
+// counts = (clusters left, merges)
+__global__ void k_ploc_compact(const int32_t *__restrict__ nn, int n, const uint32_t *__restrict__ mscan,
+                               const uint32_t *__restrict__ kscan, int next, const int32_t *__restrict__ cid,
+                               const float4 *__restrict__ cbox, int32_t *__restrict__ cid_out,
+                               float4 *__restrict__ cbox_out, float4 *__restrict__ nodes,
+                               int32_t *__restrict__ counts) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int j = nn[i];
+    const bool mutual = nn[j] == i;
+    if (i == n - 1) {
+        counts[0] = (int32_t)(kscan[i] + ((mutual && i > j) ? 0u : 1u));
+        counts[1] = (int32_t)(mscan[i] + ((mutual && i < j) ? 1u : 0u));
+    }
+    if (mutual && i > j) return;  // merged into j
+    const uint32_t o = kscan[i];
+    const float4 lo = cbox[2 * i], hi = cbox[2 * i + 1];
+    if (mutual) {
+        const int id = next - 1 - (int)mscan[i];
+        const float4 rlo = cbox[2 * j], rhi = cbox[2 * j + 1];
+        float4 *nd = nodes + 4 * (int64_t)id;
+        nd[0] = make_float4(lo.x, hi.x, lo.y, hi.y);
+        nd[1] = make_float4(rlo.x, rhi.x, rlo.y, rhi.y);
+        nd[2] = make_float4(lo.z, hi.z, rlo.z, rhi.z);
+        nd[3] = make_float4(__int_as_float(cid[i]), __int_as_float(cid[j]), 0.0f, 0.0f);
+        cid_out[o] = id;
+        cbox_out[2 * o] = make_float4(fminf(lo.x, rlo.x), fminf(lo.y, rlo.y), fminf(lo.z, rlo.z), 0.f);
+        cbox_out[2 * o + 1] = make_float4(fmaxf(hi.x, rhi.x), fmaxf(hi.y, rhi.y), fmaxf(hi.z, rhi.z), 0.f);
+    } else {
+        cid_out[o] = cid[i];
+        cbox_out[2 * o] = lo;
+        cbox_out[2 * o + 1] = hi;
+    }
+}
+
+// deepest leaf: internal nodes on its path from the root (stops counting
+// past `limit`, so a malformed tree cannot loop)
+__global__ void k_tree_depth(const int32_t *__restrict__ parent, int T, int limit, int32_t *__restrict__ depth) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= T) return;
+    int d = 1, node = parent[T - 1 + p];
+    while (node != 0 && d <= limit) {
+        node = parent[node];
+        ++d;
+    }
+    atomicMax(depth, d);
+}
+
 }  // namespace
+
+size_t ploc_scratch_bytes(int32_t T) {
+    const size_t n = (size_t)(T > 0 ? T : 1);
+    return 2 * align256(n * 4) + 2 * align256(n * 32) + align256(n * 4) + 2 * align256(n * 4) +
+           align256(n * 64) + align256(2 * n * 4) + align256(4 * 4);
+}
+
+int launch_ploc(Scene &sc, void *scratch, size_t scratch_bytes, int max_depth, cudaStream_t st, int32_t *depth_out) {
+    const int T = sc.T;
+    *depth_out = 0;
+    if (T < 3) return 0;  // the radix tree of two leaves is already optimal
+    if (scratch_bytes < ploc_scratch_bytes(T)) return DPCS_ERR_INVALID_ARG;
+    const size_t n = (size_t)T;
+    char *q = (char *)scratch;
+    auto take = [&](size_t bytes) {
+        char *r = q;
+        q += align256(bytes);
+        return (void *)r;
+    };
+    int32_t *cid[2] = {(int32_t *)take(n * 4), (int32_t *)take(n * 4)};
+    float4 *cbox[2] = {(float4 *)take(n * 32), (float4 *)take(n * 32)};
+    int32_t *nn = (int32_t *)take(n * 4);
+    uint32_t *mflag = (uint32_t *)take(n * 4), *kflag = (uint32_t *)take(n * 4);
+    float4 *nodes = (float4 *)take(n * 64);
+    int32_t *parent = (int32_t *)take(2 * n * 4);
+    int32_t *counts = (int32_t *)take(4 * 4);
+    const int tb = 256;
+    int launches = 0;
+    k_ploc_init<<<(T + tb - 1) / tb, tb, 0, st>>>(sc.tris, T, cid[0], cbox[0]);
+    ++launches;
+    int cur = 0, count = T, next = T - 1;
+    while (count > 1) {
+        const int g = (count + tb - 1) / tb;
+        k_ploc_nn<<<(count + kPlocBlock - 1) / kPlocBlock, kPlocBlock, 0, st>>>(cbox[cur], count, nn);
+        k_ploc_flags<<<g, tb, 0, st>>>(nn, count, mflag, kflag);
+        k_radix_scan<<<1, 1024, 0, st>>>(mflag, count);
+        k_radix_scan<<<1, 1024, 0, st>>>(kflag, count);
+        k_ploc_compact<<<g, tb, 0, st>>>(nn, count, mflag, kflag, next, cid[cur], cbox[cur], cid[1 - cur],
+                                         cbox[1 - cur], nodes, counts);
+        launches += 5;
+        int32_t h[2];
+        cudaError_t e = cudaMemcpyAsync(h, counts, sizeof h, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return DPCS_ERR_CUDA;
+        if (h[1] < 1 || h[0] != count - h[1] || h[1] > next) return DPCS_ERR_DEVICE_CHECK;  // every round merges
+        count = h[0];
+        next -= h[1];
+        cur = 1 - cur;
+    }
+    if (next != 0) return DPCS_ERR_DEVICE_CHECK;
+    // depth of the new tree against the traversal stack
+    k_parents<<<(T - 1 + tb - 1) / tb, tb, 0, st>>>(nodes, T, parent);
+    cudaMemsetAsync(counts, 0, 4, st);
+    k_tree_depth<<<(T + tb - 1) / tb, tb, 0, st>>>(parent, T, max_depth + 1, counts);
+    launches += 2;
+    int32_t d = 0;
+    cudaError_t e = cudaMemcpyAsync(&d, counts, 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return DPCS_ERR_CUDA;
+    *depth_out = d;
+    if (d > max_depth) return launches;  // too deep for the traversal stack: the radix tree stays
+    e = cudaMemcpyAsync(sc.nodes, nodes, (n - 1) * 64, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return DPCS_ERR_CUDA;
+    sc.root = 0;
+    return launches;
+}
 
 size_t lbvh_scratch_bytes(int32_t T) {
     const size_t n = (size_t)(T > 0 ? T : 1);

@@ -30,6 +30,9 @@
 
 namespace dpcs {
 
+static_assert(kStack >= kMaxTreeDepth, "a tree the builders accept must fit the traversal stack");
+
+
 namespace {
 
 constexpr int kWfBlock = 128;

@@ -30,6 +30,8 @@ DPCS_ACCUM_F32 = 0
 DPCS_ACCUM_F64 = 1
 DPCS_PATH_MEGAKERNEL = 0
 DPCS_PATH_WAVEFRONT = 1
+DPCS_BVH_LBVH = 0
+DPCS_BVH_PLOC = 1
 
 EXPORTED = [
     "dpcs_create", "dpcs_destroy", "dpcs_last_error", "dpcs_sync", "dpcs_memory_used", "dpcs_launch_count",
@@ -42,6 +44,7 @@ EXPORTED = [
     "dpcs_render_backward_kept", "dpcs_render_principled", "dpcs_render_backward_principled",
     "dpcs_scene_transform", "dpcs_render_loss_backward_principled", "dpcs_render_keep_principled",
     "dpcs_render_backward_kept_principled", "dpcs_set_grad_accum", "dpcs_set_render_path", "dpcs_pose_backward",
+    "dpcs_set_bvh_builder",
 ]
 
 DPCS_REQ_RELIGHT = 0
@@ -183,6 +186,7 @@ _SIGS = {
     "dpcs_debug_set_visit_cap": (ctypes.c_int32, [_P, ctypes.c_int32]),
     "dpcs_set_grad_accum": (ctypes.c_int32, [_P, ctypes.c_int32]),
     "dpcs_set_render_path": (ctypes.c_int32, [_P, ctypes.c_int32, ctypes.c_int64]),
+    "dpcs_set_bvh_builder": (ctypes.c_int32, [_P, ctypes.c_int32]),
     "dpcs_gbuffer": (ctypes.c_int32, [_P, ctypes.c_uint64, _P, _P, ctypes.c_int32, ctypes.c_int32,
                                       ctypes.POINTER(DpcsView), _P, _P]),
     "dpcs_denoise": (ctypes.c_int32, [_P, _P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(DpcsDenoiseParams),
@@ -481,6 +485,10 @@ class Context:
         DPCS_ACCUM_F64 (FP64 atomics; sums independent of the add order up to
         FP64 rounding)."""
         self.check(self.lib.dpcs_set_grad_accum(self.handle, int(mode)), "set_grad_accum")
+
+    def set_bvh_builder(self, builder: int):
+        """Tree topology of later uploads: DPCS_BVH_PLOC (default) or DPCS_BVH_LBVH."""
+        self.check(self.lib.dpcs_set_bvh_builder(self.handle, int(builder)), "set_bvh_builder")
 
     def set_render_path(self, path: int, chunk: int = 0):
         """dpcs_render's kernels: DPCS_PATH_MEGAKERNEL (one kernel) or

@@ -1,10 +1,11 @@
 """GPU LBVH build vs the oracle's reference: Morton codes, sort order, radix
-tree topology and child boxes must agree bit for bit; closest hits through
-the BVH must match brute-force FP64 tests."""
+tree topology and child boxes must agree bit for bit (radix-tree builder);
+closest hits through the BVH must match brute-force FP64 tests (both
+builders)."""
 import numpy as np
 import pytest
 
-from paper_2503_12174_gb300 import scenes
+from paper_2503_12174_gb300 import dpcs, scenes
 from gpu_util import ctx, need_cuda
 
 pytestmark = pytest.mark.gpu
@@ -32,7 +33,11 @@ def _meshes():
 def test_lbvh_bit_exact(orc, case):
     name, verts, tris, uv = list(_meshes())[case]
     c = ctx()
-    h = c.upload(verts, tris, uv)
+    c.set_bvh_builder(dpcs.DPCS_BVH_LBVH)
+    try:
+        h = c.upload(verts, tris, uv)
+    finally:
+        c.set_bvh_builder(dpcs.DPCS_BVH_PLOC)
     try:
         codes, order, child, box = c.export(h, len(tris))
         rc, ro, rch, rb = orc.lbvh(verts, tris)
@@ -44,8 +49,9 @@ def test_lbvh_bit_exact(orc, case):
         c.free(h)
 
 
+@pytest.mark.parametrize("builder", [dpcs.DPCS_BVH_LBVH, dpcs.DPCS_BVH_PLOC])
 @pytest.mark.parametrize("which", ["corner", "heightfield_small", "sphere"])
-def test_closest_hit_vs_brute_force(orc, which):
+def test_closest_hit_vs_brute_force(orc, which, builder):
     torch = need_cuda()
     rng = np.random.default_rng(11)
     if which == "corner":
@@ -64,7 +70,11 @@ def test_closest_hit_vs_brute_force(orc, which):
     o = o.astype(np.float32).astype(np.float64)
     d = d.astype(np.float32).astype(np.float64)
     c = ctx()
-    h = c.upload(verts, tris, uv)
+    c.set_bvh_builder(builder)
+    try:
+        h = c.upload(verts, tris, uv)
+    finally:
+        c.set_bvh_builder(dpcs.DPCS_BVH_PLOC)
     try:
         t, tri = c.trace(h, torch.from_numpy(o.astype(np.float32)).cuda(), torch.from_numpy(d.astype(np.float32)).cuda())
         c.sync()
