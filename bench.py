@@ -995,9 +995,11 @@ def main():
             entry = {"offered_rate_per_s": rate, "server": {k: srv[k] for k in keep},
                      "per_call": {k: per[k] for k in keep}, "server_iterations": srv["server"]["iterations"],
                      "server_memory_high_water_bytes": srv["server"]["memory_high_water"]}
-            if rate >= 8.0:  # the deadline policy beside the default fixed share
+            if rate >= 8.0:  # the deadline policies beside the default fixed share
                 dl = serving.run_server(ctx, gs, host, wl, **deadline)
                 entry["server_deadline_policy"] = {k: dl[k] for k in keep}
+                qd = serving.run_server(ctx, gs, host, wl, **dict(deadline, policy=dpcs.DPCS_SERVE_QUANTA_DEADLINE))
+                entry["server_quanta_deadline_policy"] = {k: qd[k] for k in keep}
             sweep.append(entry)
         sat = serving.make_workload(args.serve_requests, rate=0.0, seed=200 + rank)
         srv_sat = serving.run_server(ctx, gs, host, sat)
@@ -1009,7 +1011,8 @@ def main():
                         "camera side in {128..1024 step 64}, spp log-uniform 16-256; 90% relight, "
                         "10% compensation (50 Adam steps, 16 spp); Poisson arrivals",
             "policy": "server = fixed share (relighting quanta, compensation within half of each iteration); "
-                      "server_deadline_policy = earliest deadline first, slack 4 (relight) and 0.5 (compensation)",
+                      "server_deadline_policy = earliest deadline first, slack 4 (relight) and 0.5 (compensation); "
+                      "server_quanta_deadline_policy = the relighting quanta, then the deadline order",
             "load_sweep": sweep,
             "saturated": {"server_requests_per_s": srv_sat["requests_per_s"],
                           "per_call_requests_per_s": per_sat["requests_per_s"],
@@ -1088,7 +1091,9 @@ def main():
                                 "srv_comp_p99": x["server"]["compensation_p99_ms"],
                                 "call_comp_p99": x["per_call"]["compensation_p99_ms"],
                                 "deadline_relight_p99": x.get("server_deadline_policy", {}).get("relight_p99_ms"),
-                                "deadline_comp_p99": x.get("server_deadline_policy", {}).get("compensation_p99_ms")}
+                                "deadline_comp_p99": x.get("server_deadline_policy", {}).get("compensation_p99_ms"),
+                                "qdeadline_relight_p99": x.get("server_quanta_deadline_policy", {}).get("relight_p99_ms"),
+                                "qdeadline_comp_p99": x.get("server_quanta_deadline_policy", {}).get("compensation_p99_ms")}
                                for x in serving_out["load_sweep"]]
         line["summary"] = summ
         print(json.dumps(line), flush=True)

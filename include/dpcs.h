@@ -644,16 +644,19 @@ typedef struct dpcs_serve_config {
      * compensation steps.  DPCS_SERVE_DEADLINE: by earliest deadline, a
      * request's deadline being its arrival plus slack x its work /
      * est_samples_per_s (a compensation step counts its samples x 1.4 for
-     * the adjoint); no quanta. */
+     * the adjoint); no quanta.  DPCS_SERVE_QUANTA_DEADLINE: the relighting
+     * quanta first, then the rest by earliest deadline (deadline fields as
+     * for DPCS_SERVE_DEADLINE; no cap on compensation). */
     int32_t policy;
     int32_t pad;
-    double relight_slack;           /* deadline policy, > 0 */
-    double compensation_slack;      /* deadline policy, > 0 */
-    double est_samples_per_s;       /* deadline policy, > 0: the throughput the deadlines assume */
+    double relight_slack;           /* deadline policies, > 0 */
+    double compensation_slack;      /* deadline policies, > 0 */
+    double est_samples_per_s;       /* deadline policies, > 0: the throughput the deadlines assume */
     double compensation_share;      /* fixed-share policy, in (0, 1] */
 } dpcs_serve_config;
 #define DPCS_SERVE_DEADLINE 0
 #define DPCS_SERVE_FIXED_SHARE 1
+#define DPCS_SERVE_QUANTA_DEADLINE 2
 
 #define DPCS_REQ_RELIGHT 0
 #define DPCS_REQ_COMPENSATE 1

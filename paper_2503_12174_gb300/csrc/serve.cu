@@ -13,7 +13,9 @@
 //      compensation_share of the iteration; the rest goes to relighting
 //      requests in arrival order, and what relighting leaves unused runs
 //      further consecutive compensation steps, still within that share; or
-//      (deadline policy) the rest goes to requests in order of deadline;
+//      (deadline policy) everything goes to requests in order of deadline,
+//      with no quanta; or (quanta-deadline policy) the quanta first, then
+//      the rest in order of deadline;
 //   4. enqueue on the server stream: the batch descriptors, one persistent
 //      k_render_batch launch over the relighting pixels, each compensation
 //      request's step: render, loss and path adjoint in one trace
@@ -338,16 +340,17 @@ dpcs_status launch_iteration(dpcs_server *s, Batch &b) {
         vb += render_batch_vblocks(npx, q->args.log2L);
         ++nseg;
     };
-    // `active` is in arrival order.  1) (fixed share) every relighting
-    // request gets a small quantum, so short requests finish within an
-    // iteration or two; under the deadline policy the deadlines order them
+    // `active` is in arrival order.  1) (fixed share, quanta-deadline) every
+    // relighting request gets a small quantum, so short requests finish
+    // within an iteration or two; under the deadline policy the deadlines
+    // order them
     std::vector<int64_t> give(relight.size(), 0);
-    for (size_t i = 0; s->cfg.policy == DPCS_SERVE_FIXED_SHARE && i < relight.size() && budget > 0; ++i) {
+    for (size_t i = 0; s->cfg.policy != DPCS_SERVE_DEADLINE && i < relight.size() && budget > 0; ++i) {
         Req *q = relight[i];
         give[i] = std::min(q->npix - q->next_pix, std::max<int64_t>(1, s->cfg.quantum_samples / q->r.spp));
         budget -= give[i] * q->r.spp;
     }
-    if (s->cfg.policy == DPCS_SERVE_DEADLINE) {
+    if (s->cfg.policy == DPCS_SERVE_DEADLINE || s->cfg.policy == DPCS_SERVE_QUANTA_DEADLINE) {
         plan_by_deadline(s, relight, comp, give, budget, b);
     } else {
         plan_fixed_share(s, relight, comp, give, budget, total_budget, b);
@@ -518,8 +521,9 @@ dpcs_status dpcs_serve_create(dpcs_ctx *ctx, const dpcs_serve_config *cfg, dpcs_
     *out = nullptr;
     if (cfg->max_active < 1 || cfg->max_active > 1024 || cfg->max_inflight < 1 || cfg->max_inflight > 4 ||
         cfg->samples_per_iteration < 1 || cfg->quantum_samples < 1 ||
-        (cfg->policy != DPCS_SERVE_DEADLINE && cfg->policy != DPCS_SERVE_FIXED_SHARE) ||
-        (cfg->policy == DPCS_SERVE_DEADLINE &&
+        (cfg->policy != DPCS_SERVE_DEADLINE && cfg->policy != DPCS_SERVE_FIXED_SHARE &&
+         cfg->policy != DPCS_SERVE_QUANTA_DEADLINE) ||
+        (cfg->policy != DPCS_SERVE_FIXED_SHARE &&
          !(cfg->relight_slack > 0.0 && cfg->compensation_slack > 0.0 && cfg->est_samples_per_s > 0.0)) ||
         (cfg->policy == DPCS_SERVE_FIXED_SHARE && !(cfg->compensation_share > 0.0 && cfg->compensation_share <= 1.0)))
         return ctx_fail(ctx, DPCS_ERR_INVALID_ARG, "serve: bad config");

@@ -92,6 +92,7 @@ class DpcsServeConfig(ctypes.Structure):
 
 DPCS_SERVE_DEADLINE = 0
 DPCS_SERVE_FIXED_SHARE = 1
+DPCS_SERVE_QUANTA_DEADLINE = 2
 
 
 class DpcsRequest(ctypes.Structure):

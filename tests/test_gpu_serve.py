@@ -48,7 +48,8 @@ def _check_against_alone(c, gs, host, wl, outs):
             np.testing.assert_allclose(Ic_mix, Ic.cpu().numpy(), rtol=2e-3, atol=2e-4, err_msg=f"compensation {k}")
 
 
-@pytest.mark.parametrize("policy", [dpcs.DPCS_SERVE_DEADLINE, dpcs.DPCS_SERVE_FIXED_SHARE])
+@pytest.mark.parametrize("policy", [dpcs.DPCS_SERVE_DEADLINE, dpcs.DPCS_SERVE_FIXED_SHARE,
+                                    dpcs.DPCS_SERVE_QUANTA_DEADLINE])
 def test_results_same_alone_and_in_mix(env, policy):
     need_cuda()
     c, gs, host = env
