@@ -196,3 +196,24 @@ def test_adjoint_pose_refinement_recovers_the_pose(orc):
     assert np.mean(hist[-5:]) < 0.85 * np.mean(hist[:3])
     assert np.linalg.norm(xi[:3]) < 0.75 * np.linalg.norm(xi0[:3]), xi
     assert np.linalg.norm(xi[3:]) < 0.75 * np.linalg.norm(xi0[3:]), xi
+
+
+def test_pose_wrench_at_the_benchmark_size(orc):
+    """The pose step's configuration in the benchmark: the corner at
+    256 x 256, 16 spp, 3 bounces, 16 samples per pixel edge and per
+    silhouette edge, an L1 residual's sign for dLoss/dIc, carried through the
+    corner's camera response (gamma_c 0.45-0.55).  The oracle runs in its timing mode, whose hits
+    are the brute-force hits bit for bit."""
+    torch = need_cuda()
+    sc = scenes.corner(res=256, tex=256, spp=16, bounces=3, seed=6000)
+    W = np.sign(np.random.default_rng(21).normal(size=(sc.Hc, sc.Wc, 3))) / (sc.Hc * sc.Wc * 3)
+    got = _gpu(sc, W, 16, 16)
+    Ec, _ = orc.render(sc, accel=True)
+    ref = orc.pose_backward(sc, W * orc.crf_grad(Ec, sc.params), UNIT, 16, 16, accel=True)
+    scale = np.abs(ref).max()
+    assert scale > 0.0
+    for t, name in enumerate(("interior", "pixel edges", "silhouettes")):
+        err = np.abs(got[t] - ref[t])
+        assert np.all(err <= 1e-2 * np.abs(ref[t]).max() + 1e-6 * scale), (name, got[t], ref[t])
+    tot_g, tot_r = got.sum(0), ref.sum(0)
+    assert np.all(np.abs(tot_g - tot_r) <= 1e-2 * np.abs(tot_r).max()), (tot_g, tot_r)
