@@ -52,7 +52,12 @@ namespace dpcs {
 namespace {
 
 constexpr int kPoseBlock = 128;
-constexpr int kPoseBlocksPerSM = 8;
+// Blocks per SM in the grid-stride grids (4 fit at a time at these register
+// counts; the rest balance the uneven paths).  Measured on the corner at
+// 256 x 256, 16 spp: the interior kernel 0.75 / 0.73 / 0.87 ms at 8 / 16 /
+// 32 blocks per SM, the pixel-edge kernel (16 samples) 2.53 / 2.24 / 1.88 ms.
+constexpr int kPoseGridInterior = 16, kPoseGridEdges = 32, kPoseGridSil = 16;
+constexpr int kPoseBlocksPerSM = 32;  // the largest of the three: the partial sums' stride
 #ifndef DPCS_POSE_MINB
 #define DPCS_POSE_MINB 4  // resident blocks per SM asked of ptxas for the path-tracing pose kernels
 #endif
@@ -400,17 +405,19 @@ __global__ void __launch_bounds__(kPoseBlock, DPCS_POSE_MINB) k_pose_sil(const R
     block_partial(acc, p.partial + 6 * (int64_t)blockIdx.x);
 }
 
-// wrench[6 term + c] += sum over the term's blocks of partial component c,
-// blocks in increasing order
+// wrench[6 term + c] += the sum of the term's block partials of component
+// c: one warp per (term, c), lane l adding blocks l, l + 32, ... in order,
+// then a fixed shuffle tree (the same order on every call)
 __global__ void k_pose_reduce(const double *__restrict__ partial, int gmax, int g0, int g1, int g2,
                               double *__restrict__ wrench) {
-    const int t = threadIdx.x;
+    const int t = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (t >= 18) return;
     const int term = t / 6, c = t % 6;
     const int g = term == 0 ? g0 : (term == 1 ? g1 : g2);
     double s = 0.0;
-    for (int b = 0; b < g; ++b) s += partial[((int64_t)term * gmax + b) * 6 + c];
-    wrench[t] += s;
+    for (int b = lane; b < g; b += 32) s += partial[((int64_t)term * gmax + b) * 6 + c];
+    for (int off = 16; off; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+    if (lane == 0) wrench[t] += s;
 }
 
 }  // namespace
@@ -426,10 +433,12 @@ int launch_pose(const RenderArgs &a, const PoseArgs &p, int device, double *wren
     if (gmax <= 0) return DPCS_ERR_CUDA;
     const int64_t npix = (int64_t)a.Hc * a.Wc;
     const int64_t total[3] = {npix * a.spp, npix * p.edge_spp, p.edges ? p.nedges * p.sil_spp : 0};
+    const int per_sm[3] = {kPoseGridInterior, kPoseGridEdges, kPoseGridSil};
     int g[3];
     for (int k = 0; k < 3; ++k) {
         const int64_t need = (total[k] + kPoseBlock - 1) / kPoseBlock;
-        g[k] = (int)(need < gmax ? need : gmax);
+        const int64_t cap = (int64_t)gmax / kPoseBlocksPerSM * per_sm[k];
+        g[k] = (int)(need < cap ? need : cap);
     }
     int nl = 0;
     PoseArgs q = p;
@@ -448,7 +457,7 @@ int launch_pose(const RenderArgs &a, const PoseArgs &p, int device, double *wren
         k_pose_sil<<<g[2], kPoseBlock, 0, st>>>(a, q);
         ++nl;
     }
-    k_pose_reduce<<<1, 32, 0, st>>>(p.partial, gmax, g[0], g[1], g[2], wrench);
+    k_pose_reduce<<<1, 18 * 32, 0, st>>>(p.partial, gmax, g[0], g[1], g[2], wrench);
     return nl + 1;
 }
 
