@@ -998,7 +998,8 @@ def main():
             if rate >= 8.0:  # the deadline policies beside the default fixed share
                 dl = serving.run_server(ctx, gs, host, wl, **deadline)
                 entry["server_deadline_policy"] = {k: dl[k] for k in keep}
-                qd = serving.run_server(ctx, gs, host, wl, **dict(deadline, policy=dpcs.DPCS_SERVE_QUANTA_DEADLINE))
+                qd = serving.run_server(ctx, gs, host, wl, **dict(deadline, policy=dpcs.DPCS_SERVE_QUANTA_DEADLINE,
+                                                                  compensation_slack=0.1))
                 entry["server_quanta_deadline_policy"] = {k: qd[k] for k in keep}
             sweep.append(entry)
         sat = serving.make_workload(args.serve_requests, rate=0.0, seed=200 + rank)
@@ -1012,7 +1013,8 @@ def main():
                         "10% compensation (50 Adam steps, 16 spp); Poisson arrivals",
             "policy": "server = fixed share (relighting quanta, compensation within half of each iteration); "
                       "server_deadline_policy = earliest deadline first, slack 4 (relight) and 0.5 (compensation); "
-                      "server_quanta_deadline_policy = the relighting quanta, then the deadline order",
+                      "server_quanta_deadline_policy = the relighting quanta, then the deadline order, slack 4 "
+                      "(relight) and 0.1 (compensation)",
             "load_sweep": sweep,
             "saturated": {"server_requests_per_s": srv_sat["requests_per_s"],
                           "per_call_requests_per_s": per_sat["requests_per_s"],
