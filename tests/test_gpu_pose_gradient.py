@@ -217,3 +217,15 @@ def test_pose_wrench_at_the_benchmark_size(orc):
         assert np.all(err <= 1e-2 * np.abs(ref[t]).max() + 1e-6 * scale), (name, got[t], ref[t])
     tot_g, tot_r = got.sum(0), ref.sum(0)
     assert np.all(np.abs(tot_g - tot_r) <= 1e-2 * np.abs(tot_r).max()), (tot_g, tot_r)
+
+
+def test_pose_wrench_degenerate_cases():
+    """A zero dLoss/dIc, and a scene without triangles, give a zero wrench."""
+    torch = need_cuda()
+    sc = _occluder(16)
+    got = _gpu(sc, np.zeros((sc.Hc, sc.Wc, 3)), 8, 8)
+    assert np.all(got == 0.0)
+    empty = sc.replace(verts=np.zeros((0, 3), np.float32), tris=np.zeros((0, 3), np.int32),
+                       uv=np.zeros((0, 2), np.float32))
+    got = _gpu(empty, np.ones((sc.Hc, sc.Wc, 3)), 8, 8)
+    assert np.all(got == 0.0)
