@@ -1500,10 +1500,30 @@ static d3 vert_at(const float *verts, int32_t i) { return mk(verts[3 * i], verts
  * skipped.
  * Returns 0, or -1 on bad arguments.
  */
+int or_pose_backward_m(const float *verts, const int32_t *tris, int32_t T, const float *uv, const double *albedo,
+                       const double *rough, const double *metal, const double *nmap, int32_t Ht, int32_t Wt,
+                       const double *Ip, const or_view *Vw, const or_params *P, int32_t spp, int32_t bounces,
+                       uint64_t seed, const double *dEc, int32_t n_tw, const double *tw, int32_t edge_spp,
+                       int32_t sil_spp, double *out, int32_t nthreads);
+
 int or_pose_backward(const float *verts, const int32_t *tris, int32_t T, const float *uv, const double *albedo,
                      const double *rough, int32_t Ht, int32_t Wt, const double *Ip, const or_view *Vw,
                      const or_params *P, int32_t spp, int32_t bounces, uint64_t seed, const double *dEc, int32_t n_tw,
                      const double *tw, int32_t edge_spp, int32_t sil_spp, double *out, int32_t nthreads)
+{
+    return or_pose_backward_m(verts, tris, T, uv, albedo, rough, NULL, NULL, Ht, Wt, Ip, Vw, P, spp, bounces, seed,
+                              dEc, n_tw, tw, edge_spp, sil_spp, out, nthreads);
+}
+
+/* the same with the principled material's metallic (Ht x Wt) and normal
+ * (Ht x Wt x 3) maps, each optional (NULL): the first vertex's BRDF is the
+ * principled one at its shading normal, which the pose moves with the
+ * surface */
+int or_pose_backward_m(const float *verts, const int32_t *tris, int32_t T, const float *uv, const double *albedo,
+                       const double *rough, const double *metal, const double *nmap, int32_t Ht, int32_t Wt,
+                       const double *Ip, const or_view *Vw, const or_params *P, int32_t spp, int32_t bounces,
+                       uint64_t seed, const double *dEc, int32_t n_tw, const double *tw, int32_t edge_spp,
+                       int32_t sil_spp, double *out, int32_t nthreads)
 {
     if (spp <= 0 || bounces < 1 || bounces > OR_MAX_VERTS || Ht <= 0 || Wt <= 0 || Vw->Hp <= 0 || Vw->Wp <= 0 ||
         n_tw < 1 || n_tw > 16 || edge_spp < 0 || sil_spp < 0)
@@ -1516,6 +1536,8 @@ int or_pose_backward(const float *verts, const int32_t *tris, int32_t T, const f
     or_prf(Ip, ntex, P, Ep);
     rctx C;
     rctx_make(&C, &S, albedo, rough, Ht, Wt, Ep, Vw, P, spp, bounces, seed);
+    C.metal = metal;
+    C.nmap = nmap;
     const int32_t Hc = Vw->Hc, Wc = Vw->Wc;
     const int64_t npix = (int64_t)Hc * Wc;
     double acc[3][16];

@@ -67,6 +67,7 @@ def load():
         _lib.or_render_m.restype = ctypes.c_int
         _lib.or_render_backward_m.restype = ctypes.c_int
         _lib.or_pose_backward.restype = ctypes.c_int
+        _lib.or_pose_backward_m.restype = ctypes.c_int
         _lib.or_gbuffer.restype = ctypes.c_int
         _lib.or_num_threads.restype = ctypes.c_int
         _lib.or_num_threads.argtypes = [ctypes.c_int]
@@ -322,21 +323,24 @@ def crf_grad(Ec, params):
 
 
 def pose_backward(sc, dEc, twists, edge_spp, sil_spp, *, albedo=None, rough=None, Ip=None, params=None, spp=None,
-                  bounces=None, seed=None, nthreads: int = 0, accel: bool = False):
+                  bounces=None, seed=None, nthreads: int = 0, accel: bool = False, metallic=None, normal=None):
     """FP64 gradient of a loss with dLoss/dEc = ``dEc`` (Hc, Wc, 3) with
     respect to camera-pose parameters, each given by the twist (a, b) of the
     scene's motion in the camera frame (a point y moves with a x y + b);
     ``twists`` is (K, 6).  Returns (3, K): the interior, pixel-edge and
-    silhouette terms (their sum is the gradient).  Plain material only."""
+    silhouette terms (their sum is the gradient).  ``metallic`` (Ht, Wt) and
+    ``normal`` (Ht, Wt, 3) select the principled material (default: none)."""
     verts, tris, uv, albedo, rough, Ip = _scene_args(sc, albedo, rough, Ip)
+    m, nm = _maps(sc, metallic, normal, albedo.shape[0], albedo.shape[1])
     P = make_params(params or sc.params)
     V = make_view(sc)
     dEc = _c(dEc, np.float64).reshape(sc.Hc * sc.Wc, 3)
     tw = _c(twists, np.float64).reshape(-1, 6)
     out = np.zeros(3 * len(tw))
     with _Accel(accel):
-        rc = load().or_pose_backward(
+        rc = load().or_pose_backward_m(
             _p(verts), _p(tris), ctypes.c_int32(len(tris)), _p(uv), _p(albedo), _p(rough),
+            None if m is None else _p(m), None if nm is None else _p(nm),
             ctypes.c_int32(albedo.shape[0]), ctypes.c_int32(albedo.shape[1]), _p(Ip), ctypes.byref(V), ctypes.byref(P),
             ctypes.c_int32(spp or sc.spp), ctypes.c_int32(sc.bounces if bounces is None else bounces),
             ctypes.c_uint64(sc.seed if seed is None else seed), _p(dEc), ctypes.c_int32(len(tw)), _p(tw),

@@ -173,3 +173,54 @@ def test_rotation_about_the_camera_centre_has_no_silhouette_term(orc):
     out = orc.pose_backward(sc, W, tw, 0, 64, spp=4, seed=0)
     assert np.abs(out[2]).max() <= 1e-6 * np.abs(out[0]).max()
     assert np.abs(out[0]).max() > 0.0
+
+
+def _principled_plane():
+    res = 16
+    sc = scenes.plane(res=res)
+    return sc.replace(Ip=np.full((res, res, 3), 0.6, np.float32), albedo=np.full((8, 8, 3), 0.5, np.float32),
+                      rough=np.full((8, 8), 0.3, np.float32), Kp=scenes.intrinsics(res, res, 80.0),
+                      params=scenes.Params(gamma_p=(2.2,) * 3, gain_p=1.1, k_proj=1.3, ks=0.8, f0=0.04, jitter=1))
+
+
+def test_flat_principled_maps_reproduce_the_plain_pose_gradient(orc):
+    """Metallic 0 and the normal map (0.5, 0.5, 1) are the plain material:
+    the same gradient up to rounding."""
+    sc = _posed(_principled_plane(), np.array([0.01, 0.0, -0.02, 0.005, 0.0, 0.01]), np.eye(3), np.zeros(3))
+    W = np.random.default_rng(4).uniform(0.5, 1.5, (sc.Hc, sc.Wc, 3))
+    tw = pose.twists(np.zeros(6))
+    plain = orc.pose_backward(sc, W, tw, 16, 16, spp=16, seed=3)
+    flat = orc.pose_backward(sc, W, tw, 16, 16, spp=16, seed=3, metallic=np.zeros((8, 8)),
+                             normal=np.tile([0.5, 0.5, 1.0], (8, 8, 1)))
+    np.testing.assert_allclose(flat, plain, rtol=1e-9, atol=1e-12 * np.abs(plain).max())
+
+
+def test_principled_pose_gradient_matches_common_random_number_differences(orc):
+    """With a metallic map and a tilted normal map the first vertex's BRDF
+    and its turn with the camera change; the gradient still equals the
+    central differences of the oracle's renders at the same keys (the
+    posed plane has no silhouette in view, so the differences are smooth)."""
+    base = _principled_plane()
+    m = np.full((8, 8), 0.6)
+    nm = np.tile([0.62, 0.42, 0.9], (8, 8, 1))
+    W = np.random.default_rng(5).uniform(0.5, 1.5, (base.Hc, base.Wc, 3))
+    R0, t0 = pose.rotation([0.02, -0.03, 0.1]), np.array([0.01, 0.02, 0.05])
+    xi, h, spp, nseed = np.zeros(6), 2e-3, 4096, 4
+    tw = pose.twists(xi, R0, t0)
+    fd, est = [], []
+    for seed in range(nseed):
+        row = []
+        for k in range(6):
+            e = np.zeros(6)
+            e[k] = h
+            Ep, _ = orc.render(_posed(base, xi + e, R0, t0), spp=spp, seed=seed, metallic=m, normal=nm)
+            Em, _ = orc.render(_posed(base, xi - e, R0, t0), spp=spp, seed=seed, metallic=m, normal=nm)
+            row.append(np.sum(W * (Ep - Em)) / (2.0 * h))
+        fd.append(row)
+        est.append(orc.pose_backward(_posed(base, xi, R0, t0), W, tw, 64, 0, spp=256, seed=seed, metallic=m,
+                                     normal=nm).sum(0))
+    fd, est = np.array(fd), np.array(est)
+    se = (fd.std(0, ddof=1) + est.std(0, ddof=1)) / math.sqrt(nseed)
+    scale = np.abs(fd.mean(0)).max()
+    assert scale > 1.0
+    assert np.all(np.abs(est.mean(0) - fd.mean(0)) <= 5.0 * se + 2e-3 * scale), (est.mean(0), fd.mean(0), se)
