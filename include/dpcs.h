@@ -374,7 +374,8 @@ dpcs_status dpcs_render_backward(dpcs_ctx *ctx, dpcs_scene scene, const float *a
  * Output, ACCUMULATED (+=):
  *  wrench   : dev, 18 float64: interior, pixel-edge and silhouette terms,
  *             each (W_a[3], W_b[3]); their sum is W.
- * The plain material only (no metallic or normal map).  Kc's last row must
+ * The plain material (dpcs_pose_backward_principled below takes the
+ * metallic and normal maps).  Kc's last row must
  * be (0, 0, k) with k > 0.  The first call with sil_spp > 0 on a scene builds
  * its edge table on the host (one stream synchronisation); later calls,
  * updates and transforms reuse it.  Results repeat bit for bit for the same
@@ -483,6 +484,20 @@ dpcs_status dpcs_render_loss_backward_principled(dpcs_ctx *ctx, dpcs_scene scene
                                                  int32_t loss_kind, float scale, float *Ic, float *Ec, float *loss,
                                                  float *dIp, float *dAlbedo, float *dRough, float *dMetallic,
                                                  float *dNormal, float *dParams, void *stream);
+
+/*
+ * dpcs_pose_backward with the principled material (Sec. 3.2: metallic m
+ * and normal map Vn among theta, with the pose): the first vertex's BRDF
+ * and its turn with the camera are the principled lobe's at the shading
+ * normal, which moves with the surface.  mat as for dpcs_render_principled
+ * (metallic and normal may be NULL); the other arguments and the output as
+ * for dpcs_pose_backward.
+ */
+dpcs_status dpcs_pose_backward_principled(dpcs_ctx *ctx, dpcs_scene scene, const dpcs_material *mat, const float *Ip,
+                                          const dpcs_view *view, const dpcs_params *params, int32_t spp,
+                                          int32_t bounces, uint64_t seed, const float *Ec, const float *Ic,
+                                          const float *dIc, int32_t edge_spp, int32_t sil_spp, double *wrench,
+                                          void *stream);
 
 typedef struct dpcs_denoise_params {
     int32_t radius;      /* window half-width r, 0..8 (0 = identity) */

@@ -1265,11 +1265,14 @@ dpcs_status dpcs_adam(dpcs_ctx *c, float *p, const float *g, float *m, float *v,
                         "adam");
 }
 
-dpcs_status dpcs_pose_backward(dpcs_ctx *c, dpcs_scene scene, const float *albedo, const float *rough, int32_t Ht,
-                               int32_t Wt, const float *Ip, const dpcs_view *view, const dpcs_params *params,
-                               int32_t spp, int32_t bounces, uint64_t seed, const float *Ec, const float *Ic,
-                               const float *dIc, int32_t edge_spp, int32_t sil_spp, double *wrench, void *stream) {
-    Range range("dpcs_pose_backward");
+// the pose adjoint of dpcs_pose_backward and dpcs_pose_backward_principled
+// (pbr: the metallic and normal maps, each optional, are packed and used)
+static dpcs_status pose_backward_impl(dpcs_ctx *c, dpcs_scene scene, const float *albedo, const float *rough,
+                                      bool pbr, const float *metallic, const float *normal, int32_t Ht, int32_t Wt,
+                                      const float *Ip, const dpcs_view *view, const dpcs_params *params, int32_t spp,
+                                      int32_t bounces, uint64_t seed, const float *Ec, const float *Ic,
+                                      const float *dIc, int32_t edge_spp, int32_t sil_spp, double *wrench,
+                                      void *stream) {
     RenderArgs a;
     Scene *sc = nullptr;
     dpcs_status s = prepare(c, scene, albedo, rough, Ht, Wt, Ip, view, params, spp, bounces, seed, a, &sc);
@@ -1294,10 +1297,12 @@ dpcs_status dpcs_pose_backward(dpcs_ctx *c, dpcs_scene scene, const float *albed
         (s = ensure(c, c->tex4, (size_t)nt * 16, "texture scratch")) ||
         (s = ensure(c, c->gE, (size_t)npix * 12, "dEc scratch")) ||
         (s = ensure(c, c->acc, 16 * sizeof(double), "parameter accumulators")) ||
-        (s = ensure(c, c->pose, (size_t)3 * gmax * 6 * sizeof(double), "pose partial sums")))
+        (s = ensure(c, c->pose, (size_t)3 * gmax * 6 * sizeof(double), "pose partial sums")) ||
+        (pbr && (s = ensure(c, c->mat4, (size_t)nt * 16, "material scratch"))))
         return s;
     int nl = launch_prf(Ip, np, params->gamma_p, params->gain_p, (float4 *)c->ep4.p, st);
     nl += launch_pack_tex(albedo, rough, nt, (float4 *)c->tex4.p, st);
+    if (pbr) nl += launch_pack_mat(metallic, normal, nt, (float4 *)c->mat4.p, st);
     // dLoss/dEc through Eq. 5 (the response-parameter sums it also forms are not used)
     nl += launch_crf_backward(dIc, Ec, Ic, npix, params->gamma_c, params->gain_c, params->wb, (float *)c->gE.p,
                               (double *)c->acc.p, st);
@@ -1311,11 +1316,33 @@ dpcs_status dpcs_pose_backward(dpcs_ctx *c, dpcs_scene scene, const float *albed
     p.edges = tab ? tab->d : nullptr;
     p.nedges = tab ? tab->n : 0;
     p.partial = (double *)c->pose.p;
+    p.mat = pbr ? (const float4 *)c->mat4.p : nullptr;
     TimedLaunch *tl = timing_begin(c, 2, st);
     const int np2 = launch_pose(a, p, c->device, wrench, st);
     timing_end(tl, st);
     if (np2 < 0) return check_launch(c, np2, "pose_backward");
     return check_launch(c, nl + np2, "pose_backward");
+}
+
+dpcs_status dpcs_pose_backward(dpcs_ctx *c, dpcs_scene scene, const float *albedo, const float *rough, int32_t Ht,
+                               int32_t Wt, const float *Ip, const dpcs_view *view, const dpcs_params *params,
+                               int32_t spp, int32_t bounces, uint64_t seed, const float *Ec, const float *Ic,
+                               const float *dIc, int32_t edge_spp, int32_t sil_spp, double *wrench, void *stream) {
+    Range range("dpcs_pose_backward");
+    return pose_backward_impl(c, scene, albedo, rough, false, nullptr, nullptr, Ht, Wt, Ip, view, params, spp,
+                              bounces, seed, Ec, Ic, dIc, edge_spp, sil_spp, wrench, stream);
+}
+
+dpcs_status dpcs_pose_backward_principled(dpcs_ctx *c, dpcs_scene scene, const dpcs_material *mat, const float *Ip,
+                                          const dpcs_view *view, const dpcs_params *params, int32_t spp,
+                                          int32_t bounces, uint64_t seed, const float *Ec, const float *Ic,
+                                          const float *dIc, int32_t edge_spp, int32_t sil_spp, double *wrench,
+                                          void *stream) {
+    Range range("dpcs_pose_backward_principled");
+    if (!c) return DPCS_ERR_INVALID_ARG;
+    if (!mat) return fail(c, DPCS_ERR_INVALID_ARG, "null material");
+    return pose_backward_impl(c, scene, mat->albedo, mat->rough, true, mat->metallic, mat->normal, mat->Ht, mat->Wt,
+                              Ip, view, params, spp, bounces, seed, Ec, Ic, dIc, edge_spp, sil_spp, wrench, stream);
 }
 
 }  // extern "C"

@@ -46,6 +46,7 @@
 #include "device.cuh"
 #include "internal.h"
 #include "pose.h"
+#include "principled.cuh"
 
 namespace dpcs {
 
@@ -101,6 +102,37 @@ __device__ f3 spec_grad_wo(f3 n, f3 wo, f3 wi, float r, float ks, float f0) {
     return g;
 }
 
+// The principled lobe's pieces as functions of wo (a free vector), at the
+// shading normal n: S = ks D G1(ci) G1(co) / (4 ci co) and s5 = (1 - wo.h)^5,
+// so that f_j = (1 - m) rho_j / pi + S F_j with F_j = F0_j + (1 - F0_j) s5
+// has grad f_j = F_j grad S + S (1 - F0_j) grad s5.  Zero where the lobe is
+// off (wo or wi below the shading hemisphere) or ks = 0.
+__device__ void plobe_grad_wo(f3 n, f3 wo, f3 wi, float r, float ks, f3 &gS, f3 &gs5) {
+    gS = gs5 = mk3(0.f, 0.f, 0.f);
+    const float co = dot(n, wo), ci = dot(n, wi);
+    if (ks <= 0.0f || co <= 0.0f || ci <= 0.0f) return;
+    float dadr;
+    const float a = alpha_of(r, dadr);
+    const float a2 = a * a;
+    const f3 hu = wo + wi;
+    const float il = 1.0f / sqrtf(dot(hu, hu));
+    const f3 h = hu * il;
+    const float ch = dot(n, h);
+    const float t = sin2(n, h) + a2 * ch * ch;
+    const float D = a2 / (DPCS_PI_F * t * t);
+    const float si = sqrtf(a2 + (1.0f - a2) * ci * ci), so = sqrtf(a2 + (1.0f - a2) * co * co);
+    const float S = ks * D * (2.0f * ci / (ci + si)) * (2.0f * co / (co + so)) / (4.0f * ci * co);
+    const float dlnD = -4.0f * ch * (a2 - 1.0f) / t;                 // d ln D / d ch
+    const float dlnGc = -(1.0f + (1.0f - a2) * co / so) / (co + so);  // d ln(G1(co) / co) / d co
+    gS = (n - h * ch) * (S * dlnD * il) + n * (S * dlnGc);
+    const float woh = dot(wo, h);
+    const float m = 1.0f - woh;
+    if (m > 0.0f) {
+        const float m2 = m * m;
+        gs5 = (h + (wo - h * woh) * il) * (-5.0f * m2 * m2);
+    }
+}
+
 __device__ __forceinline__ f3 krow(const float *K, int r) { return mk3(K[3 * r], K[3 * r + 1], K[3 * r + 2]); }
 
 // row c (0: x, 1: y) of the Jacobian of s = (K y)_xy / (K y)_z at y
@@ -123,11 +155,16 @@ __device__ __forceinline__ f3 proj_row(const float *K, f3 y, int c) {
 //   Ai, Pi the later vertices carry f(wo, wi) of the first one: Ai sums
 //          g_j c_j / f_j(wo, wi) over their unclipped channels, and Pi is
 //          the turn of wo applied to the gradient of f's GGX part.
+// With the principled material grad f_j differs between channels (F_j and
+// F0_j do), so Ai is kept per channel (Ai3) and the continuation's turn is
+// kept as the turns of grad S and grad s5 (PiS, Pis5) with their channel
+// weights F_j and S (1 - F0_j) at wi (cF, cS5).
 struct Walk {
     int nv;        // vertices (0: the first ray left the scene)
     f3 x, L;
     float S, Ai;
     f3 Acoef, Bcoef, Qp, Pi, gf;  // gf_j = g_j / f_j(wo, wi) of the first vertex
+    f3 Ai3, PiS, Pis5, cF, cS5;   // principled material
     bool lit;
 };
 
@@ -139,12 +176,15 @@ __device__ __forceinline__ f3 wo_turn(f3 v, f3 wo, float ilx) { return (v - wo *
 // One traversal per loop iteration -- the closest hit of the current ray or
 // the shadow ray of the last vertex's light -- so that the lanes of a warp
 // run the same traversal code whatever step their paths are at.
-template <bool kInterior>
-__device__ void pose_trace(const RenderArgs &a, const float *Kc, float g0, float g1, float g2, f3 o, f3 d,
-                           uint32_t pix, uint32_t s, Walk &W, Cnt &cnt) {
+// kPbr: the principled material (mat = its packed maps); otherwise the
+// plain Lambert + GGX material.
+template <bool kInterior, bool kPbr>
+__device__ void pose_trace(const RenderArgs &a, const float4 *__restrict__ mat, const float *Kc, float g0, float g1,
+                           float g2, f3 o, f3 d, uint32_t pix, uint32_t s, Walk &W, Cnt &cnt) {
     const f3 zero = mk3(0.f, 0.f, 0.f);
     W.nv = 0;
     W.x = W.L = W.Acoef = W.Bcoef = W.Qp = W.Pi = W.gf = zero;
+    W.Ai3 = W.PiS = W.Pis5 = W.cF = W.cS5 = zero;
     W.S = W.Ai = 0.0f;
     W.lit = false;
     f3 beta = mk3(1.f, 1.f, 1.f);
@@ -163,6 +203,9 @@ __device__ void pose_trace(const RenderArgs &a, const float *Kc, float g0, float
                     W.S += g0 * pc.x + g1 * pc.y + g2 * pc.z;
                     if (pfirst)
                         W.lit = true;
+                    else if constexpr (kPbr)
+                        W.Ai3 = W.Ai3 + mk3((punc & 1u) ? W.gf.x * pc.x : 0.f, (punc & 2u) ? W.gf.y * pc.y : 0.f,
+                                            (punc & 4u) ? W.gf.z * pc.z : 0.f);
                     else
                         W.Ai += ((punc & 1u) ? W.gf.x * pc.x : 0.f) + ((punc & 2u) ? W.gf.y * pc.y : 0.f) +
                                 ((punc & 4u) ? W.gf.z * pc.z : 0.f);
@@ -179,59 +222,138 @@ __device__ void pose_trace(const RenderArgs &a, const float *Kc, float g0, float
             continue;
         }
         if (!hit) break;
-        const Surf S = surface_at(a, h, ray.d);
-        pfirst = W.nv == 0;
-        ++W.nv;
-        float ilx = 0.0f;
-        if (pfirst) {
-            W.x = S.x;
-            if constexpr (kInterior) {
-                ilx = 1.0f / sqrtf(dot(S.x, S.x));
-                // d log J = n.b / n.x - 3 k2.(a x x + b) / k2.x, k2 = Kc's third row
-                const f3 k2 = krow(Kc, 2);
-                const float w = 3.0f / dot(k2, S.x);
-                W.Acoef = cross(S.x, k2) * (-w);
-                W.Bcoef = S.n * (1.0f / dot(S.n, S.x)) - k2 * w;
+        bool cand;
+        f3 sh_o, sh_d;  // shadow ray of the vertex's light (when cand)
+        float sh_max = 0.0f;
+        if constexpr (kPbr) {
+            const PSurf S = psurface_at(a, mat, h, ray.d);
+            pfirst = W.nv == 0;
+            ++W.nv;
+            float ilx = 0.0f;
+            if (pfirst) {
+                W.x = S.x;
+                if constexpr (kInterior) {
+                    ilx = 1.0f / sqrtf(dot(S.x, S.x));
+                    const f3 k2 = krow(Kc, 2);
+                    const float w = 3.0f / dot(k2, S.x);
+                    W.Acoef = cross(S.x, k2) * (-w);
+                    W.Bcoef = S.n * (1.0f / dot(S.n, S.x)) - k2 * w;
+                }
             }
-        }
-        Nee N;
-        const bool cand = nee_prepare(a, S, N);
-        if (cand) {
-            pc = nee_contrib(a, beta, N, punc);
-            if constexpr (kInterior) {
-                if (pfirst) {
-                    const float Ap = (((punc & 1u) ? g0 * N.ep.x : 0.f) + ((punc & 2u) ? g1 * N.ep.y : 0.f) +
-                                      ((punc & 4u) ? g2 * N.ep.z : 0.f)) * N.G;  // throughput 1 at the first vertex
-                    if (Ap != 0.0f) {
-                        const f3 cp = mk3(a.cp[0], a.cp[1], a.cp[2]);
-                        const f3 v = spec_grad_wo(S.n, S.wo, normalize(cp - S.x), S.rough, a.ks, a.f0);
-                        W.Qp = wo_turn(v, S.wo, ilx) * Ap;
+            PNee N;
+            cand = pnee_prepare(a, S, N);
+            if (cand) {
+                pc = beta * N.fp * mk3(N.ep.x, N.ep.y, N.ep.z) * N.G;
+                punc = 7u;
+                if (a.clip > 0.0f) {
+                    if (pc.x > a.clip) { pc.x = a.clip; punc &= ~1u; }
+                    if (pc.y > a.clip) { pc.y = a.clip; punc &= ~2u; }
+                    if (pc.z > a.clip) { pc.z = a.clip; punc &= ~4u; }
+                }
+                sh_o = N.so;
+                sh_d = N.sdir;
+                sh_max = N.smax;
+                if constexpr (kInterior) {
+                    if (pfirst && N.L.on > 0.0f) {
+                        // weights g_j unc_j Ep_j G of grad f_j = F_j grad S + S (1 - F0_j) grad s5
+                        const f3 wgt = mk3((punc & 1u) ? g0 * N.ep.x : 0.f, (punc & 2u) ? g1 * N.ep.y : 0.f,
+                                           (punc & 4u) ? g2 * N.ep.z : 0.f) * N.G;
+                        const f3 F0 = S.rho * S.m + mk3(1.f, 1.f, 1.f) * ((1.0f - S.m) * a.f0);
+                        const f3 F = F0 + (mk3(1.f, 1.f, 1.f) - F0) * N.L.s5;
+                        const float cS = dot(wgt, F), cs5 = N.L.S * dot(wgt, mk3(1.f, 1.f, 1.f) - F0);
+                        if (cS != 0.0f || cs5 != 0.0f) {
+                            const f3 cp = mk3(a.cp[0], a.cp[1], a.cp[2]);
+                            f3 gS, gs5;
+                            plobe_grad_wo(S.ns, S.wo, normalize(cp - S.x), S.rough, a.ks, gS, gs5);
+                            W.Qp = wo_turn(gS, S.wo, ilx) * cS + wo_turn(gs5, S.wo, ilx) * cs5;
+                        }
                     }
                 }
             }
-        }
-        has_ext = false;
-        if (b < a.bounces) {
-            Cont C;
-            if (continue_prepare(a, pix, s, b, S, C)) {
+            has_ext = false;
+            if (b < a.bounces) {
+                PCont C;
+                if (pcontinue_prepare(a, pix, s, b, S, C)) {
+                    if constexpr (kInterior) {
+                        if (pfirst) {
+                            const f3 fi = pbrdf(S.rho, S.m, a.f0, C.L);
+                            W.gf = mk3(fi.x > 0.f ? g0 / fi.x : 0.f, fi.y > 0.f ? g1 / fi.y : 0.f,
+                                       fi.z > 0.f ? g2 / fi.z : 0.f);
+                            const f3 F0 = S.rho * S.m + mk3(1.f, 1.f, 1.f) * ((1.0f - S.m) * a.f0);
+                            W.cF = (F0 + (mk3(1.f, 1.f, 1.f) - F0) * C.L.s5) * C.L.on;
+                            W.cS5 = (mk3(1.f, 1.f, 1.f) - F0) * (C.L.S * C.L.on);
+                            f3 gS, gs5;
+                            plobe_grad_wo(S.ns, S.wo, C.wi, S.rough, a.ks, gS, gs5);
+                            W.PiS = wo_turn(gS, S.wo, ilx);
+                            W.Pis5 = wo_turn(gs5, S.wo, ilx);
+                        }
+                    }
+                    beta = beta * C.w;
+                    ext_o = S.x + S.n * kRayEps;
+                    ext_d = C.wi;
+                    has_ext = true;
+                }
+            }
+        } else {
+            const Surf S = surface_at(a, h, ray.d);
+            pfirst = W.nv == 0;
+            ++W.nv;
+            float ilx = 0.0f;
+            if (pfirst) {
+                W.x = S.x;
+                if constexpr (kInterior) {
+                    ilx = 1.0f / sqrtf(dot(S.x, S.x));
+                    // d log J = n.b / n.x - 3 k2.(a x x + b) / k2.x, k2 = Kc's third row
+                    const f3 k2 = krow(Kc, 2);
+                    const float w = 3.0f / dot(k2, S.x);
+                    W.Acoef = cross(S.x, k2) * (-w);
+                    W.Bcoef = S.n * (1.0f / dot(S.n, S.x)) - k2 * w;
+                }
+            }
+            Nee N;
+            cand = nee_prepare(a, S, N);
+            if (cand) {
+                pc = nee_contrib(a, beta, N, punc);
                 if constexpr (kInterior) {
                     if (pfirst) {
-                        const float f0c = S.rho.x * DPCS_INV_PI_F + C.si, f1c = S.rho.y * DPCS_INV_PI_F + C.si,
-                                    f2c = S.rho.z * DPCS_INV_PI_F + C.si;
-                        W.gf = mk3(f0c > 0.f ? g0 / f0c : 0.f, f1c > 0.f ? g1 / f1c : 0.f, f2c > 0.f ? g2 / f2c : 0.f);
-                        W.Pi = wo_turn(spec_grad_wo(S.n, S.wo, C.wi, S.rough, a.ks, a.f0), S.wo, ilx);
+                        const float Ap = (((punc & 1u) ? g0 * N.ep.x : 0.f) + ((punc & 2u) ? g1 * N.ep.y : 0.f) +
+                                          ((punc & 4u) ? g2 * N.ep.z : 0.f)) * N.G;  // throughput 1 at the first vertex
+                        if (Ap != 0.0f) {
+                            const f3 cp = mk3(a.cp[0], a.cp[1], a.cp[2]);
+                            const f3 v = spec_grad_wo(S.n, S.wo, normalize(cp - S.x), S.rough, a.ks, a.f0);
+                            W.Qp = wo_turn(v, S.wo, ilx) * Ap;
+                        }
                     }
                 }
-                beta = beta * C.w;
-                ext_o = S.x + S.n * kRayEps;
-                ext_d = C.wi;
-                has_ext = true;
+            }
+            has_ext = false;
+            if (b < a.bounces) {
+                Cont C;
+                if (continue_prepare(a, pix, s, b, S, C)) {
+                    if constexpr (kInterior) {
+                        if (pfirst) {
+                            const float f0c = S.rho.x * DPCS_INV_PI_F + C.si, f1c = S.rho.y * DPCS_INV_PI_F + C.si,
+                                        f2c = S.rho.z * DPCS_INV_PI_F + C.si;
+                            W.gf = mk3(f0c > 0.f ? g0 / f0c : 0.f, f1c > 0.f ? g1 / f1c : 0.f, f2c > 0.f ? g2 / f2c : 0.f);
+                            W.Pi = wo_turn(spec_grad_wo(S.n, S.wo, C.wi, S.rough, a.ks, a.f0), S.wo, ilx);
+                        }
+                    }
+                    beta = beta * C.w;
+                    ext_o = S.x + S.n * kRayEps;
+                    ext_d = C.wi;
+                    has_ext = true;
+                }
+            }
+            if (cand) {
+                sh_o = N.so;
+                sh_d = N.sdir;
+                sh_max = N.smax;
             }
         }
         if (cand) {
             shadow = true;
-            ray = make_ray(N.so, N.sdir);
-            tmax = N.smax;
+            ray = make_ray(sh_o, sh_d);
+            tmax = sh_max;
         } else if (has_ext) {
             ray = make_ray(ext_o, ext_d);
             tmax = INFINITY;
@@ -272,6 +394,7 @@ __device__ void block_partial(const float acc[6], double *out) {
 
 // Interior term, one item per camera sample (pixel i / spp, sample i % spp),
 // the sample's path as the render traces it.
+template <bool kPbr>
 __global__ void __launch_bounds__(kPoseBlock, DPCS_POSE_MINB) k_pose_interior(const RenderArgs a, const PoseArgs p) {
     float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     Cnt cnt;
@@ -287,9 +410,14 @@ __global__ void __launch_bounds__(kPoseBlock, DPCS_POSE_MINB) k_pose_interior(co
         f3 o, d;
         camera_ray(a, (uint32_t)pix, (uint32_t)s, o, d);
         Walk W;
-        pose_trace<true>(a, p.Kc, g0, g1, g2, o, d, (uint32_t)pix, (uint32_t)s, W, cnt);
+        pose_trace<true, kPbr>(a, p.mat, p.Kc, g0, g1, g2, o, d, (uint32_t)pix, (uint32_t)s, W, cnt);
         if (W.nv == 0) continue;
-        add6(acc, W.Acoef * W.S, W.Bcoef * W.S + (W.lit ? W.Qp : mk3(0.f, 0.f, 0.f)) + W.Pi * W.Ai);
+        f3 Qi;  // the continuation's BRDF factor, turned with wo
+        if constexpr (kPbr)
+            Qi = W.PiS * dot(W.Ai3, W.cF) + W.Pis5 * dot(W.Ai3, W.cS5);
+        else
+            Qi = W.Pi * W.Ai;
+        add6(acc, W.Acoef * W.S, W.Bcoef * W.S + (W.lit ? W.Qp : mk3(0.f, 0.f, 0.f)) + Qi);
     }
     block_partial(acc, p.partial + 6 * (int64_t)blockIdx.x);
 }
@@ -300,6 +428,7 @@ __global__ void __launch_bounds__(kPoseBlock, DPCS_POSE_MINB) k_pose_interior(co
 // (x0 + t, y0 + 1), top (x0 + t, y0), outward normals +x, -x, +y, -y -- and
 // the four paths share counter (Hc Wc + p, j, b, 0), so that the flux
 // through opposite edges is a common-random-number difference across P.
+template <bool kPbr>
 __global__ void __launch_bounds__(kPoseBlock, DPCS_POSE_MINB) k_pose_edges(const RenderArgs a, const PoseArgs p) {
     float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     Cnt cnt;
@@ -323,7 +452,7 @@ __global__ void __launch_bounds__(kPoseBlock, DPCS_POSE_MINB) k_pose_edges(const
             const float sy = k < 2 ? y0 + t : (k == 2 ? y0 + 1.0f : y0);
             const f3 d = normalize(mat3v(a.Kci, mk3(sx, sy, 1.0f)));
             Walk W;
-            pose_trace<false>(a, p.Kc, 0.f, 0.f, 0.f, mk3(0.f, 0.f, 0.f), d, vpix, (uint32_t)j, W, cnt);
+            pose_trace<false, kPbr>(a, p.mat, p.Kc, 0.f, 0.f, 0.f, mk3(0.f, 0.f, 0.f), d, vpix, (uint32_t)j, W, cnt);
             if (W.nv == 0) continue;
             // -(outward sign) g . L / edge_spp times V . n = m . (a x x + b),
             // m the Jacobian row across the edge
@@ -342,6 +471,7 @@ __global__ void __launch_bounds__(kPoseBlock, DPCS_POSE_MINB) k_pose_edges(const
 // vertex, u from counter (2 Hc Wc + k, j, 0, 0); it counts if
 // it lies in front of the camera, inside the image and in view, and the path
 // continuing behind it (B) draws the same counter's later bounces.
+template <bool kPbr>
 __global__ void __launch_bounds__(kPoseBlock, DPCS_POSE_MINB) k_pose_sil(const RenderArgs a, const PoseArgs p) {
     float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     Cnt cnt;
@@ -379,7 +509,7 @@ __global__ void __launch_bounds__(kPoseBlock, DPCS_POSE_MINB) k_pose_sil(const R
         const Ray vr = make_ray(mk3(0.f, 0.f, 0.f), d);
         if (traverse(a.nodes, a.tris, a.root, a.T, vr, dist * (1.0f - 1e-4f), true, hs, a.status, cnt)) continue;
         Walk W;
-        pose_trace<false>(a, p.Kc, 0.f, 0.f, 0.f, d * (dist * (1.0f + 1e-4f)), d, vpix, (uint32_t)j, W, cnt);
+        pose_trace<false, kPbr>(a, p.mat, p.Kc, 0.f, 0.f, 0.f, d * (dist * (1.0f + 1e-4f)), d, vpix, (uint32_t)j, W, cnt);
         if (W.nv == 0) continue;
         const int64_t px = (int64_t)floorf(sy) * Wc + (int64_t)floorf(sx);
         const float gl = W.L.x * a.gE[3 * px] + W.L.y * a.gE[3 * px + 1] + W.L.z * a.gE[3 * px + 2];
@@ -442,19 +572,29 @@ int launch_pose(const RenderArgs &a, const PoseArgs &p, int device, double *wren
     }
     int nl = 0;
     PoseArgs q = p;
+    const bool pbr = p.mat != nullptr;
     if (g[0] > 0) {
         q.partial = p.partial;
-        k_pose_interior<<<g[0], kPoseBlock, 0, st>>>(a, q);
+        if (pbr)
+            k_pose_interior<true><<<g[0], kPoseBlock, 0, st>>>(a, q);
+        else
+            k_pose_interior<false><<<g[0], kPoseBlock, 0, st>>>(a, q);
         ++nl;
     }
     if (g[1] > 0) {
         q.partial = p.partial + (size_t)gmax * 6;
-        k_pose_edges<<<g[1], kPoseBlock, 0, st>>>(a, q);
+        if (pbr)
+            k_pose_edges<true><<<g[1], kPoseBlock, 0, st>>>(a, q);
+        else
+            k_pose_edges<false><<<g[1], kPoseBlock, 0, st>>>(a, q);
         ++nl;
     }
     if (g[2] > 0) {
         q.partial = p.partial + (size_t)2 * gmax * 6;
-        k_pose_sil<<<g[2], kPoseBlock, 0, st>>>(a, q);
+        if (pbr)
+            k_pose_sil<true><<<g[2], kPoseBlock, 0, st>>>(a, q);
+        else
+            k_pose_sil<false><<<g[2], kPoseBlock, 0, st>>>(a, q);
         ++nl;
     }
     k_pose_reduce<<<1, 18 * 32, 0, st>>>(p.partial, gmax, g[0], g[1], g[2], wrench);

@@ -24,6 +24,7 @@ struct PoseArgs {
     const PoseEdge *edges;  // mesh edges (null when sil_spp == 0)
     int64_t nedges;
     double *partial;        // 3 x pose_grid(device) x 6 per-block sums
+    const float4 *mat;      // the principled material's packed maps (metallic, normal map), or null: plain
 };
 
 // blocks of each pose kernel on this device (its partial sums are 6 per block)

@@ -44,7 +44,7 @@ EXPORTED = [
     "dpcs_render_backward_kept", "dpcs_render_principled", "dpcs_render_backward_principled",
     "dpcs_scene_transform", "dpcs_render_loss_backward_principled", "dpcs_render_keep_principled",
     "dpcs_render_backward_kept_principled", "dpcs_set_grad_accum", "dpcs_set_render_path", "dpcs_pose_backward",
-    "dpcs_set_bvh_builder",
+    "dpcs_set_bvh_builder", "dpcs_pose_backward_principled",
 ]
 
 DPCS_REQ_RELIGHT = 0
@@ -157,6 +157,10 @@ _SIGS = {
                                             ctypes.POINTER(DpcsView), ctypes.POINTER(DpcsParams), ctypes.c_int32,
                                             ctypes.c_int32, ctypes.c_uint64, _P, _P, _P, ctypes.c_int32,
                                             ctypes.c_int32, _P, _P]),
+    "dpcs_pose_backward_principled": (ctypes.c_int32, [_P, ctypes.c_uint64, ctypes.POINTER(DpcsMaterial), _P,
+                                                       ctypes.POINTER(DpcsView), ctypes.POINTER(DpcsParams),
+                                                       ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, _P, _P, _P,
+                                                       ctypes.c_int32, ctypes.c_int32, _P, _P]),
     "dpcs_render_loss_backward": (ctypes.c_int32, [_P, ctypes.c_uint64, _P, _P, ctypes.c_int32, ctypes.c_int32, _P,
                                                    ctypes.POINTER(DpcsView), ctypes.POINTER(DpcsParams),
                                                    ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, _P, ctypes.c_int32,
@@ -653,6 +657,27 @@ class Context:
             _ptr(Ic, "Ic", img, f32, self.device), _ptr(dIc, "dIc", img, f32, self.device), int(edge_spp),
             int(sil_spp), _ptr(wrench, "wrench", (3, 6), torch.float64, self.device), _stream(stream))
         self.check(st, "pose_backward")
+        return wrench
+
+    def pose_backward_principled(self, scene: int, albedo, rough, metallic, normal, Ip, view: DpcsView,
+                                 params: DpcsParams, spp: int, bounces: int, seed: int, Ec, Ic, dIc, edge_spp: int,
+                                 sil_spp: int, wrench=None, stream=None):
+        """``pose_backward`` with the principled material
+        (``dpcs_pose_backward_principled``); metallic / normal may be None."""
+        import torch
+
+        f32 = torch.float32
+        img = (view.Hc, view.Wc, 3)
+        if wrench is None:
+            wrench = torch.zeros((3, 6), dtype=torch.float64, device=self.device)
+        m = self._material(albedo, rough, metallic, normal)
+        st = self.lib.dpcs_pose_backward_principled(
+            self.handle, scene, ctypes.byref(m), _ptr(Ip, "Ip", (view.Hp, view.Wp, 3), f32, self.device),
+            ctypes.byref(view), ctypes.byref(params), int(spp), int(bounces), int(seed) & (2**64 - 1),
+            _ptr(Ec, "Ec", img, f32, self.device), _ptr(Ic, "Ic", img, f32, self.device),
+            _ptr(dIc, "dIc", img, f32, self.device), int(edge_spp), int(sil_spp),
+            _ptr(wrench, "wrench", (3, 6), torch.float64, self.device), _stream(stream))
+        self.check(st, "pose_backward_principled")
         return wrench
 
     # -- principled material (metallic and normal maps) --------------------------

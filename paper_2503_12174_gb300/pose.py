@@ -122,15 +122,14 @@ class PoseRefine:
     parameters stay fixed).  ``pairs`` is a list of (Ip, Ic) device tensors;
     ``metallic`` / ``normal`` select the principled material.
 
-    ``gradient="adjoint"`` (the plain material's default): each step moves
+    ``gradient="adjoint"`` (the default, either material): each step moves
     the scene to the pose, and per pair renders, takes the L1 term and calls
     ``dpcs_pose_backward`` (``edge_spp`` and ``sil_spp`` samples per pixel
     edge and per silhouette edge), then one Adam step on xi.  Its noise
     falls with the pixel count: small images want more edge samples (64 at
     48 x 48 pixels recovers the pose about as central differences do at
     higher cost; 16 suffices at 256 x 256).
-    ``gradient="differences"`` (the principled material's only choice):
-    thirteen pose evaluations per step, each a scene transform, K renders and
+    ``gradient="differences"``: thirteen pose evaluations per step, each a scene transform, K renders and
     K L1 terms, at xi and at xi +- h e_k."""
 
     def __init__(self, ctx: dpcs.Context, scene: int, view: dpcs.DpcsView, params: dpcs.DpcsParams, albedo, rough,
@@ -141,13 +140,11 @@ class PoseRefine:
 
         self.ctx, self.scene, self.view, self.params = ctx, scene, view, params
         self.albedo, self.rough, self.metallic, self.normal = albedo, rough, metallic, normal
-        principled = metallic is not None or normal is not None
+        self.principled = metallic is not None or normal is not None
         if gradient is None:
-            gradient = "differences" if principled else "adjoint"
+            gradient = "adjoint"
         if gradient not in ("adjoint", "differences"):
             raise ValueError("gradient must be 'adjoint' or 'differences'")
-        if gradient == "adjoint" and principled:
-            raise ValueError("the pose adjoint covers the plain material only")
         self.gradient = gradient
         self.edge_spp, self.sil_spp = int(edge_spp), int(sil_spp)
         self.pairs = list(pairs)
@@ -206,12 +203,21 @@ class PoseRefine:
         self.wrench.zero_()
         for i, (Ip, target) in enumerate(self.pairs):
             s = self._key(i)
-            c.render(self.scene, self.albedo, self.rough, Ip, v, self.params, self.spp, self.bounces, s, Ic=self.Ic,
-                     Ec=self.Ec)
+            if self.principled:
+                c.render_principled(self.scene, self.albedo, self.rough, self.metallic, self.normal, Ip, v,
+                                    self.params, self.spp, self.bounces, s, Ic=self.Ic, Ec=self.Ec)
+            else:
+                c.render(self.scene, self.albedo, self.rough, Ip, v, self.params, self.spp, self.bounces, s,
+                         Ic=self.Ic, Ec=self.Ec)
             c.l1_loss(self.Ic, target, self.dIc, self.terms[12, i:i + 1], scale=self.scale)
-            c.pose_backward(self.scene, self.albedo, self.rough, Ip, v, self.params, self.spp, self.bounces,
-                            adjoint_key(s), self.Ec, self.Ic, self.dIc, self.edge_spp, self.sil_spp,
-                            wrench=self.wrench)
+            if self.principled:
+                c.pose_backward_principled(self.scene, self.albedo, self.rough, self.metallic, self.normal, Ip, v,
+                                           self.params, self.spp, self.bounces, adjoint_key(s), self.Ec, self.Ic,
+                                           self.dIc, self.edge_spp, self.sil_spp, wrench=self.wrench)
+            else:
+                c.pose_backward(self.scene, self.albedo, self.rough, Ip, v, self.params, self.spp, self.bounces,
+                                adjoint_key(s), self.Ec, self.Ic, self.dIc, self.edge_spp, self.sil_spp,
+                                wrench=self.wrench)
         g = project(self.wrench.cpu().numpy(), twists(xi, self.R0, self.t0))
         return float(self.terms[12].sum().cpu()), g
 

@@ -229,3 +229,49 @@ def test_pose_wrench_degenerate_cases():
                        uv=np.zeros((0, 2), np.float32))
     got = _gpu(empty, np.ones((sc.Hc, sc.Wc, 3)), 8, 8)
     assert np.all(got == 0.0)
+
+
+def _gpu_pbr(sc, m, nm, W, edge_spp, sil_spp):
+    torch = need_cuda()
+    g = GpuScene(sc)
+    try:
+        dev = g.ctx.device
+        mt = torch.from_numpy(np.ascontiguousarray(m, np.float32)).to(dev)
+        nt = torch.from_numpy(np.ascontiguousarray(nm, np.float32)).to(dev)
+        Ec = torch.empty((sc.Hc, sc.Wc, 3), dtype=torch.float32, device=dev)
+        Ic, _ = g.ctx.render_principled(g.handle, g.albedo, g.rough, mt, nt, g.Ip, g.view, g.params, sc.spp,
+                                        sc.bounces, sc.seed, Ec=Ec)
+        dIc = torch.from_numpy(np.ascontiguousarray(W, np.float32)).to(dev)
+        w = g.ctx.pose_backward_principled(g.handle, g.albedo, g.rough, mt, nt, g.Ip, g.view, g.params, sc.spp,
+                                           sc.bounces, sc.seed, Ec, Ic, dIc, edge_spp, sil_spp)
+        g.ctx.sync()
+        return w.cpu().numpy()
+    finally:
+        g.close()
+
+
+@pytest.mark.parametrize("case, rtol", [("plane", 2e-3), ("corner", 1e-2)])
+def test_principled_pose_wrench_matches_oracle(orc, case, rtol):
+    """The principled material (metallic and normal maps): the first
+    vertex's BRDF is the principled lobe at the shading normal."""
+    if case == "plane":
+        sc = _plane()
+        m = np.full((8, 8), 0.6, np.float32)
+        nm = np.tile(np.array([0.62, 0.42, 0.9], np.float32), (8, 8, 1))
+    else:
+        sc = scenes.with_principled(_corner())
+        m, nm = sc.metallic, sc.normal
+    W = np.random.default_rng(12).uniform(0.5, 1.5, (sc.Hc, sc.Wc, 3))
+    got = _gpu_pbr(sc, m, nm, W, 16, 16)
+    Ec, _ = orc.render(sc, metallic=m, normal=nm)
+    ref = orc.pose_backward(sc, W * orc.crf_grad(Ec, sc.params), UNIT, 16, 16, metallic=m, normal=nm)
+    scale = np.abs(ref).max()
+    assert scale > 0.0
+    for t, name in enumerate(("interior", "pixel edges", "silhouettes")):
+        err = np.abs(got[t] - ref[t])
+        assert np.all(err <= rtol * np.abs(ref[t]).max() + 1e-6 * scale), (name, got[t], ref[t])
+    # flat maps: the plain material's wrench
+    if case == "plane":
+        flat = _gpu_pbr(sc, np.zeros((8, 8)), np.tile([0.5, 0.5, 1.0], (8, 8, 1)), W, 16, 16)
+        plain = _gpu(sc, W, 16, 16)
+        np.testing.assert_allclose(flat, plain, rtol=1e-4, atol=1e-6 * np.abs(plain).max())
