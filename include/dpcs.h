@@ -225,7 +225,8 @@ dpcs_status dpcs_scene_update(dpcs_ctx *ctx, dpcs_scene scene, const float *vert
  *    side in Morton order), a tree of lower surface-area cost that rays
  *    traverse with fewer node visits.  The upload then synchronises the
  *    stream once per clustering round.  A tree deeper than the traversal
- *    stack (64) is not taken: the radix tree stays.
+ *    stack (64) is not taken, nor one whose build could not have its
+ *    scratch memory or failed a check: the radix tree stays.
  *  DPCS_BVH_LBVH: the Karras radix tree itself.
  * Codes, leaf order and the triangle records are the same for both; refits
  * (dpcs_scene_update, dpcs_scene_transform) keep whichever topology the

@@ -573,6 +573,18 @@ dpcs_status dpcs_scene_upload(dpcs_ctx *c, const float *verts, int32_t V, const 
     const size_t nv = (size_t)(V > 0 ? V : 1);
     sc.V = V;
     sc.bytes = nn * 64 + n * 48 + n * 24 + n * 8 + n * 12 + nv * 8 + nv * 12;
+    // frees what the scene holds, for every failure after its allocation
+    auto release = [&]() {
+        if (sc.nodes || sc.tris) cudaStreamSynchronize(st);  // kernels of a failed build may still use them
+        dev_free(c, sc.nodes, sc.nodes ? nn * 64 : 0);
+        dev_free(c, sc.tris, sc.tris ? n * 48 : 0);
+        dev_free(c, sc.tuv, sc.tuv ? n * 24 : 0);
+        dev_free(c, sc.codes, sc.codes ? n * 4 : 0);
+        dev_free(c, sc.order, sc.order ? n * 4 : 0);
+        dev_free(c, sc.vidx, sc.vidx ? n * 12 : 0);
+        dev_free(c, sc.uv, sc.uv ? nv * 8 : 0);
+        dev_free(c, sc.base, sc.base ? nv * 12 : 0);
+    };
     if ((s = dev_alloc(c, (void **)&sc.nodes, nn * 64, "scene nodes")) ||
         (s = dev_alloc(c, (void **)&sc.tris, n * 48, "scene triangles")) ||
         (s = dev_alloc(c, (void **)&sc.tuv, n * 24, "scene uv")) ||
@@ -581,21 +593,17 @@ dpcs_status dpcs_scene_upload(dpcs_ctx *c, const float *verts, int32_t V, const 
         (s = dev_alloc(c, (void **)&sc.vidx, n * 12, "scene vertex indices")) ||
         (s = dev_alloc(c, (void **)&sc.uv, nv * 8, "scene vertex uv")) ||
         (s = dev_alloc(c, (void **)&sc.base, nv * 12, "scene vertex positions"))) {
-        dev_free(c, sc.nodes, sc.nodes ? nn * 64 : 0);
-        dev_free(c, sc.tris, sc.tris ? n * 48 : 0);
-        dev_free(c, sc.tuv, sc.tuv ? n * 24 : 0);
-        dev_free(c, sc.codes, sc.codes ? n * 4 : 0);
-        dev_free(c, sc.order, sc.order ? n * 4 : 0);
-        dev_free(c, sc.vidx, sc.vidx ? n * 12 : 0);
-        dev_free(c, sc.uv, sc.uv ? nv * 8 : 0);
+        release();
         return s;
     }
     if (T > 0) {
         const size_t vb = (size_t)V * 12, tb = (size_t)T * 12, ub = (size_t)V * 8;
         const size_t up = ((vb + 255) & ~size_t(255)) + ((tb + 255) & ~size_t(255)) + ub;
         if ((s = ensure(c, c->upload, up, "upload staging")) ||
-            (s = ensure(c, c->build, lbvh_scratch_bytes(T), "LBVH scratch")))
+            (s = ensure(c, c->build, lbvh_scratch_bytes(T), "LBVH scratch"))) {
+            release();
             return s;
+        }
         char *p = (char *)c->upload.p;
         float *dv = (float *)p;
         int32_t *dt = (int32_t *)(p + ((vb + 255) & ~size_t(255)));
@@ -603,21 +611,36 @@ dpcs_status dpcs_scene_upload(dpcs_ctx *c, const float *verts, int32_t V, const 
         cudaError_t e = cudaMemcpyAsync(dv, verts, vb, cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(dt, tris, tb, cudaMemcpyHostToDevice, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(du, uv, ub, cudaMemcpyHostToDevice, st);
-        if (e != cudaSuccess) return cuda_fail(c, e, "scene upload");
+        if (e != cudaSuccess) {
+            release();
+            return cuda_fail(c, e, "scene upload");
+        }
         int nl = launch_lbvh_build(dv, V, dt, T, du, sc, c->build.p, c->build.n, st);
-        if ((s = check_launch(c, nl, "LBVH build"))) return s;
-        if (c->bvh_builder == DPCS_BVH_PLOC && T >= 3) {
-            if ((s = ensure(c, c->ploc, ploc_scratch_bytes(T), "PLOC scratch"))) return s;
+        if ((s = check_launch(c, nl, "LBVH build"))) {
+            release();
+            return s;
+        }
+        // the clustering is an optimisation: if it cannot have its scratch
+        // memory or a round's check fails, the radix tree stays (its nodes
+        // are replaced only at the end of a successful build)
+        if (c->bvh_builder == DPCS_BVH_PLOC && T >= 3 &&
+            ensure(c, c->ploc, ploc_scratch_bytes(T), "PLOC scratch") == DPCS_OK) {
             int32_t depth = 0;
-            if ((s = check_launch(c, launch_ploc(sc, c->ploc.p, c->ploc.n, kMaxTreeDepth, st, &depth), "PLOC build")))
-                return s;
+            const int np = launch_ploc(sc, c->ploc.p, c->ploc.n, kMaxTreeDepth, st, &depth);
+            if (np == DPCS_ERR_CUDA) {
+                release();
+                return fail(c, DPCS_ERR_CUDA, "PLOC build: a CUDA call failed");
+            }
+            if (np > 0) c->launches += (uint64_t)np;
         }
         e = cudaMemcpyAsync(sc.vidx, dt, tb, cudaMemcpyDeviceToDevice, st);  // kept for dpcs_scene_update
         if (e == cudaSuccess) e = cudaMemcpyAsync(sc.uv, du, ub, cudaMemcpyDeviceToDevice, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(sc.base, dv, vb, cudaMemcpyDeviceToDevice, st);  // rigid transforms
-        if (e != cudaSuccess) return cuda_fail(c, e, "scene upload");
-        e = cudaStreamSynchronize(st);
-        if (e != cudaSuccess) return cuda_fail(c, e, "LBVH build");
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) {
+            release();
+            return cuda_fail(c, e, "LBVH build");
+        }
     } else {
         sc.root = kEmptyRoot;
     }

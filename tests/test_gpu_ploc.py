@@ -147,3 +147,42 @@ def test_builder_setting_is_checked():
     with pytest.raises(dpcs.DPCSError) as e:
         ctx().set_bvh_builder(7)
     assert e.value.status == dpcs.DPCS_ERR_INVALID_ARG
+
+
+def test_tight_budget_keeps_the_radix_tree_and_failed_uploads_free_their_memory():
+    """The clustering is an optimisation: a context whose budget holds the
+    scene, its staging and the radix tree's scratch but not the clustering's
+    still uploads, with the radix tree.  An upload that fails on the budget
+    frees what it had taken."""
+    need_cuda()
+    verts, tris, uv = scenes.corner_mesh()
+    T, V = len(tris), len(verts)
+    ref = dpcs.Context(0)
+    ref.set_bvh_builder(dpcs.DPCS_BVH_LBVH)
+    h = ref.upload(verts, tris, uv)
+    need = ref.memory_used
+    _, _, child_l, box_l = ref.export(h, T)
+    ref.free(h)
+    ref.close()
+    tight = dpcs.Context(0, hbm_budget_bytes=need + 4096)
+    try:
+        h = tight.upload(verts, tris, uv)  # the default builder, PLOC, cannot have its scratch
+        _, _, child, box = tight.export(h, T)
+        np.testing.assert_array_equal(child, child_l)
+        np.testing.assert_array_equal(box.view(np.uint32), box_l.view(np.uint32))
+        tight.free(h)
+    finally:
+        tight.close()
+    scene_bytes = (T - 1) * 64 + T * 48 + T * 24 + T * 8 + T * 12 + V * 8 + V * 12
+    probe = dpcs.Context(0)
+    base = probe.memory_used  # the context's own status word and counters
+    probe.close()
+    small = dpcs.Context(0, hbm_budget_bytes=base + scene_bytes + 16)  # the scene fits, its staging does not
+    try:
+        assert small.memory_used == base
+        with pytest.raises(dpcs.DPCSError) as e:
+            small.upload(verts, tris, uv)
+        assert e.value.status == dpcs.DPCS_ERR_OOM
+        assert small.memory_used == base
+    finally:
+        small.close()
