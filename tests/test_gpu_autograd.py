@@ -1,6 +1,7 @@
 """The renderer as a torch.autograd.Function: its backward equals the direct
 path-replay call, agrees with central finite differences of the GPU forward
-on smooth parameters, and drives a torch optimiser."""
+on smooth parameters, and drives a torch optimiser; a camera pose given to it
+gets the pose adjoint's gradient."""
 import numpy as np
 import pytest
 
@@ -135,3 +136,37 @@ def test_principled_backward_equals_render_backward_principled():
             np.testing.assert_allclose(a, b, rtol=1e-4, atol=1e-6 * np.abs(b).max())
     finally:
         g.close()
+
+
+def test_pose_input_gradient_is_the_pose_adjoint():
+    """A camera pose given to the wrapper: the forward renders the scene moved
+    to it, and its gradient is the pose adjoint's wrench projected on the
+    pose parameters' twists, under the adjoint's own key."""
+    torch = need_cuda()
+    from paper_2503_12174_gb300 import pose
+
+    sc = scenes.corner(res=24, tex=16, spp=8, bounces=2, seed=3)
+    R0, t0 = pose.rotation([0.01, -0.02, 0.015]), np.array([0.01, 0.0, -0.02])
+    x0 = np.array([0.004, -0.003, 0.002, 0.005, 0.0, -0.004])
+    W = torch.from_numpy(np.random.default_rng(9).uniform(0.5, 1.5, (sc.Hc, sc.Wc, 3)).astype(np.float32)).cuda()
+    g = GpuScene(sc)
+    try:
+        xi = torch.tensor(x0, dtype=torch.float64, requires_grad=True)
+        Ic = autograd.render(g.ctx, g.handle, g.albedo, g.rough, g.Ip, g.view, g.params, sc.spp, sc.bounces, sc.seed,
+                             pose=xi, pose_R0=R0, pose_t0=t0, edge_spp=8, sil_spp=8)
+        (Ic * W).sum().backward()
+        got = xi.grad.numpy().copy()
+        # the same by hand
+        R, t = pose.pose_of(x0, R0, t0)
+        g.ctx.transform(g.handle, R, t)
+        v = pose.posed_view(g.view, R, t)
+        Ec = torch.empty_like(Ic)
+        Ic2, _ = g.ctx.render(g.handle, g.albedo, g.rough, g.Ip, v, g.params, sc.spp, sc.bounces, sc.seed, Ec=Ec)
+        np.testing.assert_array_equal(Ic2.cpu().numpy(), Ic.detach().cpu().numpy())
+        Wr = g.ctx.pose_backward(g.handle, g.albedo, g.rough, g.Ip, v, g.params, sc.spp, sc.bounces,
+                                 pose.adjoint_key(sc.seed), Ec, Ic2, W, 8, 8)
+        ref = pose.project(Wr.cpu().numpy(), pose.twists(x0, R0, t0))
+    finally:
+        g.close()
+    assert np.abs(ref).max() > 0.0
+    np.testing.assert_allclose(got, ref, rtol=1e-12, atol=0.0)
