@@ -1097,7 +1097,7 @@ def main():
                                 "qdeadline_relight_p99": x.get("server_quanta_deadline_policy", {}).get("relight_p99_ms"),
                                 "qdeadline_comp_p99": x.get("server_quanta_deadline_policy", {}).get("compensation_p99_ms")}
                                for x in serving_out["load_sweep"]]
-        line["summary"] = summ
+        line["summary"] = short_figures(summ)
         print(json.dumps(line), flush=True)
     ctx.free(h)
     ctx.free(hc)
@@ -1105,6 +1105,19 @@ def main():
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def short_figures(x):
+    """x with floats rounded to 4 significant digits and None entries of
+    dicts dropped (the summary is repeated at the end of the line to be read
+    from its tail, so it is kept short)."""
+    if isinstance(x, float):
+        return float(f"{x:.4g}")
+    if isinstance(x, dict):
+        return {k: short_figures(v) for k, v in x.items() if v is not None}
+    if isinstance(x, list):
+        return [short_figures(v) for v in x]
+    return x
 
 
 if __name__ == "__main__":
