@@ -5,6 +5,8 @@
 * integrating sphere: inside a closed sphere with Lambertian albedo a, every
   point receives the same indirect irradiance Phi / A * sum_n a^n, Phi the
   projector's power (form factor of a sphere);
+* white furnace: the same sphere with albedo 1 and no specular lobe absorbs
+  nothing, so every further path vertex adds the same Phi / (pi A);
 * linearity in Ep before the CRF; monotonicity in the bounce count;
   dark projector, empty scene, projector behind the surface.
 """
@@ -76,6 +78,26 @@ def test_integrating_sphere(orc):
     # pixels are independent estimates of the same value
     se = ind.std() / math.sqrt(ind.size)
     assert abs(ind.mean() - expect) < 4 * se + 0.015 * expect, (ind.mean(), expect, se)
+
+
+@pytest.mark.slow
+def test_white_furnace(orc):
+    """Albedo 1, Lambert only: after the first bounce the light is spread
+    uniformly over the sphere and nothing is absorbed, so vertex b >= 2 of
+    every path adds Phi / (pi A) to the pixel's mean radiance.  Renders with
+    B and B + 1 vertices share their first B vertices (the Philox counters
+    are per vertex), so their difference is vertex B + 1's contribution alone."""
+    sc = scenes.sphere(subdiv=3, res=32, spp=96, bounces=4, albedo=1.0, ip_value=0.8)
+    sc = sc.replace(Kp=scenes.intrinsics(32, 32, 110.0))
+    E = [orc.render(sc.replace(bounces=b))[0][..., 0].ravel() for b in (1, 2, 3, 4)]
+    V = sc.verts.astype(np.float64)[sc.tris]
+    A = 0.5 * np.linalg.norm(np.cross(V[:, 1] - V[:, 0], V[:, 2] - V[:, 0]), axis=1).sum()
+    expect = _projector_power(sc, 1.0, 0.8) / (math.pi * A)
+    for b in range(1, 4):
+        inc = E[b] - E[b - 1]
+        assert np.all(inc >= 0.0)
+        se = inc.std() / math.sqrt(inc.size)
+        assert abs(inc.mean() - expect) < 4 * se + 0.015 * expect, (b + 1, inc.mean(), expect, se)
 
 
 def test_linear_in_projector_image(orc):
