@@ -154,3 +154,61 @@ def test_unit_tap_diagnostic_counts_each_contribution_once_per_tap(orc):
     # the diagnostic is off again for the next call
     g2 = orc.render_backward(sc, W)
     np.testing.assert_allclose(g2["dIp"], g["dIp"], rtol=1e-12)
+
+
+def test_adjoint_projector_and_gains_euler_identities(orc):
+    """Homogeneity, checked without finite differences.  With no clipping,
+    channel j of Ic is homogeneous of degree gamma_p,j * gamma_c,j in channel
+    j of the projector image (Ep = Gp Ip^gamma_p per texel, Eq. 1; the paths
+    do not depend on Ip; Ic = (Gc w Ec)^gamma_c, Eq. 5), and of degree
+    gamma_c,j in Gp, in Gc and in w_j.  Euler's theorem then fixes, per seed
+    and exactly up to rounding, sum_k Ip_kj dL/dIp_kj = gamma_p,j gamma_c,j L_j
+    and Gp dL/dGp = Gc dL/dGc = sum_j gamma_c,j L_j, w_j dL/dw_j =
+    gamma_c,j L_j, for L = sum W Ic and L_j its channel-j part.  A wrong
+    exponent or a dropped factor in the PRF or CRF adjoint breaks one of them."""
+    sc = _scene(bounces=3)
+    p = sc.params
+    W = np.random.default_rng(11).normal(size=(sc.Hc, sc.Wc, 3))
+    _, Ic = orc.render(sc)
+    Lj = (W * Ic).sum(axis=(0, 1))
+    g = orc.render_backward(sc, W)
+    gp, gc = np.asarray(p.gamma_p, np.float64), np.asarray(p.gamma_c, np.float64)
+    Ip = sc.Ip.astype(np.float64)
+    lhs = (Ip * g["dIp"]).sum(axis=(0, 1))
+    np.testing.assert_allclose(lhs, gp * gc * Lj, rtol=1e-10)
+    dP = g["dparams"]
+    total = float((gc * Lj).sum())
+    assert abs(total) > 1e-3 * np.abs(Lj).sum()
+    np.testing.assert_allclose(p.gain_p * dP[3], total, rtol=1e-10)
+    np.testing.assert_allclose(p.gain_c * dP[7], total, rtol=1e-10)
+    np.testing.assert_allclose(np.asarray(p.wb) * dP[8:11], gc * Lj, rtol=1e-10)
+
+
+def test_adjoint_albedo_euler_identity(orc):
+    """With the Lambert lobe alone (ks = 0) each path's throughput is the
+    product of the albedos at its vertices (the cosine-sampling weight is
+    rho), so the contribution of vertex b is homogeneous of degree b in the
+    albedo texels of its channel.  Renders with 1..B vertices share their
+    first vertices (per-vertex Philox counters), so E_b, vertex b's part of
+    Ec, is the difference of two renders.  Euler's theorem then gives, per
+    seed and exactly up to rounding,
+        sum_k rho_kj dL/drho_kj = sum_pixels W_j g'(Ec_j) sum_b b E_b,j
+    with g' = gamma_c Ic / Ec the derivative of Eq. 5.  Dropping the
+    continuation term of the albedo adjoint turns b into 1 and fails it."""
+    sc = _scene(bounces=3)
+    sc = sc.replace(params=_with(sc.params, ks=0.0))
+    W = np.random.default_rng(12).normal(size=(sc.Hc, sc.Wc, 3))
+    E = [np.zeros((sc.Hc, sc.Wc, 3))] + [orc.render(sc, bounces=b)[0] for b in (1, 2, 3)]
+    Ec, Ic = orc.render(sc)
+    np.testing.assert_array_equal(Ec, E[3])
+    weighted = sum(b * (E[b] - E[b - 1]) for b in (1, 2, 3))
+    gc = np.asarray(sc.params.gamma_c, np.float64)
+    gprime = np.where(Ec > 0, gc * Ic / np.where(Ec > 0, Ec, 1.0), 0.0)
+    expect = (W * gprime * weighted).sum(axis=(0, 1))
+    g = orc.render_backward(sc, W)
+    lhs = (sc.albedo.astype(np.float64) * g["dalbedo"]).sum(axis=(0, 1))
+    assert np.all(np.abs(expect) > 0)
+    np.testing.assert_allclose(lhs, expect, rtol=1e-10)
+    # the identity separates the vertices: the undifferentiated sum is far off
+    plain = (W * gprime * E[3]).sum(axis=(0, 1))
+    assert np.all(np.abs(plain - expect) > 1e-3 * np.abs(expect))
