@@ -23,6 +23,11 @@ the scene stays there after the call) and renders with the posed view, and
 the backward gives its gradient by the pose adjoint (``dpcs_pose_backward``,
 ``edge_spp`` / ``sil_spp`` samples per pixel edge / silhouette edge, its paths
 under ``pose.adjoint_key(seed)``) projected on the parameters' twists.
+
+The backward re-traces the scene as it is when the backward runs, so moving
+the scene between a render and its backward (``Context.update``,
+``Context.transform``, or another render with a pose) makes that backward
+raise instead of returning the gradient of another geometry.
 """
 from __future__ import annotations
 
@@ -69,6 +74,7 @@ def _function():
             else:
                 Ic, _ = ctx.render(scene, albedo, rough, Ip, view, p, spp, bounces, seed, Ec=Ec)
             fctx.save_for_backward(albedo, rough, Ip, Ec, Ic, metallic, normal)
+            fctx.moves = ctx.scene_moves(scene)
             fctx.meta = (ctx, scene, view, p, spp, bounces, seed, pvec is not None, principled)
             fctx.pose = (xi, frame, edge_spp, sil_spp, pose_xi)
             return Ic
@@ -77,6 +83,9 @@ def _function():
         def backward(fctx, dIc):
             albedo, rough, Ip, Ec, Ic, metallic, normal = fctx.saved_tensors
             ctx, scene, view, p, spp, bounces, seed, has_pvec, principled = fctx.meta
+            if ctx.scene_moves(scene) != fctx.moves:
+                raise RuntimeError("dpcs autograd: the scene was moved (update or transform, another posed render "
+                                   "included) after this render; its backward would re-trace the moved scene")
             need = fctx.needs_input_grad
             dA = torch.zeros_like(albedo) if need[0] else None
             dR = torch.zeros_like(rough) if need[1] else None

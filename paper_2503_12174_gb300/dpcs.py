@@ -469,6 +469,7 @@ class Context:
     def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, lib=None):
         import torch
 
+        self._moves = {}  # scene -> how many updates and transforms this object has applied
         self.lib = lib if lib is not None else load_library()
         self.device = torch.device("cuda", device)
         h = _P()
@@ -559,6 +560,7 @@ class Context:
         verts = np.ascontiguousarray(verts, np.float32)
         st = self.lib.dpcs_scene_update(self.handle, scene, verts.ctypes.data_as(_P), len(verts), _stream(stream))
         self.check(st, "scene_update")
+        self._moves[scene] = self._moves.get(scene, 0) + 1
 
     def transform(self, scene: int, R, t, stream=None):
         """dpcs_scene_transform: the scene's stored vertex positions mapped by
@@ -568,6 +570,14 @@ class Context:
         st = self.lib.dpcs_scene_transform(self.handle, scene, Rf.ctypes.data_as(_P), tf.ctypes.data_as(_P),
                                            _stream(stream))
         self.check(st, "scene_transform")
+        self._moves[scene] = self._moves.get(scene, 0) + 1
+
+    def scene_moves(self, scene: int) -> int:
+        """How many times update() or transform() has moved the scene's
+        vertices through this object.  A path replay re-traces the scene as it
+        is when the replay runs, so the autograd wrapper checks that this count
+        is the same at a render and at its backward."""
+        return self._moves.get(scene, 0)
 
     def free(self, scene: int):
         self.check(self.lib.dpcs_scene_free(self.handle, scene), "scene_free")
