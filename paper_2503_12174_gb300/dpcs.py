@@ -916,6 +916,7 @@ class Server:
         ctx.check(self.lib.dpcs_serve_create(ctx.handle, ctypes.byref(cfg), ctypes.byref(h)), "serve_create")
         self.handle = h
         self._keep = {}
+        self._proj = {}  # scene slot -> projector size (Hp, Wp), to check the host buffers of requests
 
     def close(self):
         if getattr(self, "handle", None):
@@ -940,19 +941,44 @@ class Server:
                                            ctypes.byref(view), ctypes.byref(params), int(bounces), ctypes.byref(slot))
         self.ctx.check(st, "serve_add_scene")
         self._keep[("scene", slot.value)] = (albedo, rough)
+        self._proj[slot.value] = (int(view.Hp), int(view.Wp))
         return slot.value
 
     def submit(self, kind: int, scene: int, Hc: int, Wc: int, spp: int, seed: int, Ip, Ic_out, target=None,
                Ip_out=None, steps: int = 0, lr: float = 1e-2) -> int:
         """Ip, target, Ic_out, Ip_out: contiguous float32 host arrays (pinned
-        memory keeps the server's copies asynchronous)."""
-        def hp(a):
+        memory keeps the server's copies asynchronous).  The server copies
+        whole images to and from these addresses, which the library cannot
+        check, so their sizes are checked here (ValueError): Ic_out and target
+        Hc x Wc x 3, Ip and Ip_out the scene's projector size x 3.  Requests
+        whose sizes or scene the library itself refuses are passed on for it to
+        refuse (DPCSError)."""
+        def hp(a, name, n):
             if a is None:
                 return None
-            return ctypes.c_void_p(a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data)
+            if hasattr(a, "data_ptr"):  # torch tensor
+                import torch
+
+                ok = (a.device.type == "cpu" and a.dtype == torch.float32 and a.is_contiguous()
+                      and (n is None or a.numel() == n))
+                ptr = a.data_ptr()
+            elif isinstance(a, np.ndarray):
+                ok = a.dtype == np.float32 and a.flags.c_contiguous and (n is None or a.size == n)
+                ptr = a.ctypes.data
+            else:
+                ok, ptr = False, None
+            if not ok:
+                raise ValueError(f"serve_submit: {name} must be a contiguous float32 host array"
+                                 + ("" if n is None else f" of {n} elements"))
+            return ctypes.c_void_p(ptr)
+
+        img = int(Hc) * int(Wc) * 3 if int(Hc) > 0 and int(Wc) > 0 else None
+        proj = self._proj.get(int(scene))
+        npj = None if proj is None else proj[0] * proj[1] * 3
 
         req = DpcsRequest(int(kind), int(scene), int(Hc), int(Wc), int(spp), int(seed) & (2**64 - 1), int(steps),
-                          float(lr), hp(Ip), hp(target), hp(Ic_out), hp(Ip_out))
+                          float(lr), hp(Ip, "Ip", npj), hp(target, "target", img), hp(Ic_out, "Ic_out", img),
+                          hp(Ip_out, "Ip_out", npj))
         rid = ctypes.c_uint64()
         self.ctx.check(self.lib.dpcs_serve_submit(self.handle, ctypes.byref(req), ctypes.byref(rid)), "serve_submit")
         self._keep[rid.value] = (Ip, target, Ic_out, Ip_out)

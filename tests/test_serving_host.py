@@ -57,3 +57,85 @@ def test_request_view_keeps_the_field_of_view():
         np.testing.assert_allclose(Kc[:2] / side, K0[:2] / 256, rtol=1e-6)
         np.testing.assert_array_equal(Kc[2], K0[2])
         np.testing.assert_array_equal(np.array(v.Kp, np.float32), np.asarray(sc.Kp, np.float32).ravel())
+
+
+class _FakeServeLib:
+    """Stands in for libdpcs's serving entry points: records the requests it
+    is given and refuses an unknown scene slot as the library does."""
+
+    def __init__(self):
+        self.requests = []
+
+    def dpcs_serve_create(self, ctx, cfg, out):
+        return dpcs.DPCS_OK
+
+    def dpcs_serve_destroy(self, h):
+        return dpcs.DPCS_OK
+
+    def dpcs_serve_add_scene(self, h, scene, alb, rough, Ht, Wt, view, params, bounces, slot):
+        slot._obj.value = 0
+        return dpcs.DPCS_OK
+
+    def dpcs_serve_submit(self, h, req, rid):
+        r = req._obj
+        self.requests.append((r.scene, r.Hc, r.Wc, r.Ip, r.Ic_out, r.target, r.Ip_out))
+        if r.scene != 0:
+            return dpcs.DPCS_ERR_NOT_FOUND
+        rid._obj.value = len(self.requests)
+        return dpcs.DPCS_OK
+
+
+class _FakeCtx:
+    def __init__(self):
+        import torch
+
+        self.lib = _FakeServeLib()
+        self.handle = None
+        self.device = torch.device("cpu")
+
+    def check(self, status, what):
+        if status != dpcs.DPCS_OK:
+            raise dpcs.DPCSError(status, what)
+
+
+def test_submit_checks_host_buffer_sizes():
+    """The server copies whole images to and from the request's host
+    buffers, which the library cannot check: the binding refuses a buffer of
+    the wrong size, type or layout before the library sees the request."""
+    torch = pytest.importorskip("torch")
+    ctx = _FakeCtx()
+    srv = dpcs.Server(ctx)
+    view = dpcs.DpcsView()
+    view.Hc, view.Wc, view.Hp, view.Wp = 32, 32, 20, 24
+    slot = srv.add_scene(1, torch.zeros((4, 4, 3)), torch.zeros((4, 4)), view, dpcs.DpcsParams(), 2)
+    Ip = torch.zeros((20, 24, 3))
+    Ic = torch.zeros((16, 12, 3))
+    rid = srv.submit(dpcs.DPCS_REQ_RELIGHT, slot, 16, 12, 8, 1, Ip, Ic)
+    assert rid == 1 and ctx.lib.requests[-1][3] == Ip.data_ptr() and ctx.lib.requests[-1][4] == Ic.data_ptr()
+    tgt, Ipo = np.zeros((16, 12, 3), np.float32), np.zeros((20, 24, 3), np.float32)
+    srv.submit(dpcs.DPCS_REQ_COMPENSATE, slot, 16, 12, 8, 1, Ip, Ic, target=tgt, Ip_out=Ipo, steps=2)
+    assert ctx.lib.requests[-1][5] == tgt.ctypes.data and ctx.lib.requests[-1][6] == Ipo.ctypes.data
+    bad = [
+        dict(Ip=torch.zeros((20, 23, 3))),                        # projector image of another size
+        dict(Ic_out=torch.zeros((16, 11, 3))),                    # result buffer too small
+        dict(Ic_out=torch.zeros((16, 12, 3), dtype=torch.float64)),
+        dict(Ic_out=torch.zeros((12, 16, 3)).transpose(0, 1)),    # not contiguous
+        dict(target=np.zeros((16, 12, 2), np.float32)),
+        dict(Ip_out=np.zeros((20, 24, 3), np.float64)),
+        dict(Ip=[0.0] * (20 * 24 * 3)),                           # not an array the request can point into
+    ]
+    n = len(ctx.lib.requests)
+    for kw in bad:
+        args = dict(Ip=Ip, Ic_out=Ic, target=tgt, Ip_out=Ipo)
+        args.update(kw)
+        with pytest.raises(ValueError):
+            srv.submit(dpcs.DPCS_REQ_COMPENSATE, slot, 16, 12, 8, 1, args["Ip"], args["Ic_out"],
+                       target=args["target"], Ip_out=args["Ip_out"], steps=2)
+    assert len(ctx.lib.requests) == n  # none of them reached the library
+    # sizes and scenes the library refuses itself are passed on to it
+    with pytest.raises(dpcs.DPCSError) as e:
+        srv.submit(dpcs.DPCS_REQ_RELIGHT, 5, 16, 12, 8, 1, Ip, Ic)
+    assert e.value.status == dpcs.DPCS_ERR_NOT_FOUND
+    srv.submit(dpcs.DPCS_REQ_RELIGHT, slot, 0, 12, 8, 1, Ip, Ic)
+    assert ctx.lib.requests[-1][1] == 0
+    srv.close()
