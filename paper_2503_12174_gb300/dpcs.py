@@ -470,6 +470,7 @@ class Context:
         import torch
 
         self._moves = {}  # scene -> how many updates and transforms this object has applied
+        self._ntris = {}  # scene -> triangle count, to size the host arrays export() hands to the library
         self.lib = lib if lib is not None else load_library()
         self.device = torch.device("cuda", device)
         h = _P()
@@ -553,6 +554,7 @@ class Context:
         st = self.lib.dpcs_scene_upload(self.handle, verts.ctypes.data_as(_P), len(verts), tris.ctypes.data_as(_P),
                                len(tris), uv.ctypes.data_as(_P), _stream(stream), ctypes.byref(out))
         self.check(st, "scene_upload")
+        self._ntris[out.value] = len(tris)
         return out.value
 
     def update(self, scene: int, verts, stream=None):
@@ -581,8 +583,16 @@ class Context:
 
     def free(self, scene: int):
         self.check(self.lib.dpcs_scene_free(self.handle, scene), "scene_free")
+        self._ntris.pop(scene, None)
+        self._moves.pop(scene, None)
 
     def export(self, scene: int, T: int):
+        """The scene's tree in host arrays sized for T triangles.  The library
+        fills them for the scene's own triangle count, so T must be that count
+        (checked against the upload)."""
+        known = self._ntris.get(scene)
+        if known is not None and int(T) != known:
+            raise ValueError(f"export: scene {scene} has {known} triangles, not {T}")
         codes = np.zeros(T, np.uint32)
         order = np.zeros(T, np.int32)
         child = np.zeros((max(T - 1, 0), 2), np.int32)

@@ -47,3 +47,53 @@ def test_principled_maps_are_seeded_and_in_range():
     n = 2.0 * normal.astype(np.float64) - 1.0
     np.testing.assert_allclose(np.linalg.norm(n, axis=-1), 1.0, atol=1e-6)  # unit tangent-space normals
     assert n[..., 2].min() > 0.5  # tilted, but facing out of the surface
+
+
+class _FakeSceneLib:
+    """Stands in for libdpcs's context and scene entry points on the CPU."""
+
+    def __init__(self):
+        self.exports = 0
+
+    def dpcs_create(self, device, budget, out):
+        out._obj.value = 1
+        return 0
+
+    def dpcs_destroy(self, h):
+        return 0
+
+    def dpcs_last_error(self, h):
+        return b""
+
+    def dpcs_scene_upload(self, h, verts, V, tris, T, uv, stream, out):
+        out._obj.value = 7
+        return 0
+
+    def dpcs_scene_free(self, h, scene):
+        return 0
+
+    def dpcs_scene_export(self, h, scene, codes, order, child, box):
+        self.exports += 1
+        return 0
+
+
+def test_export_sizes_its_arrays_for_the_uploaded_triangle_count(monkeypatch):
+    """The library fills export()'s host arrays for the scene's own triangle
+    count, so the binding refuses any other count before calling it."""
+    import pytest
+
+    from paper_2503_12174_gb300 import dpcs, scenes
+
+    monkeypatch.setattr(dpcs, "_stream", lambda stream: None)  # no CUDA stream on the CPU
+    lib = _FakeSceneLib()
+    ctx = dpcs.Context(0, lib=lib)
+    verts, tris, uv = scenes.corner_mesh()
+    h = ctx.upload(verts, tris, uv)
+    codes, order, child, box = ctx.export(h, len(tris))
+    assert codes.shape == (len(tris),) and child.shape == (len(tris) - 1, 2) and lib.exports == 1
+    for T in (len(tris) - 1, len(tris) + 1):
+        with pytest.raises(ValueError):
+            ctx.export(h, T)
+    assert lib.exports == 1
+    ctx.free(h)
+    ctx.close()
