@@ -547,9 +547,16 @@ class Context:
 
     # -- scenes ----------------------------------------------------------------
     def upload(self, verts, tris, uv, stream=None) -> int:
+        """verts (V, 3), tris (T, 3) vertex indices, uv (V, 2).  The library
+        reads V x 3, T x 3 and V x 2 values from these host arrays, so their
+        shapes are checked here."""
         verts = np.ascontiguousarray(verts, np.float32)
         tris = np.ascontiguousarray(tris, np.int32)
         uv = np.ascontiguousarray(uv, np.float32)
+        if verts.ndim != 2 or verts.shape[1] != 3 or tris.ndim != 2 or tris.shape[1] != 3 or \
+                uv.shape != (verts.shape[0], 2):
+            raise ValueError(f"upload: expected verts (V, 3), tris (T, 3) and uv (V, 2), got {verts.shape}, "
+                             f"{tris.shape} and {uv.shape}")
         out = ctypes.c_uint64()
         st = self.lib.dpcs_scene_upload(self.handle, verts.ctypes.data_as(_P), len(verts), tris.ctypes.data_as(_P),
                                len(tris), uv.ctypes.data_as(_P), _stream(stream), ctypes.byref(out))
@@ -560,6 +567,8 @@ class Context:
     def update(self, scene: int, verts, stream=None):
         """New positions for the scene's vertices (same count); refits the tree."""
         verts = np.ascontiguousarray(verts, np.float32)
+        if verts.ndim != 2 or verts.shape[1] != 3:
+            raise ValueError(f"update: expected verts (V, 3), got {verts.shape}")
         st = self.lib.dpcs_scene_update(self.handle, scene, verts.ctypes.data_as(_P), len(verts), _stream(stream))
         self.check(st, "scene_update")
         self._moves[scene] = self._moves.get(scene, 0) + 1

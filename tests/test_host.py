@@ -77,9 +77,10 @@ class _FakeSceneLib:
         return 0
 
 
-def test_export_sizes_its_arrays_for_the_uploaded_triangle_count(monkeypatch):
+def test_host_arrays_the_library_reads_or_fills_are_checked(monkeypatch):
     """The library fills export()'s host arrays for the scene's own triangle
-    count, so the binding refuses any other count before calling it."""
+    count, and reads V x 3 positions, T x 3 indices and V x 2 UVs at upload:
+    the binding refuses other sizes before calling it."""
     import pytest
 
     from paper_2503_12174_gb300 import dpcs, scenes
@@ -95,5 +96,11 @@ def test_export_sizes_its_arrays_for_the_uploaded_triangle_count(monkeypatch):
         with pytest.raises(ValueError):
             ctx.export(h, T)
     assert lib.exports == 1
+    # the library reads V x 3, T x 3 and V x 2 values: other shapes never reach it
+    for bad in ((verts.ravel(), tris, uv), (verts, tris[:, :2], uv), (verts, tris, uv[:-1]), (verts[:, :2], tris, uv)):
+        with pytest.raises(ValueError):
+            ctx.upload(*bad)
+    with pytest.raises(ValueError):
+        ctx.update(h, verts.ravel())
     ctx.free(h)
     ctx.close()
