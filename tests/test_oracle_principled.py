@@ -14,7 +14,9 @@ finite differences of the FP64 forward.
 * the adjoint's metallic, albedo, roughness and normal-map gradients match
   central differences wherever those parameters do not move sampled paths;
 * the sampler's mean weight f cos / pdf equals the quadrature of f cos
-  with metallic on, and stays <= 1.
+  with metallic on, and stays <= 1;
+* without the specular lobe, the albedo and metallic adjoints satisfy the
+  homogeneity identities of Euler's theorem exactly, per seed.
 """
 import math
 
@@ -261,3 +263,32 @@ def test_principled_mean_weight_is_directional_albedo(orc, m):
     se = acc.std(0) / np.sqrt(N)
     assert np.all(np.abs(acc.mean(0) - albedo) < 4 * se + 1e-3), (acc.mean(0), albedo)
     assert np.all(albedo <= 1.0)
+
+
+def test_adjoint_albedo_and_metallic_homogeneity_without_the_specular_lobe(orc):
+    """With ks = 0 the principled BRDF is (1 - m) rho / pi at the shading
+    normal and each vertex's sampling weight is (1 - m) rho, so vertex b's
+    contribution is homogeneous of degree b in the albedo texels of its
+    channel and in the texels of 1 - m (bilinear weights sum to 1).  Renders
+    with 1..B vertices share their first vertices, so E_b, vertex b's part of
+    Ec, is a difference of renders, and Euler's theorem gives per seed, with
+    the normal map on and exactly up to rounding,
+        sum rho dL/drho = -sum (1 - m) dL/dm = sum W g'(Ec) sum_b b E_b
+    (per channel for the albedo, over the channels for m; g' = gamma_c Ic / Ec)."""
+    import dataclasses
+
+    sc = _principled_scene(bounces=3)
+    sc = sc.replace(params=dataclasses.replace(sc.params, ks=0.0))
+    assert sc.metallic.max() > 0.2 and np.abs(sc.normal - [0.5, 0.5, 1.0]).max() > 0.05
+    W = np.random.default_rng(13).normal(size=(sc.Hc, sc.Wc, 3))
+    E = [np.zeros((sc.Hc, sc.Wc, 3))] + [orc.render(sc, bounces=b)[0] for b in (1, 2, 3)]
+    Ec, Ic = orc.render(sc)
+    np.testing.assert_array_equal(Ec, E[3])
+    gc = np.asarray(sc.params.gamma_c, np.float64)
+    gprime = np.where(Ec > 0, gc * Ic / np.where(Ec > 0, Ec, 1.0), 0.0)
+    expect = (W * gprime * sum(b * (E[b] - E[b - 1]) for b in (1, 2, 3))).sum(axis=(0, 1))
+    g = orc.render_backward(sc, W)
+    rho_side = (sc.albedo.astype(np.float64) * g["dalbedo"]).sum(axis=(0, 1))
+    np.testing.assert_allclose(rho_side, expect, rtol=1e-10)
+    m_side = -((1.0 - sc.metallic.astype(np.float64)) * g["dmetallic"]).sum()
+    np.testing.assert_allclose(m_side, expect.sum(), rtol=1e-10)
