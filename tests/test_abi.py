@@ -81,3 +81,57 @@ def test_probe_library_exports_its_header_and_the_product_library_has_no_probes(
     assert all(hasattr(plib, n) for n in names)
     lib = dpcs.load_library()
     assert not any(hasattr(lib, n) for n in names)
+
+
+def _prototypes():
+    """{name: (return type, [parameter types])} of every function include/dpcs.h declares."""
+    src = open(HDR).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"#[^\n]*", "", src)
+    out = {}
+    for ret, name, params in re.findall(r"([A-Za-z_][\w \t\*]*?)\b(dpcs_[a-z0-9_]+)\s*\(([^()]*)\)\s*;", src):
+        ps = [p.strip() for p in params.split(",") if p.strip() and p.strip() != "void"]
+        out[name] = (ret.strip(), ps)
+    return out
+
+
+_C_INT = {"int": 4, "int32_t": 4, "uint32_t": 4, "int64_t": 8, "uint64_t": 8, "size_t": 8, "dpcs_scene": 8,
+          "dpcs_status": 4}
+
+
+def _c_kind(decl):
+    """('ptr',), ('int', bytes) or ('float', bytes) of a C declaration such as
+    'const float *Ip', 'const float R[9]', 'int32_t Ht' or 'dpcs_status'."""
+    if "*" in decl or "[" in decl:
+        return ("ptr",)
+    words = [w for w in decl.replace("const", " ").split()]
+    base = words[0]
+    if base == "float":
+        return ("float", 4)
+    if base == "double":
+        return ("float", 8)
+    return ("int", _C_INT[base])
+
+
+def _ctypes_kind(t):
+    if t in (ctypes.c_void_p, ctypes.c_char_p) or hasattr(t, "_type_") and isinstance(t._type_, type):
+        return ("ptr",)
+    if t in (ctypes.c_float, ctypes.c_double):
+        return ("float", ctypes.sizeof(t))
+    return ("int", ctypes.sizeof(t))
+
+
+def test_binding_signatures_match_the_header():
+    """Every ctypes signature the binding sets has the header's parameter
+    count and, position by position, the same kind of argument (pointer,
+    integer of the same width, float or double) and return type, so no call
+    passes arguments the library reads differently."""
+    protos = _prototypes()
+    assert set(dpcs._SIGS) <= set(protos), sorted(set(dpcs._SIGS) - set(protos))
+    assert set(dpcs.EXPORTED) <= set(dpcs._SIGS), sorted(set(dpcs.EXPORTED) - set(dpcs._SIGS))
+    for name, (res, args) in dpcs._SIGS.items():
+        ret, params = protos[name]
+        assert len(args) == len(params), (name, len(args), len(params))
+        assert _ctypes_kind(res) == _c_kind(ret), (name, ret, res)
+        for i, (a, p) in enumerate(zip(args, params)):
+            assert _ctypes_kind(a) == _c_kind(p), (name, i, p, a)
