@@ -115,14 +115,15 @@ def test_adjoint_roughness_unbiased_multi_bounce(orc):
                     params=_with(sc.params, gamma_c=(1.0, 1.0, 1.0)))
     W = np.ones((sc.Hc, sc.Wc, 3))  # total image brightness
     h, n = 0.05, 1200
+    nt = 2  # 64 pixels per call: more threads cost more to start than they save
     for B in (2, 3):
         s2 = sc.replace(bounces=B)
         adj, fd = np.zeros(n), np.zeros(n)
         for k in range(n):
             seed = 5000 + k
-            adj[k] = orc.render_backward(s2, W, seed=seed)["drough"].sum()  # d/d(uniform roughness)
-            lp = float((W * orc.render(s2, rough=s2.rough + h, seed=seed)[1]).sum())
-            lm = float((W * orc.render(s2, rough=s2.rough - h, seed=seed)[1]).sum())
+            adj[k] = orc.render_backward(s2, W, seed=seed, nthreads=nt)["drough"].sum()  # d/d(uniform roughness)
+            lp = float((W * orc.render(s2, rough=s2.rough + h, seed=seed, nthreads=nt)[1]).sum())
+            lm = float((W * orc.render(s2, rough=s2.rough - h, seed=seed, nthreads=nt)[1]).sum())
             adj[k], fd[k] = adj[k], (lp - lm) / (2 * h)
         se = np.sqrt(adj.var() / n + fd.var() / n)
         assert abs(adj.mean()) > 10 * se  # the gradient is resolved, not noise
